@@ -1,0 +1,227 @@
+/*
+ * qaoa.h -- C ABI of libqaoa: batched state-vector simulation of depth-p QAOA on sub-QUBOs and
+ * the DQAOA decompose / merge steps around it, for NVIDIA GB300 (sm_103a).
+ *
+ * Method (arXiv 2506.10531, "GPU-Accelerated Distributed QAOA on Large-scale HPC Ecosystems"):
+ *   - Section IV, Eq. 1-2: a QUBO min_x x^T Q x is mapped to the diagonal problem Hamiltonian
+ *     H|z> = E(z)|z>, E(z) = z^T Q z, and the ansatz is
+ *       |psi(gamma, beta)> = prod_{l=1..p} e^{-i beta_l B} e^{-i gamma_l H} |+>,
+ *     layer 1 acting first, with the mixer generator B = sum_q X_q. (The paper prints
+ *     H_X = -sum_q X_q; that convention is this library's with beta -> -beta.)
+ *   - Section IV: the candidate sub-solution is read from the final state; this library returns
+ *     the k most probable bitstrings (probability descending, ties to the smaller index).
+ *   - Section V-A: random and impact-factor-directed (Algorithm 1) decomposition into
+ *     sub-QUBOs; Section V step 3: aggregation that accepts only energy-lowering updates.
+ *
+ * Index convention: bit q of a basis index z is qubit q, which is sub-QUBO variable q (for a
+ * decomposed sub-QUBO, global variable idx[q], the index set sorted ascending).
+ *
+ * Memory: every pointer marked "device" is caller-owned device memory; "host" is caller-owned
+ * host memory. The library allocates only in qaoa_create, qaoa_reserve and the plan calls,
+ * never inside a launch call. Calls marked "async" enqueue work on `stream` and return at once;
+ * their outputs are valid once the stream has reached that point. Complex arrays are
+ * interleaved (re, im): complex64 = two floats (8 bytes), complex128 = two doubles.
+ *
+ * Errors: every call returns a qaoa_status. Invalid arguments (n < 1 or n > 30, p < 1 or
+ * p > 64, k < 0 or k > 16 or k > 2^n, a needed pointer NULL) give QAOA_E_INVALID before any
+ * work is enqueued; a failing CUDA call gives QAOA_E_CUDA. qaoa_last_error() returns the
+ * message of the last failure of the calling thread.
+ */
+#ifndef QAOA_H
+#define QAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QAOA_OK = 0,
+    QAOA_E_INVALID = 1,
+    QAOA_E_NOMEM = 2,
+    QAOA_E_CUDA = 3,
+    QAOA_E_TIMEOUT = 4,
+    QAOA_E_UNSUPPORTED = 5
+} qaoa_status;
+
+typedef struct qaoa_ctx qaoa_ctx;          /* opaque: device, workspace, launch plans */
+typedef struct CUstream_st* qaoa_stream_t; /* a cudaStream_t; NULL is the legacy stream */
+
+/* ---------------------------------------------------------------------------------------- */
+/* Context                                                                                   */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (makes it current on the calling thread). */
+qaoa_status qaoa_create(qaoa_ctx** out, int device);
+/* Free the context and its workspace (synchronises the device first). NULL is ignored. */
+void qaoa_destroy(qaoa_ctx* ctx);
+/* Message of the last failed call on this thread ("" if none). Valid until the next call. */
+const char* qaoa_last_error(void);
+/* Grow the context workspace to at least `bytes` (synchronous; allocates). Launch calls that
+ * need scratch use this workspace and return QAOA_E_NOMEM if it is too small and cannot grow. */
+qaoa_status qaoa_reserve(qaoa_ctx* ctx, size_t bytes);
+/* Workspace bytes that qaoa_grad / qaoa_run_layers / qaoa_expect / qaoa_topk need for n qubits
+ * (complex64 when dbl == 0, complex128 otherwise). */
+size_t qaoa_workspace_bytes(int n, int dbl);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Single instance, complex64 (FP32 energies). All pointers device, all calls async.         */
+/* ---------------------------------------------------------------------------------------- */
+
+/* E[z] = z^T Q z for z = 0..2^n-1 (Section IV, QUBO -> diagonal Hamiltonian).
+ * Q: n*n floats, row-major; read as given (E uses Q_ij and Q_ji as separate terms).
+ * E: 2^n floats. Built by Gray-code increments from direct FP32 evaluations. */
+qaoa_status qaoa_build_energies(qaoa_ctx* ctx, int n, const float* Q, float* E,
+                                qaoa_stream_t stream);
+
+/* Apply p layers of Eq. 2 to psi in place: for l = 0..p-1, psi(z) *= e^{-i gamma[l] E(z)},
+ * then e^{-i beta[l] X_q} on every qubit q. gamma, beta: p floats (device). E: 2^n floats.
+ * psi: 2^n complex64 (in/out); with init_plus != 0 it is first set to |+> (not read). */
+qaoa_status qaoa_run_layers(qaoa_ctx* ctx, int n, int p, const float* gamma, const float* beta,
+                            const float* E, void* psi, int init_plus, qaoa_stream_t stream);
+
+/* <C> = sum_z |psi(z)|^2 E(z) (Section IV, the cost C(theta) that the outer loop minimises).
+ * psi: 2^n complex64, E: 2^n floats, out: one double (device). FP32 products summed in FP32
+ * over at most 32 terms, FP64 above that, in a fixed order (deterministic). Uses workspace. */
+qaoa_status qaoa_expect(qaoa_ctx* ctx, int n, const void* psi, const float* E, double* out,
+                        qaoa_stream_t stream);
+
+/* The k (1..16) most probable basis states of psi (Section IV, the measured candidate
+ * sub-solution): idx[k] uint64 and prob[k] doubles (device; prob may be NULL), probability
+ * descending, ties broken by the smaller index. prob = re*re + im*im of the stored complex64
+ * amplitude, evaluated exactly in FP64 (one rounding). Uses workspace. */
+qaoa_status qaoa_topk(qaoa_ctx* ctx, int n, const void* psi, int k, uint64_t* idx, double* prob,
+                      qaoa_stream_t stream);
+
+/* Adjoint gradient of <C> from |+> through p layers (the reverse state-vector sweep):
+ * expect (1 double, may be NULL), dgamma[p], dbeta[p] doubles (device). Uses workspace for the
+ * forward and adjoint states when n exceeds the shared-memory tier. */
+qaoa_status qaoa_grad(qaoa_ctx* ctx, int n, int p, const float* gamma, const float* beta,
+                      const float* E, double* expect, double* dgamma, double* dbeta,
+                      qaoa_stream_t stream);
+
+/* ---- complex128 variants (FP64 energies, same semantics and layouts) ---- */
+qaoa_status qaoa_build_energies_z(qaoa_ctx* ctx, int n, const double* Q, double* E,
+                                  qaoa_stream_t stream);
+qaoa_status qaoa_run_layers_z(qaoa_ctx* ctx, int n, int p, const double* gamma,
+                              const double* beta, const double* E, void* psi, int init_plus,
+                              qaoa_stream_t stream);
+qaoa_status qaoa_expect_z(qaoa_ctx* ctx, int n, const void* psi, const double* E, double* out,
+                          qaoa_stream_t stream);
+qaoa_status qaoa_topk_z(qaoa_ctx* ctx, int n, const void* psi, int k, uint64_t* idx,
+                        double* prob, qaoa_stream_t stream);
+qaoa_status qaoa_grad_z(qaoa_ctx* ctx, int n, int p, const double* gamma, const double* beta,
+                        const double* E, double* expect, double* dgamma, double* dbeta,
+                        qaoa_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Batched sub-QUBO solves (Section V step 2: the sub-QUBOs of a cycle solved in parallel).  */
+/* ---------------------------------------------------------------------------------------- */
+
+enum { QAOA_INST_GRAD = 1 };
+
+/* One instance. Offsets are element offsets into the pools of qaoa_batch_io. */
+typedef struct {
+    int32_t n;        /* qubits, 1..30 */
+    int32_t p;        /* layers, 1..64 */
+    int32_t k;        /* top-k length, 0..16 (0: no top-k) */
+    int32_t flags;    /* QAOA_INST_GRAD: also d<C>/d(gamma, beta) */
+    int64_t q_off;    /* n*n row-major Q at io->q + q_off */
+    int64_t par_off;  /* gamma[p] then beta[p] at io->params + par_off; gradients at the same
+                         offsets in io->grad */
+    int64_t psi_off;  /* final state (2^n complex) at io->psi + psi_off, or -1: not returned */
+    int64_t e_off;    /* energies (2^n) at io->e + e_off, or -1: not returned */
+} qaoa_inst;
+
+typedef struct {
+    const void* q;       /* device: Q pool (float, or double for _z) */
+    const void* params;  /* device: parameter pool (float, or double for _z) */
+    void* psi;           /* device: state pool (complex64 / complex128) or NULL */
+    void* e;             /* device: energy pool or NULL */
+    double* expect;      /* device: count doubles, <C> of instance i at expect[i] */
+    uint64_t* topk_idx;  /* device: count * k_stride, instance i at i * k_stride */
+    double* topk_prob;   /* device: same layout, may be NULL */
+    int32_t k_stride;
+    double* grad;        /* device: gradient pool (same offsets as params) or NULL */
+} qaoa_batch_io;
+
+typedef struct qaoa_plan qaoa_plan;
+
+/* Validate the descriptors (host array, `count` entries), choose a kernel tier per instance
+ * (shared-memory resident, cluster, or HBM streaming) and upload the device descriptor
+ * tables. Synchronous; allocates the plan's device memory. The io pointers are bound into the
+ * plan: a later launch reads and writes the same buffers. */
+qaoa_status qaoa_plan_create(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
+                             const qaoa_batch_io* io, int dbl, qaoa_plan** out);
+/* Enqueue the whole batch on `stream` (kernel launches and memsets only, so the call can be
+ * captured in a CUDA graph). Async. */
+qaoa_status qaoa_plan_launch(qaoa_plan* plan, qaoa_stream_t stream);
+/* Number of kernel launches one qaoa_plan_launch enqueues. */
+int qaoa_plan_kernel_count(const qaoa_plan* plan);
+/* Free the plan (synchronises the device first). NULL is ignored. */
+void qaoa_plan_destroy(qaoa_plan* plan);
+
+/* plan_create + plan_launch + (after a stream synchronisation) plan_destroy. Synchronous. */
+qaoa_status qaoa_batch_run(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
+                           const qaoa_batch_io* io, qaoa_stream_t stream);
+qaoa_status qaoa_batch_run_z(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
+                             const qaoa_batch_io* io, qaoa_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Reference "plain" GPU path: one instance per call, one kernel per gate (cost phase, one    */
+/* kernel per qubit for the mixer) and a separate reduction. The comparison point of the     */
+/* batched path; same arguments as qaoa_run_layers plus the reductions.                     */
+/* ---------------------------------------------------------------------------------------- */
+qaoa_status qaoa_plain_solve(qaoa_ctx* ctx, int n, int p, const float* Q, const float* gamma,
+                             const float* beta, float* E, void* psi, int k, double* expect,
+                             uint64_t* topk_idx, double* topk_prob, qaoa_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* DQAOA decomposition and aggregation (host, FP64)                                          */
+/* ---------------------------------------------------------------------------------------- */
+
+enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1 };
+
+/* Section V-A. Sub-QUBO index sets: idx[m*k] (host int32), each row sorted ascending.
+ *   DQAOA_RANDOM: row j draws k distinct variables of 0..N-1 uniformly without replacement,
+ *     SplitMix64 seeded with seed ^ (cycle * 0x9E3779B97F4A7C15) ^ j, partial Fisher-Yates
+ *     (swap position i with i + draw(N - i)), draws by Lemire's multiply-shift with rejection.
+ *   DQAOA_IFD (Algorithm 1): variables ranked by |impact| descending (ties: smaller index),
+ *     impact_i = (1 - 2 x_i)(Q_ii + 2 sum_{j != i} Q_ij x_j), the energy change of flipping x_i;
+ *     row j is the window ranking[j .. j+k-1] (needs m + k - 1 <= N; Q and x required).
+ * Q: N*N row-major symmetric doubles (host), x: N bytes 0/1 (host; RANDOM may pass NULL). */
+qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t* x, int method, int m,
+                               int k, uint64_t seed, uint64_t cycle, int32_t* idx);
+
+/* Section V-A sub-QUBO matrices for given index sets: Qsub[j] = Q[S_j, S_j] (k*k full
+ * symmetric, host doubles). With conditioned != 0 the couplings to the fixed variables
+ * outside S_j are folded into the diagonal, Qsub[a][a] += 2 sum_{l not in S_j} Q[S_a][l] x_l,
+ * so the sub-QUBO energy of y is E(x with x_S = y) minus a constant. */
+qaoa_status dqaoa_decompose(const double* Q, int N, const uint8_t* x, int method, int conditioned,
+                            int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx,
+                            double* Qsub);
+
+/* The same sub-QUBO matrices built on the device, as FP32 for the complex64 solver:
+ * Q_dev N*N doubles, x_dev N bytes, idx_dev m*k int32, qsub_dev m*k*k floats (all device).
+ * The conditioning sum is accumulated in FP64, ascending l. Async. */
+qaoa_status dqaoa_subqubo_build(qaoa_ctx* ctx, const double* Q_dev, int N, const uint8_t* x_dev,
+                                int m, int k, const int32_t* idx_dev, int conditioned,
+                                float* qsub_dev, qaoa_stream_t stream);
+
+/* Section V step 3, aggregation. Sequential over sub-QUBOs j = 0..m-1 and, within j, over the
+ * K candidate bitstrings cand[j*K .. j*K+K-1] (host uint64; bit q sets variable idx[j*k+q]) in
+ * the given order: a candidate replaces x on S_j when dE = E(x') - E(x) < -tau,
+ * tau = 1e-12 sum |Q_ij|. dE = sum_{a: d_a != 0} d_a (2 (Qx)_a + sum_{b: d_b != 0} Q_ab d_b),
+ * d = x' - x, with Qx kept up to date as variables flip. x: N bytes (host, in/out);
+ * energy_out: E(x') = x'^T Q x' (host double, may be NULL); accepted_out: number of accepted
+ * candidates (may be NULL). k <= 64. Synchronous. */
+qaoa_status dqaoa_merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx,
+                        int K, const uint64_t* cand, double* energy_out, int* accepted_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAOA_H */

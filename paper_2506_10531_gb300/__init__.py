@@ -1,0 +1,270 @@
+"""Python binding of libqaoa (include/qaoa.h): batched state-vector QAOA on sub-QUBOs and the
+DQAOA decompose / merge steps, for NVIDIA GB300 (sm_103a).
+
+Every function here only marshals arguments (device pointers from torch tensors, the current
+CUDA stream, ctypes structs) and calls the C entry point of the same name; all computation
+happens in the CUDA library. Importing the package does not need a GPU; calling into the
+library needs the built ``libqaoa.so`` (``paper_2506_10531_gb300.build.build()``) and raises
+``RuntimeError`` when it is missing. There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqaoa.so")
+
+QAOA_OK, QAOA_E_INVALID, QAOA_E_NOMEM, QAOA_E_CUDA, QAOA_E_TIMEOUT, QAOA_E_UNSUPPORTED = range(6)
+QAOA_INST_GRAD = 1
+DQAOA_RANDOM, DQAOA_IFD = 0, 1
+
+# Every symbol include/qaoa.h declares.
+EXPORTS = [
+    "qaoa_create", "qaoa_destroy", "qaoa_last_error", "qaoa_reserve", "qaoa_workspace_bytes",
+    "qaoa_build_energies", "qaoa_run_layers", "qaoa_expect", "qaoa_topk", "qaoa_grad",
+    "qaoa_build_energies_z", "qaoa_run_layers_z", "qaoa_expect_z", "qaoa_topk_z", "qaoa_grad_z",
+    "qaoa_plan_create", "qaoa_plan_launch", "qaoa_plan_kernel_count", "qaoa_plan_destroy",
+    "qaoa_batch_run", "qaoa_batch_run_z", "qaoa_plain_solve",
+    "dqaoa_draw_indices", "dqaoa_decompose", "dqaoa_subqubo_build", "dqaoa_merge",
+]
+
+
+class QaoaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libqaoa status {status}: {msg}")
+        self.status = status
+
+
+class qaoa_inst(C.Structure):
+    _fields_ = [("n", C.c_int32), ("p", C.c_int32), ("k", C.c_int32), ("flags", C.c_int32),
+                ("q_off", C.c_int64), ("par_off", C.c_int64), ("psi_off", C.c_int64),
+                ("e_off", C.c_int64)]
+
+
+class qaoa_batch_io(C.Structure):
+    _fields_ = [("q", C.c_void_p), ("params", C.c_void_p), ("psi", C.c_void_p), ("e", C.c_void_p),
+                ("expect", C.c_void_p), ("topk_idx", C.c_void_p), ("topk_prob", C.c_void_p),
+                ("k_stride", C.c_int32), ("grad", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libqaoa (ctypes.CDLL). Raises RuntimeError if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libqaoa.so not built at {LIB_PATH}: run "
+                                   "paper_2506_10531_gb300.build.build() (there is no CPU path)")
+            L = C.CDLL(LIB_PATH)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i32, i64, u64, sz, dp = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_size_t, C.c_void_p
+    st = C.c_int
+    L.qaoa_create.argtypes = [C.POINTER(vp), i32]
+    L.qaoa_destroy.argtypes = [vp]
+    L.qaoa_destroy.restype = None
+    L.qaoa_last_error.restype = C.c_char_p
+    L.qaoa_reserve.argtypes = [vp, sz]
+    L.qaoa_workspace_bytes.argtypes = [i32, i32]
+    L.qaoa_workspace_bytes.restype = sz
+    for suf in ("", "_z"):
+        getattr(L, "qaoa_build_energies" + suf).argtypes = [vp, i32, vp, vp, vp]
+        getattr(L, "qaoa_run_layers" + suf).argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp]
+        getattr(L, "qaoa_expect" + suf).argtypes = [vp, i32, vp, vp, vp, vp]
+        getattr(L, "qaoa_topk" + suf).argtypes = [vp, i32, vp, i32, vp, vp, vp]
+        getattr(L, "qaoa_grad" + suf).argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.qaoa_plan_create.argtypes = [vp, vp, i32, C.POINTER(qaoa_batch_io), i32, C.POINTER(vp)]
+    L.qaoa_plan_launch.argtypes = [vp, vp]
+    L.qaoa_plan_kernel_count.argtypes = [vp]
+    L.qaoa_plan_kernel_count.restype = i32
+    L.qaoa_plan_destroy.argtypes = [vp]
+    L.qaoa_plan_destroy.restype = None
+    L.qaoa_batch_run.argtypes = [vp, vp, i32, C.POINTER(qaoa_batch_io), vp]
+    L.qaoa_batch_run_z.argtypes = [vp, vp, i32, C.POINTER(qaoa_batch_io), vp]
+    L.qaoa_plain_solve.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+    L.dqaoa_draw_indices.argtypes = [vp, i32, vp, i32, i32, i32, u64, u64, vp]
+    L.dqaoa_decompose.argtypes = [vp, i32, vp, i32, i32, i32, i32, u64, u64, vp, vp]
+    L.dqaoa_subqubo_build.argtypes = [vp, vp, i32, vp, i32, i32, vp, i32, vp, vp]
+    L.dqaoa_merge.argtypes = [vp, i32, vp, i32, i32, vp, i32, vp, vp, vp]
+    del i64, st, dp
+
+
+def _check(status):
+    if status != QAOA_OK:
+        msg = lib().qaoa_last_error()
+        raise QaoaError(status, msg.decode() if msg else "")
+
+
+def ptr(x):
+    """Device/host address of a torch tensor or numpy array, an int, or None (NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def stream_ptr(stream=None):
+    """cudaStream_t of a torch stream (default: the current stream)."""
+    if isinstance(stream, int):
+        return stream
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------------------------------------
+# thin wrappers, same names as the C entry points
+# ---------------------------------------------------------------------------------------------
+
+def qaoa_create(device: int = 0):
+    h = C.c_void_p()
+    _check(lib().qaoa_create(C.byref(h), device))
+    return h
+
+
+def qaoa_destroy(ctx):
+    lib().qaoa_destroy(ctx)
+
+
+def qaoa_reserve(ctx, nbytes: int):
+    _check(lib().qaoa_reserve(ctx, nbytes))
+
+
+def qaoa_workspace_bytes(n: int, dbl: bool = False) -> int:
+    return lib().qaoa_workspace_bytes(n, int(dbl))
+
+
+def qaoa_build_energies(ctx, n, Q, E, stream=None, dbl=False):
+    f = lib().qaoa_build_energies_z if dbl else lib().qaoa_build_energies
+    _check(f(ctx, n, ptr(Q), ptr(E), stream_ptr(stream)))
+
+
+def qaoa_run_layers(ctx, n, p, gamma, beta, E, psi, init_plus=True, stream=None, dbl=False):
+    f = lib().qaoa_run_layers_z if dbl else lib().qaoa_run_layers
+    _check(f(ctx, n, p, ptr(gamma), ptr(beta), ptr(E), ptr(psi), int(init_plus), stream_ptr(stream)))
+
+
+def qaoa_expect(ctx, n, psi, E, out, stream=None, dbl=False):
+    f = lib().qaoa_expect_z if dbl else lib().qaoa_expect
+    _check(f(ctx, n, ptr(psi), ptr(E), ptr(out), stream_ptr(stream)))
+
+
+def qaoa_topk(ctx, n, psi, k, idx, prob, stream=None, dbl=False):
+    f = lib().qaoa_topk_z if dbl else lib().qaoa_topk
+    _check(f(ctx, n, ptr(psi), k, ptr(idx), ptr(prob), stream_ptr(stream)))
+
+
+def qaoa_grad(ctx, n, p, gamma, beta, E, expect, dgamma, dbeta, stream=None, dbl=False):
+    f = lib().qaoa_grad_z if dbl else lib().qaoa_grad
+    _check(f(ctx, n, p, ptr(gamma), ptr(beta), ptr(E), ptr(expect), ptr(dgamma), ptr(dbeta),
+             stream_ptr(stream)))
+
+
+def make_io(q, params, expect=None, topk_idx=None, topk_prob=None, k_stride=0, psi=None, e=None,
+            grad=None) -> qaoa_batch_io:
+    return qaoa_batch_io(ptr(q), ptr(params), ptr(psi), ptr(e), ptr(expect), ptr(topk_idx),
+                         ptr(topk_prob), k_stride, ptr(grad))
+
+
+def make_insts(rows):
+    """rows: iterable of (n, p, k, flags, q_off, par_off, psi_off, e_off)."""
+    rows = list(rows)
+    arr = (qaoa_inst * len(rows))()
+    for i, r in enumerate(rows):
+        arr[i] = qaoa_inst(*r)
+    return arr
+
+
+def qaoa_plan_create(ctx, insts, io: qaoa_batch_io, dbl=False):
+    h = C.c_void_p()
+    _check(lib().qaoa_plan_create(ctx, C.cast(insts, C.c_void_p), len(insts), C.byref(io), int(dbl),
+                                  C.byref(h)))
+    return h
+
+
+def qaoa_plan_launch(plan, stream=None):
+    _check(lib().qaoa_plan_launch(plan, stream_ptr(stream)))
+
+
+def qaoa_plan_kernel_count(plan) -> int:
+    return lib().qaoa_plan_kernel_count(plan)
+
+
+def qaoa_plan_destroy(plan):
+    lib().qaoa_plan_destroy(plan)
+
+
+def qaoa_batch_run(ctx, insts, io: qaoa_batch_io, stream=None, dbl=False):
+    f = lib().qaoa_batch_run_z if dbl else lib().qaoa_batch_run
+    _check(f(ctx, C.cast(insts, C.c_void_p), len(insts), C.byref(io), stream_ptr(stream)))
+
+
+def qaoa_plain_solve(ctx, n, p, Q, gamma, beta, E, psi, k, expect, topk_idx, topk_prob, stream=None):
+    _check(lib().qaoa_plain_solve(ctx, n, p, ptr(Q), ptr(gamma), ptr(beta), ptr(E), ptr(psi), k,
+                                  ptr(expect), ptr(topk_idx), ptr(topk_prob), stream_ptr(stream)))
+
+
+def dqaoa_draw_indices(Q, N, x, method, m, k, seed, cycle, idx):
+    _check(lib().dqaoa_draw_indices(ptr(Q), N, ptr(x), method, m, k, seed, cycle, ptr(idx)))
+
+
+def dqaoa_decompose(Q, N, x, method, conditioned, m, k, seed, cycle, idx, qsub):
+    _check(lib().dqaoa_decompose(ptr(Q), N, ptr(x), method, int(conditioned), m, k, seed, cycle,
+                                 ptr(idx), ptr(qsub)))
+
+
+def dqaoa_subqubo_build(ctx, Q_dev, N, x_dev, m, k, idx_dev, conditioned, qsub_dev, stream=None):
+    _check(lib().dqaoa_subqubo_build(ctx, ptr(Q_dev), N, ptr(x_dev), m, k, ptr(idx_dev),
+                                     int(conditioned), ptr(qsub_dev), stream_ptr(stream)))
+
+
+def dqaoa_merge(Q, N, x, m, k, idx, K, cand):
+    """Host merge; returns (energy, accepted). x (numpy uint8) is updated in place."""
+    e = C.c_double()
+    a = C.c_int()
+    _check(lib().dqaoa_merge(ptr(Q), N, ptr(x), m, k, ptr(idx), K, ptr(cand), C.byref(e), C.byref(a)))
+    return e.value, a.value
+
+
+def qaoa_last_error() -> str:
+    m = lib().qaoa_last_error()
+    return m.decode() if m else ""
+
+
+def qaoa_build_energies_z(ctx, n, Q, E, stream=None):
+    qaoa_build_energies(ctx, n, Q, E, stream, dbl=True)
+
+
+def qaoa_run_layers_z(ctx, n, p, gamma, beta, E, psi, init_plus=True, stream=None):
+    qaoa_run_layers(ctx, n, p, gamma, beta, E, psi, init_plus, stream, dbl=True)
+
+
+def qaoa_expect_z(ctx, n, psi, E, out, stream=None):
+    qaoa_expect(ctx, n, psi, E, out, stream, dbl=True)
+
+
+def qaoa_topk_z(ctx, n, psi, k, idx, prob, stream=None):
+    qaoa_topk(ctx, n, psi, k, idx, prob, stream, dbl=True)
+
+
+def qaoa_grad_z(ctx, n, p, gamma, beta, E, expect, dgamma, dbeta, stream=None):
+    qaoa_grad(ctx, n, p, gamma, beta, E, expect, dgamma, dbeta, stream, dbl=True)
+
+
+def qaoa_batch_run_z(ctx, insts, io: qaoa_batch_io, stream=None):
+    qaoa_batch_run(ctx, insts, io, stream, dbl=True)

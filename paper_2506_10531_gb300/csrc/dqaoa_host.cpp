@@ -1,0 +1,176 @@
+// dqaoa_host.cpp -- host side of the DQAOA cycle (arXiv 2506.10531, Section V): the index
+// sets of the random and impact-factor-directed decompositions (Section V-A, Algorithm 1),
+// the sub-QUBO matrices, and the aggregation of sub-solutions (Section V step 3).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "qaoa_host.h"
+
+namespace qaoa {
+
+namespace {
+
+// SplitMix64 (Steele, Lea & Flood 2014): advance by the golden gamma, then the finaliser.
+struct SplitMix64 {
+    uint64_t s;
+    uint64_t next() {
+        s += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+    // Uniform in [0, range): Lemire (2019) multiply-shift, rejecting low words below
+    // 2^64 mod range.
+    uint64_t below(uint64_t range) {
+        __uint128_t m = (__uint128_t)next() * range;
+        uint64_t lo = (uint64_t)m;
+        if (lo < range) {
+            const uint64_t t = (0 - range) % range;
+            while (lo < t) {
+                m = (__uint128_t)next() * range;
+                lo = (uint64_t)m;
+            }
+        }
+        return (uint64_t)(m >> 64);
+    }
+};
+
+}  // namespace
+
+// Random index sets: a partial Fisher-Yates shuffle of 0..N-1 per row, with only the touched
+// positions stored (a map from position to value), which draws the same sets as a shuffle of
+// the full array.
+int draw_random(int N, int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx) {
+    std::unordered_map<int32_t, int32_t> moved;
+    moved.reserve((size_t)2 * k);
+    for (int j = 0; j < m; ++j) {
+        SplitMix64 g{seed ^ (cycle * 0x9E3779B97F4A7C15ULL) ^ (uint64_t)j};
+        moved.clear();
+        int32_t* S = idx + (int64_t)j * k;
+        for (int i = 0; i < k; ++i) {
+            const int32_t r = i + (int32_t)g.below((uint64_t)(N - i));
+            auto at = [&](int32_t pos) {
+                auto it = moved.find(pos);
+                return it == moved.end() ? pos : it->second;
+            };
+            const int32_t vi = at(i), vr = at(r);
+            moved[i] = vr;
+            moved[r] = vi;
+            S[i] = vr;
+        }
+        std::sort(S, S + k);
+    }
+    return 0;
+}
+
+// Impact factor of each variable (the energy change of flipping it) and the IFD ranking:
+// |impact| descending, ties to the smaller index; row j is the window ranking[j .. j+k-1].
+int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx) {
+    std::vector<double> imp(N);
+    for (int i = 0; i < N; ++i) {
+        const double* row = Q + (int64_t)i * N;
+        double h = 0.0;
+        for (int j = 0; j < N; ++j)
+            if (j != i && x[j]) h += row[j];
+        imp[i] = (1.0 - 2.0 * (double)x[i]) * (row[i] + 2.0 * h);
+    }
+    std::vector<int32_t> order(N);
+    for (int i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return std::fabs(imp[a]) > std::fabs(imp[b]); });
+    for (int j = 0; j < m; ++j) {
+        int32_t* S = idx + (int64_t)j * k;
+        std::copy(order.begin() + j, order.begin() + j + k, S);
+        std::sort(S, S + k);
+    }
+    return 0;
+}
+
+void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, const int32_t* idx,
+                    int conditioned, double* Qsub) {
+    std::vector<uint8_t> inS(N, 0);
+    for (int j = 0; j < m; ++j) {
+        const int32_t* S = idx + (int64_t)j * k;
+        double* Qs = Qsub + (int64_t)j * k * k;
+        for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b) Qs[a * k + b] = Q[(int64_t)S[a] * N + S[b]];
+        if (!conditioned) continue;
+        for (int a = 0; a < k; ++a) inS[S[a]] = 1;
+        for (int a = 0; a < k; ++a) {
+            const double* row = Q + (int64_t)S[a] * N;
+            double h = 0.0;
+            for (int l = 0; l < N; ++l)
+                if (!inS[l] && x[l]) h += row[l];
+            Qs[a * k + a] += 2.0 * h;
+        }
+        for (int a = 0; a < k; ++a) inS[S[a]] = 0;
+    }
+}
+
+// Aggregation: h = Qx is kept up to date (O(N) per flipped variable), so each candidate costs
+// O(|d|^2) with d = x' - x.
+int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
+          const uint64_t* cand, double* energy_out, int* accepted_out) {
+    double absq = 0.0;
+    for (int64_t t = 0; t < (int64_t)N * N; ++t) absq += std::fabs(Q[t]);
+    const double tau = 1e-12 * absq;
+    std::vector<double> h(N, 0.0);
+    double energy = 0.0;
+    for (int i = 0; i < N; ++i) {
+        if (!x[i]) continue;
+        const double* row = Q + (int64_t)i * N;
+        for (int l = 0; l < N; ++l)
+            if (x[l]) energy += row[l];
+    }
+    for (int l = 0; l < N; ++l) {
+        const double* row = Q + (int64_t)l * N;
+        double s = 0.0;
+        for (int i = 0; i < N; ++i)
+            if (x[i]) s += row[i];
+        h[l] = s;
+    }
+    int accepted = 0;
+    int nz[64];
+    double d[64];
+    for (int j = 0; j < m; ++j) {
+        const int32_t* S = idx + (int64_t)j * k;
+        for (int c = 0; c < K; ++c) {
+            const uint64_t y = cand[(int64_t)j * K + c];
+            int cnt = 0;
+            for (int a = 0; a < k; ++a) {
+                const double da = (double)((y >> a) & 1u) - (double)x[S[a]];
+                if (da != 0.0) { nz[cnt] = a; d[cnt] = da; ++cnt; }
+            }
+            if (!cnt) continue;
+            double dE = 0.0;
+            for (int u = 0; u < cnt; ++u) {
+                const double* row = Q + (int64_t)S[nz[u]] * N;
+                double inner = 0.0;
+                for (int v = 0; v < cnt; ++v) inner += row[S[nz[v]]] * d[v];
+                dE += d[u] * (2.0 * h[S[nz[u]]] + inner);
+            }
+            if (dE < -tau) {
+                for (int u = 0; u < cnt; ++u) {
+                    const int var = S[nz[u]];
+                    x[var] = (uint8_t)(d[u] > 0.0);
+                    // column var of the symmetric Q == row var
+                    const double* row = Q + (int64_t)var * N;
+                    const double du = d[u];
+                    for (int l = 0; l < N; ++l) h[l] += du * row[l];
+                }
+                energy += dE;
+                ++accepted;
+            }
+        }
+    }
+    if (energy_out) *energy_out = energy;
+    if (accepted_out) *accepted_out = accepted;
+    return 0;
+}
+
+}  // namespace qaoa

@@ -1,0 +1,495 @@
+// k_stream.cu -- HBM-streaming tier for states larger than one SM's shared memory, plus the
+// standalone energy build and the standalone <C> / top-k reductions over a state in HBM.
+//
+// A layer of Eq. 2 (Section IV) on a 2^n state is split into HBM passes. Each pass moves
+// tiles of 2^tb amplitudes between HBM and shared memory and runs the tile engine on them:
+//   kind A: the tile is 2^tb contiguous amplitudes; its tile bits are qubits 0..tb-1;
+//   kind B: the tile is 2^c contiguous amplitudes (qubits 0..c-1, c >= 4, so every run is at
+//           least 128 bytes) times 2^h values of the high qubits [s, s+h), c + h = tb; only the
+//           high qubits are mixed.
+// The HBM passes follow the same snake order as the windows of a tile (A, B1, B2, ... then
+// back), so consecutive layers share a pass; the cost phase of a layer is fused into the pass
+// that opens it, |+> is generated in the first pass, and <C> plus the top-k candidates are
+// reduced in the last one (per-tile partials, then one fixed-order finalize per instance).
+#include "qaoa_engine.cuh"
+#include "qaoa_kernels.h"
+#include "qaoa_stream.h"
+
+namespace qaoa {
+
+namespace {
+
+// Global index of tile-local index u for tile tau of pass P.
+__device__ __forceinline__ uint64_t global_index(const StreamPass& P, uint64_t tau, uint32_t u) {
+    if (P.kind == 0) return (tau << P.tb) | u;
+    const uint64_t lo = u & ((1u << P.c) - 1u);
+    const uint64_t hi = u >> P.c;
+    const int midbits = P.s - P.c;
+    const uint64_t mid = tau & ((1ull << midbits) - 1ull);
+    const uint64_t top = tau >> midbits;
+    return lo | (mid << P.c) | (hi << P.s) | (top << (P.s + P.h));
+}
+
+// Two adjacent amplitudes (16-byte aligned for complex64) in one access.
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
+__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
+
+template <typename T>
+struct StreamSmem {
+    typename Num<T>::C* psi;
+    T* E;
+    LayerConst<T>* lc;
+    double* red;
+    TopEnt* top;
+};
+
+template <typename T, int R>
+__device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_t tau,
+                            const StreamSmem<T>& s) {
+    using C = typename Num<T>::C;
+    const uint32_t TD = 1u << P.tb;
+    const bool needE = P.need_e;
+    C* gpsi = reinterpret_cast<C*>(I.psi);
+    // ---- HBM -> shared (two amplitudes per 16-byte access; c >= 1 keeps them adjacent) ----
+    if (!P.init) {
+        for (uint32_t u = 2 * threadIdx.x; u < TD; u += 2 * blockDim.x) {
+            C a, b;
+            ld_pair(gpsi + global_index(P, tau, u), a, b);
+            s.psi[swz<T>(u)] = a;
+            s.psi[swz<T>(u + 1)] = b;
+        }
+    }
+    if (needE) {
+        for (uint32_t u = threadIdx.x; u < TD; u += blockDim.x)
+            s.E[swz<T>(u)] = I.E[global_index(P, tau, u)];
+    }
+    __syncthreads();
+    // ---- tile engine: snake over the local windows of the mixed bits, layers [la, lb] ----
+    const TileRef<T> tile{s.psi, nullptr, s.E, P.tb};
+    const int m0 = (P.kind == 0) ? 0 : P.c;
+    const int G = num_windows(m0, P.tb, R);
+    const int nl = P.lb - P.la + 1;
+    const int S = snake_len(G, nl);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpTopK top;
+    top.init(P.k > 0 ? P.k : 1);
+    double ex = 0.0;
+    const T amp0 = (T)I.amp0;
+    for (int si = 0; si < S; ++si) {
+        SubPass sp;
+        snake_step(si, G, nl, P.la, P.ph_first, m0, P.tb, P.tb, R, sp);
+        const bool last = P.fin && (si == S - 1);
+        auto fin = [&](C (&v)[1 << R], uint32_t base, int a, bool valid) {
+            if (!last) return;
+            T accp = T(0);
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) {
+                if (valid) {
+                    const uint32_t u = base | ((uint32_t)i << a);
+                    accp += (v[i].x * v[i].x + v[i].y * v[i].y) * s.E[swz<T>(u)];
+                }
+            }
+            ex += (double)accp;
+            if (P.k > 0) {
+#pragma unroll
+                for (int i = 0; i < (1 << R); ++i) {
+                    const uint32_t u = base | ((uint32_t)i << a);
+                    top.offer(v[i], (uint32_t)global_index(P, tau, u), valid);
+                }
+            }
+        };
+        subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, fin);
+        __syncthreads();
+    }
+    // ---- shared -> HBM ----
+    for (uint32_t u = 2 * threadIdx.x; u < TD; u += 2 * blockDim.x)
+        st_pair(gpsi + global_index(P, tau, u), s.psi[swz<T>(u)], s.psi[swz<T>(u + 1)]);
+    if (P.fin) {
+        const double tot = block_sum(ex, s.red);
+        if (threadIdx.x == 0) I.part_expect[tau] = tot;
+        if (P.k > 0) {
+            if (lane < P.k) s.top[warp * 32 + lane] = TopEnt{top.p, top.z};
+            __syncthreads();
+            if (warp == 0) {
+                WarpTopK f;
+                f.init(P.k);
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    const bool ok = lane < P.k;
+                    const TopEnt e = ok ? s.top[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
+                    f.offer_exact(e.p, e.z, ok);
+                }
+                if (lane < P.k) {
+                    I.part_topp[tau * P.k + lane] = f.p;
+                    I.part_topz[tau * P.k + lane] = f.z;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_pass(const StreamPass P,
+                                                     const StreamInst<T>* __restrict__ insts,
+                                                     int count, const StreamInst<T> one) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    using C = typename Num<T>::C;
+    const uint32_t TD = 1u << P.tb;
+    StreamSmem<T> s;
+    size_t o = 0;
+    s.psi = reinterpret_cast<C*>(sm + o); o += (size_t)TD * sizeof(C);
+    s.E = reinterpret_cast<T*>(sm + o); o += (size_t)TD * sizeof(T);
+    s.lc = reinterpret_cast<LayerConst<T>*>(sm + o); o += 64 * sizeof(LayerConst<T>);
+    o = (o + 15) & ~(size_t)15;
+    s.red = reinterpret_cast<double*>(sm + o); o += 32 * sizeof(double);
+    s.top = reinterpret_cast<TopEnt*>(sm + o);
+    const uint64_t ntiles = 1ull << (P.n - P.tb);
+    const uint64_t total = ntiles * (uint64_t)count;
+    int cur = -1;
+    for (uint64_t b = blockIdx.x; b < total; b += gridDim.x) {
+        const int ii = (int)(b / ntiles);
+        const uint64_t tau = b % ntiles;
+        const StreamInst<T>& I = insts ? insts[ii] : one;
+        if (ii != cur) {
+            __syncthreads();
+            for (int l = threadIdx.x; l < I.p; l += blockDim.x) {
+                T sb, cb;
+                sincos_full(I.beta[l], sb, cb);
+                s.lc[l] = LayerConst<T>{I.gamma[l] / T(3.14159265358979323846), cb, sb};
+            }
+            __syncthreads();
+            cur = ii;
+        }
+        constexpr int RB = Num<T>::RB;
+        stream_tile<T, RB>(P, I, tau, s);
+    }
+}
+
+// Per-instance finalize: <C> = fixed-order sum of the tile partials; top-k = merge of the
+// tile lists (one warp; the result is unique under (probability desc, index asc)).
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_finalize(const StreamInst<T>* __restrict__ insts,
+                                                         int count, uint64_t ntiles, int k,
+                                                         const StreamInst<T> one) {
+    __shared__ double red[32];
+    __shared__ TopEnt tops[8 * 32];
+    const int ii = blockIdx.x;
+    if (ii >= count) return;
+    const StreamInst<T>& I = insts ? insts[ii] : one;
+    // sum: each thread a contiguous slice (fixed), then the block tree
+    double acc = 0.0;
+    const uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const uint64_t b0 = threadIdx.x * per;
+    for (uint64_t t = b0; t < b0 + per && t < ntiles; ++t) acc += I.part_expect[t];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0 && I.expect) *I.expect = tot;
+    if (k > 0) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        WarpTopK top;
+        top.init(k);
+        // each warp merges a strided subset of tile lists, then warp 0 merges the warps
+        const uint64_t nent = ntiles * (uint64_t)k;
+        for (uint64_t e0 = (uint64_t)warp * 32; e0 < nent; e0 += (uint64_t)(blockDim.x >> 5) * 32) {
+            const uint64_t e = e0 + lane;
+            const bool ok = e < nent;
+            top.offer_exact(ok ? I.part_topp[e] : -1.0, ok ? I.part_topz[e] : 0u, ok);
+        }
+        if (lane < k) tops[warp * 32 + lane] = TopEnt{top.p, top.z};
+        __syncthreads();
+        if (warp == 0) {
+            WarpTopK f;
+            f.init(k);
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const bool ok = lane < k;
+                const TopEnt e = ok ? tops[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
+                f.offer_exact(e.p, e.z, ok);
+            }
+            if (lane < k) {
+                if (I.topk_idx) I.topk_idx[lane] = (uint64_t)f.z;
+                if (I.topk_prob) I.topk_prob[lane] = f.p;
+            }
+        }
+    }
+}
+
+// ---- energy build into HBM --------------------------------------------------------------
+// Thread t of 2^m fixes the low m bits of z and walks the high n - m bits in Gray-code order
+// (same increment rule as the resident tier); every step writes one coalesced row of E.
+template <typename T>
+__global__ void __launch_bounds__(256) k_energy(int n, int m, const T* __restrict__ Q,
+                                                T* __restrict__ E) {
+    __shared__ T Qs[32 * 32];
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Qs[i] = Q[i];
+    __syncthreads();
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (1ull << m)) return;
+    const int nh = n - m;
+    T e = T(0);
+    for (int i = 0; i < m; ++i) {
+        if (!((t >> i) & 1u)) continue;
+        for (int j = 0; j < m; ++j)
+            if ((t >> j) & 1u) e += Qs[i * n + j];
+    }
+    constexpr int MAXH = 12;
+    T F[MAXH];
+#pragma unroll
+    for (int h = 0; h < MAXH; ++h) {
+        T f = T(0);
+        if (h < nh)
+            for (int j = 0; j < m; ++j)
+                if ((t >> j) & 1u) f += Qs[(m + h) * n + j];
+        F[h] = f;
+    }
+    uint64_t z = t;
+    E[z] = e;
+    const uint32_t steps = 1u << nh;
+    for (uint32_t k = 1; k < steps; ++k) {
+        const int b = __ffs((int)k) - 1;
+        const int hb = m + b;
+        const T d = ((z >> hb) & 1ull) ? T(-1) : T(1);
+        T fb = T(0);
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h)
+            if (h == b) fb = F[h];
+        e += d * (Qs[hb * n + hb] + T(2) * fb);
+        z ^= 1ull << hb;
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h)
+            if (h < nh && h != b) F[h] += d * Qs[(m + h) * n + hb];
+        E[z] = e;
+    }
+}
+
+// ---- standalone <C> and top-k over a state in HBM ----------------------------------------
+// Grid-stride over elements; each thread accumulates FP32 products over at most 32 elements
+// before adding them to its FP64 partial; per-CTA partials and top-k lists go to the
+// caller-provided scratch and are merged by k_stream_finalize-style reduction.
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce_state(int n, const typename Num<T>::C* __restrict__ psi,
+                                                      const T* __restrict__ E, int k,
+                                                      double* part_expect, double* part_topp,
+                                                      uint32_t* part_topz) {
+    __shared__ double red[32];
+    __shared__ TopEnt tops[8 * 32];
+    const uint64_t D = 1ull << n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpTopK top;
+    top.init(k > 0 ? k : 1);
+    double ex = 0.0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // chunks of 32 consecutive strides so that the FP32 partial has at most 32 terms
+    for (uint64_t c0 = (uint64_t)blockIdx.x * blockDim.x; c0 < D; c0 += stride * 32) {
+        T acc = T(0);
+        for (int r = 0; r < 32; ++r) {
+            const uint64_t z = c0 + (uint64_t)r * stride + threadIdx.x;
+            const bool ok = z < D;
+            typename Num<T>::C v;
+            v.x = T(0); v.y = T(0);
+            if (ok) {
+                v = psi[z];
+                if (E) acc += (v.x * v.x + v.y * v.y) * E[z];
+            }
+            if (k > 0) top.offer(v, (uint32_t)z, ok);
+        }
+        ex += (double)acc;
+    }
+    const double tot = block_sum(ex, red);
+    if (threadIdx.x == 0) part_expect[blockIdx.x] = tot;
+    if (k > 0) {
+        if (lane < k) tops[warp * 32 + lane] = TopEnt{top.p, top.z};
+        __syncthreads();
+        if (warp == 0) {
+            WarpTopK f;
+            f.init(k);
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const bool ok = lane < k;
+                const TopEnt e = ok ? tops[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
+                f.offer_exact(e.p, e.z, ok);
+            }
+            if (lane < k) {
+                part_topp[(uint64_t)blockIdx.x * k + lane] = f.p;
+                part_topz[(uint64_t)blockIdx.x * k + lane] = f.z;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_finalize(int nparts, const double* part_expect,
+                                                         const double* part_topp,
+                                                         const uint32_t* part_topz, int k,
+                                                         double* expect, uint64_t* topk_idx,
+                                                         double* topk_prob) {
+    __shared__ double red[32];
+    __shared__ TopEnt tops[8 * 32];
+    double acc = 0.0;
+    const int per = (nparts + blockDim.x - 1) / blockDim.x;
+    for (int t = threadIdx.x * per; t < (int)(threadIdx.x + 1) * per && t < nparts; ++t)
+        acc += part_expect[t];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0 && expect) *expect = tot;
+    if (k > 0) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        WarpTopK top;
+        top.init(k);
+        const int nent = nparts * k;
+        for (int e0 = warp * 32; e0 < nent; e0 += (int)(blockDim.x >> 5) * 32) {
+            const int e = e0 + lane;
+            const bool ok = e < nent;
+            top.offer_exact(ok ? part_topp[e] : -1.0, ok ? part_topz[e] : 0u, ok);
+        }
+        if (lane < k) tops[warp * 32 + lane] = TopEnt{top.p, top.z};
+        __syncthreads();
+        if (warp == 0) {
+            WarpTopK f;
+            f.init(k);
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const bool ok = lane < k;
+                const TopEnt e = ok ? tops[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
+                f.offer_exact(e.p, e.z, ok);
+            }
+            if (lane < k) {
+                if (topk_idx) topk_idx[lane] = (uint64_t)f.z;
+                if (topk_prob) topk_prob[lane] = f.p;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+
+int stream_tile_bits(bool dbl) { return dbl ? 12 : 13; }
+
+// HBM windows of a layer: window 0 = kind A (qubits 0..tb-1); windows 1.. = kind B chunks of
+// the qubits [tb, n), as equal as possible, each at most tb - 4 qubits.
+int stream_plan(bool dbl, int n, int p, int k, StreamPass* out, int max_out) {
+    const int tb = stream_tile_bits(dbl);
+    if (n <= tb) return -1;
+    const int hmax = tb - 4;
+    const int rest = n - tb;
+    const int nB = (rest + hmax - 1) / hmax;
+    int chunk_s[16], chunk_h[16];
+    int s0 = tb;
+    for (int i = 0; i < nB; ++i) {
+        const int h = rest / nB + (i < rest % nB ? 1 : 0);
+        chunk_s[i] = s0;
+        chunk_h[i] = h;
+        s0 += h;
+    }
+    const int G = 1 + nB;
+    const int S = (G <= 1) ? p : 1 + p * (G - 1);
+    if (S > max_out) return -1;
+    for (int si = 0; si < S; ++si) {
+        int l, pos;
+        if (si < G) { l = 0; pos = si; }
+        else { l = 1 + (si - G) / (G - 1); pos = 1 + (si - G) % (G - 1); }
+        const int w = (l % 2 == 0) ? pos : (G - 1 - pos);
+        StreamPass P{};
+        P.n = n;
+        P.tb = tb;
+        P.la = l;
+        P.lb = (pos == G - 1 && l + 1 < p) ? l + 1 : l;
+        P.ph_first = (l == 0 && pos == 0) ? 1 : 0;
+        P.init = (si == 0) ? 1 : 0;
+        P.fin = (si == S - 1) ? 1 : 0;
+        P.k = P.fin ? k : 0;
+        if (w == 0) {
+            P.kind = 0;
+            P.c = tb; P.s = tb; P.h = 0;
+        } else {
+            P.kind = 1;
+            P.h = chunk_h[w - 1];
+            P.s = chunk_s[w - 1];
+            P.c = tb - P.h;
+        }
+        P.need_e = (P.ph_first || P.lb > P.la || P.fin) ? 1 : 0;
+        out[si] = P;
+    }
+    return S;
+}
+
+size_t stream_smem_bytes(bool dbl) {
+    const size_t TD = (size_t)1 << stream_tile_bits(dbl);
+    const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4, lcs = dbl ? 24 : 12;
+    size_t o = TD * c + TD * r + 64 * lcs;
+    o = (o + 15) & ~(size_t)15;
+    return o + 32 * sizeof(double) + 8 * 32 * sizeof(TopEnt);
+}
+
+template <typename T>
+static StreamInst<T> one_of(const void* one) {
+    StreamInst<T> o{};
+    if (one) o = *static_cast<const StreamInst<T>*>(one);
+    return o;
+}
+
+cudaError_t launch_stream_pass(bool dbl, const StreamPass& P, const void* insts, int count,
+                               int grid, cudaStream_t st, const void* one) {
+    const size_t sm = stream_smem_bytes(dbl);
+    cudaError_t e;
+    if (dbl) {
+        e = cudaFuncSetAttribute(k_stream_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_stream_pass<double><<<grid, 256, sm, st>>>(P, static_cast<const StreamInst<double>*>(insts), count, one_of<double>(one));
+    } else {
+        e = cudaFuncSetAttribute(k_stream_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_stream_pass<float><<<grid, 256, sm, st>>>(P, static_cast<const StreamInst<float>*>(insts), count, one_of<float>(one));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint64_t ntiles, int k,
+                                   cudaStream_t st, const void* one) {
+    if (dbl) k_stream_finalize<double><<<count, 256, 0, st>>>(static_cast<const StreamInst<double>*>(insts), count, ntiles, k, one_of<double>(one));
+    else k_stream_finalize<float><<<count, 256, 0, st>>>(static_cast<const StreamInst<float>*>(insts), count, ntiles, k, one_of<float>(one));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st) {
+    // low bits fixed per thread: enough threads to fill the GPU, at most 2^12 Gray steps each
+    int m = n - 6;
+    if (m < 0) m = 0;
+    if (m > 20) m = 20;
+    if (n - m > 12) m = n - 12;
+    const uint64_t threads = 1ull << m;
+    const int block = threads < 256 ? (int)threads : 256;
+    const uint64_t grid = (threads + block - 1) / block;
+    if (dbl) k_energy<double><<<(unsigned)grid, block, 0, st>>>(n, m, static_cast<const double*>(Q), static_cast<double*>(E));
+    else k_energy<float><<<(unsigned)grid, block, 0, st>>>(n, m, static_cast<const float*>(Q), static_cast<float*>(E));
+    return cudaGetLastError();
+}
+
+int reduce_parts(int n) {
+    const uint64_t D = 1ull << n;
+    uint64_t b = (D + 256 * 32 - 1) / (256 * 32);
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_reduce_state(bool dbl, int n, const void* psi, const void* E, int k,
+                                double* part_expect, double* part_topp, uint32_t* part_topz,
+                                double* expect, uint64_t* topk_idx, double* topk_prob,
+                                cudaStream_t st) {
+    const int parts = reduce_parts(n);
+    if (dbl) k_reduce_state<double><<<parts, 256, 0, st>>>(n, static_cast<const double2*>(psi), static_cast<const double*>(E), k, part_expect, part_topp, part_topz);
+    else k_reduce_state<float><<<parts, 256, 0, st>>>(n, static_cast<const float2*>(psi), static_cast<const float*>(E), k, part_expect, part_topp, part_topz);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_finalize<<<1, 256, 0, st>>>(parts, part_expect, part_topp, part_topz, k, expect, topk_idx, topk_prob);
+    return cudaGetLastError();
+}
+
+}  // namespace qaoa

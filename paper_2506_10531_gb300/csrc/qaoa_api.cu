@@ -1,0 +1,608 @@
+// qaoa_api.cu -- the C ABI of libqaoa (include/qaoa.h): argument validation, the context and
+// its workspace, tier selection, batched launch plans, and the DQAOA host entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/qaoa.h"
+#include "qaoa_common.cuh"
+#include "qaoa_host.h"
+#include "qaoa_kernels.h"
+#include "qaoa_stream.h"
+
+using namespace qaoa;
+
+struct qaoa_ctx {
+    int device = 0;
+    int nsm = 0;
+    void* ws = nullptr;       // workspace (device)
+    size_t ws_bytes = 0;
+    int* queue = nullptr;     // work counters of the single-call launches (device)
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+qaoa_status fail(qaoa_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+qaoa_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(QAOA_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+constexpr int NMAX = 30, PMAX = 64, KMAX = 16;
+
+bool bad_nk(int n, int k) {
+    return n < 1 || n > NMAX || k < 0 || k > KMAX || (uint64_t)k > (1ull << n);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch of one streaming instance: per-tile <C> partials and top-k lists, laid out as
+// [expect (nt doubles)] [probabilities (nt*k doubles)] [indices (nt*k uint32)], each 256-aligned.
+size_t stream_scratch_bytes(bool dbl, int n, int k) {
+    const int tb = stream_tile_bits(dbl);
+    if (n <= tb) return 0;
+    const size_t nt = (size_t)1 << (n - tb), kk = (size_t)std::max(k, 1);
+    return align256(nt * sizeof(double)) + align256(nt * kk * sizeof(double)) +
+           align256(nt * kk * sizeof(uint32_t));
+}
+
+// Scratch of the standalone reductions: the same three arrays for reduce_parts(n) blocks.
+size_t reduce_scratch_bytes(int n) {
+    const size_t parts = (size_t)reduce_parts(n);
+    return align256(parts * sizeof(double)) + align256(parts * KMAX * sizeof(double)) +
+           align256(parts * KMAX * sizeof(uint32_t));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+qaoa_status ensure_ws(qaoa_ctx* c, size_t bytes) {
+    if (bytes <= c->ws_bytes) return QAOA_OK;
+    return fail(QAOA_E_NOMEM, "workspace of %zu bytes needed, %zu reserved (call qaoa_reserve)",
+                bytes, c->ws_bytes);
+}
+
+template <typename T>
+bool is_dbl() { return sizeof(T) == 8; }
+
+// ---- resident single instance ------------------------------------------------------------
+template <typename T>
+qaoa_status run_resident_one(qaoa_ctx* c, const InstDesc<T>& d, cudaStream_t st) {
+    const bool dbl = is_dbl<T>();
+    const bool grad = (d.flags & F_GRAD) != 0;
+    // the descriptor travels by value as a kernel parameter
+    CK(launch_resident(dbl, nullptr, 1, d.n, d.p, grad, nullptr, 1, st, &d));
+    return QAOA_OK;
+}
+
+// ---- streaming single instance -----------------------------------------------------------
+template <typename T>
+qaoa_status run_stream_one(qaoa_ctx* c, int n, int p, const T* gamma, const T* beta, const T* E,
+                           void* psi, bool init_plus, int k, double* expect, uint64_t* tidx,
+                           double* tprob, size_t ws_off, cudaStream_t st) {
+    const bool dbl = is_dbl<T>();
+    if (!init_plus)
+        return fail(QAOA_E_UNSUPPORTED, "streaming tier (n=%d) starts from |+> only", n);
+    StreamPass passes[256];
+    const int S = stream_plan(dbl, n, p, k, passes, 256);
+    if (S < 0) return fail(QAOA_E_INVALID, "no streaming plan for n=%d p=%d", n, p);
+    const int tb = stream_tile_bits(dbl);
+    const uint64_t nt = 1ull << (n - tb);
+    char* w = static_cast<char*>(c->ws) + ws_off;
+    StreamInst<T> I{};
+    I.p = p;
+    I.amp0 = exp2(-0.5 * n);
+    I.gamma = gamma;
+    I.beta = beta;
+    I.psi = psi;
+    I.E = E;
+    I.part_expect = reinterpret_cast<double*>(w);
+    I.part_topp = reinterpret_cast<double*>(w + align256(nt * sizeof(double)));
+    I.part_topz = reinterpret_cast<uint32_t*>(w + align256(nt * sizeof(double)) +
+                                             align256(nt * std::max(k, 1) * sizeof(double)));
+    I.expect = expect;
+    I.topk_idx = tidx;
+    I.topk_prob = tprob;
+    const int grid = (int)std::min<uint64_t>(nt, (uint64_t)c->nsm * 2);
+    for (int s = 0; s < S; ++s) CK(launch_stream_pass(dbl, passes[s], nullptr, 1, grid, st, &I));
+    if (expect || (k > 0 && tidx)) CK(launch_stream_finalize(dbl, nullptr, 1, nt, k, st, &I));
+    return QAOA_OK;
+}
+
+template <typename T>
+qaoa_status build_energies_t(qaoa_ctx* c, int n, const T* Q, T* E, qaoa_stream_t stream) {
+    if (!c) return fail(QAOA_E_INVALID, "ctx is NULL");
+    if (n < 1 || n > NMAX || !Q || !E) return fail(QAOA_E_INVALID, "build_energies: bad n or NULL");
+    CK(launch_energy(is_dbl<T>(), n, Q, E, (cudaStream_t)stream));
+    return QAOA_OK;
+}
+
+template <typename T>
+qaoa_status run_layers_t(qaoa_ctx* c, int n, int p, const T* gamma, const T* beta, const T* E,
+                         void* psi, int init_plus, qaoa_stream_t stream) {
+    if (!c) return fail(QAOA_E_INVALID, "ctx is NULL");
+    if (n < 1 || n > NMAX || p < 1 || p > PMAX || !gamma || !beta || !E || !psi)
+        return fail(QAOA_E_INVALID, "run_layers: n=%d p=%d or NULL pointer", n, p);
+    if (!aligned16(psi)) return fail(QAOA_E_INVALID, "run_layers: psi must be 16-byte aligned");
+    const bool dbl = is_dbl<T>();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n <= (dbl ? RES_NMAX_D : RES_NMAX_F)) {
+        InstDesc<T> d{};
+        d.n = n; d.p = p; d.k = 0; d.flags = init_plus ? 0 : F_INIT_PSI;
+        d.E_in = E; d.gamma = gamma; d.beta = beta;
+        d.psi_in = psi; d.psi_out = psi;
+        return run_resident_one<T>(c, d, st);
+    }
+    qaoa_status s = ensure_ws(c, stream_scratch_bytes(dbl, n, 0));
+    if (s) return s;
+    return run_stream_one<T>(c, n, p, gamma, beta, E, psi, init_plus != 0, 0, nullptr, nullptr,
+                             nullptr, 0, st);
+}
+
+template <typename T>
+qaoa_status reduce_t(qaoa_ctx* c, int n, const void* psi, const T* E, int k, double* expect,
+                     uint64_t* idx, double* prob, qaoa_stream_t stream) {
+    if (!c) return fail(QAOA_E_INVALID, "ctx is NULL");
+    if (bad_nk(n, k) || !psi) return fail(QAOA_E_INVALID, "reduce: bad n/k or NULL psi");
+    qaoa_status s = ensure_ws(c, reduce_scratch_bytes(n));
+    if (s) return s;
+    const int parts = reduce_parts(n);
+    char* w = static_cast<char*>(c->ws);
+    double* pe = reinterpret_cast<double*>(w);
+    double* pp = reinterpret_cast<double*>(w + align256(parts * sizeof(double)));
+    uint32_t* pz = reinterpret_cast<uint32_t*>(w + align256(parts * sizeof(double)) +
+                                               align256((size_t)parts * KMAX * sizeof(double)));
+    CK(launch_reduce_state(is_dbl<T>(), n, psi, E, k, pe, pp, pz, expect, idx, prob,
+                           (cudaStream_t)stream));
+    return QAOA_OK;
+}
+
+template <typename T>
+qaoa_status grad_t(qaoa_ctx* c, int n, int p, const T* gamma, const T* beta, const T* E,
+                   double* expect, double* dgamma, double* dbeta, qaoa_stream_t stream) {
+    if (!c) return fail(QAOA_E_INVALID, "ctx is NULL");
+    if (n < 1 || n > NMAX || p < 1 || p > PMAX || !gamma || !beta || !E || !dgamma || !dbeta)
+        return fail(QAOA_E_INVALID, "grad: n=%d p=%d or NULL pointer", n, p);
+    const bool dbl = is_dbl<T>();
+    if (n > (dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ))
+        return fail(QAOA_E_UNSUPPORTED, "grad: n=%d above the shared-memory tier", n);
+    InstDesc<T> d{};
+    d.n = n; d.p = p; d.k = 0; d.flags = F_GRAD;
+    d.E_in = E; d.gamma = gamma; d.beta = beta;
+    d.expect = expect; d.dgamma = dgamma; d.dbeta = dbeta;
+    return run_resident_one<T>(c, d, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+// =============================================================================================
+// Context
+// =============================================================================================
+
+extern "C" qaoa_status qaoa_create(qaoa_ctx** out, int device) {
+    if (!out) return fail(QAOA_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(QAOA_E_INVALID, "device %d of %d", device, ndev);
+    CK(cudaSetDevice(device));
+    qaoa_ctx* c = new qaoa_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaMalloc(&c->queue, 256);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(queue)"); }
+    c->ws_bytes = 1 << 20;
+    e = cudaMalloc(&c->ws, c->ws_bytes);
+    if (e != cudaSuccess) { cudaFree(c->queue); delete c; return cuda_fail(e, "cudaMalloc(ws)"); }
+    *out = c;
+    return QAOA_OK;
+}
+
+extern "C" void qaoa_destroy(qaoa_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    cudaFree(c->queue);
+    delete c;
+}
+
+extern "C" const char* qaoa_last_error(void) { return g_err.c_str(); }
+
+extern "C" qaoa_status qaoa_reserve(qaoa_ctx* c, size_t bytes) {
+    if (!c) return fail(QAOA_E_INVALID, "ctx is NULL");
+    bytes = align256(bytes);
+    if (bytes <= c->ws_bytes) return QAOA_OK;
+    CK(cudaSetDevice(c->device));
+    CK(cudaDeviceSynchronize());
+    void* nw = nullptr;
+    cudaError_t e = cudaMalloc(&nw, bytes);
+    if (e != cudaSuccess) return fail(QAOA_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    cudaFree(c->ws);
+    c->ws = nw;
+    c->ws_bytes = bytes;
+    return QAOA_OK;
+}
+
+extern "C" size_t qaoa_workspace_bytes(int n, int dbl) {
+    if (n < 1 || n > NMAX) return 0;
+    return std::max(stream_scratch_bytes(dbl != 0, n, KMAX), reduce_scratch_bytes(n));
+}
+
+// =============================================================================================
+// Single-instance calls
+// =============================================================================================
+
+extern "C" qaoa_status qaoa_build_energies(qaoa_ctx* c, int n, const float* Q, float* E, qaoa_stream_t s) {
+    return build_energies_t<float>(c, n, Q, E, s);
+}
+extern "C" qaoa_status qaoa_build_energies_z(qaoa_ctx* c, int n, const double* Q, double* E, qaoa_stream_t s) {
+    return build_energies_t<double>(c, n, Q, E, s);
+}
+extern "C" qaoa_status qaoa_run_layers(qaoa_ctx* c, int n, int p, const float* g, const float* b,
+                                       const float* E, void* psi, int init_plus, qaoa_stream_t s) {
+    return run_layers_t<float>(c, n, p, g, b, E, psi, init_plus, s);
+}
+extern "C" qaoa_status qaoa_run_layers_z(qaoa_ctx* c, int n, int p, const double* g, const double* b,
+                                         const double* E, void* psi, int init_plus, qaoa_stream_t s) {
+    return run_layers_t<double>(c, n, p, g, b, E, psi, init_plus, s);
+}
+extern "C" qaoa_status qaoa_expect(qaoa_ctx* c, int n, const void* psi, const float* E, double* out,
+                                   qaoa_stream_t s) {
+    if (!E || !out) return fail(QAOA_E_INVALID, "expect: NULL E or out");
+    return reduce_t<float>(c, n, psi, E, 0, out, nullptr, nullptr, s);
+}
+extern "C" qaoa_status qaoa_expect_z(qaoa_ctx* c, int n, const void* psi, const double* E, double* out,
+                                     qaoa_stream_t s) {
+    if (!E || !out) return fail(QAOA_E_INVALID, "expect: NULL E or out");
+    return reduce_t<double>(c, n, psi, E, 0, out, nullptr, nullptr, s);
+}
+extern "C" qaoa_status qaoa_topk(qaoa_ctx* c, int n, const void* psi, int k, uint64_t* idx, double* prob,
+                                 qaoa_stream_t s) {
+    if (k < 1 || !idx) return fail(QAOA_E_INVALID, "topk: k=%d or NULL idx", k);
+    return reduce_t<float>(c, n, psi, (const float*)nullptr, k, nullptr, idx, prob, s);
+}
+extern "C" qaoa_status qaoa_topk_z(qaoa_ctx* c, int n, const void* psi, int k, uint64_t* idx, double* prob,
+                                   qaoa_stream_t s) {
+    if (k < 1 || !idx) return fail(QAOA_E_INVALID, "topk: k=%d or NULL idx", k);
+    return reduce_t<double>(c, n, psi, (const double*)nullptr, k, nullptr, idx, prob, s);
+}
+extern "C" qaoa_status qaoa_grad(qaoa_ctx* c, int n, int p, const float* g, const float* b, const float* E,
+                                 double* ex, double* dg, double* db, qaoa_stream_t s) {
+    return grad_t<float>(c, n, p, g, b, E, ex, dg, db, s);
+}
+extern "C" qaoa_status qaoa_grad_z(qaoa_ctx* c, int n, int p, const double* g, const double* b,
+                                   const double* E, double* ex, double* dg, double* db, qaoa_stream_t s) {
+    return grad_t<double>(c, n, p, g, b, E, ex, dg, db, s);
+}
+
+// =============================================================================================
+// Batched plans
+// =============================================================================================
+
+struct qaoa_plan {
+    qaoa_ctx* ctx = nullptr;
+    bool dbl = false;
+    void* dev = nullptr;          // one device block: descriptors, scratch, counters
+    size_t dev_bytes = 0;
+    struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
+    struct StrGroup { int n, p, k, count; size_t inst_off; std::vector<StreamPass> passes; int grid;
+                      std::vector<int> e_build; std::vector<const void*> q; std::vector<void*> e; };
+    std::vector<ResGroup> res;
+    std::vector<StrGroup> str;
+    int kernels = 0;
+};
+
+namespace {
+
+template <typename T>
+qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const qaoa_batch_io* io,
+                          qaoa_plan** out) {
+    using C2 = typename qaoa::Num<T>::C;
+    const bool dbl = is_dbl<T>();
+    const T* qpool = static_cast<const T*>(io->q);
+    const T* ppool = static_cast<const T*>(io->params);
+    C2* psipool = static_cast<C2*>(io->psi);
+    T* epool = static_cast<T*>(io->e);
+    // validate
+    for (int i = 0; i < count; ++i) {
+        const qaoa_inst& d = desc[i];
+        if (bad_nk(d.n, d.k) || d.p < 1 || d.p > PMAX || d.q_off < 0 || d.par_off < 0)
+            return fail(QAOA_E_INVALID, "instance %d: n=%d p=%d k=%d offsets %lld %lld", i, d.n, d.p,
+                        d.k, (long long)d.q_off, (long long)d.par_off);
+        if (d.k > 0 && (!io->topk_idx || io->k_stride < d.k))
+            return fail(QAOA_E_INVALID, "instance %d: top-k output missing or k_stride < k", i);
+        if (d.psi_off >= 0 && !io->psi) return fail(QAOA_E_INVALID, "instance %d: psi pool NULL", i);
+        if (d.psi_off >= 0 && !aligned16(static_cast<const C2*>(io->psi) + d.psi_off))
+            return fail(QAOA_E_INVALID, "instance %d: state at psi_off must be 16-byte aligned", i);
+        if (d.e_off >= 0 && !io->e) return fail(QAOA_E_INVALID, "instance %d: energy pool NULL", i);
+        if ((d.flags & QAOA_INST_GRAD) && !io->grad) return fail(QAOA_E_INVALID, "instance %d: grad pool NULL", i);
+        if ((d.flags & QAOA_INST_GRAD) && d.n > (dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ))
+            return fail(QAOA_E_UNSUPPORTED, "instance %d: gradient for n=%d above the shared-memory tier", i, d.n);
+    }
+    qaoa_plan* P = new qaoa_plan();
+    P->ctx = c;
+    P->dbl = dbl;
+    // group: resident by (n, grad); streaming by (n, p, k)
+    std::map<std::pair<int, int>, std::vector<int>> rg;
+    std::map<std::tuple<int, int, int>, std::vector<int>> sg;
+    const int nres = dbl ? RES_NMAX_D : RES_NMAX_F;
+    for (int i = 0; i < count; ++i) {
+        const qaoa_inst& d = desc[i];
+        if (d.n <= nres) rg[{d.n, (d.flags & QAOA_INST_GRAD) ? 1 : 0}].push_back(i);
+        else sg[{d.n, d.p, d.k}].push_back(i);
+    }
+    // sizes
+    size_t bytes = 256;  // counters
+    std::vector<InstDesc<T>> rdesc;
+    int qslot = 0;
+    for (auto& kv : rg) {
+        qaoa_plan::ResGroup g{};
+        g.n = kv.first.first;
+        g.grad = kv.first.second != 0;
+        g.count = (int)kv.second.size();
+        g.pmax = 1;
+        g.desc_off = bytes;
+        g.q_slot = qslot++;
+        for (int i : kv.second) {
+            const qaoa_inst& d = desc[i];
+            g.pmax = std::max(g.pmax, d.p);
+            InstDesc<T> x{};
+            x.n = d.n; x.p = d.p; x.k = d.k;
+            x.flags = (d.flags & QAOA_INST_GRAD) ? F_GRAD : 0;
+            x.Q = qpool + d.q_off;
+            x.gamma = ppool + d.par_off;
+            x.beta = ppool + d.par_off + d.p;
+            x.psi_out = d.psi_off >= 0 ? (void*)(psipool + d.psi_off) : nullptr;
+            x.E_out = d.e_off >= 0 ? epool + d.e_off : nullptr;
+            x.expect = io->expect ? io->expect + i : nullptr;
+            x.topk_idx = d.k > 0 ? io->topk_idx + (int64_t)i * io->k_stride : nullptr;
+            x.topk_prob = (d.k > 0 && io->topk_prob) ? io->topk_prob + (int64_t)i * io->k_stride : nullptr;
+            x.dgamma = (x.flags & F_GRAD) ? io->grad + d.par_off : nullptr;
+            x.dbeta = (x.flags & F_GRAD) ? io->grad + d.par_off + d.p : nullptr;
+            rdesc.push_back(x);
+        }
+        bytes = align256(bytes + sizeof(InstDesc<T>) * g.count);
+        const int occ = std::max(1, resident_max_blocks_per_sm(dbl, g.n, g.pmax, g.grad));
+        g.grid = std::min(g.count, occ * c->nsm);
+        P->res.push_back(g);
+    }
+    if (qslot > 60) { delete P; return fail(QAOA_E_UNSUPPORTED, "too many resident groups"); }
+    // streaming: per instance its own E / psi / partial buffers inside the plan block
+    struct SI { size_t e_off, psi_off, part_off; };
+    std::vector<std::vector<SI>> sinfo;
+    const int tb = stream_tile_bits(dbl);
+    for (auto& kv : sg) {
+        qaoa_plan::StrGroup g{};
+        g.n = std::get<0>(kv.first);
+        g.p = std::get<1>(kv.first);
+        g.k = std::get<2>(kv.first);
+        g.count = (int)kv.second.size();
+        StreamPass tmp[256];
+        const int S = stream_plan(dbl, g.n, g.p, g.k, tmp, 256);
+        if (S < 0) { delete P; return fail(QAOA_E_INVALID, "no streaming plan for n=%d p=%d", g.n, g.p); }
+        g.passes.assign(tmp, tmp + S);
+        g.inst_off = bytes;
+        bytes = align256(bytes + sizeof(StreamInst<T>) * g.count);
+        std::vector<SI> v;
+        const uint64_t D = 1ull << g.n, nt = 1ull << (g.n - tb);
+        for (int i : kv.second) {
+            SI s{};
+            const qaoa_inst& d = desc[i];
+            s.e_off = (d.e_off >= 0) ? (size_t)-1 : bytes;
+            if (d.e_off < 0) bytes = align256(bytes + D * sizeof(T));
+            s.psi_off = (d.psi_off >= 0) ? (size_t)-1 : bytes;
+            if (d.psi_off < 0) bytes = align256(bytes + D * sizeof(C2));
+            s.part_off = bytes;
+            bytes = align256(bytes + nt * sizeof(double));
+            bytes = align256(bytes + nt * std::max(g.k, 1) * sizeof(double));
+            bytes = align256(bytes + nt * std::max(g.k, 1) * sizeof(uint32_t));
+            v.push_back(s);
+        }
+        const uint64_t tiles = nt * (uint64_t)g.count;
+        g.grid = (int)std::min<uint64_t>(tiles, (uint64_t)c->nsm * 2);
+        sinfo.push_back(v);
+        P->str.push_back(std::move(g));
+    }
+    cudaError_t e = cudaMalloc(&P->dev, bytes);
+    if (e != cudaSuccess) { delete P; return fail(QAOA_E_NOMEM, "plan cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e)); }
+    P->dev_bytes = bytes;
+    char* base = static_cast<char*>(P->dev);
+    // upload resident descriptors
+    size_t ri = 0;
+    for (auto& g : P->res) {
+        e = cudaMemcpy(base + g.desc_off, rdesc.data() + ri, sizeof(InstDesc<T>) * g.count, cudaMemcpyHostToDevice);
+        ri += g.count;
+        if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload descriptors"); }
+        P->kernels += 2;  // memset counter + kernel
+    }
+    // build streaming instances
+    size_t gi = 0;
+    for (auto& kv : sg) {
+        auto& g = P->str[gi];
+        std::vector<StreamInst<T>> si;
+        const uint64_t nt = 1ull << (g.n - tb);
+        size_t j = 0;
+        for (int i : kv.second) {
+            const qaoa_inst& d = desc[i];
+            const SI& s = sinfo[gi][j++];
+            StreamInst<T> I{};
+            I.p = d.p;
+            I.amp0 = exp2(-0.5 * d.n);
+            I.gamma = ppool + d.par_off;
+            I.beta = ppool + d.par_off + d.p;
+            I.psi = (s.psi_off == (size_t)-1) ? (void*)(psipool + d.psi_off) : (void*)(base + s.psi_off);
+            T* Ebuf = (s.e_off == (size_t)-1) ? epool + d.e_off : reinterpret_cast<T*>(base + s.e_off);
+            I.E = Ebuf;
+            char* pw = base + s.part_off;
+            I.part_expect = reinterpret_cast<double*>(pw);
+            pw += align256(nt * sizeof(double));
+            I.part_topp = reinterpret_cast<double*>(pw);
+            pw += align256(nt * std::max(g.k, 1) * sizeof(double));
+            I.part_topz = reinterpret_cast<uint32_t*>(pw);
+            I.expect = io->expect ? io->expect + i : nullptr;
+            I.topk_idx = d.k > 0 ? io->topk_idx + (int64_t)i * io->k_stride : nullptr;
+            I.topk_prob = (d.k > 0 && io->topk_prob) ? io->topk_prob + (int64_t)i * io->k_stride : nullptr;
+            si.push_back(I);
+            g.q.push_back(qpool + d.q_off);
+            g.e.push_back(Ebuf);
+        }
+        e = cudaMemcpy(base + g.inst_off, si.data(), sizeof(StreamInst<T>) * g.count, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload stream instances"); }
+        P->kernels += g.count + (int)g.passes.size() + 1;
+        ++gi;
+    }
+    *out = P;
+    return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" qaoa_status qaoa_plan_create(qaoa_ctx* c, const qaoa_inst* desc, int count,
+                                        const qaoa_batch_io* io, int dbl, qaoa_plan** out) {
+    if (!c || !desc || !io || !out || count < 1 || !io->q || !io->params)
+        return fail(QAOA_E_INVALID, "plan_create: NULL argument or count < 1");
+    *out = nullptr;
+    CK(cudaSetDevice(c->device));
+    return dbl ? plan_create_t<double>(c, desc, count, io, out)
+               : plan_create_t<float>(c, desc, count, io, out);
+}
+
+extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
+    if (!P) return fail(QAOA_E_INVALID, "plan is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = static_cast<char*>(P->dev);
+    int* counters = reinterpret_cast<int*>(base);
+    for (auto& g : P->res) {
+        CK(cudaMemsetAsync(counters + g.q_slot, 0, sizeof(int), st));
+        CK(launch_resident(P->dbl, base + g.desc_off, g.count, g.n, g.pmax, g.grad, counters + g.q_slot,
+                           g.grid, st));
+    }
+    const int tb = stream_tile_bits(P->dbl);
+    for (auto& g : P->str) {
+        for (int i = 0; i < g.count; ++i) CK(launch_energy(P->dbl, g.n, g.q[i], g.e[i], st));
+        for (auto& pass : g.passes) CK(launch_stream_pass(P->dbl, pass, base + g.inst_off, g.count, g.grid, st));
+        CK(launch_stream_finalize(P->dbl, base + g.inst_off, g.count, 1ull << (g.n - tb), g.k, st));
+    }
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_plan_kernel_count(const qaoa_plan* P) { return P ? P->kernels : 0; }
+
+extern "C" void qaoa_plan_destroy(qaoa_plan* P) {
+    if (!P) return;
+    cudaSetDevice(P->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(P->dev);
+    delete P;
+}
+
+static qaoa_status batch_run(qaoa_ctx* c, const qaoa_inst* desc, int count, const qaoa_batch_io* io,
+                             qaoa_stream_t stream, int dbl) {
+    qaoa_plan* P = nullptr;
+    qaoa_status s = qaoa_plan_create(c, desc, count, io, dbl, &P);
+    if (s) return s;
+    s = qaoa_plan_launch(P, stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    qaoa_plan_destroy(P);
+    if (s) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "batch_run synchronize");
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status qaoa_batch_run(qaoa_ctx* c, const qaoa_inst* d, int n, const qaoa_batch_io* io,
+                                      qaoa_stream_t s) {
+    return batch_run(c, d, n, io, s, 0);
+}
+extern "C" qaoa_status qaoa_batch_run_z(qaoa_ctx* c, const qaoa_inst* d, int n, const qaoa_batch_io* io,
+                                        qaoa_stream_t s) {
+    return batch_run(c, d, n, io, s, 1);
+}
+
+// =============================================================================================
+// Plain path
+// =============================================================================================
+
+extern "C" qaoa_status qaoa_plain_solve(qaoa_ctx* c, int n, int p, const float* Q, const float* gamma,
+                                        const float* beta, float* E, void* psi, int k, double* expect,
+                                        uint64_t* topk_idx, double* topk_prob, qaoa_stream_t stream) {
+    if (!c) return fail(QAOA_E_INVALID, "ctx is NULL");
+    if (bad_nk(n, k) || p < 1 || p > PMAX || !Q || !gamma || !beta || !E || !psi)
+        return fail(QAOA_E_INVALID, "plain_solve: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_energy(false, n, Q, E, st));
+    CK(launch_plain_layers(n, p, gamma, beta, E, static_cast<float2*>(psi), 1, st, nullptr));
+    return reduce_t<float>(c, n, psi, E, k, expect, topk_idx, topk_prob, stream);
+}
+
+// =============================================================================================
+// DQAOA host steps
+// =============================================================================================
+
+extern "C" qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t* x, int method, int m,
+                                          int k, uint64_t seed, uint64_t cycle, int32_t* idx) {
+    if (N < 1 || m < 1 || k < 1 || k > N || !idx) return fail(QAOA_E_INVALID, "draw: N=%d m=%d k=%d", N, m, k);
+    if (method == DQAOA_RANDOM) {
+        draw_random(N, m, k, seed, cycle, idx);
+        return QAOA_OK;
+    }
+    if (method == DQAOA_IFD) {
+        if (!Q || !x) return fail(QAOA_E_INVALID, "IFD needs Q and x");
+        if (m + k - 1 > N) return fail(QAOA_E_INVALID, "IFD needs m + k - 1 <= N");
+        draw_ifd(Q, N, x, m, k, idx);
+        return QAOA_OK;
+    }
+    return fail(QAOA_E_INVALID, "unknown decomposition method %d", method);
+}
+
+extern "C" qaoa_status dqaoa_decompose(const double* Q, int N, const uint8_t* x, int method, int conditioned,
+                                       int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx,
+                                       double* Qsub) {
+    if (!Q || !Qsub) return fail(QAOA_E_INVALID, "decompose: NULL Q or Qsub");
+    if (conditioned && !x) return fail(QAOA_E_INVALID, "decompose: conditioning needs x");
+    qaoa_status s = dqaoa_draw_indices(Q, N, x, method, m, k, seed, cycle, idx);
+    if (s) return s;
+    build_subqubos(Q, N, x, m, k, idx, conditioned, Qsub);
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status dqaoa_subqubo_build(qaoa_ctx* c, const double* Q, int N, const uint8_t* x, int m,
+                                           int k, const int32_t* idx, int conditioned, float* qsub,
+                                           qaoa_stream_t stream) {
+    if (!c || !Q || N < 1 || m < 1 || k < 1 || k > N || k > 4096 || !idx || !qsub || (conditioned && !x))
+        return fail(QAOA_E_INVALID, "subqubo_build: bad arguments");
+    CK(launch_subqubo(Q, N, x, m, k, idx, conditioned, qsub, (cudaStream_t)stream));
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status dqaoa_merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx,
+                                   int K, const uint64_t* cand, double* energy_out, int* accepted_out) {
+    if (!Q || N < 1 || !x || m < 1 || k < 1 || k > 64 || K < 1 || !idx || !cand)
+        return fail(QAOA_E_INVALID, "merge: bad arguments");
+    for (int64_t t = 0; t < (int64_t)m * k; ++t)
+        if (idx[t] < 0 || idx[t] >= N) return fail(QAOA_E_INVALID, "merge: index %d out of range", idx[t]);
+    merge(Q, N, x, m, k, idx, K, cand, energy_out, accepted_out);
+    return QAOA_OK;
+}

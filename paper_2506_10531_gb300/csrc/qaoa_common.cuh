@@ -1,0 +1,162 @@
+// qaoa_common.cuh -- shared device helpers of libqaoa (types, shared-memory swizzle, the
+// butterfly of the mixer, the cost phase, warp-level top-k lists and fixed-order reductions).
+//
+// Conventions used everywhere in the library (arXiv 2506.10531, Section IV, Eq. 2):
+//   * bit q of a basis index z is qubit q (sub-QUBO variable S[q]);
+//   * the cost layer multiplies psi(z) by exp(-i gamma E(z));
+//   * the mixer layer applies exp(-i beta X_q) to every qubit q: on the amplitude pair
+//     (a, b) = (psi[z], psi[z | 2^q]) with bit q of z clear,
+//       a' = cos(beta) a - i sin(beta) b,   b' = -i sin(beta) a + cos(beta) b.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qaoa {
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+    using C = float2;
+    static constexpr int RB = 5;        // register window (qubits) of one sub-pass, forward
+    static constexpr int RB_ADJ = 4;    // register window of the adjoint (two states live)
+};
+template <> struct Num<double> {
+    using C = double2;
+    static constexpr int RB = 4;
+    static constexpr int RB_ADJ = 3;
+};
+
+// Shared-memory swizzle of a tile index: XOR the low SW bits with the next SW bits. Every
+// register window [a, a+R) used by the sub-passes, with the lanes of a warp on the lowest
+// bits outside the window, then touches distinct banks (see the tile-engine comment).
+template <typename T>
+__device__ __forceinline__ uint32_t swz(uint32_t z) {
+    constexpr int SW = Num<T>::RB;
+    return z ^ ((z >> SW) & ((1u << SW) - 1u));
+}
+
+// ---- complex helpers ---------------------------------------------------------------------
+
+__device__ __forceinline__ void sincos_phase(float g_over_pi, float e, float& s, float& c) {
+    // theta = gamma * E; sin/cos(pi * y) with y = (gamma/pi) * E keeps the reduction exact.
+    sincospif(g_over_pi * e, &s, &c);
+}
+__device__ __forceinline__ void sincos_phase(double g_over_pi, double e, double& s, double& c) {
+    sincospi(g_over_pi * e, &s, &c);
+}
+
+__device__ __forceinline__ void sincos_full(float x, float& s, float& c) { sincosf(x, &s, &c); }
+__device__ __forceinline__ void sincos_full(double x, double& s, double& c) { sincos(x, &s, &c); }
+
+// psi *= exp(-i theta) given (s, c) = (sin theta, cos theta)
+template <typename C, typename T>
+__device__ __forceinline__ void rot_neg(C& v, T s, T c) {
+    const T r = v.x, i = v.y;
+    v.x = r * c + i * s;
+    v.y = i * c - r * s;
+}
+
+// exp(-i beta X) on a pair (a, b); (c, s) = (cos beta, sin beta)
+template <typename C, typename T>
+__device__ __forceinline__ void butterfly(C& a, C& b, T c, T s) {
+    const C a0 = a, b0 = b;
+    a.x = c * a0.x + s * b0.y;
+    a.y = c * a0.y - s * b0.x;
+    b.x = c * b0.x + s * a0.y;
+    b.y = c * b0.y - s * a0.x;
+}
+
+// Im(conj(x) * y)
+template <typename C>
+__device__ __forceinline__ auto im_conj_mul(const C& x, const C& y) -> decltype(x.x) {
+    return x.x * y.y - x.y * y.x;
+}
+
+// ---- warp reductions (fixed order: deterministic) ----------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---- top-k lists -------------------------------------------------------------------------
+// A warp keeps one sorted list of k entries, entry l in lane l (lanes >= k hold no entry).
+// Order: probability descending, then index ascending. Probabilities are exact FP64
+// values of |psi|^2 computed from the stored amplitudes; candidates are pre-filtered in FP32
+// against a threshold rounded down so that no entry that belongs in the list is skipped.
+
+struct TopEnt {
+    double p;
+    uint32_t z;
+};
+
+__device__ __forceinline__ bool better(double p1, uint32_t z1, double p2, uint32_t z2) {
+    return (p1 > p2) || (p1 == p2 && z1 < z2);
+}
+
+// exact probability of a stored amplitude
+__device__ __forceinline__ double exact_prob(float2 v) {
+    // the products of two floats are exact in double; the one rounding is the final add
+    return __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
+}
+__device__ __forceinline__ double exact_prob(double2 v) {
+    return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y));
+}
+
+// The list length k (1..32) is a runtime value, warp-uniform.
+struct WarpTopK {
+    double p;          // this lane's entry (lane < k)
+    uint32_t z;
+    float thr_f;       // FP32 lower bound of the k-th probability (warp-uniform)
+    int k;
+
+    __device__ __forceinline__ void init(int kk) {
+        k = kk;
+        p = -1.0;
+        z = 0xffffffffu;
+        thr_f = -1.0f;
+    }
+    // Insert candidate (cp, cz) held by lane `src` if it beats the k-th entry (warp-uniform).
+    __device__ __forceinline__ void insert_from(int src, double cp, uint32_t cz) {
+        const int lane = threadIdx.x & 31;
+        cp = __shfl_sync(0xffffffffu, cp, src);
+        cz = __shfl_sync(0xffffffffu, cz, src);
+        const bool b = (lane < k) && better(p, z, cp, cz);
+        const uint32_t ball = __ballot_sync(0xffffffffu, b);
+        const int pos = __popc(ball);      // entries better than the candidate form a prefix
+        const double up_p = __shfl_up_sync(0xffffffffu, p, 1);
+        const uint32_t up_z = __shfl_up_sync(0xffffffffu, z, 1);
+        if (pos < k) {
+            if (lane == pos) { p = cp; z = cz; }
+            else if (lane > pos && lane < k) { p = up_p; z = up_z; }
+        }
+        const double kth = __shfl_sync(0xffffffffu, p, k - 1);
+        thr_f = (kth < 0.0) ? -1.0f : __double2float_rd(kth);
+    }
+    // Offer one amplitude per lane (all lanes call; lanes with valid == false offer nothing).
+    template <typename C>
+    __device__ __forceinline__ void offer(const C& v, uint32_t zi, bool valid) {
+        const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
+        // |pf - P| <= 2^-21 P for the exact P, so P >= thr implies pf (1 + 2^-20) >= thr_f
+        const bool cand = valid && (pf * 1.00000095367431640625f >= thr_f);
+        uint32_t m = __ballot_sync(0xffffffffu, cand);
+        if (!m) return;
+        const double cp = cand ? exact_prob(v) : -1.0;
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            insert_from(src, cp, zi);
+        }
+    }
+    // Offer an entry with a known exact probability (merging lists).
+    __device__ __forceinline__ void offer_exact(double cp, uint32_t zi, bool valid) {
+        uint32_t m = __ballot_sync(0xffffffffu, valid && cp >= 0.0);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            insert_from(src, cp, zi);
+        }
+    }
+};
+
+}  // namespace qaoa

@@ -1,0 +1,245 @@
+// qaoa_engine.cuh -- the shared-memory tile engine of libqaoa.
+//
+// A tile is 2^tb amplitudes of one QAOA state held in shared memory (swizzled, see swz()).
+// The whole state is a tile in the resident tier; the streaming tier moves tiles between HBM
+// and shared memory. Inside a tile the mixer (Section IV, Eq. 2: exp(-i beta X_q) on every
+// qubit) is applied in *sub-passes*: a sub-pass loads groups of 2^R amplitudes that differ
+// only in a window of R consecutive tile bits [a, a+R) into registers, applies the
+// butterflies of the window's qubits (a bit mask chooses which), and writes them back. Each
+// thread owns whole groups; the 32 lanes of a warp own groups that differ in the lowest tile
+// bits outside the window, so with the swizzle every access of a warp hits distinct banks.
+//
+// Layers are scheduled in a "snake": within a layer the windows are visited in one order,
+// in the next layer in the reverse order, so the last window of layer l and the first window
+// of layer l+1 are the same and share one sub-pass: mixer_l(window), cost_{l+1} (elementwise),
+// mixer_{l+1}(window). With G windows per layer this takes 1 + p (G - 1) sub-passes instead of
+// p G. The adjoint runs the same sub-passes in reverse order with each operation inverted.
+#pragma once
+#include "qaoa_common.cuh"
+
+namespace qaoa {
+
+// Per-layer constants staged in shared memory: cost uses gamma/pi, the mixer (cos b, sin b).
+template <typename T>
+struct LayerConst {
+    T gpi;   // gamma_l / pi
+    T c, s;  // cos(beta_l), sin(beta_l)
+};
+
+// One sub-pass: window start a, butterfly mask over the window bits, layers [la, lb]
+// (lb <= la + 1), whether the cost of layer la opens the sub-pass.
+struct SubPass {
+    int a, mask, la, lb, ph_first;
+};
+
+// Windows of a layer over the mixed tile bits [m0, m1): window w covers bits
+// [m0 + w R, min(m0 + (w+1) R, m1)); its register window is shifted down when it would run
+// past the tile top so that it always spans R valid bits.
+__device__ __forceinline__ void window_of(int w, int m0, int m1, int tb, int R, int& a, int& mask) {
+    const int lo = m0 + w * R;
+    const int hi = min(lo + R, m1);
+    a = min(lo, tb - R);
+    if (a < 0) a = 0;
+    mask = ((1 << (hi - lo)) - 1) << (lo - a);
+}
+
+__device__ __forceinline__ int num_windows(int m0, int m1, int R) { return (m1 - m0 + R - 1) / R; }
+
+// Number of sub-passes of the snake schedule for layers [L0, L1] over G windows.
+__device__ __forceinline__ int snake_len(int G, int nl) {
+    return (G <= 1) ? nl : 1 + nl * (G - 1);
+}
+
+// The s-th sub-pass of the snake over layers L0..L0+nl-1 (ph_first of the very first one is
+// given by `first_ph`). Returns window index w plus the SubPass fields.
+__device__ __forceinline__ void snake_step(int s, int G, int nl, int L0, int first_ph, int m0,
+                                           int m1, int tb, int R, SubPass& sp) {
+    int w, la, lb, phf;
+    if (G <= 1) {
+        w = 0;
+        la = lb = L0 + s;
+        phf = (s == 0) ? first_ph : 1;
+    } else {
+        // sub-pass 0 is window order[0] of layer 0; afterwards layer l has G-1 sub-passes
+        int l, pos;
+        if (s < G) { l = 0; pos = s; }
+        else { l = 1 + (s - G) / (G - 1); pos = 1 + (s - G) % (G - 1); }
+        const bool fwd = (l % 2) == 0;
+        w = fwd ? pos : (G - 1 - pos);
+        la = L0 + l;
+        lb = (pos == G - 1 && l + 1 < nl) ? la + 1 : la;
+        phf = (l == 0 && pos == 0) ? first_ph : 0;
+    }
+    int a, mask;
+    window_of(w, m0, m1, tb, R, a, mask);
+    sp.a = a;
+    sp.mask = mask;
+    sp.la = la;
+    sp.lb = lb;
+    sp.ph_first = phf;
+}
+
+// Local index of element i of group g for window start a (R window bits).
+template <int R>
+__device__ __forceinline__ uint32_t group_base(uint32_t g, int a) {
+    const uint32_t low = g & ((1u << a) - 1u);
+    const uint32_t high = g >> a;
+    return low | (high << (a + R));
+}
+
+// Mixer of one layer on the masked window bits of a register group.
+template <int R, typename C, typename T>
+__device__ __forceinline__ void mix_group(C (&v)[1 << R], int mask, T c, T s) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (mask & (1 << j)) {
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i)
+                if (!(i & (1 << j))) butterfly(v[i], v[i | (1 << j)], c, s);
+        }
+    }
+}
+
+// Mixer inverse on two states with the accumulation of Im <lam| X_q |psi> over the masked
+// qubits (any point of the layer's mixer gives the same value: X_q commutes with every
+// exp(-i beta X_q')).
+template <int R, typename C, typename T>
+__device__ __forceinline__ T mix_group_adj(C (&v)[1 << R], C (&u)[1 << R], int mask, T c, T s) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (mask & (1 << j)) {
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i)
+                if (!(i & (1 << j))) {
+                    const int k = i | (1 << j);
+                    acc += im_conj_mul(u[i], v[k]) + im_conj_mul(u[k], v[i]);
+                    butterfly(v[i], v[k], c, -s);
+                    butterfly(u[i], u[k], c, -s);
+                }
+        }
+    }
+    return acc;
+}
+
+// Shared state of one tile.
+template <typename T>
+struct TileRef {
+    typename Num<T>::C* psi;   // 2^tb amplitudes, swizzled
+    typename Num<T>::C* lam;   // adjoint state (or nullptr)
+    const T* E;                // 2^tb energies, swizzled
+    int tb;                    // tile bits
+};
+
+// Forward sub-pass over all groups of the tile.
+//   init:  amplitudes start at amp0 instead of being read (|+> state)
+//   fin:   called once per group slot after the operations, by every thread of the block
+//          (warp-uniform trip count), as fin(v, base, a, valid).
+template <typename T, int R, typename Fin>
+__device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& sp,
+                                            const LayerConst<T>* lc, bool init, T amp0,
+                                            Fin&& fin) {
+    using C = typename Num<T>::C;
+    const uint32_t ngroups = 1u << (t.tb - R);
+    for (uint32_t g0 = 0; g0 < ngroups; g0 += blockDim.x) {
+        const uint32_t g = g0 + threadIdx.x;
+        const bool valid = g < ngroups;
+        const uint32_t base = group_base<R>(valid ? g : 0u, sp.a);
+        C v[1 << R];
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) {
+                if (init) { v[i].x = amp0; v[i].y = T(0); }
+                else v[i] = t.psi[swz<T>(base | ((uint32_t)i << sp.a))];
+            }
+            for (int l = sp.la; l <= sp.lb; ++l) {
+                if (l > sp.la || sp.ph_first) {
+                    const T gp = lc[l].gpi;
+#pragma unroll
+                    for (int i = 0; i < (1 << R); ++i) {
+                        T s, c;
+                        sincos_phase(gp, t.E[swz<T>(base | ((uint32_t)i << sp.a))], s, c);
+                        rot_neg(v[i], s, c);
+                    }
+                }
+                mix_group<R>(v, sp.mask, lc[l].c, lc[l].s);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) { v[i].x = T(0); v[i].y = T(0); }
+        }
+        fin(v, base, sp.a, valid);
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) t.psi[swz<T>(base | ((uint32_t)i << sp.a))] = v[i];
+        }
+    }
+}
+
+// Adjoint sub-pass: the forward sub-pass `sp` undone on psi and lam, accumulating
+//   acc_b[j] += Im <lam| sum_q X_q |psi> (window qubits) for layer lb - j,
+//   acc_g[j] += Im <lam| E |psi>                          for layer lb - j (its cost op).
+// lam_from_E: lam = E psi is formed on load (first adjoint sub-pass).
+template <typename T, int R>
+__device__ __forceinline__ void subpass_adj(const TileRef<T>& t, const SubPass& sp,
+                                            const LayerConst<T>* lc, bool lam_from_E,
+                                            T (&acc_b)[2], T (&acc_g)[2]) {
+    using C = typename Num<T>::C;
+    const uint32_t ngroups = 1u << (t.tb - R);
+    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const uint32_t base = group_base<R>(g, sp.a);
+        C v[1 << R], u[1 << R];
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) {
+            const uint32_t ix = swz<T>(base | ((uint32_t)i << sp.a));
+            v[i] = t.psi[ix];
+            if (lam_from_E) {
+                const T e = t.E[ix];
+                u[i].x = e * v[i].x;
+                u[i].y = e * v[i].y;
+            } else {
+                u[i] = t.lam[ix];
+            }
+        }
+        for (int l = sp.lb; l >= sp.la; --l) {
+            const int j = sp.lb - l;
+            acc_b[j] += mix_group_adj<R>(v, u, sp.mask, lc[l].c, lc[l].s);
+            if (l > sp.la || sp.ph_first) {
+                const T gp = -lc[l].gpi;
+                T ag = T(0);
+#pragma unroll
+                for (int i = 0; i < (1 << R); ++i) {
+                    const T e = t.E[swz<T>(base | ((uint32_t)i << sp.a))];
+                    ag += e * im_conj_mul(u[i], v[i]);
+                    T s, c;
+                    sincos_phase(gp, e, s, c);
+                    rot_neg(v[i], s, c);
+                    rot_neg(u[i], s, c);
+                }
+                acc_g[j] += ag;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) {
+            const uint32_t ix = swz<T>(base | ((uint32_t)i << sp.a));
+            t.psi[ix] = v[i];
+            t.lam[ix] = u[i];
+        }
+    }
+}
+
+// Block-wide sum of one value per thread into slot[0] (thread 0 only); red has blockDim/32
+// doubles. Fixed order: deterministic. Must be called by all threads.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) tot += red[i];
+    return tot;
+}
+
+}  // namespace qaoa

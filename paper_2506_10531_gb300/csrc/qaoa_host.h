@@ -1,0 +1,18 @@
+// qaoa_host.h -- internal host functions of the DQAOA steps (dqaoa_host.cpp).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qaoa {
+int draw_random(int N, int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx);
+int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx);
+void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, const int32_t* idx,
+                    int conditioned, double* Qsub);
+int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
+          const uint64_t* cand, double* energy_out, int* accepted_out);
+cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int k,
+                           const int32_t* idx, int conditioned, float* qsub, cudaStream_t st);
+cudaError_t launch_plain_layers(int n, int p, const float* gamma, const float* beta,
+                                const float* E, float2* psi, int init_plus, cudaStream_t st,
+                                int* kernels);
+}  // namespace qaoa

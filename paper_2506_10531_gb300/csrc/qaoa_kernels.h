@@ -1,0 +1,47 @@
+// qaoa_kernels.h -- internal interface between the C-ABI layer (qaoa_api.cu) and the kernel
+// translation units of libqaoa. Not installed; the public interface is include/qaoa.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qaoa {
+
+enum InstFlags : int {
+    F_GRAD = 1,       // run the adjoint sweep (d<C>/d gamma, d<C>/d beta)
+    F_INIT_PSI = 2,   // start from psi_in instead of |+>
+};
+
+// One instance of the batched forward (and optional adjoint) computation. All pointers are
+// device pointers; optional outputs are nullptr when not wanted.
+template <typename T>
+struct InstDesc {
+    int n, p, k, flags;
+    const T* Q;          // n x n row-major QUBO (energies are built from it), or nullptr
+    const T* E_in;       // 2^n energies when Q is nullptr
+    const T* gamma;      // p values
+    const T* beta;       // p values
+    const void* psi_in;  // initial state (F_INIT_PSI), complex of T
+    void* psi_out;       // final state, complex of T
+    T* E_out;            // energies
+    double* expect;      // <C>
+    uint64_t* topk_idx;  // k indices
+    double* topk_prob;   // k probabilities
+    double* dgamma;      // p values (F_GRAD)
+    double* dbeta;       // p values (F_GRAD)
+};
+
+// ---- resident tier: one CTA per instance, whole state in shared memory -----------------
+// Largest n the resident tier holds (forward / adjoint), per real type.
+constexpr int RES_NMAX_F = 14, RES_NMAX_F_ADJ = 13;
+constexpr int RES_NMAX_D = 13, RES_NMAX_D_ADJ = 12;
+
+size_t resident_smem_bytes(bool dbl, int n, int p, bool grad);
+int resident_threads(bool dbl, int n);
+// Launch a resident-tier kernel over `count` device descriptors (all with the same n).
+// queue: device int zeroed by the caller before the launch (work counter). With desc ==
+// nullptr the host descriptor `one` is passed by value and run by one block.
+cudaError_t launch_resident(bool dbl, const void* desc, int count, int n, int pmax, bool grad,
+                            int* queue, int grid, cudaStream_t st, const void* one = nullptr);
+int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad);
+
+}  // namespace qaoa

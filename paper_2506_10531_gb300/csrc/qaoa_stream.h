@@ -1,0 +1,55 @@
+// qaoa_stream.h -- internal types of the HBM-streaming tier of libqaoa.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qaoa {
+
+// One HBM pass over all tiles of the instances of a launch (uniform for the launch).
+struct StreamPass {
+    int n;          // qubits of the instances of this launch
+    int tb;         // tile bits
+    int kind;       // 0: contiguous tile (qubits 0..tb-1); 1: c low + h high qubits [s, s+h)
+    int c, s, h;
+    int la, lb;     // layers covered (lb <= la + 1)
+    int ph_first;   // the cost of layer la opens this pass
+    int init;       // generate |+> instead of reading psi
+    int fin;        // last pass: per-tile <C> partials and top-k candidates
+    int k;          // top-k length when fin
+    int need_e;     // the pass reads the energies
+};
+
+// One instance of a streaming launch (device pointers).
+template <typename T>
+struct StreamInst {
+    int p;
+    double amp0;          // 2^{-n/2}
+    const T* gamma;
+    const T* beta;
+    void* psi;            // 2^n complex state in HBM (in/out)
+    const T* E;           // 2^n energies in HBM
+    double* part_expect;  // 2^(n - tb) tile partials
+    double* part_topp;    // 2^(n - tb) * k
+    uint32_t* part_topz;  // 2^(n - tb) * k
+    double* expect;
+    uint64_t* topk_idx;
+    double* topk_prob;
+};
+
+int stream_tile_bits(bool dbl);
+// Fill the pass list of a p-layer run on n qubits; returns the number of passes or -1.
+int stream_plan(bool dbl, int n, int p, int k, StreamPass* out, int max_out);
+size_t stream_smem_bytes(bool dbl);
+// insts: device array of `count` instances, or nullptr to pass the host instance `one` by value.
+cudaError_t launch_stream_pass(bool dbl, const StreamPass& P, const void* insts, int count,
+                               int grid, cudaStream_t st, const void* one = nullptr);
+cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint64_t ntiles, int k,
+                                   cudaStream_t st, const void* one = nullptr);
+cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st);
+int reduce_parts(int n);
+cudaError_t launch_reduce_state(bool dbl, int n, const void* psi, const void* E, int k,
+                                double* part_expect, double* part_topp, uint32_t* part_topz,
+                                double* expect, uint64_t* topk_idx, double* topk_prob,
+                                cudaStream_t st);
+
+}  // namespace qaoa
