@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the DQAOA hot path on GB300: one step = one DQAOA cycle of the batch workload.
+
+Workload (the DQAOA batch configuration): a dense N = 1000 QUBO with Q_ij i.i.d. uniform[-1, 1]
+(symmetric, seed 2) is decomposed into m = 256 random sub-QUBOs of k = 16 variables conditioned on
+the current global solution; every sub-QUBO runs depth p = 3 QAOA with the fixed parameters
+gamma = (0.2, 0.4, 0.6), beta = (0.6, 0.4, 0.2) in complex64; <C> and the top-8 bitstrings of each
+are reduced on the device and merged into the global solution on the host.
+
+One step (one cycle, all steps of the hot path): index draw (host) -> sub-QUBO matrices,
+energies, p layers, <C>, top-k (device) -> merge (host). `value` is sub-QUBO solves/s with Q
+already resident in HBM; `e2e` is the same through dqaoa_session_cycle with Q copied from pinned
+host memory every step. Between timed steps L2 is flushed by writing a 256 MiB buffer.
+
+--impl reference times the FP64 oracle (the CPU baseline) on a bounded sample of the same cycle.
+Multi-GPU (torchrun): every rank runs an independent cycle on its own GPU (sub-QUBOs are
+independent units; no collective on the data path), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+CFG = dict(synth.DQAOA_BATCH)
+WORKLOAD = ("DQAOA batch cycle: dense N=1000 QUBO U[-1,1], 256 random conditioned sub-QUBOs "
+            "of n=16, p=3 fixed parameters, complex64, top-8 merged")
+METRIC = "sub-QUBO solves/s (DQAOA cycle: decompose + energies + p layers + <C> + top-k + merge)"
+UNIT = "solves/s"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.2)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2506_10531_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_family):
+    """DRAM bytes per launch of a kernel family from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    e = t.get("kernels", {}).get(kernel_family)
+    return None if e is None else e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------------------------
+
+def oracle_cycle_sample(Q, x, n_sub, cycle):
+    """The oracle on the first n_sub sub-QUBOs of one cycle: decompose, energies, state, <C>,
+    top-k, merge. Returns the number of sub-QUBOs solved."""
+    import oracle
+    idx, qs = oracle.decompose(Q, x, CFG["m"], CFG["k"], CFG["seed"], cycle)
+    idx, qs = idx[:n_sub], qs[:n_sub]
+    cand = np.zeros((n_sub, CFG["topk"]), dtype=np.uint64)
+    for j in range(n_sub):
+        Qs = qs[j].astype(np.float32).astype(np.float64)
+        E = oracle.energies(Qs)
+        psi = oracle.state(CFG["k"], CFG["gamma"], CFG["beta"], E)
+        oracle.expect(psi, E)
+        cand[j], _ = oracle.topk(psi, CFG["topk"])
+    oracle.merge(Q, x, idx, cand)
+    return n_sub
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    Q = synth.symmetric_q(CFG["N"], seed=CFG["seed"])
+    x = synth.bits(CFG["seed"] + 1, CFG["N"])
+    n_sub = 16
+    for w in range(args.warmup):
+        oracle_cycle_sample(Q, x, n_sub, w)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_cycle_sample(Q, x, n_sub, 100 + s)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = n_sub * args.steps / tot
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_per_step": n_sub},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_sub} of the 256 sub-QUBOs of a cycle per step "
+                                       "(decompose, energies, state, <C>, top-8, merge), FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    import oracle
+    oracle.build()
+    Q = synth.symmetric_q(CFG["N"], seed=CFG["seed"])
+    x = synth.bits(CFG["seed"] + 1, CFG["N"])
+    n_sub = 96
+    t0 = time.perf_counter()
+    oracle_cycle_sample(Q, x, n_sub, 0)
+    dt = time.perf_counter() - t0
+    return {"value": n_sub / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_sub} of the 256 sub-QUBOs of one cycle (decompose, energies, state, "
+                      f"<C>, top-8, merge) in FP64 with OpenMP, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2506_10531_gb300 as q
+    from paper_2506_10531_gb300 import build as qbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        qbuild.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    N, m, k, p, K = CFG["N"], CFG["m"], CFG["k"], CFG["p"], CFG["topk"]
+    seed = CFG["seed"] + 1000 * rank
+    Q = synth.symmetric_q(N, seed=seed)
+    Q_pin = torch.from_numpy(Q).pin_memory()
+    Qh = Q_pin.numpy()
+    x0 = synth.bits(seed + 1, N)
+    ctx = q.qaoa_create(local)
+    sess = q.dqaoa_session_create(ctx, N, m, k, p, K, q.DQAOA_RANDOM, True, CFG["gamma"], CFG["beta"])
+    plan = q.dqaoa_session_plan(sess)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def l2_flush():
+        flush.fill_(1)
+
+    # ---- value: Q resident in HBM ----
+    x = x0.copy()
+    q.dqaoa_session_cycle(sess, Qh, 1, x, seed, 0, stream)         # uploads Q once
+    for w in range(args.warmup):
+        q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 1 + w, stream)
+    q.qaoa_plan_set_timing(plan, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kern = {}
+    energies = []
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with Clocks(local) as clk:
+        for s in range(args.steps):
+            l2_flush()
+            ev[s][0].record(stream)
+            e, acc = q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 100 + s, stream)
+            ev[s][1].record(stream)
+            energies.append(e)
+            for name, ms in q.qaoa_plan_kernel_times(plan):
+                kern.setdefault(name, []).append(ms)
+        torch.cuda.synchronize()
+    q.qaoa_plan_set_timing(plan, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([tot_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_s = float(t.item())
+    value = m * args.steps * world / tot_s
+    plan_kernels = q.qaoa_plan_kernel_count(plan)
+    gpu_launches = args.steps * (plan_kernels + 1)
+
+    # ---- dominant kernel and its roofline ----
+    kbytes = q.qaoa_plan_kernel_bytes(plan)
+    fam_ms = {nm: sum(v) for nm, v in kern.items()}
+    dom = max(fam_ms, key=fam_ms.get)
+    # bytes per launch of that family (average over its launches in one plan launch)
+    q.qaoa_plan_set_timing(plan, True)
+    q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream)
+    order = [nm for nm, _ in q.qaoa_plan_kernel_times(plan)]
+    q.qaoa_plan_set_timing(plan, False)
+    fam_bytes = [b for nm, b in zip(order, kbytes) if nm == dom]
+    per_launch_ms = statistics.mean(kern[dom])
+    per_launch_bytes = statistics.mean(fam_bytes) if fam_bytes else 0.0
+    peaks, peak_kind = measured_peaks()
+    if dom in ("stream_pass", "energy", "stream_finalize"):
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(dom), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
+    else:
+        # on-chip kernels: FP32 pipe bound; peak = SMs x 128 FP32 lanes x 2 flop x clock
+        props = torch.cuda.get_device_properties(dev)
+        mhz = clk.summary().get("sm_mhz") or 1900.0
+        peak_tf = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
+        flops = alu_flops_per_launch(dom, m, k, p)
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": ncu_traffic(dom),
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x median SM clock",
+                "ms_per_launch": per_launch_ms}
+
+    # ---- kernel-only batch throughput and the plain one-instance-per-launch path ----
+    kb = time_plan_only(q, plan, stream, args.steps, l2_flush)
+    plain = time_plain(q, ctx, sess, stream, n_inst=16)
+
+    # ---- e2e: the public one-call cycle with Q from pinned host memory every step ----
+    xe = x0.copy()
+    for w in range(2):
+        q.dqaoa_session_cycle(sess, Qh, 1, xe, seed, 500 + w, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        q.dqaoa_session_cycle(sess, Qh, 1, xe, seed, 600 + s, stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": m * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": N * N * 8 + N + m * k * 4, "d2h_bytes_per_step": m * K * 8 + m * 8}
+
+    q.dqaoa_session_destroy(sess)
+    q.qaoa_destroy(ctx)
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    amps = m * (1 << k) * p
+    ms_step = 1e3 * tot_s / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64/f32 state, f64 reductions and merge", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "sub_qubos": m, "n": k, "p": p, "topk": K,
+                   "decomposition": "random, conditioned", "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "amp_layer_updates_per_s": amps * args.steps * world / tot_s,
+        "amp_gate_updates_per_s": amps * (k + 1) * args.steps * world / tot_s,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "kernel_only": kb, "plain_gpu_path": plain,
+        "batched_over_plain": kb["solves_per_s"] / plain["solves_per_s"],
+        "kernel_ms_per_step": {nm: sum(v) / args.steps for nm, v in kern.items()},
+        "roofline": roof,
+        "final_energy": energies[-1],
+        "e2e": e2e, "gpu_launches": gpu_launches,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def alu_flops_per_launch(family, m, k, p):
+    # per amplitude and layer: phase (sincos counted as 8) + 4 flops, mixer 4 flops per qubit
+    return m * (1 << k) * p * (12 + 4 * k)
+
+
+def time_plan_only(q, plan, stream, steps, l2_flush):
+    import torch
+    for _ in range(3):
+        q.qaoa_plan_launch(plan, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for s in range(steps):
+        l2_flush()
+        ev[s][0].record(stream)
+        q.qaoa_plan_launch(plan, stream)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    return {"ms_per_batch": ms, "solves_per_s": CFG["m"] / (ms * 1e-3)}
+
+
+def time_plain(q, ctx, sess, stream, n_inst):
+    """The plain path (one instance per call, one kernel per gate) on n_inst sub-QUBOs of the
+    same cycle."""
+    import torch
+    k, p, K = CFG["k"], CFG["p"], CFG["topk"]
+    Qs = torch.as_tensor(np.stack([synth.symmetric_q(k, seed=70 + i) for i in range(n_inst)]),
+                         dtype=torch.float32, device="cuda")
+    g = torch.tensor(CFG["gamma"], dtype=torch.float32, device="cuda")
+    b = torch.tensor(CFG["beta"], dtype=torch.float32, device="cuda")
+    E = torch.empty(1 << k, dtype=torch.float32, device="cuda")
+    psi = torch.empty(2 << k, dtype=torch.float32, device="cuda")
+    ex = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ti = torch.zeros(K, dtype=torch.int64, device="cuda")
+    tp = torch.zeros(K, dtype=torch.float64, device="cuda")
+    q.qaoa_reserve(ctx, q.qaoa_workspace_bytes(k))
+    for i in range(2):
+        q.qaoa_plain_solve(ctx, k, p, Qs[i], g, b, E, psi, K, ex, ti, tp, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n_inst):
+        q.qaoa_plain_solve(ctx, k, p, Qs[i], g, b, E, psi, K, ex, ti, tp, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n_inst
+    return {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "kernels_per_solve": 2 + p * (k + 1) + 2}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,16 @@ qaoa_status qaoa_plan_create(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
 qaoa_status qaoa_plan_launch(qaoa_plan* plan, qaoa_stream_t stream);
 /* Number of kernel launches one qaoa_plan_launch enqueues. */
 int qaoa_plan_kernel_count(const qaoa_plan* plan);
+/* Per-kernel timing: with on != 0 every later qaoa_plan_launch records a CUDA event before and
+ * after each kernel on the launch stream. qaoa_plan_kernel_times then writes, for the last
+ * launch, up to `max` entries: the duration in ms of kernel i (after synchronising on the last
+ * event) and, in names (may be NULL), a pointer to a static string naming its kernel family. */
+qaoa_status qaoa_plan_set_timing(qaoa_plan* plan, int on);
+int qaoa_plan_kernel_times(qaoa_plan* plan, float* ms, const char** names, int max);
+/* Algorithmic DRAM bytes of each kernel of one launch, in launch order (the bytes the
+ * computation must move: states, energies and matrices read or written once, no re-reads);
+ * returns the number of kernels written (at most max). */
+int qaoa_plan_kernel_bytes(const qaoa_plan* plan, double* bytes, int max);
 /* Free the plan (synchronises the device first). NULL is ignored. */
 void qaoa_plan_destroy(qaoa_plan* plan);
 
@@ -219,6 +229,35 @@ qaoa_status dqaoa_subqubo_build(qaoa_ctx* ctx, const double* Q_dev, int N, const
  * candidates (may be NULL). k <= 64. Synchronous. */
 qaoa_status dqaoa_merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx,
                         int K, const uint64_t* cand, double* energy_out, int* accepted_out);
+
+
+/* ---------------------------------------------------------------------------------------- */
+/* One DQAOA cycle in one call (Section V: decompose -> solve the sub-QUBOs in parallel ->    */
+/* aggregate). A session owns the device copies of Q and x, the sub-QUBO pools, a batched    */
+/* plan for m sub-QUBOs of k qubits at depth p, and pinned staging buffers.                  */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct dqaoa_session dqaoa_session;
+
+/* gamma, beta: p host doubles (the fixed parameters every sub-QUBO uses); K: top-k candidates
+ * per sub-QUBO fed to the merge (1..16); method: DQAOA_RANDOM or DQAOA_IFD. Allocates. */
+qaoa_status dqaoa_session_create(qaoa_ctx* ctx, int N, int m, int k, int p, int K, int method,
+                                 int conditioned, const double* gamma, const double* beta,
+                                 dqaoa_session** out);
+/* Run one cycle. Q: N*N host doubles (copied to the device when q_changed != 0, which the
+ * first call needs); x: N host bytes, in/out (the global solution). seed/cycle select the
+ * random index sets. energy_out: E(x') (may be NULL); accepted_out: accepted candidates (may
+ * be NULL). Steps: index draw (host) -> sub-QUBO build, energies, p layers, <C> and top-K
+ * (device, one stream) -> merge (host). Synchronous on `stream`. */
+qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed, uint8_t* x,
+                                uint64_t seed, uint64_t cycle, double* energy_out,
+                                int* accepted_out, qaoa_stream_t stream);
+/* Device work of the last cycle: per-sub-QUBO <C> (m doubles) and top-K indices (m*K uint64),
+ * copied to host arrays (either may be NULL). */
+qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk);
+/* The batched plan the session launches (for timing and kernel counts). */
+qaoa_plan* dqaoa_session_plan(dqaoa_session* s);
+void dqaoa_session_destroy(dqaoa_session* s);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,9 @@ EXPORTS = [
     "qaoa_plan_create", "qaoa_plan_launch", "qaoa_plan_kernel_count", "qaoa_plan_destroy",
     "qaoa_batch_run", "qaoa_batch_run_z", "qaoa_plain_solve",
     "dqaoa_draw_indices", "dqaoa_decompose", "dqaoa_subqubo_build", "dqaoa_merge",
+    "qaoa_plan_set_timing", "qaoa_plan_kernel_times", "qaoa_plan_kernel_bytes",
+    "dqaoa_session_create", "dqaoa_session_cycle", "dqaoa_session_results", "dqaoa_session_plan",
+    "dqaoa_session_destroy",
 ]
 
 
@@ -96,6 +99,18 @@ def _declare(L):
     L.dqaoa_decompose.argtypes = [vp, i32, vp, i32, i32, i32, i32, u64, u64, vp, vp]
     L.dqaoa_subqubo_build.argtypes = [vp, vp, i32, vp, i32, i32, vp, i32, vp, vp]
     L.dqaoa_merge.argtypes = [vp, i32, vp, i32, i32, vp, i32, vp, vp, vp]
+    L.qaoa_plan_set_timing.argtypes = [vp, i32]
+    L.qaoa_plan_kernel_times.argtypes = [vp, vp, vp, i32]
+    L.qaoa_plan_kernel_times.restype = i32
+    L.qaoa_plan_kernel_bytes.argtypes = [vp, vp, i32]
+    L.qaoa_plan_kernel_bytes.restype = i32
+    L.dqaoa_session_create.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, C.POINTER(vp)]
+    L.dqaoa_session_cycle.argtypes = [vp, vp, i32, vp, u64, u64, vp, vp, vp]
+    L.dqaoa_session_results.argtypes = [vp, vp, vp]
+    L.dqaoa_session_plan.argtypes = [vp]
+    L.dqaoa_session_plan.restype = vp
+    L.dqaoa_session_destroy.argtypes = [vp]
+    L.dqaoa_session_destroy.restype = None
     del i64, st, dp
 
 
@@ -268,3 +283,57 @@ def qaoa_grad_z(ctx, n, p, gamma, beta, E, expect, dgamma, dbeta, stream=None):
 
 def qaoa_batch_run_z(ctx, insts, io: qaoa_batch_io, stream=None):
     qaoa_batch_run(ctx, insts, io, stream, dbl=True)
+
+
+def qaoa_plan_set_timing(plan, on=True):
+    _check(lib().qaoa_plan_set_timing(plan, int(on)))
+
+
+def qaoa_plan_kernel_times(plan, max_kernels=256):
+    """[(kernel family, ms)] of the last launch of a plan with timing on."""
+    ms = (C.c_float * max_kernels)()
+    names = (C.c_char_p * max_kernels)()
+    n = lib().qaoa_plan_kernel_times(plan, ms, names, max_kernels)
+    return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def dqaoa_session_create(ctx, N, m, k, p, K, method, conditioned, gamma, beta):
+    import numpy as np
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    h = C.c_void_p()
+    _check(lib().dqaoa_session_create(ctx, N, m, k, p, K, method, int(conditioned), ptr(g), ptr(b),
+                                      C.byref(h)))
+    return h
+
+
+def dqaoa_session_cycle(sess, Q, q_changed, x, seed, cycle, stream=None):
+    """One DQAOA cycle; x (host uint8) is updated in place. Returns (energy, accepted)."""
+    e = C.c_double()
+    a = C.c_int()
+    _check(lib().dqaoa_session_cycle(sess, ptr(Q), int(q_changed), ptr(x), seed, cycle, C.byref(e),
+                                     C.byref(a), stream_ptr(stream)))
+    return e.value, a.value
+
+
+def dqaoa_session_results(sess, m, K):
+    import numpy as np
+    ex = np.zeros(m, dtype=np.float64)
+    tk = np.zeros((m, K), dtype=np.uint64)
+    _check(lib().dqaoa_session_results(sess, ptr(ex), ptr(tk)))
+    return ex, tk
+
+
+def dqaoa_session_plan(sess):
+    return C.c_void_p(lib().dqaoa_session_plan(sess))
+
+
+def dqaoa_session_destroy(sess):
+    lib().dqaoa_session_destroy(sess)
+
+
+def qaoa_plan_kernel_bytes(plan, max_kernels=256):
+    """Algorithmic DRAM bytes of each kernel of one launch of the plan, in launch order."""
+    b = (C.c_double * max_kernels)()
+    n = lib().qaoa_plan_kernel_bytes(plan, b, max_kernels)
+    return [float(b[i]) for i in range(n)]

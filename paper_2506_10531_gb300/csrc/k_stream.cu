@@ -223,10 +223,15 @@ __global__ void __launch_bounds__(256) k_stream_finalize(const StreamInst<T>* __
 // ---- energy build into HBM --------------------------------------------------------------
 // Thread t of 2^m fixes the low m bits of z and walks the high n - m bits in Gray-code order
 // (same increment rule as the resident tier); every step writes one coalesced row of E.
+// blockIdx.y selects the instance when insts != nullptr (then Q and E come from it).
 template <typename T>
 __global__ void __launch_bounds__(256) k_energy(int n, int m, const T* __restrict__ Q,
-                                                T* __restrict__ E) {
+                                                T* __restrict__ E, const StreamInst<T>* insts) {
     __shared__ T Qs[32 * 32];
+    if (insts) {
+        Q = insts[blockIdx.y].Q;
+        E = const_cast<T*>(insts[blockIdx.y].E);
+    }
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) Qs[i] = Q[i];
     __syncthreads();
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -457,17 +462,32 @@ cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint6
     return cudaGetLastError();
 }
 
-cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st) {
+static int energy_split(int n) {
     // low bits fixed per thread: enough threads to fill the GPU, at most 2^12 Gray steps each
     int m = n - 6;
     if (m < 0) m = 0;
     if (m > 20) m = 20;
     if (n - m > 12) m = n - 12;
+    return m;
+}
+
+cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st) {
+    const int m = energy_split(n);
     const uint64_t threads = 1ull << m;
     const int block = threads < 256 ? (int)threads : 256;
     const uint64_t grid = (threads + block - 1) / block;
-    if (dbl) k_energy<double><<<(unsigned)grid, block, 0, st>>>(n, m, static_cast<const double*>(Q), static_cast<double*>(E));
-    else k_energy<float><<<(unsigned)grid, block, 0, st>>>(n, m, static_cast<const float*>(Q), static_cast<float*>(E));
+    if (dbl) k_energy<double><<<(unsigned)grid, block, 0, st>>>(n, m, static_cast<const double*>(Q), static_cast<double*>(E), nullptr);
+    else k_energy<float><<<(unsigned)grid, block, 0, st>>>(n, m, static_cast<const float*>(Q), static_cast<float*>(E), nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_batch(bool dbl, int n, const void* insts, int count, cudaStream_t st) {
+    const int m = energy_split(n);
+    const uint64_t threads = 1ull << m;
+    const int block = threads < 256 ? (int)threads : 256;
+    const dim3 grid((unsigned)((threads + block - 1) / block), (unsigned)count);
+    if (dbl) k_energy<double><<<grid, block, 0, st>>>(n, m, nullptr, nullptr, static_cast<const StreamInst<double>*>(insts));
+    else k_energy<float><<<grid, block, 0, st>>>(n, m, nullptr, nullptr, static_cast<const StreamInst<float>*>(insts));
     return cudaGetLastError();
 }
 

@@ -313,6 +313,10 @@ struct qaoa_plan {
     std::vector<ResGroup> res;
     std::vector<StrGroup> str;
     int kernels = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;       // 2 per kernel of one launch
+    std::vector<const char*> names;    // kernel family per kernel of the last launch
+    std::vector<double> bytes;         // algorithmic DRAM bytes per kernel, launch order
 };
 
 namespace {
@@ -453,6 +457,7 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             I.amp0 = exp2(-0.5 * d.n);
             I.gamma = ppool + d.par_off;
             I.beta = ppool + d.par_off + d.p;
+            I.Q = qpool + d.q_off;
             I.psi = (s.psi_off == (size_t)-1) ? (void*)(psipool + d.psi_off) : (void*)(base + s.psi_off);
             T* Ebuf = (s.e_off == (size_t)-1) ? epool + d.e_off : reinterpret_cast<T*>(base + s.e_off);
             I.E = Ebuf;
@@ -471,8 +476,30 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         }
         e = cudaMemcpy(base + g.inst_off, si.data(), sizeof(StreamInst<T>) * g.count, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload stream instances"); }
-        P->kernels += g.count + (int)g.passes.size() + 1;
+        P->kernels += 1 + (int)g.passes.size() + 1;
         ++gi;
+    }
+    // algorithmic bytes, in the order qaoa_plan_launch issues the kernels
+    for (auto& g : P->res) {
+        double b = 0.0;
+        for (int i = 0; i < count; ++i) {
+            const qaoa_inst& d = desc[i];
+            const bool in = d.n <= nres && d.n == g.n && (((d.flags & QAOA_INST_GRAD) != 0) == g.grad);
+            if (!in) continue;
+            const double D = (double)(1ull << d.n);
+            b += (double)d.n * d.n * sizeof(T) + 2.0 * d.p * sizeof(T) + sizeof(double) +
+                 d.k * 16.0 + (d.psi_off >= 0 ? D * sizeof(C2) : 0.0) + (d.e_off >= 0 ? D * sizeof(T) : 0.0) +
+                 ((d.flags & QAOA_INST_GRAD) ? 16.0 * d.p : 0.0);
+        }
+        P->bytes.push_back(b);
+    }
+    for (auto& g : P->str) {
+        const double D = (double)(1ull << g.n), cnt = (double)g.count;
+        const double nt = (double)(1ull << (g.n - tb));
+        P->bytes.push_back(cnt * (D * sizeof(T) + (double)g.n * g.n * sizeof(T)));
+        for (auto& pass : g.passes)
+            P->bytes.push_back(cnt * D * ((pass.init ? 0.0 : sizeof(C2)) + sizeof(C2) + (pass.need_e ? sizeof(T) : 0.0)));
+        P->bytes.push_back(cnt * (nt * (sizeof(double) + std::max(g.k, 1) * 12.0) + 8.0 + g.k * 16.0));
     }
     *out = P;
     return QAOA_OK;
@@ -495,26 +522,78 @@ extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
     cudaStream_t st = (cudaStream_t)stream;
     char* base = static_cast<char*>(P->dev);
     int* counters = reinterpret_cast<int*>(base);
+    P->names.clear();
+    // wrap each kernel launch in a pair of timing events when timing is on
+    auto timed = [&](const char* name, auto&& launch) -> cudaError_t {
+        const size_t i = P->names.size();
+        if (P->timing) {
+            while (P->ev.size() < 2 * (i + 1)) {
+                cudaEvent_t e;
+                cudaError_t r = cudaEventCreate(&e);
+                if (r != cudaSuccess) return r;
+                P->ev.push_back(e);
+            }
+            cudaEventRecord(P->ev[2 * i], st);
+        }
+        cudaError_t r = launch();
+        if (P->timing) cudaEventRecord(P->ev[2 * i + 1], st);
+        P->names.push_back(name);
+        return r;
+    };
     for (auto& g : P->res) {
         CK(cudaMemsetAsync(counters + g.q_slot, 0, sizeof(int), st));
-        CK(launch_resident(P->dbl, base + g.desc_off, g.count, g.n, g.pmax, g.grad, counters + g.q_slot,
-                           g.grid, st));
+        CK(timed("resident", [&] {
+            return launch_resident(P->dbl, base + g.desc_off, g.count, g.n, g.pmax, g.grad,
+                                   counters + g.q_slot, g.grid, st);
+        }));
     }
     const int tb = stream_tile_bits(P->dbl);
     for (auto& g : P->str) {
-        for (int i = 0; i < g.count; ++i) CK(launch_energy(P->dbl, g.n, g.q[i], g.e[i], st));
-        for (auto& pass : g.passes) CK(launch_stream_pass(P->dbl, pass, base + g.inst_off, g.count, g.grid, st));
-        CK(launch_stream_finalize(P->dbl, base + g.inst_off, g.count, 1ull << (g.n - tb), g.k, st));
+        CK(timed("energy", [&] { return launch_energy_batch(P->dbl, g.n, base + g.inst_off, g.count, st); }));
+        for (auto& pass : g.passes)
+            CK(timed("stream_pass", [&] {
+                return launch_stream_pass(P->dbl, pass, base + g.inst_off, g.count, g.grid, st);
+            }));
+        CK(timed("stream_finalize", [&] {
+            return launch_stream_finalize(P->dbl, base + g.inst_off, g.count, 1ull << (g.n - tb), g.k, st);
+        }));
     }
     return QAOA_OK;
 }
 
+extern "C" qaoa_status qaoa_plan_set_timing(qaoa_plan* P, int on) {
+    if (!P) return fail(QAOA_E_INVALID, "plan is NULL");
+    P->timing = on != 0;
+    return QAOA_OK;
+}
+
+extern "C" int qaoa_plan_kernel_times(qaoa_plan* P, float* ms, const char** names, int max) {
+    if (!P || !P->timing || P->ev.size() < 2 * P->names.size()) return 0;
+    const int n = std::min<int>(max, (int)P->names.size());
+    if (n > 0) cudaEventSynchronize(P->ev[2 * (P->names.size() - 1) + 1]);
+    for (int i = 0; i < n; ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, P->ev[2 * i], P->ev[2 * i + 1]);
+        if (ms) ms[i] = t;
+        if (names) names[i] = P->names[i];
+    }
+    return n;
+}
+
 extern "C" int qaoa_plan_kernel_count(const qaoa_plan* P) { return P ? P->kernels : 0; }
+
+extern "C" int qaoa_plan_kernel_bytes(const qaoa_plan* P, double* bytes, int max) {
+    if (!P) return 0;
+    const int n = std::min<int>(max, (int)P->bytes.size());
+    for (int i = 0; i < n; ++i) bytes[i] = P->bytes[i];
+    return n;
+}
 
 extern "C" void qaoa_plan_destroy(qaoa_plan* P) {
     if (!P) return;
     cudaSetDevice(P->ctx->device);
     cudaDeviceSynchronize();
+    for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
     cudaFree(P->dev);
     delete P;
 }
@@ -605,4 +684,130 @@ extern "C" qaoa_status dqaoa_merge(const double* Q, int N, uint8_t* x, int m, in
         if (idx[t] < 0 || idx[t] >= N) return fail(QAOA_E_INVALID, "merge: index %d out of range", idx[t]);
     merge(Q, N, x, m, k, idx, K, cand, energy_out, accepted_out);
     return QAOA_OK;
+}
+
+// =============================================================================================
+// DQAOA session: one cycle per call
+// =============================================================================================
+
+struct dqaoa_session {
+    qaoa_ctx* ctx = nullptr;
+    int N = 0, m = 0, k = 0, p = 0, K = 0, method = 0, conditioned = 1;
+    void* dev = nullptr;          // Q, x, idx, qsub, params, expect, top-k
+    double* Q_dev = nullptr;
+    uint8_t* x_dev = nullptr;
+    int32_t* idx_dev = nullptr;
+    float* qsub = nullptr;
+    float* params = nullptr;
+    double* expect = nullptr;
+    uint64_t* topk = nullptr;
+    void* host = nullptr;         // pinned staging
+    int32_t* idx_h = nullptr;
+    uint8_t* x_h = nullptr;
+    uint64_t* topk_h = nullptr;
+    double* expect_h = nullptr;
+    qaoa_plan* plan = nullptr;
+};
+
+extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, int p, int K, int method,
+                                            int conditioned, const double* gamma, const double* beta,
+                                            dqaoa_session** out) {
+    if (!c || !out || N < 1 || m < 1 || k < 1 || k > N || k > NMAX || p < 1 || p > PMAX || K < 1 ||
+        K > KMAX || (uint64_t)K > (1ull << k) || !gamma || !beta || (method != DQAOA_RANDOM && method != DQAOA_IFD))
+        return fail(QAOA_E_INVALID, "session_create: bad arguments");
+    if (method == DQAOA_IFD && m + k - 1 > N) return fail(QAOA_E_INVALID, "IFD needs m + k - 1 <= N");
+    *out = nullptr;
+    CK(cudaSetDevice(c->device));
+    dqaoa_session* s = new dqaoa_session();
+    s->ctx = c; s->N = N; s->m = m; s->k = k; s->p = p; s->K = K; s->method = method;
+    s->conditioned = conditioned;
+    size_t o = 0;
+    const size_t oQ = o; o = align256(o + (size_t)N * N * sizeof(double));
+    const size_t ox = o; o = align256(o + (size_t)N);
+    const size_t oi = o; o = align256(o + (size_t)m * k * sizeof(int32_t));
+    const size_t oq = o; o = align256(o + (size_t)m * k * k * sizeof(float));
+    const size_t op = o; o = align256(o + (size_t)2 * p * sizeof(float));
+    const size_t oe = o; o = align256(o + (size_t)m * sizeof(double));
+    const size_t ot = o; o = align256(o + (size_t)m * K * sizeof(uint64_t));
+    cudaError_t e = cudaMalloc(&s->dev, o);
+    if (e != cudaSuccess) { delete s; return fail(QAOA_E_NOMEM, "session cudaMalloc: %s", cudaGetErrorString(e)); }
+    char* b = static_cast<char*>(s->dev);
+    s->Q_dev = reinterpret_cast<double*>(b + oQ);
+    s->x_dev = reinterpret_cast<uint8_t*>(b + ox);
+    s->idx_dev = reinterpret_cast<int32_t*>(b + oi);
+    s->qsub = reinterpret_cast<float*>(b + oq);
+    s->params = reinterpret_cast<float*>(b + op);
+    s->expect = reinterpret_cast<double*>(b + oe);
+    s->topk = reinterpret_cast<uint64_t*>(b + ot);
+    size_t h = 0;
+    const size_t hi = h; h = align256(h + (size_t)m * k * sizeof(int32_t));
+    const size_t hx = h; h = align256(h + (size_t)N);
+    const size_t ht = h; h = align256(h + (size_t)m * K * sizeof(uint64_t));
+    const size_t he = h; h = align256(h + (size_t)m * sizeof(double));
+    e = cudaMallocHost(&s->host, h);
+    if (e != cudaSuccess) { cudaFree(s->dev); delete s; return fail(QAOA_E_NOMEM, "session cudaMallocHost"); }
+    char* hb = static_cast<char*>(s->host);
+    s->idx_h = reinterpret_cast<int32_t*>(hb + hi);
+    s->x_h = reinterpret_cast<uint8_t*>(hb + hx);
+    s->topk_h = reinterpret_cast<uint64_t*>(hb + ht);
+    s->expect_h = reinterpret_cast<double*>(hb + he);
+    std::vector<float> par(2 * p);
+    for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)beta[l]; }
+    e = cudaMemcpy(s->params, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice);
+    std::vector<qaoa_inst> d(m);
+    for (int j = 0; j < m; ++j) d[j] = qaoa_inst{k, p, K, 0, (int64_t)j * k * k, 0, -1, -1};
+    qaoa_batch_io io{};
+    io.q = s->qsub;
+    io.params = s->params;
+    io.expect = s->expect;
+    io.topk_idx = s->topk;
+    io.k_stride = K;
+    qaoa_status st = (e == cudaSuccess) ? qaoa_plan_create(c, d.data(), m, &io, 0, &s->plan)
+                                        : cuda_fail(e, "session params upload");
+    if (st) { dqaoa_session_destroy(s); return st; }
+    *out = s;
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed, uint8_t* x,
+                                           uint64_t seed, uint64_t cycle, double* energy_out,
+                                           int* accepted_out, qaoa_stream_t stream) {
+    if (!s || !Q || !x) return fail(QAOA_E_INVALID, "session_cycle: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = s->N, m = s->m, k = s->k, K = s->K;
+    if (q_changed) CK(cudaMemcpyAsync(s->Q_dev, Q, (size_t)N * N * sizeof(double), cudaMemcpyHostToDevice, st));
+    // decompose: index sets on the host, matrices on the device
+    qaoa_status r = dqaoa_draw_indices(Q, N, x, s->method, m, k, seed, cycle, s->idx_h);
+    if (r) return r;
+    std::memcpy(s->x_h, x, (size_t)N);
+    CK(cudaMemcpyAsync(s->x_dev, s->x_h, (size_t)N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->idx_dev, s->idx_h, (size_t)m * k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(launch_subqubo(s->Q_dev, N, s->x_dev, m, k, s->idx_dev, s->conditioned, s->qsub, st));
+    // solve all sub-QUBOs
+    r = qaoa_plan_launch(s->plan, stream);
+    if (r) return r;
+    CK(cudaMemcpyAsync(s->topk_h, s->topk, (size_t)m * K * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->expect_h, s->expect, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // aggregate
+    merge(Q, N, x, m, k, s->idx_h, K, s->topk_h, energy_out, accepted_out);
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk) {
+    if (!s) return fail(QAOA_E_INVALID, "session is NULL");
+    if (expect) std::memcpy(expect, s->expect_h, (size_t)s->m * sizeof(double));
+    if (topk) std::memcpy(topk, s->topk_h, (size_t)s->m * s->K * sizeof(uint64_t));
+    return QAOA_OK;
+}
+
+extern "C" qaoa_plan* dqaoa_session_plan(dqaoa_session* s) { return s ? s->plan : nullptr; }
+
+extern "C" void dqaoa_session_destroy(dqaoa_session* s) {
+    if (!s) return;
+    cudaSetDevice(s->ctx->device);
+    qaoa_plan_destroy(s->plan);
+    cudaFreeHost(s->host);
+    cudaFree(s->dev);
+    delete s;
 }

@@ -23,6 +23,7 @@ struct StreamPass {
 template <typename T>
 struct StreamInst {
     int p;
+    const T* Q;           // n x n QUBO the energies are built from (batched energy kernel)
     double amp0;          // 2^{-n/2}
     const T* gamma;
     const T* beta;
@@ -46,6 +47,8 @@ cudaError_t launch_stream_pass(bool dbl, const StreamPass& P, const void* insts,
 cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint64_t ntiles, int k,
                                    cudaStream_t st, const void* one = nullptr);
 cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st);
+// Energies of `count` streaming instances (E written through insts[i].E from insts[i].Q).
+cudaError_t launch_energy_batch(bool dbl, int n, const void* insts, int count, cudaStream_t st);
 int reduce_parts(int n);
 cudaError_t launch_reduce_state(bool dbl, int n, const void* psi, const void* E, int k,
                                 double* part_expect, double* part_topp, uint32_t* part_topz,

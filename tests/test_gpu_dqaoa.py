@@ -1,0 +1,80 @@
+"""One DQAOA cycle at full size (N=1000, 256 sub-QUBOs of n=16, p=3, top-8) through the one-call
+session API, checked against the FP64 oracle: decomposition indices and the merged solution
+bit-exact, sampled sub-QUBOs' <C> and top-k within tolerance."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CFG = synth.DQAOA_BATCH
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_10531_gb300 import build
+    build.build()
+    import paper_2506_10531_gb300 as qq
+    return qq
+
+
+def test_session_cycle_full_size(q, orc):
+    N, m, k, p, K = CFG["N"], CFG["m"], CFG["k"], CFG["p"], CFG["topk"]
+    Q = synth.symmetric_q(N, seed=CFG["seed"])
+    x0 = synth.bits(CFG["seed"] + 1, N)
+    ctx = q.qaoa_create(0)
+    try:
+        s = q.dqaoa_session_create(ctx, N, m, k, p, K, q.DQAOA_RANDOM, True, CFG["gamma"], CFG["beta"])
+        x = x0.copy()
+        e, acc = q.dqaoa_session_cycle(s, Q, 1, x, CFG["seed"], 7)
+        ex, cand = q.dqaoa_session_results(s, m, K)
+        q.dqaoa_session_destroy(s)
+    finally:
+        q.qaoa_destroy(ctx)
+    idx, qs = orc.decompose(Q, x0, m, k, CFG["seed"], 7, conditioned=True)
+    # merge of the GPU's candidates is bit-exact with the oracle's merge
+    xo, eo, ao = orc.merge(Q, x0, idx, cand)
+    np.testing.assert_array_equal(x, xo)
+    assert acc == ao
+    assert e == pytest.approx(eo, abs=1e-9 * np.abs(Q).sum())
+    assert e <= orc.qubo_energy(Q, x0)
+    # sampled sub-QUBOs against the oracle's FP64 solve of the same FP32 sub-QUBO
+    g = np.array(CFG["gamma"], dtype=np.float32).astype(np.float64)
+    b = np.array(CFG["beta"], dtype=np.float32).astype(np.float64)
+    for j in list(range(0, m, 37)) + [m - 1]:
+        Qj = qs[j].astype(np.float32).astype(np.float64)
+        E = orc.energies(Qj)
+        psi = orc.state(k, g, b, E)
+        assert abs(ex[j] - orc.expect(psi, E)) <= 1e-5 * np.abs(Qj).sum(), j
+        pr = np.abs(psi) ** 2
+        eps = 4e-5 * np.sqrt(pr.max())
+        ri, rp = orc.topk_probs(pr, K)
+        for t in range(K):
+            clear = (t == 0 or rp[t - 1] - rp[t] > eps) and (t == K - 1 or rp[t] - rp[t + 1] > eps)
+            if clear:
+                assert int(cand[j, t]) == int(ri[t]), (j, t)
+            else:
+                assert abs(pr[int(cand[j, t])] - rp[t]) <= eps
+
+
+def test_session_cycles_lower_energy(q, orc):
+    N, m, k, p, K = 300, 64, 12, 2, 4
+    Q = synth.symmetric_q(N, seed=5)
+    x = synth.bits(6, N)
+    ctx = q.qaoa_create(0)
+    try:
+        s = q.dqaoa_session_create(ctx, N, m, k, p, K, q.DQAOA_IFD, True, [0.3, 0.5], [0.5, 0.3])
+        es = [orc.qubo_energy(Q, x)]
+        for c in range(4):
+            e, _ = q.dqaoa_session_cycle(s, Q, c == 0, x, 5, c)
+            es.append(e)
+            assert e == pytest.approx(orc.qubo_energy(Q, x), abs=1e-9 * np.abs(Q).sum())
+        q.dqaoa_session_destroy(s)
+    finally:
+        q.qaoa_destroy(ctx)
+    assert all(b <= a for a, b in zip(es, es[1:]))
+    assert es[-1] < es[0]
