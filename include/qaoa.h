@@ -66,6 +66,16 @@ qaoa_status qaoa_reserve(qaoa_ctx* ctx, size_t bytes);
  * (complex64 when dbl == 0, complex128 otherwise). */
 size_t qaoa_workspace_bytes(int n, int dbl);
 
+/* Kernel tier of the batched plans for complex64 instances of n qubits (plans created later).
+ *   QAOA_TIER_AUTO: the library's choice (resident for n <= 14, cluster for 15..18 with
+ *     14 local qubits per CTA, streaming above), or the autotuner's stored choice;
+ *   QAOA_TIER_CLUSTER: cluster tier with `param` local qubits per CTA (13 or 14; the cluster
+ *     then has 2^(n - param) CTAs, at most 16); only 15 <= n <= 18;
+ *   QAOA_TIER_STREAM: HBM streaming; n >= 15.
+ * The resident tier is always used for n <= 14. */
+enum { QAOA_TIER_AUTO = 0, QAOA_TIER_CLUSTER = 2, QAOA_TIER_STREAM = 3 };
+qaoa_status qaoa_set_tier(qaoa_ctx* ctx, int n, int tier, int param);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Single instance, complex64 (FP32 energies). All pointers device, all calls async.         */
 /* ---------------------------------------------------------------------------------------- */

@@ -18,11 +18,13 @@ LIB_PATH = os.path.join(HERE, "libqaoa.so")
 
 QAOA_OK, QAOA_E_INVALID, QAOA_E_NOMEM, QAOA_E_CUDA, QAOA_E_TIMEOUT, QAOA_E_UNSUPPORTED = range(6)
 QAOA_INST_GRAD = 1
+QAOA_TIER_AUTO, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM = 0, 2, 3
 DQAOA_RANDOM, DQAOA_IFD = 0, 1
 
 # Every symbol include/qaoa.h declares.
 EXPORTS = [
     "qaoa_create", "qaoa_destroy", "qaoa_last_error", "qaoa_reserve", "qaoa_workspace_bytes",
+    "qaoa_set_tier",
     "qaoa_build_energies", "qaoa_run_layers", "qaoa_expect", "qaoa_topk", "qaoa_grad",
     "qaoa_build_energies_z", "qaoa_run_layers_z", "qaoa_expect_z", "qaoa_topk_z", "qaoa_grad_z",
     "qaoa_plan_create", "qaoa_plan_launch", "qaoa_plan_kernel_count", "qaoa_plan_destroy",
@@ -80,6 +82,7 @@ def _declare(L):
     L.qaoa_reserve.argtypes = [vp, sz]
     L.qaoa_workspace_bytes.argtypes = [i32, i32]
     L.qaoa_workspace_bytes.restype = sz
+    L.qaoa_set_tier.argtypes = [vp, i32, i32, i32]
     for suf in ("", "_z"):
         getattr(L, "qaoa_build_energies" + suf).argtypes = [vp, i32, vp, vp, vp]
         getattr(L, "qaoa_run_layers" + suf).argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp]
@@ -337,3 +340,7 @@ def qaoa_plan_kernel_bytes(plan, max_kernels=256):
     b = (C.c_double * max_kernels)()
     n = lib().qaoa_plan_kernel_bytes(plan, b, max_kernels)
     return [float(b[i]) for i in range(n)]
+
+
+def qaoa_set_tier(ctx, n, tier, param=0):
+    _check(lib().qaoa_set_tier(ctx, n, tier, param))

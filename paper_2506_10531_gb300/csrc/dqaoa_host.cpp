@@ -113,26 +113,34 @@ void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, cons
 }
 
 // Aggregation: h = Qx is kept up to date (O(N) per flipped variable), so each candidate costs
-// O(|d|^2) with d = x' - x.
+// O(|d|^2) with d = x' - x. With a cache (h, energy, tau of the same Q and x from the previous
+// call) the O(N^2) set-up is skipped.
 int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
-          const uint64_t* cand, double* energy_out, int* accepted_out) {
-    double absq = 0.0;
-    for (int64_t t = 0; t < (int64_t)N * N; ++t) absq += std::fabs(Q[t]);
-    const double tau = 1e-12 * absq;
-    std::vector<double> h(N, 0.0);
-    double energy = 0.0;
-    for (int i = 0; i < N; ++i) {
-        if (!x[i]) continue;
-        const double* row = Q + (int64_t)i * N;
-        for (int l = 0; l < N; ++l)
-            if (x[l]) energy += row[l];
-    }
-    for (int l = 0; l < N; ++l) {
-        const double* row = Q + (int64_t)l * N;
-        double s = 0.0;
-        for (int i = 0; i < N; ++i)
-            if (x[i]) s += row[i];
-        h[l] = s;
+          const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache) {
+    std::vector<double> h_local;
+    std::vector<double>& h = cache ? cache->h : h_local;
+    double energy = 0.0, tau = 0.0;
+    if (cache && cache->valid) {
+        energy = cache->energy;
+        tau = cache->tau;
+    } else {
+        double absq = 0.0;
+        for (int64_t t = 0; t < (int64_t)N * N; ++t) absq += std::fabs(Q[t]);
+        tau = 1e-12 * absq;
+        h.assign(N, 0.0);
+        for (int i = 0; i < N; ++i) {
+            if (!x[i]) continue;
+            const double* row = Q + (int64_t)i * N;
+            for (int l = 0; l < N; ++l)
+                if (x[l]) energy += row[l];
+        }
+        for (int l = 0; l < N; ++l) {
+            const double* row = Q + (int64_t)l * N;
+            double s = 0.0;
+            for (int i = 0; i < N; ++i)
+                if (x[i]) s += row[i];
+            h[l] = s;
+        }
     }
     int accepted = 0;
     int nz[64];
@@ -170,6 +178,11 @@ int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, 
     }
     if (energy_out) *energy_out = energy;
     if (accepted_out) *accepted_out = accepted;
+    if (cache) {
+        cache->energy = energy;
+        cache->tau = tau;
+        cache->valid = true;
+    }
     return 0;
 }
 

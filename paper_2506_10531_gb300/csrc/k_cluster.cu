@@ -1,0 +1,308 @@
+// k_cluster.cu -- cluster tier: one thread-block cluster of C = 2^cb CTAs per QAOA instance
+// (complex64, 15 <= n <= 18), the state and its energies distributed over the CTAs' shared
+// memory and resident for all p layers of Eq. 2 (Section IV).
+//
+// CTA rank r of the cluster holds the 2^L amplitudes z = (r << L) | u (L = n - cb local qubits)
+// and their energies. Local qubits are mixed by the tile engine exactly as in the resident
+// tier. The cb global qubits are mixed by a "global sub-pass": CTA r takes the slab of local
+// positions u whose top cb bits equal r, gathers for each such u the C amplitudes
+// (j << L) | u, j = 0..C-1, from the C CTAs through distributed shared memory, applies
+// exp(-i beta X) on the cb global qubits in registers and writes them back to their owners.
+// Slabs of different CTAs are disjoint, so one cluster barrier before and one after the pass
+// suffice. In each layer the global sub-pass is placed before the last local window, so the
+// snake fusion of consecutive layers (last window, cost, first window) is kept.
+// <C> partials and top-k lists of the CTAs are merged by rank 0 through distributed shared
+// memory, in rank order (deterministic).
+#include <cooperative_groups.h>
+
+#include "qaoa_engine.cuh"
+#include "qaoa_kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace qaoa {
+
+namespace {
+
+constexpr int MAXH = 8;
+
+// Energies of the slice z = (r << L) | u, u < 2^L: thread t fixes the low m bits of u, walks
+// the bits [m, L) in Gray-code order (see the resident tier); the global bits r are fixed.
+__device__ void build_energy_slice(int n, int L, uint32_t r, const float* Qs, float* E) {
+    int m = 31 - __clz((int)blockDim.x);
+    if (m > L) m = L;
+    const int nh = L - m;
+    const uint32_t t = threadIdx.x;
+    if (t >= (1u << m)) return;
+    const uint32_t z0 = t | (r << L);
+    float e = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        if (!((z0 >> i) & 1u)) continue;
+        for (int j = 0; j < n; ++j)
+            if ((z0 >> j) & 1u) e += Qs[i * n + j];
+    }
+    float F[MAXH];
+#pragma unroll
+    for (int h = 0; h < MAXH; ++h) {
+        float f = 0.0f;
+        if (h < nh)
+            for (int j = 0; j < n; ++j)
+                if ((z0 >> j) & 1u) f += Qs[(m + h) * n + j];
+        F[h] = f;
+    }
+    uint32_t u = t;
+    E[swz<float>(u)] = e;
+    const uint32_t steps = 1u << nh;
+    for (uint32_t k = 1; k < steps; ++k) {
+        const int b = __ffs((int)k) - 1;
+        const int hb = m + b;
+        const float d = ((u >> hb) & 1u) ? -1.0f : 1.0f;
+        float fb = 0.0f;
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h)
+            if (h == b) fb = F[h];
+        e += d * (Qs[hb * n + hb] + 2.0f * fb);
+        u ^= 1u << hb;
+#pragma unroll
+        for (int h = 0; h < MAXH; ++h)
+            if (h < nh && h != b) F[h] += d * Qs[(m + h) * n + hb];
+        E[swz<float>(u)] = e;
+    }
+}
+
+struct ClusterSmem {
+    float2* psi;
+    float* E;
+    float* Q;
+    LayerConst<float>* lc;
+    double* red;     // 32
+    TopEnt* top;     // (blockDim/32) * 32
+    double* cex;     // this CTA's <C> partial
+    TopEnt* ctop;    // this CTA's top-k list (16)
+};
+
+__host__ __device__ inline size_t cl_align(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t cluster_layout(int n, int L, int p, int threads, size_t* off) {
+    const size_t D = (size_t)1 << L;
+    size_t o = 0;
+    off[0] = o; o = cl_align(o + D * sizeof(float2));
+    off[1] = o; o = cl_align(o + D * sizeof(float));
+    off[2] = o; o = cl_align(o + (size_t)n * n * sizeof(float));
+    off[3] = o; o = cl_align(o + (size_t)p * sizeof(LayerConst<float>));
+    off[4] = o; o = cl_align(o + 32 * sizeof(double));
+    off[5] = o; o = cl_align(o + (size_t)(threads / 32) * 32 * sizeof(TopEnt));
+    off[6] = o; o = cl_align(o + sizeof(double));
+    off[7] = o; o = cl_align(o + 16 * sizeof(TopEnt));
+    return o;
+}
+
+// Global sub-pass of layer l: mix the CB global qubits of the slab of this CTA.
+template <int CB>
+__device__ void global_subpass(cg::cluster_group& cl, const ClusterSmem& s, int L, uint32_t r,
+                               const LayerConst<float>& lc) {
+    constexpr int C = 1 << CB;
+    float2* rp[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) rp[j] = cl.map_shared_rank(s.psi, j);
+    const uint32_t slab = 1u << (L - CB);
+    const uint32_t top = r << (L - CB);
+    for (uint32_t w = threadIdx.x; w < slab; w += blockDim.x) {
+        const uint32_t ix = swz<float>(top | w);
+        float2 v[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = rp[j][ix];
+        mix_group<CB>(v, C - 1, lc.c, lc.s);
+#pragma unroll
+        for (int j = 0; j < C; ++j) rp[j][ix] = v[j];
+    }
+}
+
+template <int CB>
+__device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float>& d, int L,
+                                     unsigned char* sm) {
+    constexpr int R = Num<float>::RB;
+    const uint32_t r = cl.block_rank();
+    const int n = d.n, p = d.p;
+    size_t off[8];
+    cluster_layout(n, L, p, blockDim.x, off);
+    ClusterSmem s;
+    s.psi = reinterpret_cast<float2*>(sm + off[0]);
+    s.E = reinterpret_cast<float*>(sm + off[1]);
+    s.Q = reinterpret_cast<float*>(sm + off[2]);
+    s.lc = reinterpret_cast<LayerConst<float>*>(sm + off[3]);
+    s.red = reinterpret_cast<double*>(sm + off[4]);
+    s.top = reinterpret_cast<TopEnt*>(sm + off[5]);
+    s.cex = reinterpret_cast<double*>(sm + off[6]);
+    s.ctop = reinterpret_cast<TopEnt*>(sm + off[7]);
+    const uint32_t D = 1u << L;
+
+    for (int l = threadIdx.x; l < p; l += blockDim.x) {
+        float sb, cb;
+        sincos_full(d.beta[l], sb, cb);
+        s.lc[l] = LayerConst<float>{d.gamma[l] / 3.14159265358979323846f, cb, sb};
+    }
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
+    __syncthreads();
+    build_energy_slice(n, L, r, s.Q, s.E);
+    __syncthreads();
+    if (d.E_out)
+        for (uint32_t u = threadIdx.x; u < D; u += blockDim.x) d.E_out[(r << L) | u] = s.E[swz<float>(u)];
+
+    // ---- forward: local snake with the global sub-pass before each layer's last window ----
+    const TileRef<float> tile{s.psi, nullptr, s.E, L};
+    const int G = num_windows(0, L, R);
+    const int S = snake_len(G, p);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpTopK top;
+    top.init(d.k > 0 ? d.k : 1);
+    double ex = 0.0;
+    const float amp0 = (float)exp2(-0.5 * (double)n);
+    for (int si = 0; si < S; ++si) {
+        SubPass sp;
+        snake_step(si, G, p, 0, 1, 0, L, L, R, sp);
+        // sub-pass (l+1)(G-1) holds layer l's last local window (fused with the cost and the
+        // first window of layer l+1); the global qubits of layer l are mixed just before it,
+        // after the cost of layer l (G >= 2: L >= 10 is required by the host)
+        const bool closes = (si >= G - 1) && (si % (G - 1) == 0);
+        if (closes) {
+            cl.sync();
+            global_subpass<CB>(cl, s, L, r, s.lc[sp.la]);
+            cl.sync();
+        }
+        const bool last = (si == S - 1);
+        auto fin = [&](uint32_t base, int a, bool valid) {
+            if (!last) return;
+            float accp = 0.0f;
+#pragma unroll 1
+            for (int i = 0; i < (1 << R); ++i) {
+                const uint32_t u = base | ((uint32_t)i << a);
+                float2 v = make_float2(0.0f, 0.0f);
+                if (valid) {
+                    v = s.psi[swz<float>(u)];
+                    accp += (v.x * v.x + v.y * v.y) * s.E[swz<float>(u)];
+                }
+                if (d.k > 0) top.offer(v, (r << L) | u, valid);
+            }
+            ex += (double)accp;
+        };
+        subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, fin);
+        __syncthreads();
+    }
+    // ---- per-CTA reductions, then rank 0 merges the CTAs in rank order ----
+    const double tot = block_sum(ex, s.red);
+    if (threadIdx.x == 0) *s.cex = tot;
+    if (d.k > 0) {
+        if (lane < d.k) s.top[warp * 32 + lane] = TopEnt{top.p, top.z};
+        __syncthreads();
+        if (warp == 0) {
+            WarpTopK f;
+            f.init(d.k);
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const bool ok = lane < d.k;
+                const TopEnt e = ok ? s.top[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
+                f.offer_exact(e.p, e.z, ok);
+            }
+            if (lane < d.k) s.ctop[lane] = TopEnt{f.p, f.z};
+        }
+    }
+    if (d.psi_out) {
+        float2* pout = reinterpret_cast<float2*>(d.psi_out) + ((size_t)r << L);
+        for (uint32_t u = threadIdx.x; u < D; u += blockDim.x) pout[u] = s.psi[swz<float>(u)];
+    }
+    cl.sync();
+    if (r == 0) {
+        constexpr int C = 1 << CB;
+        if (threadIdx.x == 0 && d.expect) {
+            double acc = 0.0;
+            for (int j = 0; j < C; ++j) acc += *cl.map_shared_rank(s.cex, j);
+            *d.expect = acc;
+        }
+        if (d.k > 0 && warp == 0) {
+            WarpTopK f;
+            f.init(d.k);
+            for (int j = 0; j < C; ++j) {
+                const TopEnt* rt = cl.map_shared_rank(s.ctop, j);
+                const bool ok = lane < d.k;
+                const TopEnt e = ok ? rt[lane] : TopEnt{-1.0, 0xffffffffu};
+                f.offer_exact(e.p, e.z, ok);
+            }
+            if (lane < d.k) {
+                if (d.topk_idx) d.topk_idx[lane] = (uint64_t)f.z;
+                if (d.topk_prob) d.topk_prob[lane] = f.p;
+            }
+        }
+    }
+    cl.sync();   // the next instance reuses the shared memory rank 0 has been reading
+}
+
+// Clusters walk the descriptors round-robin: cluster c takes c, c + #clusters, ...
+template <int CB>
+__global__ void __launch_bounds__(512) k_cluster(const InstDesc<float>* __restrict__ desc, int count,
+                                                 int L) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = 1 << CB;
+    const int ncl = gridDim.x / C;
+    const int cid = blockIdx.x / C;
+    for (int ii = cid; ii < count; ii += ncl) {
+        const InstDesc<float> d = desc[ii];
+        run_cluster_instance<CB>(cl, d, L, sm);
+    }
+}
+
+template <int CB>
+cudaError_t launch_cb(const void* desc, int count, int n, int L, int pmax, int clusters,
+                      cudaStream_t st, int* max_clusters) {
+    const int threads = 512;
+    size_t off[8];
+    const size_t sm = cluster_layout(n, L, pmax, threads, off);
+    cudaError_t e = cudaFuncSetAttribute(k_cluster<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    if ((1 << CB) > 8) {
+        e = cudaFuncSetAttribute(k_cluster<CB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1 << CB;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (max_clusters) {
+        cfg.gridDim = dim3(1 << CB);
+        int mc = 0;
+        e = cudaOccupancyMaxActiveClusters(&mc, k_cluster<CB>, &cfg);
+        *max_clusters = (e == cudaSuccess) ? mc : 0;
+        return e;
+    }
+    cfg.gridDim = dim3((unsigned)(clusters << CB));
+    e = cudaLaunchKernelEx(&cfg, k_cluster<CB>, static_cast<const InstDesc<float>*>(desc), count, L);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t cluster_smem_bytes(int n, int L, int p) {
+    size_t off[8];
+    return cluster_layout(n, L, p, 512, off);
+}
+
+cudaError_t launch_cluster(const void* desc, int count, int n, int L, int pmax, int clusters,
+                           cudaStream_t st, int* max_clusters) {
+    switch (n - L) {
+        case 1: return launch_cb<1>(desc, count, n, L, pmax, clusters, st, max_clusters);
+        case 2: return launch_cb<2>(desc, count, n, L, pmax, clusters, st, max_clusters);
+        case 3: return launch_cb<3>(desc, count, n, L, pmax, clusters, st, max_clusters);
+        case 4: return launch_cb<4>(desc, count, n, L, pmax, clusters, st, max_clusters);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace qaoa

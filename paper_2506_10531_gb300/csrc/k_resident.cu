@@ -112,22 +112,21 @@ __device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s) {
         SubPass sp;
         snake_step(si, G, p, 0, 1, 0, n, n, R, sp);
         const bool last = (si == S - 1);
-        auto fin = [&](C (&v)[1 << R], uint32_t base, int a, bool valid) {
+        auto fin = [&](uint32_t base, int a, bool valid) {
             if (!last) return;
             T accp = T(0);
-#pragma unroll
+#pragma unroll 1
             for (int i = 0; i < (1 << R); ++i) {
+                const uint32_t z = base | ((uint32_t)i << a);
+                C v;
+                v.x = T(0); v.y = T(0);
                 if (valid) {
-                    const uint32_t z = base | ((uint32_t)i << a);
-                    const T pr = v[i].x * v[i].x + v[i].y * v[i].y;
-                    accp += pr * s.E[swz<T>(z)];
+                    v = s.psi[swz<T>(z)];
+                    accp += (v.x * v.x + v.y * v.y) * s.E[swz<T>(z)];
                 }
+                if (d.k > 0) top.offer(v, z, valid);
             }
             ex += (double)accp;
-            if (d.k > 0) {
-#pragma unroll
-                for (int i = 0; i < (1 << R); ++i) top.offer(v[i], base | ((uint32_t)i << a), valid);
-            }
         };
         subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, fin);
         __syncthreads();

@@ -30,18 +30,6 @@ __device__ __forceinline__ uint64_t global_index(const StreamPass& P, uint64_t t
     return lo | (mid << P.c) | (hi << P.s) | (top << (P.s + P.h));
 }
 
-// Two adjacent amplitudes (16-byte aligned for complex64) in one access.
-__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    a = make_float2(v.x, v.y);
-    b = make_float2(v.z, v.w);
-}
-__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
-    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ void ld_pair(const double2* p, double2& a, double2& b) { a = p[0]; b = p[1]; }
-__device__ __forceinline__ void st_pair(double2* p, double2 a, double2 b) { p[0] = a; p[1] = b; }
-
 template <typename T>
 struct StreamSmem {
     typename Num<T>::C* psi;
@@ -58,19 +46,19 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     const uint32_t TD = 1u << P.tb;
     const bool needE = P.need_e;
     C* gpsi = reinterpret_cast<C*>(I.psi);
-    // ---- HBM -> shared (two amplitudes per 16-byte access; c >= 1 keeps them adjacent) ----
+    // ---- HBM -> shared: asynchronous 16-byte copies, all in flight before the wait ----
+    // (tile bit 0 is global bit 0 and c >= 1, so aligned pairs stay adjacent in both layouts)
+    constexpr uint32_t PAIR = sizeof(C) == 8 ? 2u : 1u;   // amplitudes per 16-byte copy
     if (!P.init) {
-        for (uint32_t u = 2 * threadIdx.x; u < TD; u += 2 * blockDim.x) {
-            C a, b;
-            ld_pair(gpsi + global_index(P, tau, u), a, b);
-            s.psi[swz<T>(u)] = a;
-            s.psi[swz<T>(u + 1)] = b;
-        }
+        for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x)
+            cp_async16(&s.psi[swz<T>(u)], gpsi + global_index(P, tau, u));
     }
     if (needE) {
-        for (uint32_t u = threadIdx.x; u < TD; u += blockDim.x)
-            s.E[swz<T>(u)] = I.E[global_index(P, tau, u)];
+        constexpr uint32_t EP = 8u / sizeof(T);           // energies per 8-byte copy
+        for (uint32_t u = EP * threadIdx.x; u < TD; u += EP * blockDim.x)
+            cp_async8(&s.E[swz<T>(u)], I.E + global_index(P, tau, u));
     }
+    cp_async_wait_all();
     __syncthreads();
     // ---- tile engine: snake over the local windows of the mixed bits, layers [la, lb] ----
     const TileRef<T> tile{s.psi, nullptr, s.E, P.tb};
@@ -87,31 +75,30 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
         SubPass sp;
         snake_step(si, G, nl, P.la, P.ph_first, m0, P.tb, P.tb, R, sp);
         const bool last = P.fin && (si == S - 1);
-        auto fin = [&](C (&v)[1 << R], uint32_t base, int a, bool valid) {
+        auto fin = [&](uint32_t base, int a, bool valid) {
             if (!last) return;
             T accp = T(0);
-#pragma unroll
+#pragma unroll 1
             for (int i = 0; i < (1 << R); ++i) {
+                const uint32_t u = base | ((uint32_t)i << a);
+                C v;
+                v.x = T(0); v.y = T(0);
                 if (valid) {
-                    const uint32_t u = base | ((uint32_t)i << a);
-                    accp += (v[i].x * v[i].x + v[i].y * v[i].y) * s.E[swz<T>(u)];
+                    v = s.psi[swz<T>(u)];
+                    accp += (v.x * v.x + v.y * v.y) * s.E[swz<T>(u)];
                 }
+                if (P.k > 0) top.offer(v, (uint32_t)global_index(P, tau, u), valid);
             }
             ex += (double)accp;
-            if (P.k > 0) {
-#pragma unroll
-                for (int i = 0; i < (1 << R); ++i) {
-                    const uint32_t u = base | ((uint32_t)i << a);
-                    top.offer(v[i], (uint32_t)global_index(P, tau, u), valid);
-                }
-            }
         };
         subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, fin);
         __syncthreads();
     }
-    // ---- shared -> HBM ----
-    for (uint32_t u = 2 * threadIdx.x; u < TD; u += 2 * blockDim.x)
-        st_pair(gpsi + global_index(P, tau, u), s.psi[swz<T>(u)], s.psi[swz<T>(u + 1)]);
+    // ---- shared -> HBM (16-byte accesses on both sides) ----
+    for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
+        const uint4 w = *reinterpret_cast<const uint4*>(&s.psi[swz<T>(u)]);
+        *reinterpret_cast<uint4*>(gpsi + global_index(P, tau, u)) = w;
+    }
     if (P.fin) {
         const double tot = block_sum(ex, s.red);
         if (threadIdx.x == 0) I.part_expect[tau] = tot;
@@ -137,7 +124,7 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_stream_pass(const StreamPass P,
+__global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
                                                      const StreamInst<T>* __restrict__ insts,
                                                      int count, const StreamInst<T> one) {
     extern __shared__ __align__(16) unsigned char sm[];

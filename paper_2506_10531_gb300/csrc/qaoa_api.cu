@@ -25,6 +25,8 @@ struct qaoa_ctx {
     void* ws = nullptr;       // workspace (device)
     size_t ws_bytes = 0;
     int* queue = nullptr;     // work counters of the single-call launches (device)
+    int tier[32] = {0};       // QAOA_TIER_* per n for complex64 plans (0: automatic)
+    int cluster_L[32] = {0};  // local qubits per CTA of the cluster tier by n (0: default 14)
 };
 
 namespace {
@@ -246,6 +248,24 @@ extern "C" qaoa_status qaoa_reserve(qaoa_ctx* c, size_t bytes) {
     return QAOA_OK;
 }
 
+extern "C" qaoa_status qaoa_set_tier(qaoa_ctx* c, int n, int tier, int param) {
+    if (!c || n < 1 || n > NMAX) return fail(QAOA_E_INVALID, "set_tier: bad ctx or n");
+    if (tier == QAOA_TIER_AUTO) { c->tier[n] = 0; c->cluster_L[n] = 0; return QAOA_OK; }
+    if (tier == QAOA_TIER_STREAM) {
+        if (n <= RES_NMAX_F) return fail(QAOA_E_INVALID, "set_tier: n=%d is always resident", n);
+        c->tier[n] = tier;
+        return QAOA_OK;
+    }
+    if (tier == QAOA_TIER_CLUSTER) {
+        if (n < CL_NMIN || n > CL_NMAX || param < 10 || param > 14 || n - param < 1 || n - param > 4)
+            return fail(QAOA_E_INVALID, "set_tier: cluster needs 15 <= n <= 18 and 1 <= n - L <= 4");
+        c->tier[n] = tier;
+        c->cluster_L[n] = param;
+        return QAOA_OK;
+    }
+    return fail(QAOA_E_INVALID, "set_tier: unknown tier %d", tier);
+}
+
 extern "C" size_t qaoa_workspace_bytes(int n, int dbl) {
     if (n < 1 || n > NMAX) return 0;
     return std::max(stream_scratch_bytes(dbl != 0, n, KMAX), reduce_scratch_bytes(n));
@@ -308,9 +328,11 @@ struct qaoa_plan {
     void* dev = nullptr;          // one device block: descriptors, scratch, counters
     size_t dev_bytes = 0;
     struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
+    struct CluGroup { int n, L, pmax, count; size_t desc_off; int clusters; };
     struct StrGroup { int n, p, k, count; size_t inst_off; std::vector<StreamPass> passes; int grid;
                       std::vector<int> e_build; std::vector<const void*> q; std::vector<void*> e; };
     std::vector<ResGroup> res;
+    std::vector<CluGroup> clu;
     std::vector<StrGroup> str;
     int kernels = 0;
     bool timing = false;
@@ -351,13 +373,34 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     P->dbl = dbl;
     // group: resident by (n, grad); streaming by (n, p, k)
     std::map<std::pair<int, int>, std::vector<int>> rg;
+    std::map<int, std::vector<int>> cg;
     std::map<std::tuple<int, int, int>, std::vector<int>> sg;
     const int nres = dbl ? RES_NMAX_D : RES_NMAX_F;
     for (int i = 0; i < count; ++i) {
         const qaoa_inst& d = desc[i];
-        if (d.n <= nres) rg[{d.n, (d.flags & QAOA_INST_GRAD) ? 1 : 0}].push_back(i);
+        const bool grad = (d.flags & QAOA_INST_GRAD) != 0;
+        if (d.n <= nres) rg[{d.n, grad ? 1 : 0}].push_back(i);
+        else if (!dbl && !grad && d.n >= CL_NMIN && d.n <= CL_NMAX && c->tier[d.n] != QAOA_TIER_STREAM)
+            cg[d.n].push_back(i);
         else sg[{d.n, d.p, d.k}].push_back(i);
     }
+    auto make_desc = [&](int i) {
+        const qaoa_inst& d = desc[i];
+        InstDesc<T> x{};
+        x.n = d.n; x.p = d.p; x.k = d.k;
+        x.flags = (d.flags & QAOA_INST_GRAD) ? F_GRAD : 0;
+        x.Q = qpool + d.q_off;
+        x.gamma = ppool + d.par_off;
+        x.beta = ppool + d.par_off + d.p;
+        x.psi_out = d.psi_off >= 0 ? (void*)(psipool + d.psi_off) : nullptr;
+        x.E_out = d.e_off >= 0 ? epool + d.e_off : nullptr;
+        x.expect = io->expect ? io->expect + i : nullptr;
+        x.topk_idx = d.k > 0 ? io->topk_idx + (int64_t)i * io->k_stride : nullptr;
+        x.topk_prob = (d.k > 0 && io->topk_prob) ? io->topk_prob + (int64_t)i * io->k_stride : nullptr;
+        x.dgamma = (x.flags & F_GRAD) ? io->grad + d.par_off : nullptr;
+        x.dbeta = (x.flags & F_GRAD) ? io->grad + d.par_off + d.p : nullptr;
+        return x;
+    };
     // sizes
     size_t bytes = 256;  // counters
     std::vector<InstDesc<T>> rdesc;
@@ -373,25 +416,35 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         for (int i : kv.second) {
             const qaoa_inst& d = desc[i];
             g.pmax = std::max(g.pmax, d.p);
-            InstDesc<T> x{};
-            x.n = d.n; x.p = d.p; x.k = d.k;
-            x.flags = (d.flags & QAOA_INST_GRAD) ? F_GRAD : 0;
-            x.Q = qpool + d.q_off;
-            x.gamma = ppool + d.par_off;
-            x.beta = ppool + d.par_off + d.p;
-            x.psi_out = d.psi_off >= 0 ? (void*)(psipool + d.psi_off) : nullptr;
-            x.E_out = d.e_off >= 0 ? epool + d.e_off : nullptr;
-            x.expect = io->expect ? io->expect + i : nullptr;
-            x.topk_idx = d.k > 0 ? io->topk_idx + (int64_t)i * io->k_stride : nullptr;
-            x.topk_prob = (d.k > 0 && io->topk_prob) ? io->topk_prob + (int64_t)i * io->k_stride : nullptr;
-            x.dgamma = (x.flags & F_GRAD) ? io->grad + d.par_off : nullptr;
-            x.dbeta = (x.flags & F_GRAD) ? io->grad + d.par_off + d.p : nullptr;
-            rdesc.push_back(x);
+            rdesc.push_back(make_desc(i));
         }
         bytes = align256(bytes + sizeof(InstDesc<T>) * g.count);
         const int occ = std::max(1, resident_max_blocks_per_sm(dbl, g.n, g.pmax, g.grad));
         g.grid = std::min(g.count, occ * c->nsm);
         P->res.push_back(g);
+    }
+    std::vector<InstDesc<T>> cdesc;
+    for (auto& kv : cg) {
+        qaoa_plan::CluGroup g{};
+        g.n = kv.first;
+        g.L = c->cluster_L[g.n] ? c->cluster_L[g.n] : 14;
+        g.count = (int)kv.second.size();
+        g.pmax = 1;
+        g.desc_off = bytes;
+        for (int i : kv.second) {
+            g.pmax = std::max(g.pmax, desc[i].p);
+            cdesc.push_back(make_desc(i));
+        }
+        bytes = align256(bytes + sizeof(InstDesc<T>) * g.count);
+        int mc = 0;
+        cudaError_t e = launch_cluster(nullptr, 0, g.n, g.L, g.pmax, 0, nullptr, &mc);
+        if (e != cudaSuccess || mc < 1) {
+            delete P;
+            return fail(QAOA_E_UNSUPPORTED, "no cluster of %d CTAs with %zu B shared memory fits (n=%d): %s",
+                        1 << (g.n - g.L), cluster_smem_bytes(g.n, g.L, g.pmax), g.n, cudaGetErrorString(e));
+        }
+        g.clusters = std::min(g.count, mc);
+        P->clu.push_back(g);
     }
     if (qslot > 60) { delete P; return fail(QAOA_E_UNSUPPORTED, "too many resident groups"); }
     // streaming: per instance its own E / psi / partial buffers inside the plan block
@@ -442,6 +495,13 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload descriptors"); }
         P->kernels += 2;  // memset counter + kernel
     }
+    size_t ci = 0;
+    for (auto& g : P->clu) {
+        e = cudaMemcpy(base + g.desc_off, cdesc.data() + ci, sizeof(InstDesc<T>) * g.count, cudaMemcpyHostToDevice);
+        ci += g.count;
+        if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload cluster descriptors"); }
+        P->kernels += 1;
+    }
     // build streaming instances
     size_t gi = 0;
     for (auto& kv : sg) {
@@ -490,6 +550,17 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             b += (double)d.n * d.n * sizeof(T) + 2.0 * d.p * sizeof(T) + sizeof(double) +
                  d.k * 16.0 + (d.psi_off >= 0 ? D * sizeof(C2) : 0.0) + (d.e_off >= 0 ? D * sizeof(T) : 0.0) +
                  ((d.flags & QAOA_INST_GRAD) ? 16.0 * d.p : 0.0);
+        }
+        P->bytes.push_back(b);
+    }
+    for (auto& g : P->clu) {
+        double b = 0.0;
+        for (int i = 0; i < count; ++i) {
+            const qaoa_inst& d = desc[i];
+            if (d.n != g.n || d.n <= nres || (d.flags & QAOA_INST_GRAD)) continue;
+            const double D = (double)(1ull << d.n);
+            b += (double)d.n * d.n * sizeof(T) + 2.0 * d.p * sizeof(T) + sizeof(double) + d.k * 16.0 +
+                 (d.psi_off >= 0 ? D * sizeof(C2) : 0.0) + (d.e_off >= 0 ? D * sizeof(T) : 0.0);
         }
         P->bytes.push_back(b);
     }
@@ -547,6 +618,10 @@ extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
                                    counters + g.q_slot, g.grid, st);
         }));
     }
+    for (auto& g : P->clu)
+        CK(timed("cluster", [&] {
+            return launch_cluster(base + g.desc_off, g.count, g.n, g.L, g.pmax, g.clusters, st, nullptr);
+        }));
     const int tb = stream_tile_bits(P->dbl);
     for (auto& g : P->str) {
         CK(timed("energy", [&] { return launch_energy_batch(P->dbl, g.n, base + g.inst_off, g.count, st); }));
@@ -707,6 +782,8 @@ struct dqaoa_session {
     uint64_t* topk_h = nullptr;
     double* expect_h = nullptr;
     qaoa_plan* plan = nullptr;
+    MergeCache cache;             // h = Qx and E(x) after the last merge
+    std::vector<uint8_t> x_last;  // the solution the cache belongs to
 };
 
 extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, int p, int K, int method,
@@ -789,8 +866,11 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     CK(cudaMemcpyAsync(s->topk_h, s->topk, (size_t)m * K * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(s->expect_h, s->expect, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    // aggregate
-    merge(Q, N, x, m, k, s->idx_h, K, s->topk_h, energy_out, accepted_out);
+    // aggregate (reusing h = Qx when Q is unchanged and x is the solution the last merge left)
+    s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
+                     std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
+    merge(Q, N, x, m, k, s->idx_h, K, s->topk_h, energy_out, accepted_out, &s->cache);
+    s->x_last.assign(x, x + N);
     return QAOA_OK;
 }
 

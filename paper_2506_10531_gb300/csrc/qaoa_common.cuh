@@ -25,14 +25,28 @@ template <> struct Num<double> {
     static constexpr int RB_ADJ = 3;
 };
 
-// Shared-memory swizzle of a tile index: XOR the low SW bits with the next SW bits. Every
-// register window [a, a+R) used by the sub-passes, with the lanes of a warp on the lowest
-// bits outside the window, then touches distinct banks (see the tile-engine comment).
+// Shared-memory swizzle of a tile index. complex64: bits 1..4 are XORed with bits 5..8, so the
+// two amplitudes of an aligned pair (z, z^1) stay adjacent and in order (16-byte copies and
+// 16-byte shared accesses keep working); complex128: bits 0..3 XOR bits 4..7. With the lanes of
+// a warp on the lowest tile bits outside a register window [a, a+R), every sub-pass access is
+// free of bank conflicts (windows that contain bit 0 use 16-byte accesses).
 template <typename T>
-__device__ __forceinline__ uint32_t swz(uint32_t z) {
-    constexpr int SW = Num<T>::RB;
-    return z ^ ((z >> SW) & ((1u << SW) - 1u));
+__device__ __forceinline__ uint32_t swz(uint32_t z);
+template <>
+__device__ __forceinline__ uint32_t swz<float>(uint32_t z) { return z ^ ((z >> 4) & 30u); }
+template <>
+__device__ __forceinline__ uint32_t swz<double>(uint32_t z) { return z ^ ((z >> 4) & 15u); }
+
+// ---- asynchronous global -> shared copies (16 / 8 bytes, L2 only for 16) -----------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---- complex helpers ---------------------------------------------------------------------
 

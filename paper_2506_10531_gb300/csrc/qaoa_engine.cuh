@@ -122,6 +122,45 @@ __device__ __forceinline__ T mix_group_adj(C (&v)[1 << R], C (&u)[1 << R], int m
     return acc;
 }
 
+// Load / store the 2^R amplitudes of a group. complex64 windows starting at bit 0 move aligned
+// pairs with one 16-byte shared access (the swizzle keeps pairs adjacent).
+template <int R>
+__device__ __forceinline__ void load_group(const float2* psi, uint32_t base, int a, float2 (&v)[1 << R]) {
+    if (a == 0 && R >= 1) {
+#pragma unroll
+        for (int i = 0; i < (1 << R); i += 2) {
+            const float4 t = *reinterpret_cast<const float4*>(psi + swz<float>(base | (uint32_t)i));
+            v[i] = make_float2(t.x, t.y);
+            v[i + 1] = make_float2(t.z, t.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) v[i] = psi[swz<float>(base | ((uint32_t)i << a))];
+    }
+}
+template <int R>
+__device__ __forceinline__ void store_group(float2* psi, uint32_t base, int a, const float2 (&v)[1 << R]) {
+    if (a == 0 && R >= 1) {
+#pragma unroll
+        for (int i = 0; i < (1 << R); i += 2)
+            *reinterpret_cast<float4*>(psi + swz<float>(base | (uint32_t)i)) =
+                make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
+    } else {
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) psi[swz<float>(base | ((uint32_t)i << a))] = v[i];
+    }
+}
+template <int R>
+__device__ __forceinline__ void load_group(const double2* psi, uint32_t base, int a, double2 (&v)[1 << R]) {
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) v[i] = psi[swz<double>(base | ((uint32_t)i << a))];
+}
+template <int R>
+__device__ __forceinline__ void store_group(double2* psi, uint32_t base, int a, const double2 (&v)[1 << R]) {
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) psi[swz<double>(base | ((uint32_t)i << a))] = v[i];
+}
+
 // Shared state of one tile.
 template <typename T>
 struct TileRef {
@@ -133,8 +172,10 @@ struct TileRef {
 
 // Forward sub-pass over all groups of the tile.
 //   init:  amplitudes start at amp0 instead of being read (|+> state)
-//   fin:   called once per group slot after the operations, by every thread of the block
-//          (warp-uniform trip count), as fin(v, base, a, valid).
+//   fin:   called once per group slot after the group has been written back, by every thread
+//          of the block (warp-uniform trip count), as fin(base, a, valid); it re-reads the
+//          group from shared memory, which keeps the final reductions out of the register
+//          budget of the butterflies.
 template <typename T, int R, typename Fin>
 __device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& sp,
                                             const LayerConst<T>* lc, bool init, T amp0,
@@ -147,10 +188,11 @@ __device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& 
         const uint32_t base = group_base<R>(valid ? g : 0u, sp.a);
         C v[1 << R];
         if (valid) {
+            if (init) {
 #pragma unroll
-            for (int i = 0; i < (1 << R); ++i) {
-                if (init) { v[i].x = amp0; v[i].y = T(0); }
-                else v[i] = t.psi[swz<T>(base | ((uint32_t)i << sp.a))];
+                for (int i = 0; i < (1 << R); ++i) { v[i].x = amp0; v[i].y = T(0); }
+            } else {
+                load_group<R>(t.psi, base, sp.a, v);
             }
             for (int l = sp.la; l <= sp.lb; ++l) {
                 if (l > sp.la || sp.ph_first) {
@@ -168,11 +210,8 @@ __device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& 
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) { v[i].x = T(0); v[i].y = T(0); }
         }
-        fin(v, base, sp.a, valid);
-        if (valid) {
-#pragma unroll
-            for (int i = 0; i < (1 << R); ++i) t.psi[swz<T>(base | ((uint32_t)i << sp.a))] = v[i];
-        }
+        if (valid) store_group<R>(t.psi, base, sp.a, v);
+        fin(base, sp.a, valid);
     }
 }
 
@@ -189,17 +228,16 @@ __device__ __forceinline__ void subpass_adj(const TileRef<T>& t, const SubPass& 
     for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
         const uint32_t base = group_base<R>(g, sp.a);
         C v[1 << R], u[1 << R];
+        load_group<R>(t.psi, base, sp.a, v);
+        if (lam_from_E) {
 #pragma unroll
-        for (int i = 0; i < (1 << R); ++i) {
-            const uint32_t ix = swz<T>(base | ((uint32_t)i << sp.a));
-            v[i] = t.psi[ix];
-            if (lam_from_E) {
-                const T e = t.E[ix];
+            for (int i = 0; i < (1 << R); ++i) {
+                const T e = t.E[swz<T>(base | ((uint32_t)i << sp.a))];
                 u[i].x = e * v[i].x;
                 u[i].y = e * v[i].y;
-            } else {
-                u[i] = t.lam[ix];
             }
+        } else {
+            load_group<R>(t.lam, base, sp.a, u);
         }
         for (int l = sp.lb; l >= sp.la; --l) {
             const int j = sp.lb - l;
@@ -219,12 +257,8 @@ __device__ __forceinline__ void subpass_adj(const TileRef<T>& t, const SubPass& 
                 acc_g[j] += ag;
             }
         }
-#pragma unroll
-        for (int i = 0; i < (1 << R); ++i) {
-            const uint32_t ix = swz<T>(base | ((uint32_t)i << sp.a));
-            t.psi[ix] = v[i];
-            t.lam[ix] = u[i];
-        }
+        store_group<R>(t.psi, base, sp.a, v);
+        store_group<R>(t.lam, base, sp.a, u);
     }
 }
 

@@ -3,13 +3,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace qaoa {
 int draw_random(int N, int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx);
 int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx);
 void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, const int32_t* idx,
                     int conditioned, double* Qsub);
+// State the merge can carry from one call to the next on the same Q: h = Qx, E(x), tau.
+struct MergeCache {
+    std::vector<double> h;
+    double energy = 0.0, tau = 0.0;
+    bool valid = false;
+};
 int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
-          const uint64_t* cand, double* energy_out, int* accepted_out);
+          const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache = nullptr);
 cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int k,
                            const int32_t* idx, int conditioned, float* qsub, cudaStream_t st);
 cudaError_t launch_plain_layers(int n, int p, const float* gamma, const float* beta,

@@ -44,4 +44,12 @@ cudaError_t launch_resident(bool dbl, const void* desc, int count, int n, int pm
                             int* queue, int grid, cudaStream_t st, const void* one = nullptr);
 int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad);
 
+// ---- cluster tier: one cluster of 2^(n-L) CTAs per complex64 instance (15 <= n <= 18) ----
+constexpr int CL_NMIN = 15, CL_NMAX = 18;
+size_t cluster_smem_bytes(int n, int L, int p);
+// With max_clusters != nullptr nothing is launched: the occupancy limit of active clusters is
+// returned there instead. desc: device array of `count` descriptors of the same n.
+cudaError_t launch_cluster(const void* desc, int count, int n, int L, int pmax, int clusters,
+                           cudaStream_t st, int* max_clusters);
+
 }  // namespace qaoa

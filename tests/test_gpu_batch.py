@@ -64,7 +64,8 @@ def run_batch(q, ctx, specs, seed, order=None):
 
 
 SPECS = [(3, 2, 4, True), (9, 3, 8, True), (14, 2, 8, False), (12, 1, 16, True), (15, 2, 8, False),
-         (17, 3, 8, False), (14, 3, 8, False), (5, 8, 8, True), (13, 2, 1, True), (16, 1, 8, False)]
+         (17, 3, 8, False), (14, 3, 8, False), (5, 8, 8, True), (13, 2, 1, True), (16, 1, 8, False),
+         (18, 2, 8, False), (16, 3, 8, False)]
 
 
 def test_batch_matches_oracle(q, ctx, orc):
@@ -102,6 +103,33 @@ def test_batch_invariance(q, ctx):
         np.testing.assert_array_equal(alone["psi"][:2 << n], full["psi"][2 * so:2 * so + (2 << n)])
         assert alone["ex"][0] == full["ex"][i]
         np.testing.assert_array_equal(alone["ti"][0], full["ti"][i])
+
+
+@pytest.mark.parametrize("tier,param", [(2, 13), (2, 14), (3, 0)])
+def test_tiers_agree_for_large_n(q, orc, tier, param):
+    # the cluster tier (13 or 14 local qubits per CTA) and the streaming tier give the oracle's
+    # results for n = 15..18
+    specs = [(15, 2, 8, False), (16, 3, 8, False), (17, 1, 8, False), (18, 2, 4, False)]
+    c = q.qaoa_create(0)
+    try:
+        for n, *_ in specs:
+            if tier == 2 and n - param > 4:
+                continue
+            q.qaoa_set_tier(c, n, tier, param)
+        r = run_batch(q, c, specs, seed=4242)
+    finally:
+        q.qaoa_destroy(c)
+    for i, (n, p, k, grad, qo, po, so, eo) in enumerate(r["rows"]):
+        Qd = r["Qs"][i].astype(np.float64)
+        par = r["params"][i].astype(np.float64)
+        E_o = orc.energies(Qd)
+        psi_o = orc.state(n, par[:p], par[p:], E_o)
+        ps = r["psi"][2 * so:2 * (so + (1 << n))].reshape(-1, 2)
+        psi_g = ps[:, 0].astype(np.float64) + 1j * ps[:, 1]
+        assert np.max(np.abs(psi_g - psi_o)) <= 1e-5, (n, tier, param)
+        assert abs(r["ex"][i] - orc.expect(psi_o, E_o)) <= 1e-5 * np.abs(Qd).sum()
+        oi, op = orc.topk_probs(orc.probs(psi_g), k)
+        np.testing.assert_array_equal(r["ti"][i, :k].astype(np.uint64), oi)
 
 
 def test_batch_rejects_bad_descriptors(q, ctx):
