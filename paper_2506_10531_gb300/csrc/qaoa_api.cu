@@ -745,7 +745,8 @@ extern "C" qaoa_status dqaoa_decompose(const double* Q, int N, const uint8_t* x,
 extern "C" qaoa_status dqaoa_subqubo_build(qaoa_ctx* c, const double* Q, int N, const uint8_t* x, int m,
                                            int k, const int32_t* idx, int conditioned, float* qsub,
                                            qaoa_stream_t stream) {
-    if (!c || !Q || N < 1 || m < 1 || k < 1 || k > N || k > 4096 || !idx || !qsub || (conditioned && !x))
+    if (!c || !Q || N < 1 || N > 40000 || m < 1 || k < 1 || k > N || k > 4096 || !idx || !qsub ||
+        (conditioned && !x))
         return fail(QAOA_E_INVALID, "subqubo_build: bad arguments");
     CK(launch_subqubo(Q, N, x, m, k, idx, conditioned, qsub, (cudaStream_t)stream));
     return QAOA_OK;

@@ -51,8 +51,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ---- complex helpers ---------------------------------------------------------------------
 
 __device__ __forceinline__ void sincos_phase(float g_over_pi, float e, float& s, float& c) {
-    // theta = gamma * E; sin/cos(pi * y) with y = (gamma/pi) * E keeps the reduction exact.
-    sincospif(g_over_pi * e, &s, &c);
+    // theta = gamma E = pi t with t = (gamma / pi) E. Periodicity: r = t - 2 rint(t / 2) lies in
+    // [-1, 1] and is computed exactly (t and 2 rint(t/2) are within 1 of each other), so
+    // theta' = pi r in [-pi, pi] has the same sine and cosine; the hardware sin/cos is then
+    // evaluated on its accurate range (absolute error below 1e-6).
+    const float t = g_over_pi * e;
+    const float r = fmaf(-2.0f, rintf(0.5f * t), t);
+    __sincosf(3.14159265358979323846f * r, &s, &c);
 }
 __device__ __forceinline__ void sincos_phase(double g_over_pi, double e, double& s, double& c) {
     sincospi(g_over_pi * e, &s, &c);

@@ -122,43 +122,50 @@ __device__ __forceinline__ T mix_group_adj(C (&v)[1 << R], C (&u)[1 << R], int m
     return acc;
 }
 
-// Load / store the 2^R amplitudes of a group. complex64 windows starting at bit 0 move aligned
-// pairs with one 16-byte shared access (the swizzle keeps pairs adjacent).
-template <int R>
-__device__ __forceinline__ void load_group(const float2* psi, uint32_t base, int a, float2 (&v)[1 << R]) {
-    if (a == 0 && R >= 1) {
+// Element addresses of a group. The swizzle is linear over GF(2) and a group's base index and
+// its window offsets (i << A) have disjoint bits, so
+//   swz(base | (i << A)) = swz(base) ^ swz(i << A),
+// one XOR of a per-thread value with a compile-time constant per element.
+template <typename T, int A>
+__device__ __forceinline__ uint32_t woff(int i) { return swz<T>((uint32_t)i << A); }
+
+// Load / store the 2^R amplitudes of a group (window start A). complex64 windows starting at
+// bit 0 move aligned pairs with one 16-byte shared access (the swizzle keeps pairs adjacent).
+template <int R, int A>
+__device__ __forceinline__ void load_group(const float2* psi, uint32_t sb, float2 (&v)[1 << R]) {
+    if (A == 0 && R >= 1) {
 #pragma unroll
         for (int i = 0; i < (1 << R); i += 2) {
-            const float4 t = *reinterpret_cast<const float4*>(psi + swz<float>(base | (uint32_t)i));
+            const float4 t = *reinterpret_cast<const float4*>(psi + (sb ^ woff<float, A>(i)));
             v[i] = make_float2(t.x, t.y);
             v[i + 1] = make_float2(t.z, t.w);
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < (1 << R); ++i) v[i] = psi[swz<float>(base | ((uint32_t)i << a))];
+        for (int i = 0; i < (1 << R); ++i) v[i] = psi[sb ^ woff<float, A>(i)];
     }
 }
-template <int R>
-__device__ __forceinline__ void store_group(float2* psi, uint32_t base, int a, const float2 (&v)[1 << R]) {
-    if (a == 0 && R >= 1) {
+template <int R, int A>
+__device__ __forceinline__ void store_group(float2* psi, uint32_t sb, const float2 (&v)[1 << R]) {
+    if (A == 0 && R >= 1) {
 #pragma unroll
         for (int i = 0; i < (1 << R); i += 2)
-            *reinterpret_cast<float4*>(psi + swz<float>(base | (uint32_t)i)) =
+            *reinterpret_cast<float4*>(psi + (sb ^ woff<float, A>(i))) =
                 make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
     } else {
 #pragma unroll
-        for (int i = 0; i < (1 << R); ++i) psi[swz<float>(base | ((uint32_t)i << a))] = v[i];
+        for (int i = 0; i < (1 << R); ++i) psi[sb ^ woff<float, A>(i)] = v[i];
     }
 }
-template <int R>
-__device__ __forceinline__ void load_group(const double2* psi, uint32_t base, int a, double2 (&v)[1 << R]) {
+template <int R, int A>
+__device__ __forceinline__ void load_group(const double2* psi, uint32_t sb, double2 (&v)[1 << R]) {
 #pragma unroll
-    for (int i = 0; i < (1 << R); ++i) v[i] = psi[swz<double>(base | ((uint32_t)i << a))];
+    for (int i = 0; i < (1 << R); ++i) v[i] = psi[sb ^ woff<double, A>(i)];
 }
-template <int R>
-__device__ __forceinline__ void store_group(double2* psi, uint32_t base, int a, const double2 (&v)[1 << R]) {
+template <int R, int A>
+__device__ __forceinline__ void store_group(double2* psi, uint32_t sb, const double2 (&v)[1 << R]) {
 #pragma unroll
-    for (int i = 0; i < (1 << R); ++i) psi[swz<double>(base | ((uint32_t)i << a))] = v[i];
+    for (int i = 0; i < (1 << R); ++i) psi[sb ^ woff<double, A>(i)] = v[i];
 }
 
 // Shared state of one tile.
@@ -170,29 +177,25 @@ struct TileRef {
     int tb;                    // tile bits
 };
 
-// Forward sub-pass over all groups of the tile.
-//   init:  amplitudes start at amp0 instead of being read (|+> state)
-//   fin:   called once per group slot after the group has been written back, by every thread
-//          of the block (warp-uniform trip count), as fin(base, a, valid); it re-reads the
-//          group from shared memory, which keeps the final reductions out of the register
-//          budget of the butterflies.
-template <typename T, int R, typename Fin>
-__device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& sp,
-                                            const LayerConst<T>* lc, bool init, T amp0,
-                                            Fin&& fin) {
+// Forward sub-pass with a compile-time window start A (see subpass_fwd).
+template <typename T, int R, int A, typename Fin>
+__device__ __forceinline__ void subpass_fwd_a(const TileRef<T>& t, const SubPass& sp,
+                                              const LayerConst<T>* lc, bool init, T amp0,
+                                              Fin&& fin) {
     using C = typename Num<T>::C;
     const uint32_t ngroups = 1u << (t.tb - R);
     for (uint32_t g0 = 0; g0 < ngroups; g0 += blockDim.x) {
         const uint32_t g = g0 + threadIdx.x;
         const bool valid = g < ngroups;
-        const uint32_t base = group_base<R>(valid ? g : 0u, sp.a);
+        const uint32_t base = group_base<R>(valid ? g : 0u, A);
+        const uint32_t sb = swz<T>(base);
         C v[1 << R];
         if (valid) {
             if (init) {
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) { v[i].x = amp0; v[i].y = T(0); }
             } else {
-                load_group<R>(t.psi, base, sp.a, v);
+                load_group<R, A>(t.psi, sb, v);
             }
             for (int l = sp.la; l <= sp.lb; ++l) {
                 if (l > sp.la || sp.ph_first) {
@@ -200,18 +203,85 @@ __device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& 
 #pragma unroll
                     for (int i = 0; i < (1 << R); ++i) {
                         T s, c;
-                        sincos_phase(gp, t.E[swz<T>(base | ((uint32_t)i << sp.a))], s, c);
+                        sincos_phase(gp, t.E[sb ^ woff<T, A>(i)], s, c);
                         rot_neg(v[i], s, c);
                     }
                 }
                 mix_group<R>(v, sp.mask, lc[l].c, lc[l].s);
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < (1 << R); ++i) { v[i].x = T(0); v[i].y = T(0); }
+            store_group<R, A>(t.psi, sb, v);
         }
-        if (valid) store_group<R>(t.psi, base, sp.a, v);
-        fin(base, sp.a, valid);
+        fin(base, A, valid);
+    }
+}
+
+// Forward sub-pass over all groups of the tile.
+//   init:  amplitudes start at amp0 instead of being read (|+> state)
+//   fin:   called once per group slot after the group has been written back, by every thread
+//          of the block (warp-uniform trip count), as fin(base, a, valid); it re-reads the
+//          group from shared memory, which keeps the final reductions out of the register
+//          budget of the butterflies.
+// The window start is dispatched to a compile-time constant (0 <= a <= tb - R <= 9).
+template <typename T, int R, typename Fin>
+__device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& sp,
+                                            const LayerConst<T>* lc, bool init, T amp0,
+                                            Fin&& fin) {
+    switch (sp.a) {
+        case 0: subpass_fwd_a<T, R, 0>(t, sp, lc, init, amp0, fin); break;
+        case 1: subpass_fwd_a<T, R, 1>(t, sp, lc, init, amp0, fin); break;
+        case 2: subpass_fwd_a<T, R, 2>(t, sp, lc, init, amp0, fin); break;
+        case 3: subpass_fwd_a<T, R, 3>(t, sp, lc, init, amp0, fin); break;
+        case 4: subpass_fwd_a<T, R, 4>(t, sp, lc, init, amp0, fin); break;
+        case 5: subpass_fwd_a<T, R, 5>(t, sp, lc, init, amp0, fin); break;
+        case 6: subpass_fwd_a<T, R, 6>(t, sp, lc, init, amp0, fin); break;
+        case 7: subpass_fwd_a<T, R, 7>(t, sp, lc, init, amp0, fin); break;
+        case 8: subpass_fwd_a<T, R, 8>(t, sp, lc, init, amp0, fin); break;
+        default: subpass_fwd_a<T, R, 9>(t, sp, lc, init, amp0, fin); break;
+    }
+}
+
+// Adjoint sub-pass with a compile-time window start A (see subpass_adj).
+template <typename T, int R, int A>
+__device__ __forceinline__ void subpass_adj_a(const TileRef<T>& t, const SubPass& sp,
+                                              const LayerConst<T>* lc, bool lam_from_E,
+                                              T (&acc_b)[2], T (&acc_g)[2]) {
+    using C = typename Num<T>::C;
+    const uint32_t ngroups = 1u << (t.tb - R);
+    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+        const uint32_t sb = swz<T>(group_base<R>(g, A));
+        C v[1 << R], u[1 << R];
+        load_group<R, A>(t.psi, sb, v);
+        if (lam_from_E) {
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) {
+                const T e = t.E[sb ^ woff<T, A>(i)];
+                u[i].x = e * v[i].x;
+                u[i].y = e * v[i].y;
+            }
+        } else {
+            load_group<R, A>(t.lam, sb, u);
+        }
+        for (int l = sp.lb; l >= sp.la; --l) {
+            const int j = sp.lb - l;
+            const T ab = mix_group_adj<R>(v, u, sp.mask, lc[l].c, lc[l].s);
+            if (j == 0) acc_b[0] += ab; else acc_b[1] += ab;
+            if (l > sp.la || sp.ph_first) {
+                const T gp = -lc[l].gpi;
+                T ag = T(0);
+#pragma unroll
+                for (int i = 0; i < (1 << R); ++i) {
+                    const T e = t.E[sb ^ woff<T, A>(i)];
+                    ag += e * im_conj_mul(u[i], v[i]);
+                    T s, c;
+                    sincos_phase(gp, e, s, c);
+                    rot_neg(v[i], s, c);
+                    rot_neg(u[i], s, c);
+                }
+                if (j == 0) acc_g[0] += ag; else acc_g[1] += ag;
+            }
+        }
+        store_group<R, A>(t.psi, sb, v);
+        store_group<R, A>(t.lam, sb, u);
     }
 }
 
@@ -223,42 +293,17 @@ template <typename T, int R>
 __device__ __forceinline__ void subpass_adj(const TileRef<T>& t, const SubPass& sp,
                                             const LayerConst<T>* lc, bool lam_from_E,
                                             T (&acc_b)[2], T (&acc_g)[2]) {
-    using C = typename Num<T>::C;
-    const uint32_t ngroups = 1u << (t.tb - R);
-    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-        const uint32_t base = group_base<R>(g, sp.a);
-        C v[1 << R], u[1 << R];
-        load_group<R>(t.psi, base, sp.a, v);
-        if (lam_from_E) {
-#pragma unroll
-            for (int i = 0; i < (1 << R); ++i) {
-                const T e = t.E[swz<T>(base | ((uint32_t)i << sp.a))];
-                u[i].x = e * v[i].x;
-                u[i].y = e * v[i].y;
-            }
-        } else {
-            load_group<R>(t.lam, base, sp.a, u);
-        }
-        for (int l = sp.lb; l >= sp.la; --l) {
-            const int j = sp.lb - l;
-            acc_b[j] += mix_group_adj<R>(v, u, sp.mask, lc[l].c, lc[l].s);
-            if (l > sp.la || sp.ph_first) {
-                const T gp = -lc[l].gpi;
-                T ag = T(0);
-#pragma unroll
-                for (int i = 0; i < (1 << R); ++i) {
-                    const T e = t.E[swz<T>(base | ((uint32_t)i << sp.a))];
-                    ag += e * im_conj_mul(u[i], v[i]);
-                    T s, c;
-                    sincos_phase(gp, e, s, c);
-                    rot_neg(v[i], s, c);
-                    rot_neg(u[i], s, c);
-                }
-                acc_g[j] += ag;
-            }
-        }
-        store_group<R>(t.psi, base, sp.a, v);
-        store_group<R>(t.lam, base, sp.a, u);
+    switch (sp.a) {
+        case 0: subpass_adj_a<T, R, 0>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 1: subpass_adj_a<T, R, 1>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 2: subpass_adj_a<T, R, 2>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 3: subpass_adj_a<T, R, 3>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 4: subpass_adj_a<T, R, 4>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 5: subpass_adj_a<T, R, 5>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 6: subpass_adj_a<T, R, 6>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 7: subpass_adj_a<T, R, 7>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 8: subpass_adj_a<T, R, 8>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        default: subpass_adj_a<T, R, 9>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
     }
 }
 
