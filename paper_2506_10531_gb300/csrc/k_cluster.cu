@@ -36,18 +36,16 @@ __device__ void build_energy_slice(int n, int L, uint32_t r, const float* Qs, fl
     if (t >= (1u << m)) return;
     const uint32_t z0 = t | (r << L);
     float e = 0.0f;
-    for (int i = 0; i < n; ++i) {
-        if (!((z0 >> i) & 1u)) continue;
-        for (int j = 0; j < n; ++j)
-            if ((z0 >> j) & 1u) e += Qs[i * n + j];
+    for (uint32_t bi = z0; bi; bi &= bi - 1u) {         // set bits i of z0
+        const float* row = Qs + (__ffs((int)bi) - 1) * n;
+        for (uint32_t bj = z0; bj; bj &= bj - 1u) e += row[__ffs((int)bj) - 1];
     }
     float F[MAXH];
 #pragma unroll
     for (int h = 0; h < MAXH; ++h) {
         float f = 0.0f;
         if (h < nh)
-            for (int j = 0; j < n; ++j)
-                if ((z0 >> j) & 1u) f += Qs[(m + h) * n + j];
+            for (uint32_t bj = z0; bj; bj &= bj - 1u) f += Qs[(m + h) * n + (__ffs((int)bj) - 1)];
         F[h] = f;
     }
     uint32_t u = t;
@@ -83,6 +81,9 @@ struct ClusterSmem {
 
 __host__ __device__ inline size_t cl_align(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// One 32-amplitude group per thread per sub-pass.
+inline int cluster_threads(int L) { return (1 << L) / 32; }
+
 __host__ __device__ inline size_t cluster_layout(int n, int L, int p, int threads, size_t* off) {
     const size_t D = (size_t)1 << L;
     size_t o = 0;
@@ -97,24 +98,39 @@ __host__ __device__ inline size_t cluster_layout(int n, int L, int p, int thread
     return o;
 }
 
-// Global sub-pass of layer l: mix the CB global qubits of the slab of this CTA.
+// Global sub-pass of layer l: mix the CB global qubits of the slab of this CTA. Each thread
+// takes NP = 16 / C slab positions at once so that 16 remote loads are in flight together.
 template <int CB>
 __device__ void global_subpass(cg::cluster_group& cl, const ClusterSmem& s, int L, uint32_t r,
                                const LayerConst<float>& lc) {
     constexpr int C = 1 << CB;
+    constexpr int NP = (16 / C) > 0 ? (16 / C) : 1;
     float2* rp[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) rp[j] = cl.map_shared_rank(s.psi, j);
     const uint32_t slab = 1u << (L - CB);
     const uint32_t top = r << (L - CB);
-    for (uint32_t w = threadIdx.x; w < slab; w += blockDim.x) {
-        const uint32_t ix = swz<float>(top | w);
-        float2 v[C];
+    for (uint32_t w0 = threadIdx.x; w0 < slab; w0 += blockDim.x * NP) {
+        float2 v[NP][C];
+        uint32_t ix[NP];
 #pragma unroll
-        for (int j = 0; j < C; ++j) v[j] = rp[j][ix];
-        mix_group<CB>(v, C - 1, lc.c, lc.s);
+        for (int q = 0; q < NP; ++q) {
+            const uint32_t w = w0 + (uint32_t)q * blockDim.x;
+            ix[q] = swz<float>(top | (w < slab ? w : 0u));
+        }
 #pragma unroll
-        for (int j = 0; j < C; ++j) rp[j][ix] = v[j];
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+            for (int j = 0; j < C; ++j) v[q][j] = rp[j][ix[q]];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) mix_group<CB>(v[q], C - 1, lc.c, lc.s);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            if (w0 + (uint32_t)q * blockDim.x < slab) {
+#pragma unroll
+                for (int j = 0; j < C; ++j) rp[j][ix[q]] = v[q][j];
+            }
+        }
     }
 }
 
@@ -172,19 +188,9 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
         }
         const bool last = (si == S - 1);
         auto fin = [&](uint32_t base, int a, bool valid) {
-            if (!last) return;
-            float accp = 0.0f;
-#pragma unroll 1
-            for (int i = 0; i < (1 << R); ++i) {
-                const uint32_t u = base | ((uint32_t)i << a);
-                float2 v = make_float2(0.0f, 0.0f);
-                if (valid) {
-                    v = s.psi[swz<float>(u)];
-                    accp += (v.x * v.x + v.y * v.y) * s.E[swz<float>(u)];
-                }
-                if (d.k > 0) top.offer(v, (r << L) | u, valid);
-            }
-            ex += (double)accp;
+            if (last)
+                reduce_group<float, R>(tile, base, a, valid, d.k, top, ex,
+                                       [&](uint32_t u) { return (r << L) | u; });
         };
         subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, fin);
         __syncthreads();
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(512) k_cluster(const InstDesc<float>* __restri
 template <int CB>
 cudaError_t launch_cb(const void* desc, int count, int n, int L, int pmax, int clusters,
                       cudaStream_t st, int* max_clusters) {
-    const int threads = 512;
+    const int threads = cluster_threads(L);
     size_t off[8];
     const size_t sm = cluster_layout(n, L, pmax, threads, off);
     cudaError_t e = cudaFuncSetAttribute(k_cluster<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -291,7 +297,7 @@ cudaError_t launch_cb(const void* desc, int count, int n, int L, int pmax, int c
 
 size_t cluster_smem_bytes(int n, int L, int p) {
     size_t off[8];
-    return cluster_layout(n, L, p, 512, off);
+    return cluster_layout(n, L, p, cluster_threads(L), off);
 }
 
 cudaError_t launch_cluster(const void* desc, int count, int n, int L, int pmax, int clusters,

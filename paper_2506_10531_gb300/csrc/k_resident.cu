@@ -31,18 +31,16 @@ __device__ void build_energy(int n, const T* Qs, T* E) {
     const uint32_t t = threadIdx.x;
     if (t >= (1u << m)) return;
     T e = T(0);
-    for (int i = 0; i < m; ++i) {
-        if (!((t >> i) & 1u)) continue;
-        for (int j = 0; j < m; ++j)
-            if ((t >> j) & 1u) e += Qs[i * n + j];
+    for (uint32_t bi = t; bi; bi &= bi - 1u) {          // set bits i of t
+        const T* row = Qs + (__ffs((int)bi) - 1) * n;
+        for (uint32_t bj = t; bj; bj &= bj - 1u) e += row[__ffs((int)bj) - 1];
     }
     T F[MAXH];
 #pragma unroll
     for (int h = 0; h < MAXH; ++h) {
         T f = T(0);
         if (h < nh)
-            for (int j = 0; j < m; ++j)
-                if ((t >> j) & 1u) f += Qs[(m + h) * n + j];
+            for (uint32_t bj = t; bj; bj &= bj - 1u) f += Qs[(m + h) * n + (__ffs((int)bj) - 1)];
         F[h] = f;
     }
     uint32_t z = t;
@@ -97,7 +95,6 @@ __host__ __device__ inline size_t smem_layout(int n, int p, bool grad, int threa
 
 template <typename T, int R>
 __device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s) {
-    using C = typename Num<T>::C;
     const int n = d.n, p = d.p;
     const TileRef<T> tile{s.psi, s.lam, s.E, n};
     const bool init = !(d.flags & F_INIT_PSI);
@@ -113,20 +110,7 @@ __device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s) {
         snake_step(si, G, p, 0, 1, 0, n, n, R, sp);
         const bool last = (si == S - 1);
         auto fin = [&](uint32_t base, int a, bool valid) {
-            if (!last) return;
-            T accp = T(0);
-#pragma unroll 1
-            for (int i = 0; i < (1 << R); ++i) {
-                const uint32_t z = base | ((uint32_t)i << a);
-                C v;
-                v.x = T(0); v.y = T(0);
-                if (valid) {
-                    v = s.psi[swz<T>(z)];
-                    accp += (v.x * v.x + v.y * v.y) * s.E[swz<T>(z)];
-                }
-                if (d.k > 0) top.offer(v, z, valid);
-            }
-            ex += (double)accp;
+            if (last) reduce_group<T, R>(tile, base, a, valid, d.k, top, ex, [](uint32_t u) { return u; });
         };
         subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, fin);
         __syncthreads();

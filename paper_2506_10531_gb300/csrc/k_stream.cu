@@ -76,20 +76,9 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
         snake_step(si, G, nl, P.la, P.ph_first, m0, P.tb, P.tb, R, sp);
         const bool last = P.fin && (si == S - 1);
         auto fin = [&](uint32_t base, int a, bool valid) {
-            if (!last) return;
-            T accp = T(0);
-#pragma unroll 1
-            for (int i = 0; i < (1 << R); ++i) {
-                const uint32_t u = base | ((uint32_t)i << a);
-                C v;
-                v.x = T(0); v.y = T(0);
-                if (valid) {
-                    v = s.psi[swz<T>(u)];
-                    accp += (v.x * v.x + v.y * v.y) * s.E[swz<T>(u)];
-                }
-                if (P.k > 0) top.offer(v, (uint32_t)global_index(P, tau, u), valid);
-            }
-            ex += (double)accp;
+            if (last)
+                reduce_group<T, R>(tile, base, a, valid, P.k, top, ex,
+                                   [&](uint32_t u) { return (uint32_t)global_index(P, tau, u); });
         };
         subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, fin);
         __syncthreads();

@@ -92,6 +92,23 @@ __device__ __forceinline__ auto im_conj_mul(const C& x, const C& y) -> decltype(
 
 // ---- warp reductions (fixed order: deterministic) ----------------------------------------
 
+// The k-th largest (k = 1..32) of one float per lane: bitonic sort over the lanes into
+// descending order (lane l ends with the (l+1)-th largest value).
+__device__ __forceinline__ float warp_kth_largest(float v, int k) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+            const bool asc = (lane & size) == 0;
+            const bool lower = (lane & stride) == 0;
+            v = (lower != asc) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return __shfl_sync(0xffffffffu, v, k - 1);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -126,7 +143,8 @@ __device__ __forceinline__ double exact_prob(double2 v) {
 struct WarpTopK {
     double p;          // this lane's entry (lane < k)
     uint32_t z;
-    float thr_f;       // FP32 lower bound of the k-th probability (warp-uniform)
+    float thr_f;       // FP32 filter threshold (warp-uniform): max(list bound, boot)
+    float boot;        // proven lower bound on the final k-th probability (raise_threshold)
     int k;
 
     __device__ __forceinline__ void init(int kk) {
@@ -134,6 +152,7 @@ struct WarpTopK {
         p = -1.0;
         z = 0xffffffffu;
         thr_f = -1.0f;
+        boot = -1.0f;
     }
     // Insert candidate (cp, cz) held by lane `src` if it beats the k-th entry (warp-uniform).
     __device__ __forceinline__ void insert_from(int src, double cp, uint32_t cz) {
@@ -150,7 +169,7 @@ struct WarpTopK {
             else if (lane > pos && lane < k) { p = up_p; z = up_z; }
         }
         const double kth = __shfl_sync(0xffffffffu, p, k - 1);
-        thr_f = (kth < 0.0) ? -1.0f : __double2float_rd(kth);
+        thr_f = fmaxf((kth < 0.0) ? -1.0f : __double2float_rd(kth), boot);
     }
     // Offer one amplitude per lane (all lanes call; lanes with valid == false offer nothing).
     template <typename C>
@@ -166,6 +185,12 @@ struct WarpTopK {
             m &= m - 1;
             insert_from(src, cp, zi);
         }
+    }
+    // Raise the FP32 filter threshold to a value known to be <= the k-th largest probability
+    // of the elements still to be offered (no list entry is changed).
+    __device__ __forceinline__ void raise_threshold(float lower_bound) {
+        boot = fmaxf(boot, lower_bound);
+        thr_f = fmaxf(thr_f, boot);
     }
     // Offer an entry with a known exact probability (merging lists).
     __device__ __forceinline__ void offer_exact(double cp, uint32_t zi, bool valid) {

@@ -307,6 +307,44 @@ __device__ __forceinline__ void subpass_adj(const TileRef<T>& t, const SubPass& 
     }
 }
 
+// Final reductions of one group (2^R amplitudes of window start a, already written back):
+// <C> partial (FP32 over the group, FP64 across groups) and the warp's top-k list. Before
+// offering, the list threshold is raised to the k-th largest of the lanes' group maxima: the k
+// lanes with the largest maxima hold k distinct elements at least that probable, so every
+// element of the final top-k passes the FP32 filter (margins as in WarpTopK::offer), while
+// most elements are rejected without an insertion. zmap(u) gives the global index of tile
+// index u. Called by every thread of the warp.
+template <typename T, int R, typename ZMap>
+__device__ __forceinline__ void reduce_group(const TileRef<T>& t, uint32_t base, int a, bool valid,
+                                             int k, WarpTopK& top, double& ex, ZMap&& zmap) {
+    using C = typename Num<T>::C;
+    T accp = T(0);
+    float pmax = -1.0f;
+#pragma unroll 1
+    for (int i = 0; i < (1 << R); ++i) {
+        if (valid) {
+            const uint32_t ix = swz<T>(base | ((uint32_t)i << a));
+            const C v = t.psi[ix];
+            const T pr = v.x * v.x + v.y * v.y;
+            accp += pr * t.E[ix];
+            pmax = fmaxf(pmax, (float)pr);
+        }
+    }
+    ex += (double)accp;
+    if (k <= 0) return;
+    const float kth = warp_kth_largest(pmax, k);
+    if (kth > 0.0f) top.raise_threshold(kth * 0.99999904632568359375f);   // (1 - 2^-20)
+#pragma unroll 1
+    for (int i = 0; i < (1 << R); ++i) {
+        const uint32_t u = base | ((uint32_t)i << a);
+        C v;
+        v.x = T(0);
+        v.y = T(0);
+        if (valid) v = t.psi[swz<T>(u)];
+        top.offer(v, zmap(u), valid);
+    }
+}
+
 // Block-wide sum of one value per thread into slot[0] (thread 0 only); red has blockDim/32
 // doubles. Fixed order: deterministic. Must be called by all threads.
 __device__ __forceinline__ double block_sum(double v, double* red) {
