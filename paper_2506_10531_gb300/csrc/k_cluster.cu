@@ -192,7 +192,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
                 reduce_group<float, R>(tile, base, a, valid, d.k, top, ex,
                                        [&](uint32_t u) { return (r << L) | u; });
         };
-        subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, fin);
+        subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, __popc(r), fin);
         __syncthreads();
     }
     // ---- per-CTA reductions, then rank 0 merges the CTAs in rank order ----
@@ -212,9 +212,11 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
             if (lane < d.k) s.ctop[lane] = TopEnt{f.p, f.z};
         }
     }
-    if (d.psi_out) {
+    if (d.psi_out) {              // back from the rotated frame: psi = (-i)^{|z|} psi~
         float2* pout = reinterpret_cast<float2*>(d.psi_out) + ((size_t)r << L);
-        for (uint32_t u = threadIdx.x; u < D; u += blockDim.x) pout[u] = s.psi[swz<float>(u)];
+        const int pr = __popc(r);
+        for (uint32_t u = threadIdx.x; u < D; u += blockDim.x)
+            pout[u] = times_i_pow(s.psi[swz<float>(u)], -(pr + __popc(u)));
     }
     cl.sync();
     if (r == 0) {

@@ -33,10 +33,10 @@ __global__ void k_plain_rx(uint64_t half, int q, const float* __restrict__ beta,
     const uint64_t z = ((t >> q) << (q + 1)) | lo;
     float s, c;
     sincosf(beta[l], &s, &c);
-    float2 a = psi[z], b = psi[z | (1ull << q)];
-    butterfly(a, b, c, s);
-    psi[z] = a;
-    psi[z | (1ull << q)] = b;
+    // exp(-i beta X): a' = c a - i s b, b' = -i s a + c b
+    const float2 a = psi[z], b = psi[z | (1ull << q)];
+    psi[z] = make_float2(c * a.x + s * b.y, c * a.y - s * b.x);
+    psi[z | (1ull << q)] = make_float2(c * b.x + s * a.y, c * b.y - s * a.x);
 }
 
 }  // namespace

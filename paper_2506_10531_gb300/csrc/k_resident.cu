@@ -112,7 +112,7 @@ __device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s) {
         auto fin = [&](uint32_t base, int a, bool valid) {
             if (last) reduce_group<T, R>(tile, base, a, valid, d.k, top, ex, [](uint32_t u) { return u; });
         };
-        subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, fin);
+        subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, 0, fin);
         __syncthreads();
     }
     // <C>
@@ -204,9 +204,10 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     } else {
         for (uint32_t z = threadIdx.x; z < D; z += blockDim.x) s.E[swz<T>(z)] = d.E_in[z];
     }
-    if (d.flags & F_INIT_PSI) {
+    if (d.flags & F_INIT_PSI) {   // into the rotated frame: psi~ = i^{|z|} psi
         const C* pin = reinterpret_cast<const C*>(d.psi_in);
-        for (uint32_t z = threadIdx.x; z < D; z += blockDim.x) s.psi[swz<T>(z)] = pin[z];
+        for (uint32_t z = threadIdx.x; z < D; z += blockDim.x)
+            s.psi[swz<T>(z)] = times_i_pow(pin[z], __popc(z));
     }
     __syncthreads();
     if (d.E_out)
@@ -214,9 +215,10 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
 
     forward_run<T, R>(d, s);
 
-    if (d.psi_out) {
+    if (d.psi_out) {              // back from the rotated frame: psi = (-i)^{|z|} psi~
         C* pout = reinterpret_cast<C*>(d.psi_out);
-        for (uint32_t z = threadIdx.x; z < D; z += blockDim.x) pout[z] = s.psi[swz<T>(z)];
+        for (uint32_t z = threadIdx.x; z < D; z += blockDim.x)
+            pout[z] = times_i_pow(s.psi[swz<T>(z)], -__popc(z));
     }
     if (grad) adjoint_run<T, RA>(d, s);
 }

@@ -80,13 +80,21 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
                 reduce_group<T, R>(tile, base, a, valid, P.k, top, ex,
                                    [&](uint32_t u) { return (uint32_t)global_index(P, tau, u); });
         };
-        subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, fin);
+        subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, __popcll(tau), fin);
         __syncthreads();
     }
-    // ---- shared -> HBM (16-byte accesses on both sides) ----
-    for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
-        const uint4 w = *reinterpret_cast<const uint4*>(&s.psi[swz<T>(u)]);
-        *reinterpret_cast<uint4*>(gpsi + global_index(P, tau, u)) = w;
+    // ---- shared -> HBM (16-byte accesses on both sides). Between passes the state stays in
+    // the rotated frame; the last pass converts back with (-i)^{|z|} (|z| = |tau| + |u|: the
+    // tile map only permutes bits). ----
+    if (!P.fin) {
+        for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
+            const uint4 w = *reinterpret_cast<const uint4*>(&s.psi[swz<T>(u)]);
+            *reinterpret_cast<uint4*>(gpsi + global_index(P, tau, u)) = w;
+        }
+    } else {
+        const int pt = __popcll(tau);
+        for (uint32_t u = threadIdx.x; u < TD; u += blockDim.x)
+            gpsi[global_index(P, tau, u)] = times_i_pow(s.psi[swz<T>(u)], -(pt + __popc(u)));
     }
     if (P.fin) {
         const double tot = block_sum(ex, s.red);

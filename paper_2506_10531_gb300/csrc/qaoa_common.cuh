@@ -74,20 +74,80 @@ __device__ __forceinline__ void rot_neg(C& v, T s, T c) {
     v.y = i * c - r * s;
 }
 
-// exp(-i beta X) on a pair (a, b); (c, s) = (cos beta, sin beta)
-template <typename C, typename T>
-__device__ __forceinline__ void butterfly(C& a, C& b, T c, T s) {
-    const C a0 = a, b0 = b;
-    a.x = c * a0.x + s * b0.y;
-    a.y = c * a0.y - s * b0.x;
-    b.x = c * b0.x + s * a0.y;
-    b.y = c * b0.y - s * a0.x;
+// ---- the rotated frame ----------------------------------------------------------------
+// The kernels evolve psi~(z) = i^{|z|} psi(z) (|z| = number of set bits). This per-qubit
+// diagonal change of basis D = diag(1, i) commutes with the cost phase (both diagonal), leaves
+// every |amplitude|^2 unchanged bit for bit (it only swaps and negates components), and turns
+// the mixer factor into a real rotation:
+//   D exp(-i beta X) D^-1 = exp(-i beta Y) = [[cos b, -sin b], [sin b, cos b]],
+// i.e. a' = c a - s b, b' = s a + c b applied identically to the real and imaginary parts.
+// psi is converted back with (-i)^{|z|} only where a state leaves the library.
+
+// Packed FP32 pair arithmetic (one instruction for both components).
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
 }
 
-// Im(conj(x) * y)
+// Mixer coefficients of one layer in the rotated frame.
+template <typename T> struct RotCoef;
+template <> struct RotCoef<float> {
+    float2 cc, ss, ns;   // (c, c), (s, s), (-s, -s)
+    __device__ __forceinline__ RotCoef(float c, float s)
+        : cc(make_float2(c, c)), ss(make_float2(s, s)), ns(make_float2(-s, -s)) {}
+};
+template <> struct RotCoef<double> {
+    double c, s;
+    __device__ __forceinline__ RotCoef(double c_, double s_) : c(c_), s(s_) {}
+};
+
+// exp(-i beta X) on the pair (a, b) = (psi~[z], psi~[z | 2^q]) in the rotated frame.
+__device__ __forceinline__ void butterfly(float2& a, float2& b, const RotCoef<float>& k) {
+    const float2 t = mul2(b, k.ns);    // -s b
+    const float2 u = mul2(a, k.ss);    //  s a
+    a = fma2(a, k.cc, t);
+    b = fma2(b, k.cc, u);
+}
+__device__ __forceinline__ void butterfly(double2& a, double2& b, const RotCoef<double>& k) {
+    const double2 a0 = a, b0 = b;
+    a.x = k.c * a0.x - k.s * b0.x;
+    a.y = k.c * a0.y - k.s * b0.y;
+    b.x = k.s * a0.x + k.c * b0.x;
+    b.y = k.s * a0.y + k.c * b0.y;
+}
+
+// Multiply by i^m (m mod 4): the frame change of an amplitude with m set bits.
+template <typename C>
+__device__ __forceinline__ C times_i_pow(C v, int m) {
+    C r;
+    switch (m & 3) {
+        case 0: r = v; break;
+        case 1: r.x = -v.y; r.y = v.x; break;      //  i (x + iy)
+        case 2: r.x = -v.x; r.y = -v.y; break;
+        default: r.x = v.y; r.y = -v.x; break;     // -i (x + iy)
+    }
+    return r;
+}
+
+// Im(conj(x) * y) and Re(conj(x) * y)
 template <typename C>
 __device__ __forceinline__ auto im_conj_mul(const C& x, const C& y) -> decltype(x.x) {
     return x.x * y.y - x.y * y.x;
+}
+template <typename C>
+__device__ __forceinline__ auto re_conj_mul(const C& x, const C& y) -> decltype(x.x) {
+    return x.x * y.x + x.y * y.y;
 }
 
 // ---- warp reductions (fixed order: deterministic) ----------------------------------------

@@ -87,24 +87,27 @@ __device__ __forceinline__ uint32_t group_base(uint32_t g, int a) {
     return low | (high << (a + R));
 }
 
-// Mixer of one layer on the masked window bits of a register group.
+// Mixer of one layer on the masked window bits of a register group (rotated frame).
 template <int R, typename C, typename T>
 __device__ __forceinline__ void mix_group(C (&v)[1 << R], int mask, T c, T s) {
+    const RotCoef<T> k(c, s);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         if (mask & (1 << j)) {
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i)
-                if (!(i & (1 << j))) butterfly(v[i], v[i | (1 << j)], c, s);
+                if (!(i & (1 << j))) butterfly(v[i], v[i | (1 << j)], k);
         }
     }
 }
 
 // Mixer inverse on two states with the accumulation of Im <lam| X_q |psi> over the masked
-// qubits (any point of the layer's mixer gives the same value: X_q commutes with every
-// exp(-i beta X_q')).
+// qubits. Any point of the layer's mixer gives the same value (X_q commutes with every
+// exp(-i beta X_q')). In the rotated frame X_q becomes Y_q, so over the pairs (a, b)
+//   Im <lam|X_q|psi> = sum Re(conj(lam~_b) psi~_a) - Re(conj(lam~_a) psi~_b).
 template <int R, typename C, typename T>
 __device__ __forceinline__ T mix_group_adj(C (&v)[1 << R], C (&u)[1 << R], int mask, T c, T s) {
+    const RotCoef<T> k(c, -s);
     T acc = T(0);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -112,10 +115,10 @@ __device__ __forceinline__ T mix_group_adj(C (&v)[1 << R], C (&u)[1 << R], int m
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i)
                 if (!(i & (1 << j))) {
-                    const int k = i | (1 << j);
-                    acc += im_conj_mul(u[i], v[k]) + im_conj_mul(u[k], v[i]);
-                    butterfly(v[i], v[k], c, -s);
-                    butterfly(u[i], u[k], c, -s);
+                    const int b = i | (1 << j);
+                    acc += re_conj_mul(u[b], v[i]) - re_conj_mul(u[i], v[b]);
+                    butterfly(v[i], v[b], k);
+                    butterfly(u[i], u[b], k);
                 }
         }
     }
@@ -180,7 +183,7 @@ struct TileRef {
 // Forward sub-pass with a compile-time window start A (see subpass_fwd).
 template <typename T, int R, int A, typename Fin>
 __device__ __forceinline__ void subpass_fwd_a(const TileRef<T>& t, const SubPass& sp,
-                                              const LayerConst<T>* lc, bool init, T amp0,
+                                              const LayerConst<T>* lc, bool init, T amp0, int pc0,
                                               Fin&& fin) {
     using C = typename Num<T>::C;
     const uint32_t ngroups = 1u << (t.tb - R);
@@ -192,8 +195,13 @@ __device__ __forceinline__ void subpass_fwd_a(const TileRef<T>& t, const SubPass
         C v[1 << R];
         if (valid) {
             if (init) {
+                // |+> in the rotated frame: amp0 i^{|z|}, |z| = pc0 + |base| + |i|
+                const int pb = pc0 + __popc(base);
+                C a;
+                a.x = amp0;
+                a.y = T(0);
 #pragma unroll
-                for (int i = 0; i < (1 << R); ++i) { v[i].x = amp0; v[i].y = T(0); }
+                for (int i = 0; i < (1 << R); ++i) v[i] = times_i_pow(a, pb + __popc(i));
             } else {
                 load_group<R, A>(t.psi, sb, v);
             }
@@ -216,7 +224,8 @@ __device__ __forceinline__ void subpass_fwd_a(const TileRef<T>& t, const SubPass
 }
 
 // Forward sub-pass over all groups of the tile.
-//   init:  amplitudes start at amp0 instead of being read (|+> state)
+//   init:  amplitudes start as |+> (amp0 i^{|z|} in the rotated frame; pc0 = number of set
+//          global bits that the tile index itself fixes) instead of being read
 //   fin:   called once per group slot after the group has been written back, by every thread
 //          of the block (warp-uniform trip count), as fin(base, a, valid); it re-reads the
 //          group from shared memory, which keeps the final reductions out of the register
@@ -224,19 +233,19 @@ __device__ __forceinline__ void subpass_fwd_a(const TileRef<T>& t, const SubPass
 // The window start is dispatched to a compile-time constant (0 <= a <= tb - R <= 9).
 template <typename T, int R, typename Fin>
 __device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& sp,
-                                            const LayerConst<T>* lc, bool init, T amp0,
+                                            const LayerConst<T>* lc, bool init, T amp0, int pc0,
                                             Fin&& fin) {
     switch (sp.a) {
-        case 0: subpass_fwd_a<T, R, 0>(t, sp, lc, init, amp0, fin); break;
-        case 1: subpass_fwd_a<T, R, 1>(t, sp, lc, init, amp0, fin); break;
-        case 2: subpass_fwd_a<T, R, 2>(t, sp, lc, init, amp0, fin); break;
-        case 3: subpass_fwd_a<T, R, 3>(t, sp, lc, init, amp0, fin); break;
-        case 4: subpass_fwd_a<T, R, 4>(t, sp, lc, init, amp0, fin); break;
-        case 5: subpass_fwd_a<T, R, 5>(t, sp, lc, init, amp0, fin); break;
-        case 6: subpass_fwd_a<T, R, 6>(t, sp, lc, init, amp0, fin); break;
-        case 7: subpass_fwd_a<T, R, 7>(t, sp, lc, init, amp0, fin); break;
-        case 8: subpass_fwd_a<T, R, 8>(t, sp, lc, init, amp0, fin); break;
-        default: subpass_fwd_a<T, R, 9>(t, sp, lc, init, amp0, fin); break;
+        case 0: subpass_fwd_a<T, R, 0>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 1: subpass_fwd_a<T, R, 1>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 2: subpass_fwd_a<T, R, 2>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 3: subpass_fwd_a<T, R, 3>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 4: subpass_fwd_a<T, R, 4>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 5: subpass_fwd_a<T, R, 5>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 6: subpass_fwd_a<T, R, 6>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 7: subpass_fwd_a<T, R, 7>(t, sp, lc, init, amp0, pc0, fin); break;
+        case 8: subpass_fwd_a<T, R, 8>(t, sp, lc, init, amp0, pc0, fin); break;
+        default: subpass_fwd_a<T, R, 9>(t, sp, lc, init, amp0, pc0, fin); break;
     }
 }
 
