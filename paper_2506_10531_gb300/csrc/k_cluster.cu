@@ -24,59 +24,15 @@ namespace qaoa {
 
 namespace {
 
-constexpr int MAXH = 8;
-
-// Energies of the slice z = (r << L) | u, u < 2^L: thread t fixes the low m bits of u, walks
-// the bits [m, L) in Gray-code order (see the resident tier); the global bits r are fixed.
-__device__ void build_energy_slice(int n, int L, uint32_t r, const float* Qs, float* E) {
-    int m = 31 - __clz((int)blockDim.x);
-    if (m > L) m = L;
-    const int nh = L - m;
-    const uint32_t t = threadIdx.x;
-    if (t >= (1u << m)) return;
-    const uint32_t z0 = t | (r << L);
-    float e = 0.0f;
-    for (uint32_t bi = z0; bi; bi &= bi - 1u) {         // set bits i of z0
-        const float* row = Qs + (__ffs((int)bi) - 1) * n;
-        for (uint32_t bj = z0; bj; bj &= bj - 1u) e += row[__ffs((int)bj) - 1];
-    }
-    float F[MAXH];
-#pragma unroll
-    for (int h = 0; h < MAXH; ++h) {
-        float f = 0.0f;
-        if (h < nh)
-            for (uint32_t bj = z0; bj; bj &= bj - 1u) f += Qs[(m + h) * n + (__ffs((int)bj) - 1)];
-        F[h] = f;
-    }
-    uint32_t u = t;
-    E[swz<float>(u)] = e;
-    const uint32_t steps = 1u << nh;
-    for (uint32_t k = 1; k < steps; ++k) {
-        const int b = __ffs((int)k) - 1;
-        const int hb = m + b;
-        const float d = ((u >> hb) & 1u) ? -1.0f : 1.0f;
-        float fb = 0.0f;
-#pragma unroll
-        for (int h = 0; h < MAXH; ++h)
-            if (h == b) fb = F[h];
-        e += d * (Qs[hb * n + hb] + 2.0f * fb);
-        u ^= 1u << hb;
-#pragma unroll
-        for (int h = 0; h < MAXH; ++h)
-            if (h < nh && h != b) F[h] += d * Qs[(m + h) * n + hb];
-        E[swz<float>(u)] = e;
-    }
-}
-
 struct ClusterSmem {
     float2* psi;
     float* E;
     float* Q;
     LayerConst<float>* lc;
     double* red;     // 32
-    TopEnt* top;     // (blockDim/32) * 32
     double* cex;     // this CTA's <C> partial
-    TopEnt* ctop;    // this CTA's top-k list (16)
+    TileTopk tk;     // top-k scratch; tk.out is this CTA's list (read by rank 0)
+    float* escr;     // energy-build tables
 };
 
 __host__ __device__ inline size_t cl_align(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -92,9 +48,12 @@ __host__ __device__ inline size_t cluster_layout(int n, int L, int p, int thread
     off[2] = o; o = cl_align(o + (size_t)n * n * sizeof(float));
     off[3] = o; o = cl_align(o + (size_t)p * sizeof(LayerConst<float>));
     off[4] = o; o = cl_align(o + 32 * sizeof(double));
-    off[5] = o; o = cl_align(o + (size_t)(threads / 32) * 32 * sizeof(TopEnt));
+    off[5] = o; o = cl_align(o + (size_t)((threads + 31) / 32) * 32 * sizeof(TopEnt));
     off[6] = o; o = cl_align(o + sizeof(double));
     off[7] = o; o = cl_align(o + 16 * sizeof(TopEnt));
+    off[8] = o; o = cl_align(o + TOPK_CAP * sizeof(TopEnt));
+    off[9] = o; o = cl_align(o + 32 * sizeof(float) + 2 * sizeof(int));
+    off[10] = o; o = cl_align(o + (((size_t)1 << (L / 2)) + ((size_t)1 << (L - L / 2)) + 1) * sizeof(float));
     return o;
 }
 
@@ -140,7 +99,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     constexpr int R = Num<float>::RB;
     const uint32_t r = cl.block_rank();
     const int n = d.n, p = d.p;
-    size_t off[8];
+    size_t off[11];
     cluster_layout(n, L, p, blockDim.x, off);
     ClusterSmem s;
     s.psi = reinterpret_cast<float2*>(sm + off[0]);
@@ -148,9 +107,13 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     s.Q = reinterpret_cast<float*>(sm + off[2]);
     s.lc = reinterpret_cast<LayerConst<float>*>(sm + off[3]);
     s.red = reinterpret_cast<double*>(sm + off[4]);
-    s.top = reinterpret_cast<TopEnt*>(sm + off[5]);
+    s.tk.wlists = reinterpret_cast<TopEnt*>(sm + off[5]);
     s.cex = reinterpret_cast<double*>(sm + off[6]);
-    s.ctop = reinterpret_cast<TopEnt*>(sm + off[7]);
+    s.tk.out = reinterpret_cast<TopEnt*>(sm + off[7]);
+    s.tk.cand = reinterpret_cast<TopEnt*>(sm + off[8]);
+    s.tk.wb = reinterpret_cast<float*>(sm + off[9]);
+    s.tk.cnt = reinterpret_cast<int*>(sm + off[9] + 32 * sizeof(float));
+    s.escr = reinterpret_cast<float*>(sm + off[10]);
     const uint32_t D = 1u << L;
 
     for (int l = threadIdx.x; l < p; l += blockDim.x) {
@@ -160,7 +123,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     }
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
     __syncthreads();
-    build_energy_slice(n, L, r, s.Q, s.E);
+    build_tile_energy<float>(n, L, r << L, s.Q, s.E, s.escr);
     __syncthreads();
     if (d.E_out)
         for (uint32_t u = threadIdx.x; u < D; u += blockDim.x) d.E_out[(r << L) | u] = s.E[swz<float>(u)];
@@ -169,11 +132,8 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     const TileRef<float> tile{s.psi, nullptr, s.E, L};
     const int G = num_windows(0, L, R);
     const int S = snake_len(G, p);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpTopK top;
-    top.init(d.k > 0 ? d.k : 1);
-    double ex = 0.0;
     const float amp0 = (float)exp2(-0.5 * (double)n);
+    auto nofin = [](uint32_t, int, bool) {};
     for (int si = 0; si < S; ++si) {
         SubPass sp;
         snake_step(si, G, p, 0, 1, 0, L, L, R, sp);
@@ -186,32 +146,14 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
             global_subpass<CB>(cl, s, L, r, s.lc[sp.la]);
             cl.sync();
         }
-        const bool last = (si == S - 1);
-        auto fin = [&](uint32_t base, int a, bool valid) {
-            if (last)
-                reduce_group<float, R>(tile, base, a, valid, d.k, top, ex,
-                                       [&](uint32_t u) { return (r << L) | u; });
-        };
-        subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, __popc(r), fin);
+        subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, __popc(r), nofin);
         __syncthreads();
     }
-    // ---- per-CTA reductions, then rank 0 merges the CTAs in rank order ----
+    // ---- per-CTA reductions, then rank 0 merges the CTAs (rank order for <C>) ----
+    double ex = 0.0;
+    tile_reduce<float>(tile, d.k, [&](uint32_t u) { return (r << L) | u; }, s.tk, ex);
     const double tot = block_sum(ex, s.red);
     if (threadIdx.x == 0) *s.cex = tot;
-    if (d.k > 0) {
-        if (lane < d.k) s.top[warp * 32 + lane] = TopEnt{top.p, top.z};
-        __syncthreads();
-        if (warp == 0) {
-            WarpTopK f;
-            f.init(d.k);
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                const bool ok = lane < d.k;
-                const TopEnt e = ok ? s.top[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
-                f.offer_exact(e.p, e.z, ok);
-            }
-            if (lane < d.k) s.ctop[lane] = TopEnt{f.p, f.z};
-        }
-    }
     if (d.psi_out) {              // back from the rotated frame: psi = (-i)^{|z|} psi~
         float2* pout = reinterpret_cast<float2*>(d.psi_out) + ((size_t)r << L);
         const int pr = __popc(r);
@@ -226,22 +168,24 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
             for (int j = 0; j < C; ++j) acc += *cl.map_shared_rank(s.cex, j);
             *d.expect = acc;
         }
-        if (d.k > 0 && warp == 0) {
-            WarpTopK f;
-            f.init(d.k);
-            for (int j = 0; j < C; ++j) {
-                const TopEnt* rt = cl.map_shared_rank(s.ctop, j);
-                const bool ok = lane < d.k;
-                const TopEnt e = ok ? rt[lane] : TopEnt{-1.0, 0xffffffffu};
-                f.offer_exact(e.p, e.z, ok);
-            }
-            if (lane < d.k) {
-                if (d.topk_idx) d.topk_idx[lane] = (uint64_t)f.z;
-                if (d.topk_prob) d.topk_prob[lane] = f.p;
-            }
+        if (d.k > 0) {
+            // gather the C lists (k entries each) into the candidate buffer, rank-select
+            for (int e = threadIdx.x; e < C * d.k; e += blockDim.x)
+                s.tk.cand[e] = cl.map_shared_rank(s.tk.out, e / d.k)[e % d.k];
         }
     }
-    cl.sync();   // the next instance reuses the shared memory rank 0 has been reading
+    cl.sync();   // the lists of ranks != 0 have been read; rank 0 may overwrite its own
+    if (r == 0 && d.k > 0) {
+        constexpr int C = 1 << CB;
+        rank_select(s.tk.cand, C * d.k, d.k, s.tk.out);
+        __syncthreads();
+        if (threadIdx.x < (unsigned)d.k) {
+            const TopEnt e = s.tk.out[threadIdx.x];
+            if (d.topk_idx) d.topk_idx[threadIdx.x] = (uint64_t)e.z;
+            if (d.topk_prob) d.topk_prob[threadIdx.x] = e.p;
+        }
+    }
+    cl.sync();   // the next instance reuses the shared memory
 }
 
 // Clusters walk the descriptors round-robin: cluster c takes c, c + #clusters, ...
@@ -263,7 +207,7 @@ template <int CB>
 cudaError_t launch_cb(const void* desc, int count, int n, int L, int pmax, int clusters,
                       cudaStream_t st, int* max_clusters) {
     const int threads = cluster_threads(L);
-    size_t off[8];
+    size_t off[11];
     const size_t sm = cluster_layout(n, L, pmax, threads, off);
     cudaError_t e = cudaFuncSetAttribute(k_cluster<CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -298,7 +242,7 @@ cudaError_t launch_cb(const void* desc, int count, int n, int L, int pmax, int c
 }  // namespace
 
 size_t cluster_smem_bytes(int n, int L, int p) {
-    size_t off[8];
+    size_t off[11];
     return cluster_layout(n, L, p, cluster_threads(L), off);
 }
 

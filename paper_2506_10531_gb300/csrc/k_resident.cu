@@ -16,53 +16,6 @@ namespace qaoa {
 
 namespace {
 
-constexpr int MAXH = 8;   // high bits walked by the Gray code per thread
-
-// E(z) = z^T Q z for all z of an n-bit tile. Thread t (blockDim a power of two, 2^m threads
-// used) fixes the low m bits to t, evaluates E directly there, then walks the remaining
-// n - m bits in Gray-code order: flipping bit b with direction d = +1 (0 -> 1) or -1 changes
-// E by d (Q_bb + 2 F_b) with F_b = sum_{j != b} Q_bj z_j, and F of every other walked bit
-// changes by d Q_{hb}. At most 2^MAXH steps per thread, so the FP32 drift stays small.
-template <typename T>
-__device__ void build_energy(int n, const T* Qs, T* E) {
-    int m = 31 - __clz((int)blockDim.x);
-    if (m > n) m = n;
-    const int nh = n - m;
-    const uint32_t t = threadIdx.x;
-    if (t >= (1u << m)) return;
-    T e = T(0);
-    for (uint32_t bi = t; bi; bi &= bi - 1u) {          // set bits i of t
-        const T* row = Qs + (__ffs((int)bi) - 1) * n;
-        for (uint32_t bj = t; bj; bj &= bj - 1u) e += row[__ffs((int)bj) - 1];
-    }
-    T F[MAXH];
-#pragma unroll
-    for (int h = 0; h < MAXH; ++h) {
-        T f = T(0);
-        if (h < nh)
-            for (uint32_t bj = t; bj; bj &= bj - 1u) f += Qs[(m + h) * n + (__ffs((int)bj) - 1)];
-        F[h] = f;
-    }
-    uint32_t z = t;
-    E[swz<T>(z)] = e;
-    const uint32_t steps = 1u << nh;
-    for (uint32_t k = 1; k < steps; ++k) {
-        const int b = __ffs((int)k) - 1;
-        const int hb = m + b;
-        const T d = ((z >> hb) & 1u) ? T(-1) : T(1);
-        T fb = T(0);
-#pragma unroll
-        for (int h = 0; h < MAXH; ++h)
-            if (h == b) fb = F[h];
-        e += d * (Qs[hb * n + hb] + T(2) * fb);
-        z ^= 1u << hb;
-#pragma unroll
-        for (int h = 0; h < MAXH; ++h)
-            if (h < nh && h != b) F[h] += d * Qs[(m + h) * n + hb];
-        E[swz<T>(z)] = e;
-    }
-}
-
 template <typename T>
 struct Smem {
     typename Num<T>::C* psi;
@@ -72,7 +25,8 @@ struct Smem {
     LayerConst<T>* lc;
     double* red;       // 32 doubles
     double* acc;       // 2 p doubles: d gamma, d beta accumulators
-    TopEnt* top;       // (blockDim/32) * 32 entries
+    TileTopk tk;       // top-k scratch
+    T* escr;           // energy-build tables
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -89,7 +43,12 @@ __host__ __device__ inline size_t smem_layout(int n, int p, bool grad, int threa
     off[4] = o; o = align_up(o + (size_t)p * sizeof(LayerConst<T>), 16);   // layer consts
     off[5] = o; o = align_up(o + 32 * sizeof(double), 16);                 // reduction
     off[6] = o; o = align_up(o + 2 * (size_t)p * sizeof(double), 16);      // grad accum
-    off[7] = o; o = align_up(o + (size_t)(threads / 32) * 32 * sizeof(TopEnt), 16);  // top-k
+    const size_t nw = (size_t)(threads + 31) / 32;
+    off[7] = o; o = align_up(o + nw * 32 * sizeof(TopEnt), 16);          // fallback lists
+    off[8] = o; o = align_up(o + TOPK_CAP * sizeof(TopEnt), 16);         // candidates
+    off[9] = o; o = align_up(o + 16 * sizeof(TopEnt), 16);               // tile top-k
+    off[10] = o; o = align_up(o + 32 * sizeof(float) + 2 * sizeof(int), 16);  // bounds, counts
+    off[11] = o; o = align_up(o + (((size_t)1 << (n / 2)) + ((size_t)1 << (n - n / 2)) + 1) * sizeof(T), 16);
     return o;
 }
 
@@ -101,42 +60,23 @@ __device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s) {
     const T amp0 = (T)exp2(-0.5 * (double)n);
     const int G = num_windows(0, n, R);
     const int S = snake_len(G, p);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpTopK top;
-    top.init(d.k > 0 ? d.k : 1);
-    double ex = 0.0;
+    auto nofin = [](uint32_t, int, bool) {};
     for (int si = 0; si < S; ++si) {
         SubPass sp;
         snake_step(si, G, p, 0, 1, 0, n, n, R, sp);
-        const bool last = (si == S - 1);
-        auto fin = [&](uint32_t base, int a, bool valid) {
-            if (last) reduce_group<T, R>(tile, base, a, valid, d.k, top, ex, [](uint32_t u) { return u; });
-        };
-        subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, 0, fin);
+        subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, 0, nofin);
         __syncthreads();
     }
-    // <C>
+    // <C> and the top-k list of the final state (the list is unique under (probability desc,
+    // index asc), whatever the order of the reduction)
+    double ex = 0.0;
+    tile_reduce<T>(tile, d.k, [](uint32_t u) { return u; }, s.tk, ex);
     const double tot = block_sum(ex, s.red);
     if (threadIdx.x == 0 && d.expect) *d.expect = tot;
-    // top-k: per-warp lists -> shared -> warp 0 merges (order of equal keys is irrelevant:
-    // the final list is unique under (probability desc, index asc))
-    if (d.k > 0) {
-        if (lane < d.k) s.top[warp * 32 + lane] = TopEnt{top.p, top.z};
-        __syncthreads();
-        if (warp == 0) {
-            WarpTopK fin;
-            fin.init(d.k);
-            const int nw = blockDim.x >> 5;
-            for (int w = 0; w < nw; ++w) {
-                const bool ok = lane < d.k;
-                const TopEnt e = ok ? s.top[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
-                fin.offer_exact(e.p, e.z, ok);
-            }
-            if (lane < d.k) {
-                if (d.topk_idx) d.topk_idx[lane] = (uint64_t)fin.z;
-                if (d.topk_prob) d.topk_prob[lane] = fin.p;
-            }
-        }
+    if (threadIdx.x < (unsigned)d.k) {
+        const TopEnt e = s.tk.out[threadIdx.x];
+        if (d.topk_idx) d.topk_idx[threadIdx.x] = (uint64_t)e.z;
+        if (d.topk_prob) d.topk_prob[threadIdx.x] = e.p;
     }
     __syncthreads();
 }
@@ -178,7 +118,7 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     using C = typename Num<T>::C;
     const int n = d.n, p = d.p;
     const bool grad = (d.flags & F_GRAD) != 0;
-    size_t off[8];
+    size_t off[12];
     smem_layout<T>(n, p, grad, blockDim.x, off);
     Smem<T> s;
     s.psi = reinterpret_cast<C*>(sm + off[0]);
@@ -188,7 +128,12 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     s.lc = reinterpret_cast<LayerConst<T>*>(sm + off[4]);
     s.red = reinterpret_cast<double*>(sm + off[5]);
     s.acc = reinterpret_cast<double*>(sm + off[6]);
-    s.top = reinterpret_cast<TopEnt*>(sm + off[7]);
+    s.tk.wlists = reinterpret_cast<TopEnt*>(sm + off[7]);
+    s.tk.cand = reinterpret_cast<TopEnt*>(sm + off[8]);
+    s.tk.out = reinterpret_cast<TopEnt*>(sm + off[9]);
+    s.tk.wb = reinterpret_cast<float*>(sm + off[10]);
+    s.tk.cnt = reinterpret_cast<int*>(sm + off[10] + 32 * sizeof(float));
+    s.escr = reinterpret_cast<T*>(sm + off[11]);
     const uint32_t D = 1u << n;
 
     for (int l = threadIdx.x; l < p; l += blockDim.x) {
@@ -200,7 +145,7 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     if (d.Q) {
         for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
         __syncthreads();
-        build_energy<T>(n, s.Q, s.E);
+        build_tile_energy<T>(n, n, 0u, s.Q, s.E, s.escr);
     } else {
         for (uint32_t z = threadIdx.x; z < D; z += blockDim.x) s.E[swz<T>(z)] = d.E_in[z];
     }
@@ -267,7 +212,7 @@ int resident_threads(bool dbl, int n) {
 }
 
 size_t resident_smem_bytes(bool dbl, int n, int p, bool grad) {
-    size_t off[8];
+    size_t off[12];
     const int th = resident_threads(dbl, n);
     return dbl ? smem_layout<double>(n, p, grad, th, off) : smem_layout<float>(n, p, grad, th, off);
 }

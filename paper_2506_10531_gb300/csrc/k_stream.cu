@@ -36,7 +36,7 @@ struct StreamSmem {
     T* E;
     LayerConst<T>* lc;
     double* red;
-    TopEnt* top;
+    TileTopk tk;
 };
 
 template <typename T, int R>
@@ -66,21 +66,12 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     const int G = num_windows(m0, P.tb, R);
     const int nl = P.lb - P.la + 1;
     const int S = snake_len(G, nl);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpTopK top;
-    top.init(P.k > 0 ? P.k : 1);
-    double ex = 0.0;
     const T amp0 = (T)I.amp0;
+    auto nofin = [](uint32_t, int, bool) {};
     for (int si = 0; si < S; ++si) {
         SubPass sp;
         snake_step(si, G, nl, P.la, P.ph_first, m0, P.tb, P.tb, R, sp);
-        const bool last = P.fin && (si == S - 1);
-        auto fin = [&](uint32_t base, int a, bool valid) {
-            if (last)
-                reduce_group<T, R>(tile, base, a, valid, P.k, top, ex,
-                                   [&](uint32_t u) { return (uint32_t)global_index(P, tau, u); });
-        };
-        subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, __popcll(tau), fin);
+        subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, __popcll(tau), nofin);
         __syncthreads();
     }
     // ---- shared -> HBM (16-byte accesses on both sides). Between passes the state stays in
@@ -97,24 +88,14 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
             gpsi[global_index(P, tau, u)] = times_i_pow(s.psi[swz<T>(u)], -(pt + __popc(u)));
     }
     if (P.fin) {
+        double ex = 0.0;
+        tile_reduce<T>(tile, P.k, [&](uint32_t u) { return (uint32_t)global_index(P, tau, u); }, s.tk, ex);
         const double tot = block_sum(ex, s.red);
         if (threadIdx.x == 0) I.part_expect[tau] = tot;
-        if (P.k > 0) {
-            if (lane < P.k) s.top[warp * 32 + lane] = TopEnt{top.p, top.z};
-            __syncthreads();
-            if (warp == 0) {
-                WarpTopK f;
-                f.init(P.k);
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                    const bool ok = lane < P.k;
-                    const TopEnt e = ok ? s.top[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
-                    f.offer_exact(e.p, e.z, ok);
-                }
-                if (lane < P.k) {
-                    I.part_topp[tau * P.k + lane] = f.p;
-                    I.part_topz[tau * P.k + lane] = f.z;
-                }
-            }
+        if (threadIdx.x < (unsigned)P.k) {
+            const TopEnt e = s.tk.out[threadIdx.x];
+            I.part_topp[tau * P.k + threadIdx.x] = e.p;
+            I.part_topz[tau * P.k + threadIdx.x] = e.z;
         }
     }
     __syncthreads();
@@ -134,7 +115,11 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
     s.lc = reinterpret_cast<LayerConst<T>*>(sm + o); o += 64 * sizeof(LayerConst<T>);
     o = (o + 15) & ~(size_t)15;
     s.red = reinterpret_cast<double*>(sm + o); o += 32 * sizeof(double);
-    s.top = reinterpret_cast<TopEnt*>(sm + o);
+    s.tk.wlists = reinterpret_cast<TopEnt*>(sm + o); o += 8 * 32 * sizeof(TopEnt);
+    s.tk.cand = reinterpret_cast<TopEnt*>(sm + o); o += TOPK_CAP * sizeof(TopEnt);
+    s.tk.out = reinterpret_cast<TopEnt*>(sm + o); o += 16 * sizeof(TopEnt);
+    s.tk.wb = reinterpret_cast<float*>(sm + o); o += 32 * sizeof(float);
+    s.tk.cnt = reinterpret_cast<int*>(sm + o);
     const uint64_t ntiles = 1ull << (P.n - P.tb);
     const uint64_t total = ntiles * (uint64_t)count;
     int cur = -1;
@@ -413,7 +398,8 @@ size_t stream_smem_bytes(bool dbl) {
     const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4, lcs = dbl ? 24 : 12;
     size_t o = TD * c + TD * r + 64 * lcs;
     o = (o + 15) & ~(size_t)15;
-    return o + 32 * sizeof(double) + 8 * 32 * sizeof(TopEnt);
+    return o + 32 * sizeof(double) + (8 * 32 + TOPK_CAP + 16) * sizeof(TopEnt) + 32 * sizeof(float) +
+           2 * sizeof(int);
 }
 
 template <typename T>

@@ -354,6 +354,230 @@ __device__ __forceinline__ void reduce_group(const TileRef<T>& t, uint32_t base,
     }
 }
 
+// ---- energies of a tile -----------------------------------------------------------------
+// E(z) = z^T Q z for the 2^L tile indices u of one n-qubit instance, z = zfix | u (zfix holds
+// global bits >= L that the tile fixes, e.g. the CTA rank of a cluster). With u = (hi, lo),
+// lo = the low B bits, and S = the set bits of zfix:
+//   E(z) = E_S + El[lo] + Eh[hi] + X(lo, hi),
+//   El[lo] = sum_{i,j in lo} Q_ij + sum_{i in lo, j in S} (Q_ij + Q_ji),  Eh likewise for hi,
+//   X(lo, hi) = sum_{i in lo, j in hi} (Q_ij + Q_ji)  (linear in the hi bits for fixed lo).
+// El and Eh are small shared tables (2^B and 2^(L-B) entries); each thread fixes lo and the
+// top hi bits and walks the remaining hi bits in Gray-code order, where flipping bit j changes
+// X by +-W_j(lo), W_j = sum_{i in lo} (Q_ij + Q_ji) held in registers. Every E is the sum of
+// at most three table terms plus X (at most 2^5 increments), all in the tile's real type.
+// scratch: 2^B + 2^(L-B) + 1 values of T. Contains __syncthreads (all threads call).
+constexpr int EW_MAX = 6;   // walked bits per thread
+template <typename T>
+__device__ __forceinline__ void build_tile_energy(int n, int L, uint32_t zfix, const T* Qs, T* E,
+                                                  T* scratch) {
+    const int B = L / 2, H = L - B;
+    const uint32_t NL = 1u << B, NH = 1u << H;
+    T* El = scratch;
+    T* Eh = scratch + NL;
+    T* Es = scratch + NL + NH;
+    // pair weight of bits i, j (i != j): Q_ij + Q_ji; a set bit i alone: Q_ii
+    for (uint32_t x = threadIdx.x; x < NL + NH + 1; x += blockDim.x) {
+        T acc = T(0);
+        if (x == NL + NH) {                       // E_S
+            for (uint32_t bi = zfix; bi; bi &= bi - 1u) {
+                const int i = __ffs((int)bi) - 1;
+                for (uint32_t bj = zfix; bj; bj &= bj - 1u) acc += Qs[i * n + (__ffs((int)bj) - 1)];
+            }
+            Es[0] = acc;
+            continue;
+        }
+        const bool hi = x >= NL;
+        const uint32_t bits = hi ? ((x - NL) << B) : x;
+        for (uint32_t bi = bits; bi; bi &= bi - 1u) {
+            const int i = __ffs((int)bi) - 1;
+            for (uint32_t bj = bits; bj; bj &= bj - 1u) acc += Qs[i * n + (__ffs((int)bj) - 1)];
+            for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
+                const int j = __ffs((int)bj) - 1;
+                acc += Qs[i * n + j] + Qs[j * n + i];
+            }
+        }
+        (hi ? Eh[x - NL] : El[x]) = acc;
+    }
+    __syncthreads();
+    // combos (lo, top hi bits) per thread; the remaining hi bits are walked
+    uint32_t NC = blockDim.x < NL ? NL : blockDim.x;
+    if (NC > (1u << L)) NC = 1u << L;
+    while ((1u << L) / NC > (1u << EW_MAX)) NC <<= 1;     // keep the walk short
+    const int cb = 31 - __clz((int)NC);                   // log2(NC) >= B
+    const int hw = L - cb;                                // walked bits (top of hi: [cb, L))
+    const int hf = cb - B;                                // fixed hi bits [B, cb)
+    for (uint32_t c = threadIdx.x; c < NC; c += blockDim.x) {
+        const uint32_t lo = c & (NL - 1u);
+        const uint32_t hfix = c >> B;                     // hf bits
+        T W[EW_MAX];
+#pragma unroll
+        for (int j = 0; j < EW_MAX; ++j) {
+            T w = T(0);
+            if (j < hw) {
+                const int qj = cb + j;
+                for (uint32_t bi = lo; bi; bi &= bi - 1u) {
+                    const int i = __ffs((int)bi) - 1;
+                    w += Qs[i * n + qj] + Qs[qj * n + i];
+                }
+            }
+            W[j] = w;
+        }
+        T X = T(0);   // cross term of lo with the fixed hi bits
+        for (uint32_t bj = hfix; bj; bj &= bj - 1u) {
+            const int qj = B + __ffs((int)bj) - 1;
+            for (uint32_t bi = lo; bi; bi &= bi - 1u) {
+                const int i = __ffs((int)bi) - 1;
+                X += Qs[i * n + qj] + Qs[qj * n + i];
+            }
+        }
+        const T base = Es[0] + El[lo];
+        uint32_t hiv = hfix;                              // hi index (H bits)
+        E[swz<T>(lo | (hiv << B))] = base + Eh[hiv] + X;
+        const uint32_t steps = 1u << hw;
+        for (uint32_t k = 1; k < steps; ++k) {
+            const int b = __ffs((int)k) - 1;
+            const uint32_t bit = 1u << (hf + b);
+            T wb = T(0);
+#pragma unroll
+            for (int j = 0; j < EW_MAX; ++j)
+                if (j == b) wb = W[j];
+            X += (hiv & bit) ? -wb : wb;
+            hiv ^= bit;
+            E[swz<T>(lo | (hiv << B))] = base + Eh[hiv] + X;
+        }
+    }
+    (void)hf;
+}
+
+// ---- final reductions of a tile -----------------------------------------------------------
+// Shared scratch of tile_reduce (sizes: wb nwarps floats, cand TOPK_CAP entries, out 16).
+constexpr int TOPK_CAP = 256;
+struct TileTopk {
+    float* wb;        // per-warp lower bounds
+    TopEnt* cand;     // candidate buffer
+    TopEnt* out;      // the tile's top-k (valid after tile_reduce)
+    TopEnt* wlists;   // (blockDim/32) * 32 entries, used only by the fallback
+    int* cnt;         // [0] candidate count, [1] overflow flag
+};
+
+// <C> partial and top-k list of the whole tile, after the last sub-pass. Every thread reads
+// the elements u = tid + j*blockDim:
+//  1. FP32 |psi|^2 E over at most 32 elements per thread (FP64 above, in `ex`), and the
+//     thread's largest FP32 probability;
+//  2. a lower bound on the tile's k-th largest probability: within a warp the k lanes with
+//     the largest maxima hold k distinct elements at least that probable; the block takes
+//     the largest warp bound;
+//  3. every element whose FP32 probability can reach the bound (margins as in
+//     WarpTopK::offer) goes to a shared candidate buffer with its exact FP64 probability;
+//  4. each candidate's rank = number of candidates better than it (probability descending,
+//     index ascending: a strict total order, so ranks are distinct); ranks < k are the list.
+// The result does not depend on the order of the buffer, so the reduction is deterministic.
+// If more than TOPK_CAP elements qualify (near-uniform probabilities) the warps fall back to
+// sorted insertion lists merged by warp 0. zmap(u): global index of tile index u.
+template <typename T, typename ZMap>
+__device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& zmap,
+                                            const TileTopk& ts, double& ex) {
+    using C = typename Num<T>::C;
+    const uint32_t D = 1u << t.tb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    T accp = T(0);
+    int nacc = 0;
+    float pmax = -1.0f;
+    for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
+        const uint32_t u = u0 + threadIdx.x;
+        if (u < D) {
+            const uint32_t ix = swz<T>(u);
+            const C v = t.psi[ix];
+            const T pr = v.x * v.x + v.y * v.y;
+            accp += pr * t.E[ix];
+            pmax = fmaxf(pmax, (float)pr);
+            if (++nacc == 32) { ex += (double)accp; accp = T(0); nacc = 0; }
+        }
+    }
+    ex += (double)accp;
+    if (k <= 0) return;
+    const float wbound = warp_kth_largest(pmax, k);
+    if (lane == 0) ts.wb[warp] = wbound;
+    if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
+    __syncthreads();
+    float thr = -1.0f;
+    for (int w = 0; w < nw; ++w) thr = fmaxf(thr, ts.wb[w]);
+    const float thr_lo = thr > 0.0f ? thr * 0.99999904632568359375f : -1.0f;   // (1 - 2^-20)
+    for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
+        const uint32_t u = u0 + threadIdx.x;
+        C v;
+        v.x = T(0);
+        v.y = T(0);
+        if (u < D) v = t.psi[swz<T>(u)];
+        const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
+        const bool c = (u < D) && (pf * 1.00000095367431640625f >= thr_lo);
+        const uint32_t m = __ballot_sync(0xffffffffu, c);
+        if (m) {
+            int base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(&ts.cnt[0], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+            if (c) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{exact_prob(v), zmap(u)};
+                else ts.cnt[1] = 1;
+            }
+        }
+    }
+    __syncthreads();
+    const int cnt = min(ts.cnt[0], TOPK_CAP);
+    if (!ts.cnt[1]) {
+        for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+            const TopEnt me = ts.cand[c];
+            int rank = 0;
+            for (int j = 0; j < cnt; ++j) {
+                const TopEnt o = ts.cand[j];
+                rank += better(o.p, o.z, me.p, me.z) ? 1 : 0;
+            }
+            if (rank < k) ts.out[rank] = me;
+        }
+        if (threadIdx.x < (unsigned)k && threadIdx.x >= (unsigned)cnt) ts.out[threadIdx.x] = TopEnt{-1.0, 0xffffffffu};
+    } else {
+        WarpTopK top;
+        top.init(k);
+        for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
+            const uint32_t u = u0 + threadIdx.x;
+            C v;
+            v.x = T(0);
+            v.y = T(0);
+            if (u < D) v = t.psi[swz<T>(u)];
+            top.offer(v, zmap(u < D ? u : 0u), u < D);
+        }
+        if (lane < k) ts.wlists[warp * 32 + lane] = TopEnt{top.p, top.z};
+        __syncthreads();
+        if (warp == 0) {
+            WarpTopK f;
+            f.init(k);
+            for (int w = 0; w < nw; ++w) {
+                const bool ok = lane < k;
+                const TopEnt e = ok ? ts.wlists[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
+                f.offer_exact(e.p, e.z, ok);
+            }
+            if (lane < k) ts.out[lane] = TopEnt{f.p, f.z};
+        }
+    }
+    __syncthreads();
+}
+
+// Top-k of a small set of candidate lists already in shared memory (count entries, entries
+// with p < 0 are empty): rank selection as in tile_reduce; result in out[0..k).
+__device__ __forceinline__ void rank_select(const TopEnt* cand, int count, int k, TopEnt* out) {
+    for (int c = threadIdx.x; c < count; c += blockDim.x) {
+        const TopEnt me = cand[c];
+        if (me.p < 0.0) continue;
+        int rank = 0;
+        for (int j = 0; j < count; ++j) {
+            const TopEnt o = cand[j];
+            rank += (o.p >= 0.0 && better(o.p, o.z, me.p, me.z)) ? 1 : 0;
+        }
+        if (rank < k) out[rank] = me;
+    }
+}
+
 // Block-wide sum of one value per thread into slot[0] (thread 0 only); red has blockDim/32
 // doubles. Fixed order: deterministic. Must be called by all threads.
 __device__ __forceinline__ double block_sum(double v, double* red) {
