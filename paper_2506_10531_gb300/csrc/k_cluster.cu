@@ -52,7 +52,7 @@ __host__ __device__ inline size_t cluster_layout(int n, int L, int p, int thread
     off[6] = o; o = cl_align(o + sizeof(double));
     off[7] = o; o = cl_align(o + 16 * sizeof(TopEnt));
     off[8] = o; o = cl_align(o + TOPK_CAP * sizeof(TopEnt));
-    off[9] = o; o = cl_align(o + 32 * sizeof(float) + 2 * sizeof(int));
+    off[9] = o; o = cl_align(o + 16 * 32 * sizeof(float) + 4 * sizeof(int));
     off[10] = o; o = cl_align(o + (((size_t)1 << (L / 2)) + ((size_t)1 << (L - L / 2)) + 1) * sizeof(float));
     return o;
 }
@@ -112,7 +112,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     s.tk.out = reinterpret_cast<TopEnt*>(sm + off[7]);
     s.tk.cand = reinterpret_cast<TopEnt*>(sm + off[8]);
     s.tk.wb = reinterpret_cast<float*>(sm + off[9]);
-    s.tk.cnt = reinterpret_cast<int*>(sm + off[9] + 32 * sizeof(float));
+    s.tk.cnt = reinterpret_cast<int*>(sm + off[9] + 16 * 32 * sizeof(float));
     s.escr = reinterpret_cast<float*>(sm + off[10]);
     const uint32_t D = 1u << L;
 

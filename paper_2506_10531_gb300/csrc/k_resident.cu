@@ -47,7 +47,7 @@ __host__ __device__ inline size_t smem_layout(int n, int p, bool grad, int threa
     off[7] = o; o = align_up(o + nw * 32 * sizeof(TopEnt), 16);          // fallback lists
     off[8] = o; o = align_up(o + TOPK_CAP * sizeof(TopEnt), 16);         // candidates
     off[9] = o; o = align_up(o + 16 * sizeof(TopEnt), 16);               // tile top-k
-    off[10] = o; o = align_up(o + 32 * sizeof(float) + 2 * sizeof(int), 16);  // bounds, counts
+    off[10] = o; o = align_up(o + 16 * 32 * sizeof(float) + 4 * sizeof(int), 16);  // bounds, counts
     off[11] = o; o = align_up(o + (((size_t)1 << (n / 2)) + ((size_t)1 << (n - n / 2)) + 1) * sizeof(T), 16);
     return o;
 }
@@ -132,7 +132,7 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     s.tk.cand = reinterpret_cast<TopEnt*>(sm + off[8]);
     s.tk.out = reinterpret_cast<TopEnt*>(sm + off[9]);
     s.tk.wb = reinterpret_cast<float*>(sm + off[10]);
-    s.tk.cnt = reinterpret_cast<int*>(sm + off[10] + 32 * sizeof(float));
+    s.tk.cnt = reinterpret_cast<int*>(sm + off[10] + 16 * 32 * sizeof(float));
     s.escr = reinterpret_cast<T*>(sm + off[11]);
     const uint32_t D = 1u << n;
 

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
     s.tk.wlists = reinterpret_cast<TopEnt*>(sm + o); o += 8 * 32 * sizeof(TopEnt);
     s.tk.cand = reinterpret_cast<TopEnt*>(sm + o); o += TOPK_CAP * sizeof(TopEnt);
     s.tk.out = reinterpret_cast<TopEnt*>(sm + o); o += 16 * sizeof(TopEnt);
-    s.tk.wb = reinterpret_cast<float*>(sm + o); o += 32 * sizeof(float);
+    s.tk.wb = reinterpret_cast<float*>(sm + o); o += 16 * 32 * sizeof(float);
     s.tk.cnt = reinterpret_cast<int*>(sm + o);
     const uint64_t ntiles = 1ull << (P.n - P.tb);
     const uint64_t total = ntiles * (uint64_t)count;
@@ -398,8 +398,8 @@ size_t stream_smem_bytes(bool dbl) {
     const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4, lcs = dbl ? 24 : 12;
     size_t o = TD * c + TD * r + 64 * lcs;
     o = (o + 15) & ~(size_t)15;
-    return o + 32 * sizeof(double) + (8 * 32 + TOPK_CAP + 16) * sizeof(TopEnt) + 32 * sizeof(float) +
-           2 * sizeof(int);
+    return o + 32 * sizeof(double) + (8 * 32 + TOPK_CAP + 16) * sizeof(TopEnt) +
+           16 * 32 * sizeof(float) + 4 * sizeof(int);
 }
 
 template <typename T>

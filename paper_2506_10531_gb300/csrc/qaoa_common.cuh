@@ -152,8 +152,24 @@ __device__ __forceinline__ auto re_conj_mul(const C& x, const C& y) -> decltype(
 
 // ---- warp reductions (fixed order: deterministic) ----------------------------------------
 
-// The k-th largest (k = 1..32) of one float per lane: bitonic sort over the lanes into
-// descending order (lane l ends with the (l+1)-th largest value).
+// Bitonic sort of one float per lane into descending order: lane l ends with the (l+1)-th
+// largest value of the warp.
+__device__ __forceinline__ float warp_sort_desc(float v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+            const bool asc = (lane & size) == 0;
+            const bool lower = (lane & stride) == 0;
+            v = (lower != asc) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return v;
+}
+
+// The k-th largest (k = 1..32) of one float per lane.
 __device__ __forceinline__ float warp_kth_largest(float v, int k) {
     const int lane = threadIdx.x & 31;
 #pragma unroll

@@ -450,30 +450,71 @@ __device__ __forceinline__ void build_tile_energy(int n, int L, uint32_t zfix, c
 }
 
 // ---- final reductions of a tile -----------------------------------------------------------
-// Shared scratch of tile_reduce (sizes: wb nwarps floats, cand TOPK_CAP entries, out 16).
+// Shared scratch of tile_reduce (sizes: wb 16 * nwarps floats, cand TOPK_CAP entries, out 16,
+// wlists 32 * nwarps entries, cnt 4 ints).
 constexpr int TOPK_CAP = 256;
 struct TileTopk {
-    float* wb;        // per-warp lower bounds
+    float* wb;        // per-warp sorted lane maxima (k per warp)
     TopEnt* cand;     // candidate buffer
     TopEnt* out;      // the tile's top-k (valid after tile_reduce)
     TopEnt* wlists;   // (blockDim/32) * 32 entries, used only by the fallback
-    int* cnt;         // [0] candidate count, [1] overflow flag
+    int* cnt;         // [0] candidate count, [1] overflow flag, [2..3] bound (float / double bits)
 };
+
+// Collect the elements whose probability can reach `bound` (FP32 filter with the margins of
+// WarpTopK::offer; with exact != 0 the exact probability must also be >= *exact_bound) into
+// ts.cand. Sets ts.cnt[1] on overflow.
+template <typename T, typename ZMap>
+__device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float bound_lo,
+                                                   const double* exact_bound, ZMap&& zmap,
+                                                   const TileTopk& ts) {
+    using C = typename Num<T>::C;
+    const uint32_t D = 1u << t.tb;
+    const int lane = threadIdx.x & 31;
+    const double eb = exact_bound ? *exact_bound : -1.0;
+    for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
+        const uint32_t u = u0 + threadIdx.x;
+        C v;
+        v.x = T(0);
+        v.y = T(0);
+        if (u < D) v = t.psi[swz<T>(u)];
+        const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
+        bool c = (u < D) && (pf * 1.00000095367431640625f >= bound_lo);
+        double pe = 0.0;
+        if (c) {
+            pe = exact_prob(v);
+            c = pe >= eb;
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, c);
+        if (m) {
+            int base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(&ts.cnt[0], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+            if (c) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{pe, zmap(u)};
+                else ts.cnt[1] = 1;
+            }
+        }
+    }
+}
 
 // <C> partial and top-k list of the whole tile, after the last sub-pass. Every thread reads
 // the elements u = tid + j*blockDim:
 //  1. FP32 |psi|^2 E over at most 32 elements per thread (FP64 above, in `ex`), and the
-//     thread's largest FP32 probability;
-//  2. a lower bound on the tile's k-th largest probability: within a warp the k lanes with
-//     the largest maxima hold k distinct elements at least that probable; the block takes
-//     the largest warp bound;
-//  3. every element whose FP32 probability can reach the bound (margins as in
-//     WarpTopK::offer) goes to a shared candidate buffer with its exact FP64 probability;
+//     thread's largest FP32 probability (its lane maximum);
+//  2. a lower bound on the tile's k-th largest probability: the k-th largest of all lane
+//     maxima (k distinct elements are at least that probable). Each warp sorts its lane
+//     maxima and offers its k largest; their k-th largest is found by rank;
+//  3. every element whose probability can reach the bound goes to a shared candidate buffer
+//     with its exact FP64 probability; on overflow (flat distributions) the bound is raised
+//     to the k-th largest exact probability among the buffered elements and the collection
+//     repeated with an exact test;
 //  4. each candidate's rank = number of candidates better than it (probability descending,
 //     index ascending: a strict total order, so ranks are distinct); ranks < k are the list.
 // The result does not depend on the order of the buffer, so the reduction is deterministic.
-// If more than TOPK_CAP elements qualify (near-uniform probabilities) the warps fall back to
-// sorted insertion lists merged by warp 0. zmap(u): global index of tile index u.
+// If the buffer still overflows (massive ties) the warps fall back to sorted insertion lists
+// merged by warp 0. zmap(u): global index of tile index u. Called by all threads.
 template <typename T, typename ZMap>
 __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& zmap,
                                             const TileTopk& ts, double& ex) {
@@ -496,34 +537,47 @@ __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& z
     }
     ex += (double)accp;
     if (k <= 0) return;
-    const float wbound = warp_kth_largest(pmax, k);
-    if (lane == 0) ts.wb[warp] = wbound;
+    // (2) the k-th largest lane maximum of the block
+    const float srt = warp_sort_desc(pmax);
+    if (lane < k) ts.wb[warp * k + lane] = srt;
     if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
     __syncthreads();
-    float thr = -1.0f;
-    for (int w = 0; w < nw; ++w) thr = fmaxf(thr, ts.wb[w]);
-    const float thr_lo = thr > 0.0f ? thr * 0.99999904632568359375f : -1.0f;   // (1 - 2^-20)
-    for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
-        const uint32_t u = u0 + threadIdx.x;
-        C v;
-        v.x = T(0);
-        v.y = T(0);
-        if (u < D) v = t.psi[swz<T>(u)];
-        const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
-        const bool c = (u < D) && (pf * 1.00000095367431640625f >= thr_lo);
-        const uint32_t m = __ballot_sync(0xffffffffu, c);
-        if (m) {
-            int base = 0;
-            if (lane == __ffs(m) - 1) base = atomicAdd(&ts.cnt[0], __popc(m));
-            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-            if (c) {
-                const int pos = base + __popc(m & ((1u << lane) - 1u));
-                if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{exact_prob(v), zmap(u)};
-                else ts.cnt[1] = 1;
-            }
+    float* bound = reinterpret_cast<float*>(&ts.cnt[2]);
+    const int nl = nw * k;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+        const float me = ts.wb[i];
+        int rank = 0;
+        for (int j = 0; j < nl; ++j) {
+            const float o = ts.wb[j];
+            rank += (o > me || (o == me && j < i)) ? 1 : 0;
         }
+        if (rank == k - 1) *bound = me;
     }
     __syncthreads();
+    const float thr = *bound;
+    const float thr_lo = thr > 0.0f ? thr * 0.99999904632568359375f : -1.0f;   // (1 - 2^-20)
+    // (3) candidates
+    collect_candidates<T>(t, thr_lo, nullptr, zmap, ts);
+    __syncthreads();
+    if (ts.cnt[1]) {
+        // raise the bound to the k-th best buffered exact probability and collect again
+        double* b2 = reinterpret_cast<double*>(ts.wlists);
+        for (int c = threadIdx.x; c < TOPK_CAP; c += blockDim.x) {
+            const TopEnt me = ts.cand[c];
+            int rank = 0;
+            for (int j = 0; j < TOPK_CAP; ++j) {
+                const TopEnt o = ts.cand[j];
+                rank += better(o.p, o.z, me.p, me.z) ? 1 : 0;
+            }
+            if (rank == k - 1) *b2 = me.p;
+        }
+        __syncthreads();
+        const float b2lo = __double2float_rd(*b2) * 0.99999904632568359375f;
+        if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
+        __syncthreads();
+        collect_candidates<T>(t, b2lo, b2, zmap, ts);
+        __syncthreads();
+    }
     const int cnt = min(ts.cnt[0], TOPK_CAP);
     if (!ts.cnt[1]) {
         for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
@@ -537,6 +591,7 @@ __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& z
         }
         if (threadIdx.x < (unsigned)k && threadIdx.x >= (unsigned)cnt) ts.out[threadIdx.x] = TopEnt{-1.0, 0xffffffffu};
     } else {
+        __syncthreads();
         WarpTopK top;
         top.init(k);
         for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
