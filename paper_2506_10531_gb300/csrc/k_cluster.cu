@@ -48,12 +48,17 @@ __host__ __device__ inline size_t cluster_layout(int n, int L, int p, int thread
     off[2] = o; o = cl_align(o + (size_t)n * n * sizeof(float));
     off[3] = o; o = cl_align(o + (size_t)p * sizeof(LayerConst<float>));
     off[4] = o; o = cl_align(o + 32 * sizeof(double));
+    // top-k scratch (used after the last sub-pass) and energy tables (used before the first)
+    // share one region
+    const size_t r0 = o;
     off[5] = o; o = cl_align(o + (size_t)((threads + 31) / 32) * 32 * sizeof(TopEnt));
     off[6] = o; o = cl_align(o + sizeof(double));
     off[7] = o; o = cl_align(o + 16 * sizeof(TopEnt));
     off[8] = o; o = cl_align(o + TOPK_CAP * sizeof(TopEnt));
     off[9] = o; o = cl_align(o + 16 * 32 * sizeof(float) + 4 * sizeof(int));
-    off[10] = o; o = cl_align(o + (((size_t)1 << (L / 2)) + ((size_t)1 << (L - L / 2)) + 1) * sizeof(float));
+    off[10] = r0;
+    const size_t eend = cl_align(r0 + tile_energy_scratch(L) * sizeof(float));
+    if (eend > o) o = eend;
     return o;
 }
 

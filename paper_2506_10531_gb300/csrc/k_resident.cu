@@ -43,12 +43,17 @@ __host__ __device__ inline size_t smem_layout(int n, int p, bool grad, int threa
     off[4] = o; o = align_up(o + (size_t)p * sizeof(LayerConst<T>), 16);   // layer consts
     off[5] = o; o = align_up(o + 32 * sizeof(double), 16);                 // reduction
     off[6] = o; o = align_up(o + 2 * (size_t)p * sizeof(double), 16);      // grad accum
+    // the energy-build tables are used before the first sub-pass and the top-k scratch after
+    // the last one: both live in one region
     const size_t nw = (size_t)(threads + 31) / 32;
+    const size_t r0 = o;
     off[7] = o; o = align_up(o + nw * 32 * sizeof(TopEnt), 16);          // fallback lists
     off[8] = o; o = align_up(o + TOPK_CAP * sizeof(TopEnt), 16);         // candidates
     off[9] = o; o = align_up(o + 16 * sizeof(TopEnt), 16);               // tile top-k
     off[10] = o; o = align_up(o + 16 * 32 * sizeof(float) + 4 * sizeof(int), 16);  // bounds, counts
-    off[11] = o; o = align_up(o + (((size_t)1 << (n / 2)) + ((size_t)1 << (n - n / 2)) + 1) * sizeof(T), 16);
+    off[11] = r0;                                                         // energy tables
+    const size_t eend = align_up(r0 + tile_energy_scratch(n) * sizeof(T), 16);
+    if (eend > o) o = eend;
     return o;
 }
 

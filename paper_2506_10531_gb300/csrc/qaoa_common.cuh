@@ -254,8 +254,9 @@ struct WarpTopK {
         // |pf - P| <= 2^-21 P for the exact P, so P >= thr implies pf (1 + 2^-20) >= thr_f
         const bool cand = valid && (pf * 1.00000095367431640625f >= thr_f);
         uint32_t m = __ballot_sync(0xffffffffu, cand);
-        if (!m) return;
-        const double cp = cand ? exact_prob(v) : -1.0;
+        if (!m) return;   // warp-uniform: the FP64 below runs only for warps with candidates
+        double cp = -1.0;
+        if (cand) cp = exact_prob(v);
         while (m) {
             const int src = __ffs(m) - 1;
             m &= m - 1;

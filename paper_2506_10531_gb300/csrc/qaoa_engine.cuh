@@ -195,13 +195,19 @@ __device__ __forceinline__ void subpass_fwd_a(const TileRef<T>& t, const SubPass
         C v[1 << R];
         if (valid) {
             if (init) {
-                // |+> in the rotated frame: amp0 i^{|z|}, |z| = pc0 + |base| + |i|
+                // |+> in the rotated frame: amp0 i^{|z|}, |z| = pc0 + |base| + |i|; the four
+                // values i^m amp0 are formed once and picked by the compile-time |i|
                 const int pb = pc0 + __popc(base);
                 C a;
                 a.x = amp0;
                 a.y = T(0);
+                const C q0 = times_i_pow(a, pb), q1 = times_i_pow(a, pb + 1);
+                const C q2 = times_i_pow(a, pb + 2), q3 = times_i_pow(a, pb + 3);
 #pragma unroll
-                for (int i = 0; i < (1 << R); ++i) v[i] = times_i_pow(a, pb + __popc(i));
+                for (int i = 0; i < (1 << R); ++i) {
+                    const int m = __popc(i) & 3;
+                    v[i] = m == 0 ? q0 : (m == 1 ? q1 : (m == 2 ? q2 : q3));
+                }
             } else {
                 load_group<R, A>(t.psi, sb, v);
             }
@@ -356,97 +362,100 @@ __device__ __forceinline__ void reduce_group(const TileRef<T>& t, uint32_t base,
 
 // ---- energies of a tile -----------------------------------------------------------------
 // E(z) = z^T Q z for the 2^L tile indices u of one n-qubit instance, z = zfix | u (zfix holds
-// global bits >= L that the tile fixes, e.g. the CTA rank of a cluster). With u = (hi, lo),
-// lo = the low B bits, and S = the set bits of zfix:
-//   E(z) = E_S + El[lo] + Eh[hi] + X(lo, hi),
-//   El[lo] = sum_{i,j in lo} Q_ij + sum_{i in lo, j in S} (Q_ij + Q_ji),  Eh likewise for hi,
-//   X(lo, hi) = sum_{i in lo, j in hi} (Q_ij + Q_ji)  (linear in the hi bits for fixed lo).
-// El and Eh are small shared tables (2^B and 2^(L-B) entries); each thread fixes lo and the
-// top hi bits and walks the remaining hi bits in Gray-code order, where flipping bit j changes
-// X by +-W_j(lo), W_j = sum_{i in lo} (Q_ij + Q_ji) held in registers. Every E is the sum of
-// at most three table terms plus X (at most 2^5 increments), all in the tile's real type.
-// scratch: 2^B + 2^(L-B) + 1 values of T. Contains __syncthreads (all threads call).
-constexpr int EW_MAX = 6;   // walked bits per thread
+// global bits >= L that the tile fixes, e.g. the CTA rank of a cluster). With u split into
+// three bit fields lo = [0, B), ha = [B, B+A), hb = [B+A, L) and S = the set bits of zfix:
+//   E(z) = E_S + El[lo] + Ea[ha] + Eb[hb] + Xa[lo][ha] + Xb[lo][hb] + Xab[ha][hb],
+//   El[lo]  = sum_{i,j in lo} Q_ij + sum_{i in lo, j in S} (Q_ij + Q_ji)   (Ea, Eb likewise),
+//   Xa[lo][ha] = sum_{i in lo, j in ha} (Q_ij + Q_ji)                        (Xb, Xab likewise).
+// Every pair of set bits of z falls in exactly one term. The tables are small (a few KB)
+// and built in parallel; then every element is six table reads and six adds, independent of
+// all other elements (no serial walk). scratch: tile_energy_scratch(L) values of T.
+__host__ __device__ inline void energy_fields(int L, int& B, int& A) {
+    B = (L + 1) / 2;
+    A = (L - B) / 2;
+}
+__host__ __device__ inline size_t tile_energy_scratch(int L) {
+    int B, A;
+    energy_fields(L, B, A);
+    const int Hb = L - B - A;
+    return 1 + ((size_t)1 << B) + ((size_t)1 << A) + ((size_t)1 << Hb) +
+           ((size_t)1 << (B + A)) + ((size_t)1 << (B + Hb)) + ((size_t)1 << (A + Hb));
+}
+
+template <typename T>
+__device__ __forceinline__ T pair_sum(const T* Qs, int n, uint32_t x, int xs, uint32_t y, int ys) {
+    // sum over set bits i of x (shifted by xs) and j of y (shifted by ys) of Q_ij + Q_ji
+    T acc = T(0);
+    for (uint32_t bi = x; bi; bi &= bi - 1u) {
+        const int i = xs + __ffs((int)bi) - 1;
+        for (uint32_t bj = y; bj; bj &= bj - 1u) {
+            const int j = ys + __ffs((int)bj) - 1;
+            acc += Qs[i * n + j] + Qs[j * n + i];
+        }
+    }
+    return acc;
+}
+template <typename T>
+__device__ __forceinline__ T self_sum(const T* Qs, int n, uint32_t x, int xs, uint32_t zfix) {
+    // sum_{i,j in x} Q_ij + sum_{i in x, j in zfix} (Q_ij + Q_ji)
+    T acc = T(0);
+    for (uint32_t bi = x; bi; bi &= bi - 1u) {
+        const int i = xs + __ffs((int)bi) - 1;
+        for (uint32_t bj = x; bj; bj &= bj - 1u) acc += Qs[i * n + xs + __ffs((int)bj) - 1];
+        for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
+            const int j = __ffs((int)bj) - 1;
+            acc += Qs[i * n + j] + Qs[j * n + i];
+        }
+    }
+    return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ void build_tile_energy(int n, int L, uint32_t zfix, const T* Qs, T* E,
                                                   T* scratch) {
-    const int B = L / 2, H = L - B;
-    const uint32_t NL = 1u << B, NH = 1u << H;
-    T* El = scratch;
-    T* Eh = scratch + NL;
-    T* Es = scratch + NL + NH;
-    // pair weight of bits i, j (i != j): Q_ij + Q_ji; a set bit i alone: Q_ii
-    for (uint32_t x = threadIdx.x; x < NL + NH + 1; x += blockDim.x) {
-        T acc = T(0);
-        if (x == NL + NH) {                       // E_S
+    int B, A;
+    energy_fields(L, B, A);
+    const int Hb = L - B - A;
+    const uint32_t NL = 1u << B, NA = 1u << A, NB = 1u << Hb;
+    T* Es = scratch;
+    T* El = Es + 1;
+    T* Ea = El + NL;
+    T* Eb = Ea + NA;
+    T* Xa = Eb + NB;            // [lo][ha]
+    T* Xb = Xa + NL * NA;       // [lo][hb]
+    T* Xab = Xb + NL * NB;      // [ha][hb]
+    const uint32_t total = 1u + NL + NA + NB + NL * NA + NL * NB + NA * NB;
+    for (uint32_t x = threadIdx.x; x < total; x += blockDim.x) {
+        uint32_t y = x;
+        if (y == 0) {                                   // E_S
+            T acc = T(0);
             for (uint32_t bi = zfix; bi; bi &= bi - 1u) {
                 const int i = __ffs((int)bi) - 1;
-                for (uint32_t bj = zfix; bj; bj &= bj - 1u) acc += Qs[i * n + (__ffs((int)bj) - 1)];
+                for (uint32_t bj = zfix; bj; bj &= bj - 1u) acc += Qs[i * n + __ffs((int)bj) - 1];
             }
             Es[0] = acc;
             continue;
         }
-        const bool hi = x >= NL;
-        const uint32_t bits = hi ? ((x - NL) << B) : x;
-        for (uint32_t bi = bits; bi; bi &= bi - 1u) {
-            const int i = __ffs((int)bi) - 1;
-            for (uint32_t bj = bits; bj; bj &= bj - 1u) acc += Qs[i * n + (__ffs((int)bj) - 1)];
-            for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
-                const int j = __ffs((int)bj) - 1;
-                acc += Qs[i * n + j] + Qs[j * n + i];
-            }
-        }
-        (hi ? Eh[x - NL] : El[x]) = acc;
+        y -= 1;
+        if (y < NL) { El[y] = self_sum(Qs, n, y, 0, zfix); continue; }
+        y -= NL;
+        if (y < NA) { Ea[y] = self_sum(Qs, n, y, B, zfix); continue; }
+        y -= NA;
+        if (y < NB) { Eb[y] = self_sum(Qs, n, y, B + A, zfix); continue; }
+        y -= NB;
+        if (y < NL * NA) { Xa[y] = pair_sum(Qs, n, y / NA, 0, y % NA, B); continue; }
+        y -= NL * NA;
+        if (y < NL * NB) { Xb[y] = pair_sum(Qs, n, y / NB, 0, y % NB, B + A); continue; }
+        y -= NL * NB;
+        Xab[y] = pair_sum(Qs, n, y / NB, B, y % NB, B + A);
     }
     __syncthreads();
-    // combos (lo, top hi bits) per thread; the remaining hi bits are walked
-    uint32_t NC = blockDim.x < NL ? NL : blockDim.x;
-    if (NC > (1u << L)) NC = 1u << L;
-    while ((1u << L) / NC > (1u << EW_MAX)) NC <<= 1;     // keep the walk short
-    const int cb = 31 - __clz((int)NC);                   // log2(NC) >= B
-    const int hw = L - cb;                                // walked bits (top of hi: [cb, L))
-    const int hf = cb - B;                                // fixed hi bits [B, cb)
-    for (uint32_t c = threadIdx.x; c < NC; c += blockDim.x) {
-        const uint32_t lo = c & (NL - 1u);
-        const uint32_t hfix = c >> B;                     // hf bits
-        T W[EW_MAX];
-#pragma unroll
-        for (int j = 0; j < EW_MAX; ++j) {
-            T w = T(0);
-            if (j < hw) {
-                const int qj = cb + j;
-                for (uint32_t bi = lo; bi; bi &= bi - 1u) {
-                    const int i = __ffs((int)bi) - 1;
-                    w += Qs[i * n + qj] + Qs[qj * n + i];
-                }
-            }
-            W[j] = w;
-        }
-        T X = T(0);   // cross term of lo with the fixed hi bits
-        for (uint32_t bj = hfix; bj; bj &= bj - 1u) {
-            const int qj = B + __ffs((int)bj) - 1;
-            for (uint32_t bi = lo; bi; bi &= bi - 1u) {
-                const int i = __ffs((int)bi) - 1;
-                X += Qs[i * n + qj] + Qs[qj * n + i];
-            }
-        }
-        const T base = Es[0] + El[lo];
-        uint32_t hiv = hfix;                              // hi index (H bits)
-        E[swz<T>(lo | (hiv << B))] = base + Eh[hiv] + X;
-        const uint32_t steps = 1u << hw;
-        for (uint32_t k = 1; k < steps; ++k) {
-            const int b = __ffs((int)k) - 1;
-            const uint32_t bit = 1u << (hf + b);
-            T wb = T(0);
-#pragma unroll
-            for (int j = 0; j < EW_MAX; ++j)
-                if (j == b) wb = W[j];
-            X += (hiv & bit) ? -wb : wb;
-            hiv ^= bit;
-            E[swz<T>(lo | (hiv << B))] = base + Eh[hiv] + X;
-        }
+    const T es = Es[0];
+    for (uint32_t u = threadIdx.x; u < (1u << L); u += blockDim.x) {
+        const uint32_t lo = u & (NL - 1u), ha = (u >> B) & (NA - 1u), hb = u >> (B + A);
+        E[swz<T>(u)] = ((es + El[lo]) + (Ea[ha] + Eb[hb])) +
+                       ((Xa[lo * NA + ha] + Xb[lo * NB + hb]) + Xab[ha * NB + hb]);
     }
-    (void)hf;
 }
 
 // ---- final reductions of a tile -----------------------------------------------------------
@@ -471,7 +480,6 @@ __device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float bo
     using C = typename Num<T>::C;
     const uint32_t D = 1u << t.tb;
     const int lane = threadIdx.x & 31;
-    const double eb = exact_bound ? *exact_bound : -1.0;
     for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
         const uint32_t u = u0 + threadIdx.x;
         C v;
@@ -480,20 +488,24 @@ __device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float bo
         if (u < D) v = t.psi[swz<T>(u)];
         const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
         bool c = (u < D) && (pf * 1.00000095367431640625f >= bound_lo);
-        double pe = 0.0;
-        if (c) {
-            pe = exact_prob(v);
-            c = pe >= eb;
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, c);
-        if (m) {
-            int base = 0;
-            if (lane == __ffs(m) - 1) base = atomicAdd(&ts.cnt[0], __popc(m));
-            base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        // FP64 work only behind a warp-uniform branch: GB300 issues FP64 at 1/64 of the FP32
+        // rate, so it must never sit (predicated) on the per-element path
+        if (__any_sync(0xffffffffu, c)) {
+            double pe = 0.0;
             if (c) {
-                const int pos = base + __popc(m & ((1u << lane) - 1u));
-                if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{pe, zmap(u)};
-                else ts.cnt[1] = 1;
+                pe = exact_prob(v);
+                if (exact_bound) c = pe >= *exact_bound;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, c);
+            if (m) {
+                int base = 0;
+                if (lane == __ffs(m) - 1) base = atomicAdd(&ts.cnt[0], __popc(m));
+                base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+                if (c) {
+                    const int pos = base + __popc(m & ((1u << lane) - 1u));
+                    if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{pe, zmap(u)};
+                    else ts.cnt[1] = 1;
+                }
             }
         }
     }
@@ -521,21 +533,23 @@ __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& z
     using C = typename Num<T>::C;
     const uint32_t D = 1u << t.tb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    T accp = T(0);
-    int nacc = 0;
     float pmax = -1.0f;
-    for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
-        const uint32_t u = u0 + threadIdx.x;
-        if (u < D) {
-            const uint32_t ix = swz<T>(u);
-            const C v = t.psi[ix];
-            const T pr = v.x * v.x + v.y * v.y;
-            accp += pr * t.E[ix];
-            pmax = fmaxf(pmax, (float)pr);
-            if (++nacc == 32) { ex += (double)accp; accp = T(0); nacc = 0; }
+    // chunks of at most 32 elements per thread in FP32; the FP64 add sits outside the chunk
+    for (uint32_t c0 = 0; c0 < D; c0 += 32u * blockDim.x) {
+        T accp = T(0);
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t u = c0 + (uint32_t)j * blockDim.x + threadIdx.x;
+            if (u < D) {
+                const uint32_t ix = swz<T>(u);
+                const C v = t.psi[ix];
+                const T pr = v.x * v.x + v.y * v.y;
+                accp += pr * t.E[ix];
+                pmax = fmaxf(pmax, (float)pr);
+            }
         }
+        ex += (double)accp;
     }
-    ex += (double)accp;
     if (k <= 0) return;
     // (2) the k-th largest lane maximum of the block
     const float srt = warp_sort_desc(pmax);
