@@ -421,9 +421,9 @@ __device__ __forceinline__ void build_tile_energy(int n, int L, uint32_t zfix, c
     T* El = Es + 1;
     T* Ea = El + NL;
     T* Eb = Ea + NA;
-    T* Xa = Eb + NB;            // [lo][ha]
-    T* Xb = Xa + NL * NA;       // [lo][hb]
-    T* Xab = Xb + NL * NB;      // [ha][hb]
+    T* Xa = Eb + NB;            // [ha][lo]: consecutive lanes read consecutive lo (no conflicts)
+    T* Xb = Xa + NL * NA;       // [hb][lo]
+    T* Xab = Xb + NL * NB;      // [ha][hb] (one address per warp: broadcast)
     const uint32_t total = 1u + NL + NA + NB + NL * NA + NL * NB + NA * NB;
     for (uint32_t x = threadIdx.x; x < total; x += blockDim.x) {
         uint32_t y = x;
@@ -443,18 +443,18 @@ __device__ __forceinline__ void build_tile_energy(int n, int L, uint32_t zfix, c
         y -= NA;
         if (y < NB) { Eb[y] = self_sum(Qs, n, y, B + A, zfix); continue; }
         y -= NB;
-        if (y < NL * NA) { Xa[y] = pair_sum(Qs, n, y / NA, 0, y % NA, B); continue; }
+        if (y < NL * NA) { Xa[y] = pair_sum(Qs, n, y & (NL - 1u), 0, y >> B, B); continue; }
         y -= NL * NA;
-        if (y < NL * NB) { Xb[y] = pair_sum(Qs, n, y / NB, 0, y % NB, B + A); continue; }
+        if (y < NL * NB) { Xb[y] = pair_sum(Qs, n, y & (NL - 1u), 0, y >> B, B + A); continue; }
         y -= NL * NB;
-        Xab[y] = pair_sum(Qs, n, y / NB, B, y % NB, B + A);
+        Xab[y] = pair_sum(Qs, n, y >> Hb, B, y & (NB - 1u), B + A);
     }
     __syncthreads();
     const T es = Es[0];
     for (uint32_t u = threadIdx.x; u < (1u << L); u += blockDim.x) {
         const uint32_t lo = u & (NL - 1u), ha = (u >> B) & (NA - 1u), hb = u >> (B + A);
         E[swz<T>(u)] = ((es + El[lo]) + (Ea[ha] + Eb[hb])) +
-                       ((Xa[lo * NA + ha] + Xb[lo * NB + hb]) + Xab[ha * NB + hb]);
+                       ((Xa[(ha << B) | lo] + Xb[(hb << B) | lo]) + Xab[(ha << Hb) | hb]);
     }
 }
 
