@@ -128,7 +128,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     }
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
     __syncthreads();
-    build_tile_energy<float>(n, L, r << L, s.Q, s.E, s.escr);
+    build_tile_energy_any<float>(n, L, r << L, s.Q, s.E, s.escr);
     __syncthreads();
     if (d.E_out)
         for (uint32_t u = threadIdx.x; u < D; u += blockDim.x) d.E_out[(r << L) | u] = s.E[swz<float>(u)];

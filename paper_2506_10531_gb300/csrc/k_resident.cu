@@ -150,7 +150,7 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     if (d.Q) {
         for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
         __syncthreads();
-        build_tile_energy<T>(n, n, 0u, s.Q, s.E, s.escr);
+        build_tile_energy_any<T>(n, n, 0u, s.Q, s.E, s.escr);
     } else {
         for (uint32_t z = threadIdx.x; z < D; z += blockDim.x) s.E[swz<T>(z)] = d.E_in[z];
     }

@@ -458,6 +458,81 @@ __device__ __forceinline__ void build_tile_energy(int n, int L, uint32_t zfix, c
     }
 }
 
+// Fast path of the tile energies when blockDim = 2^(L - HB): thread t owns the low field
+// lo = t (B = L - HB bits) and the 2^HB elements u = t | (j << B). With S the set bits of zfix
+//   E(z) = [E_S + El(t)] + Eh[j] + X_t(j),   X_t(j) = sum_{b in j} W_b(t),
+//   W_b(t) = sum_{i in t} (Q_{i,B+b} + Q_{B+b,i}),
+// El(t) and W_b(t) are evaluated by the thread (sums over the set bits of t), Eh (2^HB
+// entries, shared) by 2^HB threads, and X_t(j) for all j by subset doubling in registers
+// (2^HB - 1 additions). Each element is then one broadcast read, two adds and one store.
+template <typename T, int HB>
+__device__ __forceinline__ void build_tile_energy_fast(int n, int L, uint32_t zfix, const T* Qs,
+                                                       T* E, T* scratch) {
+    const int B = L - HB;
+    const uint32_t t = threadIdx.x;
+    T* Eh = scratch;                 // 2^HB entries: hi self terms + hi x S
+    if (t < (1u << HB)) {
+        T acc = T(0);
+        const uint32_t hbits = t << B;
+        for (uint32_t bi = hbits; bi; bi &= bi - 1u) {
+            const int i = __ffs((int)bi) - 1;
+            for (uint32_t bj = hbits; bj; bj &= bj - 1u) acc += Qs[i * n + __ffs((int)bj) - 1];
+            for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
+                const int j = __ffs((int)bj) - 1;
+                acc += Qs[i * n + j] + Qs[j * n + i];
+            }
+        }
+        Eh[t] = acc;
+    }
+    // E_S + El(t)
+    T base = T(0);
+    for (uint32_t bi = zfix; bi; bi &= bi - 1u) {
+        const int i = __ffs((int)bi) - 1;
+        for (uint32_t bj = zfix; bj; bj &= bj - 1u) base += Qs[i * n + __ffs((int)bj) - 1];
+    }
+    for (uint32_t bi = t; bi; bi &= bi - 1u) {
+        const int i = __ffs((int)bi) - 1;
+        for (uint32_t bj = t; bj; bj &= bj - 1u) base += Qs[i * n + __ffs((int)bj) - 1];
+        for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
+            const int j = __ffs((int)bj) - 1;
+            base += Qs[i * n + j] + Qs[j * n + i];
+        }
+    }
+    T X[1 << HB];
+    X[0] = T(0);
+#pragma unroll
+    for (int b = 0; b < HB; ++b) {
+        T w = T(0);
+        const int q = B + b;
+        for (uint32_t bi = t; bi; bi &= bi - 1u) {
+            const int i = __ffs((int)bi) - 1;
+            w += Qs[i * n + q] + Qs[q * n + i];
+        }
+#pragma unroll
+        for (int m = 0; m < (1 << b); ++m) X[m | (1 << b)] = X[m] + w;
+    }
+    __syncthreads();
+    const uint32_t st = swz<T>(t);
+#pragma unroll
+    for (int j = 0; j < (1 << HB); ++j)
+        E[st ^ swz<T>((uint32_t)j << B)] = base + (Eh[j] + X[j]);
+}
+
+template <typename T>
+__device__ __forceinline__ void build_tile_energy_any(int n, int L, uint32_t zfix, const T* Qs,
+                                                      T* E, T* scratch) {
+    const int lg = 31 - __clz((int)blockDim.x);
+    switch (L - lg) {
+        case 0: build_tile_energy_fast<T, 0>(n, L, zfix, Qs, E, scratch); return;
+        case 1: build_tile_energy_fast<T, 1>(n, L, zfix, Qs, E, scratch); return;
+        case 2: build_tile_energy_fast<T, 2>(n, L, zfix, Qs, E, scratch); return;
+        case 3: build_tile_energy_fast<T, 3>(n, L, zfix, Qs, E, scratch); return;
+        case 4: build_tile_energy_fast<T, 4>(n, L, zfix, Qs, E, scratch); return;
+        case 5: build_tile_energy_fast<T, 5>(n, L, zfix, Qs, E, scratch); return;
+        default: build_tile_energy<T>(n, L, zfix, Qs, E, scratch); return;
+    }
+}
+
 // ---- final reductions of a tile -----------------------------------------------------------
 // Shared scratch of tile_reduce (sizes: wb 16 * nwarps floats, cand TOPK_CAP entries, out 16,
 // wlists 32 * nwarps entries, cnt 4 ints).
