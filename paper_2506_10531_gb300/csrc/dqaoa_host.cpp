@@ -5,7 +5,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <unordered_map>
 #include <vector>
 
 #include "qaoa_host.h"
@@ -43,24 +42,30 @@ struct SplitMix64 {
 }  // namespace
 
 // Random index sets: a partial Fisher-Yates shuffle of 0..N-1 per row, with only the touched
-// positions stored (a map from position to value), which draws the same sets as a shuffle of
-// the full array.
+// positions stored, which draws the same sets as a shuffle of the full array: positions
+// 0..k-1 in a direct array, positions >= k (at most k of them) in a short list.
 int draw_random(int N, int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx) {
-    std::unordered_map<int32_t, int32_t> moved;
-    moved.reserve((size_t)2 * k);
+    std::vector<int32_t> pre((size_t)k), pos((size_t)k), val((size_t)k);
     for (int j = 0; j < m; ++j) {
         SplitMix64 g{seed ^ (cycle * 0x9E3779B97F4A7C15ULL) ^ (uint64_t)j};
-        moved.clear();
+        for (int i = 0; i < k; ++i) pre[i] = i;
+        int used = 0;
         int32_t* S = idx + (int64_t)j * k;
         for (int i = 0; i < k; ++i) {
             const int32_t r = i + (int32_t)g.below((uint64_t)(N - i));
-            auto at = [&](int32_t pos) {
-                auto it = moved.find(pos);
-                return it == moved.end() ? pos : it->second;
-            };
-            const int32_t vi = at(i), vr = at(r);
-            moved[i] = vr;
-            moved[r] = vi;
+            const int32_t vi = pre[i];
+            int32_t vr;
+            if (r < k) {
+                vr = pre[r];
+                pre[r] = vi;
+            } else {
+                int e = 0;
+                while (e < used && pos[e] != r) ++e;
+                vr = (e < used) ? val[e] : r;
+                if (e == used) { pos[used] = r; ++used; }
+                val[e] = vi;
+            }
+            pre[i] = vr;
             S[i] = vr;
         }
         std::sort(S, S + k);

@@ -785,6 +785,10 @@ struct dqaoa_session {
     qaoa_plan* plan = nullptr;
     MergeCache cache;             // h = Qx and E(x) after the last merge
     std::vector<uint8_t> x_last;  // the solution the cache belongs to
+    // random index sets of the next cycle, drawn on the host while the device works
+    std::vector<int32_t> next_idx;
+    bool next_valid = false;
+    uint64_t next_seed = 0, next_cycle = 0;
 };
 
 extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, int p, int K, int method,
@@ -854,8 +858,14 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     cudaStream_t st = (cudaStream_t)stream;
     const int N = s->N, m = s->m, k = s->k, K = s->K;
     if (q_changed) CK(cudaMemcpyAsync(s->Q_dev, Q, (size_t)N * N * sizeof(double), cudaMemcpyHostToDevice, st));
-    // decompose: index sets on the host, matrices on the device
-    qaoa_status r = dqaoa_draw_indices(Q, N, x, s->method, m, k, seed, cycle, s->idx_h);
+    // decompose: index sets on the host (random sets drawn ahead during the previous cycle
+    // when seed and cycle match), matrices on the device
+    qaoa_status r = QAOA_OK;
+    if (s->method == DQAOA_RANDOM && s->next_valid && s->next_seed == seed && s->next_cycle == cycle)
+        std::memcpy(s->idx_h, s->next_idx.data(), (size_t)m * k * sizeof(int32_t));
+    else
+        r = dqaoa_draw_indices(Q, N, x, s->method, m, k, seed, cycle, s->idx_h);
+    s->next_valid = false;
     if (r) return r;
     std::memcpy(s->x_h, x, (size_t)N);
     CK(cudaMemcpyAsync(s->x_dev, s->x_h, (size_t)N, cudaMemcpyHostToDevice, st));
@@ -866,6 +876,13 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     if (r) return r;
     CK(cudaMemcpyAsync(s->topk_h, s->topk, (size_t)m * K * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(s->expect_h, s->expect, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (s->method == DQAOA_RANDOM) {   // overlaps the device work of this cycle
+        s->next_idx.resize((size_t)m * k);
+        draw_random(N, m, k, seed, cycle + 1, s->next_idx.data());
+        s->next_valid = true;
+        s->next_seed = seed;
+        s->next_cycle = cycle + 1;
+    }
     CK(cudaStreamSynchronize(st));
     // aggregate (reusing h = Qx when Q is unchanged and x is the solution the last merge left)
     s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
