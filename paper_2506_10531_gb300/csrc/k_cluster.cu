@@ -121,11 +121,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     s.escr = reinterpret_cast<float*>(sm + off[10]);
     const uint32_t D = 1u << L;
 
-    for (int l = threadIdx.x; l < p; l += blockDim.x) {
-        float sb, cb;
-        sincos_full(d.beta[l], sb, cb);
-        s.lc[l] = LayerConst<float>{d.gamma[l] / 3.14159265358979323846f, cb, sb};
-    }
+    set_layer_consts<float>(s.lc, d.gamma, d.beta, p, n, true);
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
     __syncthreads();
     build_tile_energy_any<float>(n, L, r << L, s.Q, s.E, s.escr);
@@ -151,6 +147,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
             global_subpass<CB>(cl, s, L, r, s.lc[sp.la]);
             cl.sync();
         }
+        sp.post = (si == S - 1);
         subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, __popc(r), nofin);
         __syncthreads();
     }

@@ -69,6 +69,7 @@ __device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s) {
     for (int si = 0; si < S; ++si) {
         SubPass sp;
         snake_step(si, G, p, 0, 1, 0, n, n, R, sp);
+        sp.post = (si == S - 1);
         subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, 0, nofin);
         __syncthreads();
     }
@@ -141,12 +142,7 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     s.escr = reinterpret_cast<T*>(sm + off[11]);
     const uint32_t D = 1u << n;
 
-    for (int l = threadIdx.x; l < p; l += blockDim.x) {
-        const T g = d.gamma[l], b = d.beta[l];
-        T sb, cb;
-        sincos_full(b, sb, cb);
-        s.lc[l] = LayerConst<T>{g / T(3.14159265358979323846), cb, sb};
-    }
+    set_layer_consts<T>(s.lc, d.gamma, d.beta, p, n, true);
     if (d.Q) {
         for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
         __syncthreads();

@@ -71,6 +71,7 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     for (int si = 0; si < S; ++si) {
         SubPass sp;
         snake_step(si, G, nl, P.la, P.ph_first, m0, P.tb, P.tb, R, sp);
+        sp.post = P.fin && (si == S - 1);
         subpass_fwd<T, R>(tile, sp, s.lc, P.init && si == 0, amp0, __popcll(tau), nofin);
         __syncthreads();
     }
@@ -129,11 +130,7 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
         const StreamInst<T>& I = insts ? insts[ii] : one;
         if (ii != cur) {
             __syncthreads();
-            for (int l = threadIdx.x; l < I.p; l += blockDim.x) {
-                T sb, cb;
-                sincos_full(I.beta[l], sb, cb);
-                s.lc[l] = LayerConst<T>{I.gamma[l] / T(3.14159265358979323846), cb, sb};
-            }
+            set_layer_consts<T>(s.lc, I.gamma, I.beta, I.p, P.n, true);
             __syncthreads();
             cur = ii;
         }
@@ -395,7 +392,7 @@ int stream_plan(bool dbl, int n, int p, int k, StreamPass* out, int max_out) {
 
 size_t stream_smem_bytes(bool dbl) {
     const size_t TD = (size_t)1 << stream_tile_bits(dbl);
-    const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4, lcs = dbl ? 24 : 12;
+    const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4, lcs = dbl ? sizeof(LayerConst<double>) : sizeof(LayerConst<float>);
     size_t o = TD * c + TD * r + 64 * lcs;
     o = (o + 15) & ~(size_t)15;
     return o + 32 * sizeof(double) + (8 * 32 + TOPK_CAP + 16) * sizeof(TopEnt) +

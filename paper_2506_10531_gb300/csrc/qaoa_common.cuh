@@ -127,6 +127,23 @@ __device__ __forceinline__ void butterfly(double2& a, double2& b, const RotCoef<
     b.y = k.s * a0.y + k.c * b0.y;
 }
 
+// Unscaled shear form of the same rotation, used when |cos b| >= |sin b|:
+//   [[c, -s], [s, c]] = c [[1, -t], [t, 1]],  t = tan b,
+// so a' = a - t b, b' = b + t a (two packed FMAs per pair) and every qubit of the layer leaves
+// a factor c that is applied once per amplitude (c^n) at the next cost phase or at the end.
+__device__ __forceinline__ void butterfly_shear(float2& a, float2& b, float t) {
+    const float2 a0 = a;
+    a = fma2(b, make_float2(-t, -t), a);
+    b = fma2(a0, make_float2(t, t), b);
+}
+__device__ __forceinline__ void butterfly_shear(double2& a, double2& b, double t) {
+    const double2 a0 = a;
+    a.x = fma(-t, b.x, a0.x);
+    a.y = fma(-t, b.y, a0.y);
+    b.x = fma(t, a0.x, b.x);
+    b.y = fma(t, a0.y, b.y);
+}
+
 // Multiply by i^m (m mod 4): the frame change of an amplitude with m set bits.
 template <typename C>
 __device__ __forceinline__ C times_i_pow(C v, int m) {

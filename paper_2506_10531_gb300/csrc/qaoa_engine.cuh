@@ -20,16 +20,50 @@
 namespace qaoa {
 
 // Per-layer constants staged in shared memory: cost uses gamma/pi, the mixer (cos b, sin b).
+// A layer with |cos b| >= |sin b| mixes with unscaled shears (t = tan b); the factor
+// (cos b)^n it leaves is applied by the next layer's cost phase (`pre`) or, for the last layer,
+// by the last sub-pass (`post`).
 template <typename T>
 struct LayerConst {
-    T gpi;   // gamma_l / pi
-    T c, s;  // cos(beta_l), sin(beta_l)
+    T gpi;     // gamma_l / pi
+    T c, s;    // cos(beta_l), sin(beta_l)
+    T t;       // tan(beta_l) when shear != 0
+    T pre;     // scale applied with this layer's cost phase (pending factor of layer l-1)
+    T post;    // scale still pending after this layer (used for the last layer)
+    int shear;
 };
 
+// Fill the constants of p layers of an n-qubit instance (one thread per layer).
+template <typename T>
+__device__ __forceinline__ void set_layer_consts(LayerConst<T>* lc, const T* gamma, const T* beta,
+                                                 int p, int n, bool allow_shear) {
+    for (int l = threadIdx.x; l < p; l += blockDim.x) {
+        T sb, cb;
+        sincos_full(beta[l], sb, cb);
+        LayerConst<T> k;
+        k.gpi = gamma[l] / T(3.14159265358979323846);
+        k.c = cb;
+        k.s = sb;
+        k.shear = (allow_shear && fabs(cb) >= fabs(sb)) ? 1 : 0;
+        k.t = k.shear ? sb / cb : T(0);
+        k.post = k.shear ? (T)pow((double)cb, (double)n) : T(1);
+        T pre = T(1);
+        if (l > 0) {
+            T sp, cp;
+            sincos_full(beta[l - 1], sp, cp);
+            if (allow_shear && fabs(cp) >= fabs(sp)) pre = (T)pow((double)cp, (double)n);
+        }
+        k.pre = pre;
+        lc[l] = k;
+    }
+}
+
 // One sub-pass: window start a, butterfly mask over the window bits, layers [la, lb]
-// (lb <= la + 1), whether the cost of layer la opens the sub-pass.
+// (lb <= la + 1), whether the cost of layer la opens the sub-pass; post != 0 applies the
+// pending shear factor of layer lb after its mixer (set by the caller on the very last
+// sub-pass of a state).
 struct SubPass {
-    int a, mask, la, lb, ph_first;
+    int a, mask, la, lb, ph_first, post;
 };
 
 // Windows of a layer over the mixed tile bits [m0, m1): window w covers bits
@@ -77,6 +111,7 @@ __device__ __forceinline__ void snake_step(int s, int G, int nl, int L0, int fir
     sp.la = la;
     sp.lb = lb;
     sp.ph_first = phf;
+    sp.post = 0;
 }
 
 // Local index of element i of group g for window start a (R window bits).
@@ -99,6 +134,36 @@ __device__ __forceinline__ void mix_group(C (&v)[1 << R], int mask, T c, T s) {
                 if (!(i & (1 << j))) butterfly(v[i], v[i | (1 << j)], k);
         }
     }
+}
+
+// Shear-form mixer (see LayerConst): a' = a - t b, b' = b + t a on the masked window bits.
+template <int R, typename C, typename T>
+__device__ __forceinline__ void mix_group_shear(C (&v)[1 << R], int mask, T t) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (mask & (1 << j)) {
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i)
+                if (!(i & (1 << j))) butterfly_shear(v[i], v[i | (1 << j)], t);
+        }
+    }
+}
+
+// Scale every amplitude of a group.
+template <int R, typename C, typename T>
+__device__ __forceinline__ void scale_group(C (&v)[1 << R], T f) {
+#pragma unroll
+    for (int i = 0; i < (1 << R); ++i) {
+        v[i].x *= f;
+        v[i].y *= f;
+    }
+}
+
+// Mixer of layer constants k on a register group (shear or full rotation).
+template <int R, typename C, typename T>
+__device__ __forceinline__ void mix_layer(C (&v)[1 << R], int mask, const LayerConst<T>& k) {
+    if (k.shear) mix_group_shear<R>(v, mask, k.t);
+    else mix_group<R>(v, mask, k.c, k.s);
 }
 
 // Mixer inverse on two states with the accumulation of Im <lam| X_q |psi> over the masked
@@ -213,16 +278,17 @@ __device__ __forceinline__ void subpass_fwd_a(const TileRef<T>& t, const SubPass
             }
             for (int l = sp.la; l <= sp.lb; ++l) {
                 if (l > sp.la || sp.ph_first) {
-                    const T gp = lc[l].gpi;
+                    const T gp = lc[l].gpi, pre = lc[l].pre;
 #pragma unroll
                     for (int i = 0; i < (1 << R); ++i) {
                         T s, c;
                         sincos_phase(gp, t.E[sb ^ woff<T, A>(i)], s, c);
-                        rot_neg(v[i], s, c);
+                        rot_neg(v[i], s * pre, c * pre);
                     }
                 }
-                mix_group<R>(v, sp.mask, lc[l].c, lc[l].s);
+                mix_layer<R>(v, sp.mask, lc[l]);
             }
+            if (sp.post && lc[sp.lb].shear) scale_group<R>(v, lc[sp.lb].post);
             store_group<R, A>(t.psi, sb, v);
         }
         fin(base, A, valid);
