@@ -87,7 +87,7 @@ __device__ void global_subpass(cg::cluster_group& cl, const ClusterSmem& s, int 
 #pragma unroll
             for (int j = 0; j < C; ++j) v[q][j] = rp[j][ix[q]];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) mix_group<CB>(v[q], C - 1, lc.c, lc.s);
+        for (int q = 0; q < NP; ++q) mix_layer<CB>(v[q], C - 1, lc);
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
             if (w0 + (uint32_t)q * blockDim.x < slab) {
