@@ -124,7 +124,9 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     set_layer_consts<float>(s.lc, d.gamma, d.beta, p, n, true);
     for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
     __syncthreads();
-    build_tile_energy_any<float>(n, L, r << L, s.Q, s.E, s.escr);
+    const FusedInit<float> fi{s.psi, (float)exp2(-0.5 * (double)n),
+                              d.gamma[0] / 3.14159265358979323846f, __popc(r)};
+    const bool started = build_tile_energy_any<float>(n, L, r << L, s.Q, s.E, s.escr, fi);
     __syncthreads();
     if (d.E_out)
         for (uint32_t u = threadIdx.x; u < D; u += blockDim.x) d.E_out[(r << L) | u] = s.E[swz<float>(u)];
@@ -137,7 +139,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
     auto nofin = [](uint32_t, int, bool) {};
     for (int si = 0; si < S; ++si) {
         SubPass sp;
-        snake_step(si, G, p, 0, 1, 0, L, L, R, sp);
+        snake_step(si, G, p, 0, started ? 0 : 1, 0, L, L, R, sp);
         // sub-pass (l+1)(G-1) holds layer l's last local window (fused with the cost and the
         // first window of layer l+1); the global qubits of layer l are mixed just before it,
         // after the cost of layer l (G >= 2: L >= 10 is required by the host)
@@ -148,7 +150,7 @@ __device__ void run_cluster_instance(cg::cluster_group& cl, const InstDesc<float
             cl.sync();
         }
         sp.post = (si == S - 1);
-        subpass_fwd<float, R>(tile, sp, s.lc, si == 0, amp0, __popc(r), nofin);
+        subpass_fwd<float, R>(tile, sp, s.lc, si == 0 && !started, amp0, __popc(r), nofin);
         __syncthreads();
     }
     // ---- per-CTA reductions, then rank 0 merges the CTAs (rank order for <C>) ----

@@ -58,17 +58,18 @@ __host__ __device__ inline size_t smem_layout(int n, int p, bool grad, int threa
 }
 
 template <typename T, int R>
-__device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s) {
+__device__ void forward_run(const InstDesc<T>& d, const Smem<T>& s, bool started) {
     const int n = d.n, p = d.p;
     const TileRef<T> tile{s.psi, s.lam, s.E, n};
-    const bool init = !(d.flags & F_INIT_PSI);
+    // started: the energy build already wrote |+> after the first cost layer
+    const bool init = !(d.flags & F_INIT_PSI) && !started;
     const T amp0 = (T)exp2(-0.5 * (double)n);
     const int G = num_windows(0, n, R);
     const int S = snake_len(G, p);
     auto nofin = [](uint32_t, int, bool) {};
     for (int si = 0; si < S; ++si) {
         SubPass sp;
-        snake_step(si, G, p, 0, 1, 0, n, n, R, sp);
+        snake_step(si, G, p, 0, started ? 0 : 1, 0, n, n, R, sp);
         sp.post = (si == S - 1);
         subpass_fwd<T, R>(tile, sp, s.lc, init && si == 0, amp0, 0, nofin);
         __syncthreads();
@@ -143,10 +144,17 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     const uint32_t D = 1u << n;
 
     set_layer_consts<T>(s.lc, d.gamma, d.beta, p, n, true);
+    bool started = false;
     if (d.Q) {
         for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.Q[i] = d.Q[i];
         __syncthreads();
-        build_tile_energy_any<T>(n, n, 0u, s.Q, s.E, s.escr);
+        FusedInit<T> fi{nullptr, T(0), T(0), 0};
+        if (!(d.flags & F_INIT_PSI)) {
+            fi.psi = s.psi;
+            fi.amp0 = (T)exp2(-0.5 * (double)n);
+            fi.gpi0 = d.gamma[0] / T(3.14159265358979323846);
+        }
+        started = build_tile_energy_any<T>(n, n, 0u, s.Q, s.E, s.escr, fi);
     } else {
         for (uint32_t z = threadIdx.x; z < D; z += blockDim.x) s.E[swz<T>(z)] = d.E_in[z];
     }
@@ -159,7 +167,7 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     if (d.E_out)
         for (uint32_t z = threadIdx.x; z < D; z += blockDim.x) d.E_out[z] = s.E[swz<T>(z)];
 
-    forward_run<T, R>(d, s);
+    forward_run<T, R>(d, s, started);
 
     if (d.psi_out) {              // back from the rotated frame: psi = (-i)^{|z|} psi~
         C* pout = reinterpret_cast<C*>(d.psi_out);

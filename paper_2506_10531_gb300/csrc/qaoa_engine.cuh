@@ -33,6 +33,18 @@ struct LayerConst {
     int shear;
 };
 
+// x^n by repeated squaring in the working precision (no FP64 on the complex64 path).
+template <typename T>
+__device__ __forceinline__ T ipow(T x, int n) {
+    T r = T(1);
+    while (n) {
+        if (n & 1) r *= x;
+        x *= x;
+        n >>= 1;
+    }
+    return r;
+}
+
 // Fill the constants of p layers of an n-qubit instance (one thread per layer).
 template <typename T>
 __device__ __forceinline__ void set_layer_consts(LayerConst<T>* lc, const T* gamma, const T* beta,
@@ -46,12 +58,12 @@ __device__ __forceinline__ void set_layer_consts(LayerConst<T>* lc, const T* gam
         k.s = sb;
         k.shear = (allow_shear && fabs(cb) >= fabs(sb)) ? 1 : 0;
         k.t = k.shear ? sb / cb : T(0);
-        k.post = k.shear ? (T)pow((double)cb, (double)n) : T(1);
+        k.post = k.shear ? ipow(cb, n) : T(1);
         T pre = T(1);
         if (l > 0) {
             T sp, cp;
             sincos_full(beta[l - 1], sp, cp);
-            if (allow_shear && fabs(cp) >= fabs(sp)) pre = (T)pow((double)cp, (double)n);
+            if (allow_shear && fabs(cp) >= fabs(sp)) pre = ipow(cp, n);
         }
         k.pre = pre;
         lc[l] = k;
@@ -531,9 +543,29 @@ __device__ __forceinline__ void build_tile_energy(int n, int L, uint32_t zfix, c
 // El(t) and W_b(t) are evaluated by the thread (sums over the set bits of t), Eh (2^HB
 // entries, shared) by 2^HB threads, and X_t(j) for all j by subset doubling in registers
 // (2^HB - 1 additions). Each element is then one broadcast read, two adds and one store.
+// Optional fused start of the state: with psi != nullptr every element is also set to the
+// |+> amplitude after the first cost layer, amp0 i^{|z|} e^{-i gamma_0 E(z)} (rotated frame,
+// |z| = pc0 + |u|), so the first sub-pass starts with the first mixer.
+template <typename T>
+struct FusedInit {
+    typename Num<T>::C* psi;   // nullptr: energies only
+    T amp0, gpi0;              // 2^{-n/2}, gamma_0 / pi
+    int pc0;                   // set bits of zfix
+};
+
+template <typename T>
+__device__ __forceinline__ void fused_init_store(const FusedInit<T>& fi, uint32_t u, uint32_t ix, T e) {
+    typename Num<T>::C a;
+    T s, c;
+    sincos_phase(fi.gpi0, e, s, c);
+    a.x = fi.amp0 * c;          // amp0 e^{-i theta}
+    a.y = -fi.amp0 * s;
+    fi.psi[ix] = times_i_pow(a, fi.pc0 + __popc(u));
+}
+
 template <typename T, int HB>
 __device__ __forceinline__ void build_tile_energy_fast(int n, int L, uint32_t zfix, const T* Qs,
-                                                       T* E, T* scratch) {
+                                                       T* E, T* scratch, const FusedInit<T>& fi) {
     const int B = L - HB;
     const uint32_t t = threadIdx.x;
     T* Eh = scratch;                 // 2^HB entries: hi self terms + hi x S
@@ -580,22 +612,28 @@ __device__ __forceinline__ void build_tile_energy_fast(int n, int L, uint32_t zf
     __syncthreads();
     const uint32_t st = swz<T>(t);
 #pragma unroll
-    for (int j = 0; j < (1 << HB); ++j)
-        E[st ^ swz<T>((uint32_t)j << B)] = base + (Eh[j] + X[j]);
+    for (int j = 0; j < (1 << HB); ++j) {
+        const uint32_t ix = st ^ swz<T>((uint32_t)j << B);
+        const T ev = base + (Eh[j] + X[j]);
+        E[ix] = ev;
+        if (fi.psi) fused_init_store(fi, t | ((uint32_t)j << B), ix, ev);
+    }
 }
 
+// Energies of the tile (fast path when blockDim = 2^(L - HB), HB <= 5), and optionally the
+// fused start of the state (see FusedInit). Returns true if the state was started.
 template <typename T>
-__device__ __forceinline__ void build_tile_energy_any(int n, int L, uint32_t zfix, const T* Qs,
-                                                      T* E, T* scratch) {
+__device__ __forceinline__ bool build_tile_energy_any(int n, int L, uint32_t zfix, const T* Qs,
+                                                      T* E, T* scratch, const FusedInit<T>& fi) {
     const int lg = 31 - __clz((int)blockDim.x);
     switch (L - lg) {
-        case 0: build_tile_energy_fast<T, 0>(n, L, zfix, Qs, E, scratch); return;
-        case 1: build_tile_energy_fast<T, 1>(n, L, zfix, Qs, E, scratch); return;
-        case 2: build_tile_energy_fast<T, 2>(n, L, zfix, Qs, E, scratch); return;
-        case 3: build_tile_energy_fast<T, 3>(n, L, zfix, Qs, E, scratch); return;
-        case 4: build_tile_energy_fast<T, 4>(n, L, zfix, Qs, E, scratch); return;
-        case 5: build_tile_energy_fast<T, 5>(n, L, zfix, Qs, E, scratch); return;
-        default: build_tile_energy<T>(n, L, zfix, Qs, E, scratch); return;
+        case 0: build_tile_energy_fast<T, 0>(n, L, zfix, Qs, E, scratch, fi); return fi.psi != nullptr;
+        case 1: build_tile_energy_fast<T, 1>(n, L, zfix, Qs, E, scratch, fi); return fi.psi != nullptr;
+        case 2: build_tile_energy_fast<T, 2>(n, L, zfix, Qs, E, scratch, fi); return fi.psi != nullptr;
+        case 3: build_tile_energy_fast<T, 3>(n, L, zfix, Qs, E, scratch, fi); return fi.psi != nullptr;
+        case 4: build_tile_energy_fast<T, 4>(n, L, zfix, Qs, E, scratch, fi); return fi.psi != nullptr;
+        case 5: build_tile_energy_fast<T, 5>(n, L, zfix, Qs, E, scratch, fi); return fi.psi != nullptr;
+        default: build_tile_energy<T>(n, L, zfix, Qs, E, scratch); return false;
     }
 }
 
