@@ -144,16 +144,18 @@ __device__ __forceinline__ void butterfly_shear(double2& a, double2& b, double t
     b.y = fma(t, a0.y, b.y);
 }
 
-// Multiply by i^m (m mod 4): the frame change of an amplitude with m set bits.
+// Multiply by i^m (m mod 4): the frame change of an amplitude with m set bits. Branch-free
+// (lanes of a warp usually have different m): i^m (x + iy) is (x, y), (-y, x), (-x, -y) or
+// (y, -x).
 template <typename C>
 __device__ __forceinline__ C times_i_pow(C v, int m) {
+    const int q = m & 3;
+    const bool swap = q & 1;
     C r;
-    switch (m & 3) {
-        case 0: r = v; break;
-        case 1: r.x = -v.y; r.y = v.x; break;      //  i (x + iy)
-        case 2: r.x = -v.x; r.y = -v.y; break;
-        default: r.x = v.y; r.y = -v.x; break;     // -i (x + iy)
-    }
+    r.x = swap ? v.y : v.x;
+    r.y = swap ? v.x : v.y;
+    if (q == 1 || q == 2) r.x = -r.x;
+    if (q >= 2) r.y = -r.y;
     return r;
 }
 

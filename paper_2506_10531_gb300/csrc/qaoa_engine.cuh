@@ -45,7 +45,8 @@ __device__ __forceinline__ T ipow(T x, int n) {
     return r;
 }
 
-// Fill the constants of p layers of an n-qubit instance (one thread per layer).
+// Fill the constants of p layers of an n-qubit instance (one thread per layer; contains a
+// __syncthreads, so every thread of the block calls it).
 template <typename T>
 __device__ __forceinline__ void set_layer_consts(LayerConst<T>* lc, const T* gamma, const T* beta,
                                                  int p, int n, bool allow_shear) {
@@ -53,21 +54,18 @@ __device__ __forceinline__ void set_layer_consts(LayerConst<T>* lc, const T* gam
         T sb, cb;
         sincos_full(beta[l], sb, cb);
         LayerConst<T> k;
-        k.gpi = gamma[l] / T(3.14159265358979323846);
+        k.gpi = gamma[l] * T(0.31830988618379067154);   // 1 / pi
         k.c = cb;
         k.s = sb;
         k.shear = (allow_shear && fabs(cb) >= fabs(sb)) ? 1 : 0;
         k.t = k.shear ? sb / cb : T(0);
         k.post = k.shear ? ipow(cb, n) : T(1);
-        T pre = T(1);
-        if (l > 0) {
-            T sp, cp;
-            sincos_full(beta[l - 1], sp, cp);
-            if (allow_shear && fabs(cp) >= fabs(sp)) pre = ipow(cp, n);
-        }
-        k.pre = pre;
+        k.pre = T(1);
         lc[l] = k;
     }
+    __syncthreads();
+    for (int l = 1 + (int)threadIdx.x; l < p; l += blockDim.x) lc[l].pre = lc[l - 1].post;
+    __syncthreads();
 }
 
 // One sub-pass: window start a, butterfly mask over the window bits, layers [la, lb]
@@ -582,19 +580,25 @@ __device__ __forceinline__ void build_tile_energy_fast(int n, int L, uint32_t zf
         }
         Eh[t] = acc;
     }
-    // E_S + El(t)
+    // E_S + El(t), and W_b(t): loops over bit positions (the same for every lane, so each Q
+    // read is a shared-memory broadcast) with predicated adds instead of loops over the set
+    // bits of t (which diverge across the warp)
     T base = T(0);
     for (uint32_t bi = zfix; bi; bi &= bi - 1u) {
         const int i = __ffs((int)bi) - 1;
         for (uint32_t bj = zfix; bj; bj &= bj - 1u) base += Qs[i * n + __ffs((int)bj) - 1];
     }
-    for (uint32_t bi = t; bi; bi &= bi - 1u) {
-        const int i = __ffs((int)bi) - 1;
-        for (uint32_t bj = t; bj; bj &= bj - 1u) base += Qs[i * n + __ffs((int)bj) - 1];
+    for (int i = 0; i < B; ++i) {
+        const bool ti = (t >> i) & 1u;
+        T si = Qs[i * n + i];
         for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
             const int j = __ffs((int)bj) - 1;
-            base += Qs[i * n + j] + Qs[j * n + i];
+            si += Qs[i * n + j] + Qs[j * n + i];
         }
+        T cross = T(0);
+        for (int j = 0; j < i; ++j)
+            if ((t >> j) & 1u) cross += Qs[i * n + j] + Qs[j * n + i];
+        if (ti) base += si + cross;
     }
     T X[1 << HB];
     X[0] = T(0);
@@ -602,10 +606,8 @@ __device__ __forceinline__ void build_tile_energy_fast(int n, int L, uint32_t zf
     for (int b = 0; b < HB; ++b) {
         T w = T(0);
         const int q = B + b;
-        for (uint32_t bi = t; bi; bi &= bi - 1u) {
-            const int i = __ffs((int)bi) - 1;
-            w += Qs[i * n + q] + Qs[q * n + i];
-        }
+        for (int i = 0; i < B; ++i)
+            if ((t >> i) & 1u) w += Qs[i * n + q] + Qs[q * n + i];
 #pragma unroll
         for (int m = 0; m < (1 << b); ++m) X[m | (1 << b)] = X[m] + w;
     }
