@@ -623,9 +623,11 @@ __device__ __forceinline__ void build_tile_energy_fast(int n, int L, uint32_t zf
 }
 
 // Energies of the tile (fast path when blockDim = 2^(L - HB), HB <= 5), and optionally the
-// fused start of the state (see FusedInit). Returns true if the state was started.
+// fused start of the state (see FusedInit). Returns true if the state was started. Not
+// inlined: its 2^HB register subset sums would otherwise add to the register pressure of the
+// whole calling kernel (spills there cost more than the call).
 template <typename T>
-__device__ __forceinline__ bool build_tile_energy_any(int n, int L, uint32_t zfix, const T* Qs,
+__device__ __noinline__ bool build_tile_energy_any(int n, int L, uint32_t zfix, const T* Qs,
                                                       T* E, T* scratch, const FusedInit<T>& fi) {
     const int lg = 31 - __clz((int)blockDim.x);
     switch (L - lg) {
