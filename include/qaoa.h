@@ -105,6 +105,26 @@ qaoa_status qaoa_expect(qaoa_ctx* ctx, int n, const void* psi, const float* E, d
 qaoa_status qaoa_topk(qaoa_ctx* ctx, int n, const void* psi, int k, uint64_t* idx, double* prob,
                       qaoa_stream_t stream);
 
+/* <C> and top-k of a complex64 state, like qaoa_expect and qaoa_topk together, for callers that
+ * cannot allocate device memory: code whose device memory is owned by another allocator or a
+ * fixed budget (a host framework's memory pool, where an extra cudaMalloc fragments or exceeds
+ * it), latency-critical loops that must not pay for cudaMalloc's implicit synchronisation, and
+ * thin callers that hold no qaoa_ctx (and so no workspace). It needs no context and allocates
+ * nothing: its scratch, the per-block partial sums and top-k lists (at most 1024 blocks x 16
+ * entries, about 200 KB), is one fixed array inside the library, reserved on every GPU that
+ * loads the library and held until the process exits. The paper has no counterpart.
+ *   n: 1..30 (larger n is rejected with QAOA_E_INVALID); k: 0..16 and <= 2^n (0: no top-k);
+ *   psi: 2^n complex64, E: 2^n floats (may be NULL when expect is NULL); expect: one double;
+ *   idx: k uint64, prob: k doubles (may be NULL); all device pointers. Same results and order
+ *   rules as qaoa_expect / qaoa_topk. Async on `stream`.
+ * The first call on a device looks up the array's device address with that device current;
+ * make that first call before any stream capture. Every call uses the same array, which keeps
+ * the last call's contents (each call writes every slot before reading it, so nothing needs
+ * clearing); calls whose work overlaps on the GPU (other streams, other host threads) race on it
+ * and must be ordered by the caller. */
+qaoa_status qaoa_expect_topk_static(int n, const void* psi, const float* E, int k, double* expect,
+                                    uint64_t* idx, double* prob, qaoa_stream_t stream);
+
 /* Adjoint gradient of <C> from |+> through p layers (the reverse state-vector sweep):
  * expect (1 double, may be NULL), dgamma[p], dbeta[p] doubles (device). Uses workspace for the
  * forward and adjoint states when n exceeds the shared-memory tier. */

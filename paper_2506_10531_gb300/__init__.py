@@ -31,6 +31,7 @@ EXPORTS = [
     "qaoa_batch_run", "qaoa_batch_run_z", "qaoa_plain_solve",
     "dqaoa_draw_indices", "dqaoa_decompose", "dqaoa_subqubo_build", "dqaoa_merge",
     "qaoa_plan_set_timing", "qaoa_plan_kernel_times", "qaoa_plan_kernel_bytes",
+    "qaoa_expect_topk_static",
     "dqaoa_session_create", "dqaoa_session_cycle", "dqaoa_session_results", "dqaoa_session_plan",
     "dqaoa_session_destroy",
 ]
@@ -83,6 +84,7 @@ def _declare(L):
     L.qaoa_workspace_bytes.argtypes = [i32, i32]
     L.qaoa_workspace_bytes.restype = sz
     L.qaoa_set_tier.argtypes = [vp, i32, i32, i32]
+    L.qaoa_expect_topk_static.argtypes = [i32, vp, vp, i32, vp, vp, vp, vp]
     for suf in ("", "_z"):
         getattr(L, "qaoa_build_energies" + suf).argtypes = [vp, i32, vp, vp, vp]
         getattr(L, "qaoa_run_layers" + suf).argtypes = [vp, i32, i32, vp, vp, vp, vp, i32, vp]
@@ -344,3 +346,9 @@ def qaoa_plan_kernel_bytes(plan, max_kernels=256):
 
 def qaoa_set_tier(ctx, n, tier, param=0):
     _check(lib().qaoa_set_tier(ctx, n, tier, param))
+
+
+def qaoa_expect_topk_static(n, psi, E, k, expect, idx, prob, stream=None):
+    """<C> and top-k without a context or any allocation (fixed scratch inside the library)."""
+    _check(lib().qaoa_expect_topk_static(n, ptr(psi), ptr(E), k, ptr(expect), ptr(idx), ptr(prob),
+                                         stream_ptr(stream)))

@@ -199,6 +199,8 @@ qaoa_status grad_t(qaoa_ctx* c, int n, int p, const T* gamma, const T* beta, con
 
 }  // namespace
 
+qaoa_status qaoa::report(qaoa_status s, const char* msg) { return fail(s, "%s", msg); }
+
 // =============================================================================================
 // Context
 // =============================================================================================

@@ -4,7 +4,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/qaoa.h"
+
 namespace qaoa {
+
+// Record `msg` as the calling thread's last error (qaoa_last_error) and return s.
+qaoa_status report(qaoa_status s, const char* msg);
 
 enum InstFlags : int {
     F_GRAD = 1,       // run the adjoint sweep (d<C>/d gamma, d<C>/d beta)
