@@ -78,7 +78,7 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     // ---- shared -> HBM (16-byte accesses on both sides). Between passes the state stays in
     // the rotated frame; the last pass converts back with (-i)^{|z|} (|z| = |tau| + |u|: the
     // tile map only permutes bits). ----
-    if (!P.fin) {
+    if (!P.fin || P.keep_frame) {
         for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
             const uint4 w = *reinterpret_cast<const uint4*>(&s.psi[swz<T>(u)]);
             *reinterpret_cast<uint4*>(gpsi + global_index(P, tau, u)) = w;
@@ -182,6 +182,128 @@ __global__ void __launch_bounds__(256) k_stream_finalize(const StreamInst<T>* __
                 if (I.topk_idx) I.topk_idx[lane] = (uint64_t)f.z;
                 if (I.topk_prob) I.topk_prob[lane] = f.p;
             }
+        }
+    }
+}
+
+// ---- adjoint passes -----------------------------------------------------------------------
+// The forward pass P undone on a tile of psi and lam (both in the rotated frame), with the
+// gradient accumulations of the tile engine's adjoint sub-passes: the local snake of P with
+// RB_ADJ-bit windows, run in reverse. Per tile, four partial sums are written (as FP64):
+//   [0] Im <lam|B|psi> of layer lb, [1] of layer la (lb > la), [2] Im <lam|E|psi> of layer lb,
+//   [3] of layer la -- zero where the pass holds no such operation.
+template <typename T, int RA>
+__device__ void stream_adj_tile(const StreamPass& P, int si, bool lam_first, bool store,
+                                const StreamInst<T>& I, uint64_t tau, const StreamSmem<T>& s,
+                                typename Num<T>::C* slam) {
+    using C = typename Num<T>::C;
+    const uint32_t TD = 1u << P.tb;
+    C* gpsi = reinterpret_cast<C*>(I.psi);
+    C* glam = reinterpret_cast<C*>(I.lam);
+    constexpr uint32_t PAIR = sizeof(C) == 8 ? 2u : 1u;
+    for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
+        const uint64_t gz = global_index(P, tau, u);
+        cp_async16(&s.psi[swz<T>(u)], gpsi + gz);
+        if (!lam_first) cp_async16(&slam[swz<T>(u)], glam + gz);
+    }
+    constexpr uint32_t EP = 8u / sizeof(T);
+    for (uint32_t u = EP * threadIdx.x; u < TD; u += EP * blockDim.x)
+        cp_async8(&s.E[swz<T>(u)], I.E + global_index(P, tau, u));
+    cp_async_wait_all();
+    __syncthreads();
+    const TileRef<T> tile{s.psi, slam, s.E, P.tb};
+    const int m0 = (P.kind == 0) ? 0 : P.c;
+    const int G = num_windows(m0, P.tb, RA);
+    const int nl = P.lb - P.la + 1;
+    const int S = snake_len(G, nl);
+    T ab[2] = {T(0), T(0)}, ag[2] = {T(0), T(0)};
+    for (int k = S - 1; k >= 0; --k) {
+        SubPass sp;
+        snake_step(k, G, nl, P.la, P.ph_first, m0, P.tb, P.tb, RA, sp);
+        subpass_adj<T, RA>(tile, sp, s.lc, lam_first && k == S - 1, ab, ag);
+        __syncthreads();
+    }
+    double* out = I.part_grad + ((uint64_t)si << (P.n - P.tb)) * 4 + tau * 4;
+    const double v0 = block_sum((double)ab[0], s.red);
+    const double v1 = block_sum((double)ab[1], s.red);
+    const double v2 = block_sum((double)ag[0], s.red);
+    const double v3 = block_sum((double)ag[1], s.red);
+    if (threadIdx.x == 0) { out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; }
+    if (store) {
+        for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
+            const uint64_t gz = global_index(P, tau, u);
+            *reinterpret_cast<uint4*>(gpsi + gz) = *reinterpret_cast<const uint4*>(&s.psi[swz<T>(u)]);
+            *reinterpret_cast<uint4*>(glam + gz) = *reinterpret_cast<const uint4*>(&slam[swz<T>(u)]);
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_adj_pass(const StreamPass P, int si, int lam_first,
+                                                         int store,
+                                                         const StreamInst<T>* __restrict__ insts,
+                                                         int count, const StreamInst<T> one) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    using C = typename Num<T>::C;
+    const uint32_t TD = 1u << P.tb;
+    StreamSmem<T> s;
+    size_t o = 0;
+    s.psi = reinterpret_cast<C*>(sm + o); o += (size_t)TD * sizeof(C);
+    C* slam = reinterpret_cast<C*>(sm + o); o += (size_t)TD * sizeof(C);
+    s.E = reinterpret_cast<T*>(sm + o); o += (size_t)TD * sizeof(T);
+    s.lc = reinterpret_cast<LayerConst<T>*>(sm + o); o += 64 * sizeof(LayerConst<T>);
+    o = (o + 15) & ~(size_t)15;
+    s.red = reinterpret_cast<double*>(sm + o);
+    const uint64_t ntiles = 1ull << (P.n - P.tb);
+    const uint64_t total = ntiles * (uint64_t)count;
+    int cur = -1;
+    for (uint64_t b = blockIdx.x; b < total; b += gridDim.x) {
+        const int ii = (int)(b / ntiles);
+        const uint64_t tau = b % ntiles;
+        const StreamInst<T>& I = insts ? insts[ii] : one;
+        if (ii != cur) {
+            __syncthreads();
+            set_layer_consts<T>(s.lc, I.gamma, I.beta, I.p, P.n, false);
+            cur = ii;
+        }
+        constexpr int RA = Num<T>::RB_ADJ;
+        stream_adj_tile<T, RA>(P, si, lam_first != 0, store != 0, I, tau, s, slam);
+    }
+}
+
+// Per instance: dgamma_l = 2 sum of the gamma slots of layer l, dbeta_l = 2 sum of the beta
+// slots, over passes in order and tiles in fixed contiguous chunks per thread.
+struct PassLayers {
+    int la[256], lb[256];
+};
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_grad_reduce(const PassLayers pl, int S,
+                                                            const StreamInst<T>* __restrict__ insts,
+                                                            int count, uint64_t ntiles,
+                                                            const StreamInst<T> one) {
+    __shared__ double red[32];
+    const int ii = blockIdx.x;
+    if (ii >= count) return;
+    const StreamInst<T>& I = insts ? insts[ii] : one;
+    const uint64_t per = (ntiles + blockDim.x - 1) / blockDim.x;
+    for (int l = 0; l < I.p; ++l) {
+        double gb = 0.0, gg = 0.0;
+        for (int s = 0; s < S; ++s) {
+            const bool hb = pl.lb[s] == l, ha = pl.la[s] == l && pl.lb[s] != pl.la[s];
+            if (!hb && !ha) continue;
+            const double* base = I.part_grad + ((uint64_t)s * ntiles) * 4;
+            for (uint64_t t = threadIdx.x * per; t < (threadIdx.x + 1) * per && t < ntiles; ++t) {
+                const double* q = base + t * 4;
+                if (hb) { gb += q[0]; gg += q[2]; }
+                if (ha) { gb += q[1]; gg += q[3]; }
+            }
+        }
+        const double sb = block_sum(gb, red);
+        const double sg = block_sum(gg, red);
+        if (threadIdx.x == 0) {
+            if (I.dbeta) I.dbeta[l] = 2.0 * sb;
+            if (I.dgamma) I.dgamma[l] = 2.0 * sg;
         }
     }
 }
@@ -455,6 +577,42 @@ cudaError_t launch_energy_batch(bool dbl, int n, const void* insts, int count, c
     const dim3 grid((unsigned)((threads + block - 1) / block), (unsigned)count);
     if (dbl) k_energy<double><<<grid, block, 0, st>>>(n, m, nullptr, nullptr, static_cast<const StreamInst<double>*>(insts));
     else k_energy<float><<<grid, block, 0, st>>>(n, m, nullptr, nullptr, static_cast<const StreamInst<float>*>(insts));
+    return cudaGetLastError();
+}
+
+size_t stream_adj_smem_bytes(bool dbl) {
+    const size_t TD = (size_t)1 << stream_tile_bits(dbl);
+    const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4;
+    const size_t lcs = dbl ? sizeof(LayerConst<double>) : sizeof(LayerConst<float>);
+    size_t o = 2 * TD * c + TD * r + 64 * lcs;
+    o = (o + 15) & ~(size_t)15;
+    return o + 32 * sizeof(double);
+}
+
+cudaError_t launch_stream_adj_pass(bool dbl, const StreamPass& P, int si, bool lam_first, bool store,
+                                   const void* insts, int count, int grid, cudaStream_t st,
+                                   const void* one) {
+    const size_t sm = stream_adj_smem_bytes(dbl);
+    cudaError_t e;
+    if (dbl) {
+        e = cudaFuncSetAttribute(k_stream_adj_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_stream_adj_pass<double><<<grid, 256, sm, st>>>(P, si, lam_first, store, static_cast<const StreamInst<double>*>(insts), count, one_of<double>(one));
+    } else {
+        e = cudaFuncSetAttribute(k_stream_adj_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_stream_adj_pass<float><<<grid, 256, sm, st>>>(P, si, lam_first, store, static_cast<const StreamInst<float>*>(insts), count, one_of<float>(one));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_grad_reduce(bool dbl, const StreamPass* passes, int S, const void* insts,
+                                      int count, uint64_t ntiles, cudaStream_t st, const void* one) {
+    if (S > 256) return cudaErrorInvalidValue;
+    PassLayers pl;
+    for (int i = 0; i < S; ++i) { pl.la[i] = passes[i].la; pl.lb[i] = passes[i].lb; }
+    if (dbl) k_stream_grad_reduce<double><<<count, 256, 0, st>>>(pl, S, static_cast<const StreamInst<double>*>(insts), count, ntiles, one_of<double>(one));
+    else k_stream_grad_reduce<float><<<count, 256, 0, st>>>(pl, S, static_cast<const StreamInst<float>*>(insts), count, ntiles, one_of<float>(one));
     return cudaGetLastError();
 }
 

@@ -80,6 +80,18 @@ size_t reduce_scratch_bytes(int n) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Workspace of a streaming gradient: psi and lam (2^n complex each), the forward scratch and the
+// per-pass, per-tile gradient partials (4 doubles).
+size_t stream_grad_bytes(bool dbl, int n, int p) {
+    const int tb = stream_tile_bits(dbl);
+    if (n <= tb) return 0;
+    StreamPass tmp[256];
+    const int S = stream_plan(dbl, n, p, 0, tmp, 256);
+    if (S < 0) return 0;
+    const size_t D = (size_t)1 << n, nt = (size_t)1 << (n - tb), cs = dbl ? 16 : 8;
+    return 2 * align256(D * cs) + stream_scratch_bytes(dbl, n, 0) + align256((size_t)S * nt * 4 * sizeof(double));
+}
+
 qaoa_status ensure_ws(qaoa_ctx* c, size_t bytes) {
     if (bytes <= c->ws_bytes) return QAOA_OK;
     return fail(QAOA_E_NOMEM, "workspace of %zu bytes needed, %zu reserved (call qaoa_reserve)",
@@ -130,6 +142,46 @@ qaoa_status run_stream_one(qaoa_ctx* c, int n, int p, const T* gamma, const T* b
     const int grid = (int)std::min<uint64_t>(nt, (uint64_t)c->nsm * 2);
     for (int s = 0; s < S; ++s) CK(launch_stream_pass(dbl, passes[s], nullptr, 1, grid, st, &I));
     if (expect || (k > 0 && tidx)) CK(launch_stream_finalize(dbl, nullptr, 1, nt, k, st, &I));
+    return QAOA_OK;
+}
+
+template <typename T>
+qaoa_status grad_stream_one(qaoa_ctx* c, int n, int p, const T* gamma, const T* beta, const T* E,
+                            double* expect, double* dgamma, double* dbeta, cudaStream_t st) {
+    const bool dbl = is_dbl<T>();
+    qaoa_status q = ensure_ws(c, stream_grad_bytes(dbl, n, p));
+    if (q) return q;
+    StreamPass passes[256];
+    const int S = stream_plan(dbl, n, p, 0, passes, 256);
+    if (S < 0) return fail(QAOA_E_INVALID, "no streaming plan for n=%d p=%d", n, p);
+    passes[S - 1].keep_frame = 1;
+    const int tb = stream_tile_bits(dbl);
+    const uint64_t nt = 1ull << (n - tb), D = 1ull << n;
+    const size_t cs = sizeof(typename qaoa::Num<T>::C);
+    char* w = static_cast<char*>(c->ws);
+    StreamInst<T> I{};
+    I.p = p;
+    I.amp0 = exp2(-0.5 * n);
+    I.gamma = gamma;
+    I.beta = beta;
+    I.E = E;
+    I.psi = w; w += align256(D * cs);
+    I.lam = w; w += align256(D * cs);
+    I.part_expect = reinterpret_cast<double*>(w);
+    I.part_topp = reinterpret_cast<double*>(w + align256(nt * sizeof(double)));
+    I.part_topz = reinterpret_cast<uint32_t*>(w + align256(nt * sizeof(double)) + align256(nt * sizeof(double)));
+    w += stream_scratch_bytes(dbl, n, 0);
+    I.part_grad = reinterpret_cast<double*>(w);
+    I.expect = expect;
+    I.dgamma = dgamma;
+    I.dbeta = dbeta;
+    const int grid = (int)std::min<uint64_t>(nt, (uint64_t)c->nsm * 2);
+    const int agrid = (int)std::min<uint64_t>(nt, (uint64_t)c->nsm);
+    for (int s = 0; s < S; ++s) CK(launch_stream_pass(dbl, passes[s], nullptr, 1, grid, st, &I));
+    if (expect) CK(launch_stream_finalize(dbl, nullptr, 1, nt, 0, st, &I));
+    for (int s = S - 1; s >= 0; --s)
+        CK(launch_stream_adj_pass(dbl, passes[s], s, s == S - 1, s > 0, nullptr, 1, agrid, st, &I));
+    CK(launch_stream_grad_reduce(dbl, passes, S, nullptr, 1, nt, st, &I));
     return QAOA_OK;
 }
 
@@ -189,7 +241,7 @@ qaoa_status grad_t(qaoa_ctx* c, int n, int p, const T* gamma, const T* beta, con
         return fail(QAOA_E_INVALID, "grad: n=%d p=%d or NULL pointer", n, p);
     const bool dbl = is_dbl<T>();
     if (n > (dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ))
-        return fail(QAOA_E_UNSUPPORTED, "grad: n=%d above the shared-memory tier", n);
+        return grad_stream_one<T>(c, n, p, gamma, beta, E, expect, dgamma, dbeta, (cudaStream_t)stream);
     InstDesc<T> d{};
     d.n = n; d.p = p; d.k = 0; d.flags = F_GRAD;
     d.E_in = E; d.gamma = gamma; d.beta = beta;
@@ -270,7 +322,8 @@ extern "C" qaoa_status qaoa_set_tier(qaoa_ctx* c, int n, int tier, int param) {
 
 extern "C" size_t qaoa_workspace_bytes(int n, int dbl) {
     if (n < 1 || n > NMAX) return 0;
-    return std::max(stream_scratch_bytes(dbl != 0, n, KMAX), reduce_scratch_bytes(n));
+    return std::max({stream_scratch_bytes(dbl != 0, n, KMAX), reduce_scratch_bytes(n),
+                     stream_grad_bytes(dbl != 0, n, PMAX)});
 }
 
 // =============================================================================================
@@ -331,8 +384,8 @@ struct qaoa_plan {
     size_t dev_bytes = 0;
     struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
     struct CluGroup { int n, L, pmax, count; size_t desc_off; int clusters; };
-    struct StrGroup { int n, p, k, count; size_t inst_off; std::vector<StreamPass> passes; int grid;
-                      std::vector<int> e_build; std::vector<const void*> q; std::vector<void*> e; };
+    struct StrGroup { int n, p, k, count; bool grad; size_t inst_off; std::vector<StreamPass> passes;
+                      int grid, agrid; std::vector<const void*> q; std::vector<void*> e; };
     std::vector<ResGroup> res;
     std::vector<CluGroup> clu;
     std::vector<StrGroup> str;
@@ -367,8 +420,9 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             return fail(QAOA_E_INVALID, "instance %d: state at psi_off must be 16-byte aligned", i);
         if (d.e_off >= 0 && !io->e) return fail(QAOA_E_INVALID, "instance %d: energy pool NULL", i);
         if ((d.flags & QAOA_INST_GRAD) && !io->grad) return fail(QAOA_E_INVALID, "instance %d: grad pool NULL", i);
-        if ((d.flags & QAOA_INST_GRAD) && d.n > (dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ))
-            return fail(QAOA_E_UNSUPPORTED, "instance %d: gradient for n=%d above the shared-memory tier", i, d.n);
+        if ((d.flags & QAOA_INST_GRAD) && d.n > (dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ) && d.psi_off >= 0)
+            return fail(QAOA_E_UNSUPPORTED, "instance %d: the final state is returned with a gradient only for n <= %d",
+                        i, dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ);
     }
     qaoa_plan* P = new qaoa_plan();
     P->ctx = c;
@@ -376,15 +430,16 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     // group: resident by (n, grad); streaming by (n, p, k)
     std::map<std::pair<int, int>, std::vector<int>> rg;
     std::map<int, std::vector<int>> cg;
-    std::map<std::tuple<int, int, int>, std::vector<int>> sg;
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> sg;
     const int nres = dbl ? RES_NMAX_D : RES_NMAX_F;
+    const int nres_adj = dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ;
     for (int i = 0; i < count; ++i) {
         const qaoa_inst& d = desc[i];
         const bool grad = (d.flags & QAOA_INST_GRAD) != 0;
-        if (d.n <= nres) rg[{d.n, grad ? 1 : 0}].push_back(i);
+        if (d.n <= nres && (!grad || d.n <= nres_adj)) rg[{d.n, grad ? 1 : 0}].push_back(i);
         else if (!dbl && !grad && d.n >= CL_NMIN && d.n <= CL_NMAX && c->tier[d.n] != QAOA_TIER_STREAM)
             cg[d.n].push_back(i);
-        else sg[{d.n, d.p, d.k}].push_back(i);
+        else sg[{d.n, d.p, d.k, grad ? 1 : 0}].push_back(i);
     }
     auto make_desc = [&](int i) {
         const qaoa_inst& d = desc[i];
@@ -450,7 +505,7 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     }
     if (qslot > 60) { delete P; return fail(QAOA_E_UNSUPPORTED, "too many resident groups"); }
     // streaming: per instance its own E / psi / partial buffers inside the plan block
-    struct SI { size_t e_off, psi_off, part_off; };
+    struct SI { size_t e_off, psi_off, part_off, lam_off, grad_off; };
     std::vector<std::vector<SI>> sinfo;
     const int tb = stream_tile_bits(dbl);
     for (auto& kv : sg) {
@@ -458,10 +513,12 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         g.n = std::get<0>(kv.first);
         g.p = std::get<1>(kv.first);
         g.k = std::get<2>(kv.first);
+        g.grad = std::get<3>(kv.first) != 0;
         g.count = (int)kv.second.size();
         StreamPass tmp[256];
         const int S = stream_plan(dbl, g.n, g.p, g.k, tmp, 256);
         if (S < 0) { delete P; return fail(QAOA_E_INVALID, "no streaming plan for n=%d p=%d", g.n, g.p); }
+        if (g.grad) tmp[S - 1].keep_frame = 1;
         g.passes.assign(tmp, tmp + S);
         g.inst_off = bytes;
         bytes = align256(bytes + sizeof(StreamInst<T>) * g.count);
@@ -478,10 +535,18 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             bytes = align256(bytes + nt * sizeof(double));
             bytes = align256(bytes + nt * std::max(g.k, 1) * sizeof(double));
             bytes = align256(bytes + nt * std::max(g.k, 1) * sizeof(uint32_t));
+            s.lam_off = s.grad_off = 0;
+            if (g.grad) {
+                s.lam_off = bytes;
+                bytes = align256(bytes + D * sizeof(C2));
+                s.grad_off = bytes;
+                bytes = align256(bytes + (size_t)S * nt * 4 * sizeof(double));
+            }
             v.push_back(s);
         }
         const uint64_t tiles = nt * (uint64_t)g.count;
         g.grid = (int)std::min<uint64_t>(tiles, (uint64_t)c->nsm * 2);
+        g.agrid = (int)std::min<uint64_t>(tiles, (uint64_t)c->nsm);
         sinfo.push_back(v);
         P->str.push_back(std::move(g));
     }
@@ -532,13 +597,19 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             I.expect = io->expect ? io->expect + i : nullptr;
             I.topk_idx = d.k > 0 ? io->topk_idx + (int64_t)i * io->k_stride : nullptr;
             I.topk_prob = (d.k > 0 && io->topk_prob) ? io->topk_prob + (int64_t)i * io->k_stride : nullptr;
+            if (g.grad) {
+                I.lam = base + s.lam_off;
+                I.part_grad = reinterpret_cast<double*>(base + s.grad_off);
+                I.dgamma = io->grad + d.par_off;
+                I.dbeta = io->grad + d.par_off + d.p;
+            }
             si.push_back(I);
             g.q.push_back(qpool + d.q_off);
             g.e.push_back(Ebuf);
         }
         e = cudaMemcpy(base + g.inst_off, si.data(), sizeof(StreamInst<T>) * g.count, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload stream instances"); }
-        P->kernels += 1 + (int)g.passes.size() + 1;
+        P->kernels += 1 + (int)g.passes.size() + 1 + (g.grad ? (int)g.passes.size() + 1 : 0);
         ++gi;
     }
     // algorithmic bytes, in the order qaoa_plan_launch issues the kernels
@@ -573,6 +644,13 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         for (auto& pass : g.passes)
             P->bytes.push_back(cnt * D * ((pass.init ? 0.0 : sizeof(C2)) + sizeof(C2) + (pass.need_e ? sizeof(T) : 0.0)));
         P->bytes.push_back(cnt * (nt * (sizeof(double) + std::max(g.k, 1) * 12.0) + 8.0 + g.k * 16.0));
+        if (g.grad) {
+            const int S = (int)g.passes.size();
+            for (int s = S - 1; s >= 0; --s)   // psi and lam read (lam formed in the first), E read, both written back
+                P->bytes.push_back(cnt * D * ((s == S - 1 ? 1.0 : 2.0) * sizeof(C2) + sizeof(T) +
+                                              (s > 0 ? 2.0 * sizeof(C2) : 0.0)));
+            P->bytes.push_back(cnt * (double)S * nt * 32.0);
+        }
     }
     *out = P;
     return QAOA_OK;
@@ -634,6 +712,18 @@ extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
         CK(timed("stream_finalize", [&] {
             return launch_stream_finalize(P->dbl, base + g.inst_off, g.count, 1ull << (g.n - tb), g.k, st);
         }));
+        if (g.grad) {
+            const int S = (int)g.passes.size();
+            for (int s = S - 1; s >= 0; --s)
+                CK(timed("stream_adjoint", [&] {
+                    return launch_stream_adj_pass(P->dbl, g.passes[s], s, s == S - 1, s > 0, base + g.inst_off,
+                                                  g.count, g.agrid, st);
+                }));
+            CK(timed("stream_grad_reduce", [&] {
+                return launch_stream_grad_reduce(P->dbl, g.passes.data(), S, base + g.inst_off, g.count,
+                                                 1ull << (g.n - tb), st);
+            }));
+        }
     }
     return QAOA_OK;
 }

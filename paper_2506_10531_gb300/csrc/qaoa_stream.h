@@ -17,6 +17,7 @@ struct StreamPass {
     int fin;        // last pass: per-tile <C> partials and top-k candidates
     int k;          // top-k length when fin
     int need_e;     // the pass reads the energies
+    int keep_frame; // fin pass of a gradient run: leave psi in the rotated frame for the adjoint
 };
 
 // One instance of a streaming launch (device pointers).
@@ -35,6 +36,11 @@ struct StreamInst {
     double* expect;
     uint64_t* topk_idx;
     double* topk_prob;
+    // adjoint (gradient runs only)
+    void* lam;            // 2^n complex adjoint state in HBM
+    double* part_grad;    // passes * 2^(n - tb) * 4 per-tile partials
+    double* dgamma;       // p
+    double* dbeta;        // p
 };
 
 int stream_tile_bits(bool dbl);
@@ -46,6 +52,16 @@ cudaError_t launch_stream_pass(bool dbl, const StreamPass& P, const void* insts,
                                int grid, cudaStream_t st, const void* one = nullptr);
 cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint64_t ntiles, int k,
                                    cudaStream_t st, const void* one = nullptr);
+// Adjoint pass `si` (the forward pass P run backwards on psi and lam): lam_first forms
+// lam = E psi on load, store == 0 skips writing the states back (last adjoint pass).
+cudaError_t launch_stream_adj_pass(bool dbl, const StreamPass& P, int si, bool lam_first, bool store,
+                                   const void* insts, int count, int grid, cudaStream_t st,
+                                   const void* one = nullptr);
+// Sum the per-tile gradient partials of the S passes into dgamma / dbeta (fixed order).
+cudaError_t launch_stream_grad_reduce(bool dbl, const StreamPass* passes, int S, const void* insts,
+                                      int count, uint64_t ntiles, cudaStream_t st,
+                                      const void* one = nullptr);
+size_t stream_adj_smem_bytes(bool dbl);
 cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st);
 // Energies of `count` streaming instances (E written through insts[i].E from insts[i].Q).
 cudaError_t launch_energy_batch(bool dbl, int n, const void* insts, int count, cudaStream_t st);

@@ -65,7 +65,7 @@ def run_batch(q, ctx, specs, seed, order=None):
 
 SPECS = [(3, 2, 4, True), (9, 3, 8, True), (14, 2, 8, False), (12, 1, 16, True), (15, 2, 8, False),
          (17, 3, 8, False), (14, 3, 8, False), (5, 8, 8, True), (13, 2, 1, True), (16, 1, 8, False),
-         (18, 2, 8, False), (16, 3, 8, False)]
+         (18, 2, 8, False), (16, 3, 8, False), (14, 2, 8, True), (16, 2, 4, True)]
 
 
 def test_batch_matches_oracle(q, ctx, orc):

@@ -29,7 +29,7 @@ def q():
 @pytest.fixture(scope="module")
 def ctx(q):
     c = q.qaoa_create(0)
-    q.qaoa_reserve(c, q.qaoa_workspace_bytes(30))
+    q.qaoa_reserve(c, q.qaoa_workspace_bytes(22))
     yield c
     q.qaoa_destroy(c)
 
@@ -132,8 +132,9 @@ def test_complex128_layers(q, ctx, orc, n, p):
     assert out.item() == pytest.approx(orc.expect(psi_o, E_o), abs=1e-11 * np.abs(Q).sum())
 
 
-@pytest.mark.parametrize("n,p", [(1, 1), (3, 2), (7, 3), (10, 2), (13, 4)])
-def test_resident_grad(q, ctx, orc, n, p):
+@pytest.mark.parametrize("n,p", [(1, 1), (3, 2), (7, 3), (10, 2), (13, 4), (14, 2), (15, 3), (17, 2),
+                                 (20, 1)])
+def test_grad_vs_oracle(q, ctx, orc, n, p):
     Q = synth.symmetric_q(n, seed=7000 + n, dist="normal")
     Q32 = Q.astype(np.float32)
     Qd = Q32.astype(np.float64)
@@ -155,8 +156,8 @@ def test_resident_grad(q, ctx, orc, n, p):
     assert np.max(np.abs(got - ref)) <= 1e-5 * max(np.max(np.abs(ref)), 1.0) * max(1.0, n / 4)
 
 
-def test_grad_complex128(q, ctx, orc):
-    n, p = 9, 3
+@pytest.mark.parametrize("n,p", [(9, 3), (14, 2)])
+def test_grad_complex128(q, ctx, orc, n, p):
     Q = synth.symmetric_q(n, seed=71)
     g, b = synth.random_params(p, seed=72)
     E = torch.empty(1 << n, dtype=torch.float64, device="cuda")
