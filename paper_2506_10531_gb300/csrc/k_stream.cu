@@ -216,11 +216,22 @@ __device__ void stream_adj_tile(const StreamPass& P, int si, bool lam_first, boo
     const int G = num_windows(m0, P.tb, RA);
     const int nl = P.lb - P.la + 1;
     const int S = snake_len(G, nl);
+    // tile accumulators by the pass's layer slot (0: layer lb, 1: layer la); a local
+    // sub-pass reports relative to its own last layer, mapped here
     T ab[2] = {T(0), T(0)}, ag[2] = {T(0), T(0)};
     for (int k = S - 1; k >= 0; --k) {
         SubPass sp;
         snake_step(k, G, nl, P.la, P.ph_first, m0, P.tb, P.tb, RA, sp);
-        subpass_adj<T, RA>(tile, sp, s.lc, lam_first && k == S - 1, ab, ag);
+        T lb_[2] = {T(0), T(0)}, lg_[2] = {T(0), T(0)};
+        subpass_adj<T, RA>(tile, sp, s.lc, lam_first && k == S - 1, lb_, lg_);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int slot = P.lb - (sp.lb - j);
+            if (j <= sp.lb - sp.la) {
+                if (slot == 0) { ab[0] += lb_[j]; ag[0] += lg_[j]; }
+                else { ab[1] += lb_[j]; ag[1] += lg_[j]; }
+            }
+        }
         __syncthreads();
     }
     double* out = I.part_grad + ((uint64_t)si << (P.n - P.tb)) * 4 + tau * 4;
