@@ -209,6 +209,15 @@ qaoa_status qaoa_batch_run(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
 qaoa_status qaoa_batch_run_z(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
                              const qaoa_batch_io* io, qaoa_stream_t stream);
 
+/* One Adam step (Kingma & Ba 2015) on `count` parameters, the optimiser that replaces the
+ * paper's COBYLA outer loop (Section IV): theta (floats, in/out), grad (doubles, e.g. the grad
+ * pool of a batch with QAOA_INST_GRAD), m and v (floats, in/out, zero before step 1), all device;
+ * step >= 1 is the 1-based step number used for bias correction. minimise != 0 descends <C>.
+ * Async on `stream`. */
+qaoa_status qaoa_adam_step(int count, float* theta, const double* grad, float* m, float* v,
+                           int step, float lr, float beta1, float beta2, float eps, int minimise,
+                           qaoa_stream_t stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Reference "plain" GPU path: one instance per call, one kernel per gate (cost phase, one    */
 /* kernel per qubit for the mixer) and a separate reduction. The comparison point of the     */

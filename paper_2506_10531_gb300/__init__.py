@@ -31,7 +31,7 @@ EXPORTS = [
     "qaoa_batch_run", "qaoa_batch_run_z", "qaoa_plain_solve",
     "dqaoa_draw_indices", "dqaoa_decompose", "dqaoa_subqubo_build", "dqaoa_merge",
     "qaoa_plan_set_timing", "qaoa_plan_kernel_times", "qaoa_plan_kernel_bytes",
-    "qaoa_expect_topk_static",
+    "qaoa_expect_topk_static", "qaoa_adam_step",
     "dqaoa_session_create", "dqaoa_session_cycle", "dqaoa_session_results", "dqaoa_session_plan",
     "dqaoa_session_destroy",
 ]
@@ -84,6 +84,8 @@ def _declare(L):
     L.qaoa_workspace_bytes.argtypes = [i32, i32]
     L.qaoa_workspace_bytes.restype = sz
     L.qaoa_set_tier.argtypes = [vp, i32, i32, i32]
+    L.qaoa_adam_step.argtypes = [i32, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float,
+                                 i32, vp]
     L.qaoa_expect_topk_static.argtypes = [i32, vp, vp, i32, vp, vp, vp, vp]
     for suf in ("", "_z"):
         getattr(L, "qaoa_build_energies" + suf).argtypes = [vp, i32, vp, vp, vp]
@@ -352,3 +354,9 @@ def qaoa_expect_topk_static(n, psi, E, k, expect, idx, prob, stream=None):
     """<C> and top-k without a context or any allocation (fixed scratch inside the library)."""
     _check(lib().qaoa_expect_topk_static(n, ptr(psi), ptr(E), k, ptr(expect), ptr(idx), ptr(prob),
                                          stream_ptr(stream)))
+
+
+def qaoa_adam_step(count, theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, minimise=True,
+                   stream=None):
+    _check(lib().qaoa_adam_step(count, ptr(theta), ptr(grad), ptr(m), ptr(v), step, lr, beta1, beta2, eps,
+                                int(minimise), stream_ptr(stream)))

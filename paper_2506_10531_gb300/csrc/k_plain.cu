@@ -65,3 +65,29 @@ cudaError_t launch_plain_layers(int n, int p, const float* gamma, const float* b
 }
 
 }  // namespace qaoa
+
+// ---- Adam update of QAOA parameters (Kingma & Ba 2015) --------------------------------------
+namespace qaoa {
+namespace {
+__global__ void k_adam(int count, float* __restrict__ theta, const double* __restrict__ grad,
+                       float* __restrict__ m, float* __restrict__ v, int step, float lr, float b1,
+                       float b2, float eps, int minimise) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float g = minimise ? (float)grad[i] : -(float)grad[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.0f - powf(b1, (float)step));
+    const float vh = vi / (1.0f - powf(b2, (float)step));
+    theta[i] -= lr * mh / (sqrtf(vh) + eps);
+}
+}  // namespace
+
+cudaError_t launch_adam(int count, float* theta, const double* grad, float* m, float* v, int step,
+                        float lr, float b1, float b2, float eps, int minimise, cudaStream_t st) {
+    k_adam<<<(count + 255) / 256, 256, 0, st>>>(count, theta, grad, m, v, step, lr, b1, b2, eps, minimise);
+    return cudaGetLastError();
+}
+}  // namespace qaoa

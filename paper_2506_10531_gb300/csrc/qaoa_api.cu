@@ -787,6 +787,17 @@ extern "C" qaoa_status qaoa_batch_run_z(qaoa_ctx* c, const qaoa_inst* d, int n, 
     return batch_run(c, d, n, io, s, 1);
 }
 
+extern "C" qaoa_status qaoa_adam_step(int count, float* theta, const double* grad, float* m, float* v,
+                                      int step, float lr, float b1, float b2, float eps, int minimise,
+                                      qaoa_stream_t stream) {
+    if (count < 0 || (count > 0 && (!theta || !grad || !m || !v)) || step < 1 || !(lr > 0.0f) ||
+        !(b1 >= 0.0f && b1 < 1.0f) || !(b2 >= 0.0f && b2 < 1.0f) || !(eps > 0.0f))
+        return fail(QAOA_E_INVALID, "adam_step: bad arguments");
+    if (count == 0) return QAOA_OK;
+    CK(launch_adam(count, theta, grad, m, v, step, lr, b1, b2, eps, minimise, (cudaStream_t)stream));
+    return QAOA_OK;
+}
+
 // =============================================================================================
 // Plain path
 // =============================================================================================

@@ -128,3 +128,23 @@ def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
 # Config of the DQAOA batch cycle: dense N=1000 QUBO, 256 sub-QUBOs of 16 variables, p=3.
 DQAOA_BATCH = dict(seed=2, N=1000, m=256, k=16, p=3,
                    gamma=(0.2, 0.4, 0.6), beta=(0.6, 0.4, 0.2), topk=8)
+
+
+def uneven_batch(count: int, seed: int, n_lo: int, n_hi: int, p_lo: int, p_hi: int,
+                 dist: str = "normal"):
+    """Instances of an uneven batch: (n, p) from uneven_mix, instance i's Q from the stream seeded
+    with output i of the seed's own sequence, and its initial (gamma, beta) from random_params
+    seeded with that value XOR 0x5151."""
+    ns, ps = uneven_mix(count, seed, n_lo, n_hi, p_lo, p_hi)
+    seeds = splitmix64(seed ^ 0xA5A5A5A5, count)
+    out = []
+    for i in range(count):
+        s = int(seeds[i])
+        g, b = random_params(int(ps[i]), s ^ 0x5151)
+        out.append((symmetric_q(int(ns[i]), s, dist), g, b))
+    return out
+
+
+# Config of the uneven training batch: 4096 instances, n in 8..24, p in 1..6, normal Q,
+# 20 Adam steps at learning rate 0.05.
+UNEVEN_BATCH = dict(seed=3, count=4096, n=(8, 24), p=(1, 6), dist="normal", steps=20, lr=0.05)
