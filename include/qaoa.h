@@ -162,7 +162,7 @@ typedef struct {
     int64_t par_off;  /* gamma[p] then beta[p] at io->params + par_off; gradients at the same
                          offsets in io->grad */
     int64_t psi_off;  /* final state (2^n complex) at io->psi + psi_off, or -1: not returned */
-    int64_t e_off;    /* energies (2^n) at io->e + e_off, or -1: not returned */
+    int64_t e_off;    /* energies (2^n) at io->e + e_off (8-byte aligned), or -1: not returned */
 } qaoa_inst;
 
 typedef struct {

@@ -319,6 +319,116 @@ __global__ void __launch_bounds__(256) k_stream_grad_reduce(const PassLayers pl,
     }
 }
 
+// ---- energy build into HBM, row form (n >= 2) ------------------------------------------
+// E(z) = sum_i Q_ii z_i + sum_{i<j} W_ij z_i z_j with W_ij = Q_ij + Q_ji (Q need not be
+// symmetric). Split z = (hi, lo) with hi the top nh bits and m = n - nh. A thread fixes lo up to
+// its two lowest bits and holds the four energies E(hi, lo | v), v = 0..3, and the cross fields
+//   P_h(lo | v) = sum_{j in lo|v} W_{m+h, j}              (h < nh),
+// then walks hi in Gray-code order: flipping bit b of hi changes every energy by
+//   s * (P_b(lo|v) + Q_{b'b'} + sum_{j in hi, j != b} W_{b'j'})   (s = +1 setting, -1 clearing;
+// primes: positions m + b, m + j). The hi-only part depends on the step alone, so a table D[k]
+// of it (sign included) is built once per block; each step costs one select, eight adds and one
+// 16-byte (float) or two (double) stores of four consecutive energies. The walk is at most 2^8
+// steps, which bounds the FP32 rounding drift of the running sums.
+constexpr int ROWS_NH_MAX = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_energy_rows(int n, int nh, const T* __restrict__ Q,
+                                                     T* __restrict__ E, const StreamInst<T>* insts) {
+    __shared__ T W[32 * 32];
+    __shared__ T D[1 << ROWS_NH_MAX];
+    if (insts) {
+        Q = insts[blockIdx.y].Q;
+        E = const_cast<T*>(insts[blockIdx.y].E);
+    }
+    for (int x = threadIdx.x; x < n * n; x += blockDim.x) {
+        const int i = x / n, j = x - i * n;
+        W[x] = (i == j) ? Q[x] : Q[x] + Q[j * n + i];
+    }
+    __syncthreads();
+    const int m = n - nh;
+    const int steps = 1 << nh;
+    for (int k = 1 + threadIdx.x; k < steps; k += blockDim.x) {
+        const int b = __ffs(k) - 1;
+        const uint32_t g = (uint32_t)(k - 1) ^ ((uint32_t)(k - 1) >> 1);   // hi before the flip
+        const T* row = W + (m + b) * n + m;
+        T d = row[b];
+        for (int j = 0; j < nh; ++j)
+            if (j != b && ((g >> j) & 1u)) d += row[j];
+        D[k] = ((g >> b) & 1u) ? -d : d;
+    }
+    __syncthreads();
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (1ull << (m - 2))) return;
+    const uint32_t base = (uint32_t)gid << 2;
+    // exact energies of lo = base | v at hi = 0
+    T eb = T(0), f0 = W[0], f1 = W[n + 1];
+    for (int i = 2; i < m; ++i) {
+        if (!((base >> i) & 1u)) continue;
+        const T* row = W + i * n;
+        T r = row[i];
+        for (int j = 2; j < i; ++j)
+            if ((base >> j) & 1u) r += row[j];
+        eb += r;
+        f0 += row[0];
+        f1 += row[1];
+    }
+    T e[4] = {eb, eb + f0, eb + f1, eb + f0 + f1 + W[1]};
+    T P[ROWS_NH_MAX][4];
+#pragma unroll
+    for (int h = 0; h < ROWS_NH_MAX; ++h) {
+        if (h < nh) {
+            const T* row = W + (m + h) * n;
+            T pb = T(0);
+            for (int j = 2; j < m; ++j)
+                if ((base >> j) & 1u) pb += row[j];
+            P[h][0] = pb;
+            P[h][1] = pb + row[0];
+            P[h][2] = pb + row[1];
+            P[h][3] = pb + row[0] + row[1];
+        } else {
+            P[h][0] = P[h][1] = P[h][2] = P[h][3] = T(0);
+        }
+    }
+    // E is 8-byte aligned (checked when the plan is made); 16-byte stores where it is 16-aligned
+    const bool v16 = (reinterpret_cast<uintptr_t>(E) & 15u) == 0;
+    auto put = [&](uint32_t hi) {
+        T* dst = E + (((uint64_t)hi << m) | base);
+        if constexpr (sizeof(T) == 4) {
+            if (v16) {
+                *reinterpret_cast<float4*>(dst) = make_float4(e[0], e[1], e[2], e[3]);
+            } else {
+                reinterpret_cast<float2*>(dst)[0] = make_float2(e[0], e[1]);
+                reinterpret_cast<float2*>(dst)[1] = make_float2(e[2], e[3]);
+            }
+        } else {
+            if (v16) {
+                reinterpret_cast<double2*>(dst)[0] = make_double2(e[0], e[1]);
+                reinterpret_cast<double2*>(dst)[1] = make_double2(e[2], e[3]);
+            } else {
+                dst[0] = e[0]; dst[1] = e[1]; dst[2] = e[2]; dst[3] = e[3];
+            }
+        }
+    };
+    put(0u);
+    uint32_t hi = 0;
+    for (int k = 1; k < steps; ++k) {
+        const int b = __ffs(k) - 1;
+        hi ^= 1u << b;
+        T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+#pragma unroll
+        for (int h = 0; h < ROWS_NH_MAX; ++h)
+            if (h == b) { p0 = P[h][0]; p1 = P[h][1]; p2 = P[h][2]; p3 = P[h][3]; }
+        if (!((hi >> b) & 1u)) { p0 = -p0; p1 = -p1; p2 = -p2; p3 = -p3; }
+        const T d = D[k];
+        e[0] += p0 + d;
+        e[1] += p1 + d;
+        e[2] += p2 + d;
+        e[3] += p3 + d;
+        put(hi);
+    }
+}
+
 // ---- energy build into HBM --------------------------------------------------------------
 // Thread t of 2^m fixes the low m bits of z and walks the high n - m bits in Gray-code order
 // (same increment rule as the resident tier); every step writes one coalesced row of E.
@@ -571,7 +681,37 @@ static int energy_split(int n) {
     return m;
 }
 
+// Top bits walked per thread by the row form: enough threads in total (instances x 2^(n-2-nh))
+// to fill the GPU, a walk of at most 2^8 steps.
+static int rows_nh(int n, int count) {
+    int lc = 0;
+    while ((2ull << lc) <= (unsigned long long)count) ++lc;
+    int nh = n - 20 + lc;
+    if (nh > ROWS_NH_MAX) nh = ROWS_NH_MAX;
+    if (nh > n - 4) nh = n - 4;
+    return nh < 0 ? 0 : nh;
+}
+
+template <typename T>
+static cudaError_t launch_rows(int n, int count, const void* Q, void* E, const void* insts, cudaStream_t st) {
+    const int nh = rows_nh(n, count);
+    const uint64_t threads = 1ull << (n - nh - 2);
+    const int block = threads < 256 ? (int)threads : 256;
+    const unsigned gx = (unsigned)((threads + block - 1) / block);
+    const StreamInst<T>* in = static_cast<const StreamInst<T>*>(insts);
+    for (int c0 = 0; c0 < count; c0 += 65535) {          // grid.y limit
+        const int cy = count - c0 < 65535 ? count - c0 : 65535;
+        k_energy_rows<T><<<dim3(gx, (unsigned)cy), block, 0, st>>>(n, nh, static_cast<const T*>(Q),
+                                                                  static_cast<T*>(E), in ? in + c0 : nullptr);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st) {
+    if (n >= 2 && (reinterpret_cast<uintptr_t>(E) & 7u) == 0)
+        return dbl ? launch_rows<double>(n, 1, Q, E, nullptr, st) : launch_rows<float>(n, 1, Q, E, nullptr, st);
     const int m = energy_split(n);
     const uint64_t threads = 1ull << m;
     const int block = threads < 256 ? (int)threads : 256;
@@ -582,6 +722,10 @@ cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t 
 }
 
 cudaError_t launch_energy_batch(bool dbl, int n, const void* insts, int count, cudaStream_t st) {
+    // every instance's E is at least 8-byte aligned (plan validation)
+    if (n >= 2)
+        return dbl ? launch_rows<double>(n, count, nullptr, nullptr, insts, st)
+                   : launch_rows<float>(n, count, nullptr, nullptr, insts, st);
     const int m = energy_split(n);
     const uint64_t threads = 1ull << m;
     const int block = threads < 256 ? (int)threads : 256;

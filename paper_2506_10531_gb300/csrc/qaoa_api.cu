@@ -419,6 +419,8 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         if (d.psi_off >= 0 && !aligned16(static_cast<const C2*>(io->psi) + d.psi_off))
             return fail(QAOA_E_INVALID, "instance %d: state at psi_off must be 16-byte aligned", i);
         if (d.e_off >= 0 && !io->e) return fail(QAOA_E_INVALID, "instance %d: energy pool NULL", i);
+        if (d.e_off >= 0 && (reinterpret_cast<uintptr_t>(static_cast<const T*>(io->e) + d.e_off) & 7u) != 0)
+            return fail(QAOA_E_INVALID, "instance %d: energies at e_off must be 8-byte aligned", i);
         if ((d.flags & QAOA_INST_GRAD) && !io->grad) return fail(QAOA_E_INVALID, "instance %d: grad pool NULL", i);
         if ((d.flags & QAOA_INST_GRAD) && d.n > (dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ) && d.psi_off >= 0)
             return fail(QAOA_E_UNSUPPORTED, "instance %d: the final state is returned with a gradient only for n <= %d",

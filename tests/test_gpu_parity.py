@@ -202,3 +202,31 @@ def test_subqubo_build_bit_exact(q, ctx, orc):
     q.dqaoa_subqubo_build(ctx, dev(Q), N, dev(x), m, k, dev(idx), True, out)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy().reshape(m, k, k), qs_o.astype(np.float32))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 12, 14, 17, 21])
+def test_energies_nonsymmetric_q(q, ctx, orc, n):
+    # E(z) = z^T Q z uses Q_ij and Q_ji as separate terms (Section IV): a non-symmetric Q
+    rng = np.random.default_rng(900 + n)
+    Q32 = rng.uniform(-1, 1, (n, n)).astype(np.float32)
+    E = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    q.qaoa_build_energies(ctx, n, dev(Q32), E)
+    Ed = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    q.qaoa_build_energies(ctx, n, dev(Q32, torch.float64), Ed, dbl=True)
+    torch.cuda.synchronize()
+    E_o = orc.energies(Q32.astype(np.float64))
+    absq = np.abs(Q32).sum()
+    assert np.max(np.abs(E.cpu().numpy() - E_o)) <= 1e-5 * absq
+    assert np.max(np.abs(Ed.cpu().numpy() - E_o)) <= 1e-12 * absq
+
+
+def test_energies_unaligned_pointer(q, ctx, orc):
+    # an energy array that is 8- but not 16-byte aligned takes the narrow stores
+    n = 16
+    Q32 = synth.symmetric_q(n, seed=77).astype(np.float32)
+    buf = torch.zeros((1 << n) + 2, dtype=torch.float32, device="cuda")
+    q.qaoa_build_energies(ctx, n, dev(Q32), buf[2:])
+    torch.cuda.synchronize()
+    E_o = orc.energies(Q32.astype(np.float64))
+    assert np.max(np.abs(buf[2:].cpu().numpy() - E_o)) <= 1e-5 * np.abs(Q32).sum()
+    assert buf[0].item() == 0.0 and buf[1].item() == 0.0
