@@ -187,6 +187,8 @@ __global__ void __launch_bounds__(256) k_stream_finalize(const StreamInst<T>* __
 }
 
 // ---- adjoint passes -----------------------------------------------------------------------
+// Two CTAs per SM: psi, lam and E tiles of 2^12 (float) or 2^11 (double) amplitudes each.
+constexpr int ADJ_THREADS = 256;
 // The forward pass P undone on a tile of psi and lam (both in the rotated frame), with the
 // gradient accumulations of the tile engine's adjoint sub-passes: the local snake of P with
 // RB_ADJ-bit windows, run in reverse. Per tile, four partial sums are written (as FP64):
@@ -251,7 +253,7 @@ __device__ void stream_adj_tile(const StreamPass& P, int si, bool lam_first, boo
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_stream_adj_pass(const StreamPass P, int si, int lam_first,
+__global__ void __launch_bounds__(ADJ_THREADS, 2) k_stream_adj_pass(const StreamPass P, int si, int lam_first,
                                                          int store,
                                                          const StreamInst<T>* __restrict__ insts,
                                                          int count, const StreamInst<T> one) {
@@ -584,11 +586,12 @@ __global__ void __launch_bounds__(256) k_reduce_finalize(int nparts, const doubl
 // ---------------------------------------------------------------------------------------------
 
 int stream_tile_bits(bool dbl) { return dbl ? 12 : 13; }
+int stream_adj_tile_bits(bool dbl) { return dbl ? 11 : 12; }
 
 // HBM windows of a layer: window 0 = kind A (qubits 0..tb-1); windows 1.. = kind B chunks of
 // the qubits [tb, n), as equal as possible, each at most tb - 4 qubits.
-int stream_plan(bool dbl, int n, int p, int k, StreamPass* out, int max_out) {
-    const int tb = stream_tile_bits(dbl);
+int stream_plan(bool dbl, int n, int p, int k, StreamPass* out, int max_out, int tb) {
+    if (tb < 0) tb = stream_tile_bits(dbl);
     if (n <= tb) return -1;
     const int hmax = tb - 4;
     const int rest = n - tb;
@@ -736,7 +739,7 @@ cudaError_t launch_energy_batch(bool dbl, int n, const void* insts, int count, c
 }
 
 size_t stream_adj_smem_bytes(bool dbl) {
-    const size_t TD = (size_t)1 << stream_tile_bits(dbl);
+    const size_t TD = (size_t)1 << stream_adj_tile_bits(dbl);
     const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4;
     const size_t lcs = dbl ? sizeof(LayerConst<double>) : sizeof(LayerConst<float>);
     size_t o = 2 * TD * c + TD * r + 64 * lcs;
@@ -752,11 +755,11 @@ cudaError_t launch_stream_adj_pass(bool dbl, const StreamPass& P, int si, bool l
     if (dbl) {
         e = cudaFuncSetAttribute(k_stream_adj_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_stream_adj_pass<double><<<grid, 256, sm, st>>>(P, si, lam_first, store, static_cast<const StreamInst<double>*>(insts), count, one_of<double>(one));
+        k_stream_adj_pass<double><<<grid, ADJ_THREADS, sm, st>>>(P, si, lam_first, store, static_cast<const StreamInst<double>*>(insts), count, one_of<double>(one));
     } else {
         e = cudaFuncSetAttribute(k_stream_adj_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_stream_adj_pass<float><<<grid, 256, sm, st>>>(P, si, lam_first, store, static_cast<const StreamInst<float>*>(insts), count, one_of<float>(one));
+        k_stream_adj_pass<float><<<grid, ADJ_THREADS, sm, st>>>(P, si, lam_first, store, static_cast<const StreamInst<float>*>(insts), count, one_of<float>(one));
     }
     return cudaGetLastError();
 }

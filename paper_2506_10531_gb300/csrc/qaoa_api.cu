@@ -81,15 +81,15 @@ size_t reduce_scratch_bytes(int n) {
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Workspace of a streaming gradient: psi and lam (2^n complex each), the forward scratch and the
-// per-pass, per-tile gradient partials (4 doubles).
+// per-pass, per-tile gradient partials of the adjoint plan (4 doubles).
 size_t stream_grad_bytes(bool dbl, int n, int p) {
-    const int tb = stream_tile_bits(dbl);
+    const int tb = stream_tile_bits(dbl), tba = stream_adj_tile_bits(dbl);
     if (n <= tb) return 0;
     StreamPass tmp[256];
-    const int S = stream_plan(dbl, n, p, 0, tmp, 256);
+    const int S = stream_plan(dbl, n, p, 0, tmp, 256, tba);
     if (S < 0) return 0;
-    const size_t D = (size_t)1 << n, nt = (size_t)1 << (n - tb), cs = dbl ? 16 : 8;
-    return 2 * align256(D * cs) + stream_scratch_bytes(dbl, n, 0) + align256((size_t)S * nt * 4 * sizeof(double));
+    const size_t D = (size_t)1 << n, nta = (size_t)1 << (n - tba), cs = dbl ? 16 : 8;
+    return 2 * align256(D * cs) + stream_scratch_bytes(dbl, n, 0) + align256((size_t)S * nta * 4 * sizeof(double));
 }
 
 qaoa_status ensure_ws(qaoa_ctx* c, size_t bytes) {
@@ -175,13 +175,18 @@ qaoa_status grad_stream_one(qaoa_ctx* c, int n, int p, const T* gamma, const T* 
     I.expect = expect;
     I.dgamma = dgamma;
     I.dbeta = dbeta;
+    StreamPass apasses[256];
+    const int tba = stream_adj_tile_bits(dbl);
+    const int SA = stream_plan(dbl, n, p, 0, apasses, 256, tba);
+    if (SA < 0) return fail(QAOA_E_INVALID, "no adjoint plan for n=%d p=%d", n, p);
+    const uint64_t nta = 1ull << (n - tba);
     const int grid = (int)std::min<uint64_t>(nt, (uint64_t)c->nsm * 2);
-    const int agrid = (int)std::min<uint64_t>(nt, (uint64_t)c->nsm);
+    const int agrid = (int)std::min<uint64_t>(nta, (uint64_t)c->nsm * 2);
     for (int s = 0; s < S; ++s) CK(launch_stream_pass(dbl, passes[s], nullptr, 1, grid, st, &I));
     if (expect) CK(launch_stream_finalize(dbl, nullptr, 1, nt, 0, st, &I));
-    for (int s = S - 1; s >= 0; --s)
-        CK(launch_stream_adj_pass(dbl, passes[s], s, s == S - 1, s > 0, nullptr, 1, agrid, st, &I));
-    CK(launch_stream_grad_reduce(dbl, passes, S, nullptr, 1, nt, st, &I));
+    for (int s = SA - 1; s >= 0; --s)
+        CK(launch_stream_adj_pass(dbl, apasses[s], s, s == SA - 1, s > 0, nullptr, 1, agrid, st, &I));
+    CK(launch_stream_grad_reduce(dbl, apasses, SA, nullptr, 1, nta, st, &I));
     return QAOA_OK;
 }
 
@@ -385,6 +390,7 @@ struct qaoa_plan {
     struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
     struct CluGroup { int n, L, pmax, count; size_t desc_off; int clusters; };
     struct StrGroup { int n, p, k, count; bool grad; size_t inst_off; std::vector<StreamPass> passes;
+                      std::vector<StreamPass> apasses;   // adjoint plan (adjoint tile bits)
                       int grid, agrid; std::vector<const void*> q; std::vector<void*> e; };
     std::vector<ResGroup> res;
     std::vector<CluGroup> clu;
@@ -509,7 +515,7 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     // streaming: per instance its own E / psi / partial buffers inside the plan block
     struct SI { size_t e_off, psi_off, part_off, lam_off, grad_off; };
     std::vector<std::vector<SI>> sinfo;
-    const int tb = stream_tile_bits(dbl);
+    const int tb = stream_tile_bits(dbl), tba = stream_adj_tile_bits(dbl);
     for (auto& kv : sg) {
         qaoa_plan::StrGroup g{};
         g.n = std::get<0>(kv.first);
@@ -522,6 +528,14 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         if (S < 0) { delete P; return fail(QAOA_E_INVALID, "no streaming plan for n=%d p=%d", g.n, g.p); }
         if (g.grad) tmp[S - 1].keep_frame = 1;
         g.passes.assign(tmp, tmp + S);
+        int SA = 0;
+        if (g.grad) {
+            StreamPass atmp[256];
+            SA = stream_plan(dbl, g.n, g.p, 0, atmp, 256, tba);
+            if (SA < 0) { delete P; return fail(QAOA_E_INVALID, "no adjoint plan for n=%d p=%d", g.n, g.p); }
+            g.apasses.assign(atmp, atmp + SA);
+        }
+        const uint64_t nta = 1ull << (g.n - tba);
         g.inst_off = bytes;
         bytes = align256(bytes + sizeof(StreamInst<T>) * g.count);
         std::vector<SI> v;
@@ -542,13 +556,13 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
                 s.lam_off = bytes;
                 bytes = align256(bytes + D * sizeof(C2));
                 s.grad_off = bytes;
-                bytes = align256(bytes + (size_t)S * nt * 4 * sizeof(double));
+                bytes = align256(bytes + (size_t)SA * nta * 4 * sizeof(double));
             }
             v.push_back(s);
         }
         const uint64_t tiles = nt * (uint64_t)g.count;
         g.grid = (int)std::min<uint64_t>(tiles, (uint64_t)c->nsm * 2);
-        g.agrid = (int)std::min<uint64_t>(tiles, (uint64_t)c->nsm);
+        g.agrid = (int)std::min<uint64_t>(nta * (uint64_t)g.count, (uint64_t)c->nsm * 2);
         sinfo.push_back(v);
         P->str.push_back(std::move(g));
     }
@@ -611,7 +625,7 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         }
         e = cudaMemcpy(base + g.inst_off, si.data(), sizeof(StreamInst<T>) * g.count, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload stream instances"); }
-        P->kernels += 1 + (int)g.passes.size() + 1 + (g.grad ? (int)g.passes.size() + 1 : 0);
+        P->kernels += 1 + (int)g.passes.size() + 1 + (g.grad ? (int)g.apasses.size() + 1 : 0);
         ++gi;
     }
     // algorithmic bytes, in the order qaoa_plan_launch issues the kernels
@@ -647,11 +661,12 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             P->bytes.push_back(cnt * D * ((pass.init ? 0.0 : sizeof(C2)) + sizeof(C2) + (pass.need_e ? sizeof(T) : 0.0)));
         P->bytes.push_back(cnt * (nt * (sizeof(double) + std::max(g.k, 1) * 12.0) + 8.0 + g.k * 16.0));
         if (g.grad) {
-            const int S = (int)g.passes.size();
-            for (int s = S - 1; s >= 0; --s)   // psi and lam read (lam formed in the first), E read, both written back
-                P->bytes.push_back(cnt * D * ((s == S - 1 ? 1.0 : 2.0) * sizeof(C2) + sizeof(T) +
+            const int SA = (int)g.apasses.size();
+            const double nta = (double)(1ull << (g.n - tba));
+            for (int s = SA - 1; s >= 0; --s)   // psi and lam read (lam formed in the first), E read, both written back
+                P->bytes.push_back(cnt * D * ((s == SA - 1 ? 1.0 : 2.0) * sizeof(C2) + sizeof(T) +
                                               (s > 0 ? 2.0 * sizeof(C2) : 0.0)));
-            P->bytes.push_back(cnt * (double)S * nt * 32.0);
+            P->bytes.push_back(cnt * (double)SA * nta * 32.0);
         }
     }
     *out = P;
@@ -715,15 +730,15 @@ extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
             return launch_stream_finalize(P->dbl, base + g.inst_off, g.count, 1ull << (g.n - tb), g.k, st);
         }));
         if (g.grad) {
-            const int S = (int)g.passes.size();
-            for (int s = S - 1; s >= 0; --s)
+            const int SA = (int)g.apasses.size();
+            for (int s = SA - 1; s >= 0; --s)
                 CK(timed("stream_adjoint", [&] {
-                    return launch_stream_adj_pass(P->dbl, g.passes[s], s, s == S - 1, s > 0, base + g.inst_off,
+                    return launch_stream_adj_pass(P->dbl, g.apasses[s], s, s == SA - 1, s > 0, base + g.inst_off,
                                                   g.count, g.agrid, st);
                 }));
             CK(timed("stream_grad_reduce", [&] {
-                return launch_stream_grad_reduce(P->dbl, g.passes.data(), S, base + g.inst_off, g.count,
-                                                 1ull << (g.n - tb), st);
+                return launch_stream_grad_reduce(P->dbl, g.apasses.data(), SA, base + g.inst_off, g.count,
+                                                 1ull << (g.n - stream_adj_tile_bits(P->dbl)), st);
             }));
         }
     }

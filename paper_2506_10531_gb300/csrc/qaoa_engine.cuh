@@ -180,24 +180,30 @@ __device__ __forceinline__ void mix_layer(C (&v)[1 << R], int mask, const LayerC
 // qubits. Any point of the layer's mixer gives the same value (X_q commutes with every
 // exp(-i beta X_q')). In the rotated frame X_q becomes Y_q, so over the pairs (a, b)
 //   Im <lam|X_q|psi> = sum Re(conj(lam~_b) psi~_a) - Re(conj(lam~_a) psi~_b).
+// Four independent partial sums keep the accumulation off the FMA latency chain.
 template <int R, typename C, typename T>
 __device__ __forceinline__ T mix_group_adj(C (&v)[1 << R], C (&u)[1 << R], int mask, T c, T s) {
     const RotCoef<T> k(c, -s);
-    T acc = T(0);
+    T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         if (mask & (1 << j)) {
+            int slot = 0;
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i)
                 if (!(i & (1 << j))) {
                     const int b = i | (1 << j);
-                    acc += re_conj_mul(u[b], v[i]) - re_conj_mul(u[i], v[b]);
+                    T& a = acc[slot++ & 3];
+                    a = fma(u[b].x, v[i].x, a);
+                    a = fma(u[b].y, v[i].y, a);
+                    a = fma(-u[i].x, v[b].x, a);
+                    a = fma(-u[i].y, v[b].y, a);
                     butterfly(v[i], v[b], k);
                     butterfly(u[i], u[b], k);
                 }
         }
     }
-    return acc;
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 // Element addresses of a group. The swizzle is linear over GF(2) and a group's base index and
@@ -358,17 +364,18 @@ __device__ __forceinline__ void subpass_adj_a(const TileRef<T>& t, const SubPass
             if (j == 0) acc_b[0] += ab; else acc_b[1] += ab;
             if (l > sp.la || sp.ph_first) {
                 const T gp = -lc[l].gpi;
-                T ag = T(0);
+                T ag[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) {
                     const T e = t.E[sb ^ woff<T, A>(i)];
-                    ag += e * im_conj_mul(u[i], v[i]);
+                    ag[i & 3] = fma(e, im_conj_mul(u[i], v[i]), ag[i & 3]);
                     T s, c;
                     sincos_phase(gp, e, s, c);
                     rot_neg(v[i], s, c);
                     rot_neg(u[i], s, c);
                 }
-                if (j == 0) acc_g[0] += ag; else acc_g[1] += ag;
+                const T agt = (ag[0] + ag[1]) + (ag[2] + ag[3]);
+                if (j == 0) acc_g[0] += agt; else acc_g[1] += agt;
             }
         }
         store_group<R, A>(t.psi, sb, v);

@@ -38,22 +38,27 @@ struct StreamInst {
     double* topk_prob;
     // adjoint (gradient runs only)
     void* lam;            // 2^n complex adjoint state in HBM
-    double* part_grad;    // passes * 2^(n - tb) * 4 per-tile partials
+    double* part_grad;    // adjoint passes * 2^(n - adjoint tile bits) * 4 per-tile partials
     double* dgamma;       // p
     double* dbeta;        // p
 };
 
 int stream_tile_bits(bool dbl);
-// Fill the pass list of a p-layer run on n qubits; returns the number of passes or -1.
-int stream_plan(bool dbl, int n, int p, int k, StreamPass* out, int max_out);
+// Tile bits of the adjoint passes: one bit fewer than the forward tiles, so that two CTAs
+// (psi, lam and E tiles each) share an SM.
+int stream_adj_tile_bits(bool dbl);
+// Fill the pass list of a p-layer run on n qubits with tiles of tb bits (tb < 0: the forward
+// tile size); returns the number of passes or -1.
+int stream_plan(bool dbl, int n, int p, int k, StreamPass* out, int max_out, int tb = -1);
 size_t stream_smem_bytes(bool dbl);
 // insts: device array of `count` instances, or nullptr to pass the host instance `one` by value.
 cudaError_t launch_stream_pass(bool dbl, const StreamPass& P, const void* insts, int count,
                                int grid, cudaStream_t st, const void* one = nullptr);
 cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint64_t ntiles, int k,
                                    cudaStream_t st, const void* one = nullptr);
-// Adjoint pass `si` (the forward pass P run backwards on psi and lam): lam_first forms
-// lam = E psi on load, store == 0 skips writing the states back (last adjoint pass).
+// Adjoint pass `si` (pass P of the adjoint plan, i.e. stream_plan with the adjoint tile bits,
+// run backwards on psi and lam): lam_first forms lam = E psi on load, store == 0 skips writing
+// the states back (last adjoint pass).
 cudaError_t launch_stream_adj_pass(bool dbl, const StreamPass& P, int si, bool lam_first, bool store,
                                    const void* insts, int count, int grid, cudaStream_t st,
                                    const void* one = nullptr);
