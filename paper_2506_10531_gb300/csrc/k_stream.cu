@@ -30,6 +30,73 @@ __device__ __forceinline__ uint64_t global_index(const StreamPass& P, uint64_t t
     return lo | (mid << P.c) | (hi << P.s) | (top << (P.s + P.h));
 }
 
+// Per-thread strided walk over a tile: element u = u0 + j * step (step a multiple of 2^c for kind
+// B, any for kind A) has global index global_index(P, tau, u0) + j * gstep. Returns false when
+// kind B's contiguous run is longer than the step (then the index is formed per element).
+__device__ __forceinline__ bool linear_walk(const StreamPass& P, uint32_t step, uint64_t& gstep) {
+    if (P.kind == 0) { gstep = step; return true; }
+    if (step & ((1u << P.c) - 1u)) return false;
+    gstep = (uint64_t)(step >> P.c) << P.s;
+    return true;
+}
+
+// Stage the tile's amplitudes (16-byte copies) and optionally energies (8-byte copies) of
+// tile tau into shared memory, asynchronously. The swizzle only permutes bits below the copy
+// stride, so the shared-memory offset advances linearly as well.
+template <typename T>
+__device__ __forceinline__ void stage_tile(const StreamPass& P, uint64_t tau,
+                                           const typename Num<T>::C* gsrc,
+                                           typename Num<T>::C* sdst, const T* gE, T* sE) {
+    using C = typename Num<T>::C;
+    const uint32_t TD = 1u << P.tb;
+    constexpr uint32_t PAIR = sizeof(C) == 8 ? 2u : 1u;   // amplitudes per 16-byte copy
+    const uint32_t step = PAIR * blockDim.x, u0 = PAIR * threadIdx.x;
+    uint64_t gstep;
+    if (!gsrc) {
+    } else if (linear_walk(P, step, gstep)) {
+        const C* g = gsrc + global_index(P, tau, u0);
+        C* sp = sdst + swz<T>(u0);
+#pragma unroll 4
+        for (uint32_t u = u0; u < TD; u += step, g += gstep, sp += step) cp_async16(sp, g);
+    } else {
+        for (uint32_t u = u0; u < TD; u += step) cp_async16(&sdst[swz<T>(u)], gsrc + global_index(P, tau, u));
+    }
+    if (gE) {
+        constexpr uint32_t EP = 8u / sizeof(T);           // energies per 8-byte copy
+        const uint32_t estep = EP * blockDim.x, e0 = EP * threadIdx.x;
+        uint64_t egstep;
+        if (linear_walk(P, estep, egstep)) {
+            const T* g = gE + global_index(P, tau, e0);
+            T* sp = sE + swz<T>(e0);
+#pragma unroll 4
+            for (uint32_t u = e0; u < TD; u += estep, g += egstep, sp += estep) cp_async8(sp, g);
+        } else {
+            for (uint32_t u = e0; u < TD; u += estep) cp_async8(&sE[swz<T>(u)], gE + global_index(P, tau, u));
+        }
+    }
+}
+
+// Write the tile back (16-byte accesses on both sides), same walk as stage_tile.
+template <typename T>
+__device__ __forceinline__ void store_tile(const StreamPass& P, uint64_t tau, const typename Num<T>::C* ssrc,
+                                          typename Num<T>::C* gdst) {
+    using C = typename Num<T>::C;
+    const uint32_t TD = 1u << P.tb;
+    constexpr uint32_t PAIR = sizeof(C) == 8 ? 2u : 1u;
+    const uint32_t step = PAIR * blockDim.x, u0 = PAIR * threadIdx.x;
+    uint64_t gstep;
+    if (linear_walk(P, step, gstep)) {
+        C* g = gdst + global_index(P, tau, u0);
+        const C* sp = ssrc + swz<T>(u0);
+        for (uint32_t u = u0; u < TD; u += step, g += gstep, sp += step)
+            *reinterpret_cast<uint4*>(g) = *reinterpret_cast<const uint4*>(sp);
+    } else {
+        for (uint32_t u = u0; u < TD; u += step)
+            *reinterpret_cast<uint4*>(gdst + global_index(P, tau, u)) =
+                *reinterpret_cast<const uint4*>(&ssrc[swz<T>(u)]);
+    }
+}
+
 template <typename T>
 struct StreamSmem {
     typename Num<T>::C* psi;
@@ -48,16 +115,8 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     C* gpsi = reinterpret_cast<C*>(I.psi);
     // ---- HBM -> shared: asynchronous 16-byte copies, all in flight before the wait ----
     // (tile bit 0 is global bit 0 and c >= 1, so aligned pairs stay adjacent in both layouts)
-    constexpr uint32_t PAIR = sizeof(C) == 8 ? 2u : 1u;   // amplitudes per 16-byte copy
-    if (!P.init) {
-        for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x)
-            cp_async16(&s.psi[swz<T>(u)], gpsi + global_index(P, tau, u));
-    }
-    if (needE) {
-        constexpr uint32_t EP = 8u / sizeof(T);           // energies per 8-byte copy
-        for (uint32_t u = EP * threadIdx.x; u < TD; u += EP * blockDim.x)
-            cp_async8(&s.E[swz<T>(u)], I.E + global_index(P, tau, u));
-    }
+    if (!P.init) stage_tile<T>(P, tau, gpsi, s.psi, needE ? I.E : nullptr, s.E);
+    else if (needE) stage_tile<T>(P, tau, nullptr, nullptr, I.E, s.E);
     cp_async_wait_all();
     __syncthreads();
     // ---- tile engine: snake over the local windows of the mixed bits, layers [la, lb] ----
@@ -79,10 +138,7 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     // the rotated frame; the last pass converts back with (-i)^{|z|} (|z| = |tau| + |u|: the
     // tile map only permutes bits). ----
     if (!P.fin || P.keep_frame) {
-        for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
-            const uint4 w = *reinterpret_cast<const uint4*>(&s.psi[swz<T>(u)]);
-            *reinterpret_cast<uint4*>(gpsi + global_index(P, tau, u)) = w;
-        }
+        store_tile<T>(P, tau, s.psi, gpsi);
     } else {
         const int pt = __popcll(tau);
         for (uint32_t u = threadIdx.x; u < TD; u += blockDim.x)
@@ -199,18 +255,10 @@ __device__ void stream_adj_tile(const StreamPass& P, int si, bool lam_first, boo
                                 const StreamInst<T>& I, uint64_t tau, const StreamSmem<T>& s,
                                 typename Num<T>::C* slam) {
     using C = typename Num<T>::C;
-    const uint32_t TD = 1u << P.tb;
     C* gpsi = reinterpret_cast<C*>(I.psi);
     C* glam = reinterpret_cast<C*>(I.lam);
-    constexpr uint32_t PAIR = sizeof(C) == 8 ? 2u : 1u;
-    for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
-        const uint64_t gz = global_index(P, tau, u);
-        cp_async16(&s.psi[swz<T>(u)], gpsi + gz);
-        if (!lam_first) cp_async16(&slam[swz<T>(u)], glam + gz);
-    }
-    constexpr uint32_t EP = 8u / sizeof(T);
-    for (uint32_t u = EP * threadIdx.x; u < TD; u += EP * blockDim.x)
-        cp_async8(&s.E[swz<T>(u)], I.E + global_index(P, tau, u));
+    stage_tile<T>(P, tau, gpsi, s.psi, I.E, s.E);
+    if (!lam_first) stage_tile<T>(P, tau, glam, slam, nullptr, nullptr);
     cp_async_wait_all();
     __syncthreads();
     const TileRef<T> tile{s.psi, slam, s.E, P.tb};
@@ -243,11 +291,8 @@ __device__ void stream_adj_tile(const StreamPass& P, int si, bool lam_first, boo
     const double v3 = block_sum((double)ag[1], s.red);
     if (threadIdx.x == 0) { out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; }
     if (store) {
-        for (uint32_t u = PAIR * threadIdx.x; u < TD; u += PAIR * blockDim.x) {
-            const uint64_t gz = global_index(P, tau, u);
-            *reinterpret_cast<uint4*>(gpsi + gz) = *reinterpret_cast<const uint4*>(&s.psi[swz<T>(u)]);
-            *reinterpret_cast<uint4*>(glam + gz) = *reinterpret_cast<const uint4*>(&slam[swz<T>(u)]);
-        }
+        store_tile<T>(P, tau, s.psi, gpsi);
+        store_tile<T>(P, tau, slam, glam);
     }
     __syncthreads();
 }
