@@ -266,35 +266,10 @@ def run_ours(args):
     gpu_launches = args.steps * (plan_kernels + 1)
 
     # ---- dominant kernel and its roofline ----
-    kbytes = q.qaoa_plan_kernel_bytes(plan)
-    fam_ms = {nm: sum(v) for nm, v in kern.items()}
-    dom = max(fam_ms, key=fam_ms.get)
-    # bytes per launch of that family (average over its launches in one plan launch)
-    q.qaoa_plan_set_timing(plan, True)
-    q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream)
-    order = [nm for nm, _ in q.qaoa_plan_kernel_times(plan)]
-    q.qaoa_plan_set_timing(plan, False)
-    fam_bytes = [b for nm, b in zip(order, kbytes) if nm == dom]
-    per_launch_ms = statistics.mean(kern[dom])
-    per_launch_bytes = statistics.mean(fam_bytes) if fam_bytes else 0.0
-    peaks, peak_kind = measured_peaks()
-    if dom in ("stream_pass", "energy", "stream_finalize"):
-        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": ncu_traffic(dom), "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
-    else:
-        # on-chip kernels: FP32 pipe bound; peak = SMs x 128 FP32 lanes x 2 flop x clock
-        props = torch.cuda.get_device_properties(dev)
-        mhz = clk.summary().get("sm_mhz") or 1900.0
-        peak_tf = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
-        flops = alu_flops_per_launch(dom, m, k, p)
-        achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": ncu_traffic(dom),
-                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x median SM clock",
-                "ms_per_launch": per_launch_ms}
+    def relaunch():
+        q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream)
+    roof = plan_roofline(q, plan, kern, relaunch, clk, dev,
+                         alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p))
 
     # ---- kernel-only batch throughput and the plain one-instance-per-launch path ----
     kb = time_plan_only(q, plan, stream, args.steps, l2_flush)
@@ -352,6 +327,44 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+HBM_FAMILIES = ("stream_pass", "stream_adjoint", "energy", "stream_finalize", "stream_grad_reduce")
+
+
+def plan_roofline(q, plan, kern, relaunch, clk, dev, alu_flops=None):
+    """Roofline entry of the kernel family with the largest time in `kern` ({family: [ms per
+    launch]}, measured with CUDA events on the launch stream inside the timed region). Algorithmic
+    bytes per launch come from the plan; `relaunch` runs the plan once more with timing on to map
+    launch order to families."""
+    import torch
+    kbytes = q.qaoa_plan_kernel_bytes(plan, 8192)
+    fam_ms = {nm: sum(v) for nm, v in kern.items()}
+    dom = max(fam_ms, key=fam_ms.get)
+    q.qaoa_plan_set_timing(plan, True)
+    relaunch()
+    order = [nm for nm, _ in q.qaoa_plan_kernel_times(plan, 8192)]
+    q.qaoa_plan_set_timing(plan, False)
+    fam_bytes = [b for nm, b in zip(order, kbytes) if nm == dom]
+    per_launch_ms = statistics.mean(kern[dom])
+    per_launch_bytes = statistics.mean(fam_bytes) if fam_bytes else 0.0
+    peaks, peak_kind = measured_peaks()
+    if dom in HBM_FAMILIES or alu_flops is None:
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(dom), "peak_source": peak_kind + " (hbm_gbs, copy burst)",
+                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                "launches_per_step": len(fam_bytes)}
+    # on-chip kernels: FP32 pipe bound; peak = SMs x 128 FP32 lanes x 2 flop x clock
+    props = torch.cuda.get_device_properties(dev)
+    mhz = clk.summary().get("sm_mhz") or 1900.0
+    peak_tf = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = alu_flops(dom) / (per_launch_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
+            "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": ncu_traffic(dom),
+            "peak_source": "derived: SMs x 128 FP32 lanes x 2 x median SM clock",
+            "ms_per_launch": per_launch_ms}
+
+
 def alu_flops_per_launch(family, m, k, p):
     # per amplitude and layer: phase (sincos counted as 8) + 4 flops, mixer 4 flops per qubit
     return m * (1 << k) * p * (12 + 4 * k)
@@ -401,6 +414,322 @@ def time_plain(q, ctx, sess, stream, n_inst):
     return {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "kernels_per_solve": 2 + p * (k + 1) + 2}
 
 
+# ---------------------------------------------------------------------------------------------
+# Other measured configurations (one JSON line each, same keys)
+# ---------------------------------------------------------------------------------------------
+
+LARGE = dict(seed=5, n=30, p=2, gamma=(0.4, 0.7), beta=(0.6, 0.3), k=8)
+PLAIN10 = dict(seed=1, n=10, k=8)
+
+
+def _timed_steps(stream, steps, body, flush=None):
+    """Run body() `steps` times between CUDA events on `stream`; returns ms per step list."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s in range(steps):
+        if flush is not None:
+            flush()
+        ev[s][0].record(stream)
+        body(s)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _line(metric, value, unit, args, world, ms_step, dtype, config, **extra):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+    d.update(extra)
+    return d
+
+
+def _plan_kern_times(q, plan, kern):
+    for name, ms in q.qaoa_plan_kernel_times(plan, 8192):
+        kern.setdefault(name, []).append(ms)
+
+
+def run_large(args):
+    """The n = 30, p = 2 streaming solve: energies, two layers, <C> and top-8 (one plan)."""
+    import torch
+    import paper_2506_10531_gb300 as q
+    from paper_2506_10531_gb300 import build as qbuild
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, p, k = LARGE["n"], LARGE["p"], LARGE["k"]
+    Q = synth.symmetric_q(n, seed=LARGE["seed"] + 1000 * rank).astype(np.float32)
+    par = np.array(LARGE["gamma"] + LARGE["beta"], dtype=np.float32)
+    ctx = q.qaoa_create(local)
+    qd = torch.as_tensor(Q.reshape(-1)).to(dev)
+    pd = torch.as_tensor(par).to(dev)
+    ex = torch.zeros(1, dtype=torch.float64, device=dev)
+    ti = torch.zeros(k, dtype=torch.int64, device=dev)
+    tp = torch.zeros(k, dtype=torch.float64, device=dev)
+    io = q.make_io(qd, pd, expect=ex, topk_idx=ti, topk_prob=tp, k_stride=k)
+    insts = q.make_insts([(n, p, k, 0, 0, 0, -1, -1)])
+    plan = q.qaoa_plan_create(ctx, insts, io)
+    for _ in range(args.warmup):
+        q.qaoa_plan_launch(plan, stream)
+    torch.cuda.synchronize()
+    kern = {}
+    q.qaoa_plan_set_timing(plan, True)
+
+    def body(s):
+        q.qaoa_plan_launch(plan, stream)
+        _plan_kern_times(q, plan, kern)
+    with Clocks(local) as clk:
+        step_ms = _timed_steps(stream, args.steps, body)
+    q.qaoa_plan_set_timing(plan, False)
+    tot_s = sum(step_ms) / 1e3
+    amps = (1 << n) * p
+    roof = plan_roofline(q, plan, kern, lambda: q.qaoa_plan_launch(plan, stream), clk, dev)
+    per_pass = {"ms": [round(v, 3) for v in kern.get("stream_pass", [])[:8]]}
+    # e2e: Q and parameters from pinned host memory, <C> and top-k back, every step
+    Qp = torch.from_numpy(Q.reshape(-1)).pin_memory()
+    Pp = torch.from_numpy(par).pin_memory()
+    out = torch.empty(1 + 2 * k, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        qd.copy_(Qp, non_blocking=True)
+        pd.copy_(Pp, non_blocking=True)
+        q.qaoa_plan_launch(plan, stream)
+        out[0:1].copy_(ex, non_blocking=True)
+        out[1:1 + k].copy_(tp, non_blocking=True)
+        out[1 + k:].copy_(ti.view(torch.float64), non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    kernels = q.qaoa_plan_kernel_count(plan)
+    q.qaoa_plan_destroy(plan)
+    q.qaoa_destroy(ctx)
+    line = _line("amp-layer-updates/s (n=30 streaming solve: energies + 2 layers + <C> + top-8)",
+                 amps * args.steps / tot_s, "amp-layer-updates/s", args, world, 1e3 * tot_s / args.steps,
+                 "c64 state, f32 energies, f64 reductions",
+                 {"workload": "large instance: dense n=30 QUBO U[-1,1] (seed 5), p=2, gamma=(0.4,0.7), "
+                              "beta=(0.6,0.3), complex64 (8 GiB) + FP32 energies (4 GiB), top-8",
+                  "l2": "inputs larger than L2 (12 GiB state + energies)", "parallelism": f"replicas x{world}"},
+                 solves_per_s=args.steps / tot_s,
+                 amp_gate_updates_per_s=amps * (n + 1) * args.steps / tot_s,
+                 latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+                 kernel_ms_per_step={nm: sum(v) / args.steps for nm, v in kern.items()},
+                 stream_pass_ms_first_step=per_pass, roofline=roof,
+                 e2e={"value": amps * args.steps / e2e_s, "unit": "amp-layer-updates/s",
+                      "h2d_bytes_per_step": Q.nbytes + par.nbytes, "d2h_bytes_per_step": 8 * (1 + 2 * k)},
+                 gpu_launches=kernels * args.steps, clocks=clk.summary())
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = large_cpu_baseline()
+    return line
+
+
+def large_cpu_baseline():
+    """The oracle on the n = 24 twin of the large instance (same generator and parameters)."""
+    import oracle
+    oracle.build()
+    n, p = 24, LARGE["p"]
+    Q = synth.symmetric_q(n, seed=LARGE["seed"]).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    E = oracle.energies(Q)
+    psi = oracle.state(n, LARGE["gamma"], LARGE["beta"], E)
+    oracle.expect(psi, E)
+    oracle.topk(psi, LARGE["k"])
+    dt = time.perf_counter() - t0
+    return {"value": (1 << n) * p / dt, "unit": "amp-layer-updates/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": f"one n=24 twin solve (energies, 2 layers, <C>, top-8) in FP64, {dt:.1f} s"}
+
+
+def run_plain10(args):
+    """The plain n = 10 grid: 256 (gamma, beta) points at p = 1 in complex128, one batch."""
+    import torch
+    import paper_2506_10531_gb300 as q
+    from paper_2506_10531_gb300 import build as qbuild
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, k = PLAIN10["n"], PLAIN10["k"]
+    Q = synth.symmetric_q(n, seed=PLAIN10["seed"] + 1000 * rank)
+    gg, bb = synth.grid_params(16)
+    count = gg.size
+    par = np.stack([gg, bb], axis=1).reshape(-1)
+    ctx = q.qaoa_create(local)
+    qd = torch.as_tensor(Q.reshape(-1)).to(dev)
+    pd = torch.as_tensor(par).to(dev)
+    ex = torch.zeros(count, dtype=torch.float64, device=dev)
+    ti = torch.zeros(count * k, dtype=torch.int64, device=dev)
+    tp = torch.zeros(count * k, dtype=torch.float64, device=dev)
+    io = q.make_io(qd, pd, expect=ex, topk_idx=ti, topk_prob=tp, k_stride=k)
+    insts = q.make_insts([(n, 1, k, 0, 0, 2 * i, -1, -1) for i in range(count)])
+    plan = q.qaoa_plan_create(ctx, insts, io, dbl=True)
+    for _ in range(args.warmup):
+        q.qaoa_plan_launch(plan, stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    kern = {}
+    q.qaoa_plan_set_timing(plan, True)
+
+    def body(s):
+        q.qaoa_plan_launch(plan, stream)
+        _plan_kern_times(q, plan, kern)
+    with Clocks(local) as clk:
+        step_ms = _timed_steps(stream, args.steps, body, flush=lambda: flush.fill_(1))
+    q.qaoa_plan_set_timing(plan, False)
+    tot_s = sum(step_ms) / 1e3
+    # on-chip FP64 work: phase (sincos ~ 20 flops) + 4 flops + 4 flops per qubit per amplitude
+    flops = count * (1 << n) * (24 + 4 * n)
+    props = torch.cuda.get_device_properties(dev)
+    ms_launch = statistics.mean(kern["resident"])
+    mhz = clk.summary().get("sm_mhz") or 1900.0
+    fp64_peak = props.multi_processor_count * 2 * 2 * mhz * 1e6 / 1e12   # 2 FP64 FMA lanes per SM
+    roof = {"bound": "alu", "kernel": "resident", "achieved": flops / (ms_launch * 1e-3) / 1e12,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": flops / (ms_launch * 1e-3) / 1e12 / fp64_peak,
+            "traffic": ncu_traffic("resident"), "ms_per_launch": ms_launch,
+            "peak_source": "derived: SMs x 2 FP64 FMA lanes x 2 x median SM clock (FP64 at 1/64 of FP32)"}
+    Pp = torch.from_numpy(par).pin_memory()
+    Qp = torch.from_numpy(Q.reshape(-1)).pin_memory()
+    oex = torch.empty(count, dtype=torch.float64).pin_memory()
+    oti = torch.empty(count * k, dtype=torch.int64).pin_memory()
+    otp = torch.empty(count * k, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        qd.copy_(Qp, non_blocking=True)
+        pd.copy_(Pp, non_blocking=True)
+        q.qaoa_plan_launch(plan, stream)
+        oex.copy_(ex, non_blocking=True)
+        oti.copy_(ti, non_blocking=True)
+        otp.copy_(tp, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    kernels = q.qaoa_plan_kernel_count(plan)
+    q.qaoa_plan_destroy(plan)
+    q.qaoa_destroy(ctx)
+    line = _line("grid points solved/s (n=10, p=1, complex128: energies + layer + <C> + top-8)",
+                 count * args.steps / tot_s, "solves/s", args, world, 1e3 * tot_s / args.steps,
+                 "c128 state, f64 energies and reductions",
+                 {"workload": "plain n=10 QUBO U[-1,1] (seed 1), p=1, 16x16 (gamma, beta) grid over "
+                              "[0,pi]x[0,pi/2] as 256 resident instances sharing Q, complex128, top-8",
+                  "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
+                 amp_layer_updates_per_s=count * (1 << n) * args.steps / tot_s,
+                 latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+                 kernel_ms_per_step={nm: sum(v) / args.steps for nm, v in kern.items()},
+                 roofline=roof,
+                 e2e={"value": count * args.steps / e2e_s, "unit": "solves/s",
+                      "h2d_bytes_per_step": Q.nbytes + par.nbytes, "d2h_bytes_per_step": count * (8 + 16 * k)},
+                 gpu_launches=kernels * args.steps, clocks=clk.summary())
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        E = oracle.energies(Q)
+        for i in range(count):
+            psi = oracle.state(n, [gg[i]], [bb[i]], E)
+            oracle.expect(psi, E)
+            oracle.topk(psi, k)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": count / dt, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"all 256 grid points in FP64, {dt:.2f} s"}
+    return line
+
+
+def run_uneven(args):
+    """The uneven training batch: 4096 instances (n 8..24, p 1..6, normal Q); one step = <C> and
+    adjoint gradients of every instance plus one Adam update, all on the device."""
+    import torch
+    import paper_2506_10531_gb300 as q
+    from paper_2506_10531_gb300 import build as qbuild
+    from paper_2506_10531_gb300.train import QAOABatch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    U = synth.UNEVEN_BATCH
+    inst = synth.uneven_batch(U["count"], U["seed"] + 1000 * rank, *U["n"], *U["p"], dist=U["dist"])
+    ns = np.array([x[0].shape[0] for x in inst])
+    ps = np.array([len(x[1]) for x in inst])
+    ctx = q.qaoa_create(local)
+    B = QAOABatch(ctx, [x[0] for x in inst], [(x[1], x[2]) for x in inst], device=dev)
+    for _ in range(args.warmup):
+        B.run(stream)
+        B.adam_step(U["lr"], stream)
+    torch.cuda.synchronize()
+    kern = {}
+    q.qaoa_plan_set_timing(B.plan, True)
+
+    def body(s):
+        B.run(stream)
+        _plan_kern_times(q, B.plan, kern)
+        B.adam_step(U["lr"], stream)
+    with Clocks(local) as clk:
+        step_ms = _timed_steps(stream, args.steps, body)
+    q.qaoa_plan_set_timing(B.plan, False)
+    tot_s = sum(step_ms) / 1e3
+    roof = plan_roofline(q, B.plan, kern, lambda: B.run(stream), clk, dev)
+    amps = float(np.sum((2.0 ** ns) * ps))
+    # e2e: Q pool and parameters from pinned host memory, <C> of every instance back, per step
+    qh = B.q.cpu().pin_memory()
+    ph = B.params.cpu().pin_memory()
+    eh = torch.empty(B.count, dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, args.steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        B.q.copy_(qh, non_blocking=True)
+        B.params.copy_(ph, non_blocking=True)
+        B.run(stream)
+        B.adam_step(U["lr"], stream)
+        eh.copy_(B.expect, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    kernels = B.kernels_per_launch + 1
+    B.close()
+    q.qaoa_destroy(ctx)
+    line = _line("instance optimisation steps/s (uneven batch: <C> + adjoint gradient + Adam, all instances)",
+                 B.count * args.steps / tot_s, "instance-steps/s", args, world, 1e3 * tot_s / args.steps,
+                 "c64 state, f32 energies, f64 reductions and gradients",
+                 {"workload": "uneven batch: 4096 sub-QUBOs, n uniform 8..24, p uniform 1..6, Q N(0,1) "
+                              "symmetric (seed 3), complex64, adjoint gradients, Adam lr 0.05",
+                  "l2": "inputs larger than L2 (about 160 GB of states and energies)",
+                  "parallelism": f"replicas x{world}"},
+                 amp_layer_updates_per_s=amps * args.steps / tot_s,
+                 latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+                 kernel_ms_per_step={nm: sum(v) / args.steps for nm, v in kern.items()},
+                 roofline=roof,
+                 e2e={"value": B.count * e2e_steps / e2e_s, "unit": "instance-steps/s",
+                      "h2d_bytes_per_step": int(qh.numel() * 4 + ph.numel() * 4),
+                      "d2h_bytes_per_step": B.count * 8},
+                 gpu_launches=kernels * args.steps, clocks=clk.summary())
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        done, sampled = 0, 0.0
+        for Qi, g, b in inst:
+            if time.perf_counter() - t0 > 10.0:
+                break
+            if Qi.shape[0] > 20:
+                continue
+            E = oracle.energies(Qi.astype(np.float32).astype(np.float64))
+            oracle.grad(Qi.shape[0], g, b, E)
+            done += 1
+            sampled += (2.0 ** Qi.shape[0]) * len(g)
+        dt = time.perf_counter() - t0
+        # the oracle's amp-layer rate on the sample, converted to whole-batch instance steps
+        rate = sampled / dt
+        line["cpu_baseline"] = {"value": B.count * rate / amps, "unit": "instance-steps/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{done} instances of the batch with n <= 20 (energies + adjoint "
+                                          f"gradient, FP64) in {dt:.1f} s: {rate:.3g} amp-layers/s, scaled "
+                                          f"to the batch's {amps:.3g} amp-layers per step"}
+    return line
+
+
+CONFIGS = {"large": run_large, "plain10": run_plain10, "uneven": run_uneven}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,13 +737,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="dqaoa", choices=["dqaoa"] + sorted(CONFIGS),
+                    help="dqaoa: the DQAOA batch cycle (headline); the others are the further "
+                         "measured configurations")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.config == "dqaoa":
         run_ours(args)
+    else:
+        rank, world, _ = dist_env()
+        line = CONFIGS[args.config](args)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -139,10 +139,27 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     // tile map only permutes bits). ----
     if (!P.fin || P.keep_frame) {
         store_tile<T>(P, tau, s.psi, gpsi);
-    } else {
+    } else if (!P.no_store) {
         const int pt = __popcll(tau);
-        for (uint32_t u = threadIdx.x; u < TD; u += blockDim.x)
-            gpsi[global_index(P, tau, u)] = times_i_pow(s.psi[swz<T>(u)], -(pt + __popc(u)));
+        constexpr uint32_t PAIR = sizeof(C) == 8 ? 2u : 1u;
+        const uint32_t step = PAIR * blockDim.x, u0 = PAIR * threadIdx.x;
+        uint64_t gstep;
+        if (linear_walk(P, step, gstep)) {
+            C* g = gpsi + global_index(P, tau, u0);
+            for (uint32_t u = u0; u < TD; u += step, g += gstep) {
+                const uint32_t su = swz<T>(u);
+                if constexpr (PAIR == 2) {
+                    const C a = times_i_pow(s.psi[su], -(pt + __popc(u)));
+                    const C b = times_i_pow(s.psi[su + 1], -(pt + __popc(u + 1)));
+                    *reinterpret_cast<float4*>(g) = make_float4(a.x, a.y, b.x, b.y);
+                } else {
+                    *g = times_i_pow(s.psi[su], -(pt + __popc(u)));
+                }
+            }
+        } else {
+            for (uint32_t u = threadIdx.x; u < TD; u += blockDim.x)
+                gpsi[global_index(P, tau, u)] = times_i_pow(s.psi[swz<T>(u)], -(pt + __popc(u)));
+        }
     }
     if (P.fin) {
         double ex = 0.0;
@@ -195,12 +212,65 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
     }
 }
 
-// Per-instance finalize: <C> = fixed-order sum of the tile partials; top-k = merge of the
-// tile lists (one warp; the result is unique under (probability desc, index asc)).
+// Merge the top-k lists of `nl` lists (list j at tile slot j * stride) into one list of the k
+// best (probability desc, index asc; unique, so any merge order gives the same list): each warp
+// takes a strided share of the entries, then warp 0 merges the warps' lists. The result is in
+// lanes 0..k-1 of warp 0 (f.p, f.z).
+__device__ __forceinline__ void merge_lists(const double* topp, const uint32_t* topz, uint64_t nl,
+                                            uint64_t stride, int k, TopEnt* tops, WarpTopK& f) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpTopK top;
+    top.init(k);
+    const uint64_t nent = nl * (uint64_t)k;
+    for (uint64_t e0 = (uint64_t)warp * 32; e0 < nent; e0 += (uint64_t)(blockDim.x >> 5) * 32) {
+        const uint64_t e = e0 + lane;
+        const bool ok = e < nent;
+        const uint64_t a = ok ? (e / k) * stride * k + e % k : 0;
+        top.offer_exact(ok ? topp[a] : -1.0, ok ? topz[a] : 0u, ok);
+    }
+    if (lane < k) tops[warp * 32 + lane] = TopEnt{top.p, top.z};
+    __syncthreads();
+    if (warp == 0) {
+        f.init(k);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const bool ok = lane < k;
+            const TopEnt e = ok ? tops[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
+            f.offer_exact(e.p, e.z, ok);
+        }
+    }
+}
+
+// First merge level for instances with many tiles: block (c, i) merges the lists of tiles
+// [c * FIN_CHUNK, (c + 1) * FIN_CHUNK) of instance i and writes the result over the list of the
+// chunk's first tile (only this block reads the chunk, and it reads everything first).
+constexpr uint64_t FIN_CHUNK = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stream_topk_chunks(const StreamInst<T>* __restrict__ insts,
+                                                           int count, uint64_t ntiles, int k,
+                                                           const StreamInst<T> one) {
+    __shared__ TopEnt tops[8 * 32];
+    const int ii = blockIdx.y;
+    if (ii >= count) return;
+    const StreamInst<T>& I = insts ? insts[ii] : one;
+    const uint64_t t0 = (uint64_t)blockIdx.x * FIN_CHUNK;
+    const uint64_t nl = (ntiles - t0) < FIN_CHUNK ? (ntiles - t0) : FIN_CHUNK;
+    WarpTopK f;
+    merge_lists(I.part_topp + t0 * k, I.part_topz + t0 * k, nl, 1, k, tops, f);
+    __syncthreads();   // every read of the chunk is done before its first list is overwritten
+    if (threadIdx.x < (unsigned)k) {
+        I.part_topp[t0 * k + threadIdx.x] = f.p;
+        I.part_topz[t0 * k + threadIdx.x] = f.z;
+    }
+}
+
+// Per-instance finalize: <C> = fixed-order sum of the tile partials; top-k = merge of the lists
+// at tile slots 0, stride, 2 stride, ... (stride 1: every tile's list; FIN_CHUNK after the first
+// merge level).
 template <typename T>
 __global__ void __launch_bounds__(256) k_stream_finalize(const StreamInst<T>* __restrict__ insts,
                                                          int count, uint64_t ntiles, int k,
-                                                         const StreamInst<T> one) {
+                                                         uint64_t stride, const StreamInst<T> one) {
     __shared__ double red[32];
     __shared__ TopEnt tops[8 * 32];
     const int ii = blockIdx.x;
@@ -214,30 +284,12 @@ __global__ void __launch_bounds__(256) k_stream_finalize(const StreamInst<T>* __
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0 && I.expect) *I.expect = tot;
     if (k > 0) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        WarpTopK top;
-        top.init(k);
-        // each warp merges a strided subset of tile lists, then warp 0 merges the warps
-        const uint64_t nent = ntiles * (uint64_t)k;
-        for (uint64_t e0 = (uint64_t)warp * 32; e0 < nent; e0 += (uint64_t)(blockDim.x >> 5) * 32) {
-            const uint64_t e = e0 + lane;
-            const bool ok = e < nent;
-            top.offer_exact(ok ? I.part_topp[e] : -1.0, ok ? I.part_topz[e] : 0u, ok);
-        }
-        if (lane < k) tops[warp * 32 + lane] = TopEnt{top.p, top.z};
-        __syncthreads();
-        if (warp == 0) {
-            WarpTopK f;
-            f.init(k);
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                const bool ok = lane < k;
-                const TopEnt e = ok ? tops[w * 32 + lane] : TopEnt{-1.0, 0xffffffffu};
-                f.offer_exact(e.p, e.z, ok);
-            }
-            if (lane < k) {
-                if (I.topk_idx) I.topk_idx[lane] = (uint64_t)f.z;
-                if (I.topk_prob) I.topk_prob[lane] = f.p;
-            }
+        const uint64_t nl = (ntiles + stride - 1) / stride;
+        WarpTopK f;
+        merge_lists(I.part_topp, I.part_topz, nl, stride, k, tops, f);
+        if (threadIdx.x < (unsigned)k) {
+            if (I.topk_idx) I.topk_idx[threadIdx.x] = (uint64_t)f.z;
+            if (I.topk_prob) I.topk_prob[threadIdx.x] = f.p;
         }
     }
 }
@@ -713,10 +765,21 @@ cudaError_t launch_stream_pass(bool dbl, const StreamPass& P, const void* insts,
     return cudaGetLastError();
 }
 
+bool stream_finalize_two_level(uint64_t ntiles, int k) { return k > 0 && ntiles > FIN_CHUNK; }
+
 cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint64_t ntiles, int k,
                                    cudaStream_t st, const void* one) {
-    if (dbl) k_stream_finalize<double><<<count, 256, 0, st>>>(static_cast<const StreamInst<double>*>(insts), count, ntiles, k, one_of<double>(one));
-    else k_stream_finalize<float><<<count, 256, 0, st>>>(static_cast<const StreamInst<float>*>(insts), count, ntiles, k, one_of<float>(one));
+    uint64_t stride = 1;
+    if (stream_finalize_two_level(ntiles, k)) {
+        const dim3 grid((unsigned)((ntiles + FIN_CHUNK - 1) / FIN_CHUNK), (unsigned)count);
+        if (dbl) k_stream_topk_chunks<double><<<grid, 256, 0, st>>>(static_cast<const StreamInst<double>*>(insts), count, ntiles, k, one_of<double>(one));
+        else k_stream_topk_chunks<float><<<grid, 256, 0, st>>>(static_cast<const StreamInst<float>*>(insts), count, ntiles, k, one_of<float>(one));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        stride = FIN_CHUNK;
+    }
+    if (dbl) k_stream_finalize<double><<<count, 256, 0, st>>>(static_cast<const StreamInst<double>*>(insts), count, ntiles, k, stride, one_of<double>(one));
+    else k_stream_finalize<float><<<count, 256, 0, st>>>(static_cast<const StreamInst<float>*>(insts), count, ntiles, k, stride, one_of<float>(one));
     return cudaGetLastError();
 }
 

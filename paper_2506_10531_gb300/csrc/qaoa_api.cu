@@ -527,6 +527,10 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         const int S = stream_plan(dbl, g.n, g.p, g.k, tmp, 256);
         if (S < 0) { delete P; return fail(QAOA_E_INVALID, "no streaming plan for n=%d p=%d", g.n, g.p); }
         if (g.grad) tmp[S - 1].keep_frame = 1;
+        // the final state is written back only when an instance of the group returns it
+        bool any_psi = false;
+        for (int i : kv.second) any_psi = any_psi || desc[i].psi_off >= 0;
+        if (!g.grad && !any_psi) tmp[S - 1].no_store = 1;
         g.passes.assign(tmp, tmp + S);
         int SA = 0;
         if (g.grad) {
@@ -625,7 +629,8 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         }
         e = cudaMemcpy(base + g.inst_off, si.data(), sizeof(StreamInst<T>) * g.count, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload stream instances"); }
-        P->kernels += 1 + (int)g.passes.size() + 1 + (g.grad ? (int)g.apasses.size() + 1 : 0);
+        P->kernels += 1 + (int)g.passes.size() + 1 + (g.grad ? (int)g.apasses.size() + 1 : 0) +
+                      (stream_finalize_two_level(1ull << (g.n - tb), g.k) ? 1 : 0);
         ++gi;
     }
     // algorithmic bytes, in the order qaoa_plan_launch issues the kernels
@@ -658,7 +663,8 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         const double nt = (double)(1ull << (g.n - tb));
         P->bytes.push_back(cnt * (D * sizeof(T) + (double)g.n * g.n * sizeof(T)));
         for (auto& pass : g.passes)
-            P->bytes.push_back(cnt * D * ((pass.init ? 0.0 : sizeof(C2)) + sizeof(C2) + (pass.need_e ? sizeof(T) : 0.0)));
+            P->bytes.push_back(cnt * D * ((pass.init ? 0.0 : sizeof(C2)) + (pass.no_store ? 0.0 : sizeof(C2)) +
+                                          (pass.need_e ? sizeof(T) : 0.0)));
         P->bytes.push_back(cnt * (nt * (sizeof(double) + std::max(g.k, 1) * 12.0) + 8.0 + g.k * 16.0));
         if (g.grad) {
             const int SA = (int)g.apasses.size();

@@ -18,6 +18,7 @@ struct StreamPass {
     int k;          // top-k length when fin
     int need_e;     // the pass reads the energies
     int keep_frame; // fin pass of a gradient run: leave psi in the rotated frame for the adjoint
+    int no_store;   // fin pass whose final state nobody reads: reductions only, no write-back
 };
 
 // One instance of a streaming launch (device pointers).
@@ -54,8 +55,11 @@ size_t stream_smem_bytes(bool dbl);
 // insts: device array of `count` instances, or nullptr to pass the host instance `one` by value.
 cudaError_t launch_stream_pass(bool dbl, const StreamPass& P, const void* insts, int count,
                                int grid, cudaStream_t st, const void* one = nullptr);
+// <C> and top-k of each instance from its tile partials; with many tiles and k > 0 a first
+// merge level runs as its own kernel (stream_finalize_two_level: two launches instead of one).
 cudaError_t launch_stream_finalize(bool dbl, const void* insts, int count, uint64_t ntiles, int k,
                                    cudaStream_t st, const void* one = nullptr);
+bool stream_finalize_two_level(uint64_t ntiles, int k);
 // Adjoint pass `si` (pass P of the adjoint plan, i.e. stream_plan with the adjoint tile bits,
 // run backwards on psi and lam): lam_first forms lam = E psi on load, store == 0 skips writing
 // the states back (last adjoint pass).
