@@ -298,6 +298,61 @@ qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* to
 qaoa_plan* dqaoa_session_plan(dqaoa_session* s);
 void dqaoa_session_destroy(dqaoa_session* s);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Serving: continuous batching of optimise-and-sample jobs. A job is one sub-QUBO (n, p, Q,  */
+/* initial gamma/beta) that runs `steps` Adam steps on <C> (adjoint gradients; Adam replaces  */
+/* the paper's COBYLA loop of Section IV) and then one forward pass returning <C> and the     */
+/* top-k bitstrings at the final parameters (the sample step of Section V step 2). Jobs wait  */
+/* in a FIFO queue and are admitted while a job slot and the job's scratch bytes (the HBM      */
+/* footprint of its state buffers, qaoa_server_job_bytes) are free. Every tick runs one step   */
+/* of every admitted job in a single batched launch; jobs join and leave between ticks. Q,    */
+/* parameters, gradients and Adam moments stay on the device for the job's life. The kernels  */
+/* are batch-invariant: a job's results do not depend on the other jobs of its ticks.         */
+/* This has no counterpart in the paper (its sub-QUBOs run to completion one per core).       */
+/* Single-threaded use. All memory is allocated by qaoa_server_create.                        */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct qaoa_server qaoa_server;
+
+typedef struct {
+    int64_t job_id;
+    int32_t n, p, steps, k;
+    double expect;          /* <C> at the final parameters */
+    uint64_t topk_idx[16];  /* k most probable bitstrings (probability desc, index asc) */
+    double topk_prob[16];   /* their probabilities; unused entries -1 */
+    float params[128];      /* final gamma[p] then beta[p] */
+    double t_submit;        /* qaoa_server_clock() at submission */
+    double t_done;          /* qaoa_server_clock() when poll saw the result */
+} qaoa_job_result;
+
+/* scratch_bytes: device bytes for the jobs' state buffers (admission budget); max_jobs: job
+ * slots (1..65536); k: top-k length of the final pass (0..16). Allocates the job pools, the
+ * scratch and pinned staging. Uses the current device. */
+qaoa_status qaoa_server_create(qaoa_ctx* ctx, size_t scratch_bytes, int max_jobs, int k,
+                               qaoa_server** out);
+void qaoa_server_destroy(qaoa_server* s);
+/* Scratch bytes a job of n qubits and p layers occupies while admitted. */
+size_t qaoa_server_job_bytes(qaoa_server* s, int n, int p);
+/* Queue a job. Q: n*n host floats (row-major); params: 2p host floats (gamma then beta);
+ * steps >= 0 Adam steps at learning rate lr. Copies the inputs. QAOA_E_NOMEM if the job could
+ * never fit the scratch budget. job_id may be NULL. */
+qaoa_status qaoa_server_submit(qaoa_server* s, int n, int p, const float* Q, const float* params,
+                               int steps, float lr, int64_t* job_id);
+/* Admit queued jobs that fit, then enqueue one step of every admitted job on `stream` (async;
+ * blocks only when three earlier ticks are still running). active/queued (may be NULL): jobs
+ * admitted and waiting after admission. */
+qaoa_status qaoa_server_tick(qaoa_server* s, qaoa_stream_t stream, int* active, int* queued);
+/* Copy up to max finished jobs into out (in completion order) and return how many; with
+ * wait != 0 first waits for every tick in flight. */
+int qaoa_server_poll(qaoa_server* s, int wait, qaoa_job_result* out, int max);
+/* Queue and admission state, plus totals over the ticks so far: the algorithmic DRAM bytes of
+ * every launched tick, the device time of the ticks already harvested and the kernel launches
+ * enqueued (any may be NULL). */
+qaoa_status qaoa_server_stats(qaoa_server* s, int* queued, int* active, size_t* scratch_used,
+                              double* bytes_total, double* gpu_ms_total, long long* launches);
+/* Monotonic host clock in seconds (the time base of t_submit / t_done). */
+double qaoa_server_clock(void);
+
 #ifdef __cplusplus
 }
 #endif

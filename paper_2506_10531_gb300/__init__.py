@@ -34,6 +34,8 @@ EXPORTS = [
     "qaoa_expect_topk_static", "qaoa_adam_step",
     "dqaoa_session_create", "dqaoa_session_cycle", "dqaoa_session_results", "dqaoa_session_plan",
     "dqaoa_session_destroy",
+    "qaoa_server_create", "qaoa_server_destroy", "qaoa_server_job_bytes", "qaoa_server_submit",
+    "qaoa_server_tick", "qaoa_server_poll", "qaoa_server_stats", "qaoa_server_clock",
 ]
 
 
@@ -47,6 +49,13 @@ class qaoa_inst(C.Structure):
     _fields_ = [("n", C.c_int32), ("p", C.c_int32), ("k", C.c_int32), ("flags", C.c_int32),
                 ("q_off", C.c_int64), ("par_off", C.c_int64), ("psi_off", C.c_int64),
                 ("e_off", C.c_int64)]
+
+
+class qaoa_job_result(C.Structure):
+    _fields_ = [("job_id", C.c_int64), ("n", C.c_int32), ("p", C.c_int32), ("steps", C.c_int32),
+                ("k", C.c_int32), ("expect", C.c_double), ("topk_idx", C.c_uint64 * 16),
+                ("topk_prob", C.c_double * 16), ("params", C.c_float * 128), ("t_submit", C.c_double),
+                ("t_done", C.c_double)]
 
 
 class qaoa_batch_io(C.Structure):
@@ -118,7 +127,20 @@ def _declare(L):
     L.dqaoa_session_plan.restype = vp
     L.dqaoa_session_destroy.argtypes = [vp]
     L.dqaoa_session_destroy.restype = None
-    del i64, st, dp
+    L.qaoa_server_create.argtypes = [vp, sz, i32, i32, C.POINTER(vp)]
+    L.qaoa_server_destroy.argtypes = [vp]
+    L.qaoa_server_destroy.restype = None
+    L.qaoa_server_job_bytes.argtypes = [vp, i32, i32]
+    L.qaoa_server_job_bytes.restype = sz
+    L.qaoa_server_submit.argtypes = [vp, i32, i32, vp, vp, i32, C.c_float, C.POINTER(i64)]
+    L.qaoa_server_tick.argtypes = [vp, vp, C.POINTER(i32), C.POINTER(i32)]
+    L.qaoa_server_poll.argtypes = [vp, i32, C.POINTER(qaoa_job_result), i32]
+    L.qaoa_server_poll.restype = i32
+    L.qaoa_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(sz), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.qaoa_server_clock.argtypes = []
+    L.qaoa_server_clock.restype = C.c_double
+    del st, dp
 
 
 def _check(status):
@@ -360,3 +382,58 @@ def qaoa_adam_step(count, theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, e
                    stream=None):
     _check(lib().qaoa_adam_step(count, ptr(theta), ptr(grad), ptr(m), ptr(v), step, lr, beta1, beta2, eps,
                                 int(minimise), stream_ptr(stream)))
+
+
+# ---- serving ---------------------------------------------------------------------------------
+
+def qaoa_server_create(ctx, scratch_bytes: int, max_jobs: int, k: int):
+    h = C.c_void_p()
+    _check(lib().qaoa_server_create(ctx, scratch_bytes, max_jobs, k, C.byref(h)))
+    return h
+
+
+def qaoa_server_destroy(srv):
+    lib().qaoa_server_destroy(srv)
+
+
+def qaoa_server_job_bytes(srv, n, p) -> int:
+    return lib().qaoa_server_job_bytes(srv, n, p)
+
+
+def qaoa_server_submit(srv, n, p, Q, params, steps, lr) -> int:
+    """Q: n*n host floats, params: 2p host floats (gamma then beta). Returns the job id."""
+    import numpy as np
+    Qa = np.ascontiguousarray(Q, dtype=np.float32).reshape(-1)
+    Pa = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+    jid = C.c_int64()
+    _check(lib().qaoa_server_submit(srv, n, p, Qa.ctypes.data, Pa.ctypes.data, steps, lr, C.byref(jid)))
+    return jid.value
+
+
+def qaoa_server_tick(srv, stream=None):
+    """Returns (active, queued) after admission."""
+    a, q = C.c_int(), C.c_int()
+    _check(lib().qaoa_server_tick(srv, stream_ptr(stream), C.byref(a), C.byref(q)))
+    return a.value, q.value
+
+
+def qaoa_server_poll(srv, wait=False, max_results=4096):
+    """Finished jobs as a list of qaoa_job_result."""
+    buf = (qaoa_job_result * max_results)()
+    n = lib().qaoa_server_poll(srv, int(wait), buf, max_results)
+    if n < 0:
+        raise QaoaError(QAOA_E_INVALID, "server_poll: NULL server")
+    return [buf[i] for i in range(n)]
+
+
+def qaoa_server_stats(srv):
+    """(queued, active, scratch bytes in use, algorithmic bytes launched, device ms harvested,
+    kernel launches)."""
+    q, a, u, b, t, n = C.c_int(), C.c_int(), C.c_size_t(), C.c_double(), C.c_double(), C.c_longlong()
+    _check(lib().qaoa_server_stats(srv, C.byref(q), C.byref(a), C.byref(u), C.byref(b), C.byref(t),
+                                   C.byref(n)))
+    return q.value, a.value, u.value, b.value, t.value, n.value
+
+
+def qaoa_server_clock() -> float:
+    return lib().qaoa_server_clock()

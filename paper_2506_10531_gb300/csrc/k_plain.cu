@@ -74,14 +74,7 @@ __global__ void k_adam(int count, float* __restrict__ theta, const double* __res
                        float b2, float eps, int minimise) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
-    const float g = minimise ? (float)grad[i] : -(float)grad[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * g;
-    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
-    m[i] = mi;
-    v[i] = vi;
-    const float mh = mi / (1.0f - powf(b1, (float)step));
-    const float vh = vi / (1.0f - powf(b2, (float)step));
-    theta[i] -= lr * mh / (sqrtf(vh) + eps);
+    adam_update(theta[i], m[i], v[i], grad[i], step, lr, b1, b2, eps, minimise);
 }
 }  // namespace
 

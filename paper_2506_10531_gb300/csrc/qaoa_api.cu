@@ -385,8 +385,9 @@ extern "C" qaoa_status qaoa_grad_z(qaoa_ctx* c, int n, int p, const double* g, c
 struct qaoa_plan {
     qaoa_ctx* ctx = nullptr;
     bool dbl = false;
-    void* dev = nullptr;          // one device block: descriptors, scratch, counters
+    void* dev = nullptr;          // one device block: counters and descriptors, then scratch
     size_t dev_bytes = 0;
+    bool owns = true;             // dev was allocated by the plan (else caller memory)
     struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
     struct CluGroup { int n, L, pmax, count; size_t desc_off; int clusters; };
     struct StrGroup { int n, p, k, count; bool grad; size_t inst_off; std::vector<StreamPass> passes;
@@ -404,9 +405,20 @@ struct qaoa_plan {
 
 namespace {
 
+// Caller-provided placement of a plan: the device block lives in [base, base + bytes) and the
+// descriptor header is uploaded asynchronously on `st` from the pinned host buffer `staging`
+// (staging_bytes), which must stay untouched until that copy has run.
+struct PlanMem {
+    void* base;
+    size_t bytes;
+    cudaStream_t st;
+    void* staging;
+    size_t staging_bytes;
+};
+
 template <typename T>
 qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const qaoa_batch_io* io,
-                          qaoa_plan** out) {
+                          const PlanMem* mem, qaoa_plan** out, size_t* need = nullptr) {
     using C2 = typename qaoa::Num<T>::C;
     const bool dbl = is_dbl<T>();
     const T* qpool = static_cast<const T*>(io->q);
@@ -466,8 +478,9 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         x.dbeta = (x.flags & F_GRAD) ? io->grad + d.par_off + d.p : nullptr;
         return x;
     };
-    // sizes
-    size_t bytes = 256;  // counters
+    // layout: header (256 bytes of counters, then every descriptor array) and scratch (the
+    // per-instance buffers of the streaming tier); scratch offsets are relative to its start
+    size_t hdr = 256, scr = 0;
     std::vector<InstDesc<T>> rdesc;
     int qslot = 0;
     for (auto& kv : rg) {
@@ -476,14 +489,14 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         g.grad = kv.first.second != 0;
         g.count = (int)kv.second.size();
         g.pmax = 1;
-        g.desc_off = bytes;
+        g.desc_off = hdr;
         g.q_slot = qslot++;
         for (int i : kv.second) {
             const qaoa_inst& d = desc[i];
             g.pmax = std::max(g.pmax, d.p);
             rdesc.push_back(make_desc(i));
         }
-        bytes = align256(bytes + sizeof(InstDesc<T>) * g.count);
+        hdr = align256(hdr + sizeof(InstDesc<T>) * g.count);
         const int occ = std::max(1, resident_max_blocks_per_sm(dbl, g.n, g.pmax, g.grad));
         g.grid = std::min(g.count, occ * c->nsm);
         P->res.push_back(g);
@@ -495,12 +508,12 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         g.L = c->cluster_L[g.n] ? c->cluster_L[g.n] : 14;
         g.count = (int)kv.second.size();
         g.pmax = 1;
-        g.desc_off = bytes;
+        g.desc_off = hdr;
         for (int i : kv.second) {
             g.pmax = std::max(g.pmax, desc[i].p);
             cdesc.push_back(make_desc(i));
         }
-        bytes = align256(bytes + sizeof(InstDesc<T>) * g.count);
+        hdr = align256(hdr + sizeof(InstDesc<T>) * g.count);
         int mc = 0;
         cudaError_t e = launch_cluster(nullptr, 0, g.n, g.L, g.pmax, 0, nullptr, &mc);
         if (e != cudaSuccess || mc < 1) {
@@ -540,27 +553,27 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             g.apasses.assign(atmp, atmp + SA);
         }
         const uint64_t nta = 1ull << (g.n - tba);
-        g.inst_off = bytes;
-        bytes = align256(bytes + sizeof(StreamInst<T>) * g.count);
+        g.inst_off = hdr;
+        hdr = align256(hdr + sizeof(StreamInst<T>) * g.count);
         std::vector<SI> v;
         const uint64_t D = 1ull << g.n, nt = 1ull << (g.n - tb);
         for (int i : kv.second) {
             SI s{};
             const qaoa_inst& d = desc[i];
-            s.e_off = (d.e_off >= 0) ? (size_t)-1 : bytes;
-            if (d.e_off < 0) bytes = align256(bytes + D * sizeof(T));
-            s.psi_off = (d.psi_off >= 0) ? (size_t)-1 : bytes;
-            if (d.psi_off < 0) bytes = align256(bytes + D * sizeof(C2));
-            s.part_off = bytes;
-            bytes = align256(bytes + nt * sizeof(double));
-            bytes = align256(bytes + nt * std::max(g.k, 1) * sizeof(double));
-            bytes = align256(bytes + nt * std::max(g.k, 1) * sizeof(uint32_t));
+            s.e_off = (d.e_off >= 0) ? (size_t)-1 : scr;
+            if (d.e_off < 0) scr = align256(scr + D * sizeof(T));
+            s.psi_off = (d.psi_off >= 0) ? (size_t)-1 : scr;
+            if (d.psi_off < 0) scr = align256(scr + D * sizeof(C2));
+            s.part_off = scr;
+            scr = align256(scr + nt * sizeof(double));
+            scr = align256(scr + nt * std::max(g.k, 1) * sizeof(double));
+            scr = align256(scr + nt * std::max(g.k, 1) * sizeof(uint32_t));
             s.lam_off = s.grad_off = 0;
             if (g.grad) {
-                s.lam_off = bytes;
-                bytes = align256(bytes + D * sizeof(C2));
-                s.grad_off = bytes;
-                bytes = align256(bytes + (size_t)SA * nta * 4 * sizeof(double));
+                s.lam_off = scr;
+                scr = align256(scr + D * sizeof(C2));
+                s.grad_off = scr;
+                scr = align256(scr + (size_t)SA * nta * 4 * sizeof(double));
             }
             v.push_back(s);
         }
@@ -570,23 +583,37 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         sinfo.push_back(v);
         P->str.push_back(std::move(g));
     }
-    cudaError_t e = cudaMalloc(&P->dev, bytes);
-    if (e != cudaSuccess) { delete P; return fail(QAOA_E_NOMEM, "plan cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e)); }
+    const size_t sbase = align256(hdr);
+    const size_t bytes = sbase + scr;
+    if (need) *need = bytes;
+    cudaError_t e = cudaSuccess;
+    if (mem) {
+        if (bytes > mem->bytes || sbase > mem->staging_bytes) {
+            delete P;
+            return fail(QAOA_E_NOMEM, "plan needs %zu bytes (%zu of header), %zu / %zu provided", bytes, sbase,
+                        mem->bytes, mem->staging_bytes);
+        }
+        P->dev = mem->base;
+        P->owns = false;
+    } else {
+        e = cudaMalloc(&P->dev, bytes);
+        if (e != cudaSuccess) { delete P; return fail(QAOA_E_NOMEM, "plan cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e)); }
+    }
     P->dev_bytes = bytes;
     char* base = static_cast<char*>(P->dev);
-    // upload resident descriptors
+    char* sb = base + sbase;
+    // host image of the header: zero counters, then the descriptor arrays
+    std::vector<char> img(sbase, 0);
     size_t ri = 0;
     for (auto& g : P->res) {
-        e = cudaMemcpy(base + g.desc_off, rdesc.data() + ri, sizeof(InstDesc<T>) * g.count, cudaMemcpyHostToDevice);
+        std::memcpy(img.data() + g.desc_off, rdesc.data() + ri, sizeof(InstDesc<T>) * g.count);
         ri += g.count;
-        if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload descriptors"); }
         P->kernels += 2;  // memset counter + kernel
     }
     size_t ci = 0;
     for (auto& g : P->clu) {
-        e = cudaMemcpy(base + g.desc_off, cdesc.data() + ci, sizeof(InstDesc<T>) * g.count, cudaMemcpyHostToDevice);
+        std::memcpy(img.data() + g.desc_off, cdesc.data() + ci, sizeof(InstDesc<T>) * g.count);
         ci += g.count;
-        if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload cluster descriptors"); }
         P->kernels += 1;
     }
     // build streaming instances
@@ -605,10 +632,10 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             I.gamma = ppool + d.par_off;
             I.beta = ppool + d.par_off + d.p;
             I.Q = qpool + d.q_off;
-            I.psi = (s.psi_off == (size_t)-1) ? (void*)(psipool + d.psi_off) : (void*)(base + s.psi_off);
-            T* Ebuf = (s.e_off == (size_t)-1) ? epool + d.e_off : reinterpret_cast<T*>(base + s.e_off);
+            I.psi = (s.psi_off == (size_t)-1) ? (void*)(psipool + d.psi_off) : (void*)(sb + s.psi_off);
+            T* Ebuf = (s.e_off == (size_t)-1) ? epool + d.e_off : reinterpret_cast<T*>(sb + s.e_off);
             I.E = Ebuf;
-            char* pw = base + s.part_off;
+            char* pw = sb + s.part_off;
             I.part_expect = reinterpret_cast<double*>(pw);
             pw += align256(nt * sizeof(double));
             I.part_topp = reinterpret_cast<double*>(pw);
@@ -618,8 +645,8 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             I.topk_idx = d.k > 0 ? io->topk_idx + (int64_t)i * io->k_stride : nullptr;
             I.topk_prob = (d.k > 0 && io->topk_prob) ? io->topk_prob + (int64_t)i * io->k_stride : nullptr;
             if (g.grad) {
-                I.lam = base + s.lam_off;
-                I.part_grad = reinterpret_cast<double*>(base + s.grad_off);
+                I.lam = sb + s.lam_off;
+                I.part_grad = reinterpret_cast<double*>(sb + s.grad_off);
                 I.dgamma = io->grad + d.par_off;
                 I.dbeta = io->grad + d.par_off + d.p;
             }
@@ -627,12 +654,20 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             g.q.push_back(qpool + d.q_off);
             g.e.push_back(Ebuf);
         }
-        e = cudaMemcpy(base + g.inst_off, si.data(), sizeof(StreamInst<T>) * g.count, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload stream instances"); }
+        std::memcpy(img.data() + g.inst_off, si.data(), sizeof(StreamInst<T>) * g.count);
         P->kernels += 1 + (int)g.passes.size() + 1 + (g.grad ? (int)g.apasses.size() + 1 : 0) +
                       (stream_finalize_two_level(1ull << (g.n - tb), g.k) ? 1 : 0);
         ++gi;
     }
+    // upload the header: synchronously into the plan's own memory, else asynchronously on the
+    // caller's stream from its pinned staging buffer
+    if (mem) {
+        std::memcpy(mem->staging, img.data(), sbase);
+        e = cudaMemcpyAsync(base, mem->staging, sbase, cudaMemcpyHostToDevice, mem->st);
+    } else {
+        e = cudaMemcpy(base, img.data(), sbase, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) { qaoa_plan_destroy(P); return cuda_fail(e, "upload plan descriptors"); }
     // algorithmic bytes, in the order qaoa_plan_launch issues the kernels
     for (auto& g : P->res) {
         double b = 0.0;
@@ -681,14 +716,55 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
 
 }  // namespace
 
+namespace qaoa {
+
+// Record an error message for qaoa_last_error from another translation unit.
+qaoa_status set_error(qaoa_status st, const char* msg) { return fail(st, "%s", msg); }
+
+// Scratch bytes one complex64 instance adds to a plan (the streaming tier's per-instance
+// buffers; the resident and cluster tiers need none), as plan_create_t lays them out.
+size_t plan_inst_scratch_bytes(qaoa_ctx* c, int n, int p, int k, bool grad) {
+    const bool res = n <= RES_NMAX_F && (!grad || n <= RES_NMAX_F_ADJ);
+    const bool clu = !grad && n >= CL_NMIN && n <= CL_NMAX && c->tier[n] != QAOA_TIER_STREAM;
+    if (res || clu) return 0;
+    const int tb = stream_tile_bits(false), tba = stream_adj_tile_bits(false);
+    const size_t D = (size_t)1 << n, nt = (size_t)1 << (n - tb), kk = (size_t)std::max(k, 1);
+    size_t b = align256(D * sizeof(float)) + align256(D * sizeof(float2)) + align256(nt * sizeof(double)) +
+               align256(nt * kk * sizeof(double)) + align256(nt * kk * sizeof(uint32_t));
+    if (grad) {
+        StreamPass tmp[256];
+        const int SA = stream_plan(false, n, p, 0, tmp, 256, tba);
+        b += align256(D * sizeof(float2)) + align256((size_t)std::max(SA, 0) * ((size_t)1 << (n - tba)) * 32);
+    }
+    return b;
+}
+
+// Upper bound of a complex64 plan's header (counters and descriptor arrays) for `count` instances.
+size_t plan_header_bound(int count) {
+    const size_t d = std::max(sizeof(InstDesc<float>), sizeof(StreamInst<float>));
+    return align256(256 + (size_t)count * (align256(d) + 256));
+}
+
+// A complex64 plan placed in caller memory, its header uploaded on `st` from pinned `staging`.
+qaoa_status plan_create_placed(qaoa_ctx* c, const qaoa_inst* desc, int count, const qaoa_batch_io* io,
+                               void* base, size_t bytes, cudaStream_t st, void* staging,
+                               size_t staging_bytes, qaoa_plan** out) {
+    if (!c || !desc || !io || !out || count < 1) return fail(QAOA_E_INVALID, "plan_create_placed: bad arguments");
+    *out = nullptr;
+    const PlanMem m{base, bytes, st, staging, staging_bytes};
+    return plan_create_t<float>(c, desc, count, io, &m, out);
+}
+
+}  // namespace qaoa
+
 extern "C" qaoa_status qaoa_plan_create(qaoa_ctx* c, const qaoa_inst* desc, int count,
                                         const qaoa_batch_io* io, int dbl, qaoa_plan** out) {
     if (!c || !desc || !io || !out || count < 1 || !io->q || !io->params)
         return fail(QAOA_E_INVALID, "plan_create: NULL argument or count < 1");
     *out = nullptr;
     CK(cudaSetDevice(c->device));
-    return dbl ? plan_create_t<double>(c, desc, count, io, out)
-               : plan_create_t<float>(c, desc, count, io, out);
+    return dbl ? plan_create_t<double>(c, desc, count, io, nullptr, out)
+               : plan_create_t<float>(c, desc, count, io, nullptr, out);
 }
 
 extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
@@ -782,9 +858,11 @@ extern "C" int qaoa_plan_kernel_bytes(const qaoa_plan* P, double* bytes, int max
 extern "C" void qaoa_plan_destroy(qaoa_plan* P) {
     if (!P) return;
     cudaSetDevice(P->ctx->device);
-    cudaDeviceSynchronize();
+    if (P->owns) {
+        cudaDeviceSynchronize();
+        cudaFree(P->dev);
+    }
     for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
-    cudaFree(P->dev);
     delete P;
 }
 

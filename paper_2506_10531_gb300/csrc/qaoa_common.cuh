@@ -48,6 +48,21 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ---- optimiser ------------------------------------------------------------------------------
+// One Adam step (Kingma & Ba 2015) on one parameter; step >= 1 (bias correction). Shared by the
+// flat-array and the per-job (serving) update kernels so both give the same bits.
+__device__ __forceinline__ void adam_update(float& theta, float& m, float& v, double grad, int step,
+                                            float lr, float b1, float b2, float eps, int minimise) {
+    const float g = minimise ? (float)grad : -(float)grad;
+    const float mi = b1 * m + (1.0f - b1) * g;
+    const float vi = b2 * v + (1.0f - b2) * g * g;
+    m = mi;
+    v = vi;
+    const float mh = mi / (1.0f - powf(b1, (float)step));
+    const float vh = vi / (1.0f - powf(b2, (float)step));
+    theta -= lr * mh / (sqrtf(vh) + eps);
+}
+
 // ---- complex helpers ---------------------------------------------------------------------
 
 __device__ __forceinline__ void sincos_phase(float g_over_pi, float e, float& s, float& c) {

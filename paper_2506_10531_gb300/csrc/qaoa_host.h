@@ -26,3 +26,14 @@ cudaError_t launch_plain_layers(int n, int p, const float* gamma, const float* b
 cudaError_t launch_adam(int count, float* theta, const double* grad, float* m, float* v, int step,
                         float lr, float b1, float b2, float eps, int minimise, cudaStream_t st);
 }  // namespace qaoa
+
+// Plans placed in caller memory (used by the serving loop; qaoa_api.cu).
+#include "../../include/qaoa.h"
+namespace qaoa {
+size_t plan_inst_scratch_bytes(qaoa_ctx* c, int n, int p, int k, bool grad);
+size_t plan_header_bound(int count);
+qaoa_status plan_create_placed(qaoa_ctx* c, const qaoa_inst* desc, int count, const qaoa_batch_io* io,
+                               void* base, size_t bytes, cudaStream_t st, void* staging,
+                               size_t staging_bytes, qaoa_plan** out);
+qaoa_status set_error(qaoa_status s, const char* msg);
+}  // namespace qaoa
