@@ -76,6 +76,22 @@ size_t qaoa_workspace_bytes(int n, int dbl);
 enum { QAOA_TIER_AUTO = 0, QAOA_TIER_CLUSTER = 2, QAOA_TIER_STREAM = 3 };
 qaoa_status qaoa_set_tier(qaoa_ctx* ctx, int n, int tier, int param);
 
+/* Autotuner (no counterpart in the paper). Times every kernel configuration that can run a
+ * complex64 batch of `count` instances of (n, p) with top-k length k -- for 15 <= n <= 18 the
+ * cluster tier with 13 or 14 local qubits per CTA and the streaming tier; elsewhere the single
+ * configuration -- on synthetic inputs (best of 5 timed plan launches on `stream`, CUDA events)
+ * and stores the fastest for (n, p) in the context; plans created later use it unless
+ * qaoa_set_tier overrides n. best_ms (may be NULL): the winning batch time. Synchronous;
+ * allocates temporary buffers. */
+qaoa_status qaoa_autotune(qaoa_ctx* ctx, int n, int p, int k, int count, qaoa_stream_t stream,
+                          double* best_ms);
+/* The stored choice for (n, p): tier 0 when none. */
+qaoa_status qaoa_tuning_get(qaoa_ctx* ctx, int n, int p, int* tier, int* param, double* ms);
+/* Save / load the stored choices as JSON ({"format": "libqaoa-tuning-1", "entries": [...]}).
+ * Loading adds the file's valid entries to the context. */
+qaoa_status qaoa_tuning_save(qaoa_ctx* ctx, const char* path);
+qaoa_status qaoa_tuning_load(qaoa_ctx* ctx, const char* path);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Single instance, complex64 (FP32 energies). All pointers device, all calls async.         */
 /* ---------------------------------------------------------------------------------------- */
@@ -188,6 +204,12 @@ qaoa_status qaoa_plan_create(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
 /* Enqueue the whole batch on `stream` (kernel launches and memsets only, so the call can be
  * captured in a CUDA graph). Async. */
 qaoa_status qaoa_plan_launch(qaoa_plan* plan, qaoa_stream_t stream);
+/* Record the plan's launch sequence once into a CUDA graph (stream capture on `stream`, which
+ * must not be capturing already); every later qaoa_plan_launch replays the graph with one
+ * cudaGraphLaunch instead of issuing each kernel. The graph reads the same bound buffers, so
+ * new inputs written there are picked up. Per-kernel timing is not available for a captured
+ * plan. Synchronous. */
+qaoa_status qaoa_plan_capture(qaoa_plan* plan, qaoa_stream_t stream);
 /* Number of kernel launches one qaoa_plan_launch enqueues. */
 int qaoa_plan_kernel_count(const qaoa_plan* plan);
 /* Per-kernel timing: with on != 0 every later qaoa_plan_launch records a CUDA event before and

@@ -36,6 +36,7 @@ EXPORTS = [
     "dqaoa_session_destroy",
     "qaoa_server_create", "qaoa_server_destroy", "qaoa_server_job_bytes", "qaoa_server_submit",
     "qaoa_server_tick", "qaoa_server_poll", "qaoa_server_stats", "qaoa_server_clock",
+    "qaoa_autotune", "qaoa_tuning_get", "qaoa_tuning_save", "qaoa_tuning_load", "qaoa_plan_capture",
 ]
 
 
@@ -138,6 +139,11 @@ def _declare(L):
     L.qaoa_server_poll.restype = i32
     L.qaoa_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(sz), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.qaoa_autotune.argtypes = [vp, i32, i32, i32, i32, vp, C.POINTER(C.c_double)]
+    L.qaoa_tuning_get.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)]
+    L.qaoa_tuning_save.argtypes = [vp, C.c_char_p]
+    L.qaoa_tuning_load.argtypes = [vp, C.c_char_p]
+    L.qaoa_plan_capture.argtypes = [vp, vp]
     L.qaoa_server_clock.argtypes = []
     L.qaoa_server_clock.restype = C.c_double
     del st, dp
@@ -221,8 +227,11 @@ def qaoa_grad(ctx, n, p, gamma, beta, E, expect, dgamma, dbeta, stream=None, dbl
 
 def make_io(q, params, expect=None, topk_idx=None, topk_prob=None, k_stride=0, psi=None, e=None,
             grad=None) -> qaoa_batch_io:
-    return qaoa_batch_io(ptr(q), ptr(params), ptr(psi), ptr(e), ptr(expect), ptr(topk_idx),
-                         ptr(topk_prob), k_stride, ptr(grad))
+    io = qaoa_batch_io(ptr(q), ptr(params), ptr(psi), ptr(e), ptr(expect), ptr(topk_idx),
+                       ptr(topk_prob), k_stride, ptr(grad))
+    # the descriptor holds raw addresses: keep the buffers alive as long as it is
+    io._keep = (q, params, expect, topk_idx, topk_prob, psi, e, grad)
+    return io
 
 
 def make_insts(rows):
@@ -437,3 +446,32 @@ def qaoa_server_stats(srv):
 
 def qaoa_server_clock() -> float:
     return lib().qaoa_server_clock()
+
+
+# ---- autotuner and graph capture -------------------------------------------------------------
+
+def qaoa_autotune(ctx, n, p, k, count, stream=None) -> float:
+    """Time the configurations for (n, p) batches and store the fastest; returns its ms."""
+    ms = C.c_double()
+    _check(lib().qaoa_autotune(ctx, n, p, k, count, stream_ptr(stream), C.byref(ms)))
+    return ms.value
+
+
+def qaoa_tuning_get(ctx, n, p):
+    """(tier, param, ms) stored for (n, p); tier 0 when none."""
+    t, prm, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(lib().qaoa_tuning_get(ctx, n, p, C.byref(t), C.byref(prm), C.byref(ms)))
+    return t.value, prm.value, ms.value
+
+
+def qaoa_tuning_save(ctx, path):
+    _check(lib().qaoa_tuning_save(ctx, os.fsencode(path)))
+
+
+def qaoa_tuning_load(ctx, path):
+    _check(lib().qaoa_tuning_load(ctx, os.fsencode(path)))
+
+
+def qaoa_plan_capture(plan, stream):
+    """Capture the plan's launch into a CUDA graph; later launches replay it (non-legacy stream)."""
+    _check(lib().qaoa_plan_capture(plan, stream_ptr(stream)))

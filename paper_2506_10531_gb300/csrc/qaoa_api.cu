@@ -19,15 +19,7 @@
 
 using namespace qaoa;
 
-struct qaoa_ctx {
-    int device = 0;
-    int nsm = 0;
-    void* ws = nullptr;       // workspace (device)
-    size_t ws_bytes = 0;
-    int* queue = nullptr;     // work counters of the single-call launches (device)
-    int tier[32] = {0};       // QAOA_TIER_* per n for complex64 plans (0: automatic)
-    int cluster_L[32] = {0};  // local qubits per CTA of the cluster tier by n (0: default 14)
-};
+#include "qaoa_ctx.h"
 
 namespace {
 
@@ -388,6 +380,7 @@ struct qaoa_plan {
     void* dev = nullptr;          // one device block: counters and descriptors, then scratch
     size_t dev_bytes = 0;
     bool owns = true;             // dev was allocated by the plan (else caller memory)
+    cudaGraphExec_t graph = nullptr;  // captured launch sequence (qaoa_plan_capture)
     struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
     struct CluGroup { int n, L, pmax, count; size_t desc_off; int clusters; };
     struct StrGroup { int n, p, k, count; bool grad; size_t inst_off; std::vector<StreamPass> passes;
@@ -449,7 +442,7 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     P->dbl = dbl;
     // group: resident by (n, grad); streaming by (n, p, k)
     std::map<std::pair<int, int>, std::vector<int>> rg;
-    std::map<int, std::vector<int>> cg;
+    std::map<std::pair<int, int>, std::vector<int>> cg;   // cluster groups by (n, local qubits)
     std::map<std::tuple<int, int, int, int>, std::vector<int>> sg;
     const int nres = dbl ? RES_NMAX_D : RES_NMAX_F;
     const int nres_adj = dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ;
@@ -457,8 +450,8 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         const qaoa_inst& d = desc[i];
         const bool grad = (d.flags & QAOA_INST_GRAD) != 0;
         if (d.n <= nres && (!grad || d.n <= nres_adj)) rg[{d.n, grad ? 1 : 0}].push_back(i);
-        else if (!dbl && !grad && d.n >= CL_NMIN && d.n <= CL_NMAX && c->tier[d.n] != QAOA_TIER_STREAM)
-            cg[d.n].push_back(i);
+        else if (!dbl && !grad && d.n >= CL_NMIN && d.n <= CL_NMAX && qaoa::eff_tier(c, d.n, d.p) != QAOA_TIER_STREAM)
+            cg[{d.n, qaoa::eff_cluster_L(c, d.n, d.p)}].push_back(i);
         else sg[{d.n, d.p, d.k, grad ? 1 : 0}].push_back(i);
     }
     auto make_desc = [&](int i) {
@@ -504,8 +497,8 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     std::vector<InstDesc<T>> cdesc;
     for (auto& kv : cg) {
         qaoa_plan::CluGroup g{};
-        g.n = kv.first;
-        g.L = c->cluster_L[g.n] ? c->cluster_L[g.n] : 14;
+        g.n = kv.first.first;
+        g.L = kv.first.second;
         g.count = (int)kv.second.size();
         g.pmax = 1;
         g.desc_off = hdr;
@@ -725,7 +718,7 @@ qaoa_status set_error(qaoa_status st, const char* msg) { return fail(st, "%s", m
 // buffers; the resident and cluster tiers need none), as plan_create_t lays them out.
 size_t plan_inst_scratch_bytes(qaoa_ctx* c, int n, int p, int k, bool grad) {
     const bool res = n <= RES_NMAX_F && (!grad || n <= RES_NMAX_F_ADJ);
-    const bool clu = !grad && n >= CL_NMIN && n <= CL_NMAX && c->tier[n] != QAOA_TIER_STREAM;
+    const bool clu = !grad && n >= CL_NMIN && n <= CL_NMAX && eff_tier(c, n, p) != QAOA_TIER_STREAM;
     if (res || clu) return 0;
     const int tb = stream_tile_bits(false), tba = stream_adj_tile_bits(false);
     const size_t D = (size_t)1 << n, nt = (size_t)1 << (n - tb), kk = (size_t)std::max(k, 1);
@@ -767,9 +760,47 @@ extern "C" qaoa_status qaoa_plan_create(qaoa_ctx* c, const qaoa_inst* desc, int 
                : plan_create_t<float>(c, desc, count, io, nullptr, out);
 }
 
+namespace {
+qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st);
+}
+
 extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
     if (!P) return fail(QAOA_E_INVALID, "plan is NULL");
     cudaStream_t st = (cudaStream_t)stream;
+    if (P->graph) {
+        CK(cudaGraphLaunch(P->graph, st));
+        return QAOA_OK;
+    }
+    return plan_enqueue(P, st);
+}
+
+extern "C" qaoa_status qaoa_plan_capture(qaoa_plan* P, qaoa_stream_t stream) {
+    if (!P || !stream) return fail(QAOA_E_INVALID, "plan_capture: NULL plan or the legacy stream");
+    if (P->graph) return QAOA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool timing = P->timing;
+    P->timing = false;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const qaoa_status q = plan_enqueue(P, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    P->timing = timing;
+    if (q != QAOA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return q;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    const cudaError_t e2 = cudaGraphInstantiate(&P->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        P->graph = nullptr;
+        return cuda_fail(e2, "cudaGraphInstantiate");
+    }
+    return QAOA_OK;
+}
+
+namespace {
+qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st) {
     char* base = static_cast<char*>(P->dev);
     int* counters = reinterpret_cast<int*>(base);
     P->names.clear();
@@ -827,6 +858,8 @@ extern "C" qaoa_status qaoa_plan_launch(qaoa_plan* P, qaoa_stream_t stream) {
     return QAOA_OK;
 }
 
+}  // namespace
+
 extern "C" qaoa_status qaoa_plan_set_timing(qaoa_plan* P, int on) {
     if (!P) return fail(QAOA_E_INVALID, "plan is NULL");
     P->timing = on != 0;
@@ -858,6 +891,7 @@ extern "C" int qaoa_plan_kernel_bytes(const qaoa_plan* P, double* bytes, int max
 extern "C" void qaoa_plan_destroy(qaoa_plan* P) {
     if (!P) return;
     cudaSetDevice(P->ctx->device);
+    if (P->graph) cudaGraphExecDestroy(P->graph);
     if (P->owns) {
         cudaDeviceSynchronize();
         cudaFree(P->dev);

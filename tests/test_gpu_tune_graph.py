@@ -1,0 +1,127 @@
+"""Autotuner table (tune, store, save / load as JSON, plans follow it) and CUDA-graph capture of
+a plan (replays give the same results as direct launches and pick up new inputs)."""
+import json
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_10531_gb300 import build
+    build.build()
+    import paper_2506_10531_gb300 as qq
+    return qq
+
+
+def batch(q, specs, seed):
+    Qs, pars, rows = [], [], []
+    qo = po = 0
+    for i, (n, p, k) in enumerate(specs):
+        Q = synth.symmetric_q(n, seed=seed + i).astype(np.float32)
+        g, b = synth.random_params(p, seed=seed + 100 + i)
+        Qs.append(Q.reshape(-1))
+        pars.append(np.concatenate([g, b]).astype(np.float32))
+        rows.append((n, p, k, 0, qo, po, -1, -1))
+        qo += n * n
+        po += 2 * p
+    qd = torch.as_tensor(np.concatenate(Qs)).cuda()
+    pd = torch.as_tensor(np.concatenate(pars)).cuda()
+    cnt = len(specs)
+    ex = torch.zeros(cnt, dtype=torch.float64, device="cuda")
+    ti = torch.zeros(cnt * 8, dtype=torch.int64, device="cuda")
+    tp = torch.zeros(cnt * 8, dtype=torch.float64, device="cuda")
+    io = q.make_io(qd, pd, expect=ex, topk_idx=ti, topk_prob=tp, k_stride=8)
+    return q.make_insts(rows), io, pd, (ex, ti, tp)
+
+
+def test_autotune_table_roundtrip(q, tmp_path):
+    ctx = q.qaoa_create(0)
+    try:
+        ms = q.qaoa_autotune(ctx, 16, 3, 8, 64)
+        assert ms > 0
+        tier, prm, ms2 = q.qaoa_tuning_get(ctx, 16, 3)
+        assert tier in (q.QAOA_TIER_CLUSTER, q.QAOA_TIER_STREAM) and ms2 == pytest.approx(ms)
+        if tier == q.QAOA_TIER_CLUSTER:
+            assert prm in (13, 14)
+        assert q.qaoa_tuning_get(ctx, 16, 4)[0] == 0       # only the tuned shape is stored
+        ms_small = q.qaoa_autotune(ctx, 12, 2, 8, 64)       # one configuration: timed, not stored
+        assert ms_small > 0 and q.qaoa_tuning_get(ctx, 12, 2)[0] == 0
+        path = tmp_path / "tuning.json"
+        q.qaoa_tuning_save(ctx, str(path))
+        doc = json.loads(path.read_text())
+        assert doc["format"] == "libqaoa-tuning-1"
+        assert [(e["n"], e["p"], e["tier"]) for e in doc["entries"]] == [(16, 3, tier)]
+    finally:
+        q.qaoa_destroy(ctx)
+    ctx2 = q.qaoa_create(0)
+    try:
+        q.qaoa_tuning_load(ctx2, str(path))
+        assert q.qaoa_tuning_get(ctx2, 16, 3)[:2] == (tier, prm)
+        insts, io, _, _ = batch(q, [(16, 3, 8)] * 4, 5)
+        plan = q.qaoa_plan_create(ctx2, insts, io)
+        try:
+            q.qaoa_plan_set_timing(plan, True)
+            q.qaoa_plan_launch(plan)
+            names = {nm for nm, _ in q.qaoa_plan_kernel_times(plan)}
+            assert ("cluster" in names) == (tier == q.QAOA_TIER_CLUSTER)
+            assert ("stream_pass" in names) == (tier == q.QAOA_TIER_STREAM)
+        finally:
+            q.qaoa_plan_destroy(plan)
+        # an explicit tier setting overrides the table
+        q.qaoa_set_tier(ctx2, 16, q.QAOA_TIER_STREAM, 0)
+        plan = q.qaoa_plan_create(ctx2, insts, io)
+        try:
+            q.qaoa_plan_set_timing(plan, True)
+            q.qaoa_plan_launch(plan)
+            assert "stream_pass" in {nm for nm, _ in q.qaoa_plan_kernel_times(plan)}
+        finally:
+            q.qaoa_plan_destroy(plan)
+    finally:
+        q.qaoa_destroy(ctx2)
+
+
+def test_plan_graph_capture_replays(q):
+    ctx = q.qaoa_create(0)
+    specs = [(10, 2, 8), (14, 3, 8), (16, 2, 8), (20, 2, 8), (12, 1, 8), (16, 2, 8)]
+    try:
+        insts, io, pd, outs = batch(q, specs, 31)
+        direct = q.qaoa_plan_create(ctx, insts, io)
+        q.qaoa_plan_launch(direct)
+        torch.cuda.synchronize()
+        ref = [o.clone() for o in outs]
+        s = torch.cuda.Stream()
+        graph = q.qaoa_plan_create(ctx, insts, io)
+        q.qaoa_plan_capture(graph, s)
+        for o in outs:
+            o.zero_()
+        torch.cuda.synchronize()
+        for _ in range(2):
+            q.qaoa_plan_launch(graph, s)
+        s.synchronize()
+        for a, b in zip(outs, ref):
+            assert torch.equal(a, b)
+        # new parameters written into the bound pool are seen by the replay
+        pd.mul_(0.5)
+        q.qaoa_plan_launch(direct)
+        torch.cuda.synchronize()
+        ref2 = [o.clone() for o in outs]
+        assert not torch.equal(ref2[0], ref[0])
+        for o in outs:
+            o.zero_()
+        torch.cuda.synchronize()
+        q.qaoa_plan_launch(graph, s)
+        s.synchronize()
+        for a, b in zip(outs, ref2):
+            assert torch.equal(a, b)
+        q.qaoa_plan_destroy(graph)
+        q.qaoa_plan_destroy(direct)
+    finally:
+        q.qaoa_destroy(ctx)
