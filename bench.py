@@ -459,7 +459,7 @@ def run_large(args):
     qbuild.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    n, p, k = LARGE["n"], LARGE["p"], LARGE["k"]
+    n, p, k = args.large_n, LARGE["p"], LARGE["k"]
     Q = synth.symmetric_q(n, seed=LARGE["seed"] + 1000 * rank).astype(np.float32)
     par = np.array(LARGE["gamma"] + LARGE["beta"], dtype=np.float32)
     ctx = q.qaoa_create(local)
@@ -505,12 +505,12 @@ def run_large(args):
     kernels = q.qaoa_plan_kernel_count(plan)
     q.qaoa_plan_destroy(plan)
     q.qaoa_destroy(ctx)
-    line = _line("amp-layer-updates/s (n=30 streaming solve: energies + 2 layers + <C> + top-8)",
+    line = _line(f"amp-layer-updates/s (n={n} streaming solve: energies + 2 layers + <C> + top-8)",
                  amps * args.steps / tot_s, "amp-layer-updates/s", args, world, 1e3 * tot_s / args.steps,
                  "c64 state, f32 energies, f64 reductions",
-                 {"workload": "large instance: dense n=30 QUBO U[-1,1] (seed 5), p=2, gamma=(0.4,0.7), "
-                              "beta=(0.6,0.3), complex64 (8 GiB) + FP32 energies (4 GiB), top-8",
-                  "l2": "inputs larger than L2 (12 GiB state + energies)", "parallelism": f"replicas x{world}"},
+                 {"workload": f"large instance: dense n={n} QUBO U[-1,1] (seed 5), p=2, gamma=(0.4,0.7), "
+                              f"beta=(0.6,0.3), complex64 ({(8 << n) / 2**30:g} GiB) + FP32 energies, top-8",
+                  "l2": "inputs larger than L2 (state + energies)", "parallelism": f"replicas x{world}"},
                  solves_per_s=args.steps / tot_s,
                  amp_gate_updates_per_s=amps * (n + 1) * args.steps / tot_s,
                  latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
@@ -646,7 +646,8 @@ def run_uneven(args):
     qbuild.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    U = synth.UNEVEN_BATCH
+    U = dict(synth.UNEVEN_BATCH)
+    U["count"] = args.uneven_count or U["count"]
     inst = synth.uneven_batch(U["count"], U["seed"] + 1000 * rank, *U["n"], *U["p"], dist=U["dist"])
     ns = np.array([x[0].shape[0] for x in inst])
     ps = np.array([len(x[1]) for x in inst])
@@ -690,7 +691,7 @@ def run_uneven(args):
     line = _line("instance optimisation steps/s (uneven batch: <C> + adjoint gradient + Adam, all instances)",
                  B.count * args.steps / tot_s, "instance-steps/s", args, world, 1e3 * tot_s / args.steps,
                  "c64 state, f32 energies, f64 reductions and gradients",
-                 {"workload": "uneven batch: 4096 sub-QUBOs, n uniform 8..24, p uniform 1..6, Q N(0,1) "
+                 {"workload": f"uneven batch: {U['count']} sub-QUBOs, n uniform 8..24, p uniform 1..6, Q N(0,1) "
                               "symmetric (seed 3), complex64, adjoint gradients, Adam lr 0.05",
                   "l2": "inputs larger than L2 (about 160 GB of states and energies)",
                   "parallelism": f"replicas x{world}"},
@@ -816,6 +817,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=100, help="requests per rate (serving config)")
+    ap.add_argument("--large-n", type=int, default=LARGE["n"],
+                    help="qubits of the large configuration (smaller values: profiling cases)")
+    ap.add_argument("--uneven-count", type=int, default=0,
+                    help="instances of the uneven batch (0: the full 4096; smaller: profiling cases)")
     ap.add_argument("--config", default="dqaoa", choices=["dqaoa"] + sorted(CONFIGS),
                     help="dqaoa: the DQAOA batch cycle (headline); the others are the further "
                          "measured configurations")
