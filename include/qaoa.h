@@ -67,8 +67,8 @@ qaoa_status qaoa_reserve(qaoa_ctx* ctx, size_t bytes);
 size_t qaoa_workspace_bytes(int n, int dbl);
 
 /* Kernel tier of the batched plans for complex64 instances of n qubits (plans created later).
- *   QAOA_TIER_AUTO: the library's choice (resident for n <= 14, cluster for 15..18 with
- *     14 local qubits per CTA, streaming above), or the autotuner's stored choice;
+ *   QAOA_TIER_AUTO: the autotuner's stored choice for (n, p), else the library's default
+ *     (resident for n <= 14, cluster with 13 local qubits per CTA for n = 15, streaming above);
  *   QAOA_TIER_CLUSTER: cluster tier with `param` local qubits per CTA (13 or 14; the cluster
  *     then has 2^(n - param) CTAs, at most 16); only 15 <= n <= 18;
  *   QAOA_TIER_STREAM: HBM streaming; n >= 15.
