@@ -8,16 +8,23 @@ namespace qaoa {
 
 namespace {
 
-// One CTA per sub-QUBO; thread a < k sums the conditioning term of row a sequentially in
-// ascending l (FP64, additions only), then all threads write the k*k FP32 entries. The
-// solution x is staged in shared memory as a 0/1 mask with the sub-QUBO's own variables
-// cleared, and the row is read 8 values at a time so the loads overlap the dependent adds.
-__global__ void k_subqubo(const double* __restrict__ Q, int N, const uint8_t* __restrict__ x,
-                          int k, const int32_t* __restrict__ idx, int conditioned,
-                          float* __restrict__ qsub) {
-    extern __shared__ int32_t S[];
+// One CTA per sub-QUBO. The conditioning term of row a is summed by thread a sequentially in
+// ascending l (FP64, additions only, skipping l in S and x_l = 0), the order the definition
+// gives. The rows are staged through shared memory in chunks of SQ_CHUNK columns, loaded by all
+// warps with coalesced reads, so the sequential adds read shared memory instead of waiting on
+// global loads. All threads then write the k*k FP32 entries.
+constexpr int SQ_CHUNK = 128;
+
+__global__ void __launch_bounds__(128) k_subqubo(const double* __restrict__ Q, int N,
+                                                 const uint8_t* __restrict__ x, int k,
+                                                 const int32_t* __restrict__ idx, int conditioned,
+                                                 float* __restrict__ qsub) {
+    extern __shared__ __align__(8) unsigned char sq_smem[];
+    double* rows = reinterpret_cast<double*>(sq_smem);                    // k x (SQ_CHUNK + 1)
+    int32_t* S = reinterpret_cast<int32_t*>(rows + (size_t)k * (SQ_CHUNK + 1));
     uint8_t* xm = reinterpret_cast<uint8_t*>(S + k);
     const int j = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = threadIdx.x; a < k; a += blockDim.x) S[a] = idx[(int64_t)j * k + a];
     if (conditioned)
         for (int l = threadIdx.x; l < N; l += blockDim.x) xm[l] = x[l];
@@ -31,23 +38,25 @@ __global__ void k_subqubo(const double* __restrict__ Q, int N, const uint8_t* __
         const int a = e / k, b = e % k;
         if (a != b || !conditioned) out[e] = (float)Q[(int64_t)S[a] * N + S[b]];
     }
-    if (conditioned) {
-        for (int a = threadIdx.x; a < k; a += blockDim.x) {
-            const double* row = Q + (int64_t)S[a] * N;
-            double h = 0.0;
-            int l = 0;
-            for (; l + 8 <= N; l += 8) {
-                double v[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) v[t] = row[l + t];
-#pragma unroll
-                for (int t = 0; t < 8; ++t)
-                    if (xm[l + t]) h += v[t];
-            }
-            for (; l < N; ++l)
-                if (xm[l]) h += row[l];
-            out[a * k + a] = (float)(row[S[a]] + 2.0 * h);
+    if (!conditioned) return;
+    double h = 0.0;
+    for (int c0 = 0; c0 < N; c0 += SQ_CHUNK) {
+        const int len = min(SQ_CHUNK, N - c0);
+        for (int a = warp; a < k; a += nw) {
+            const double* row = Q + (int64_t)S[a] * N + c0;
+            for (int l = lane; l < len; l += 32) rows[a * (SQ_CHUNK + 1) + l] = row[l];
         }
+        __syncthreads();
+        if (threadIdx.x < k) {
+            const double* r = rows + threadIdx.x * (SQ_CHUNK + 1);
+            for (int l = 0; l < len; ++l)
+                if (xm[c0 + l]) h += r[l];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < k) {
+        const int a = threadIdx.x;
+        out[a * k + a] = (float)(Q[(int64_t)S[a] * N + S[a]] + 2.0 * h);
     }
 }
 
@@ -55,8 +64,12 @@ __global__ void k_subqubo(const double* __restrict__ Q, int N, const uint8_t* __
 
 cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int k,
                            const int32_t* idx, int conditioned, float* qsub, cudaStream_t st) {
-    const size_t sm = k * sizeof(int32_t) + (size_t)N;
-    k_subqubo<<<m, 64, sm, st>>>(Q, N, x, k, idx, conditioned, qsub);
+    const size_t sm = (size_t)k * (SQ_CHUNK + 1) * sizeof(double) + k * sizeof(int32_t) + (size_t)N;
+    if (sm > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_subqubo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_subqubo<<<m, 128, sm, st>>>(Q, N, x, k, idx, conditioned, qsub);
     return cudaGetLastError();
 }
 
