@@ -121,7 +121,8 @@ void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, cons
 // O(|d|^2) with d = x' - x. With a cache (h, energy, tau of the same Q and x from the previous
 // call) the O(N^2) set-up is skipped.
 int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
-          const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache) {
+          const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache,
+          const double* qblk) {
     std::vector<double> h_local;
     std::vector<double>& h = cache ? cache->h : h_local;
     double energy = 0.0, tau = 0.0;
@@ -152,6 +153,7 @@ int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, 
     double d[64];
     for (int j = 0; j < m; ++j) {
         const int32_t* S = idx + (int64_t)j * k;
+        const double* blk = qblk ? qblk + (int64_t)j * k * k : nullptr;
         for (int c = 0; c < K; ++c) {
             const uint64_t y = cand[(int64_t)j * K + c];
             int cnt = 0;
@@ -160,13 +162,25 @@ int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, 
                 if (da != 0.0) { nz[cnt] = a; d[cnt] = da; ++cnt; }
             }
             if (!cnt) continue;
-            double dE = 0.0;
-            for (int u = 0; u < cnt; ++u) {
-                const double* row = Q + (int64_t)S[nz[u]] * N;
-                double inner = 0.0;
-                for (int v = 0; v < cnt; ++v) inner += row[S[nz[v]]] * d[v];
-                dE += d[u] * (2.0 * h[S[nz[u]]] + inner);
+            // inner[u] = sum over v (ascending) of Q[S_u][S_v] d_v; the u sums are independent,
+            // so they advance together (each keeps its own order)
+            double inner[64];
+            for (int u = 0; u < cnt; ++u) inner[u] = 0.0;
+            if (blk) {
+                for (int v = 0; v < cnt; ++v) {
+                    const double dv = d[v];
+                    const int cv = nz[v];
+                    for (int u = 0; u < cnt; ++u) inner[u] += blk[nz[u] * k + cv] * dv;
+                }
+            } else {
+                for (int v = 0; v < cnt; ++v) {
+                    const double dv = d[v];
+                    const int64_t cv = S[nz[v]];
+                    for (int u = 0; u < cnt; ++u) inner[u] += Q[(int64_t)S[nz[u]] * N + cv] * dv;
+                }
             }
+            double dE = 0.0;
+            for (int u = 0; u < cnt; ++u) dE += d[u] * (2.0 * h[S[nz[u]]] + inner[u]);
             if (dE < -tau) {
                 for (int u = 0; u < cnt; ++u) {
                     const int var = S[nz[u]];

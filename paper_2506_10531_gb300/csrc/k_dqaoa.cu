@@ -12,13 +12,14 @@ namespace {
 // ascending l (FP64, additions only, skipping l in S and x_l = 0), the order the definition
 // gives. The rows are staged through shared memory in chunks of SQ_CHUNK columns, loaded by all
 // warps with coalesced reads, so the sequential adds read shared memory instead of waiting on
-// global loads. All threads then write the k*k FP32 entries.
+// global loads. All threads then write the k*k FP32 entries and, when qblk is given, the raw
+// FP64 block Q[S, S] (the merge evaluates its candidates on it).
 constexpr int SQ_CHUNK = 128;
 
 __global__ void __launch_bounds__(128) k_subqubo(const double* __restrict__ Q, int N,
                                                  const uint8_t* __restrict__ x, int k,
                                                  const int32_t* __restrict__ idx, int conditioned,
-                                                 float* __restrict__ qsub) {
+                                                 float* __restrict__ qsub, double* __restrict__ qblk) {
     extern __shared__ __align__(8) unsigned char sq_smem[];
     double* rows = reinterpret_cast<double*>(sq_smem);                    // k x (SQ_CHUNK + 1)
     int32_t* S = reinterpret_cast<int32_t*>(rows + (size_t)k * (SQ_CHUNK + 1));
@@ -36,7 +37,9 @@ __global__ void __launch_bounds__(128) k_subqubo(const double* __restrict__ Q, i
     float* out = qsub + (int64_t)j * k * k;
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         const int a = e / k, b = e % k;
-        if (a != b || !conditioned) out[e] = (float)Q[(int64_t)S[a] * N + S[b]];
+        const double q = Q[(int64_t)S[a] * N + S[b]];
+        if (a != b || !conditioned) out[e] = (float)q;
+        if (qblk) qblk[(int64_t)j * k * k + e] = q;
     }
     if (!conditioned) return;
     double h = 0.0;
@@ -63,13 +66,14 @@ __global__ void __launch_bounds__(128) k_subqubo(const double* __restrict__ Q, i
 }  // namespace
 
 cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int k,
-                           const int32_t* idx, int conditioned, float* qsub, cudaStream_t st) {
+                           const int32_t* idx, int conditioned, float* qsub, cudaStream_t st,
+                           double* qblk) {
     const size_t sm = (size_t)k * (SQ_CHUNK + 1) * sizeof(double) + k * sizeof(int32_t) + (size_t)N;
     if (sm > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_subqubo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_subqubo<<<m, 128, sm, st>>>(Q, N, x, k, idx, conditioned, qsub);
+    k_subqubo<<<m, 128, sm, st>>>(Q, N, x, k, idx, conditioned, qsub, qblk);
     return cudaGetLastError();
 }
 

@@ -1012,6 +1012,7 @@ struct dqaoa_session {
     uint8_t* x_dev = nullptr;
     int32_t* idx_dev = nullptr;
     float* qsub = nullptr;
+    double* qblk = nullptr;       // raw FP64 blocks Q[S_j, S_j] for the merge
     float* params = nullptr;
     double* expect = nullptr;
     uint64_t* topk = nullptr;
@@ -1020,6 +1021,7 @@ struct dqaoa_session {
     uint8_t* x_h = nullptr;
     uint64_t* topk_h = nullptr;
     double* expect_h = nullptr;
+    double* qblk_h = nullptr;
     qaoa_plan* plan = nullptr;
     MergeCache cache;             // h = Qx and E(x) after the last merge
     std::vector<uint8_t> x_last;  // the solution the cache belongs to
@@ -1046,6 +1048,7 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     const size_t ox = o; o = align256(o + (size_t)N);
     const size_t oi = o; o = align256(o + (size_t)m * k * sizeof(int32_t));
     const size_t oq = o; o = align256(o + (size_t)m * k * k * sizeof(float));
+    const size_t ob = o; o = align256(o + (size_t)m * k * k * sizeof(double));
     const size_t op = o; o = align256(o + (size_t)2 * p * sizeof(float));
     const size_t oe = o; o = align256(o + (size_t)m * sizeof(double));
     const size_t ot = o; o = align256(o + (size_t)m * K * sizeof(uint64_t));
@@ -1056,6 +1059,7 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     s->x_dev = reinterpret_cast<uint8_t*>(b + ox);
     s->idx_dev = reinterpret_cast<int32_t*>(b + oi);
     s->qsub = reinterpret_cast<float*>(b + oq);
+    s->qblk = reinterpret_cast<double*>(b + ob);
     s->params = reinterpret_cast<float*>(b + op);
     s->expect = reinterpret_cast<double*>(b + oe);
     s->topk = reinterpret_cast<uint64_t*>(b + ot);
@@ -1064,6 +1068,7 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     const size_t hx = h; h = align256(h + (size_t)N);
     const size_t ht = h; h = align256(h + (size_t)m * K * sizeof(uint64_t));
     const size_t he = h; h = align256(h + (size_t)m * sizeof(double));
+    const size_t hb2 = h; h = align256(h + (size_t)m * k * k * sizeof(double));
     e = cudaMallocHost(&s->host, h);
     if (e != cudaSuccess) { cudaFree(s->dev); delete s; return fail(QAOA_E_NOMEM, "session cudaMallocHost"); }
     char* hb = static_cast<char*>(s->host);
@@ -1071,6 +1076,7 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     s->x_h = reinterpret_cast<uint8_t*>(hb + hx);
     s->topk_h = reinterpret_cast<uint64_t*>(hb + ht);
     s->expect_h = reinterpret_cast<double*>(hb + he);
+    s->qblk_h = reinterpret_cast<double*>(hb + hb2);
     std::vector<float> par(2 * p);
     for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)beta[l]; }
     e = cudaMemcpy(s->params, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -1108,7 +1114,8 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     std::memcpy(s->x_h, x, (size_t)N);
     CK(cudaMemcpyAsync(s->x_dev, s->x_h, (size_t)N, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->idx_dev, s->idx_h, (size_t)m * k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CK(launch_subqubo(s->Q_dev, N, s->x_dev, m, k, s->idx_dev, s->conditioned, s->qsub, st));
+    CK(launch_subqubo(s->Q_dev, N, s->x_dev, m, k, s->idx_dev, s->conditioned, s->qsub, st, s->qblk));
+    CK(cudaMemcpyAsync(s->qblk_h, s->qblk, (size_t)m * k * k * sizeof(double), cudaMemcpyDeviceToHost, st));
     // solve all sub-QUBOs
     r = qaoa_plan_launch(s->plan, stream);
     if (r) return r;
@@ -1125,7 +1132,7 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     // aggregate (reusing h = Qx when Q is unchanged and x is the solution the last merge left)
     s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
                      std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
-    merge(Q, N, x, m, k, s->idx_h, K, s->topk_h, energy_out, accepted_out, &s->cache);
+    merge(Q, N, x, m, k, s->idx_h, K, s->topk_h, energy_out, accepted_out, &s->cache, s->qblk_h);
     s->x_last.assign(x, x + N);
     return QAOA_OK;
 }

@@ -16,10 +16,14 @@ struct MergeCache {
     double energy = 0.0, tau = 0.0;
     bool valid = false;
 };
+// qblk (optional): the m raw FP64 blocks Q[S_j, S_j] (k*k each, row-major), read instead of
+// gathering the entries from Q (same values, contiguous).
 int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
-          const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache = nullptr);
+          const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache = nullptr,
+          const double* qblk = nullptr);
 cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int k,
-                           const int32_t* idx, int conditioned, float* qsub, cudaStream_t st);
+                           const int32_t* idx, int conditioned, float* qsub, cudaStream_t st,
+                           double* qblk = nullptr);
 cudaError_t launch_plain_layers(int n, int p, const float* gamma, const float* beta,
                                 const float* E, float2* psi, int init_plus, cudaStream_t st,
                                 int* kernels);
