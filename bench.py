@@ -46,6 +46,23 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value, device=None):
+    """Largest value over the ranks of the default process group (the value itself with one
+    rank). Timing uses it: the job takes as long as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(base, rank):
+    """Seed of a replica's workload: independent problems per rank (weak scaling)."""
+    return base + 1000 * rank
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -218,7 +235,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     N, m, k, p, K = CFG["N"], CFG["m"], CFG["k"], CFG["p"], CFG["topk"]
-    seed = CFG["seed"] + 1000 * rank
+    seed = replica_seed(CFG["seed"], rank)
     Q = synth.symmetric_q(N, seed=seed)
     Q_pin = torch.from_numpy(Q).pin_memory()
     Qh = Q_pin.numpy()
@@ -256,11 +273,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     q.qaoa_plan_set_timing(plan, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([tot_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_s = float(t.item())
+    tot_s = max_over_ranks(sum(step_ms) / 1e3, dev)
     value = m * args.steps * world / tot_s
     plan_kernels = q.qaoa_plan_kernel_count(plan)
     gpu_launches = args.steps * (plan_kernels + 1)
@@ -284,11 +297,7 @@ def run_ours(args):
     for s in range(args.steps):
         q.dqaoa_session_cycle(sess, Qh, 1, xe, seed, 600 + s, stream)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     e2e = {"value": m * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": N * N * 8 + N + m * k * 4, "d2h_bytes_per_step": m * K * 8 + m * 8}
 

@@ -1,0 +1,71 @@
+"""The multi-process (replica) path on the CPU: world size 2 over gloo.
+
+Sub-QUBOs are independent units, so the N-GPU form runs one replica per rank with no collective on
+the data path; the only cross-rank steps are the barrier and the maximum of the timed durations.
+These tests run that logic with two gloo ranks, and launch the reference arm of bench.py under
+torchrun with two ranks (rank 0 prints one JSON line, the other exits without work).
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t = bench.max_over_ranks(0.25 + rank)          # per-rank "durations"
+        seeds = [None] * world
+        dist.all_gather_object(seeds, bench.replica_seed(2, rank))
+        dist.barrier()
+        out[rank] = (t, seeds)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_replica_seeds_gloo():
+    import torch.multiprocessing as mp
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(2, free_port(), out), nprocs=2, join=True)
+    for r in range(2):
+        t, seeds = out[r]
+        assert t == 1.25                                 # every rank sees the slowest replica
+        assert len(set(seeds)) == 2                      # independent workloads per replica
+
+
+def test_max_over_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(0.5) == 0.5
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    port = free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
