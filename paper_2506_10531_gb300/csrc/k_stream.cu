@@ -196,16 +196,21 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
     s.tk.cnt = reinterpret_cast<int*>(sm + o);
     const uint64_t ntiles = 1ull << (P.n - P.tb);
     const uint64_t total = ntiles * (uint64_t)count;
-    int cur = -1;
+    // layer constants are rebuilt only when the parameters change (instances of a batch often
+    // share one parameter vector)
+    const T *cur_g = nullptr, *cur_b = nullptr;
+    int cur_p = 0;
     for (uint64_t b = blockIdx.x; b < total; b += gridDim.x) {
         const int ii = (int)(b / ntiles);
         const uint64_t tau = b % ntiles;
         const StreamInst<T>& I = insts ? insts[ii] : one;
-        if (ii != cur) {
+        if (I.gamma != cur_g || I.beta != cur_b || I.p != cur_p) {
             __syncthreads();
             set_layer_consts<T>(s.lc, I.gamma, I.beta, I.p, P.n, true);
             __syncthreads();
-            cur = ii;
+            cur_g = I.gamma;
+            cur_b = I.beta;
+            cur_p = I.p;
         }
         constexpr int RB = Num<T>::RB;
         stream_tile<T, RB>(P, I, tau, s);
@@ -367,15 +372,18 @@ __global__ void __launch_bounds__(ADJ_THREADS, 2) k_stream_adj_pass(const Stream
     s.red = reinterpret_cast<double*>(sm + o);
     const uint64_t ntiles = 1ull << (P.n - P.tb);
     const uint64_t total = ntiles * (uint64_t)count;
-    int cur = -1;
+    const T *cur_g = nullptr, *cur_b = nullptr;
+    int cur_p = 0;
     for (uint64_t b = blockIdx.x; b < total; b += gridDim.x) {
         const int ii = (int)(b / ntiles);
         const uint64_t tau = b % ntiles;
         const StreamInst<T>& I = insts ? insts[ii] : one;
-        if (ii != cur) {
+        if (I.gamma != cur_g || I.beta != cur_b || I.p != cur_p) {
             __syncthreads();
             set_layer_consts<T>(s.lc, I.gamma, I.beta, I.p, P.n, false);
-            cur = ii;
+            cur_g = I.gamma;
+            cur_b = I.beta;
+            cur_p = I.p;
         }
         constexpr int RA = Num<T>::RB_ADJ;
         stream_adj_tile<T, RA>(P, si, lam_first != 0, store != 0, I, tau, s, slam);
