@@ -242,7 +242,7 @@ def run_ours(args):
     x0 = synth.bits(seed + 1, N)
     ctx = q.qaoa_create(local)
     sess = q.dqaoa_session_create(ctx, N, m, k, p, K, q.DQAOA_RANDOM, True, CFG["gamma"], CFG["beta"])
-    plan = q.dqaoa_session_plan(sess)
+    plans = q.dqaoa_session_plans(sess)      # the sub-QUBO chunks, solved one after the other
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def l2_flush():
@@ -253,7 +253,8 @@ def run_ours(args):
     q.dqaoa_session_cycle(sess, Qh, 1, x, seed, 0, stream)         # uploads Q once
     for w in range(args.warmup):
         q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 1 + w, stream)
-    q.qaoa_plan_set_timing(plan, True)
+    for pl in plans:
+        q.qaoa_plan_set_timing(pl, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     kern = {}
@@ -268,24 +269,26 @@ def run_ours(args):
             e, acc = q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 100 + s, stream)
             ev[s][1].record(stream)
             energies.append(e)
-            for name, ms in q.qaoa_plan_kernel_times(plan):
-                kern.setdefault(name, []).append(ms)
+            for pl in plans:
+                for name, ms in q.qaoa_plan_kernel_times(pl):
+                    kern.setdefault(name, []).append(ms)
         torch.cuda.synchronize()
-    q.qaoa_plan_set_timing(plan, False)
+    for pl in plans:
+        q.qaoa_plan_set_timing(pl, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_s = max_over_ranks(sum(step_ms) / 1e3, dev)
     value = m * args.steps * world / tot_s
-    plan_kernels = q.qaoa_plan_kernel_count(plan)
+    plan_kernels = sum(q.qaoa_plan_kernel_count(pl) for pl in plans)
     gpu_launches = args.steps * (plan_kernels + 1)
 
     # ---- dominant kernel and its roofline ----
     def relaunch():
         q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream)
-    roof = plan_roofline(q, plan, kern, relaunch, clk, dev,
+    roof = plan_roofline(q, plans, kern, relaunch, clk, dev,
                          alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p))
 
     # ---- kernel-only batch throughput and the plain one-instance-per-launch path ----
-    kb = time_plan_only(q, plan, stream, args.steps, l2_flush)
+    kb = time_plan_only(q, plans, stream, args.steps, l2_flush)
     plain = time_plain(q, ctx, sess, stream, n_inst=16)
 
     # ---- e2e: the public one-call cycle with Q from pinned host memory every step ----
@@ -339,19 +342,25 @@ def run_ours(args):
 HBM_FAMILIES = ("stream_pass", "stream_adjoint", "energy", "stream_finalize", "stream_grad_reduce")
 
 
-def plan_roofline(q, plan, kern, relaunch, clk, dev, alu_flops=None):
+def plan_roofline(q, plans, kern, relaunch, clk, dev, alu_flops=None):
     """Roofline entry of the kernel family with the largest time in `kern` ({family: [ms per
     launch]}, measured with CUDA events on the launch stream inside the timed region). Algorithmic
-    bytes per launch come from the plan; `relaunch` runs the plan once more with timing on to map
+    bytes per launch come from the plan(s); `relaunch` runs them once more with timing on to map
     launch order to families."""
     import torch
-    kbytes = q.qaoa_plan_kernel_bytes(plan, 8192)
+    if not isinstance(plans, (list, tuple)):
+        plans = [plans]
+    kbytes, order = [], []
     fam_ms = {nm: sum(v) for nm, v in kern.items()}
     dom = max(fam_ms, key=fam_ms.get)
-    q.qaoa_plan_set_timing(plan, True)
+    for pl in plans:
+        q.qaoa_plan_set_timing(pl, True)
     relaunch()
-    order = [nm for nm, _ in q.qaoa_plan_kernel_times(plan, 8192)]
-    q.qaoa_plan_set_timing(plan, False)
+    for pl in plans:
+        kb = q.qaoa_plan_kernel_bytes(pl, 8192)
+        kbytes += kb
+        order += [nm for nm, _ in q.qaoa_plan_kernel_times(pl, 8192)][:len(kb)]
+        q.qaoa_plan_set_timing(pl, False)
     fam_bytes = [b for nm, b in zip(order, kbytes) if nm == dom]
     per_launch_ms = statistics.mean(kern[dom])
     per_launch_bytes = statistics.mean(fam_bytes) if fam_bytes else 0.0
@@ -379,16 +388,18 @@ def alu_flops_per_launch(family, m, k, p):
     return m * (1 << k) * p * (12 + 4 * k)
 
 
-def time_plan_only(q, plan, stream, steps, l2_flush):
+def time_plan_only(q, plans, stream, steps, l2_flush):
     import torch
     for _ in range(3):
-        q.qaoa_plan_launch(plan, stream)
+        for pl in plans:
+            q.qaoa_plan_launch(pl, stream)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     for s in range(steps):
         l2_flush()
         ev[s][0].record(stream)
-        q.qaoa_plan_launch(plan, stream)
+        for pl in plans:
+            q.qaoa_plan_launch(pl, stream)
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)

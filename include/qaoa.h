@@ -316,8 +316,10 @@ qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed
 /* Device work of the last cycle: per-sub-QUBO <C> (m doubles) and top-K indices (m*K uint64),
  * copied to host arrays (either may be NULL). */
 qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk);
-/* The batched plan the session launches (for timing and kernel counts). */
-qaoa_plan* dqaoa_session_plan(dqaoa_session* s);
+/* The batched plans the session launches, in order (for timing and kernel counts): the m
+ * sub-QUBOs are solved in two chunks of m/2 when m >= 128 (the host merges the first chunk while
+ * the device solves the second), else in one. Returns NULL for i past the last plan. */
+qaoa_plan* dqaoa_session_plan(dqaoa_session* s, int i);
 void dqaoa_session_destroy(dqaoa_session* s);
 
 /* ---------------------------------------------------------------------------------------- */

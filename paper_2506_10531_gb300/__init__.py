@@ -124,7 +124,7 @@ def _declare(L):
     L.dqaoa_session_create.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, C.POINTER(vp)]
     L.dqaoa_session_cycle.argtypes = [vp, vp, i32, vp, u64, u64, vp, vp, vp]
     L.dqaoa_session_results.argtypes = [vp, vp, vp]
-    L.dqaoa_session_plan.argtypes = [vp]
+    L.dqaoa_session_plan.argtypes = [vp, i32]
     L.dqaoa_session_plan.restype = vp
     L.dqaoa_session_destroy.argtypes = [vp]
     L.dqaoa_session_destroy.restype = None
@@ -362,8 +362,20 @@ def dqaoa_session_results(sess, m, K):
     return ex, tk
 
 
-def dqaoa_session_plan(sess):
-    return C.c_void_p(lib().dqaoa_session_plan(sess))
+def dqaoa_session_plan(sess, i=0):
+    """Plan i of the session (None past the last one)."""
+    h = lib().dqaoa_session_plan(sess, i)
+    return C.c_void_p(h) if h else None
+
+
+def dqaoa_session_plans(sess):
+    out, i = [], 0
+    while True:
+        h = dqaoa_session_plan(sess, i)
+        if h is None:
+            return out
+        out.append(h)
+        i += 1
 
 
 def dqaoa_session_destroy(sess):

@@ -1022,7 +1022,12 @@ struct dqaoa_session {
     uint64_t* topk_h = nullptr;
     double* expect_h = nullptr;
     double* qblk_h = nullptr;
-    qaoa_plan* plan = nullptr;
+    // the sub-QUBOs are solved in chunks, one plan each, so that the host merges chunk c while
+    // the device solves chunk c + 1 (the merge is sequential over sub-QUBOs in index order)
+    int chunks = 1;
+    int chunk_start[3] = {0, 0, 0};
+    qaoa_plan* plans[2] = {nullptr, nullptr};
+    cudaEvent_t chunk_done[2] = {nullptr, nullptr};
     MergeCache cache;             // h = Qx and E(x) after the last merge
     std::vector<uint8_t> x_last;  // the solution the cache belongs to
     // random index sets of the next cycle, drawn on the host while the device works
@@ -1080,17 +1085,25 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     std::vector<float> par(2 * p);
     for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)beta[l]; }
     e = cudaMemcpy(s->params, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice);
-    std::vector<qaoa_inst> d(m);
-    for (int j = 0; j < m; ++j) d[j] = qaoa_inst{k, p, K, 0, (int64_t)j * k * k, 0, -1, -1};
-    qaoa_batch_io io{};
-    io.q = s->qsub;
-    io.params = s->params;
-    io.expect = s->expect;
-    io.topk_idx = s->topk;
-    io.k_stride = K;
-    qaoa_status st = (e == cudaSuccess) ? qaoa_plan_create(c, d.data(), m, &io, 0, &s->plan)
-                                        : cuda_fail(e, "session params upload");
-    if (st) { dqaoa_session_destroy(s); return st; }
+    if (e != cudaSuccess) { dqaoa_session_destroy(s); return cuda_fail(e, "session params upload"); }
+    s->chunks = m >= 128 ? 2 : 1;
+    s->chunk_start[1] = s->chunks == 2 ? m / 2 : m;
+    s->chunk_start[2] = m;
+    for (int ch = 0; ch < s->chunks; ++ch) {
+        const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
+        std::vector<qaoa_inst> d(mc);
+        for (int j = 0; j < mc; ++j) d[j] = qaoa_inst{k, p, K, 0, (int64_t)(j0 + j) * k * k, 0, -1, -1};
+        qaoa_batch_io io{};
+        io.q = s->qsub;
+        io.params = s->params;
+        io.expect = s->expect + j0;
+        io.topk_idx = s->topk + (size_t)j0 * K;
+        io.k_stride = K;
+        qaoa_status st = qaoa_plan_create(c, d.data(), mc, &io, 0, &s->plans[ch]);
+        if (st == QAOA_OK && cudaEventCreateWithFlags(&s->chunk_done[ch], cudaEventDisableTiming) != cudaSuccess)
+            st = fail(QAOA_E_CUDA, "session event");
+        if (st) { dqaoa_session_destroy(s); return st; }
+    }
     *out = s;
     return QAOA_OK;
 }
@@ -1116,11 +1129,16 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     CK(cudaMemcpyAsync(s->idx_dev, s->idx_h, (size_t)m * k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(launch_subqubo(s->Q_dev, N, s->x_dev, m, k, s->idx_dev, s->conditioned, s->qsub, st, s->qblk));
     CK(cudaMemcpyAsync(s->qblk_h, s->qblk, (size_t)m * k * k * sizeof(double), cudaMemcpyDeviceToHost, st));
-    // solve all sub-QUBOs
-    r = qaoa_plan_launch(s->plan, stream);
-    if (r) return r;
-    CK(cudaMemcpyAsync(s->topk_h, s->topk, (size_t)m * K * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(s->expect_h, s->expect, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // solve the sub-QUBOs chunk by chunk; each chunk's results come back behind its own event
+    for (int ch = 0; ch < s->chunks; ++ch) {
+        const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
+        r = qaoa_plan_launch(s->plans[ch], stream);
+        if (r) return r;
+        CK(cudaMemcpyAsync(s->topk_h + (size_t)j0 * K, s->topk + (size_t)j0 * K, (size_t)mc * K * sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(s->expect_h + j0, s->expect + j0, (size_t)mc * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(s->chunk_done[ch], st));
+    }
     if (s->method == DQAOA_RANDOM) {   // overlaps the device work of this cycle
         s->next_idx.resize((size_t)m * k);
         draw_random(N, m, k, seed, cycle + 1, s->next_idx.data());
@@ -1128,11 +1146,21 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         s->next_seed = seed;
         s->next_cycle = cycle + 1;
     }
-    CK(cudaStreamSynchronize(st));
-    // aggregate (reusing h = Qx when Q is unchanged and x is the solution the last merge left)
+    // aggregate chunk by chunk in sub-QUBO order (reusing h = Qx when Q is unchanged and x is the
+    // solution the last merge left); merging chunk c overlaps the device work of chunk c + 1
     s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
                      std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
-    merge(Q, N, x, m, k, s->idx_h, K, s->topk_h, energy_out, accepted_out, &s->cache, s->qblk_h);
+    int accepted = 0;
+    for (int ch = 0; ch < s->chunks; ++ch) {
+        CK(cudaEventSynchronize(s->chunk_done[ch]));
+        const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
+        int acc = 0;
+        merge(Q, N, x, mc, k, s->idx_h + (size_t)j0 * k, K, s->topk_h + (size_t)j0 * K, energy_out, &acc,
+              &s->cache, s->qblk_h + (size_t)j0 * k * k);
+        accepted += acc;
+    }
+    CK(cudaStreamSynchronize(st));
+    if (accepted_out) *accepted_out = accepted;
     s->x_last.assign(x, x + N);
     return QAOA_OK;
 }
@@ -1144,12 +1172,17 @@ extern "C" qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, u
     return QAOA_OK;
 }
 
-extern "C" qaoa_plan* dqaoa_session_plan(dqaoa_session* s) { return s ? s->plan : nullptr; }
+extern "C" qaoa_plan* dqaoa_session_plan(dqaoa_session* s, int i) {
+    return (s && i >= 0 && i < s->chunks) ? s->plans[i] : nullptr;
+}
 
 extern "C" void dqaoa_session_destroy(dqaoa_session* s) {
     if (!s) return;
     cudaSetDevice(s->ctx->device);
-    qaoa_plan_destroy(s->plan);
+    for (int ch = 0; ch < 2; ++ch) {
+        qaoa_plan_destroy(s->plans[ch]);
+        if (s->chunk_done[ch]) cudaEventDestroy(s->chunk_done[ch]);
+    }
     cudaFreeHost(s->host);
     cudaFree(s->dev);
     delete s;
