@@ -131,9 +131,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_family):
-    """DRAM bytes per launch of a kernel family from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def ncu_traffic(workload, kernel_family):
+    """DRAM bytes per launch of a kernel family in a workload (profiles/traffic.json, written from
+    ncu captures), if it was taken on the current kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
@@ -141,7 +141,7 @@ def ncu_traffic(kernel_family):
         return None
     if t.get("source_hash") != kernel_source_hash():
         return None
-    e = t.get("kernels", {}).get(kernel_family)
+    e = t.get("workloads", {}).get(workload, {}).get(kernel_family)
     return None if e is None else e.get("dram_bytes_per_launch")
 
 
@@ -285,7 +285,7 @@ def run_ours(args):
     def relaunch():
         q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream)
     roof = plan_roofline(q, plans, kern, relaunch, clk, dev,
-                         alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p))
+                         alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p), workload="dqaoa")
 
     # ---- kernel-only batch throughput and the plain one-instance-per-launch path ----
     kb = time_plan_only(q, plans, stream, args.steps, l2_flush)
@@ -342,7 +342,7 @@ def run_ours(args):
 HBM_FAMILIES = ("stream_pass", "stream_adjoint", "energy", "stream_finalize", "stream_grad_reduce")
 
 
-def plan_roofline(q, plans, kern, relaunch, clk, dev, alu_flops=None):
+def plan_roofline(q, plans, kern, relaunch, clk, dev, alu_flops=None, workload=None):
     """Roofline entry of the kernel family with the largest time in `kern` ({family: [ms per
     launch]}, measured with CUDA events on the launch stream inside the timed region). Algorithmic
     bytes per launch come from the plan(s); `relaunch` runs them once more with timing on to map
@@ -369,7 +369,7 @@ def plan_roofline(q, plans, kern, relaunch, clk, dev, alu_flops=None):
         achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
         return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": ncu_traffic(dom), "peak_source": peak_kind + " (hbm_gbs, copy burst)",
+                "traffic": ncu_traffic(workload, dom), "peak_source": peak_kind + " (hbm_gbs, copy burst)",
                 "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
                 "launches_per_step": len(fam_bytes)}
     # on-chip kernels: FP32 pipe bound; peak = SMs x 128 FP32 lanes x 2 flop x clock
@@ -378,7 +378,7 @@ def plan_roofline(q, plans, kern, relaunch, clk, dev, alu_flops=None):
     peak_tf = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
     achieved = alu_flops(dom) / (per_launch_ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
-            "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": ncu_traffic(dom),
+            "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": ncu_traffic(workload, dom),
             "peak_source": "derived: SMs x 128 FP32 lanes x 2 x median SM clock",
             "ms_per_launch": per_launch_ms}
 
@@ -505,7 +505,8 @@ def run_large(args):
     q.qaoa_plan_set_timing(plan, False)
     tot_s = sum(step_ms) / 1e3
     amps = (1 << n) * p
-    roof = plan_roofline(q, plan, kern, lambda: q.qaoa_plan_launch(plan, stream), clk, dev)
+    roof = plan_roofline(q, plan, kern, lambda: q.qaoa_plan_launch(plan, stream), clk, dev,
+                         workload=f"large_n{n}")
     per_pass = {"ms": [round(v, 3) for v in kern.get("stream_pass", [])[:8]]}
     # e2e: Q and parameters from pinned host memory, <C> and top-k back, every step
     Qp = torch.from_numpy(Q.reshape(-1)).pin_memory()
@@ -605,7 +606,7 @@ def run_plain10(args):
     fp64_peak = props.multi_processor_count * 2 * 2 * mhz * 1e6 / 1e12   # 2 FP64 FMA lanes per SM
     roof = {"bound": "alu", "kernel": "resident", "achieved": flops / (ms_launch * 1e-3) / 1e12,
             "peak": fp64_peak, "unit": "TFLOP/s", "frac": flops / (ms_launch * 1e-3) / 1e12 / fp64_peak,
-            "traffic": ncu_traffic("resident"), "ms_per_launch": ms_launch,
+            "traffic": ncu_traffic("plain10", "resident"), "ms_per_launch": ms_launch,
             "peak_source": "derived: SMs x 2 FP64 FMA lanes x 2 x median SM clock (FP64 at 1/64 of FP32)"}
     Pp = torch.from_numpy(par).pin_memory()
     Qp = torch.from_numpy(Q.reshape(-1)).pin_memory()
@@ -688,7 +689,7 @@ def run_uneven(args):
         step_ms = _timed_steps(stream, args.steps, body)
     q.qaoa_plan_set_timing(B.plan, False)
     tot_s = sum(step_ms) / 1e3
-    roof = plan_roofline(q, B.plan, kern, lambda: B.run(stream), clk, dev)
+    roof = plan_roofline(q, B.plan, kern, lambda: B.run(stream), clk, dev, workload=f"uneven_{U['count']}")
     amps = float(np.sum((2.0 ** ns) * ps))
     # e2e: Q pool and parameters from pinned host memory, <C> of every instance back, per step
     qh = B.q.cpu().pin_memory()
