@@ -316,6 +316,10 @@ qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed
 /* Device work of the last cycle: per-sub-QUBO <C> (m doubles) and top-K indices (m*K uint64),
  * copied to host arrays (either may be NULL). */
 qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk);
+/* Times of the last cycle in ms, out[4]: the host's decompose-and-enqueue time (index draw,
+ * copies and launches), the device time from the first copy to the last chunk's results, the
+ * host merge time (the first chunk's merge overlaps the device), and the whole call. */
+qaoa_status dqaoa_session_timing(dqaoa_session* s, double* out);
 /* The batched plans the session launches, in order (for timing and kernel counts): the m
  * sub-QUBOs are solved in two chunks of m/2 when m >= 128 (the host merges the first chunk while
  * the device solves the second), else in one. Returns NULL for i past the last plan. */

@@ -37,6 +37,7 @@ EXPORTS = [
     "qaoa_server_create", "qaoa_server_destroy", "qaoa_server_job_bytes", "qaoa_server_submit",
     "qaoa_server_tick", "qaoa_server_poll", "qaoa_server_stats", "qaoa_server_clock",
     "qaoa_autotune", "qaoa_tuning_get", "qaoa_tuning_save", "qaoa_tuning_load", "qaoa_plan_capture",
+    "dqaoa_session_timing",
 ]
 
 
@@ -124,6 +125,7 @@ def _declare(L):
     L.dqaoa_session_create.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, C.POINTER(vp)]
     L.dqaoa_session_cycle.argtypes = [vp, vp, i32, vp, u64, u64, vp, vp, vp]
     L.dqaoa_session_results.argtypes = [vp, vp, vp]
+    L.dqaoa_session_timing.argtypes = [vp, vp]
     L.dqaoa_session_plan.argtypes = [vp, i32]
     L.dqaoa_session_plan.restype = vp
     L.dqaoa_session_destroy.argtypes = [vp]
@@ -487,3 +489,11 @@ def qaoa_tuning_load(ctx, path):
 def qaoa_plan_capture(plan, stream):
     """Capture the plan's launch into a CUDA graph; later launches replay it (non-legacy stream)."""
     _check(lib().qaoa_plan_capture(plan, stream_ptr(stream)))
+
+
+def dqaoa_session_timing(sess):
+    """{decompose_ms, device_ms, merge_ms, cycle_ms} of the session's last cycle."""
+    import numpy as np
+    out = np.zeros(4)
+    _check(lib().dqaoa_session_timing(sess, out.ctypes.data))
+    return dict(zip(("decompose_ms", "device_ms", "merge_ms", "cycle_ms"), out.tolist()))

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -1028,6 +1029,8 @@ struct dqaoa_session {
     int chunk_start[3] = {0, 0, 0};
     qaoa_plan* plans[2] = {nullptr, nullptr};
     cudaEvent_t chunk_done[2] = {nullptr, nullptr};
+    cudaEvent_t dev_begin = nullptr, dev_end = nullptr;   // device part of the last cycle
+    double t_decompose = 0.0, t_merge = 0.0, t_cycle = 0.0; // host ms of the last cycle
     MergeCache cache;             // h = Qx and E(x) after the last merge
     std::vector<uint8_t> x_last;  // the solution the cache belongs to
     // random index sets of the next cycle, drawn on the host while the device works
@@ -1104,6 +1107,10 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
             st = fail(QAOA_E_CUDA, "session event");
         if (st) { dqaoa_session_destroy(s); return st; }
     }
+    if (cudaEventCreate(&s->dev_begin) != cudaSuccess || cudaEventCreate(&s->dev_end) != cudaSuccess) {
+        dqaoa_session_destroy(s);
+        return fail(QAOA_E_CUDA, "session events");
+    }
     *out = s;
     return QAOA_OK;
 }
@@ -1114,6 +1121,10 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     if (!s || !Q || !x) return fail(QAOA_E_INVALID, "session_cycle: NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     const int N = s->N, m = s->m, k = s->k, K = s->K;
+    auto now_ms = []() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+    };
+    const double t0 = now_ms();
     if (q_changed) CK(cudaMemcpyAsync(s->Q_dev, Q, (size_t)N * N * sizeof(double), cudaMemcpyHostToDevice, st));
     // decompose: index sets on the host (random sets drawn ahead during the previous cycle
     // when seed and cycle match), matrices on the device
@@ -1125,6 +1136,7 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     s->next_valid = false;
     if (r) return r;
     std::memcpy(s->x_h, x, (size_t)N);
+    CK(cudaEventRecord(s->dev_begin, st));
     CK(cudaMemcpyAsync(s->x_dev, s->x_h, (size_t)N, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->idx_dev, s->idx_h, (size_t)m * k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(launch_subqubo(s->Q_dev, N, s->x_dev, m, k, s->idx_dev, s->conditioned, s->qsub, st, s->qblk));
@@ -1139,6 +1151,8 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         CK(cudaMemcpyAsync(s->expect_h + j0, s->expect + j0, (size_t)mc * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaEventRecord(s->chunk_done[ch], st));
     }
+    CK(cudaEventRecord(s->dev_end, st));
+    const double t1 = now_ms();
     if (s->method == DQAOA_RANDOM) {   // overlaps the device work of this cycle
         s->next_idx.resize((size_t)m * k);
         draw_random(N, m, k, seed, cycle + 1, s->next_idx.data());
@@ -1151,17 +1165,34 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
                      std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
     int accepted = 0;
+    double t_merge = 0.0;
     for (int ch = 0; ch < s->chunks; ++ch) {
         CK(cudaEventSynchronize(s->chunk_done[ch]));
+        const double tm = now_ms();
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
         int acc = 0;
         merge(Q, N, x, mc, k, s->idx_h + (size_t)j0 * k, K, s->topk_h + (size_t)j0 * K, energy_out, &acc,
               &s->cache, s->qblk_h + (size_t)j0 * k * k);
         accepted += acc;
+        t_merge += now_ms() - tm;
     }
     CK(cudaStreamSynchronize(st));
     if (accepted_out) *accepted_out = accepted;
     s->x_last.assign(x, x + N);
+    s->t_decompose = t1 - t0;
+    s->t_merge = t_merge;
+    s->t_cycle = now_ms() - t0;
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status dqaoa_session_timing(dqaoa_session* s, double* out) {
+    if (!s || !out) return fail(QAOA_E_INVALID, "session_timing: NULL argument");
+    float dev = 0.0f;
+    CK(cudaEventElapsedTime(&dev, s->dev_begin, s->dev_end));
+    out[0] = s->t_decompose;
+    out[1] = dev;
+    out[2] = s->t_merge;
+    out[3] = s->t_cycle;
     return QAOA_OK;
 }
 
@@ -1183,6 +1214,8 @@ extern "C" void dqaoa_session_destroy(dqaoa_session* s) {
         qaoa_plan_destroy(s->plans[ch]);
         if (s->chunk_done[ch]) cudaEventDestroy(s->chunk_done[ch]);
     }
+    if (s->dev_begin) cudaEventDestroy(s->dev_begin);
+    if (s->dev_end) cudaEventDestroy(s->dev_end);
     cudaFreeHost(s->host);
     cudaFree(s->dev);
     delete s;

@@ -78,3 +78,29 @@ def test_session_cycles_lower_energy(q, orc):
         q.qaoa_destroy(ctx)
     assert all(b <= a for a, b in zip(es, es[1:]))
     assert es[-1] < es[0]
+
+
+def test_driver_cycles_to_convergence(q, orc):
+    from paper_2506_10531_gb300.dqaoa import solve
+    N = 200
+    Q = synth.symmetric_q(N, seed=21)
+    x0 = synth.bits(22, N)
+    ctx = q.qaoa_create(0)
+    try:
+        r = solve(ctx, Q, 32, 10, 2, 4, (0.3, 0.5), (0.4, 0.2), x0, seed=3, max_cycles=60, patience=3)
+        # the same run judged against its own final energy as the reference: it stops as soon as
+        # the energy is within tolerance for three cycles
+        r2 = solve(ctx, Q, 32, 10, 2, 4, (0.3, 0.5), (0.4, 0.2), x0, seed=3, max_cycles=60, patience=3,
+                   ref_energy=r.energy, tol=1e-12)
+    finally:
+        q.qaoa_destroy(ctx)
+    assert r.converged and r.cycles <= 60
+    assert all(b <= a for a, b in zip(r.energies, r.energies[1:]))          # merges never go up
+    assert r.energy == pytest.approx(orc.qubo_energy(Q, r.x), abs=1e-9 * np.abs(Q).sum())
+    assert r.energy < orc.qubo_energy(Q, x0)
+    assert 0.0 <= r.tts_s <= r.wall_s
+    for t in r.timing:
+        assert t["device_ms"] > 0 and t["cycle_ms"] >= t["merge_ms"] >= 0 and t["decompose_ms"] >= 0
+    # deterministic: the second run follows the same trajectory
+    assert r2.energies == r.energies[:len(r2.energies)]
+    assert r2.converged and r2.cycles <= r.cycles
