@@ -122,10 +122,20 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
+# Source files that define each kernel family (the kernel itself and the headers it includes).
+KERNEL_SOURCES = {
+    "stream": ["k_stream.cu", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_stream.h", "qaoa_kernels.h"],
+    "resident": ["k_resident.cu", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_kernels.h"],
+    "cluster": ["k_cluster.cu", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_kernels.h"],
+}
+
+
+def kernel_source_hash(family):
+    """Hash of the sources of a kernel family (stream_* and energy: the streaming files)."""
+    group = "stream" if family.startswith("stream") or family == "energy" else family
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2506_10531_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES.get(group, sorted(os.listdir(d))):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -133,16 +143,16 @@ def kernel_source_hash():
 
 def ncu_traffic(workload, kernel_family):
     """DRAM bytes per launch of a kernel family in a workload (profiles/traffic.json, written from
-    ncu captures), if it was taken on the current kernel sources."""
+    ncu captures), if it was taken on the current sources of that kernel."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
     except OSError:
         return None
-    if t.get("source_hash") != kernel_source_hash():
-        return None
     e = t.get("workloads", {}).get(workload, {}).get(kernel_family)
-    return None if e is None else e.get("dram_bytes_per_launch")
+    if e is None or e.get("source_hash") != kernel_source_hash(kernel_family):
+        return None
+    return e.get("dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------------------------
