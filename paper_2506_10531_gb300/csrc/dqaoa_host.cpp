@@ -106,11 +106,17 @@ void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, cons
             for (int b = 0; b < k; ++b) Qs[a * k + b] = Q[(int64_t)S[a] * N + S[b]];
         if (!conditioned) continue;
         for (int a = 0; a < k; ++a) inS[S[a]] = 1;
+        // conditioning sum in eight interleaved partial sums (l = r mod 8, ascending), combined
+        // pairwise: the summation order the device kernel uses
         for (int a = 0; a < k; ++a) {
             const double* row = Q + (int64_t)S[a] * N;
-            double h = 0.0;
-            for (int l = 0; l < N; ++l)
-                if (!inS[l] && x[l]) h += row[l];
+            double sr[8];
+            for (int r = 0; r < 8; ++r) {
+                sr[r] = 0.0;
+                for (int l = r; l < N; l += 8)
+                    if (!inS[l] && x[l]) sr[r] += row[l];
+            }
+            const double h = ((sr[0] + sr[1]) + (sr[2] + sr[3])) + ((sr[4] + sr[5]) + (sr[6] + sr[7]));
             Qs[a * k + a] += 2.0 * h;
         }
         for (int a = 0; a < k; ++a) inS[S[a]] = 0;

@@ -8,15 +8,16 @@ namespace qaoa {
 
 namespace {
 
-// One CTA per sub-QUBO. The conditioning term of row a is summed by thread a sequentially in
-// ascending l (FP64, additions only, skipping l in S and x_l = 0), the order the definition
-// gives. The rows are staged through shared memory in chunks of SQ_CHUNK columns, loaded by all
-// warps with coalesced reads, so the sequential adds read shared memory instead of waiting on
-// global loads. All threads then write the k*k FP32 entries and, when qblk is given, the raw
-// FP64 block Q[S, S] (the merge evaluates its candidates on it).
+// One CTA per sub-QUBO. The conditioning term of row a is the FP64 sum over l not in S with
+// x_l = 1 of Q[S_a][l], taken as eight partial sums over l = r (mod 8) (thread 8a + r, ascending
+// l) combined pairwise ((s0+s1)+(s2+s3))+((s4+s5)+(s6+s7)) by xor-shuffles within the row's eight
+// lanes (addition is commutative, so every lane ends with the same bits). The rows are staged
+// through shared memory in chunks of SQ_CHUNK columns, loaded by all warps with coalesced reads.
+// All threads then write the k*k FP32 entries and, when qblk is given, the raw FP64 block
+// Q[S, S] (the merge evaluates its candidates on it).
 constexpr int SQ_CHUNK = 128;
 
-__global__ void __launch_bounds__(128) k_subqubo(const double* __restrict__ Q, int N,
+__global__ void __launch_bounds__(256) k_subqubo(const double* __restrict__ Q, int N,
                                                  const uint8_t* __restrict__ x, int k,
                                                  const int32_t* __restrict__ idx, int conditioned,
                                                  float* __restrict__ qsub, double* __restrict__ qblk) {
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(128) k_subqubo(const double* __restrict__ Q, i
         if (qblk) qblk[(int64_t)j * k * k + e] = q;
     }
     if (!conditioned) return;
+    const int ra = threadIdx.x >> 3, rr = threadIdx.x & 7;   // row and residue of this thread
     double h = 0.0;
     for (int c0 = 0; c0 < N; c0 += SQ_CHUNK) {
         const int len = min(SQ_CHUNK, N - c0);
@@ -50,17 +52,18 @@ __global__ void __launch_bounds__(128) k_subqubo(const double* __restrict__ Q, i
             for (int l = lane; l < len; l += 32) rows[a * (SQ_CHUNK + 1) + l] = row[l];
         }
         __syncthreads();
-        if (threadIdx.x < k) {
-            const double* r = rows + threadIdx.x * (SQ_CHUNK + 1);
-            for (int l = 0; l < len; ++l)
+        if (ra < k) {
+            const double* r = rows + ra * (SQ_CHUNK + 1);
+            // c0 is a multiple of 8, so column c0 + l has residue l mod 8
+            for (int l = rr; l < len; l += 8)
                 if (xm[c0 + l]) h += r[l];
         }
         __syncthreads();
     }
-    if (threadIdx.x < k) {
-        const int a = threadIdx.x;
-        out[a * k + a] = (float)(Q[(int64_t)S[a] * N + S[a]] + 2.0 * h);
-    }
+    h = h + __shfl_xor_sync(0xffffffffu, h, 1);
+    h = h + __shfl_xor_sync(0xffffffffu, h, 2);
+    h = h + __shfl_xor_sync(0xffffffffu, h, 4);
+    if (ra < k && rr == 0) out[ra * k + ra] = (float)(Q[(int64_t)S[ra] * N + S[ra]] + 2.0 * h);
 }
 
 }  // namespace
@@ -73,7 +76,8 @@ cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int 
         const cudaError_t e = cudaFuncSetAttribute(k_subqubo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_subqubo<<<m, 128, sm, st>>>(Q, N, x, k, idx, conditioned, qsub, qblk);
+    // eight threads per row (k <= 30): 256 threads cover every row
+    k_subqubo<<<m, 256, sm, st>>>(Q, N, x, k, idx, conditioned, qsub, qblk);
     return cudaGetLastError();
 }
 
