@@ -104,11 +104,14 @@ struct StreamSmem {
     LayerConst<T>* lc;
     double* red;
     TileTopk tk;
+    TopEnt* run;     // running top-k of the state's tiles this block reduced (last pass)
 };
 
+// have_run: this block reduced tile prev_tau of the same state just before (last pass, k >= 1);
+// s.run then holds the top-k of all the state's tiles it reduced so far.
 template <typename T, int R>
 __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_t tau,
-                            const StreamSmem<T>& s) {
+                            const StreamSmem<T>& s, bool have_run, uint64_t prev_tau) {
     using C = typename Num<T>::C;
     const uint32_t TD = 1u << P.tb;
     const bool needE = P.need_e;
@@ -163,13 +166,29 @@ __device__ void stream_tile(const StreamPass& P, const StreamInst<T>& I, uint64_
     }
     if (P.fin) {
         double ex = 0.0;
-        tile_reduce<T>(tile, P.k, [&](uint32_t u) { return (uint32_t)global_index(P, tau, u); }, s.tk, ex);
+        const StreamPass Pm = P;   // by value: the lambda then holds no address of a kernel parameter
+        const auto zmap = [Pm, tau](uint32_t u) { return (uint32_t)global_index(Pm, tau, u); };
+        const float pmax = tile_expect<T>(tile, ex);
+        if (P.k > 0) {
+            if (have_run) {
+                running_topk<T>(tile, P.k, pmax, zmap, s.tk, s.run);
+            } else {
+                tile_topk<T>(tile, P.k, pmax, zmap, s.tk);
+                if (threadIdx.x < (unsigned)P.k) s.run[threadIdx.x] = s.tk.out[threadIdx.x];
+            }
+        }
         const double tot = block_sum(ex, s.red);
         if (threadIdx.x == 0) I.part_expect[tau] = tot;
+        // the running list goes to this tile's slot and the previous tile's slot is emptied (the
+        // same thread wrote it), so each state's slots hold every candidate exactly once
         if (threadIdx.x < (unsigned)P.k) {
-            const TopEnt e = s.tk.out[threadIdx.x];
+            const TopEnt e = s.run[threadIdx.x];
             I.part_topp[tau * P.k + threadIdx.x] = e.p;
             I.part_topz[tau * P.k + threadIdx.x] = e.z;
+            if (have_run) {
+                I.part_topp[prev_tau * P.k + threadIdx.x] = -1.0;
+                I.part_topz[prev_tau * P.k + threadIdx.x] = 0xffffffffu;
+            }
         }
     }
     __syncthreads();
@@ -192,6 +211,7 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
     s.tk.wlists = reinterpret_cast<TopEnt*>(sm + o); o += 8 * 32 * sizeof(TopEnt);
     s.tk.cand = reinterpret_cast<TopEnt*>(sm + o); o += TOPK_CAP * sizeof(TopEnt);
     s.tk.out = reinterpret_cast<TopEnt*>(sm + o); o += 16 * sizeof(TopEnt);
+    s.run = reinterpret_cast<TopEnt*>(sm + o); o += 16 * sizeof(TopEnt);
     s.tk.wb = reinterpret_cast<float*>(sm + o); o += 16 * 32 * sizeof(float);
     s.tk.cnt = reinterpret_cast<int*>(sm + o);
     const uint64_t ntiles = 1ull << (P.n - P.tb);
@@ -200,7 +220,19 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
     // share one parameter vector)
     const T *cur_g = nullptr, *cur_b = nullptr;
     int cur_p = 0;
-    for (uint64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    // The last pass with a top-k gives each block a run of consecutive tiles instead of a
+    // grid-strided share (the longest share is the same), so that the tiles of one state follow
+    // each other and the block carries one top-k list across them.
+    uint64_t b = blockIdx.x, bstep = gridDim.x, bend = total;
+    if (P.fin && P.k > 0) {
+        const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+        b = (uint64_t)blockIdx.x * per;
+        bend = b + per < total ? b + per : total;
+        bstep = 1;
+    }
+    int run_ii = -1;
+    uint64_t run_tau = 0;
+    for (; b < bend; b += bstep) {
         const int ii = (int)(b / ntiles);
         const uint64_t tau = b % ntiles;
         const StreamInst<T>& I = insts ? insts[ii] : one;
@@ -213,7 +245,9 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
             cur_p = I.p;
         }
         constexpr int RB = Num<T>::RB;
-        stream_tile<T, RB>(P, I, tau, s);
+        stream_tile<T, RB>(P, I, tau, s, run_ii == ii, run_tau);
+        run_ii = ii;
+        run_tau = tau;
     }
 }
 
@@ -746,7 +780,7 @@ size_t stream_smem_bytes(bool dbl) {
     const size_t c = dbl ? 16 : 8, r = dbl ? 8 : 4, lcs = dbl ? sizeof(LayerConst<double>) : sizeof(LayerConst<float>);
     size_t o = TD * c + TD * r + 64 * lcs;
     o = (o + 15) & ~(size_t)15;
-    return o + 32 * sizeof(double) + (8 * 32 + TOPK_CAP + 16) * sizeof(TopEnt) +
+    return o + 32 * sizeof(double) + (8 * 32 + TOPK_CAP + 16 + 16) * sizeof(TopEnt) +
            16 * 32 * sizeof(float) + 4 * sizeof(int);
 }
 

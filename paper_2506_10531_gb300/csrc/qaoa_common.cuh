@@ -236,8 +236,16 @@ struct TopEnt {
     uint32_t z;
 };
 
+// Probabilities are non-negative doubles (never -0: a sum of squares rounds to +0) and an empty
+// entry holds -1. On those values the IEEE bit patterns, read as signed 64-bit integers, order
+// exactly as the doubles do (every empty entry below every probability), so the list logic
+// compares integers: GB300 issues FP64 at a small fraction of the integer rate.
+__device__ __forceinline__ long long pbits(double p) { return __double_as_longlong(p); }
+__device__ __forceinline__ bool is_entry(double p) { return pbits(p) >= 0; }
+
 __device__ __forceinline__ bool better(double p1, uint32_t z1, double p2, uint32_t z2) {
-    return (p1 > p2) || (p1 == p2 && z1 < z2);
+    const long long a = pbits(p1), b = pbits(p2);
+    return (a > b) || (a == b && z1 < z2);
 }
 
 // exact probability of a stored amplitude
@@ -279,7 +287,7 @@ struct WarpTopK {
             else if (lane > pos && lane < k) { p = up_p; z = up_z; }
         }
         const double kth = __shfl_sync(0xffffffffu, p, k - 1);
-        thr_f = fmaxf((kth < 0.0) ? -1.0f : __double2float_rd(kth), boot);
+        thr_f = fmaxf(is_entry(kth) ? __double2float_rd(kth) : -1.0f, boot);
     }
     // Offer one amplitude per lane (all lanes call; lanes with valid == false offer nothing).
     template <typename C>
@@ -305,7 +313,7 @@ struct WarpTopK {
     }
     // Offer an entry with a known exact probability (merging lists).
     __device__ __forceinline__ void offer_exact(double cp, uint32_t zi, bool valid) {
-        uint32_t m = __ballot_sync(0xffffffffu, valid && cp >= 0.0);
+        uint32_t m = __ballot_sync(0xffffffffu, valid && is_entry(cp));
         while (m) {
             const int src = __ffs(m) - 1;
             m &= m - 1;

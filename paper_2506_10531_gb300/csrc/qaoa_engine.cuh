@@ -660,71 +660,55 @@ struct TileTopk {
     int* cnt;         // [0] candidate count, [1] overflow flag, [2..3] bound (float / double bits)
 };
 
-// Collect the elements whose probability can reach `bound` (FP32 filter with the margins of
-// WarpTopK::offer; with exact != 0 the exact probability must also be >= *exact_bound) into
-// ts.cand. Sets ts.cnt[1] on overflow.
+// Collect the elements whose probability can reach `bound_lo` (FP32 filter with the margins of
+// WarpTopK::offer; with exact_bound != 0 the exact probability must also be >= *exact_bound)
+// into ts.cand. Sets ts.cnt[1] on overflow. Each thread scans only its own elements
+// u = tid + j * blockDim, and only if its FP32 maximum over them (pmax, from the pass that
+// computed the tile's <C> partial) can reach the bound: a list of k entries has few owners, so
+// most threads skip the scan. pmax and the per-element value are two FP32 roundings of the same
+// probability, each within 2^-21 of it, hence the wider 2^-18 margin of the thread test.
 template <typename T, typename ZMap>
-__device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float bound_lo,
+__device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float pmax, float bound_lo,
                                                    const double* exact_bound, ZMap&& zmap,
                                                    const TileTopk& ts) {
     using C = typename Num<T>::C;
     const uint32_t D = 1u << t.tb;
-    const int lane = threadIdx.x & 31;
-    for (uint32_t u0 = 0; u0 < D; u0 += blockDim.x) {
-        const uint32_t u = u0 + threadIdx.x;
-        C v;
-        v.x = T(0);
-        v.y = T(0);
-        if (u < D) v = t.psi[swz<T>(u)];
-        const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
-        bool c = (u < D) && (pf * 1.00000095367431640625f >= bound_lo);
-        // FP64 work only behind a warp-uniform branch: GB300 issues FP64 at 1/64 of the FP32
-        // rate, so it must never sit (predicated) on the per-element path
-        if (__any_sync(0xffffffffu, c)) {
-            double pe = 0.0;
-            if (c) {
-                pe = exact_prob(v);
-                if (exact_bound) c = pe >= *exact_bound;
+    if (!(pmax * 1.000003814697265625f >= bound_lo)) return;
+    const long long eb = exact_bound ? pbits(*exact_bound) : -1ll;
+    for (uint32_t c0 = 0; c0 < D; c0 += 32u * blockDim.x) {
+        // FP32 test of up to 32 elements first (independent loads), then the hits one by one
+        uint32_t hits = 0;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t u = c0 + (uint32_t)j * blockDim.x + threadIdx.x;
+            if (u < D) {
+                const C v = t.psi[swz<T>(u)];
+                const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
+                if (pf * 1.00000095367431640625f >= bound_lo) hits |= 1u << j;
             }
-            const uint32_t m = __ballot_sync(0xffffffffu, c);
-            if (m) {
-                int base = 0;
-                if (lane == __ffs(m) - 1) base = atomicAdd(&ts.cnt[0], __popc(m));
-                base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-                if (c) {
-                    const int pos = base + __popc(m & ((1u << lane) - 1u));
-                    if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{pe, zmap(u)};
-                    else ts.cnt[1] = 1;
-                }
+        }
+        while (hits) {
+            const int j = __ffs(hits) - 1;
+            hits &= hits - 1;
+            const uint32_t u = c0 + (uint32_t)j * blockDim.x + threadIdx.x;
+            const double pe = exact_prob(t.psi[swz<T>(u)]);
+            if (pbits(pe) >= eb) {
+                const int pos = atomicAdd(&ts.cnt[0], 1);
+                if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{pe, zmap(u)};
+                else ts.cnt[1] = 1;
             }
         }
     }
 }
 
-// <C> partial and top-k list of the whole tile, after the last sub-pass. Every thread reads
-// the elements u = tid + j*blockDim:
-//  1. FP32 |psi|^2 E over at most 32 elements per thread (FP64 above, in `ex`), and the
-//     thread's largest FP32 probability (its lane maximum);
-//  2. a lower bound on the tile's k-th largest probability: the k-th largest of all lane
-//     maxima (k distinct elements are at least that probable). Each warp sorts its lane
-//     maxima and offers its k largest; their k-th largest is found by rank;
-//  3. every element whose probability can reach the bound goes to a shared candidate buffer
-//     with its exact FP64 probability; on overflow (flat distributions) the bound is raised
-//     to the k-th largest exact probability among the buffered elements and the collection
-//     repeated with an exact test;
-//  4. each candidate's rank = number of candidates better than it (probability descending,
-//     index ascending: a strict total order, so ranks are distinct); ranks < k are the list.
-// The result does not depend on the order of the buffer, so the reduction is deterministic.
-// If the buffer still overflows (massive ties) the warps fall back to sorted insertion lists
-// merged by warp 0. zmap(u): global index of tile index u. Called by all threads.
-template <typename T, typename ZMap>
-__device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& zmap,
-                                            const TileTopk& ts, double& ex) {
+// <C> partial of the tile (FP32 |psi|^2 E over at most 32 elements per thread, FP64 above, added
+// to `ex`) and the thread's largest FP32 probability over its elements u = tid + j * blockDim
+// (its lane maximum, returned). Called by all threads; no barrier.
+template <typename T>
+__device__ __forceinline__ float tile_expect(const TileRef<T>& t, double& ex) {
     using C = typename Num<T>::C;
     const uint32_t D = 1u << t.tb;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     float pmax = -1.0f;
-    // chunks of at most 32 elements per thread in FP32; the FP64 add sits outside the chunk
     for (uint32_t c0 = 0; c0 < D; c0 += 32u * blockDim.x) {
         T accp = T(0);
 #pragma unroll 8
@@ -740,8 +724,29 @@ __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& z
         }
         ex += (double)accp;
     }
-    if (k <= 0) return;
-    // (2) the k-th largest lane maximum of the block
+    return pmax;
+}
+
+// Top-k list of the whole tile into ts.out, given each thread's lane maximum pmax:
+//  1. a lower bound on the tile's k-th largest probability: the k-th largest of all lane
+//     maxima (k distinct elements are at least that probable). Each warp sorts its lane
+//     maxima and offers its k largest; their k-th largest is found by rank;
+//  2. every element whose probability can reach the bound goes to a shared candidate buffer
+//     with its exact FP64 probability; on overflow (flat distributions) the bound is raised
+//     to the k-th largest exact probability among the buffered elements and the collection
+//     repeated with an exact test;
+//  3. each candidate's rank = number of candidates better than it (probability descending,
+//     index ascending: a strict total order, so ranks are distinct); ranks < k are the list.
+// The result does not depend on the order of the buffer, so the reduction is deterministic.
+// If the buffer still overflows (massive ties) the warps fall back to sorted insertion lists
+// merged by warp 0. zmap(u): global index of tile index u. Called by all threads, k >= 1.
+template <typename T, typename ZMap>
+__device__ __forceinline__ void tile_topk(const TileRef<T>& t, int k, float pmax, ZMap&& zmap,
+                                          const TileTopk& ts) {
+    using C = typename Num<T>::C;
+    const uint32_t D = 1u << t.tb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    // (1) the k-th largest lane maximum of the block
     const float srt = warp_sort_desc(pmax);
     if (lane < k) ts.wb[warp * k + lane] = srt;
     if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
@@ -760,8 +765,8 @@ __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& z
     __syncthreads();
     const float thr = *bound;
     const float thr_lo = thr > 0.0f ? thr * 0.99999904632568359375f : -1.0f;   // (1 - 2^-20)
-    // (3) candidates
-    collect_candidates<T>(t, thr_lo, nullptr, zmap, ts);
+    // (2) candidates
+    collect_candidates<T>(t, pmax, thr_lo, nullptr, zmap, ts);
     __syncthreads();
     if (ts.cnt[1]) {
         // raise the bound to the k-th best buffered exact probability and collect again
@@ -779,11 +784,12 @@ __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& z
         const float b2lo = __double2float_rd(*b2) * 0.99999904632568359375f;
         if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
         __syncthreads();
-        collect_candidates<T>(t, b2lo, b2, zmap, ts);
+        collect_candidates<T>(t, pmax, b2lo, b2, zmap, ts);
         __syncthreads();
     }
     const int cnt = min(ts.cnt[0], TOPK_CAP);
     if (!ts.cnt[1]) {
+        // (3) rank selection
         for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
             const TopEnt me = ts.cand[c];
             int rank = 0;
@@ -822,16 +828,63 @@ __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& z
     __syncthreads();
 }
 
+// <C> partial (added to `ex`) and, for k >= 1, the top-k list (ts.out) of the whole tile after
+// its last sub-pass. Called by all threads.
+template <typename T, typename ZMap>
+__device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& zmap,
+                                            const TileTopk& ts, double& ex) {
+    const float pmax = tile_expect<T>(t, ex);
+    if (k <= 0) return;
+    tile_topk<T>(t, k, pmax, zmap, ts);
+}
+
+// Fold the tile into `run`, the top-k list (k entries, all present) of the tiles of the same
+// state that this block reduced before: only elements that can beat run's k-th entry are
+// collected (usually none once a few tiles are in), and the merged list is the k best of the
+// candidates and run by rank. On candidate overflow the tile's own list (tile_topk) is merged
+// instead. pmax as from tile_expect. Called by all threads.
+template <typename T, typename ZMap>
+__device__ __forceinline__ void running_topk(const TileRef<T>& t, int k, float pmax, ZMap&& zmap,
+                                             const TileTopk& ts, TopEnt* run) {
+    const double* pk = &run[k - 1].p;
+    const float lo = __double2float_rd(*pk) * 0.99999904632568359375f;
+    if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
+    if (!__syncthreads_or(pmax * 1.000003814697265625f >= lo)) return;
+    collect_candidates<T>(t, pmax, lo, pk, zmap, ts);
+    __syncthreads();
+    const TopEnt* a = ts.cand;
+    int na = ts.cnt[0];
+    if (ts.cnt[1]) {
+        __syncthreads();                        // every thread has read the counters that tile_topk resets
+        tile_topk<T>(t, k, pmax, zmap, ts);
+        a = ts.out;
+        na = k;
+    }
+    if (na == 0) return;                        // uniform: every thread read the same count
+    TopEnt* merged = ts.wlists;                 // free here (tile_topk ended with a barrier)
+    for (int c = threadIdx.x; c < na + k; c += blockDim.x) {
+        const TopEnt me = c < na ? a[c] : run[c - na];
+        if (!is_entry(me.p)) continue;
+        int rank = 0;
+        for (int j = 0; j < na; ++j) rank += better(a[j].p, a[j].z, me.p, me.z) ? 1 : 0;
+        for (int j = 0; j < k; ++j) rank += better(run[j].p, run[j].z, me.p, me.z) ? 1 : 0;
+        if (rank < k) merged[rank] = me;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)k) run[threadIdx.x] = merged[threadIdx.x];
+    __syncthreads();
+}
+
 // Top-k of a small set of candidate lists already in shared memory (count entries, entries
 // with p < 0 are empty): rank selection as in tile_reduce; result in out[0..k).
 __device__ __forceinline__ void rank_select(const TopEnt* cand, int count, int k, TopEnt* out) {
     for (int c = threadIdx.x; c < count; c += blockDim.x) {
         const TopEnt me = cand[c];
-        if (me.p < 0.0) continue;
+        if (!is_entry(me.p)) continue;
         int rank = 0;
         for (int j = 0; j < count; ++j) {
             const TopEnt o = cand[j];
-            rank += (o.p >= 0.0 && better(o.p, o.z, me.p, me.z)) ? 1 : 0;
+            rank += (is_entry(o.p) && better(o.p, o.z, me.p, me.z)) ? 1 : 0;
         }
         if (rank < k) out[rank] = me;
     }

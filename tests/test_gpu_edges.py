@@ -1,7 +1,8 @@
 """Edge cases through the C ABI: the largest depth (p = 64) on every tier, a batch of one and of
 zero instances, k = 0 (no top-k requested), k = 2^n (every bitstring ranked), the DQAOA session
-with one chunk and with two chunks giving the same cycle, and a zero-parameter layer (γ = β = 0:
-the state stays |+>)."""
+with one chunk and with two chunks giving the same cycle, a zero-parameter layer (γ = β = 0:
+the state stays |+>), and the streaming top-k carried across runs of tiles (runs crossing states,
+long runs, all-tied probabilities, FP64 states)."""
 import numpy as np
 import pytest
 
@@ -129,3 +130,60 @@ def test_session_chunking_does_not_change_the_cycle(q, orc):
         xo, eo, _ = orc.merge(Q, x0, idx, out[m][2])
         np.testing.assert_array_equal(out[m][0], xo)
     np.testing.assert_array_equal(out[127][2], out[128][2][:127])
+
+
+def batch_states_topk(q, ctx, n, count, k, p, seed, zero=False, dbl=False):
+    """One plan over `count` instances of n qubits; returns the final states and the top-k."""
+    rt, tt = (np.float64, torch.float64) if dbl else (np.float32, torch.float32)
+    Qs, pars = [], []
+    for i in range(count):
+        Qs.append(synth.symmetric_q(n, seed=seed + i).astype(rt).reshape(-1))
+        g, b = synth.random_params(p, seed=seed + 1000 + i)
+        if zero:
+            g, b = 0.0 * g, 0.0 * b
+        pars.append(np.concatenate([g, b]).astype(rt))
+    qd = torch.as_tensor(np.concatenate(Qs)).cuda()
+    pd = torch.as_tensor(np.concatenate(pars)).cuda()
+    psi = torch.zeros(count << (n + 1), dtype=tt, device="cuda")
+    ex = torch.zeros(count, dtype=torch.float64, device="cuda")
+    ti = torch.zeros(count * k, dtype=torch.int64, device="cuda")
+    tp = torch.zeros(count * k, dtype=torch.float64, device="cuda")
+    io = q.make_io(qd, pd, expect=ex, topk_idx=ti, topk_prob=tp, k_stride=k, psi=psi)
+    rows = [(n, p, k, 0, i * n * n, i * 2 * p, i << n, -1) for i in range(count)]
+    plan = q.qaoa_plan_create(ctx, q.make_insts(rows), io, dbl=dbl)
+    try:
+        q.qaoa_plan_launch(plan)
+        torch.cuda.synchronize()
+    finally:
+        q.qaoa_plan_destroy(plan)
+    amps = psi.cpu().numpy().reshape(count, 1 << n, 2).astype(np.float64)
+    return amps, ti.cpu().numpy().reshape(count, k), tp.cpu().numpy().reshape(count, k)
+
+
+def host_topk(a, k):
+    # |psi|^2 of the stored amplitudes as the device forms it: two rounded squares, one rounded add
+    pr = a[:, 0] * a[:, 0] + a[:, 1] * a[:, 1]
+    order = np.lexsort((np.arange(pr.size), -pr))[:k]
+    return order, pr[order]
+
+
+# The last streaming pass hands each block a run of consecutive tiles and carries one top-k list
+# across the tiles of a state. These cases make the runs cross state boundaries (40 states of 32
+# tiles), run long inside one state (n = 24), tie every probability (zero angles: the candidate
+# buffer overflows on every tile), and use FP64 states. The list must equal the top-k of the
+# returned state, bit for bit.
+@pytest.mark.parametrize("n,count,k,p,zero,dbl", [
+    (18, 40, 8, 2, False, False),
+    (18, 40, 16, 1, False, False),
+    (24, 1, 8, 2, False, False),
+    (18, 40, 8, 1, True, False),
+    (17, 48, 5, 2, False, True),
+])
+def test_stream_topk_runs(q, ctx, n, count, k, p, zero, dbl):
+    amps, ti, tp = batch_states_topk(q, ctx, n, count, k, p, 1300 + n, zero=zero, dbl=dbl)
+    for i in range(count):
+        oi, op = host_topk(amps[i], k)
+        np.testing.assert_array_equal(ti[i].astype(np.int64), oi)
+        np.testing.assert_array_equal(tp[i], op)
+    if zero:
+        assert (ti == np.arange(k)[None, :]).all()
