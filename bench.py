@@ -269,6 +269,7 @@ def run_ours(args):
           for _ in range(args.steps)]
     kern = {}
     energies = []
+    phases = []
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -279,6 +280,7 @@ def run_ours(args):
             e, acc = q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 100 + s, stream)
             ev[s][1].record(stream)
             energies.append(e)
+            phases.append(q.dqaoa_session_timing(sess))
             for pl in plans:
                 for name, ms in q.qaoa_plan_kernel_times(pl):
                     kern.setdefault(name, []).append(ms)
@@ -336,6 +338,8 @@ def run_ours(args):
         "kernel_only": kb, "plain_gpu_path": plain,
         "batched_over_plain": kb["solves_per_s"] / plain["solves_per_s"],
         "kernel_ms_per_step": {nm: sum(v) / args.steps for nm, v in kern.items()},
+        # host clock: index draw + uploads + launches, device span, merge, whole call
+        "cycle_phases_ms": {key: float(np.mean([ph[key] for ph in phases])) for key in phases[0]},
         "roofline": roof,
         "final_energy": energies[-1],
         "e2e": e2e, "gpu_launches": gpu_launches,

@@ -13,7 +13,8 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["qaoa_api.cu", "k_resident.cu", "k_cluster.cu", "k_stream.cu", "k_plain.cu", "k_dqaoa.cu",
            "k_noalloc.cu", "qaoa_server.cu", "qaoa_tune.cu", "dqaoa_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# host code without FP contraction: the host merge rounds the same way on every architecture
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"] + ARCH
 
 

@@ -157,36 +157,48 @@ int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, 
     int accepted = 0;
     int nz[64];
     double d[64];
+    const uint64_t kmask = k >= 64 ? ~0ull : (1ull << k) - 1ull;
     for (int j = 0; j < m; ++j) {
         const int32_t* S = idx + (int64_t)j * k;
         const double* blk = qblk ? qblk + (int64_t)j * k * k : nullptr;
+        // x on S_j packed like a candidate: the changed positions of a candidate are then the set
+        // bits of y ^ xs, visited in ascending order without a data-dependent branch per position
+        uint64_t xs = 0;
+        for (int a = 0; a < k; ++a) xs |= (uint64_t)(x[S[a]] != 0) << a;
         for (int c = 0; c < K; ++c) {
             const uint64_t y = cand[(int64_t)j * K + c];
             int cnt = 0;
-            for (int a = 0; a < k; ++a) {
-                const double da = (double)((y >> a) & 1u) - (double)x[S[a]];
-                if (da != 0.0) { nz[cnt] = a; d[cnt] = da; ++cnt; }
+            for (uint64_t diff = (y ^ xs) & kmask; diff; diff &= diff - 1) {
+                const int a = __builtin_ctzll(diff);
+                nz[cnt] = a;
+                d[cnt] = ((y >> a) & 1u) ? 1.0 : -1.0;   // x'_a - x_a
+                ++cnt;
             }
             if (!cnt) continue;
             // inner[u] = sum over v (ascending) of Q[S_u][S_v] d_v; the u sums are independent,
             // so they advance together (each keeps its own order)
             double inner[64];
-            for (int u = 0; u < cnt; ++u) inner[u] = 0.0;
+            double dE = 0.0;
             if (blk) {
+                // with the block at hand, every row a of it advances (contiguous, vectorisable:
+                // Q[S_a][S_v] = Q[S_v][S_a] is row v of the symmetric block) and the changed
+                // rows are read at the end; the sums of the changed rows are the same sums
+                for (int a = 0; a < k; ++a) inner[a] = 0.0;
                 for (int v = 0; v < cnt; ++v) {
                     const double dv = d[v];
-                    const int cv = nz[v];
-                    for (int u = 0; u < cnt; ++u) inner[u] += blk[nz[u] * k + cv] * dv;
+                    const double* col = blk + (int64_t)nz[v] * k;
+                    for (int a = 0; a < k; ++a) inner[a] += col[a] * dv;
                 }
+                for (int u = 0; u < cnt; ++u) dE += d[u] * (2.0 * h[S[nz[u]]] + inner[nz[u]]);
             } else {
+                for (int u = 0; u < cnt; ++u) inner[u] = 0.0;
                 for (int v = 0; v < cnt; ++v) {
                     const double dv = d[v];
                     const int64_t cv = S[nz[v]];
                     for (int u = 0; u < cnt; ++u) inner[u] += Q[(int64_t)S[nz[u]] * N + cv] * dv;
                 }
+                for (int u = 0; u < cnt; ++u) dE += d[u] * (2.0 * h[S[nz[u]]] + inner[u]);
             }
-            double dE = 0.0;
-            for (int u = 0; u < cnt; ++u) dE += d[u] * (2.0 * h[S[nz[u]]] + inner[u]);
             if (dE < -tau) {
                 for (int u = 0; u < cnt; ++u) {
                     const int var = S[nz[u]];
@@ -198,6 +210,8 @@ int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, 
                 }
                 energy += dE;
                 ++accepted;
+                xs = 0;
+                for (int a = 0; a < k; ++a) xs |= (uint64_t)(x[S[a]] != 0) << a;
             }
         }
     }

@@ -1030,6 +1030,9 @@ struct dqaoa_session {
     qaoa_plan* plans[2] = {nullptr, nullptr};
     cudaEvent_t chunk_done[2] = {nullptr, nullptr};
     cudaEvent_t dev_begin = nullptr, dev_end = nullptr;   // device part of the last cycle
+    // the FP64 blocks go to the host on a side stream, beside the first chunk's kernels
+    cudaStream_t side = nullptr;
+    cudaEvent_t sub_done = nullptr, qblk_done = nullptr;
     double t_decompose = 0.0, t_merge = 0.0, t_cycle = 0.0; // host ms of the last cycle
     MergeCache cache;             // h = Qx and E(x) after the last merge
     std::vector<uint8_t> x_last;  // the solution the cache belongs to
@@ -1107,7 +1110,10 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
             st = fail(QAOA_E_CUDA, "session event");
         if (st) { dqaoa_session_destroy(s); return st; }
     }
-    if (cudaEventCreate(&s->dev_begin) != cudaSuccess || cudaEventCreate(&s->dev_end) != cudaSuccess) {
+    if (cudaEventCreate(&s->dev_begin) != cudaSuccess || cudaEventCreate(&s->dev_end) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->sub_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->qblk_done, cudaEventDisableTiming) != cudaSuccess) {
         dqaoa_session_destroy(s);
         return fail(QAOA_E_CUDA, "session events");
     }
@@ -1140,7 +1146,10 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     CK(cudaMemcpyAsync(s->x_dev, s->x_h, (size_t)N, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->idx_dev, s->idx_h, (size_t)m * k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(launch_subqubo(s->Q_dev, N, s->x_dev, m, k, s->idx_dev, s->conditioned, s->qsub, st, s->qblk));
-    CK(cudaMemcpyAsync(s->qblk_h, s->qblk, (size_t)m * k * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(s->sub_done, st));
+    CK(cudaStreamWaitEvent(s->side, s->sub_done, 0));
+    CK(cudaMemcpyAsync(s->qblk_h, s->qblk, (size_t)m * k * k * sizeof(double), cudaMemcpyDeviceToHost, s->side));
+    CK(cudaEventRecord(s->qblk_done, s->side));
     // solve the sub-QUBOs chunk by chunk; each chunk's results come back behind its own event
     for (int ch = 0; ch < s->chunks; ++ch) {
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
@@ -1166,6 +1175,7 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
                      std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
     int accepted = 0;
     double t_merge = 0.0;
+    CK(cudaEventSynchronize(s->qblk_done));
     for (int ch = 0; ch < s->chunks; ++ch) {
         CK(cudaEventSynchronize(s->chunk_done[ch]));
         const double tm = now_ms();
@@ -1216,6 +1226,9 @@ extern "C" void dqaoa_session_destroy(dqaoa_session* s) {
     }
     if (s->dev_begin) cudaEventDestroy(s->dev_begin);
     if (s->dev_end) cudaEventDestroy(s->dev_end);
+    if (s->sub_done) cudaEventDestroy(s->sub_done);
+    if (s->qblk_done) cudaEventDestroy(s->qblk_done);
+    if (s->side) cudaStreamDestroy(s->side);
     cudaFreeHost(s->host);
     cudaFree(s->dev);
     delete s;
