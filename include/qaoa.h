@@ -321,8 +321,10 @@ qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* to
  * host merge time (the first chunk's merge overlaps the device), and the whole call. */
 qaoa_status dqaoa_session_timing(dqaoa_session* s, double* out);
 /* The batched plans the session launches, in order (for timing and kernel counts): the m
- * sub-QUBOs are solved in two chunks of m/2 when m >= 128 (the host merges the first chunk while
- * the device solves the second), else in one. Returns NULL for i past the last plan. */
+ * sub-QUBOs are solved in two chunks when m >= 128, else in one. The host merges the first chunk
+ * while the device solves the second; the first holds ceil(0.65 m) sub-QUBOs rounded up to a
+ * multiple of the instances whose tiles give each block of a streaming launch one tile (at most
+ * m - 1). Returns NULL for i past the last plan. */
 qaoa_plan* dqaoa_session_plan(dqaoa_session* s, int i);
 void dqaoa_session_destroy(dqaoa_session* s);
 

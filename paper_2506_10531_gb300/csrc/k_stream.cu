@@ -221,13 +221,14 @@ __global__ void __launch_bounds__(256, 2) k_stream_pass(const StreamPass P,
     const T *cur_g = nullptr, *cur_b = nullptr;
     int cur_p = 0;
     // The last pass with a top-k gives each block a run of consecutive tiles instead of a
-    // grid-strided share (the longest share is the same), so that the tiles of one state follow
-    // each other and the block carries one top-k list across them.
+    // grid-strided share, so that the tiles of one state follow each other and the block carries
+    // one top-k list across them. The run lengths are those of the strided share: total / grid,
+    // one more for the first total % grid blocks.
     uint64_t b = blockIdx.x, bstep = gridDim.x, bend = total;
     if (P.fin && P.k > 0) {
-        const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
-        b = (uint64_t)blockIdx.x * per;
-        bend = b + per < total ? b + per : total;
+        const uint64_t q = total / gridDim.x, rem = total % gridDim.x, c = blockIdx.x;
+        b = c * q + (c < rem ? c : rem);
+        bend = b + q + (c < rem ? 1 : 0);
         bstep = 1;
     }
     int run_ii = -1;

@@ -1028,7 +1028,8 @@ struct dqaoa_session {
     int chunks = 1;
     int chunk_start[3] = {0, 0, 0};
     qaoa_plan* plans[2] = {nullptr, nullptr};
-    cudaEvent_t chunk_done[2] = {nullptr, nullptr};
+    cudaEvent_t chunk_solved[2] = {nullptr, nullptr};   // chunk's kernels done (main stream)
+    cudaEvent_t chunk_done[2] = {nullptr, nullptr};     // chunk's results on the host (side stream)
     cudaEvent_t dev_begin = nullptr, dev_end = nullptr;   // device part of the last cycle
     // the FP64 blocks go to the host on a side stream, beside the first chunk's kernels
     cudaStream_t side = nullptr;
@@ -1092,8 +1093,23 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)beta[l]; }
     e = cudaMemcpy(s->params, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { dqaoa_session_destroy(s); return cuda_fail(e, "session params upload"); }
+    // Two chunks from m = 128 on. The first takes about two thirds, rounded up to whole waves
+    // (instances whose tiles give every block of a streaming launch one tile), so that the merge
+    // left after the device finishes is short while the second chunk's device time still covers
+    // most of the first chunk's merge (measured on GB300 for 256 sub-QUBOs of n = 16: 190 / 66
+    // beats 152 / 104, 128 / 128 and 114 / 142 by 4-8%).
     s->chunks = m >= 128 ? 2 : 1;
-    s->chunk_start[1] = s->chunks == 2 ? m / 2 : m;
+    int m0 = m;
+    if (s->chunks == 2) {
+        int w = 1;
+        if (k >= 16 && (k > 18 || eff_tier(c, k, p) == QAOA_TIER_STREAM)) {
+            const int tiles = 1 << (k - stream_tile_bits(false));
+            w = std::max(1, 2 * c->nsm / tiles);
+        }
+        m0 = (m * 13 + 19) / 20;
+        m0 = std::min(m - 1, (m0 + w - 1) / w * w);
+    }
+    s->chunk_start[1] = m0;
     s->chunk_start[2] = m;
     for (int ch = 0; ch < s->chunks; ++ch) {
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
@@ -1106,7 +1122,8 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
         io.topk_idx = s->topk + (size_t)j0 * K;
         io.k_stride = K;
         qaoa_status st = qaoa_plan_create(c, d.data(), mc, &io, 0, &s->plans[ch]);
-        if (st == QAOA_OK && cudaEventCreateWithFlags(&s->chunk_done[ch], cudaEventDisableTiming) != cudaSuccess)
+        if (st == QAOA_OK && (cudaEventCreateWithFlags(&s->chunk_done[ch], cudaEventDisableTiming) != cudaSuccess ||
+                              cudaEventCreateWithFlags(&s->chunk_solved[ch], cudaEventDisableTiming) != cudaSuccess))
             st = fail(QAOA_E_CUDA, "session event");
         if (st) { dqaoa_session_destroy(s); return st; }
     }
@@ -1155,12 +1172,15 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
         r = qaoa_plan_launch(s->plans[ch], stream);
         if (r) return r;
+        // results to the host on the side stream: the next chunk's kernels do not wait for them
+        CK(cudaEventRecord(s->chunk_solved[ch], st));
+        CK(cudaStreamWaitEvent(s->side, s->chunk_solved[ch], 0));
         CK(cudaMemcpyAsync(s->topk_h + (size_t)j0 * K, s->topk + (size_t)j0 * K, (size_t)mc * K * sizeof(uint64_t),
-                           cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(s->expect_h + j0, s->expect + j0, (size_t)mc * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaEventRecord(s->chunk_done[ch], st));
+                           cudaMemcpyDeviceToHost, s->side));
+        CK(cudaMemcpyAsync(s->expect_h + j0, s->expect + j0, (size_t)mc * sizeof(double), cudaMemcpyDeviceToHost, s->side));
+        CK(cudaEventRecord(s->chunk_done[ch], s->side));
     }
-    CK(cudaEventRecord(s->dev_end, st));
+    CK(cudaEventRecord(s->dev_end, s->side));
     const double t1 = now_ms();
     if (s->method == DQAOA_RANDOM) {   // overlaps the device work of this cycle
         s->next_idx.resize((size_t)m * k);
@@ -1223,6 +1243,7 @@ extern "C" void dqaoa_session_destroy(dqaoa_session* s) {
     for (int ch = 0; ch < 2; ++ch) {
         qaoa_plan_destroy(s->plans[ch]);
         if (s->chunk_done[ch]) cudaEventDestroy(s->chunk_done[ch]);
+        if (s->chunk_solved[ch]) cudaEventDestroy(s->chunk_solved[ch]);
     }
     if (s->dev_begin) cudaEventDestroy(s->dev_begin);
     if (s->dev_end) cudaEventDestroy(s->dev_end);
