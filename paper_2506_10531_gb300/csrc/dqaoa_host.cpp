@@ -136,23 +136,26 @@ int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, 
         energy = cache->energy;
         tau = cache->tau;
     } else {
-        double absq = 0.0;
-        for (int64_t t = 0; t < (int64_t)N * N; ++t) absq += std::fabs(Q[t]);
+        // tau only scales the acceptance threshold: eight partial sums (vectorisable)
+        const int64_t NN = (int64_t)N * N;
+        double part[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int64_t t = 0;
+        for (; t + 8 <= NN; t += 8)
+            for (int u = 0; u < 8; ++u) part[u] += std::fabs(Q[t + u]);
+        double absq = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+        for (; t < NN; ++t) absq += std::fabs(Q[t]);
         tau = 1e-12 * absq;
+        // h = Qx: the rows of the set variables added in ascending order (symmetric Q: column l
+        // = row l), whole rows at a time; then E(x) = sum_i x_i h_i
         h.assign(N, 0.0);
+        double* hp = h.data();
         for (int i = 0; i < N; ++i) {
             if (!x[i]) continue;
             const double* row = Q + (int64_t)i * N;
-            for (int l = 0; l < N; ++l)
-                if (x[l]) energy += row[l];
+            for (int l = 0; l < N; ++l) hp[l] += row[l];
         }
-        for (int l = 0; l < N; ++l) {
-            const double* row = Q + (int64_t)l * N;
-            double s = 0.0;
-            for (int i = 0; i < N; ++i)
-                if (x[i]) s += row[i];
-            h[l] = s;
-        }
+        for (int i = 0; i < N; ++i)
+            if (x[i]) energy += hp[i];
     }
     int accepted = 0;
     int nz[64];
