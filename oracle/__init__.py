@@ -167,7 +167,7 @@ def impact(Q, x):
     return out
 
 
-RANDOM, IFD = 0, 1
+RANDOM, IFD, BFS, PFS = 0, 1, 2, 3
 
 
 def decompose(Q, x, m, k, seed, cycle=0, method=RANDOM, conditioned=True):

@@ -296,6 +296,86 @@ static void impact_ranking(const double* Q, int N, const uint8_t* x, int32_t* or
     free(dE);
 }
 
+/* Strong interactions (Section V-A, BFS/PFS; the paper leaves "strongly interacted" open). Read
+ * here as: j is a strong neighbour of i when j != i, Q_ij != 0 and |Q_ij| is at least the d-th
+ * largest off-diagonal magnitude of row i, d = min(k - 1, nonzeros of the row off the diagonal);
+ * ties at the threshold are all strong (every edge of an unweighted graph is strong). thr[i] is
+ * that threshold, or +inf for a row without off-diagonal nonzeros. */
+static void strong_thresholds(const double* Q, int N, int k, double* thr)
+{
+    double* mag = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int i = 0; i < N; ++i) {
+        int nz = 0;
+        for (int j = 0; j < N; ++j)
+            if (j != i && Q[(int64_t)i * N + j] != 0.0) mag[nz++] = fabs(Q[(int64_t)i * N + j]);
+        const int d = (k - 1 < nz) ? k - 1 : nz;
+        if (d < 1) { thr[i] = INFINITY; continue; }
+        /* selection by repeated maximum: the d-th largest value */
+        double t = INFINITY;
+        for (int r = 0; r < d; ++r) {
+            int best = -1;
+            for (int a = 0; a < nz; ++a)
+                if (mag[a] <= t && (best < 0 || mag[a] > mag[best])) best = a;
+            /* remove one copy of the maximum so that equal values count once each */
+            t = mag[best];
+            mag[best] = -1.0;
+        }
+        thr[i] = t;
+    }
+    free(mag);
+}
+
+static int strong(const double* Q, int N, const double* thr, int i, int j)
+{
+    const double q = Q[(int64_t)i * N + j];
+    return j != i && q != 0.0 && fabs(q) >= thr[i];
+}
+
+/* Sub-QUBO j of the graph traversals (Section V-A, BFS / PFS), rooted at rank[j] (the j-th
+ * variable by impact, as Algorithm 1's windows start at rank[j]):
+ *   BFS: a FIFO queue; the front variable's strong neighbours join in ascending index order;
+ *   PFS: the next variable is the unselected one of highest impact (rank order) among the
+ *        strong neighbours of the selected variables.
+ * When the traversal runs out before k variables, it restarts from the best-ranked unselected
+ * variable. S receives the k variables in selection order. */
+static void traverse(const double* Q, int N, const double* thr, const int32_t* rank, int method,
+                     int j, int k, int32_t* S, uint8_t* inS, uint8_t* inF, int32_t* queue)
+{
+    memset(inS, 0, (size_t)N);
+    memset(inF, 0, (size_t)N);
+    int size = 0, head = 0, tail = 0;
+    int32_t next = rank[j];
+    while (size < k) {
+        if (next < 0) {
+            /* restart: best-ranked unselected variable */
+            for (int t = 0; t < N; ++t)
+                if (!inS[rank[t]]) { next = rank[t]; break; }
+        }
+        const int32_t v = next;
+        next = -1;
+        S[size++] = v;
+        inS[v] = 1;
+        if (method == 2) {
+            queue[tail++] = v;
+            /* expand queued variables until one neighbour is found or the queue empties */
+            while (size < k && head < tail) {
+                const int32_t w = queue[head++];
+                for (int u = 0; u < N && size < k; ++u)
+                    if (!inS[u] && strong(Q, N, thr, w, u)) {
+                        S[size++] = u;
+                        inS[u] = 1;
+                        queue[tail++] = u;
+                    }
+            }
+        } else {
+            for (int u = 0; u < N; ++u)
+                if (strong(Q, N, thr, v, u)) inF[u] = 1;
+            for (int t = 0; t < N; ++t)
+                if (inF[rank[t]] && !inS[rank[t]]) { next = rank[t]; break; }
+        }
+    }
+}
+
 /*
  * Decompose the N-variable QUBO into m sub-QUBOs of k variables.
  *   method 0 (random, Section V-A): sub-QUBO j draws k distinct variables uniformly without
@@ -303,6 +383,7 @@ static void impact_ranking(const double* Q, int N, const uint8_t* x, int32_t* or
  *     Fisher-Yates shuffle of 0..N-1 (swap position i with i + draw(N - i)), then sorts them.
  *   method 1 (IFD, Algorithm 1): variables ranked by impact; sub-QUBO j takes the window
  *     ranking[j .. j+k-1] and sorts it (requires m + k - 1 <= N).
+ *   methods 2 (BFS) and 3 (PFS): the traversals above from rank[j], sorted (requires m <= N).
  * Qsub[j] = Q[S_j, S_j] as a full symmetric k x k matrix. With conditioned != 0 the couplings to
  * the fixed variables outside S_j are folded into the diagonal:
  *   Qsub[a][a] += 2 sum_{l not in S_j} Q[S_a][l] x_l,
@@ -316,11 +397,20 @@ int orc_decompose(const double* Q, int N, const uint8_t* x, int method, int cond
     if (!Q || N < 1 || m < 1 || k < 1 || k > N || !idx || !Qsub) return ORC_EINVAL;
     if ((conditioned || method == 1) && !x) return ORC_EINVAL;
     if (method == 1 && m + k - 1 > N) return ORC_EINVAL;
-    if (method != 0 && method != 1) return ORC_EINVAL;
+    if ((method == 2 || method == 3) && m > N) return ORC_EINVAL;
+    if (method < 0 || method > 3) return ORC_EINVAL;
+    if (method >= 1 && !x) return ORC_EINVAL;
     int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
     uint8_t* inS = (uint8_t*)malloc((size_t)N);
-    if (!perm || !inS) { free(perm); free(inS); return ORC_ENOMEM; }
-    if (method == 1) impact_ranking(Q, N, x, perm);
+    uint8_t* inF = (uint8_t*)malloc((size_t)N);
+    int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    double* thr = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!perm || !inS || !inF || !queue || !thr) {
+        free(perm); free(inS); free(inF); free(queue); free(thr);
+        return ORC_ENOMEM;
+    }
+    if (method >= 1) impact_ranking(Q, N, x, perm);
+    if (method >= 2) strong_thresholds(Q, N, k, thr);
     for (int j = 0; j < m; ++j) {
         int32_t* S = idx + (int64_t)j * k;
         if (method == 0) {
@@ -333,8 +423,10 @@ int orc_decompose(const double* Q, int N, const uint8_t* x, int method, int cond
                 perm[i + r] = t;
             }
             memcpy(S, perm, sizeof(int32_t) * (size_t)k);
-        } else {
+        } else if (method == 1) {
             memcpy(S, perm + j, sizeof(int32_t) * (size_t)k);
+        } else {
+            traverse(Q, N, thr, perm, method, j, k, S, inS, inF, queue);
         }
         qsort(S, (size_t)k, sizeof(int32_t), cmp_i32);
         double* Qs = Qsub + (int64_t)j * k * k;
@@ -357,6 +449,9 @@ int orc_decompose(const double* Q, int N, const uint8_t* x, int method, int cond
     }
     free(perm);
     free(inS);
+    free(inF);
+    free(queue);
+    free(thr);
     return ORC_OK;
 }
 

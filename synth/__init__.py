@@ -93,6 +93,34 @@ def maxcut_form_q(n: int, seed: int, edge_prob: float = 0.5) -> np.ndarray:
     return a
 
 
+def maxcut_graph_q(n: int, seed: int, edges: int | None = None) -> np.ndarray:
+    """Max-Cut QUBO of an unweighted random graph with exactly ``edges`` edges (default
+    n(n-1)/8, the edge count of the paper's Max-Cut study, Section VI).
+
+    The edge set is the ``edges`` vertex pairs (i < j, row-major order) with the smallest
+    SplitMix64 keys of stream ``seed``: a uniform subset of that size. The QUBO is
+    Q_ij = Q_ji = 1 for every edge and Q_ii = -deg(i), so that x^T Q x = -cut(x).
+    """
+    if edges is None:
+        edges = n * (n - 1) // 8
+    iu, ju = np.triu_indices(n, 1)
+    keys = splitmix64(seed, iu.size)
+    pick = np.argsort(keys, kind="stable")[:edges]
+    q = np.zeros((n, n))
+    q[iu[pick], ju[pick]] = 1.0
+    q = q + q.T
+    np.fill_diagonal(q, -q.sum(axis=1))
+    return q
+
+
+def cut_value(Q: np.ndarray, x: np.ndarray) -> float:
+    """Cut size of the bit vector x on the graph of a ``maxcut_graph_q`` matrix (its off-diagonal
+    ones), counted edge by edge."""
+    a = np.triu(Q, 1) != 0
+    xb = np.asarray(x).astype(bool)
+    return float(np.sum(a & (xb[:, None] != xb[None, :])))
+
+
 # ---------------------------------------------------------------------------------------------
 # Workload recipes (sizes and seeds of the measured configurations)
 # ---------------------------------------------------------------------------------------------

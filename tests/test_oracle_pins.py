@@ -345,6 +345,92 @@ def test_ifd_windows_follow_impact_ranking(orc):
         np.testing.assert_array_equal(qs[j], Q[np.ix_(idx[j], idx[j])])
 
 
+def _figure_case():
+    import json
+    with open(os.path.join(HERE, "golden", "bfs_pfs_figure.json")) as f:
+        g = json.load(f)
+    Q = np.diag(np.array(g["diag"]))
+    for a, b in g["strong_pairs"]:
+        Q[a, b] = Q[b, a] = g["coupling"]
+    return g, Q
+
+
+def test_bfs_pfs_paper_figure(orc):
+    # Fig. bfs-pfs: BFS reaches x2 first, PFS x4 (higher impact); the fixture's index sets are
+    # derived by hand from the traversal rules
+    g, Q = _figure_case()
+    x = np.zeros(Q.shape[0], dtype=np.uint8)
+    assert sorted(range(7), key=lambda i: (-abs(orc.impact(Q, x)[i]), i)) == g["impact_rank"]
+    for c in g["cases"]:
+        for name, method in (("bfs", orc.BFS), ("pfs", orc.PFS)):
+            idx, qs = orc.decompose(Q, x, c["j"] + 1, c["k"], seed=0, method=method, conditioned=False)
+            assert idx[c["j"]].tolist() == c[name], (c, name)
+            np.testing.assert_array_equal(qs[c["j"]], Q[np.ix_(idx[c["j"]], idx[c["j"]])])
+
+
+def _strong_sets(Q, k):
+    # strong neighbours by the reading: |Q_ij| >= the d-th largest off-diagonal magnitude of row i
+    N = Q.shape[0]
+    out = []
+    for i in range(N):
+        mags = sorted((abs(Q[i, j]) for j in range(N) if j != i and Q[i, j] != 0.0), reverse=True)
+        d = min(k - 1, len(mags))
+        thr = mags[d - 1] if d >= 1 else float("inf")
+        out.append([j for j in range(N) if j != i and Q[i, j] != 0.0 and abs(Q[i, j]) >= thr])
+    return out
+
+
+def _traverse_py(strong, rank, root, k, bfs):
+    # the traversals written out directly over Python lists (BFS: deque of discovered variables;
+    # PFS: frontier set, best by rank position)
+    from collections import deque
+    pos = {v: t for t, v in enumerate(rank)}
+    sel, order = set(), []
+    frontier = set()
+    nxt = root
+    q = deque()
+    while len(order) < k:
+        if nxt is None:
+            nxt = next(v for v in rank if v not in sel)
+        v, nxt = nxt, None
+        sel.add(v)
+        order.append(v)
+        if bfs:
+            q.append(v)
+            while len(order) < k and q:
+                w = q.popleft()
+                for u in strong[w]:
+                    if len(order) < k and u not in sel:
+                        sel.add(u)
+                        order.append(u)
+                        q.append(u)
+        else:
+            frontier.update(strong[v])
+            cand = [u for u in frontier if u not in sel]
+            nxt = min(cand, key=lambda u: pos[u]) if cand else None
+    return sorted(order)
+
+
+@pytest.mark.parametrize("kind", ["dense", "maxcut", "sparse"])
+@pytest.mark.parametrize("k", [2, 4, 7])
+def test_bfs_pfs_against_direct_traversal(orc, kind, k):
+    N = 30
+    if kind == "dense":
+        Q = synth.symmetric_q(N, seed=71)
+    elif kind == "maxcut":
+        Q = synth.maxcut_graph_q(N, seed=72, edges=40)        # unit weights: ties everywhere
+    else:
+        Q = synth.maxcut_graph_q(N, seed=73, edges=12)        # isolated vertices force restarts
+    x = synth.bits(74, N)
+    dE = orc.impact(Q, x)
+    rank = sorted(range(N), key=lambda i: (-abs(dE[i]), i))
+    strong = _strong_sets(Q, k)
+    for method, bfs in ((orc.BFS, True), (orc.PFS, False)):
+        idx, _ = orc.decompose(Q, x, N, k, seed=0, method=method, conditioned=False)
+        for j in range(N):
+            assert idx[j].tolist() == _traverse_py(strong, rank, rank[j], k, bfs), (kind, k, j, bfs)
+
+
 def test_merge_single_subqubo_takes_best(orc):
     # N = k: every candidate fixes the whole solution, so sequential "accept if lower" ends at
     # the minimum of the starting energy and all candidate energies
