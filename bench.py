@@ -841,7 +841,131 @@ def run_serving(args):
     return line
 
 
-CONFIGS = {"large": run_large, "plain10": run_plain10, "uneven": run_uneven, "serving": run_serving}
+MAXCUT = dict(seed=6, N=1000, m=500, k=12, p=3, topk=8, gamma=(0.2, 0.4, 0.6), beta=(0.6, 0.4, 0.2),
+              max_cycles=60, patience=5)
+MAXCUT_METHODS = ("random", "ifd", "bfs", "pfs")
+
+
+def maxcut_cpu_baseline():
+    """The oracle on whole PFS cycles of the Max-Cut workload until at least 10 s of CPU work."""
+    import oracle
+    oracle.build()
+    c = MAXCUT
+    Q = synth.maxcut_graph_q(c["N"], seed=c["seed"])
+    x = synth.bits(c["seed"] + 1, c["N"])
+    solved, cycles = 0, 0
+    t0 = time.perf_counter()
+    while cycles < 16 and (time.perf_counter() - t0) < 10.0:
+        idx, qs = oracle.decompose(Q, x, c["m"], c["k"], c["seed"], cycles, method=oracle.PFS)
+        cand = np.zeros((c["m"], c["topk"]), dtype=np.uint64)
+        for j in range(c["m"]):
+            Qs = qs[j].astype(np.float32).astype(np.float64)
+            E = oracle.energies(Qs)
+            psi = oracle.state(c["k"], c["gamma"], c["beta"], E)
+            oracle.expect(psi, E)
+            cand[j], _ = oracle.topk(psi, c["topk"])
+        x, _, _ = oracle.merge(Q, x, idx, cand)
+        solved += c["m"]
+        cycles += 1
+    dt = time.perf_counter() - t0
+    return {"value": solved / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{cycles} full PFS cycle(s) of {c['m']} sub-QUBOs of n={c['k']} (decompose, "
+                      f"energies, state, <C>, top-8, merge) in FP64, {dt:.1f} s"}
+
+
+def run_maxcut(args):
+    """DQAOA cycles on the synthetic Max-Cut workload with each decomposition method (random,
+    IFD, BFS, PFS; Section V-A and the Max-Cut study of Section VI): throughput per cycle with
+    CUDA events, and per method the cut reached and the cycles until the stopping rule holds."""
+    import torch
+    import paper_2506_10531_gb300 as q
+    from paper_2506_10531_gb300 import build as qbuild
+    from paper_2506_10531_gb300 import dqaoa
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    qbuild.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    c = MAXCUT
+    N, m, k, p, K = c["N"], c["m"], c["k"], c["p"], c["topk"]
+    seed = replica_seed(c["seed"], rank)
+    Q = synth.maxcut_graph_q(N, seed=seed)
+    Qh = torch.from_numpy(Q).pin_memory().numpy()
+    x0 = synth.bits(seed + 1, N)
+    ctx = q.qaoa_create(local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    codes = {"random": q.DQAOA_RANDOM, "ifd": q.DQAOA_IFD, "bfs": q.DQAOA_BFS, "pfs": q.DQAOA_PFS}
+    per, kern, all_ms, launches = {}, {}, [], 0
+    e2e_s, e2e_cycles = 0.0, 0
+    roof = None
+    with Clocks(local) as clk:
+        for name in MAXCUT_METHODS:
+            sess = q.dqaoa_session_create(ctx, N, m, k, p, K, codes[name], True, c["gamma"], c["beta"])
+            plans = q.dqaoa_session_plans(sess)
+            x = x0.copy()
+            q.dqaoa_session_cycle(sess, Qh, 1, x, seed, 0, stream)
+            for w in range(args.warmup):
+                q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 1 + w, stream)
+            for pl in plans:
+                q.qaoa_plan_set_timing(pl, True)
+            mk = {}
+
+            def body(s):
+                q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 100 + s, stream)
+                for pl in plans:
+                    _plan_kern_times(q, pl, mk)
+            step_ms = _timed_steps(stream, args.steps, body, flush=lambda: flush.fill_(1))
+            for pl in plans:
+                q.qaoa_plan_set_timing(pl, False)
+            if name == "pfs":
+                roof = plan_roofline(q, plans, mk, lambda: q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream),
+                                     clk, dev, alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p) / len(plans),
+                                     workload="maxcut")
+            for nm, v in mk.items():
+                kern.setdefault(nm, []).extend(v)
+            launches += args.steps * (sum(q.qaoa_plan_kernel_count(pl) for pl in plans) + 1)
+            # e2e: Q from pinned host memory every cycle (the session rebuilds what depends on Q)
+            xe = x0.copy()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s in range(args.steps):
+                q.dqaoa_session_cycle(sess, Qh, 1, xe, seed, 600 + s, stream)
+            torch.cuda.synchronize()
+            e2e_s += time.perf_counter() - t0
+            e2e_cycles += args.steps
+            q.dqaoa_session_destroy(sess)
+            # solution quality: cycles from x0 until the energy stops decreasing (patience cycles)
+            r = dqaoa.solve(ctx, Q, m, k, p, K, c["gamma"], c["beta"], x0, seed=seed, method=codes[name],
+                            max_cycles=c["max_cycles"], patience=c["patience"], stream=stream)
+            per[name] = {"ms_per_cycle": float(np.mean(step_ms)),
+                         "solves_per_s": m * args.steps / (sum(step_ms) / 1e3),
+                         "cut_x0": synth.cut_value(Q, x0), "cut": synth.cut_value(Q, r.x),
+                         "cycles": r.cycles, "converged": r.converged, "tts_s": r.tts_s, "wall_s": r.wall_s,
+                         "host_phases_ms": {key: float(np.mean([t[key] for t in r.timing])) for key in r.timing[0]}}
+            all_ms += step_ms
+    q.qaoa_destroy(ctx)
+    tot_s = max_over_ranks(sum(all_ms) / 1e3, dev)
+    cycles = len(MAXCUT_METHODS) * args.steps
+    line = _line(f"sub-QUBO solves/s (DQAOA cycles on synthetic Max-Cut, random / IFD / BFS / PFS decompositions)",
+                 m * cycles * world / tot_s, UNIT, args, world, 1e3 * tot_s / cycles, "c64/f32 state, f64 reductions and merge",
+                 {"workload": f"DQAOA on synthetic Max-Cut: unweighted graph of N={N} vertices with N(N-1)/8 edges "
+                              f"(seed {c['seed']}), m={m} conditioned sub-QUBOs of n={k}, p={p} fixed parameters, "
+                              f"complex64, top-{K} merged; {args.steps} timed cycles per decomposition method",
+                  "N": N, "sub_qubos": m, "n": k, "p": p, "topk": K, "methods": list(MAXCUT_METHODS),
+                  "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
+                 latency_ms={"p50": float(np.percentile(all_ms, 50)), "p99": float(np.percentile(all_ms, 99))},
+                 per_method=per,
+                 kernel_ms_per_step={nm: sum(v) / cycles for nm, v in kern.items()},
+                 roofline=roof,
+                 e2e={"value": m * e2e_cycles * world / max_over_ranks(e2e_s, dev), "unit": UNIT,
+                      "h2d_bytes_per_step": N * N * 8 + N + m * k * 4, "d2h_bytes_per_step": m * K * 8 + m * 8},
+                 gpu_launches=launches, clocks=clk.summary())
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = maxcut_cpu_baseline()
+    return line
+
+
+CONFIGS = {"large": run_large, "maxcut": run_maxcut, "plain10": run_plain10, "uneven": run_uneven, "serving": run_serving}
 
 
 def main():

@@ -253,7 +253,7 @@ qaoa_status qaoa_plain_solve(qaoa_ctx* ctx, int n, int p, const float* Q, const 
 /* DQAOA decomposition and aggregation (host, FP64)                                          */
 /* ---------------------------------------------------------------------------------------- */
 
-enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1 };
+enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1, DQAOA_BFS = 2, DQAOA_PFS = 3 };
 
 /* Section V-A. Sub-QUBO index sets: idx[m*k] (host int32), each row sorted ascending.
  *   DQAOA_RANDOM: row j draws k distinct variables of 0..N-1 uniformly without replacement,
@@ -262,6 +262,13 @@ enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1 };
  *   DQAOA_IFD (Algorithm 1): variables ranked by |impact| descending (ties: smaller index),
  *     impact_i = (1 - 2 x_i)(Q_ii + 2 sum_{j != i} Q_ij x_j), the energy change of flipping x_i;
  *     row j is the window ranking[j .. j+k-1] (needs m + k - 1 <= N; Q and x required).
+ *   DQAOA_BFS, DQAOA_PFS (the graph traversals of Section V-A): j is a strong neighbour of i
+ *     when j != i, Q_ij != 0 and |Q_ij| >= the d-th largest off-diagonal |Q_i.|, d = min(k - 1,
+ *     nonzeros of row i off the diagonal), ties included. Row j starts at ranking[j] (the IFD
+ *     ranking). BFS: FIFO queue, the front's strong neighbours join in ascending index order.
+ *     PFS: the next variable is the best-ranked unselected strong neighbour of any selected one.
+ *     A traversal that runs out restarts at the best-ranked unselected variable. Needs m <= N;
+ *     Q and x required.
  * Q: N*N row-major symmetric doubles (host), x: N bytes 0/1 (host; RANDOM may pass NULL). */
 qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t* x, int method, int m,
                                int k, uint64_t seed, uint64_t cycle, int32_t* idx);
@@ -301,7 +308,8 @@ qaoa_status dqaoa_merge(const double* Q, int N, uint8_t* x, int m, int k, const 
 typedef struct dqaoa_session dqaoa_session;
 
 /* gamma, beta: p host doubles (the fixed parameters every sub-QUBO uses); K: top-k candidates
- * per sub-QUBO fed to the merge (1..16); method: DQAOA_RANDOM or DQAOA_IFD. Allocates. */
+ * per sub-QUBO fed to the merge (1..16); method: one of DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS,
+ * DQAOA_PFS. Allocates. */
 qaoa_status dqaoa_session_create(qaoa_ctx* ctx, int N, int m, int k, int p, int K, int method,
                                  int conditioned, const double* gamma, const double* beta,
                                  dqaoa_session** out);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libqaoa.so")
 QAOA_OK, QAOA_E_INVALID, QAOA_E_NOMEM, QAOA_E_CUDA, QAOA_E_TIMEOUT, QAOA_E_UNSUPPORTED = range(6)
 QAOA_INST_GRAD = 1
 QAOA_TIER_AUTO, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM = 0, 2, 3
-DQAOA_RANDOM, DQAOA_IFD = 0, 1
+DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS, DQAOA_PFS = 0, 1, 2, 3
 
 # Every symbol include/qaoa.h declares.
 EXPORTS = [

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "qaoa_host.h"
@@ -73,9 +74,9 @@ int draw_random(int N, int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx
     return 0;
 }
 
-// Impact factor of each variable (the energy change of flipping it) and the IFD ranking:
-// |impact| descending, ties to the smaller index; row j is the window ranking[j .. j+k-1].
-int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx) {
+// Impact factor of each variable (the energy change of flipping it) and the ranking by
+// |impact| descending, ties to the smaller index.
+static std::vector<int32_t> impact_order(const double* Q, int N, const uint8_t* x) {
     std::vector<double> imp(N);
     for (int i = 0; i < N; ++i) {
         const double* row = Q + (int64_t)i * N;
@@ -88,9 +89,96 @@ int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* id
     for (int i = 0; i < N; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t a, int32_t b) { return std::fabs(imp[a]) > std::fabs(imp[b]); });
+    return order;
+}
+
+// IFD (Algorithm 1): row j is the window ranking[j .. j+k-1].
+int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx) {
+    const std::vector<int32_t> order = impact_order(Q, N, x);
     for (int j = 0; j < m; ++j) {
         int32_t* S = idx + (int64_t)j * k;
         std::copy(order.begin() + j, order.begin() + j + k, S);
+        std::sort(S, S + k);
+    }
+    return 0;
+}
+
+// BFS / PFS traversals (Section V-A). Strong neighbours of i: j != i with Q_ij != 0 and |Q_ij| at
+// least the d-th largest off-diagonal magnitude of row i, d = min(k - 1, off-diagonal nonzeros),
+// ties included; kept as ascending lists in CSR form (they depend on Q and k only).
+void build_strong_graph(const double* Q, int N, int k, StrongGraph* g) {
+    g->N = N;
+    g->k = k;
+    g->off.assign((size_t)N + 1, 0);
+    g->nbr.clear();
+    std::vector<double> mag;
+    for (int i = 0; i < N; ++i) {
+        const double* row = Q + (int64_t)i * N;
+        mag.clear();
+        for (int j = 0; j < N; ++j)
+            if (j != i && row[j] != 0.0) mag.push_back(std::fabs(row[j]));
+        const int d = std::min<int>(k - 1, (int)mag.size());
+        if (d >= 1) {
+            std::nth_element(mag.begin(), mag.begin() + (d - 1), mag.end(), std::greater<double>());
+            const double thr = mag[d - 1];
+            for (int j = 0; j < N; ++j)
+                if (j != i && row[j] != 0.0 && std::fabs(row[j]) >= thr) g->nbr.push_back(j);
+        }
+        g->off[i + 1] = (int64_t)g->nbr.size();
+    }
+}
+
+// Row j starts at ranking[j]; BFS takes the strong neighbours of the queue's front in ascending
+// index order, PFS the best-ranked unselected strong neighbour of any selected variable; an
+// exhausted traversal restarts at the best-ranked unselected variable. g: the strong graph of
+// (Q, k), built here when null.
+int draw_graph(const double* Q, int N, const uint8_t* x, int method, int m, int k, int32_t* idx,
+               const StrongGraph* g) {
+    StrongGraph local;
+    if (!g) {
+        build_strong_graph(Q, N, k, &local);
+        g = &local;
+    }
+    const std::vector<int32_t> order = impact_order(Q, N, x);
+    const int64_t* off = g->off.data();
+    const int32_t* nbr = g->nbr.data();
+    std::vector<uint8_t> inS(N), inF(N);
+    std::vector<int32_t> queue(N);
+    for (int j = 0; j < m; ++j) {
+        int32_t* S = idx + (int64_t)j * k;
+        int size = 0, head = 0, tail = 0, scan = 0;   // scan: restart cursor into the ranking
+        int32_t next = order[j];
+        while (size < k) {
+            if (next < 0) {
+                while (inS[order[scan]]) ++scan;
+                next = order[scan];
+            }
+            const int32_t v = next;
+            next = -1;
+            S[size++] = v;
+            inS[v] = 1;
+            if (method == 2) {          // BFS
+                queue[tail++] = v;
+                while (size < k && head < tail) {
+                    const int32_t w = queue[head++];
+                    for (int64_t e = off[w]; e < off[w + 1] && size < k; ++e) {
+                        const int32_t u = nbr[e];
+                        if (!inS[u]) { S[size++] = u; inS[u] = 1; queue[tail++] = u; }
+                    }
+                }
+            } else {                    // PFS: first frontier variable in ranking order
+                for (int64_t e = off[v]; e < off[v + 1]; ++e) inF[nbr[e]] = 1;
+                for (int t = 0; t < N; ++t) {
+                    const int32_t u = order[t];
+                    if (inF[u] && !inS[u]) { next = u; break; }
+                }
+            }
+        }
+        // clear the marks of this row only
+        for (int a = 0; a < k; ++a) inS[S[a]] = 0;
+        if (method != 2)
+            for (int a = 0; a < k; ++a)
+                for (int64_t e = off[S[a]]; e < off[S[a] + 1]; ++e) inF[nbr[e]] = 0;
         std::sort(S, S + k);
     }
     return 0;

@@ -967,6 +967,12 @@ extern "C" qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t*
         draw_ifd(Q, N, x, m, k, idx);
         return QAOA_OK;
     }
+    if (method == DQAOA_BFS || method == DQAOA_PFS) {
+        if (!Q || !x) return fail(QAOA_E_INVALID, "BFS / PFS need Q and x");
+        if (m > N) return fail(QAOA_E_INVALID, "BFS / PFS need m <= N");
+        draw_graph(Q, N, x, method, m, k, idx);
+        return QAOA_OK;
+    }
     return fail(QAOA_E_INVALID, "unknown decomposition method %d", method);
 }
 
@@ -1036,6 +1042,8 @@ struct dqaoa_session {
     cudaEvent_t sub_done = nullptr, qblk_done = nullptr;
     double t_decompose = 0.0, t_merge = 0.0, t_cycle = 0.0; // host ms of the last cycle
     MergeCache cache;             // h = Qx and E(x) after the last merge
+    StrongGraph graph;            // BFS / PFS strong-interaction graph of the current Q
+    bool graph_valid = false;
     std::vector<uint8_t> x_last;  // the solution the cache belongs to
     // random index sets of the next cycle, drawn on the host while the device works
     std::vector<int32_t> next_idx;
@@ -1047,9 +1055,10 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
                                             int conditioned, const double* gamma, const double* beta,
                                             dqaoa_session** out) {
     if (!c || !out || N < 1 || m < 1 || k < 1 || k > N || k > NMAX || p < 1 || p > PMAX || K < 1 ||
-        K > KMAX || (uint64_t)K > (1ull << k) || !gamma || !beta || (method != DQAOA_RANDOM && method != DQAOA_IFD))
+        K > KMAX || (uint64_t)K > (1ull << k) || !gamma || !beta || method < DQAOA_RANDOM || method > DQAOA_PFS)
         return fail(QAOA_E_INVALID, "session_create: bad arguments");
     if (method == DQAOA_IFD && m + k - 1 > N) return fail(QAOA_E_INVALID, "IFD needs m + k - 1 <= N");
+    if ((method == DQAOA_BFS || method == DQAOA_PFS) && m > N) return fail(QAOA_E_INVALID, "BFS / PFS need m <= N");
     *out = nullptr;
     CK(cudaSetDevice(c->device));
     dqaoa_session* s = new dqaoa_session();
@@ -1154,7 +1163,13 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     qaoa_status r = QAOA_OK;
     if (s->method == DQAOA_RANDOM && s->next_valid && s->next_seed == seed && s->next_cycle == cycle)
         std::memcpy(s->idx_h, s->next_idx.data(), (size_t)m * k * sizeof(int32_t));
-    else
+    else if (s->method == DQAOA_BFS || s->method == DQAOA_PFS) {
+        if (q_changed || !s->graph_valid) {
+            build_strong_graph(Q, N, k, &s->graph);
+            s->graph_valid = true;
+        }
+        draw_graph(Q, N, x, s->method, m, k, s->idx_h, &s->graph);
+    } else
         r = dqaoa_draw_indices(Q, N, x, s->method, m, k, seed, cycle, s->idx_h);
     s->next_valid = false;
     if (r) return r;

@@ -44,6 +44,23 @@ def test_ifd_decompose_bit_exact(orc):
     np.testing.assert_array_equal(q_l, q_o)
 
 
+@pytest.mark.parametrize("kind,N,m,k", [("maxcut", 400, 200, 12), ("dense", 300, 300, 20),
+                                         ("sparse", 120, 120, 12), ("maxcut", 60, 60, 2)])
+def test_bfs_pfs_decompose_bit_exact(orc, kind, N, m, k):
+    if kind == "maxcut":
+        Q = synth.maxcut_graph_q(N, seed=21)
+    elif kind == "sparse":
+        Q = synth.maxcut_graph_q(N, seed=22, edges=N // 2)     # many components: restarts
+    else:
+        Q = synth.symmetric_q(N, seed=23)
+    x = synth.bits(24, N)
+    for lm, om in ((q.DQAOA_BFS, orc.BFS), (q.DQAOA_PFS, orc.PFS)):
+        i_l, q_l = lib_decompose(Q, x, m, k, 0, 0, lm, True)
+        i_o, q_o = orc.decompose(Q, x, m, k, 0, 0, method=om, conditioned=True)
+        np.testing.assert_array_equal(i_l, i_o)
+        np.testing.assert_array_equal(q_l, q_o)
+
+
 def test_draw_indices_matches_decompose(orc):
     N, m, k = 1000, 64, 16
     idx = np.zeros((m, k), dtype=np.int32)
@@ -74,6 +91,14 @@ def test_host_argument_errors():
     assert e.value.status == q.QAOA_E_INVALID
     with pytest.raises(q.QaoaError):
         q.dqaoa_draw_indices(None, 10, None, q.DQAOA_IFD, 4, 3, 0, 0, np.zeros(12, np.int32))
+    Qz, xz = np.zeros((10, 10)), np.zeros(10, np.uint8)
+    for meth in (q.DQAOA_BFS, q.DQAOA_PFS):
+        with pytest.raises(q.QaoaError):          # m > N
+            q.dqaoa_draw_indices(Qz, 10, xz, meth, 11, 3, 0, 0, np.zeros(33, np.int32))
+        with pytest.raises(q.QaoaError):          # needs Q and x
+            q.dqaoa_draw_indices(None, 10, None, meth, 4, 3, 0, 0, np.zeros(12, np.int32))
+    with pytest.raises(q.QaoaError):
+        q.dqaoa_draw_indices(Qz, 10, xz, 4, 4, 3, 0, 0, np.zeros(12, np.int32))
     idx = np.array([[0, 12]], dtype=np.int32)
     with pytest.raises(q.QaoaError):
         q.dqaoa_merge(np.zeros((10, 10)), 10, np.zeros(10, np.uint8), 1, 2, idx, 1,

@@ -104,3 +104,34 @@ def test_driver_cycles_to_convergence(q, orc):
     # deterministic: the second run follows the same trajectory
     assert r2.energies == r.energies[:len(r2.energies)]
     assert r2.converged and r2.cycles <= r.cycles
+
+
+@pytest.mark.parametrize("method", ["bfs", "pfs", "ifd"])
+def test_session_graph_decompositions_on_maxcut(q, orc, method):
+    # the synthetic Max-Cut workload (n(n-1)/8 unit edges) decomposed by the graph traversals:
+    # a cycle's index sets come from the session's own draw, so the oracle's decomposition of the
+    # same x and its merge of the session's candidates must reproduce the merged x bit for bit
+    N, m, k, p, K = 300, 150, 12, 3, 8
+    Q = synth.maxcut_graph_q(N, seed=31)
+    x0 = synth.bits(32, N)
+    lm = {"bfs": q.DQAOA_BFS, "pfs": q.DQAOA_PFS, "ifd": q.DQAOA_IFD}[method]
+    om = {"bfs": orc.BFS, "pfs": orc.PFS, "ifd": orc.IFD}[method]
+    mm = m
+    ctx = q.qaoa_create(0)
+    try:
+        s = q.dqaoa_session_create(ctx, N, mm, k, p, K, lm, True, (0.2, 0.4, 0.6), (0.6, 0.4, 0.2))
+        x = x0.copy()
+        xs = [x0.copy()]
+        for c in range(3):
+            e, acc = q.dqaoa_session_cycle(s, Q, 1 if c == 0 else 0, x, 0, c)
+            ex, cand = q.dqaoa_session_results(s, mm, K)
+            idx, _ = orc.decompose(Q, xs[-1], mm, k, 0, c, method=om, conditioned=True)
+            xo, eo, _ = orc.merge(Q, xs[-1], idx, cand)
+            np.testing.assert_array_equal(x, xo)
+            assert e == pytest.approx(eo, abs=1e-9 * np.abs(Q).sum())
+            assert -e == pytest.approx(synth.cut_value(Q, x))          # x^T Q x = -cut(x)
+            xs.append(x.copy())
+        q.dqaoa_session_destroy(s)
+    finally:
+        q.qaoa_destroy(ctx)
+    assert synth.cut_value(Q, xs[-1]) >= synth.cut_value(Q, x0)
