@@ -897,7 +897,7 @@ def run_maxcut(args):
     codes = {"random": q.DQAOA_RANDOM, "ifd": q.DQAOA_IFD, "bfs": q.DQAOA_BFS, "pfs": q.DQAOA_PFS}
     per, kern, all_ms, launches = {}, {}, [], 0
     e2e_s, e2e_cycles = 0.0, 0
-    roof = None
+    roof_args = None
     with Clocks(local) as clk:
         for name in MAXCUT_METHODS:
             sess = q.dqaoa_session_create(ctx, N, m, k, p, K, codes[name], True, c["gamma"], c["beta"])
@@ -917,10 +917,6 @@ def run_maxcut(args):
             step_ms = _timed_steps(stream, args.steps, body, flush=lambda: flush.fill_(1))
             for pl in plans:
                 q.qaoa_plan_set_timing(pl, False)
-            if name == "pfs":
-                roof = plan_roofline(q, plans, mk, lambda: q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream),
-                                     clk, dev, alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p) / len(plans),
-                                     workload="maxcut")
             for nm, v in mk.items():
                 kern.setdefault(nm, []).extend(v)
             launches += args.steps * (sum(q.qaoa_plan_kernel_count(pl) for pl in plans) + 1)
@@ -933,7 +929,10 @@ def run_maxcut(args):
             torch.cuda.synchronize()
             e2e_s += time.perf_counter() - t0
             e2e_cycles += args.steps
-            q.dqaoa_session_destroy(sess)
+            if name == "pfs":
+                roof_args = (sess, plans, mk, x)      # roofline after the clock sampler stops
+            else:
+                q.dqaoa_session_destroy(sess)
             # solution quality: cycles from x0 until the energy stops decreasing (patience cycles)
             r = dqaoa.solve(ctx, Q, m, k, p, K, c["gamma"], c["beta"], x0, seed=seed, method=codes[name],
                             max_cycles=c["max_cycles"], patience=c["patience"], stream=stream)
@@ -943,6 +942,11 @@ def run_maxcut(args):
                          "cycles": r.cycles, "converged": r.converged, "tts_s": r.tts_s, "wall_s": r.wall_s,
                          "host_phases_ms": {key: float(np.mean([t[key] for t in r.timing])) for key in r.timing[0]}}
             all_ms += step_ms
+    sess, plans, mk, x = roof_args
+    roof = plan_roofline(q, plans, mk, lambda: q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream),
+                         clk, dev, alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p) / len(plans),
+                         workload="maxcut")
+    q.dqaoa_session_destroy(sess)
     q.qaoa_destroy(ctx)
     tot_s = max_over_ranks(sum(all_ms) / 1e3, dev)
     cycles = len(MAXCUT_METHODS) * args.steps
