@@ -144,6 +144,17 @@ void build_strong_graph(const double* Q, int N, int k, StrongGraph* g) {
         }
         g->off[i + 1] = (int64_t)g->nbr.size();
     }
+    // dense graphs (at least 32 strong neighbours per row on average, N <= 16384) also get bitset
+    // rows, so that PFS unites frontiers a word at a time instead of marking every neighbour
+    g->words = 0;
+    g->bits.clear();
+    if (N <= 16384 && (int64_t)g->nbr.size() >= 32 * (int64_t)N) {
+        g->words = (N + 63) / 64;
+        g->bits.assign((size_t)N * g->words, 0ull);
+        for (int i = 0; i < N; ++i)
+            for (int64_t e = g->off[i]; e < g->off[i + 1]; ++e)
+                g->bits[(size_t)i * g->words + (g->nbr[e] >> 6)] |= 1ull << (g->nbr[e] & 63);
+    }
 }
 
 // Row j starts at ranking[j]; BFS takes the strong neighbours of the queue's front in ascending
@@ -162,6 +173,8 @@ int draw_graph(const double* Q, int N, const uint8_t* x, int method, int m, int 
     const int32_t* nbr = g->nbr.data();
     std::vector<uint8_t> inS(N), inF(N);
     std::vector<int32_t> queue(N);
+    const int W = (method != 2) ? g->words : 0;
+    std::vector<uint64_t> fbits((size_t)W, 0ull);
     for (int j = 0; j < m; ++j) {
         int32_t* S = idx + (int64_t)j * k;
         int size = 0, head = 0, tail = 0, scan = 0;   // scan: restart cursor into the ranking
@@ -184,6 +197,13 @@ int draw_graph(const double* Q, int N, const uint8_t* x, int method, int m, int 
                         if (!inS[u]) { S[size++] = u; inS[u] = 1; queue[tail++] = u; }
                     }
                 }
+            } else if (W) {             // PFS, bitset rows: frontier |= row v
+                const uint64_t* rb = g->bits.data() + (size_t)v * W;
+                for (int w = 0; w < W; ++w) fbits[w] |= rb[w];
+                for (int t = 0; t < N; ++t) {
+                    const int32_t u = order[t];
+                    if (((fbits[u >> 6] >> (u & 63)) & 1ull) && !inS[u]) { next = u; break; }
+                }
             } else {                    // PFS: first frontier variable in ranking order
                 for (int64_t e = off[v]; e < off[v + 1]; ++e) inF[nbr[e]] = 1;
                 for (int t = 0; t < N; ++t) {
@@ -194,7 +214,9 @@ int draw_graph(const double* Q, int N, const uint8_t* x, int method, int m, int 
         }
         // clear the marks of this row only
         for (int a = 0; a < k; ++a) inS[S[a]] = 0;
-        if (method != 2)
+        if (W)
+            std::fill(fbits.begin(), fbits.end(), 0ull);
+        else if (method != 2)
             for (int a = 0; a < k; ++a)
                 for (int64_t e = off[S[a]]; e < off[S[a] + 1]; ++e) inF[nbr[e]] = 0;
         std::sort(S, S + k);

@@ -13,6 +13,8 @@ struct StrongGraph {
     int N = 0, k = 0;
     std::vector<int64_t> off;
     std::vector<int32_t> nbr;
+    int words = 0;                // > 0: rows also as bitsets of `words` 64-bit words (dense graphs)
+    std::vector<uint64_t> bits;
 };
 void build_strong_graph(const double* Q, int N, int k, StrongGraph* g);
 int draw_graph(const double* Q, int N, const uint8_t* x, int method, int m, int k, int32_t* idx,
