@@ -62,6 +62,7 @@ def _declare(L):
     L.orc_expect.restype = C.c_double
     L.orc_probs.argtypes = [C.c_int64, dp, dp]
     L.orc_topk_probs.argtypes = [C.c_int64, dp, C.c_int, u64p, dp]
+    L.orc_sample_probs.argtypes = [C.c_int64, dp, C.c_int64, dp, u64p]
     L.orc_grad.argtypes = [C.c_int, C.c_int, dp, dp, dp, C.c_int, dp, dp, dp]
     L.orc_splitmix64.argtypes = [C.c_uint64, C.c_int, u64p]
     L.orc_impact.argtypes = [dp, C.c_int, u8p, dp]
@@ -140,6 +141,19 @@ def topk_probs(prob, k):
 
 def topk(psi, k):
     return topk_probs(probs(psi), k)
+
+
+def sample_probs(prob, u):
+    """Inverse-CDF shots: for each uniform u_s, the first z with cumsum(prob)[z] > u_s * sum(prob)."""
+    prob, u = _f64(prob), _f64(np.atleast_1d(u))
+    out = np.empty(u.size, dtype=np.uint64)
+    _chk(lib().orc_sample_probs(prob.size, _p(prob, C.c_double), u.size, _p(u, C.c_double),
+                                _p(out, C.c_uint64)))
+    return out
+
+
+def sample(psi, u):
+    return sample_probs(probs(psi), u)
 
 
 def grad(n, gamma, beta, E, mixer_sign: int = 1):

@@ -150,6 +150,38 @@ void orc_probs(int64_t D, const cplx* psi, double* prob)
         prob[z] = creal(psi[z]) * creal(psi[z]) + cimag(psi[z]) * cimag(psi[z]);
 }
 
+/* Measurement shots (Section IV: the sub-solution is read from measurements of the final state;
+ * the paper's simulators sample shots). Shot s returns the smallest z whose cumulative
+ * probability C(z) = sum_{y <= z} prob[y] (FP64, ascending y) exceeds u[s] * C(D - 1), i.e.
+ * inverse-CDF sampling with the caller's uniforms u[s] in [0, 1). A target that no cumulative
+ * sum exceeds (only possible through rounding) returns the largest z with nonzero probability. */
+int orc_sample_probs(int64_t D, const double* prob, int64_t shots, const double* u, uint64_t* out)
+{
+    if (D < 1 || shots < 0 || !prob || (shots > 0 && (!u || !out))) return ORC_EINVAL;
+    double* cdf = (double*)malloc(sizeof(double) * (size_t)D);
+    if (!cdf) return ORC_ENOMEM;
+    double acc = 0.0;
+    int64_t last = 0;
+    for (int64_t z = 0; z < D; ++z) {
+        acc += prob[z];
+        cdf[z] = acc;
+        if (prob[z] > 0.0) last = z;
+    }
+    for (int64_t s = 0; s < shots; ++s) {
+        const double t = u[s] * acc;
+        /* binary search for the first cdf[z] > t */
+        int64_t lo = 0, hi = D;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (cdf[mid] > t) hi = mid;
+            else lo = mid + 1;
+        }
+        out[s] = (uint64_t)(lo < D ? lo : last);
+    }
+    free(cdf);
+    return ORC_OK;
+}
+
 /* k most probable indices: probability descending, ties to the smaller z. Plain insertion into
  * a sorted list of length k over one ascending scan; prob_out may be NULL. */
 int orc_topk_probs(int64_t D, const double* prob, int k, uint64_t* idx, double* prob_out)

@@ -431,6 +431,35 @@ def test_bfs_pfs_against_direct_traversal(orc, kind, k):
             assert idx[j].tolist() == _traverse_py(strong, rank, rank[j], k, bfs), (kind, k, j, bfs)
 
 
+def test_sample_two_level_and_basis_states(orc):
+    # inverse CDF on a hand-made distribution: P = (0, 0.25, 0, 0.75) -> u < 0.25 gives 1, else 3
+    pr = np.array([0.0, 0.25, 0.0, 0.75])
+    u = np.array([0.0, 0.1, 0.2499, 0.25, 0.5, 0.9999])
+    assert orc.sample_probs(pr, u).tolist() == [1, 1, 1, 3, 3, 3]
+    # a basis state returns its index for every uniform; scaling the distribution changes nothing
+    for z in (0, 5, 15):
+        e = np.zeros(16)
+        e[z] = 1.0
+        assert set(orc.sample_probs(e, synth.uniform01(3, 64)).tolist()) == {z}
+        assert set(orc.sample_probs(3.5 * e, synth.uniform01(4, 64)).tolist()) == {z}
+
+
+def test_sample_frequencies_match_probabilities(orc):
+    # shots of a p=2 QAOA state follow |psi|^2: Pearson chi-square over the 2^6 outcomes
+    n, shots = 6, 200000
+    Q = synth.symmetric_q(n, seed=81)
+    psi = orc.state(n, [0.4, 0.7], [0.6, 0.3], orc.energies(Q))
+    pr = np.abs(psi) ** 2
+    z = orc.sample(psi, synth.uniform01(82, shots))
+    counts = np.bincount(z.astype(np.int64), minlength=1 << n)
+    expect = shots * pr
+    chi2 = float(np.sum((counts - expect) ** 2 / expect))
+    assert chi2 < 63 + 6 * np.sqrt(2 * 63)          # 63 degrees of freedom, six sigma
+    # and the order statistics: sorted uniforms give non-decreasing indices
+    us = np.sort(synth.uniform01(83, 1000))
+    assert np.all(np.diff(orc.sample(psi, us).astype(np.int64)) >= 0)
+
+
 def test_merge_single_subqubo_takes_best(orc):
     # N = k: every candidate fixes the whole solution, so sequential "accept if lower" ends at
     # the minimum of the starting energy and all candidate energies
