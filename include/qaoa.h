@@ -121,6 +121,19 @@ qaoa_status qaoa_expect(qaoa_ctx* ctx, int n, const void* psi, const float* E, d
 qaoa_status qaoa_topk(qaoa_ctx* ctx, int n, const void* psi, int k, uint64_t* idx, double* prob,
                       qaoa_stream_t stream);
 
+/* Measurement shots of a complex64 state (Section IV: the paper reads the sub-solution from
+ * measured shots; qaoa_topk is this library's default). Shot s returns the smallest basis index z
+ * whose cumulative probability exceeds u[s] times the total probability (inverse-CDF sampling
+ * over |psi|^2 in FP64), with the caller's uniforms u[s] in [0, 1), so that a seeded generator
+ * reproduces the shots. The cumulative sums are FP64 sums over parts of 2^(n-12) amplitudes
+ * (n > 12), then a warp prefix scan inside a part: against a sequential sum, a uniform within a
+ * few ulps of a boundary may select the neighbouring index. A target that no running sum exceeds
+ * (rounding) returns the last nonzero amplitude of its part.
+ *   n: 1..30; psi: 2^n complex64 (device), not all zero; shots: 0..2^26; u: shots doubles
+ *   (device); out: shots uint64 (device). Uses workspace. Asynchronous on `stream`. */
+qaoa_status qaoa_sample(qaoa_ctx* ctx, int n, const void* psi, int64_t shots, const double* u,
+                        uint64_t* out, qaoa_stream_t stream);
+
 /* <C> and top-k of a complex64 state, like qaoa_expect and qaoa_topk together, for callers that
  * cannot allocate device memory: code whose device memory is owned by another allocator or a
  * fixed budget (a host framework's memory pool, where an extra cudaMalloc fragments or exceeds

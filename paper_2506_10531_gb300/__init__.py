@@ -37,7 +37,7 @@ EXPORTS = [
     "qaoa_server_create", "qaoa_server_destroy", "qaoa_server_job_bytes", "qaoa_server_submit",
     "qaoa_server_tick", "qaoa_server_poll", "qaoa_server_stats", "qaoa_server_clock",
     "qaoa_autotune", "qaoa_tuning_get", "qaoa_tuning_save", "qaoa_tuning_load", "qaoa_plan_capture",
-    "dqaoa_session_timing",
+    "dqaoa_session_timing", "qaoa_sample",
 ]
 
 
@@ -146,6 +146,7 @@ def _declare(L):
     L.qaoa_tuning_save.argtypes = [vp, C.c_char_p]
     L.qaoa_tuning_load.argtypes = [vp, C.c_char_p]
     L.qaoa_plan_capture.argtypes = [vp, vp]
+    L.qaoa_sample.argtypes = [vp, i32, vp, i64, vp, vp, vp]
     L.qaoa_server_clock.argtypes = []
     L.qaoa_server_clock.restype = C.c_double
     del st, dp
@@ -214,6 +215,11 @@ def qaoa_run_layers(ctx, n, p, gamma, beta, E, psi, init_plus=True, stream=None,
 def qaoa_expect(ctx, n, psi, E, out, stream=None, dbl=False):
     f = lib().qaoa_expect_z if dbl else lib().qaoa_expect
     _check(f(ctx, n, ptr(psi), ptr(E), ptr(out), stream_ptr(stream)))
+
+
+def qaoa_sample(ctx, n, psi, shots, u, out, stream=None):
+    """Inverse-CDF shots of a complex64 state with the caller's uniforms u (device doubles)."""
+    _check(lib().qaoa_sample(ctx, n, ptr(psi), int(shots), ptr(u), ptr(out), stream_ptr(stream)))
 
 
 def qaoa_topk(ctx, n, psi, k, idx, prob, stream=None, dbl=False):

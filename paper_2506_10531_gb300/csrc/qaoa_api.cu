@@ -362,6 +362,16 @@ extern "C" qaoa_status qaoa_topk_z(qaoa_ctx* c, int n, const void* psi, int k, u
     if (k < 1 || !idx) return fail(QAOA_E_INVALID, "topk: k=%d or NULL idx", k);
     return reduce_t<double>(c, n, psi, (const double*)nullptr, k, nullptr, idx, prob, s);
 }
+extern "C" qaoa_status qaoa_sample(qaoa_ctx* c, int n, const void* psi, int64_t shots, const double* u,
+                                   uint64_t* out, qaoa_stream_t s) {
+    if (!c) return fail(QAOA_E_INVALID, "ctx is NULL");
+    if (n < 1 || n > 30 || !psi || shots < 0 || shots > ((int64_t)1 << 26) || (shots > 0 && (!u || !out)))
+        return fail(QAOA_E_INVALID, "sample: n=%d shots=%lld or NULL pointer", n, (long long)shots);
+    qaoa_status st = ensure_ws(c, sample_scratch_bytes(n));
+    if (st) return st;
+    CK(launch_sample(n, psi, shots, u, out, static_cast<double*>(c->ws), (cudaStream_t)s));
+    return QAOA_OK;
+}
 extern "C" qaoa_status qaoa_grad(qaoa_ctx* c, int n, int p, const float* g, const float* b, const float* E,
                                  double* ex, double* dg, double* db, qaoa_stream_t s) {
     return grad_t<float>(c, n, p, g, b, E, ex, dg, db, s);

@@ -38,6 +38,10 @@ cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int 
 cudaError_t launch_plain_layers(int n, int p, const float* gamma, const float* beta,
                                 const float* E, float2* psi, int init_plus, cudaStream_t st,
                                 int* kernels);
+int sample_part_bits(int n);
+size_t sample_scratch_bytes(int n);
+cudaError_t launch_sample(int n, const void* psi, int64_t shots, const double* u, uint64_t* out,
+                          double* scratch, cudaStream_t st);
 cudaError_t launch_adam(int count, float* theta, const double* grad, float* m, float* v, int step,
                         float lr, float b1, float b2, float eps, int minimise, cudaStream_t st);
 }  // namespace qaoa
