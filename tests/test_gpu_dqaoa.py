@@ -88,7 +88,7 @@ def test_driver_cycles_to_convergence(q, orc):
     ctx = q.qaoa_create(0)
     try:
         r = solve(ctx, Q, 32, 10, 2, 4, (0.3, 0.5), (0.4, 0.2), x0, seed=3, max_cycles=60, patience=3)
-        # the same run judged against its own final energy as the reference: it stops as soon as
+        # the same run measured against its own final energy as the reference: it stops as soon as
         # the energy is within tolerance for three cycles
         r2 = solve(ctx, Q, 32, 10, 2, 4, (0.3, 0.5), (0.4, 0.2), x0, seed=3, max_cycles=60, patience=3,
                    ref_energy=r.energy, tol=1e-12)
