@@ -230,8 +230,17 @@ int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad) {
     int nb = 0;
     const int th = resident_threads(dbl, n);
     const size_t sm = resident_smem_bytes(dbl, n, pmax, grad);
-    if (dbl) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_resident<double>, th, sm);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_resident<float>, th, sm);
+    // the occupancy query counts a block that needs more than 48 KB of dynamic shared memory only
+    // once the kernel may use that much, so the limit is raised first (the launch sets it again)
+    if (dbl) {
+        if (cudaFuncSetAttribute(k_resident<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_resident<double>, th, sm) != cudaSuccess)
+            nb = 0;
+    } else {
+        if (cudaFuncSetAttribute(k_resident<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_resident<float>, th, sm) != cudaSuccess)
+            nb = 0;
+    }
     return nb;
 }
 
