@@ -254,6 +254,87 @@ void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, cons
 // Aggregation: h = Qx is kept up to date (O(N) per flipped variable), so each candidate costs
 // O(|d|^2) with d = x' - x. With a cache (h, energy, tau of the same Q and x from the previous
 // call) the O(N^2) set-up is skipped.
+// The sequential candidate loop of merge (one instantiation with the FP64 blocks at hand, one
+// that gathers the entries from Q). KC > 0 fixes the sub-QUBO size at compile time (the common
+// sizes; the arithmetic is the same, only the loops are unrolled). Returns the accepted count;
+// energy is updated in place.
+template <bool BLK, int KC>
+static int merge_loop(const double* Q, int N, uint8_t* x, int m, int k_rt, const int32_t* idx, int K,
+                      const uint64_t* cand, const double* qblk, double tau, double* hq_in,
+                      double& energy) {
+    const int k = KC > 0 ? KC : k_rt;
+    int accepted = 0;
+    int nz[64];
+    double d[64], h2[64];
+    const uint64_t kmask = k >= 64 ? ~0ull : (1ull << k) - 1ull;
+    double* __restrict__ hq = hq_in;
+    for (int j = 0; j < m; ++j) {
+        const int32_t* S = idx + (int64_t)j * k;
+        const double* blk = BLK ? qblk + (int64_t)j * k * k : nullptr;
+        // x on S_j packed like a candidate: the changed positions of a candidate are then the set
+        // bits of y ^ xs, visited in ascending order without a data-dependent branch per position;
+        // h2 = 2 h on S_j (exact doubling), refreshed whenever a candidate is accepted
+        uint64_t xs = 0;
+        for (int a = 0; a < k; ++a) {
+            xs |= (uint64_t)(x[S[a]] != 0) << a;
+            h2[a] = 2.0 * hq[S[a]];
+        }
+        for (int c = 0; c < K; ++c) {
+            const uint64_t y = cand[(int64_t)j * K + c];
+            int cnt = 0;
+            for (uint64_t diff = (y ^ xs) & kmask; diff; diff &= diff - 1) {
+                const int a = __builtin_ctzll(diff);
+                nz[cnt] = a;
+                d[cnt] = ((y >> a) & 1u) ? 1.0 : -1.0;   // x'_a - x_a
+                ++cnt;
+            }
+            if (!cnt) continue;
+            // inner[u] = sum over v (ascending) of Q[S_u][S_v] d_v; the u sums are independent,
+            // so they advance together (each keeps its own order)
+            double inner[64];
+            double dE = 0.0;
+            if constexpr (BLK) {
+                // with the block at hand, every row a of it advances (contiguous, vectorisable:
+                // Q[S_a][S_v] = Q[S_v][S_a] is row v of the symmetric block) and the changed
+                // rows are read at the end; the sums of the changed rows are the same sums
+                for (int a = 0; a < k; ++a) inner[a] = 0.0;
+                for (int v = 0; v < cnt; ++v) {
+                    const double dv = d[v];
+                    const double* col = blk + (int64_t)nz[v] * k;
+                    for (int a = 0; a < k; ++a) inner[a] += col[a] * dv;
+                }
+                for (int u = 0; u < cnt; ++u) dE += d[u] * (h2[nz[u]] + inner[nz[u]]);
+            } else {
+                for (int u = 0; u < cnt; ++u) inner[u] = 0.0;
+                for (int v = 0; v < cnt; ++v) {
+                    const double dv = d[v];
+                    const int64_t cv = S[nz[v]];
+                    for (int u = 0; u < cnt; ++u) inner[u] += Q[(int64_t)S[nz[u]] * N + cv] * dv;
+                }
+                for (int u = 0; u < cnt; ++u) dE += d[u] * (h2[nz[u]] + inner[u]);
+            }
+            if (dE < -tau) {
+                for (int u = 0; u < cnt; ++u) {
+                    const int var = S[nz[u]];
+                    x[var] = (uint8_t)(d[u] > 0.0);
+                    // column var of the symmetric Q == row var
+                    const double* __restrict__ row = Q + (int64_t)var * N;
+                    const double du = d[u];
+                    for (int l = 0; l < N; ++l) hq[l] += du * row[l];
+                }
+                energy += dE;
+                ++accepted;
+                xs = 0;
+                for (int a = 0; a < k; ++a) {
+                    xs |= (uint64_t)(x[S[a]] != 0) << a;
+                    h2[a] = 2.0 * hq[S[a]];
+                }
+            }
+        }
+    }
+    return accepted;
+}
+
 int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
           const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache,
           const double* qblk) {
@@ -285,67 +366,13 @@ int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, 
         for (int i = 0; i < N; ++i)
             if (x[i]) energy += hp[i];
     }
-    int accepted = 0;
-    int nz[64];
-    double d[64];
-    const uint64_t kmask = k >= 64 ? ~0ull : (1ull << k) - 1ull;
-    for (int j = 0; j < m; ++j) {
-        const int32_t* S = idx + (int64_t)j * k;
-        const double* blk = qblk ? qblk + (int64_t)j * k * k : nullptr;
-        // x on S_j packed like a candidate: the changed positions of a candidate are then the set
-        // bits of y ^ xs, visited in ascending order without a data-dependent branch per position
-        uint64_t xs = 0;
-        for (int a = 0; a < k; ++a) xs |= (uint64_t)(x[S[a]] != 0) << a;
-        for (int c = 0; c < K; ++c) {
-            const uint64_t y = cand[(int64_t)j * K + c];
-            int cnt = 0;
-            for (uint64_t diff = (y ^ xs) & kmask; diff; diff &= diff - 1) {
-                const int a = __builtin_ctzll(diff);
-                nz[cnt] = a;
-                d[cnt] = ((y >> a) & 1u) ? 1.0 : -1.0;   // x'_a - x_a
-                ++cnt;
-            }
-            if (!cnt) continue;
-            // inner[u] = sum over v (ascending) of Q[S_u][S_v] d_v; the u sums are independent,
-            // so they advance together (each keeps its own order)
-            double inner[64];
-            double dE = 0.0;
-            if (blk) {
-                // with the block at hand, every row a of it advances (contiguous, vectorisable:
-                // Q[S_a][S_v] = Q[S_v][S_a] is row v of the symmetric block) and the changed
-                // rows are read at the end; the sums of the changed rows are the same sums
-                for (int a = 0; a < k; ++a) inner[a] = 0.0;
-                for (int v = 0; v < cnt; ++v) {
-                    const double dv = d[v];
-                    const double* col = blk + (int64_t)nz[v] * k;
-                    for (int a = 0; a < k; ++a) inner[a] += col[a] * dv;
-                }
-                for (int u = 0; u < cnt; ++u) dE += d[u] * (2.0 * h[S[nz[u]]] + inner[nz[u]]);
-            } else {
-                for (int u = 0; u < cnt; ++u) inner[u] = 0.0;
-                for (int v = 0; v < cnt; ++v) {
-                    const double dv = d[v];
-                    const int64_t cv = S[nz[v]];
-                    for (int u = 0; u < cnt; ++u) inner[u] += Q[(int64_t)S[nz[u]] * N + cv] * dv;
-                }
-                for (int u = 0; u < cnt; ++u) dE += d[u] * (2.0 * h[S[nz[u]]] + inner[u]);
-            }
-            if (dE < -tau) {
-                for (int u = 0; u < cnt; ++u) {
-                    const int var = S[nz[u]];
-                    x[var] = (uint8_t)(d[u] > 0.0);
-                    // column var of the symmetric Q == row var
-                    const double* row = Q + (int64_t)var * N;
-                    const double du = d[u];
-                    for (int l = 0; l < N; ++l) h[l] += du * row[l];
-                }
-                energy += dE;
-                ++accepted;
-                xs = 0;
-                for (int a = 0; a < k; ++a) xs |= (uint64_t)(x[S[a]] != 0) << a;
-            }
-        }
-    }
+    int accepted;
+    double* hp0 = h.data();
+    if (!qblk) accepted = merge_loop<false, 0>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
+    else if (k == 16) accepted = merge_loop<true, 16>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
+    else if (k == 12) accepted = merge_loop<true, 12>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
+    else if (k == 20) accepted = merge_loop<true, 20>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
+    else accepted = merge_loop<true, 0>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
     if (energy_out) *energy_out = energy;
     if (accepted_out) *accepted_out = accepted;
     if (cache) {
