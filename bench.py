@@ -517,8 +517,8 @@ def run_large(args):
     with Clocks(local) as clk:
         step_ms = _timed_steps(stream, args.steps, body)
     q.qaoa_plan_set_timing(plan, False)
-    tot_s = sum(step_ms) / 1e3
-    amps = (1 << n) * p
+    tot_s = max_over_ranks(sum(step_ms) / 1e3, dev)
+    amps = (1 << n) * p * world
     roof = plan_roofline(q, plan, kern, lambda: q.qaoa_plan_launch(plan, stream), clk, dev,
                          workload=f"large_n{n}")
     per_pass = {"ms": [round(v, 3) for v in kern.get("stream_pass", [])[:8]]}
@@ -536,7 +536,7 @@ def run_large(args):
         out[1:1 + k].copy_(tp, non_blocking=True)
         out[1 + k:].copy_(ti.view(torch.float64), non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     kernels = q.qaoa_plan_kernel_count(plan)
     q.qaoa_plan_destroy(plan)
     q.qaoa_destroy(ctx)
@@ -546,7 +546,7 @@ def run_large(args):
                  {"workload": f"large instance: dense n={n} QUBO U[-1,1] (seed 5), p=2, gamma=(0.4,0.7), "
                               f"beta=(0.6,0.3), complex64 ({(8 << n) / 2**30:g} GiB) + FP32 energies, top-8",
                   "l2": "inputs larger than L2 (state + energies)", "parallelism": f"replicas x{world}"},
-                 solves_per_s=args.steps / tot_s,
+                 solves_per_s=args.steps * world / tot_s,
                  amp_gate_updates_per_s=amps * (n + 1) * args.steps / tot_s,
                  latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
                  kernel_ms_per_step={nm: sum(v) / args.steps for nm, v in kern.items()},
@@ -611,7 +611,7 @@ def run_plain10(args):
     with Clocks(local) as clk:
         step_ms = _timed_steps(stream, args.steps, body, flush=lambda: flush.fill_(1))
     q.qaoa_plan_set_timing(plan, False)
-    tot_s = sum(step_ms) / 1e3
+    tot_s = max_over_ranks(sum(step_ms) / 1e3, dev)
     # on-chip FP64 work: phase (sincos ~ 20 flops) + 4 flops + 4 flops per qubit per amplitude
     flops = count * (1 << n) * (24 + 4 * n)
     props = torch.cuda.get_device_properties(dev)
@@ -637,21 +637,21 @@ def run_plain10(args):
         oti.copy_(ti, non_blocking=True)
         otp.copy_(tp, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     kernels = q.qaoa_plan_kernel_count(plan)
     q.qaoa_plan_destroy(plan)
     q.qaoa_destroy(ctx)
     line = _line("grid points solved/s (n=10, p=1, complex128: energies + layer + <C> + top-8)",
-                 count * args.steps / tot_s, "solves/s", args, world, 1e3 * tot_s / args.steps,
+                 count * args.steps * world / tot_s, "solves/s", args, world, 1e3 * tot_s / args.steps,
                  "c128 state, f64 energies and reductions",
                  {"workload": "plain n=10 QUBO U[-1,1] (seed 1), p=1, 16x16 (gamma, beta) grid over "
                               "[0,pi]x[0,pi/2] as 256 resident instances sharing Q, complex128, top-8",
                   "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
-                 amp_layer_updates_per_s=count * (1 << n) * args.steps / tot_s,
+                 amp_layer_updates_per_s=count * (1 << n) * args.steps * world / tot_s,
                  latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
                  kernel_ms_per_step={nm: sum(v) / args.steps for nm, v in kern.items()},
                  roofline=roof,
-                 e2e={"value": count * args.steps / e2e_s, "unit": "solves/s",
+                 e2e={"value": count * args.steps * world / e2e_s, "unit": "solves/s",
                       "h2d_bytes_per_step": Q.nbytes + par.nbytes, "d2h_bytes_per_step": count * (8 + 16 * k)},
                  gpu_launches=kernels * args.steps, clocks=clk.summary())
     if rank == 0 and not args.no_cpu_baseline:
@@ -702,7 +702,7 @@ def run_uneven(args):
     with Clocks(local) as clk:
         step_ms = _timed_steps(stream, args.steps, body)
     q.qaoa_plan_set_timing(B.plan, False)
-    tot_s = sum(step_ms) / 1e3
+    tot_s = max_over_ranks(sum(step_ms) / 1e3, dev)
     roof = plan_roofline(q, B.plan, kern, lambda: B.run(stream), clk, dev, workload=f"uneven_{U['count']}")
     amps = float(np.sum((2.0 ** ns) * ps))
     # e2e: Q pool and parameters from pinned host memory, <C> of every instance back, per step
@@ -719,22 +719,22 @@ def run_uneven(args):
         B.adam_step(U["lr"], stream)
         eh.copy_(B.expect, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     kernels = B.kernels_per_launch + 1
     B.close()
     q.qaoa_destroy(ctx)
     line = _line("instance optimisation steps/s (uneven batch: <C> + adjoint gradient + Adam, all instances)",
-                 B.count * args.steps / tot_s, "instance-steps/s", args, world, 1e3 * tot_s / args.steps,
+                 B.count * args.steps * world / tot_s, "instance-steps/s", args, world, 1e3 * tot_s / args.steps,
                  "c64 state, f32 energies, f64 reductions and gradients",
                  {"workload": f"uneven batch: {U['count']} sub-QUBOs, n uniform 8..24, p uniform 1..6, Q N(0,1) "
                               "symmetric (seed 3), complex64, adjoint gradients, Adam lr 0.05",
                   "l2": "inputs larger than L2 (about 160 GB of states and energies)",
                   "parallelism": f"replicas x{world}"},
-                 amp_layer_updates_per_s=amps * args.steps / tot_s,
+                 amp_layer_updates_per_s=amps * args.steps * world / tot_s,
                  latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
                  kernel_ms_per_step={nm: sum(v) / args.steps for nm, v in kern.items()},
                  roofline=roof,
-                 e2e={"value": B.count * e2e_steps / e2e_s, "unit": "instance-steps/s",
+                 e2e={"value": B.count * e2e_steps * world / e2e_s, "unit": "instance-steps/s",
                       "h2d_bytes_per_step": int(qh.numel() * 4 + ph.numel() * 4),
                       "d2h_bytes_per_step": B.count * 8},
                  gpu_launches=kernels * args.steps, clocks=clk.summary())
@@ -823,8 +823,10 @@ def run_serving(args):
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
             "peak_source": peak_kind + " (hbm_gbs, copy burst)",
             "note": "algorithmic bytes of every tick at the saturating rate over the ticks' device time"}
+    # replicas: the whole job serves world streams, at the pace of the slowest replica
+    job_rate = -max_over_ranks(-sat["solves_per_s"], dev) * world
     line = _line("optimise-and-sample jobs/s at saturation (serving: Poisson arrivals, continuous batching)",
-                 sat["solves_per_s"], "jobs/s", args, world, 1e3 / sat["solves_per_s"] if sat["solves_per_s"] else None,
+                 job_rate, "jobs/s", args, world, 1e3 / sat["solves_per_s"] if sat["solves_per_s"] else None,
                  "c64 state, f32 energies, f64 reductions and gradients",
                  {"workload": f"serving: Poisson arrivals at {list(SERVING['rates'])} req/s, {count} requests per "
                               "rate, n uniform 12..26, p uniform 1..8, Q U[-1,1], 50 adjoint-Adam steps then "
@@ -832,7 +834,7 @@ def run_serving(args):
                   "scratch_bytes": scratch, "max_jobs": 4096, "l2": "inputs larger than L2",
                   "parallelism": f"replicas x{world}"},
                  latency_s={"p50": sat["p50_s"], "p99": sat["p99_s"]}, rates=rows, roofline=roof,
-                 e2e={"value": sat["solves_per_s"], "unit": "jobs/s",
+                 e2e={"value": job_rate, "unit": "jobs/s",
                       "h2d_bytes_per_step": sat["h2d_bytes_per_job"], "d2h_bytes_per_step": sat["d2h_bytes_per_job"],
                       "note": "the serving loop is end to end (host Q and parameters in, results out); "
                               "bytes per job"},
@@ -995,10 +997,19 @@ def main():
     elif args.config == "dqaoa":
         run_ours(args)
     else:
-        rank, world, _ = dist_env()
+        import torch
+        import torch.distributed as dist
+        rank, world, local = dist_env()
+        if world > 1:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+            dist.barrier()
         line = CONFIGS[args.config](args)
         if rank == 0:
             print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":
