@@ -134,6 +134,26 @@ qaoa_status qaoa_topk(qaoa_ctx* ctx, int n, const void* psi, int k, uint64_t* id
 qaoa_status qaoa_sample(qaoa_ctx* ctx, int n, const void* psi, int64_t shots, const double* u,
                         uint64_t* out, qaoa_stream_t stream);
 
+/* Derivative-free minimisation for the gradient-free outer loop of Section IV (the paper tunes
+ * each sub-QUBO's angles with COBYLA; this library's default is the adjoint gradient with Adam).
+ * The method of Powell (1994), unconstrained case: a linear interpolation model on a simplex of
+ * nvar + 1 points, trust-region steps of length rho against the model gradient, geometry steps
+ * that keep the simplex well shaped, rho halved from rhobeg down to rhoend. Host code, no GPU.
+ * Reverse communication: qaoa_cobyla_ask writes the next point to evaluate into x and returns 1
+ * (the caller evaluates f there and calls qaoa_cobyla_tell), or writes the best point found and
+ * returns 0 once rho has reached rhoend or maxfun values have been told. So many independent
+ * minimisations can have their points evaluated together, e.g. one batched plan launch for every
+ * sub-QUBO of a batch. nvar 1..256, 0 < rhoend <= rhobeg, maxfun >= nvar + 2. Non-finite values
+ * count as +inf. */
+typedef struct qaoa_cobyla qaoa_cobyla;
+qaoa_status qaoa_cobyla_create(int nvar, const double* x0, double rhobeg, double rhoend, int maxfun,
+                               qaoa_cobyla** out);
+int qaoa_cobyla_ask(qaoa_cobyla* s, double* x);
+qaoa_status qaoa_cobyla_tell(qaoa_cobyla* s, double f);
+/* Best point, its value and the number of values told so far (any pointer may be NULL). */
+qaoa_status qaoa_cobyla_result(qaoa_cobyla* s, double* x, double* f, int* nfev);
+void qaoa_cobyla_destroy(qaoa_cobyla* s);
+
 /* <C> and top-k of a complex64 state, like qaoa_expect and qaoa_topk together, for callers that
  * cannot allocate device memory: code whose device memory is owned by another allocator or a
  * fixed budget (a host framework's memory pool, where an extra cudaMalloc fragments or exceeds

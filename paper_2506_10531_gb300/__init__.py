@@ -38,6 +38,7 @@ EXPORTS = [
     "qaoa_server_tick", "qaoa_server_poll", "qaoa_server_stats", "qaoa_server_clock",
     "qaoa_autotune", "qaoa_tuning_get", "qaoa_tuning_save", "qaoa_tuning_load", "qaoa_plan_capture",
     "dqaoa_session_timing", "qaoa_sample",
+    "qaoa_cobyla_create", "qaoa_cobyla_ask", "qaoa_cobyla_tell", "qaoa_cobyla_result", "qaoa_cobyla_destroy",
 ]
 
 
@@ -147,6 +148,13 @@ def _declare(L):
     L.qaoa_tuning_load.argtypes = [vp, C.c_char_p]
     L.qaoa_plan_capture.argtypes = [vp, vp]
     L.qaoa_sample.argtypes = [vp, i32, vp, i64, vp, vp, vp]
+    L.qaoa_cobyla_create.argtypes = [i32, vp, C.c_double, C.c_double, i32, C.POINTER(vp)]
+    L.qaoa_cobyla_ask.argtypes = [vp, vp]
+    L.qaoa_cobyla_ask.restype = i32
+    L.qaoa_cobyla_tell.argtypes = [vp, C.c_double]
+    L.qaoa_cobyla_result.argtypes = [vp, vp, vp, vp]
+    L.qaoa_cobyla_destroy.argtypes = [vp]
+    L.qaoa_cobyla_destroy.restype = None
     L.qaoa_server_clock.argtypes = []
     L.qaoa_server_clock.restype = C.c_double
     del st, dp
@@ -220,6 +228,45 @@ def qaoa_expect(ctx, n, psi, E, out, stream=None, dbl=False):
 def qaoa_sample(ctx, n, psi, shots, u, out, stream=None):
     """Inverse-CDF shots of a complex64 state with the caller's uniforms u (device doubles)."""
     _check(lib().qaoa_sample(ctx, n, ptr(psi), int(shots), ptr(u), ptr(out), stream_ptr(stream)))
+
+
+class Cobyla:
+    """Reverse-communication minimiser (qaoa_cobyla_*): ask() returns the next point to evaluate
+    (numpy float64) or None when finished; tell(f) reports its value; result() the best point."""
+
+    def __init__(self, x0, rhobeg, rhoend, maxfun):
+        import numpy as np
+        self.x = np.array(x0, dtype=np.float64).ravel()
+        h = C.c_void_p()
+        _check(lib().qaoa_cobyla_create(self.x.size, self.x.ctypes.data, float(rhobeg), float(rhoend),
+                                        int(maxfun), C.byref(h)))
+        self._h = h
+
+    def ask(self):
+        need = lib().qaoa_cobyla_ask(self._h, self.x.ctypes.data)
+        return self.x.copy() if need else None
+
+    def tell(self, f):
+        _check(lib().qaoa_cobyla_tell(self._h, float(f)))
+
+    def result(self):
+        import numpy as np
+        x = np.empty_like(self.x)
+        f = C.c_double()
+        n = C.c_int()
+        _check(lib().qaoa_cobyla_result(self._h, x.ctypes.data, C.byref(f), C.byref(n)))
+        return x, f.value, n.value
+
+    def close(self):
+        if self._h:
+            lib().qaoa_cobyla_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def qaoa_topk(ctx, n, psi, k, idx, prob, stream=None, dbl=False):

@@ -12,7 +12,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (QAOA_INST_GRAD, make_insts, make_io, qaoa_adam_step, qaoa_plan_create,
+from . import (QAOA_INST_GRAD, Cobyla, make_insts, make_io, qaoa_adam_step, qaoa_plan_create,
                qaoa_plan_destroy, qaoa_plan_kernel_count, qaoa_plan_launch)
 
 
@@ -132,3 +132,59 @@ def waves_by_footprint(ns, budget_bytes: int, grad: bool = True):
     if cur:
         waves.append(cur)
     return waves
+
+
+def cobyla_lockstep(x0s, evaluate, rhobeg: float = 0.2, rhoend: float = 1e-4, maxfun: int = 300):
+    """Independent derivative-free minimisations (libqaoa's qaoa_cobyla_*, Powell's method) advanced
+    together: every round asks each unfinished minimisation for its next point and evaluates all
+    of them with one call evaluate(points) -> values (a list of arrays in, a sequence of floats
+    out; finished minimisations contribute their best point, whose value is not used). Returns
+    (best points, best values, values evaluated per minimisation, rounds)."""
+    states = [Cobyla(x0, rhobeg, rhoend, maxfun) for x0 in x0s]
+    points = [np.array(x0, dtype=np.float64) for x0 in x0s]
+    active = [True] * len(states)
+    rounds = 0
+    try:
+        while True:
+            for i, st in enumerate(states):
+                if active[i]:
+                    x = st.ask()
+                    if x is None:
+                        active[i] = False
+                        points[i] = st.result()[0]
+                    else:
+                        points[i] = x
+            if not any(active):
+                break
+            values = evaluate(points)
+            for i, st in enumerate(states):
+                if active[i]:
+                    st.tell(float(values[i]))
+            rounds += 1
+        res = [st.result() for st in states]
+    finally:
+        for st in states:
+            st.close()
+    return [r[0] for r in res], [r[1] for r in res], [r[2] for r in res], rounds
+
+
+def cobyla_train(batch: QAOABatch, rhobeg: float = 0.2, rhoend: float = 1e-4, maxfun: int = 300,
+                 stream=None):
+    """Gradient-free training of every instance of `batch` (the paper's optimiser family, Section
+    IV): one COBYLA-type minimisation per instance over its (gamma, beta), all advanced in
+    lockstep, each round one plan launch evaluating <C> of every instance. The best parameters
+    end up in the batch's parameter pool (FP32). Returns (best <C> per instance, rounds)."""
+    offs = np.cumsum([0] + [2 * p for p in batch.ps])
+    flat = batch.params.detach().cpu().numpy().astype(np.float64)
+    x0s = [flat[offs[i]:offs[i + 1]] for i in range(batch.count)]
+
+    def evaluate(points):
+        buf = np.concatenate(points).astype(np.float32)
+        batch.params.copy_(torch.from_numpy(buf).to(batch.params.device))
+        batch.run(stream)
+        torch.cuda.synchronize(batch.params.device)
+        return batch.expect.detach().cpu().numpy()
+
+    best, fbest, _, rounds = cobyla_lockstep(x0s, evaluate, rhobeg, rhoend, maxfun)
+    batch.params.copy_(torch.from_numpy(np.concatenate(best).astype(np.float32)).to(batch.params.device))
+    return np.array(fbest), rounds
