@@ -230,36 +230,60 @@ def qaoa_sample(ctx, n, psi, shots, u, out, stream=None):
     _check(lib().qaoa_sample(ctx, n, ptr(psi), int(shots), ptr(u), ptr(out), stream_ptr(stream)))
 
 
+def qaoa_cobyla_create(nvar, x0, rhobeg, rhoend, maxfun):
+    """Handle of a new minimisation (x0: host float64 array of nvar values)."""
+    h = C.c_void_p()
+    _check(lib().qaoa_cobyla_create(int(nvar), ptr(x0), float(rhobeg), float(rhoend), int(maxfun),
+                                    C.byref(h)))
+    return h
+
+
+def qaoa_cobyla_ask(h, x) -> int:
+    """1: evaluate at x (written into the float64 array x); 0: finished, x = best point."""
+    return lib().qaoa_cobyla_ask(h, ptr(x))
+
+
+def qaoa_cobyla_tell(h, f):
+    _check(lib().qaoa_cobyla_tell(h, float(f)))
+
+
+def qaoa_cobyla_result(h, x):
+    """Writes the best point into x; returns (best value, values told)."""
+    f = C.c_double()
+    n = C.c_int()
+    _check(lib().qaoa_cobyla_result(h, ptr(x), C.byref(f), C.byref(n)))
+    return f.value, n.value
+
+
+def qaoa_cobyla_destroy(h):
+    lib().qaoa_cobyla_destroy(h)
+
+
 class Cobyla:
     """Reverse-communication minimiser (qaoa_cobyla_*): ask() returns the next point to evaluate
     (numpy float64) or None when finished; tell(f) reports its value; result() the best point."""
 
     def __init__(self, x0, rhobeg, rhoend, maxfun):
         import numpy as np
+        self._h = None
         self.x = np.array(x0, dtype=np.float64).ravel()
-        h = C.c_void_p()
-        _check(lib().qaoa_cobyla_create(self.x.size, self.x.ctypes.data, float(rhobeg), float(rhoend),
-                                        int(maxfun), C.byref(h)))
-        self._h = h
+        self._h = qaoa_cobyla_create(self.x.size, self.x, rhobeg, rhoend, maxfun)
 
     def ask(self):
-        need = lib().qaoa_cobyla_ask(self._h, self.x.ctypes.data)
-        return self.x.copy() if need else None
+        return self.x.copy() if qaoa_cobyla_ask(self._h, self.x) else None
 
     def tell(self, f):
-        _check(lib().qaoa_cobyla_tell(self._h, float(f)))
+        qaoa_cobyla_tell(self._h, f)
 
     def result(self):
         import numpy as np
         x = np.empty_like(self.x)
-        f = C.c_double()
-        n = C.c_int()
-        _check(lib().qaoa_cobyla_result(self._h, x.ctypes.data, C.byref(f), C.byref(n)))
-        return x, f.value, n.value
+        f, n = qaoa_cobyla_result(self._h, x)
+        return x, f, n
 
     def close(self):
         if self._h:
-            lib().qaoa_cobyla_destroy(self._h)
+            qaoa_cobyla_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -42,7 +42,7 @@ def _worker(rank, world, port, out):
 
 def test_max_over_ranks_and_replica_seeds_gloo():
     import torch.multiprocessing as mp
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(2, free_port(), out), nprocs=2, join=True)
     for r in range(2):
