@@ -182,7 +182,8 @@ def cobyla_train(batch: QAOABatch, rhobeg: float = 0.2, rhoend: float = 1e-4, ma
         buf = np.concatenate(points).astype(np.float32)
         batch.params.copy_(torch.from_numpy(buf).to(batch.params.device))
         batch.run(stream)
-        torch.cuda.synchronize(batch.params.device)
+        if batch.params.is_cuda:
+            torch.cuda.synchronize(batch.params.device)
         return batch.expect.detach().cpu().numpy()
 
     best, fbest, _, rounds = cobyla_lockstep(x0s, evaluate, rhobeg, rhoend, maxfun)

@@ -99,3 +99,52 @@ def test_lockstep_equals_separate_runs(orc):
         x, fv, n, _ = minimise(objs[i], x0s[i], 0.2, 1e-5, 500)
         np.testing.assert_array_equal(best[i], x)
         assert fbest[i] == fv and nfev[i] == n
+
+
+class _OracleBatch:
+    """Stand-in with QAOABatch's pools and layout (count, ps, float32 params as gamma[p] beta[p]
+    per instance, float64 expect) whose run() evaluates <C> with the oracle."""
+
+    def __init__(self, orc, specs):
+        self.orc = orc
+        self.Es, self.ns, self.ps, pars = [], [], [], []
+        for n, p, seed in specs:
+            self.Es.append(orc.energies(synth.symmetric_q(n, seed=seed)))
+            self.ns.append(n)
+            self.ps.append(p)
+            pars.append(0.3 * np.concatenate(synth.random_params(p, seed=seed + 50)))
+        import torch
+        self.count = len(specs)
+        self.params = torch.as_tensor(np.concatenate(pars).astype(np.float32))
+        self.expect = torch.zeros(self.count, dtype=torch.float64)
+        self.runs = 0
+
+    def run(self, stream=None):
+        flat = self.params.numpy().astype(np.float64)
+        o = 0
+        for i in range(self.count):
+            n, p, E = self.ns[i], self.ps[i], self.Es[i]
+            x = flat[o:o + 2 * p]
+            self.expect[i] = float(self.orc.expect(self.orc.state(n, x[:p], x[p:], E), E))
+            o += 2 * p
+        self.runs += 1
+
+
+def test_cobyla_train_layout_and_result(orc):
+    from paper_2506_10531_gb300.train import cobyla_train
+    b = _OracleBatch(orc, [(6, 1, 31), (7, 2, 32), (5, 3, 33)])
+    b.run()
+    start = b.expect.numpy().copy()
+    fbest, rounds = cobyla_train(b, rhobeg=0.2, rhoend=1e-6, maxfun=2000)
+    assert rounds > 0 and b.runs == rounds + 1
+    assert np.all(fbest < start)
+    # the pool holds the best parameters (FP32): re-evaluating reproduces the best values
+    b.run()
+    np.testing.assert_allclose(b.expect.numpy(), fbest, rtol=0, atol=1e-5 * np.abs(fbest).max())
+    o = 0
+    for i in range(b.count):
+        n, p, E = b.ns[i], b.ps[i], b.Es[i]
+        x = b.params.numpy()[o:o + 2 * p].astype(np.float64)
+        _, dg, db = orc.grad(n, x[:p], x[p:], E)
+        assert np.abs(np.concatenate([dg, db])).max() < 1e-3 * np.abs(E).max()
+        o += 2 * p
