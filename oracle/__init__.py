@@ -182,6 +182,7 @@ def impact(Q, x):
 
 
 RANDOM, IFD, BFS, PFS = 0, 1, 2, 3
+SIGNED = 16     # or-ed with IFD / BFS / PFS: rank by the energy change, largest decrease first
 
 
 def decompose(Q, x, m, k, seed, cycle=0, method=RANDOM, conditioned=True):

@@ -309,22 +309,29 @@ void orc_impact(const double* Q, int N, const uint8_t* x, double* dE)
     }
 }
 
-/* Ranking of Algorithm 1's impact_analysis: |dE_i| descending, ties to the smaller index. */
-static void impact_ranking(const double* Q, int N, const uint8_t* x, int32_t* order)
+/* Ranking of Algorithm 1's impact_analysis, ties to the smaller index. Section V-A ranks by the
+ * impact factor without saying whether a large energy increase counts as a high impact: the
+ * default reading ranks by |dE_i| descending; with `signed` the ranking is dE_i ascending (the
+ * largest energy decrease first). */
+static void impact_ranking(const double* Q, int N, const uint8_t* x, int32_t* order, int signed_rank)
 {
     double* dE = (double*)malloc(sizeof(double) * (size_t)N);
     orc_impact(Q, N, x, dE);
+    double* key = (double*)malloc(sizeof(double) * (size_t)N);
+    /* key descending = rank order */
+    for (int i = 0; i < N; ++i) key[i] = signed_rank ? -dE[i] : fabs(dE[i]);
     for (int i = 0; i < N; ++i) order[i] = i;
     /* insertion sort: plain and stable */
     for (int i = 1; i < N; ++i) {
         const int32_t v = order[i];
         int j = i;
-        while (j > 0 && fabs(dE[order[j - 1]]) < fabs(dE[v])) {
+        while (j > 0 && key[order[j - 1]] < key[v]) {
             order[j] = order[j - 1];
             --j;
         }
         order[j] = v;
     }
+    free(key);
     free(dE);
 }
 
@@ -416,6 +423,7 @@ static void traverse(const double* Q, int N, const double* thr, const int32_t* r
  *   method 1 (IFD, Algorithm 1): variables ranked by impact; sub-QUBO j takes the window
  *     ranking[j .. j+k-1] and sorts it (requires m + k - 1 <= N).
  *   methods 2 (BFS) and 3 (PFS): the traversals above from rank[j], sorted (requires m <= N).
+ *   methods 1-3 plus 16: the same with the signed impact ranking (see impact_ranking).
  * Qsub[j] = Q[S_j, S_j] as a full symmetric k x k matrix. With conditioned != 0 the couplings to
  * the fixed variables outside S_j are folded into the diagonal:
  *   Qsub[a][a] += 2 sum_{l not in S_j} Q[S_a][l] x_l,
@@ -423,9 +431,12 @@ static void traverse(const double* Q, int N, const double* thr, const int32_t* r
  * value, not the order of the FP64 additions; the order used here is eight partial sums
  * s_r over l = r (mod 8), each in ascending l, combined as ((s0+s1)+(s2+s3))+((s4+s5)+(s6+s7)).
  */
-int orc_decompose(const double* Q, int N, const uint8_t* x, int method, int conditioned, int m,
+int orc_decompose(const double* Q, int N, const uint8_t* x, int method_flags, int conditioned, int m,
                   int k, uint64_t seed, uint64_t cycle, int32_t* idx, double* Qsub)
 {
+    /* method_flags: the method in the low four bits, bit 4 (16) selects the signed ranking */
+    const int method = method_flags & 15, signed_rank = (method_flags >> 4) & 1;
+    if ((method_flags & ~31) || (signed_rank && method == 0)) return ORC_EINVAL;
     if (!Q || N < 1 || m < 1 || k < 1 || k > N || !idx || !Qsub) return ORC_EINVAL;
     if ((conditioned || method == 1) && !x) return ORC_EINVAL;
     if (method == 1 && m + k - 1 > N) return ORC_EINVAL;
@@ -441,7 +452,7 @@ int orc_decompose(const double* Q, int N, const uint8_t* x, int method, int cond
         free(perm); free(inS); free(inF); free(queue); free(thr);
         return ORC_ENOMEM;
     }
-    if (method >= 1) impact_ranking(Q, N, x, perm);
+    if (method >= 1) impact_ranking(Q, N, x, perm, signed_rank);
     if (method >= 2) strong_thresholds(Q, N, k, thr);
     for (int j = 0; j < m; ++j) {
         int32_t* S = idx + (int64_t)j * k;

@@ -328,6 +328,22 @@ def test_conditioned_subqubo_equals_global_energy(orc):
         np.testing.assert_allclose(diffs, diffs[0], atol=1e-10)
 
 
+def test_signed_ifd_windows_and_invalid_flags(orc):
+    N, m, k = 40, 8, 5
+    Q = synth.symmetric_q(N, seed=43)
+    x = synth.bits(44, N)
+    dE = orc.impact(Q, x)
+    assert (dE < 0).any() and (dE > 0).any()              # both signs occur
+    rank = sorted(range(N), key=lambda i: (dE[i], i))      # largest decrease first
+    idx, _ = orc.decompose(Q, x, m, k, seed=0, method=orc.IFD | orc.SIGNED, conditioned=False)
+    for j in range(m):
+        np.testing.assert_array_equal(idx[j], np.sort(rank[j:j + k]))
+    with pytest.raises(RuntimeError):
+        orc.decompose(Q, x, m, k, seed=0, method=orc.RANDOM | orc.SIGNED)
+    with pytest.raises(RuntimeError):
+        orc.decompose(Q, x, m, k, seed=0, method=orc.IFD | 32)
+
+
 def test_ifd_windows_follow_impact_ranking(orc):
     N, m, k = 50, 6, 5
     Q = synth.symmetric_q(N, seed=41)
@@ -411,9 +427,10 @@ def _traverse_py(strong, rank, root, k, bfs):
     return sorted(order)
 
 
+@pytest.mark.parametrize("signed", [False, True])
 @pytest.mark.parametrize("kind", ["dense", "maxcut", "sparse"])
 @pytest.mark.parametrize("k", [2, 4, 7])
-def test_bfs_pfs_against_direct_traversal(orc, kind, k):
+def test_bfs_pfs_against_direct_traversal(orc, kind, k, signed):
     N = 30
     if kind == "dense":
         Q = synth.symmetric_q(N, seed=71)
@@ -423,10 +440,12 @@ def test_bfs_pfs_against_direct_traversal(orc, kind, k):
         Q = synth.maxcut_graph_q(N, seed=73, edges=12)        # isolated vertices force restarts
     x = synth.bits(74, N)
     dE = orc.impact(Q, x)
-    rank = sorted(range(N), key=lambda i: (-abs(dE[i]), i))
+    # default ranking |dE| descending; signed ranking dE ascending (largest decrease first)
+    rank = sorted(range(N), key=(lambda i: (dE[i], i)) if signed else (lambda i: (-abs(dE[i]), i)))
     strong = _strong_sets(Q, k)
+    flag = orc.SIGNED if signed else 0
     for method, bfs in ((orc.BFS, True), (orc.PFS, False)):
-        idx, _ = orc.decompose(Q, x, N, k, seed=0, method=method, conditioned=False)
+        idx, _ = orc.decompose(Q, x, N, k, seed=0, method=method | flag, conditioned=False)
         for j in range(N):
             assert idx[j].tolist() == _traverse_py(strong, rank, rank[j], k, bfs), (kind, k, j, bfs)
 
