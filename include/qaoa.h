@@ -286,7 +286,7 @@ qaoa_status qaoa_plain_solve(qaoa_ctx* ctx, int n, int p, const float* Q, const 
 /* DQAOA decomposition and aggregation (host, FP64)                                          */
 /* ---------------------------------------------------------------------------------------- */
 
-enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1, DQAOA_BFS = 2, DQAOA_PFS = 3 };
+enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1, DQAOA_BFS = 2, DQAOA_PFS = 3, DQAOA_SIGNED_IMPACT = 16 };
 
 /* Section V-A. Sub-QUBO index sets: idx[m*k] (host int32), each row sorted ascending.
  *   DQAOA_RANDOM: row j draws k distinct variables of 0..N-1 uniformly without replacement,
@@ -302,6 +302,10 @@ enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1, DQAOA_BFS = 2, DQAOA_PFS = 3 };
  *     PFS: the next variable is the best-ranked unselected strong neighbour of any selected one.
  *     A traversal that runs out restarts at the best-ranked unselected variable. Needs m <= N;
  *     Q and x required.
+ *   DQAOA_SIGNED_IMPACT, or-ed with DQAOA_IFD, DQAOA_BFS or DQAOA_PFS: the ranking is impact_i
+ *     ascending (the largest energy decrease first, ties: smaller index) instead of |impact_i|
+ *     descending; Section V-A does not say which one "higher impact" means. Not valid with
+ *     DQAOA_RANDOM; any other bit is invalid.
  * Q: N*N row-major symmetric doubles (host), x: N bytes 0/1 (host; RANDOM may pass NULL). */
 qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t* x, int method, int m,
                                int k, uint64_t seed, uint64_t cycle, int32_t* idx);
@@ -342,7 +346,7 @@ typedef struct dqaoa_session dqaoa_session;
 
 /* gamma, beta: p host doubles (the fixed parameters every sub-QUBO uses); K: top-k candidates
  * per sub-QUBO fed to the merge (1..16); method: one of DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS,
- * DQAOA_PFS. Allocates. */
+ * DQAOA_PFS, the last three optionally | DQAOA_SIGNED_IMPACT. Allocates. */
 qaoa_status dqaoa_session_create(qaoa_ctx* ctx, int N, int m, int k, int p, int K, int method,
                                  int conditioned, const double* gamma, const double* beta,
                                  dqaoa_session** out);

@@ -20,6 +20,7 @@ QAOA_OK, QAOA_E_INVALID, QAOA_E_NOMEM, QAOA_E_CUDA, QAOA_E_TIMEOUT, QAOA_E_UNSUP
 QAOA_INST_GRAD = 1
 QAOA_TIER_AUTO, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM = 0, 2, 3
 DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS, DQAOA_PFS = 0, 1, 2, 3
+DQAOA_SIGNED_IMPACT = 16   # or-ed with IFD / BFS / PFS: rank by impact ascending
 
 # Every symbol include/qaoa.h declares.
 EXPORTS = [

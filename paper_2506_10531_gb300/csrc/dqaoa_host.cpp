@@ -76,7 +76,7 @@ int draw_random(int N, int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx
 
 // Impact factor of each variable (the energy change of flipping it) and the ranking by
 // |impact| descending, ties to the smaller index.
-static std::vector<int32_t> impact_order(const double* Q, int N, const uint8_t* x) {
+static std::vector<int32_t> impact_order(const double* Q, int N, const uint8_t* x, bool signed_rank) {
     std::vector<double> imp(N);
     // h_i = sum over j != i with x_j = 1, ascending j. Eight rows advance together (independent
     // sums, each in its own order); a skipped term adds +0.0, which leaves every sum unchanged.
@@ -105,14 +105,18 @@ static std::vector<int32_t> impact_order(const double* Q, int N, const uint8_t* 
     }
     std::vector<int32_t> order(N);
     for (int i = 0; i < N; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int32_t a, int32_t b) { return std::fabs(imp[a]) > std::fabs(imp[b]); });
+    // default: |impact| descending; signed: impact ascending (largest energy decrease first)
+    if (signed_rank)
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return imp[a] < imp[b]; });
+    else
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return std::fabs(imp[a]) > std::fabs(imp[b]); });
     return order;
 }
 
 // IFD (Algorithm 1): row j is the window ranking[j .. j+k-1].
-int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx) {
-    const std::vector<int32_t> order = impact_order(Q, N, x);
+int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx, bool signed_rank) {
+    const std::vector<int32_t> order = impact_order(Q, N, x, signed_rank);
     for (int j = 0; j < m; ++j) {
         int32_t* S = idx + (int64_t)j * k;
         std::copy(order.begin() + j, order.begin() + j + k, S);
@@ -162,13 +166,13 @@ void build_strong_graph(const double* Q, int N, int k, StrongGraph* g) {
 // exhausted traversal restarts at the best-ranked unselected variable. g: the strong graph of
 // (Q, k), built here when null.
 int draw_graph(const double* Q, int N, const uint8_t* x, int method, int m, int k, int32_t* idx,
-               const StrongGraph* g) {
+               const StrongGraph* g, bool signed_rank) {
     StrongGraph local;
     if (!g) {
         build_strong_graph(Q, N, k, &local);
         g = &local;
     }
-    const std::vector<int32_t> order = impact_order(Q, N, x);
+    const std::vector<int32_t> order = impact_order(Q, N, x, signed_rank);
     const int64_t* off = g->off.data();
     const int32_t* nbr = g->nbr.data();
     std::vector<uint8_t> inS(N), inF(N);

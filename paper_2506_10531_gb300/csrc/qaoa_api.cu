@@ -967,20 +967,24 @@ extern "C" qaoa_status qaoa_plain_solve(qaoa_ctx* c, int n, int p, const float* 
 extern "C" qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t* x, int method, int m,
                                           int k, uint64_t seed, uint64_t cycle, int32_t* idx) {
     if (N < 1 || m < 1 || k < 1 || k > N || !idx) return fail(QAOA_E_INVALID, "draw: N=%d m=%d k=%d", N, m, k);
+    const int base = method & 15;
+    const bool sgn = (method & DQAOA_SIGNED_IMPACT) != 0;
+    if ((method & ~31) || base > DQAOA_PFS || (sgn && base == DQAOA_RANDOM))
+        return fail(QAOA_E_INVALID, "unknown decomposition method %d", method);
     if (method == DQAOA_RANDOM) {
         draw_random(N, m, k, seed, cycle, idx);
         return QAOA_OK;
     }
-    if (method == DQAOA_IFD) {
+    if (base == DQAOA_IFD) {
         if (!Q || !x) return fail(QAOA_E_INVALID, "IFD needs Q and x");
         if (m + k - 1 > N) return fail(QAOA_E_INVALID, "IFD needs m + k - 1 <= N");
-        draw_ifd(Q, N, x, m, k, idx);
+        draw_ifd(Q, N, x, m, k, idx, sgn);
         return QAOA_OK;
     }
-    if (method == DQAOA_BFS || method == DQAOA_PFS) {
+    if (base == DQAOA_BFS || base == DQAOA_PFS) {
         if (!Q || !x) return fail(QAOA_E_INVALID, "BFS / PFS need Q and x");
         if (m > N) return fail(QAOA_E_INVALID, "BFS / PFS need m <= N");
-        draw_graph(Q, N, x, method, m, k, idx);
+        draw_graph(Q, N, x, base, m, k, idx, nullptr, sgn);
         return QAOA_OK;
     }
     return fail(QAOA_E_INVALID, "unknown decomposition method %d", method);
@@ -1065,10 +1069,12 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
                                             int conditioned, const double* gamma, const double* beta,
                                             dqaoa_session** out) {
     if (!c || !out || N < 1 || m < 1 || k < 1 || k > N || k > NMAX || p < 1 || p > PMAX || K < 1 ||
-        K > KMAX || (uint64_t)K > (1ull << k) || !gamma || !beta || method < DQAOA_RANDOM || method > DQAOA_PFS)
+        K > KMAX || (uint64_t)K > (1ull << k) || !gamma || !beta || (method & ~31) || (method & 15) > DQAOA_PFS ||
+        method == (DQAOA_RANDOM | DQAOA_SIGNED_IMPACT))
         return fail(QAOA_E_INVALID, "session_create: bad arguments");
-    if (method == DQAOA_IFD && m + k - 1 > N) return fail(QAOA_E_INVALID, "IFD needs m + k - 1 <= N");
-    if ((method == DQAOA_BFS || method == DQAOA_PFS) && m > N) return fail(QAOA_E_INVALID, "BFS / PFS need m <= N");
+    if ((method & 15) == DQAOA_IFD && m + k - 1 > N) return fail(QAOA_E_INVALID, "IFD needs m + k - 1 <= N");
+    if (((method & 15) == DQAOA_BFS || (method & 15) == DQAOA_PFS) && m > N)
+        return fail(QAOA_E_INVALID, "BFS / PFS need m <= N");
     *out = nullptr;
     CK(cudaSetDevice(c->device));
     dqaoa_session* s = new dqaoa_session();
@@ -1173,12 +1179,12 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     qaoa_status r = QAOA_OK;
     if (s->method == DQAOA_RANDOM && s->next_valid && s->next_seed == seed && s->next_cycle == cycle)
         std::memcpy(s->idx_h, s->next_idx.data(), (size_t)m * k * sizeof(int32_t));
-    else if (s->method == DQAOA_BFS || s->method == DQAOA_PFS) {
+    else if ((s->method & 15) == DQAOA_BFS || (s->method & 15) == DQAOA_PFS) {
         if (q_changed || !s->graph_valid) {
             build_strong_graph(Q, N, k, &s->graph);
             s->graph_valid = true;
         }
-        draw_graph(Q, N, x, s->method, m, k, s->idx_h, &s->graph);
+        draw_graph(Q, N, x, s->method & 15, m, k, s->idx_h, &s->graph, (s->method & DQAOA_SIGNED_IMPACT) != 0);
     } else
         r = dqaoa_draw_indices(Q, N, x, s->method, m, k, seed, cycle, s->idx_h);
     s->next_valid = false;

@@ -7,7 +7,7 @@
 
 namespace qaoa {
 int draw_random(int N, int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx);
-int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx);
+int draw_ifd(const double* Q, int N, const uint8_t* x, int m, int k, int32_t* idx, bool signed_rank = false);
 // Strong-interaction graph of the BFS / PFS decompositions for (Q, k), CSR form.
 struct StrongGraph {
     int N = 0, k = 0;
@@ -18,7 +18,7 @@ struct StrongGraph {
 };
 void build_strong_graph(const double* Q, int N, int k, StrongGraph* g);
 int draw_graph(const double* Q, int N, const uint8_t* x, int method, int m, int k, int32_t* idx,
-               const StrongGraph* g = nullptr);
+               const StrongGraph* g = nullptr, bool signed_rank = false);
 void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, const int32_t* idx,
                     int conditioned, double* Qsub);
 // State the merge can carry from one call to the next on the same Q: h = Qx, E(x), tau.

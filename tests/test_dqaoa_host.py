@@ -38,10 +38,11 @@ def test_ifd_decompose_bit_exact(orc):
     N, m, k = 300, 45, 20
     Q = synth.symmetric_q(N, seed=4)
     x = synth.bits(5, N)
-    i_l, q_l = lib_decompose(Q, x, m, k, 0, 0, q.DQAOA_IFD, True)
-    i_o, q_o = orc.decompose(Q, x, m, k, 0, 0, method=orc.IFD, conditioned=True)
-    np.testing.assert_array_equal(i_l, i_o)
-    np.testing.assert_array_equal(q_l, q_o)
+    for flag, oflag in ((0, 0), (q.DQAOA_SIGNED_IMPACT, orc.SIGNED)):
+        i_l, q_l = lib_decompose(Q, x, m, k, 0, 0, q.DQAOA_IFD | flag, True)
+        i_o, q_o = orc.decompose(Q, x, m, k, 0, 0, method=orc.IFD | oflag, conditioned=True)
+        np.testing.assert_array_equal(i_l, i_o)
+        np.testing.assert_array_equal(q_l, q_o)
 
 
 @pytest.mark.parametrize("kind,N,m,k", [("maxcut", 400, 200, 12), ("dense", 300, 300, 20),
@@ -54,11 +55,12 @@ def test_bfs_pfs_decompose_bit_exact(orc, kind, N, m, k):
     else:
         Q = synth.symmetric_q(N, seed=23)
     x = synth.bits(24, N)
-    for lm, om in ((q.DQAOA_BFS, orc.BFS), (q.DQAOA_PFS, orc.PFS)):
-        i_l, q_l = lib_decompose(Q, x, m, k, 0, 0, lm, True)
-        i_o, q_o = orc.decompose(Q, x, m, k, 0, 0, method=om, conditioned=True)
-        np.testing.assert_array_equal(i_l, i_o)
-        np.testing.assert_array_equal(q_l, q_o)
+    for flag, oflag in ((0, 0), (q.DQAOA_SIGNED_IMPACT, orc.SIGNED)):
+        for lm, om in ((q.DQAOA_BFS, orc.BFS), (q.DQAOA_PFS, orc.PFS)):
+            i_l, q_l = lib_decompose(Q, x, m, k, 0, 0, lm | flag, True)
+            i_o, q_o = orc.decompose(Q, x, m, k, 0, 0, method=om | oflag, conditioned=True)
+            np.testing.assert_array_equal(i_l, i_o)
+            np.testing.assert_array_equal(q_l, q_o)
 
 
 def test_draw_indices_matches_decompose(orc):
@@ -99,6 +101,9 @@ def test_host_argument_errors():
             q.dqaoa_draw_indices(None, 10, None, meth, 4, 3, 0, 0, np.zeros(12, np.int32))
     with pytest.raises(q.QaoaError):
         q.dqaoa_draw_indices(Qz, 10, xz, 4, 4, 3, 0, 0, np.zeros(12, np.int32))
+    for bad in (q.DQAOA_RANDOM | q.DQAOA_SIGNED_IMPACT, q.DQAOA_IFD | 32, 4 | q.DQAOA_SIGNED_IMPACT):
+        with pytest.raises(q.QaoaError):
+            q.dqaoa_draw_indices(Qz, 10, xz, bad, 4, 3, 0, 0, np.zeros(12, np.int32))
     idx = np.array([[0, 12]], dtype=np.int32)
     with pytest.raises(q.QaoaError):
         q.dqaoa_merge(np.zeros((10, 10)), 10, np.zeros(10, np.uint8), 1, 2, idx, 1,
