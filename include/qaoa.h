@@ -143,8 +143,11 @@ qaoa_status qaoa_sample(qaoa_ctx* ctx, int n, const void* psi, int64_t shots, co
  * (the caller evaluates f there and calls qaoa_cobyla_tell), or writes the best point found and
  * returns 0 once rho has reached rhoend or maxfun values have been told. So many independent
  * minimisations can have their points evaluated together, e.g. one batched plan launch for every
- * sub-QUBO of a batch. nvar 1..256, 0 < rhoend <= rhobeg, maxfun >= nvar + 2. Non-finite values
- * count as +inf. */
+ * sub-QUBO of a batch. nvar 1..256, 0 < rhoend <= rhobeg, maxfun >= nvar + 2, else create returns
+ * QAOA_E_INVALID and allocates nothing. Non-finite values count as +inf. x: nvar host doubles
+ * (the caller's). tell on a finished minimisation returns QAOA_E_INVALID; ask with a NULL state
+ * or x returns 0. The state is owned by the caller and freed by qaoa_cobyla_destroy (NULL is a
+ * no-op). Not thread-safe per state; independent states may be used from different threads. */
 typedef struct qaoa_cobyla qaoa_cobyla;
 qaoa_status qaoa_cobyla_create(int nvar, const double* x0, double rhobeg, double rhoend, int maxfun,
                                qaoa_cobyla** out);
