@@ -316,14 +316,19 @@ qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t* x, int met
 /* Section V-A sub-QUBO matrices for given index sets: Qsub[j] = Q[S_j, S_j] (k*k full
  * symmetric, host doubles). With conditioned != 0 the couplings to the fixed variables
  * outside S_j are folded into the diagonal, Qsub[a][a] += 2 sum_{l not in S_j} Q[S_a][l] x_l,
- * so the sub-QUBO energy of y is E(x with x_S = y) minus a constant. */
+ * so the sub-QUBO energy of y is E(x with x_S = y) minus a constant. The paper fixes the value
+ * of that sum, not the order of its FP64 additions: here it is eight interleaved partial sums
+ * (l = r mod 8, each ascending) combined pairwise, the order dqaoa_subqubo_build uses on the
+ * device, so host and device matrices agree bit for bit; against any other order (a plain
+ * ascending sum) an entry differs by FP64 rounding only. */
 qaoa_status dqaoa_decompose(const double* Q, int N, const uint8_t* x, int method, int conditioned,
                             int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx,
                             double* Qsub);
 
 /* The same sub-QUBO matrices built on the device, as FP32 for the complex64 solver:
  * Q_dev N*N doubles, x_dev N bytes, idx_dev m*k int32, qsub_dev m*k*k floats (all device).
- * The conditioning sum is accumulated in FP64, ascending l. Async. */
+ * The conditioning sum is accumulated in FP64 in the order dqaoa_decompose states (eight
+ * interleaved partial sums combined pairwise) and rounded once to FP32. Async. */
 qaoa_status dqaoa_subqubo_build(qaoa_ctx* ctx, const double* Q_dev, int N, const uint8_t* x_dev,
                                 int m, int k, const int32_t* idx_dev, int conditioned,
                                 float* qsub_dev, qaoa_stream_t stream);

@@ -427,9 +427,8 @@ static void traverse(const double* Q, int N, const double* thr, const int32_t* r
  * Qsub[j] = Q[S_j, S_j] as a full symmetric k x k matrix. With conditioned != 0 the couplings to
  * the fixed variables outside S_j are folded into the diagonal:
  *   Qsub[a][a] += 2 sum_{l not in S_j} Q[S_a][l] x_l,
- * so that the sub-QUBO energy of y equals E(x with x_S = y) minus a constant. The paper fixes the
- * value, not the order of the FP64 additions; the order used here is eight partial sums
- * s_r over l = r (mod 8), each in ascending l, combined as ((s0+s1)+(s2+s3))+((s4+s5)+(s6+s7)).
+ * so that the sub-QUBO energy of y equals E(x with x_S = y) minus a constant. The sum is the plain
+ * FP64 sum over l = 0..N-1 in ascending order.
  */
 int orc_decompose(const double* Q, int N, const uint8_t* x, int method_flags, int conditioned, int m,
                   int k, uint64_t seed, uint64_t cycle, int32_t* idx, double* Qsub)
@@ -479,13 +478,9 @@ int orc_decompose(const double* Q, int N, const uint8_t* x, int method_flags, in
             memset(inS, 0, (size_t)N);
             for (int a = 0; a < k; ++a) inS[S[a]] = 1;
             for (int a = 0; a < k; ++a) {
-                double sr[8];
-                for (int r = 0; r < 8; ++r) {
-                    sr[r] = 0.0;
-                    for (int l = r; l < N; l += 8)
-                        if (!inS[l] && x[l]) sr[r] += Q[(int64_t)S[a] * N + l];
-                }
-                const double h = ((sr[0] + sr[1]) + (sr[2] + sr[3])) + ((sr[4] + sr[5]) + (sr[6] + sr[7]));
+                double h = 0.0;
+                for (int l = 0; l < N; ++l)
+                    if (!inS[l] && x[l]) h += Q[(int64_t)S[a] * N + l];
                 Qs[a * k + a] += 2.0 * h;
             }
         }

@@ -1,5 +1,7 @@
 """Host DQAOA steps of libqaoa (index draws, sub-QUBO matrices, merge) against the FP64 oracle:
-bit-exact on integer results and on the FP64 sub-QUBO matrices. Host code only, no GPU."""
+bit-exact on integer results and on the copied entries of the sub-QUBO matrices; the conditioned
+diagonal (a sum of up to N FP64 terms, whose order the paper does not fix) within the rounding
+bound of two summation orders. Host code only, no GPU."""
 import numpy as np
 import pytest
 
@@ -11,6 +13,42 @@ import paper_2506_10531_gb300 as q
 def built():
     from paper_2506_10531_gb300 import build
     build.build()
+
+
+U64 = 2.0 ** -53
+
+
+def qsub_diag_bound(Q, x, idx, conditioned):
+    """Per-entry bound on |Qsub_lib - Qsub_oracle| for m x k x k sub-QUBO matrices.
+
+    Off-diagonal entries are copies of Q (bound 0). A conditioned diagonal entry is
+    Q_aa + 2 sum_{l not in S, x_l = 1} Q[S_a][l]: two FP64 summation orders of the same A terms
+    (absolute sum T) each lie within (A-1) u T of the exact sum (Higham, Accuracy and Stability,
+    eq. 4.4), and the final doubling and addition round once more."""
+    m, k = idx.shape
+    bound = np.zeros((m, k, k))
+    if not conditioned:
+        return bound
+    N = Q.shape[0]
+    xs = np.asarray(x, dtype=bool)
+    for j in range(m):
+        out = xs.copy()
+        out[idx[j]] = False
+        for a in range(k):
+            T = float(np.abs(Q[idx[j][a], out]).sum())
+            A = int(out.sum())
+            bound[j, a, a] = 2.0 * (2.0 * A * U64 * T) + 4.0 * U64 * (abs(Q[idx[j][a], idx[j][a]]) + 2.0 * T)
+    return bound
+
+
+def assert_qsub_close(got, want, bound, what=""):
+    """Element-wise |got - want| <= bound; copies (bound 0) must be equal. Returns how many
+    entries differ at all (reported by the callers)."""
+    diff = np.abs(got - want)
+    bad = diff > bound
+    assert not bad.any(), f"{what}: {int(bad.sum())} entries beyond the rounding bound, max excess " \
+                          f"{float((diff - bound)[bad].max())}"
+    return int((diff > 0).sum())
 
 
 def lib_decompose(Q, x, m, k, seed, cycle, method, conditioned):
@@ -31,7 +69,8 @@ def test_random_decompose_bit_exact(orc, N, m, k, seed, cycle):
         i_l, q_l = lib_decompose(Q, x, m, k, seed, cycle, q.DQAOA_RANDOM, cond)
         i_o, q_o = orc.decompose(Q, x, m, k, seed, cycle, method=orc.RANDOM, conditioned=cond)
         np.testing.assert_array_equal(i_l, i_o)
-        np.testing.assert_array_equal(q_l, q_o)          # same FP64 sums in the same order
+        nd = assert_qsub_close(q_l, q_o, qsub_diag_bound(Q, x, i_o, cond), f"cond={cond}")
+        print(f"N={N} m={m} k={k} conditioned={cond}: {nd} of {q_o.size} entries differ by rounding")
 
 
 def test_ifd_decompose_bit_exact(orc):
@@ -42,7 +81,7 @@ def test_ifd_decompose_bit_exact(orc):
         i_l, q_l = lib_decompose(Q, x, m, k, 0, 0, q.DQAOA_IFD | flag, True)
         i_o, q_o = orc.decompose(Q, x, m, k, 0, 0, method=orc.IFD | oflag, conditioned=True)
         np.testing.assert_array_equal(i_l, i_o)
-        np.testing.assert_array_equal(q_l, q_o)
+        assert_qsub_close(q_l, q_o, qsub_diag_bound(Q, x, i_o, True), "IFD")
 
 
 @pytest.mark.parametrize("kind,N,m,k", [("maxcut", 400, 200, 12), ("dense", 300, 300, 20),
@@ -60,7 +99,21 @@ def test_bfs_pfs_decompose_bit_exact(orc, kind, N, m, k):
             i_l, q_l = lib_decompose(Q, x, m, k, 0, 0, lm | flag, True)
             i_o, q_o = orc.decompose(Q, x, m, k, 0, 0, method=om | oflag, conditioned=True)
             np.testing.assert_array_equal(i_l, i_o)
-            np.testing.assert_array_equal(q_l, q_o)
+            assert_qsub_close(q_l, q_o, qsub_diag_bound(Q, x, i_o, True), f"{kind} method {lm}")
+
+
+def test_draw_indices_worked_examples():
+    # the library's draw against the index sets worked by hand from published SplitMix64
+    # outputs (tests/golden/random_draw.json; Section V-A random selection, reading O5)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "random_draw.json")) as f:
+        cases = json.load(f)["cases"]
+    for c in cases:
+        N, k, j = c["N"], c["k"], c["j"]
+        idx = np.zeros((j + 1, k), dtype=np.int32)
+        q.dqaoa_draw_indices(None, N, None, q.DQAOA_RANDOM, j + 1, k, int(c["seed"]), c["cycle"], idx)
+        assert list(idx[j]) == c["S_sorted"], c["note"]
 
 
 def test_draw_indices_matches_decompose(orc):

@@ -33,6 +33,55 @@ def test_splitmix64_published_vector(orc):
     assert [int(v) for v in synth.splitmix64(1234567, 5)] == want
 
 
+def test_random_draw_worked_examples(orc):
+    # Section V-A random selection, pinned by index sets worked by hand from published SplitMix64
+    # outputs and Lemire's bounded draw (tests/golden/random_draw.json): the row state is
+    # seed ^ (cycle * golden gamma) ^ j, step i swaps positions i and i + r, and a draw whose low
+    # word is below (2^64 - range) mod range is redrawn. The cases include a rejected draw, a draw
+    # accepted with the low word exactly at the threshold, and rows / cycles reached only by xor.
+    import json
+    with open(os.path.join(HERE, "golden", "random_draw.json")) as f:
+        gold = json.load(f)
+    pub = {k: [int(v) for v in vals] for k, vals in gold["published_outputs"].items() if not k.startswith("_")}
+    assert pub["1234567"][:len(_golden_ints("splitmix64_seed1234567.txt"))] == \
+        _golden_ints("splitmix64_seed1234567.txt")[:len(pub["1234567"])]
+    M64, PHI = (1 << 64) - 1, 0x9E3779B97F4A7C15
+    saw_reject = saw_boundary = False
+    for c in gold["cases"]:
+        N, k, j, cyc, seed = c["N"], c["k"], c["j"], c["cycle"], int(c["seed"])
+        state = seed ^ ((cyc * PHI) & M64) ^ j
+        assert state == int(c["state"]), c["note"]
+        xs = [int(d["x"]) for st in c["steps"] for d in st["draws"]]
+        # the worked draws are the generator's stream from that state ...
+        assert [int(v) for v in orc.splitmix64(state, len(xs))] == xs, c["note"]
+        # ... which is a published stream where the case says so
+        if c["stream_seed"] in pub:
+            ref = pub[c["stream_seed"]]
+            tail = xs[len(xs) - len(ref):] if c["stream_seed"] == "0" else xs[:len(ref)]
+            assert tail[:len(ref)] == ref[:len(tail)], c["note"]
+        # the worked arithmetic is self-consistent (a check of the golden file, not of the oracle)
+        perm = list(range(N))
+        for st in c["steps"]:
+            rng = N - st["i"]
+            assert st["range"] == rng
+            for d in st["draws"]:
+                prod = int(d["x"]) * rng
+                assert int(d["x_times_range_hi"]) == prod >> 64 and int(d["x_times_range_lo"]) == prod & M64
+                assert int(d["threshold"]) == ((1 << 64) - rng) % rng
+                assert d["rejected"] == (int(d["x_times_range_lo"]) < int(d["threshold"]))
+                saw_reject |= d["rejected"]
+                saw_boundary |= int(d["x_times_range_lo"]) == int(d["threshold"])
+            assert not st["draws"][-1]["rejected"] and st["r"] == int(st["draws"][-1]["x_times_range_hi"])
+            i, r = st["i"], st["r"]
+            perm[i], perm[i + r] = perm[i + r], perm[i]
+            assert perm[:i + 1] == st["perm_prefix"]
+        assert sorted(perm[:k]) == c["S_sorted"]
+        # the oracle's decomposition reproduces the worked index set in row j
+        idx, _ = orc.decompose(np.zeros((N, N)), None, j + 1, k, seed, cyc, conditioned=False)
+        assert list(idx[j]) == c["S_sorted"], c["note"]
+    assert saw_reject and saw_boundary
+
+
 # ---------------------------------------------------------------------------------------------
 # QUBO energies: E(z) = z^T Q z
 # ---------------------------------------------------------------------------------------------
