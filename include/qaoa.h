@@ -170,7 +170,9 @@ void qaoa_cobyla_destroy(qaoa_cobyla* s);
  *   idx: k uint64, prob: k doubles (may be NULL); all device pointers. Same results and order
  *   rules as qaoa_expect / qaoa_topk. Async on `stream`.
  * The first call on a device looks up the array's device address with that device current;
- * make that first call before any stream capture. Every call uses the same array, which keeps
+ * make that first call before any stream capture. The address is kept with the id of the
+ * device's context, so the first call after that context is replaced (cudaDeviceReset) looks it
+ * up again; that call too belongs outside a capture. Every call uses the same array, which keeps
  * the last call's contents (each call writes every slot before reading it, so nothing needs
  * clearing); calls whose work overlaps on the GPU (other streams, other host threads) race on it
  * and must be ordered by the caller. */

@@ -44,8 +44,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
 
+    headers = [d for d in _inputs() if d.endswith((".h", ".cuh"))]
+    newest_header = max(os.path.getmtime(h) for h in headers)
+
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        # an object newer than its source and every header is reused (the flags are fixed)
+        if (not force and os.path.exists(obj)
+                and os.path.getmtime(obj) >= max(os.path.getmtime(os.path.join(CSRC, src)), newest_header)):
+            return obj
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + NVCC_FLAGS
         if src.endswith(".cpp"):
             cmd = [nvcc, "-x", "cu", "-c", os.path.join(CSRC, src), "-o", obj] + NVCC_FLAGS

@@ -127,6 +127,23 @@ void plan_next(qaoa_cobyla* s) {
         s->opt = 0;
         for (int j = 1; j <= n; ++j)
             if (s->F[j] < s->F[s->opt]) s->opt = j;
+        if (!(s->F[s->opt] < HUGE_VAL)) {   // no finite value anywhere: nothing to model
+            s->phase = 2;
+            return;
+        }
+        // a vertex whose value was not finite cannot enter the linear model: move it halfway
+        // towards the best vertex and evaluate it again (a geometry step of half its length)
+        for (int j = 0; j <= n; ++j) {
+            if (j == s->opt || s->F[j] < HUGE_VAL) continue;
+            const double* xo = vert(s, s->opt);
+            const double* v = vert(s, j);
+            s->trial.assign(n, 0.0);
+            for (int k = 0; k < n; ++k) s->trial[k] = xo[k] + 0.5 * (v[k] - xo[k]);
+            s->trial_kind = 1;
+            s->geo_j = j;
+            s->phase = 1;
+            return;
+        }
         s->rows.clear();
         for (int j = 0; j <= n; ++j)
             if (j != s->opt) s->rows.push_back(j);
@@ -257,6 +274,13 @@ extern "C" qaoa_status qaoa_cobyla_tell(qaoa_cobyla* s, double f) {
     if (s->trial_kind == 1) {
         std::memcpy(vert(s, s->geo_j), s->trial.data(), sizeof(double) * n);
         s->F[s->geo_j] = f;
+        plan_next(s);
+        return QAOA_OK;
+    }
+    // a trust-region trial without a finite value stays out of the simplex: treated as a poor
+    // step, it leads to a smaller radius (after a geometry repair if one is due)
+    if (!(f < HUGE_VAL)) {
+        s->poor = true;
         plan_next(s);
         return QAOA_OK;
     }

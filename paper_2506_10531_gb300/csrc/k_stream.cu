@@ -925,14 +925,6 @@ cudaError_t launch_stream_grad_reduce(bool dbl, const StreamPass* passes, int S,
     return cudaGetLastError();
 }
 
-int reduce_parts(int n) {
-    const uint64_t D = 1ull << n;
-    uint64_t b = (D + 256 * 32 - 1) / (256 * 32);
-    if (b > 1024) b = 1024;
-    if (b < 1) b = 1;
-    return (int)b;
-}
-
 cudaError_t launch_reduce_state(bool dbl, int n, const void* psi, const void* E, int k,
                                 double* part_expect, double* part_topp, uint32_t* part_topz,
                                 double* expect, uint64_t* topk_idx, double* topk_prob,

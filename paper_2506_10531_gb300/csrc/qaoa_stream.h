@@ -74,7 +74,12 @@ size_t stream_adj_smem_bytes(bool dbl);
 cudaError_t launch_energy(bool dbl, int n, const void* Q, void* E, cudaStream_t st);
 // Energies of `count` streaming instances (E written through insts[i].E from insts[i].Q).
 cudaError_t launch_energy_batch(bool dbl, int n, const void* insts, int count, cudaStream_t st);
-int reduce_parts(int n);
+// Blocks of the standalone reduction of a 2^n state: one per 8192 amplitudes, 1 to 1024.
+constexpr int reduce_parts(int n) {
+    return (int)(((1ull << n) + 256 * 32 - 1) / (256 * 32) > 1024 ? 1024
+                 : ((1ull << n) + 256 * 32 - 1) / (256 * 32) < 1 ? 1
+                 : ((1ull << n) + 256 * 32 - 1) / (256 * 32));
+}
 cudaError_t launch_reduce_state(bool dbl, int n, const void* psi, const void* E, int k,
                                 double* part_expect, double* part_topp, uint32_t* part_topz,
                                 double* expect, uint64_t* topk_idx, double* topk_prob,

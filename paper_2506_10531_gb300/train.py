@@ -174,18 +174,28 @@ def cobyla_train(batch: QAOABatch, rhobeg: float = 0.2, rhoend: float = 1e-4, ma
     IV): one COBYLA-type minimisation per instance over its (gamma, beta), all advanced in
     lockstep, each round one plan launch evaluating <C> of every instance. The best parameters
     end up in the batch's parameter pool (FP32). Returns (best <C> per instance, rounds)."""
-    offs = np.cumsum([0] + [2 * p for p in batch.ps])
-    flat = batch.params.detach().cpu().numpy().astype(np.float64)
-    x0s = [flat[offs[i]:offs[i + 1]] for i in range(batch.count)]
+    import contextlib
+    dev = batch.params.device
+    # every copy into the pool and every read of <C> is ordered on the stream the plan runs on
+    if dev.type == "cuda":
+        s = (torch.cuda.current_stream(dev) if stream is None else
+             torch.cuda.ExternalStream(stream, device=dev) if isinstance(stream, int) else stream)
+        on_stream = torch.cuda.stream(s)
+    else:
+        s, on_stream = None, contextlib.nullcontext()
+    with on_stream:
+        offs = np.cumsum([0] + [2 * p for p in batch.ps])
+        flat = batch.params.detach().cpu().numpy().astype(np.float64)
+        x0s = [flat[offs[i]:offs[i + 1]] for i in range(batch.count)]
 
-    def evaluate(points):
-        buf = np.concatenate(points).astype(np.float32)
-        batch.params.copy_(torch.from_numpy(buf).to(batch.params.device))
-        batch.run(stream)
-        if batch.params.is_cuda:
-            torch.cuda.synchronize(batch.params.device)
-        return batch.expect.detach().cpu().numpy()
+        def evaluate(points):
+            buf = np.concatenate(points).astype(np.float32)
+            batch.params.copy_(torch.from_numpy(buf).to(dev))
+            batch.run(s)
+            return batch.expect.detach().cpu().numpy()
 
-    best, fbest, _, rounds = cobyla_lockstep(x0s, evaluate, rhobeg, rhoend, maxfun)
-    batch.params.copy_(torch.from_numpy(np.concatenate(best).astype(np.float32)).to(batch.params.device))
+        best, fbest, _, rounds = cobyla_lockstep(x0s, evaluate, rhobeg, rhoend, maxfun)
+        batch.params.copy_(torch.from_numpy(np.concatenate(best).astype(np.float32)).to(dev))
+        if s is not None:
+            s.synchronize()
     return np.array(fbest), rounds

@@ -51,6 +51,22 @@ def test_budget_and_best_point():
     assert fv == min(told) and fv < -1.0
 
 
+def test_non_finite_values_stay_out_of_the_model():
+    # an objective that is NaN (or +inf) on part of the space, with its minimum near the edge of
+    # that region: the failed evaluations are neither kept as simplex values nor allowed to stop
+    # the search early
+    a = np.array([1.0, -0.5])
+    for bad in (np.nan, np.inf):
+        def f(x, bad=bad):
+            return bad if x[0] > 1.2 else float(np.sum((x - a) ** 2))
+        x, fv, n, told = minimise(f, np.zeros(2), 1.0, 1e-6, 2000)
+        assert any(not np.isfinite(v) for v in told)         # the bad region was hit
+        assert np.isfinite(fv) and np.abs(x - a).max() < 1e-4 and fv < 1e-8
+    # a start inside the bad region has nothing to work from: the run ends with no finite value
+    x, fv, n, told = minimise(lambda x: np.nan, np.zeros(2), 0.5, 1e-3, 50)
+    assert not np.isfinite(fv) and n == 3
+
+
 def test_protocol_errors():
     with pytest.raises(q.QaoaError):
         q.Cobyla(np.zeros(3), 0.1, 0.2, 100)        # rhoend > rhobeg

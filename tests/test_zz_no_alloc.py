@@ -67,6 +67,18 @@ def test_static_scratch_matches_workspace_entry_points(q):
                 assert abs(ex.item() - ref_ex.item()) <= 1e-5 * absq, (n, call)
                 np.testing.assert_array_equal(ti.cpu().numpy(), ref_i.cpu().numpy())
                 np.testing.assert_allclose(tp.cpu().numpy(), ref_p.cpu().numpy(), rtol=0, atol=1e-12)
+            # optional outputs: top-k alone (expect and E NULL, prob NULL) and <C> alone (k = 0)
+            ti2 = torch.full((k,), -1, dtype=torch.int64, device="cuda")
+            st = L.qaoa_expect_topk_static(n, C.c_void_p(psi.data_ptr()), None, k, None,
+                                           C.c_void_p(ti2.data_ptr()), None, C.c_void_p(stream))
+            assert st == q.QAOA_OK, q.qaoa_last_error()
+            ex2 = torch.full((1,), -7.0, dtype=torch.float64, device="cuda")
+            st = L.qaoa_expect_topk_static(n, C.c_void_p(psi.data_ptr()), C.c_void_p(E.data_ptr()), 0,
+                                           C.c_void_p(ex2.data_ptr()), None, None, C.c_void_p(stream))
+            assert st == q.QAOA_OK, q.qaoa_last_error()
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(ti2.cpu().numpy(), ref_i.cpu().numpy())
+            assert abs(ex2.item() - ref_ex.item()) <= 1e-5 * absq
         # sizes beyond the fixed scratch are refused before any launch
         assert L.qaoa_expect_topk_static(31, C.c_void_p(psi.data_ptr()), None, 1, None,
                                          C.c_void_p(ti.data_ptr()), None, None) == q.QAOA_E_INVALID
