@@ -296,8 +296,8 @@ def run_ours(args):
     # ---- dominant kernel and its roofline ----
     def relaunch():
         q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream)
-    roof = plan_roofline(q, plans, kern, relaunch, clk, dev,
-                         alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p), workload="dqaoa")
+    roof = plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=method_flops_per_step(m, k, p),
+                         steps=args.steps, workload="dqaoa")
 
     # ---- kernel-only batch throughput and the plain one-instance-per-launch path ----
     kb = time_plan_only(q, plans, stream, args.steps, l2_flush)
@@ -356,11 +356,18 @@ def run_ours(args):
 HBM_FAMILIES = ("stream_pass", "stream_adjoint", "energy", "stream_finalize", "stream_grad_reduce")
 
 
-def plan_roofline(q, plans, kern, relaunch, clk, dev, alu_flops=None, workload=None):
+def plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=None, steps=None, workload=None):
     """Roofline entry of the kernel family with the largest time in `kern` ({family: [ms per
-    launch]}, measured with CUDA events on the launch stream inside the timed region). Algorithmic
-    bytes per launch come from the plan(s); `relaunch` runs them once more with timing on to map
-    launch order to families."""
+    launch]}, measured with CUDA events on the launch stream inside the timed region).
+
+    HBM-bound workloads (a state in HBM; method_flops_per_step None): algorithmic bytes per launch
+    come from the plan(s) (states, energies and matrices read or written once per pass); `relaunch`
+    runs them once more with timing on to map launch order to families.
+    On-chip workloads (method_flops_per_step given: the method's arithmetic on states that fit on
+    chip, SMEM / FP32 bound): achieved = the method's FP32 operations per step / the dominant
+    family's event time per step, against SMs x 128 FP32 lanes x 2 x median SM clock. The same
+    family's HBM view (the bytes the implementation chose to move) is reported beside it as
+    `implementation_traffic`, not as the bound."""
     import torch
     if not isinstance(plans, (list, tuple)):
         plans = [plans]
@@ -379,27 +386,35 @@ def plan_roofline(q, plans, kern, relaunch, clk, dev, alu_flops=None, workload=N
     per_launch_ms = statistics.mean(kern[dom])
     per_launch_bytes = statistics.mean(fam_bytes) if fam_bytes else 0.0
     peaks, peak_kind = measured_peaks()
-    if dom in HBM_FAMILIES or alu_flops is None:
-        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-        return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "traffic": ncu_traffic(workload, dom), "peak_source": peak_kind + " (hbm_gbs, copy burst)",
-                "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-                "launches_per_step": len(fam_bytes)}
-    # on-chip kernels: FP32 pipe bound; peak = SMs x 128 FP32 lanes x 2 flop x clock
+    hbm_achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    hbm = {"bound": "hbm", "kernel": dom, "achieved": hbm_achieved, "peak": peaks["hbm_gbs"],
+           "unit": "GB/s", "frac": hbm_achieved / peaks["hbm_gbs"],
+           "traffic": ncu_traffic(workload, dom), "peak_source": peak_kind + " (hbm_gbs, copy burst)",
+           "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+           "launches_per_step": len(fam_bytes)}
+    if method_flops_per_step is None:
+        return hbm
     props = torch.cuda.get_device_properties(dev)
     mhz = clk.summary().get("sm_mhz") or 1900.0
     peak_tf = props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
-    achieved = alu_flops(dom) / (per_launch_ms * 1e-3) / 1e12
+    fam_ms_step = fam_ms[dom] / steps
+    achieved = method_flops_per_step / (fam_ms_step * 1e-3) / 1e12
+    hbm_impl = {key: hbm[key] for key in ("achieved", "peak", "unit", "frac", "algorithmic_bytes_per_launch",
+                                          "ms_per_launch", "launches_per_step", "peak_source")}
+    hbm_impl["what"] = "bytes this kernel family moves through HBM per launch (the implementation's choice)"
     return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf,
             "unit": "TFLOP/s", "frac": achieved / peak_tf, "traffic": ncu_traffic(workload, dom),
-            "peak_source": "derived: SMs x 128 FP32 lanes x 2 x median SM clock",
-            "ms_per_launch": per_launch_ms}
+            "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz "
+                           "(median SM clock under load)",
+            "method_flops_per_step": method_flops_per_step, "kernel_ms_per_step": fam_ms_step,
+            "ms_per_launch": per_launch_ms, "implementation_traffic": hbm_impl}
 
 
-def alu_flops_per_launch(family, m, k, p):
-    # per amplitude and layer: phase (sincos counted as 8) + 4 flops, mixer 4 flops per qubit
-    return m * (1 << k) * p * (12 + 4 * k)
+def method_flops_per_step(m, k, p):
+    """FP32 operations of the method per step: (4n + 20) per amplitude and layer (cost phase with
+    its sine and cosine, n mixer rotations at 4 per amplitude, and the fused reductions), times
+    m sub-QUBOs x 2^n amplitudes x p layers."""
+    return m * (1 << k) * p * (4 * k + 20)
 
 
 def time_plan_only(q, plans, stream, steps, l2_flush):
@@ -946,7 +961,7 @@ def run_maxcut(args):
             all_ms += step_ms
     sess, plans, mk, x = roof_args
     roof = plan_roofline(q, plans, mk, lambda: q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream),
-                         clk, dev, alu_flops=lambda fam: alu_flops_per_launch(fam, m, k, p) / len(plans),
+                         clk, dev, method_flops_per_step=method_flops_per_step(m, k, p), steps=args.steps,
                          workload="maxcut")
     q.dqaoa_session_destroy(sess)
     q.qaoa_destroy(ctx)
