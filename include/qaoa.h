@@ -68,12 +68,15 @@ size_t qaoa_workspace_bytes(int n, int dbl);
 
 /* Kernel tier of the batched plans for complex64 instances of n qubits (plans created later).
  *   QAOA_TIER_AUTO: the autotuner's stored choice for (n, p), else the library's default
- *     (resident for n <= 14, cluster with 13 local qubits per CTA for n = 15, streaming above);
+ *     (resident for n <= 14, cluster streaming for n = 15..17, streaming above);
  *   QAOA_TIER_CLUSTER: cluster tier with `param` local qubits per CTA (13 or 14; the cluster
  *     then has 2^(n - param) CTAs, at most 16); only 15 <= n <= 18;
- *   QAOA_TIER_STREAM: HBM streaming; n >= 15.
+ *   QAOA_TIER_STREAM: HBM streaming; n >= 15;
+ *   QAOA_TIER_CSTREAM: cluster streaming (one thread-block cluster per instance runs all its
+ *     passes through L2, tiles moved by TMA); 15 <= n <= 17, forward runs only (gradient
+ *     instances use the streaming tier). QAOA_E_UNSUPPORTED if the device cannot run it.
  * The resident tier is always used for n <= 14. */
-enum { QAOA_TIER_AUTO = 0, QAOA_TIER_CLUSTER = 2, QAOA_TIER_STREAM = 3 };
+enum { QAOA_TIER_AUTO = 0, QAOA_TIER_CLUSTER = 2, QAOA_TIER_STREAM = 3, QAOA_TIER_CSTREAM = 4 };
 qaoa_status qaoa_set_tier(qaoa_ctx* ctx, int n, int tier, int param);
 
 /* Autotuner (no counterpart in the paper). Times every kernel configuration that can run a
@@ -260,6 +263,11 @@ int qaoa_plan_kernel_times(qaoa_plan* plan, float* ms, const char** names, int m
  * computation must move: states, energies and matrices read or written once, no re-reads);
  * returns the number of kernels written (at most max). */
 int qaoa_plan_kernel_bytes(const qaoa_plan* plan, double* bytes, int max);
+/* Device status of the plan's launches so far (synchronous: reads one word). Kernels with
+ * device-side waits bound each wait; a wait that ran out sets the plan's status word, and this
+ * call then returns QAOA_E_TIMEOUT (sticky for the plan). qaoa_batch_run and
+ * dqaoa_session_cycle check it at their synchronisation point. */
+qaoa_status qaoa_plan_check(qaoa_plan* plan);
 /* Free the plan (synchronises the device first). NULL is ignored. */
 void qaoa_plan_destroy(qaoa_plan* plan);
 

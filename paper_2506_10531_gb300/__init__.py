@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libqaoa.so")
 
 QAOA_OK, QAOA_E_INVALID, QAOA_E_NOMEM, QAOA_E_CUDA, QAOA_E_TIMEOUT, QAOA_E_UNSUPPORTED = range(6)
 QAOA_INST_GRAD = 1
-QAOA_TIER_AUTO, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM = 0, 2, 3
+QAOA_TIER_AUTO, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM, QAOA_TIER_CSTREAM = 0, 2, 3, 4
 DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS, DQAOA_PFS = 0, 1, 2, 3
 DQAOA_SIGNED_IMPACT = 16   # or-ed with IFD / BFS / PFS: rank by impact ascending
 
@@ -28,7 +28,7 @@ EXPORTS = [
     "qaoa_set_tier",
     "qaoa_build_energies", "qaoa_run_layers", "qaoa_expect", "qaoa_topk", "qaoa_grad",
     "qaoa_build_energies_z", "qaoa_run_layers_z", "qaoa_expect_z", "qaoa_topk_z", "qaoa_grad_z",
-    "qaoa_plan_create", "qaoa_plan_launch", "qaoa_plan_kernel_count", "qaoa_plan_destroy",
+    "qaoa_plan_create", "qaoa_plan_launch", "qaoa_plan_kernel_count", "qaoa_plan_check", "qaoa_plan_destroy",
     "qaoa_batch_run", "qaoa_batch_run_z", "qaoa_plain_solve",
     "dqaoa_draw_indices", "dqaoa_decompose", "dqaoa_subqubo_build", "dqaoa_merge",
     "qaoa_plan_set_timing", "qaoa_plan_kernel_times", "qaoa_plan_kernel_bytes",
@@ -110,6 +110,8 @@ def _declare(L):
     L.qaoa_plan_launch.argtypes = [vp, vp]
     L.qaoa_plan_kernel_count.argtypes = [vp]
     L.qaoa_plan_kernel_count.restype = i32
+    L.qaoa_plan_check.argtypes = [vp]
+    L.qaoa_plan_check.restype = st
     L.qaoa_plan_destroy.argtypes = [vp]
     L.qaoa_plan_destroy.restype = None
     L.qaoa_batch_run.argtypes = [vp, vp, i32, C.POINTER(qaoa_batch_io), vp]
@@ -336,6 +338,11 @@ def qaoa_plan_launch(plan, stream=None):
 
 def qaoa_plan_kernel_count(plan) -> int:
     return lib().qaoa_plan_kernel_count(plan)
+
+
+def qaoa_plan_check(plan):
+    """Raises QaoaError (QAOA_E_TIMEOUT) if a device-side wait of the plan's launches ran out."""
+    _check(lib().qaoa_plan_check(plan))
 
 
 def qaoa_plan_destroy(plan):

@@ -14,6 +14,7 @@
 
 #include "../../include/qaoa.h"
 #include "qaoa_common.cuh"
+#include "qaoa_cstream.h"
 #include "qaoa_host.h"
 #include "qaoa_kernels.h"
 #include "qaoa_stream.h"
@@ -53,6 +54,9 @@ bool bad_nk(int n, int k) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Counter slot of a plan's header that holds its device status word (bit 0: a bounded wait ran out).
+constexpr int PLAN_STATUS_SLOT = 62;
 
 // Scratch of one streaming instance: per-tile <C> partials and top-k lists, laid out as
 // [expect (nt doubles)] [probabilities (nt*k doubles)] [indices (nt*k uint32)], each 256-aligned.
@@ -308,6 +312,13 @@ extern "C" qaoa_status qaoa_set_tier(qaoa_ctx* c, int n, int tier, int param) {
         c->tier[n] = tier;
         return QAOA_OK;
     }
+    if (tier == QAOA_TIER_CSTREAM) {
+        if (n < CS_NMIN || n > CS_NMAX) return fail(QAOA_E_INVALID, "set_tier: cluster streaming needs 15 <= n <= 17");
+        if (!cstream_usable(c, n))
+            return fail(QAOA_E_UNSUPPORTED, "set_tier: the cluster-streaming tier cannot run n=%d on this device", n);
+        c->tier[n] = tier;
+        return QAOA_OK;
+    }
     if (tier == QAOA_TIER_CLUSTER) {
         if (n < CL_NMIN || n > CL_NMAX || param < 10 || param > 14 || n - param < 1 || n - param > 4)
             return fail(QAOA_E_INVALID, "set_tier: cluster needs 15 <= n <= 18 and 1 <= n - L <= 4");
@@ -394,11 +405,13 @@ struct qaoa_plan {
     cudaGraphExec_t graph = nullptr;  // captured launch sequence (qaoa_plan_capture)
     struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
     struct CluGroup { int n, L, pmax, count; size_t desc_off; int clusters; };
+    struct CsGroup { int n, count; size_t desc_off; int clusters; };
     struct StrGroup { int n, p, k, count; bool grad; size_t inst_off; std::vector<StreamPass> passes;
                       std::vector<StreamPass> apasses;   // adjoint plan (adjoint tile bits)
                       int grid, agrid; std::vector<const void*> q; std::vector<void*> e; };
     std::vector<ResGroup> res;
     std::vector<CluGroup> clu;
+    std::vector<CsGroup> cs;
     std::vector<StrGroup> str;
     int kernels = 0;
     bool timing = false;
@@ -454,14 +467,20 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     // group: resident by (n, grad); streaming by (n, p, k)
     std::map<std::pair<int, int>, std::vector<int>> rg;
     std::map<std::pair<int, int>, std::vector<int>> cg;   // cluster groups by (n, local qubits)
+    std::map<int, std::vector<int>> csg;                   // cluster-streaming groups by n
     std::map<std::tuple<int, int, int, int>, std::vector<int>> sg;
     const int nres = dbl ? RES_NMAX_D : RES_NMAX_F;
     const int nres_adj = dbl ? RES_NMAX_D_ADJ : RES_NMAX_F_ADJ;
     for (int i = 0; i < count; ++i) {
         const qaoa_inst& d = desc[i];
         const bool grad = (d.flags & QAOA_INST_GRAD) != 0;
+        const int tier = (!dbl && !grad) ? qaoa::eff_tier(c, d.n, d.p) : QAOA_TIER_STREAM;
+        // the cluster-streaming tier moves the energies by TMA: an energy output must be 16-byte aligned
+        const bool e_ok = d.e_off < 0 || (reinterpret_cast<uintptr_t>(epool + d.e_off) & 15u) == 0;
         if (d.n <= nres && (!grad || d.n <= nres_adj)) rg[{d.n, grad ? 1 : 0}].push_back(i);
-        else if (!dbl && !grad && d.n >= CL_NMIN && d.n <= CL_NMAX && qaoa::eff_tier(c, d.n, d.p) != QAOA_TIER_STREAM)
+        else if (tier == QAOA_TIER_CSTREAM && d.n >= CS_NMIN && d.n <= CS_NMAX && e_ok && cstream_usable(c, d.n))
+            csg[d.n].push_back(i);
+        else if (!dbl && !grad && d.n >= CL_NMIN && d.n <= CL_NMAX && tier == QAOA_TIER_CLUSTER)
             cg[{d.n, qaoa::eff_cluster_L(c, d.n, d.p)}].push_back(i);
         else sg[{d.n, d.p, d.k, grad ? 1 : 0}].push_back(i);
     }
@@ -527,6 +546,35 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         }
         g.clusters = std::min(g.count, mc);
         P->clu.push_back(g);
+    }
+    // cluster-streaming: descriptors, then four tensor maps per instance (64-byte aligned);
+    // per-instance state and energies in the scratch unless the caller receives them
+    struct CsI { size_t psi_off, e_off; };
+    std::vector<std::vector<CsI>> csinfo;
+    std::vector<size_t> cs_maps_off;
+    for (auto& kv : csg) {
+        qaoa_plan::CsGroup g{};
+        g.n = kv.first;
+        g.count = (int)kv.second.size();
+        g.desc_off = hdr;
+        hdr = align256(hdr + cstream_inst_bytes() * g.count);
+        cs_maps_off.push_back(hdr);
+        hdr = align256(hdr + CS_MAPS_BYTES * g.count);
+        int mc = 0;
+        cstream_max_clusters(g.n, &mc);
+        g.clusters = std::max(1, std::min(g.count, mc));
+        std::vector<CsI> v;
+        const size_t D = (size_t)1 << g.n;
+        for (int i : kv.second) {
+            CsI x{};
+            x.psi_off = (desc[i].psi_off >= 0) ? (size_t)-1 : scr;
+            if (desc[i].psi_off < 0) scr = align256(scr + D * sizeof(C2));
+            x.e_off = (desc[i].e_off >= 0) ? (size_t)-1 : scr;
+            if (desc[i].e_off < 0) scr = align256(scr + D * sizeof(T));
+            v.push_back(x);
+        }
+        csinfo.push_back(v);
+        P->cs.push_back(g);
     }
     if (qslot > 60) { delete P; return fail(QAOA_E_UNSUPPORTED, "too many resident groups"); }
     // streaming: per instance its own E / psi / partial buffers inside the plan block
@@ -620,6 +668,36 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         ci += g.count;
         P->kernels += 1;
     }
+    {
+        size_t gi = 0;
+        for (auto& kv : csg) {
+            auto& g = P->cs[gi];
+            size_t j = 0;
+            for (int i : kv.second) {
+                const qaoa_inst& d = desc[i];
+                const CsI& x = csinfo[gi][j];
+                void* psi = (x.psi_off == (size_t)-1) ? (void*)(psipool + d.psi_off) : (void*)(sb + x.psi_off);
+                void* E = (x.e_off == (size_t)-1) ? (void*)(epool + d.e_off) : (void*)(sb + x.e_off);
+                const size_t moff = cs_maps_off[gi] + CS_MAPS_BYTES * j;
+                if (!cstream_encode_maps(d.n, psi, E, img.data() + moff)) {
+                    if (P->owns) cudaFree(P->dev);
+                    delete P;
+                    return fail(QAOA_E_CUDA, "instance %d: tensor maps of the cluster-streaming tier refused", i);
+                }
+                cstream_fill_inst(img.data() + g.desc_off + cstream_inst_bytes() * j, d.n, d.p, d.k,
+                                  d.psi_off >= 0, reinterpret_cast<const float*>(qpool + d.q_off),
+                                  reinterpret_cast<const float*>(ppool + d.par_off),
+                                  reinterpret_cast<const float*>(ppool + d.par_off + d.p),
+                                  io->expect ? io->expect + i : nullptr,
+                                  d.k > 0 ? io->topk_idx + (int64_t)i * io->k_stride : nullptr,
+                                  (d.k > 0 && io->topk_prob) ? io->topk_prob + (int64_t)i * io->k_stride : nullptr,
+                                  base + moff);
+                ++j;
+            }
+            P->kernels += 1;
+            ++gi;
+        }
+    }
     // build streaming instances
     size_t gi = 0;
     for (auto& kv : sg) {
@@ -697,6 +775,20 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         }
         P->bytes.push_back(b);
     }
+    {
+        size_t gi = 0;
+        for (auto& kv : csg) {
+            double b = 0.0;
+            for (int i : kv.second) {
+                const qaoa_inst& d = desc[i];
+                const double D = (double)(1ull << d.n);
+                b += (double)d.n * d.n * sizeof(T) + 2.0 * d.p * sizeof(T) + sizeof(double) + d.k * 16.0 +
+                     (d.psi_off >= 0 ? D * sizeof(C2) : 0.0) + (d.e_off >= 0 ? D * sizeof(T) : 0.0);
+            }
+            P->bytes.push_back(b);
+            ++gi;
+        }
+    }
     for (auto& g : P->str) {
         const double D = (double)(1ull << g.n), cnt = (double)g.count;
         const double nt = (double)(1ull << (g.n - tb));
@@ -722,6 +814,20 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
 
 namespace qaoa {
 
+bool cstream_usable(qaoa_ctx* c, int n) {
+    if (n < CS_NMIN || n > CS_NMAX) return false;
+    if (c->cs_ok[n] == 0) {
+        int mc = 0, dev = -1;
+        cudaGetDevice(&dev);
+        if (dev != c->device) cudaSetDevice(c->device);
+        const bool ok = cstream_available() && cstream_max_clusters(n, &mc) == cudaSuccess && mc >= 1;
+        cudaGetLastError();
+        if (dev >= 0 && dev != c->device) cudaSetDevice(dev);
+        c->cs_ok[n] = ok ? 1 : -1;
+    }
+    return c->cs_ok[n] > 0;
+}
+
 // Record an error message for qaoa_last_error from another translation unit.
 qaoa_status set_error(qaoa_status st, const char* msg) { return fail(st, "%s", msg); }
 
@@ -729,8 +835,11 @@ qaoa_status set_error(qaoa_status st, const char* msg) { return fail(st, "%s", m
 // buffers; the resident and cluster tiers need none), as plan_create_t lays them out.
 size_t plan_inst_scratch_bytes(qaoa_ctx* c, int n, int p, int k, bool grad) {
     const bool res = n <= RES_NMAX_F && (!grad || n <= RES_NMAX_F_ADJ);
-    const bool clu = !grad && n >= CL_NMIN && n <= CL_NMAX && eff_tier(c, n, p) != QAOA_TIER_STREAM;
+    const int tier = grad ? QAOA_TIER_STREAM : eff_tier(c, n, p);
+    const bool clu = !grad && n >= CL_NMIN && n <= CL_NMAX && tier == QAOA_TIER_CLUSTER;
     if (res || clu) return 0;
+    if (!grad && tier == QAOA_TIER_CSTREAM && n >= CS_NMIN && n <= CS_NMAX && cstream_usable(c, n))
+        return align256(((size_t)1 << n) * sizeof(float2)) + align256(((size_t)1 << n) * sizeof(float));
     const int tb = stream_tile_bits(false), tba = stream_adj_tile_bits(false);
     const size_t D = (size_t)1 << n, nt = (size_t)1 << (n - tb), kk = (size_t)std::max(k, 1);
     size_t b = align256(D * sizeof(float)) + align256(D * sizeof(float2)) + align256(nt * sizeof(double)) +
@@ -745,8 +854,8 @@ size_t plan_inst_scratch_bytes(qaoa_ctx* c, int n, int p, int k, bool grad) {
 
 // Upper bound of a complex64 plan's header (counters and descriptor arrays) for `count` instances.
 size_t plan_header_bound(int count) {
-    const size_t d = std::max(sizeof(InstDesc<float>), sizeof(StreamInst<float>));
-    return align256(256 + (size_t)count * (align256(d) + 256));
+    const size_t d = std::max(std::max(sizeof(InstDesc<float>), sizeof(StreamInst<float>)), cstream_inst_bytes());
+    return align256(256 + (size_t)count * (align256(d) + CS_MAPS_BYTES + 512));
 }
 
 // A complex64 plan placed in caller memory, its header uploaded on `st` from pinned `staging`.
@@ -843,6 +952,11 @@ qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st) {
         CK(timed("cluster", [&] {
             return launch_cluster(base + g.desc_off, g.count, g.n, g.L, g.pmax, g.clusters, st, nullptr);
         }));
+    for (auto& g : P->cs)
+        CK(timed("cstream", [&] {
+            return launch_cstream(g.n, base + g.desc_off, g.count, g.clusters,
+                                  reinterpret_cast<unsigned*>(counters + PLAN_STATUS_SLOT), st);
+        }));
     const int tb = stream_tile_bits(P->dbl);
     for (auto& g : P->str) {
         CK(timed("energy", [&] { return launch_energy_batch(P->dbl, g.n, base + g.inst_off, g.count, st); }));
@@ -892,6 +1006,16 @@ extern "C" int qaoa_plan_kernel_times(qaoa_plan* P, float* ms, const char** name
 
 extern "C" int qaoa_plan_kernel_count(const qaoa_plan* P) { return P ? P->kernels : 0; }
 
+extern "C" qaoa_status qaoa_plan_check(qaoa_plan* P) {
+    if (!P) return fail(QAOA_E_INVALID, "plan is NULL");
+    unsigned st = 0;
+    CK(cudaSetDevice(P->ctx->device));
+    CK(cudaMemcpy(&st, static_cast<char*>(P->dev) + PLAN_STATUS_SLOT * sizeof(int), sizeof(st),
+                  cudaMemcpyDeviceToHost));
+    if (st) return fail(QAOA_E_TIMEOUT, "a device-side wait of the plan ran out of time (status %u)", st);
+    return QAOA_OK;
+}
+
 extern "C" int qaoa_plan_kernel_bytes(const qaoa_plan* P, double* bytes, int max) {
     if (!P) return 0;
     const int n = std::min<int>(max, (int)P->bytes.size());
@@ -918,10 +1042,11 @@ static qaoa_status batch_run(qaoa_ctx* c, const qaoa_inst* desc, int count, cons
     if (s) return s;
     s = qaoa_plan_launch(P, stream);
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    const qaoa_status st = (s == QAOA_OK && e == cudaSuccess) ? qaoa_plan_check(P) : QAOA_OK;
     qaoa_plan_destroy(P);
     if (s) return s;
     if (e != cudaSuccess) return cuda_fail(e, "batch_run synchronize");
-    return QAOA_OK;
+    return st;
 }
 
 extern "C" qaoa_status qaoa_batch_run(qaoa_ctx* c, const qaoa_inst* d, int n, const qaoa_batch_io* io,
@@ -1043,6 +1168,7 @@ struct dqaoa_session {
     uint64_t* topk_h = nullptr;
     double* expect_h = nullptr;
     double* qblk_h = nullptr;
+    unsigned* status_h = nullptr; // device status word of each chunk plan after its launch
     // the sub-QUBOs are solved in chunks, one plan each, so that the host merges chunk c while
     // the device solves chunk c + 1 (the merge is sequential over sub-QUBOs in index order)
     int chunks = 1;
@@ -1106,6 +1232,7 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     const size_t ht = h; h = align256(h + (size_t)m * K * sizeof(uint64_t));
     const size_t he = h; h = align256(h + (size_t)m * sizeof(double));
     const size_t hb2 = h; h = align256(h + (size_t)m * k * k * sizeof(double));
+    const size_t hst = h; h = align256(h + 2 * sizeof(unsigned));
     e = cudaMallocHost(&s->host, h);
     if (e != cudaSuccess) { cudaFree(s->dev); delete s; return fail(QAOA_E_NOMEM, "session cudaMallocHost"); }
     char* hb = static_cast<char*>(s->host);
@@ -1114,6 +1241,7 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     s->topk_h = reinterpret_cast<uint64_t*>(hb + ht);
     s->expect_h = reinterpret_cast<double*>(hb + he);
     s->qblk_h = reinterpret_cast<double*>(hb + hb2);
+    s->status_h = reinterpret_cast<unsigned*>(hb + hst);
     std::vector<float> par(2 * p);
     for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)beta[l]; }
     e = cudaMemcpy(s->params, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -1127,7 +1255,13 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     int m0 = m;
     if (s->chunks == 2) {
         int w = 1;
-        if (k >= 16 && (k > 18 || eff_tier(c, k, p) == QAOA_TIER_STREAM)) {
+        const int tier = eff_tier(c, k, p);
+        if (k >= CS_NMIN && k <= CS_NMAX && tier == QAOA_TIER_CSTREAM && cstream_usable(c, k)) {
+            // whole waves of clusters (one instance per cluster at a time)
+            int mc = 0;
+            cstream_max_clusters(k, &mc);
+            w = std::max(1, mc);
+        } else if (k >= 16 && (k > 18 || tier == QAOA_TIER_STREAM)) {
             const int tiles = 1 << (k - stream_tile_bits(false));
             w = std::max(1, 2 * c->nsm / tiles);
         }
@@ -1209,6 +1343,8 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         CK(cudaMemcpyAsync(s->topk_h + (size_t)j0 * K, s->topk + (size_t)j0 * K, (size_t)mc * K * sizeof(uint64_t),
                            cudaMemcpyDeviceToHost, s->side));
         CK(cudaMemcpyAsync(s->expect_h + j0, s->expect + j0, (size_t)mc * sizeof(double), cudaMemcpyDeviceToHost, s->side));
+        CK(cudaMemcpyAsync(s->status_h + ch, static_cast<char*>(s->plans[ch]->dev) + PLAN_STATUS_SLOT * sizeof(int),
+                           sizeof(unsigned), cudaMemcpyDeviceToHost, s->side));
         CK(cudaEventRecord(s->chunk_done[ch], s->side));
     }
     CK(cudaEventRecord(s->dev_end, s->side));
@@ -1229,6 +1365,11 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     CK(cudaEventSynchronize(s->qblk_done));
     for (int ch = 0; ch < s->chunks; ++ch) {
         CK(cudaEventSynchronize(s->chunk_done[ch]));
+        if (s->status_h[ch]) {
+            // a device-side wait of this chunk ran out: its results are not valid, x is left as is
+            cudaStreamSynchronize(st);
+            return fail(QAOA_E_TIMEOUT, "session_cycle: a device-side wait of chunk %d ran out of time", ch);
+        }
         const double tm = now_ms();
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
         int acc = 0;

@@ -23,18 +23,21 @@ struct qaoa_ctx {
     int tier[32] = {0};       // QAOA_TIER_* per n for complex64 plans (0: automatic)
     int cluster_L[32] = {0};  // local qubits per CTA of the cluster tier by n (0: default 14)
     qaoa_tuned tuned[32][65]; // autotuner table by (n, p)
+    int cs_ok[32] = {0};      // cluster-streaming tier: 0 unknown, 1 usable, -1 not on this device
 };
 
 namespace qaoa {
-// Tier of a complex64 instance of (n, p) without gradient in the 15..18 cluster range: an
-// explicit qaoa_set_tier wins, then the autotuner's entry, then the default measured on GB300
-// for batches of a few hundred instances at p = 3: the cluster tier with 13 local qubits for
-// n = 15, the streaming tier for n = 16..18 (faster by 7%, 34% and 50%).
+// Tier of a complex64 instance of (n, p) without gradient above the resident range: an explicit
+// qaoa_set_tier wins, then the autotuner's entry, then the default: the cluster-streaming tier for
+// n = 15..17, the streaming tier above.
 inline int eff_tier(const qaoa_ctx* c, int n, int p) {
     if (c->tier[n]) return c->tier[n];
     if (p >= 1 && p <= 64 && c->tuned[n][p].tier) return c->tuned[n][p].tier;
-    return n == 15 ? QAOA_TIER_CLUSTER : QAOA_TIER_STREAM;
+    return (n >= 15 && n <= 17) ? QAOA_TIER_CSTREAM : QAOA_TIER_STREAM;
 }
+// The cluster-streaming tier can run n-qubit instances on the context's device (tensor-map
+// encoder found, a cluster of its shape fits); cached per n.
+bool cstream_usable(qaoa_ctx* c, int n);
 inline int eff_cluster_L(const qaoa_ctx* c, int n, int p) {
     if (c->tier[n] == QAOA_TIER_CLUSTER && c->cluster_L[n]) return c->cluster_L[n];
     if (p >= 1 && p <= 64 && c->tuned[n][p].tier == QAOA_TIER_CLUSTER && c->tuned[n][p].L) return c->tuned[n][p].L;

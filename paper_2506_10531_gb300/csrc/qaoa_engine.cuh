@@ -649,6 +649,14 @@ __device__ __noinline__ bool build_tile_energy_any(int n, int L, uint32_t zfix, 
 }
 
 // ---- final reductions of a tile -----------------------------------------------------------
+// Shared-memory placement of tile index u for the state (p) and the energies (e): the engine's
+// swizzle for both (default), or another layout supplied by a tier (a TMA-staged tile).
+template <typename T>
+struct SwzLayout {
+    __device__ __forceinline__ static uint32_t p(uint32_t u) { return swz<T>(u); }
+    __device__ __forceinline__ static uint32_t e(uint32_t u) { return swz<T>(u); }
+};
+
 // Shared scratch of tile_reduce (sizes: wb 16 * nwarps floats, cand TOPK_CAP entries, out 16,
 // wlists 32 * nwarps entries, cnt 4 ints).
 constexpr int TOPK_CAP = 256;
@@ -667,7 +675,7 @@ struct TileTopk {
 // computed the tile's <C> partial) can reach the bound: a list of k entries has few owners, so
 // most threads skip the scan. pmax and the per-element value are two FP32 roundings of the same
 // probability, each within 2^-21 of it, hence the wider 2^-18 margin of the thread test.
-template <typename T, typename ZMap>
+template <typename T, typename Lay = SwzLayout<T>, typename ZMap>
 __device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float pmax, float bound_lo,
                                                    const double* exact_bound, ZMap&& zmap,
                                                    const TileTopk& ts) {
@@ -682,7 +690,7 @@ __device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float pm
         for (int j = 0; j < 32; ++j) {
             const uint32_t u = c0 + (uint32_t)j * blockDim.x + threadIdx.x;
             if (u < D) {
-                const C v = t.psi[swz<T>(u)];
+                const C v = t.psi[Lay::p(u)];
                 const float pf = (float)v.x * (float)v.x + (float)v.y * (float)v.y;
                 if (pf * 1.00000095367431640625f >= bound_lo) hits |= 1u << j;
             }
@@ -691,7 +699,7 @@ __device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float pm
             const int j = __ffs(hits) - 1;
             hits &= hits - 1;
             const uint32_t u = c0 + (uint32_t)j * blockDim.x + threadIdx.x;
-            const double pe = exact_prob(t.psi[swz<T>(u)]);
+            const double pe = exact_prob(t.psi[Lay::p(u)]);
             if (pbits(pe) >= eb) {
                 const int pos = atomicAdd(&ts.cnt[0], 1);
                 if (pos < TOPK_CAP) ts.cand[pos] = TopEnt{pe, zmap(u)};
@@ -704,7 +712,7 @@ __device__ __forceinline__ void collect_candidates(const TileRef<T>& t, float pm
 // <C> partial of the tile (FP32 |psi|^2 E over at most 32 elements per thread, FP64 above, added
 // to `ex`) and the thread's largest FP32 probability over its elements u = tid + j * blockDim
 // (its lane maximum, returned). Called by all threads; no barrier.
-template <typename T>
+template <typename T, typename Lay = SwzLayout<T>>
 __device__ __forceinline__ float tile_expect(const TileRef<T>& t, double& ex) {
     using C = typename Num<T>::C;
     const uint32_t D = 1u << t.tb;
@@ -715,10 +723,9 @@ __device__ __forceinline__ float tile_expect(const TileRef<T>& t, double& ex) {
         for (int j = 0; j < 32; ++j) {
             const uint32_t u = c0 + (uint32_t)j * blockDim.x + threadIdx.x;
             if (u < D) {
-                const uint32_t ix = swz<T>(u);
-                const C v = t.psi[ix];
+                const C v = t.psi[Lay::p(u)];
                 const T pr = v.x * v.x + v.y * v.y;
-                accp += pr * t.E[ix];
+                accp += pr * t.E[Lay::e(u)];
                 pmax = fmaxf(pmax, (float)pr);
             }
         }
@@ -740,7 +747,7 @@ __device__ __forceinline__ float tile_expect(const TileRef<T>& t, double& ex) {
 // The result does not depend on the order of the buffer, so the reduction is deterministic.
 // If the buffer still overflows (massive ties) the warps fall back to sorted insertion lists
 // merged by warp 0. zmap(u): global index of tile index u. Called by all threads, k >= 1.
-template <typename T, typename ZMap>
+template <typename T, typename Lay = SwzLayout<T>, typename ZMap>
 __device__ __forceinline__ void tile_topk(const TileRef<T>& t, int k, float pmax, ZMap&& zmap,
                                           const TileTopk& ts) {
     using C = typename Num<T>::C;
@@ -766,7 +773,7 @@ __device__ __forceinline__ void tile_topk(const TileRef<T>& t, int k, float pmax
     const float thr = *bound;
     const float thr_lo = thr > 0.0f ? thr * 0.99999904632568359375f : -1.0f;   // (1 - 2^-20)
     // (2) candidates
-    collect_candidates<T>(t, pmax, thr_lo, nullptr, zmap, ts);
+    collect_candidates<T, Lay>(t, pmax, thr_lo, nullptr, zmap, ts);
     __syncthreads();
     if (ts.cnt[1]) {
         // raise the bound to the k-th best buffered exact probability and collect again
@@ -784,7 +791,7 @@ __device__ __forceinline__ void tile_topk(const TileRef<T>& t, int k, float pmax
         const float b2lo = __double2float_rd(*b2) * 0.99999904632568359375f;
         if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
         __syncthreads();
-        collect_candidates<T>(t, pmax, b2lo, b2, zmap, ts);
+        collect_candidates<T, Lay>(t, pmax, b2lo, b2, zmap, ts);
         __syncthreads();
     }
     const int cnt = min(ts.cnt[0], TOPK_CAP);
@@ -809,7 +816,7 @@ __device__ __forceinline__ void tile_topk(const TileRef<T>& t, int k, float pmax
             C v;
             v.x = T(0);
             v.y = T(0);
-            if (u < D) v = t.psi[swz<T>(u)];
+            if (u < D) v = t.psi[Lay::p(u)];
             top.offer(v, zmap(u < D ? u : 0u), u < D);
         }
         if (lane < k) ts.wlists[warp * 32 + lane] = TopEnt{top.p, top.z};
@@ -830,12 +837,12 @@ __device__ __forceinline__ void tile_topk(const TileRef<T>& t, int k, float pmax
 
 // <C> partial (added to `ex`) and, for k >= 1, the top-k list (ts.out) of the whole tile after
 // its last sub-pass. Called by all threads.
-template <typename T, typename ZMap>
+template <typename T, typename Lay = SwzLayout<T>, typename ZMap>
 __device__ __forceinline__ void tile_reduce(const TileRef<T>& t, int k, ZMap&& zmap,
                                             const TileTopk& ts, double& ex) {
-    const float pmax = tile_expect<T>(t, ex);
+    const float pmax = tile_expect<T, Lay>(t, ex);
     if (k <= 0) return;
-    tile_topk<T>(t, k, pmax, zmap, ts);
+    tile_topk<T, Lay>(t, k, pmax, zmap, ts);
 }
 
 // Fold the tile into `run`, the top-k list (k entries, all present) of the tiles of the same

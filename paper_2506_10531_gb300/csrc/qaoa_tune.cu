@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/qaoa.h"
+#include "qaoa_cstream.h"
 #include "qaoa_ctx.h"
 #include "qaoa_host.h"
 
@@ -61,6 +62,7 @@ extern "C" qaoa_status qaoa_autotune(qaoa_ctx* c, int n, int p, int k, int count
     TCK(cudaSetDevice(c->device), "cudaSetDevice");
     std::vector<Candidate> cand;
     if (n >= 15 && n <= 18) {
+        if (n <= qaoa::CS_NMAX && qaoa::cstream_usable(c, n)) cand.push_back({QAOA_TIER_CSTREAM, 0});
         for (int L = 14; L >= 13; --L)
             if (n - L >= 1 && n - L <= 4) cand.push_back({QAOA_TIER_CLUSTER, L});
         cand.push_back({QAOA_TIER_STREAM, 0});
@@ -206,7 +208,8 @@ extern "C" qaoa_status qaoa_tuning_load(qaoa_ctx* c, const char* path) {
         if (sscanf(text.c_str() + pos, "{\"n\": %d, \"p\": %d, \"tier\": %d, \"L\": %d, \"ms\": %lf, \"count\": %d, \"k\": %d}",
                    &n, &p, &tier, &L, &ms, &cnt, &k) == 7 &&
             n >= 15 && n <= 18 && p >= 1 && p <= 64 &&
-            (tier == QAOA_TIER_STREAM || (tier == QAOA_TIER_CLUSTER && n - L >= 1 && n - L <= 4 && L >= 10))) {
+            (tier == QAOA_TIER_STREAM || (tier == QAOA_TIER_CSTREAM && n <= qaoa::CS_NMAX) ||
+             (tier == QAOA_TIER_CLUSTER && n - L >= 1 && n - L <= 4 && L >= 10))) {
             qaoa_tuned& t = c->tuned[n][p];
             t.tier = tier;
             t.L = L;

@@ -1,0 +1,151 @@
+"""The cluster-streaming tier (complex64, n = 15..17, one thread-block cluster per instance, tiles
+moved by TMA) against the FP64 oracle and against the streaming tier.
+
+* A batch of uneven instances (n 15..17, p 1..5, k 0..16, some returning the state and the
+  energies) with more instances than clusters in flight, so that every cluster runs several
+  instances one after the other: amplitudes within 1e-5 of the oracle, <C> within 1e-5 sum|Q|,
+  energies within 1e-5 sum|Q|, top-k bit-exact against the oracle's ranking of the returned
+  amplitudes (else the near-tie rule against the FP64 state).
+* Batch invariance: an instance alone and inside the batch gives identical bits.
+* The plan runs the tier (its kernel family is "cstream") and reports no device timeout.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K = 16
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_10531_gb300 import build
+    build.build()
+    import paper_2506_10531_gb300 as qq
+    return qq
+
+
+def make_specs(count, seed):
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(rng.integers(15, 18))
+        p = int(rng.integers(1, 6))
+        k = int(rng.choice([0, 1, 5, 8, 16]))
+        ret = bool(rng.integers(0, 2)) or i < 6
+        specs.append((n, p, k, ret))
+    return specs
+
+
+def run(q, specs, seed, tier=None, check_family=False):
+    qpool, ppool, rows, Qs, pars = [], [], [], [], []
+    qo = po = so = eo = 0
+    for i, (n, p, k, ret) in enumerate(specs):
+        Q = synth.symmetric_q(n, seed=seed + i).astype(np.float32)
+        g, b = synth.random_params(p, seed=seed + 5000 + i)
+        par = np.concatenate([g, b]).astype(np.float32)
+        rows.append((n, p, k, 0, qo, po, so if ret else -1, eo if ret else -1))
+        qpool.append(Q.reshape(-1)); ppool.append(par); Qs.append(Q); pars.append(par)
+        qo += n * n; po += 2 * p
+        if ret:
+            so += 1 << n
+            eo += 1 << n
+    count = len(rows)
+    qd = torch.as_tensor(np.concatenate(qpool)).cuda()
+    pd = torch.as_tensor(np.concatenate(ppool)).cuda()
+    psi = torch.zeros(2 * max(so, 1), dtype=torch.float32, device="cuda")
+    E = torch.zeros(max(eo, 1), dtype=torch.float32, device="cuda")
+    ex = torch.zeros(count, dtype=torch.float64, device="cuda")
+    ti = torch.zeros(count * K, dtype=torch.int64, device="cuda")
+    tp = torch.zeros(count * K, dtype=torch.float64, device="cuda")
+    io = q.make_io(qd, pd, expect=ex, topk_idx=ti, topk_prob=tp, k_stride=K, psi=psi, e=E)
+    ctx = q.qaoa_create(0)
+    try:
+        if tier is not None:
+            for n in (15, 16, 17):
+                q.qaoa_set_tier(ctx, n, tier, 0)
+        plan = q.qaoa_plan_create(ctx, q.make_insts(rows), io)
+        try:
+            q.qaoa_plan_set_timing(plan, True)
+            q.qaoa_plan_launch(plan)
+            torch.cuda.synchronize()
+            fams = [nm for nm, _ in q.qaoa_plan_kernel_times(plan)]
+            q.qaoa_plan_check(plan)
+        finally:
+            q.qaoa_plan_destroy(plan)
+    finally:
+        q.qaoa_destroy(ctx)
+    return dict(rows=rows, Qs=Qs, pars=pars, psi=psi.cpu().numpy(), E=E.cpu().numpy(), ex=ex.cpu().numpy(),
+                ti=ti.cpu().numpy().reshape(count, K), tp=tp.cpu().numpy().reshape(count, K), fams=fams)
+
+
+def check_against_oracle(orc, r, i):
+    n, p, k, _, qo, po, so, eo = r["rows"][i]
+    Qd = r["Qs"][i].astype(np.float64)
+    par = r["pars"][i].astype(np.float64)
+    E_o = orc.energies(Qd)
+    psi_o = orc.state(n, par[:p], par[p:], E_o)
+    absq = np.abs(Qd).sum()
+    assert abs(r["ex"][i] - orc.expect(psi_o, E_o)) <= 1e-5 * absq, (i, n, p)
+    if so >= 0:
+        assert np.max(np.abs(r["E"][eo:eo + (1 << n)] - E_o)) <= 1e-5 * absq, (i, n)
+        ps = r["psi"][2 * so:2 * (so + (1 << n))].reshape(-1, 2)
+        psi_g = ps[:, 0].astype(np.float64) + 1j * ps[:, 1]
+        err = np.max(np.abs(psi_g - psi_o))
+        assert err <= 1e-5, (i, n, p, err)
+        if k:
+            oi, op = orc.topk_probs(orc.probs(psi_g), k)
+            np.testing.assert_array_equal(r["ti"][i, :k].astype(np.uint64), oi)
+            np.testing.assert_array_equal(r["tp"][i, :k], op)
+    elif k:
+        pr = np.abs(psi_o) ** 2
+        eps = 4e-5 * np.sqrt(pr.max())
+        ri, rp = orc.topk_probs(pr, k)
+        for t in range(k):
+            clear = (t == 0 or rp[t - 1] - rp[t] > eps) and (t == k - 1 or rp[t] - rp[t + 1] > eps)
+            if clear:
+                assert int(r["ti"][i, t]) == int(ri[t]), (i, t)
+            else:
+                assert abs(pr[int(r["ti"][i, t])] - rp[t]) <= eps, (i, t)
+
+
+def test_cstream_batch_vs_oracle(q, orc):
+    specs = make_specs(160, seed=77)
+    r = run(q, specs, seed=3100, check_family=True)
+    assert "cstream" in r["fams"] and "stream_pass" not in r["fams"], r["fams"]
+    # every instance that returns its state, and a sample of the others
+    idx = [i for i, s in enumerate(specs) if s[3]][:40] + [i for i, s in enumerate(specs) if not s[3]][:12]
+    for i in idx:
+        check_against_oracle(orc, r, i)
+
+
+def test_cstream_agrees_with_streaming_tier(q):
+    specs = make_specs(48, seed=78)
+    a = run(q, specs, seed=3200)
+    b = run(q, specs, seed=3200, tier=q.QAOA_TIER_STREAM)
+    assert "stream_pass" in b["fams"] and "cstream" not in b["fams"]
+    for i, (n, p, k, _, qo, po, so, eo) in enumerate(a["rows"]):
+        absq = float(np.abs(a["Qs"][i]).sum())
+        assert abs(a["ex"][i] - b["ex"][i]) <= 2e-5 * absq, i
+        if so >= 0:
+            d = np.abs(a["psi"][2 * so:2 * (so + (1 << n))] - b["psi"][2 * so:2 * (so + (1 << n))])
+            assert d.max() <= 2e-5, (i, n, p)
+
+
+def test_cstream_batch_invariance(q):
+    specs = make_specs(60, seed=79)
+    full = run(q, specs, seed=3300)
+    for i in (0, 7, 33, 59):
+        alone = run(q, [specs[i]], seed=3300 + i)
+        n, p, k, ret = specs[i]
+        assert alone["ex"][0] == full["ex"][i]
+        np.testing.assert_array_equal(alone["ti"][0], full["ti"][i])
+        np.testing.assert_array_equal(alone["tp"][0], full["tp"][i])
+        if ret:
+            so = full["rows"][i][6]
+            np.testing.assert_array_equal(alone["psi"][:2 << n], full["psi"][2 * so:2 * so + (2 << n)])

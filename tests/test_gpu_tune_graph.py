@@ -48,7 +48,7 @@ def test_autotune_table_roundtrip(q, tmp_path):
         ms = q.qaoa_autotune(ctx, 16, 3, 8, 64)
         assert ms > 0
         tier, prm, ms2 = q.qaoa_tuning_get(ctx, 16, 3)
-        assert tier in (q.QAOA_TIER_CLUSTER, q.QAOA_TIER_STREAM) and ms2 == pytest.approx(ms)
+        assert tier in (q.QAOA_TIER_CLUSTER, q.QAOA_TIER_STREAM, q.QAOA_TIER_CSTREAM) and ms2 == pytest.approx(ms)
         if tier == q.QAOA_TIER_CLUSTER:
             assert prm in (13, 14)
         assert q.qaoa_tuning_get(ctx, 16, 4)[0] == 0       # only the tuned shape is stored
@@ -73,6 +73,7 @@ def test_autotune_table_roundtrip(q, tmp_path):
             names = {nm for nm, _ in q.qaoa_plan_kernel_times(plan)}
             assert ("cluster" in names) == (tier == q.QAOA_TIER_CLUSTER)
             assert ("stream_pass" in names) == (tier == q.QAOA_TIER_STREAM)
+            assert ("cstream" in names) == (tier == q.QAOA_TIER_CSTREAM)
         finally:
             q.qaoa_plan_destroy(plan)
         # an explicit tier setting overrides the table
