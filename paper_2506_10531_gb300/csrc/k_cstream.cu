@@ -53,7 +53,6 @@ __device__ __forceinline__ uint32_t psw(uint32_t u) { return u ^ ((u >> 3) & 14u
 
 struct TmaLayout {
     __device__ __forceinline__ static uint32_t p(uint32_t u) { return psw(u); }
-    __device__ __forceinline__ static uint32_t e(uint32_t u) { return u; }
 };
 
 // ---- TMA, mbarrier and proxy-fence primitives ------------------------------------------------
@@ -119,10 +118,22 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 // order global accesses of the generic and the async proxy (around the cluster hand-off)
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+// split cluster barrier: arrive and wait (acquire), strictly alternating per thread. After a CTA
+// barrier (which orders every write of the CTA before warp 0), warp 0 arrives with release
+// semantics and the other warps arrive relaxed.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 // ---- shared-memory layout ------------------------------------------------------------------
+// One state tile and one energy tile, shared by the two instance slots of a CTA; the energy tile
+// doubles as the top-k scratch of the final pass (after the <C> partial has read it) and of the
+// merge on rank 0. Per slot: Q, layer constants, the CTA's top-k lists and <C> partial.
 struct CsOff {
-    size_t psi, E, Q, lc, red, wb, cnt, cand, out, wlists, lists, cex, mbar, total;
+    size_t psi, E, red, escr, wbound, Q[2], lc[2], lists[2], cex[2], mbar, total;
+    size_t wb, cnt, cand, out, wlists;   // inside the energy tile
 };
 __host__ __device__ inline size_t cs_al(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline CsOff cs_offsets(int tpc) {
@@ -130,18 +141,23 @@ __host__ __device__ inline CsOff cs_offsets(int tpc) {
     size_t x = 0;
     o.psi = x; x += (size_t)TD * 8;                        // 64 KiB, 1024-byte aligned at run time
     o.E = x; x += (size_t)TD * 4;                          // 32 KiB
-    o.Q = x; x = cs_al(x + (size_t)CS_NMAX * CS_NMAX * 4);
-    o.lc = x; x = cs_al(x + 64 * sizeof(LayerConst<float>));
     o.red = x; x = cs_al(x + 32 * sizeof(double));
-    o.wb = x; x = cs_al(x + 16 * (NT / 32) * sizeof(float));
-    o.cnt = x; x = cs_al(x + 4 * sizeof(int));
-    o.cand = x; x = cs_al(x + TOPK_CAP * sizeof(TopEnt));
-    o.out = x; x = cs_al(x + 16 * sizeof(TopEnt));
-    o.wlists = x; x = cs_al(x + (NT / 32) * 32 * sizeof(TopEnt));
-    o.lists = x; x = cs_al(x + (size_t)tpc * 16 * sizeof(TopEnt));
-    o.cex = x; x = cs_al(x + sizeof(double));
+    o.escr = x; x = cs_al(x + 256 * sizeof(float));       // energy tables of pass 0
+    o.wbound = x; x = cs_al(x + (NT / 32) * sizeof(float));
+    for (int s = 0; s < 2; ++s) {
+        o.Q[s] = x; x = cs_al(x + (size_t)CS_NMAX * CS_NMAX * 4);
+        o.lc[s] = x; x = cs_al(x + 64 * sizeof(LayerConst<float>));
+        o.lists[s] = x; x = cs_al(x + (size_t)tpc * 16 * sizeof(TopEnt));
+        o.cex[s] = x; x = cs_al(x + sizeof(double));
+    }
     o.mbar = x; x = cs_al(x + sizeof(uint64_t));
     o.total = x + 1024;                                    // room to align psi to 1024 bytes
+    size_t y = o.E;
+    o.wb = y; y = cs_al(y + 16 * (NT / 32) * sizeof(float));
+    o.cnt = y; y = cs_al(y + 4 * sizeof(int));
+    o.cand = y; y = cs_al(y + TOPK_CAP * sizeof(TopEnt));
+    o.out = y; y = cs_al(y + 16 * sizeof(TopEnt));
+    o.wlists = y;
     return o;
 }
 
@@ -226,60 +242,204 @@ struct CsInstDev {
 };
 
 // Energies of kind-A tile tau of pass 0 in the W2 layout (thread t owns u = t | j << 8), with
-// the tile's fixed global bits S = tau << 13:
-//   E(z) = [E_S + El(t)] + Eh[j] + X_t(j),  X_t(j) = sum_{b in j} W_b(t),
-//   W_b(t) = sum_{i in t} (Q_{i, 8+b} + Q_{8+b, i}),
-// (every pair of set bits of z counted once, Q_ij and Q_ji both). Eh is built by 32 threads in
-// the scratch `eh`. ev[j] receives the energies; they are also written to sE (unswizzled).
-__device__ __forceinline__ void w2_energies(int n, uint32_t zfix, const float* Qs, float* eh, float* sE,
+// the tile's fixed global bits S = tau << 13. With P_ik = Q_ik + Q_ki (i < k, tile qubits),
+// d_i = Q_ii + sum_{s in S} (Q_is + Q_si) and E_S = sum_{s, s' in S} Q_ss',
+//   E(z) = E_S + sum_{i<8} t_i d_i + sum_{i<k<8} t_i t_k P_ik + Eh[j] + sum_{b in j} W_b(t),
+//   W_b(t) = sum_{i<8} t_i P_{i,8+b},   Eh[j] = sum_{b in j} d_{8+b} + sum_{b<c in j} P_{8+b,8+c},
+// every pair of set bits of z counted once with both Q_ik and Q_ki. The tables (scr: 256 floats)
+// are built once per tile; each thread's sums are unrolled with 0/1 weights (independent loads,
+// no serial chains). ev[j] receives the energies, also written to sE (unswizzled).
+__device__ __forceinline__ void w2_energies(int n, uint32_t zfix, const float* Qs, float* scr, float* sE,
                                             float (&ev)[32]) {
+    float* P = scr;           // 13 x 13, upper triangle
+    float* d = scr + 169;     // 13
+    float* Eh = scr + 184;    // 32
+    float* es = scr + 216;    // 1
     const uint32_t t = threadIdx.x;
-    if (t < 32u) {
-        float acc = 0.0f;
-        const uint32_t hb = t << 8;
-        for (uint32_t bi = hb; bi; bi &= bi - 1u) {
+    if (t < 169u) {
+        const int i = (int)t / 13, k = (int)t % 13;
+        P[t] = (i < k) ? Qs[i * n + k] + Qs[k * n + i] : 0.0f;
+    } else if (t < 182u) {
+        const int i = (int)t - 169;
+        float a = Qs[i * n + i];
+        for (uint32_t bs = zfix; bs; bs &= bs - 1u) {
+            const int sb = __ffs((int)bs) - 1;
+            a += Qs[i * n + sb] + Qs[sb * n + i];
+        }
+        d[i] = a;
+    } else if (t == 182u) {
+        float a = 0.0f;
+        for (uint32_t bi = zfix; bi; bi &= bi - 1u) {
             const int i = __ffs((int)bi) - 1;
-            for (uint32_t bj = hb; bj; bj &= bj - 1u) acc += Qs[i * n + __ffs((int)bj) - 1];
-            for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
-                const int j = __ffs((int)bj) - 1;
-                acc += Qs[i * n + j] + Qs[j * n + i];
-            }
+            for (uint32_t bj = zfix; bj; bj &= bj - 1u) a += Qs[i * n + __ffs((int)bj) - 1];
         }
-        eh[t] = acc;
+        *es = a;
     }
-    float base = 0.0f;
-    for (uint32_t bi = zfix; bi; bi &= bi - 1u) {
-        const int i = __ffs((int)bi) - 1;
-        for (uint32_t bj = zfix; bj; bj &= bj - 1u) base += Qs[i * n + __ffs((int)bj) - 1];
+    __syncthreads();
+    if (t < 32u) {
+        float a = 0.0f, c = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            const float wb = (float)((t >> b) & 1u);
+            a = fmaf(wb, d[8 + b], a);
+#pragma unroll
+            for (int e = b + 1; e < 5; ++e) c = fmaf(wb * (float)((t >> e) & 1u), P[(8 + b) * 13 + 8 + e], c);
+        }
+        Eh[t] = a + c;
     }
+    float tb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tb[i] = (float)((t >> i) & 1u);
+    float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f, b3 = 0.0f;
+#pragma unroll
     for (int i = 0; i < 8; ++i) {
-        float si = Qs[i * n + i];
-        for (uint32_t bj = zfix; bj; bj &= bj - 1u) {
-            const int j = __ffs((int)bj) - 1;
-            si += Qs[i * n + j] + Qs[j * n + i];
-        }
-        float cross = 0.0f;
-        for (int j = 0; j < i; ++j)
-            if ((t >> j) & 1u) cross += Qs[i * n + j] + Qs[j * n + i];
-        if ((t >> i) & 1u) base += si + cross;
+        b0 = fmaf(tb[i], d[i], b0);
+        float r = 0.0f;
+#pragma unroll
+        for (int k = i + 1; k < 8; ++k) r = fmaf(tb[k], P[i * 13 + k], r);
+        if (i & 1) b1 = fmaf(tb[i], r, b1);
+        else b2 = fmaf(tb[i], r, b2);
     }
+    float W[5];
+#pragma unroll
+    for (int bb = 0; bb < 5; ++bb) {
+        float w0 = 0.0f, w1 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            w0 = fmaf(tb[i], P[i * 13 + 8 + bb], w0);
+            w1 = fmaf(tb[i + 1], P[(i + 1) * 13 + 8 + bb], w1);
+        }
+        W[bb] = w0 + w1;
+    }
+    __syncthreads();   // Eh and es ready
+    const float base = *es + ((b0 + b3) + (b1 + b2));
     float X[32];
     X[0] = 0.0f;
 #pragma unroll
-    for (int b = 0; b < 5; ++b) {
-        float w = 0.0f;
-        const int q = 8 + b;
-        for (int i = 0; i < 8; ++i)
-            if ((t >> i) & 1u) w += Qs[i * n + q] + Qs[q * n + i];
+    for (int bb = 0; bb < 5; ++bb)
 #pragma unroll
-        for (int m = 0; m < (1 << b); ++m) X[m | (1 << b)] = X[m] + w;
-    }
-    __syncthreads();
+        for (int m = 0; m < (1 << bb); ++m) X[m | (1 << bb)] = X[m] + W[bb];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-        ev[j] = base + (eh[j] + X[j]);
+        ev[j] = base + (Eh[j] + X[j]);
         sE[t + ((uint32_t)j << 8)] = ev[j];
     }
+}
+
+// Block sum of one FP32 value per thread in double-float arithmetic (each partial an unevaluated
+// sum hi + lo of two floats, combined with Knuth's TwoSum), fixed order, returned to thread 0 as
+// one FP64 value: about 44 bits of precision without the FP64 pipe, whose latency on this part
+// would dominate a warp shuffle tree of FP64 adds. red: 2 * (NT / 32) floats.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ double block_sum_df(float v, float* red) {
+    float hi = v, lo = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, oh, s, e);
+        e += lo + ol;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) { red[2 * w] = hi; red[2 * w + 1] = lo; }
+    __syncthreads();
+    double tot = 0.0;
+    if (threadIdx.x == 0) {
+        float th = 0.0f, tl = 0.0f;
+        for (int i = 0; i < NT / 32; ++i) {
+            float s, e;
+            two_sum(th, red[2 * i], s, e);
+            e += tl + red[2 * i + 1];
+            th = s + e;
+            tl = e - (th - s);
+        }
+        tot = (double)th + (double)tl;
+    }
+    return tot;
+}
+
+// Top-k list of a tile whose amplitudes are in shared memory, given each thread's FP32
+// probability maximum pmax over its own 32 elements elem(i) -> (shared index, global index):
+// the bound is the k-th largest of the 256 thread maxima (k distinct elements are at least that
+// probable, so the tile's k-th largest probability is not below it); every element that can
+// reach it (FP32 test with the margins of WarpTopK::offer) goes to the candidate buffer with its
+// exact FP64 probability, and the candidates are ranked (probability descending, index
+// ascending). Returns false when the buffer overflowed (flat distributions); the caller then
+// falls back to tile_topk. Called by all threads; result in ts.out.
+template <typename Elem>
+__device__ __forceinline__ bool topk_own(const float2* sp, int k, float pmax, Elem&& elem, const TileTopk& ts,
+                                         float* wbound) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // (1) the k-th largest thread maximum of the tile: each warp offers its k largest (sorted),
+    //     the k-th largest of those 8k values is found by rank
+    const float srt = warp_sort_desc(pmax);
+    if (lane < k) ts.wb[warp * k + lane] = srt;
+    if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
+    __syncthreads();
+    const int nl = (NT / 32) * k;
+    if (threadIdx.x < (unsigned)nl) {
+        const float me = ts.wb[threadIdx.x];
+        int rank = 0;
+        for (int q = 0; q < nl; ++q) {
+            const float o = ts.wb[q];
+            rank += (o > me || (o == me && q < (int)threadIdx.x)) ? 1 : 0;
+        }
+        if (rank == k - 1) *wbound = me;
+    }
+    __syncthreads();
+    const float bnd = *wbound;
+    const float lo = bnd > 0.0f ? bnd * 0.99999904632568359375f : -1.0f;   // (1 - 2^-20)
+    // (2) candidates: only threads whose maximum can reach the bound scan their elements; a
+    //     candidate is buffered with its amplitude (the slot's probability field holds the two
+    //     floats) and its exact FP64 probability is formed afterwards, one thread per candidate,
+    //     so that the slow FP64 pipe never runs in a serial per-thread chain
+    if (pmax * 1.000003814697265625f >= lo) {
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            uint32_t ix, z;
+            elem(i, ix, z);
+            const float2 v = sp[ix];
+            const float pf = v.x * v.x + v.y * v.y;
+            if (pf * 1.00000095367431640625f >= lo) {
+                const int pos = atomicAdd(&ts.cnt[0], 1);
+                if (pos < TOPK_CAP) {
+                    ts.cand[pos].p = __hiloint2double(__float_as_int(v.y), __float_as_int(v.x));
+                    ts.cand[pos].z = z;
+                } else {
+                    ts.cnt[1] = 1;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (ts.cnt[1]) return false;
+    const int cnt = ts.cnt[0];
+    for (int c = threadIdx.x; c < cnt; c += NT) {
+        const double raw = ts.cand[c].p;
+        ts.cand[c].p = exact_prob(make_float2(__int_as_float(__double2loint(raw)), __int_as_float(__double2hiint(raw))));
+    }
+    __syncthreads();
+    // (3) rank selection (probability descending, index ascending: distinct ranks)
+    for (int c = threadIdx.x; c < cnt; c += NT) {
+        const TopEnt me = ts.cand[c];
+        int rank = 0;
+        for (int q = 0; q < cnt; ++q) {
+            const TopEnt o = ts.cand[q];
+            rank += better(o.p, o.z, me.p, me.z) ? 1 : 0;
+        }
+        if (rank < k) ts.out[rank] = me;
+    }
+    if (threadIdx.x < (unsigned)k && threadIdx.x >= (unsigned)cnt) ts.out[threadIdx.x] = TopEnt{-1.0, 0xffffffffu};
+    __syncthreads();
+    return true;
 }
 
 template <int H>
@@ -298,8 +458,6 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
     const CsOff o = cs_offsets(TPC);
     float2* sp = reinterpret_cast<float2*>(sm + o.psi);
     float* sE = reinterpret_cast<float*>(sm + o.E);
-    float* sQ = reinterpret_cast<float*>(sm + o.Q);
-    LayerConst<float>* lc = reinterpret_cast<LayerConst<float>*>(sm + o.lc);
     double* red = reinterpret_cast<double*>(sm + o.red);
     TileTopk ts;
     ts.wb = reinterpret_cast<float*>(sm + o.wb);
@@ -307,8 +465,6 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
     ts.cand = reinterpret_cast<TopEnt*>(sm + o.cand);
     ts.out = reinterpret_cast<TopEnt*>(sm + o.out);
     ts.wlists = reinterpret_cast<TopEnt*>(sm + o.wlists);
-    TopEnt* lists = reinterpret_cast<TopEnt*>(sm + o.lists);
-    double* cex = reinterpret_cast<double*>(sm + o.cex);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + o.mbar);
     if (threadIdx.x == 0) mbar_init(mbar, 1);
     __syncthreads();
@@ -316,34 +472,94 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
     bool ok = true;
     const int ncl = (int)(gridDim.x / C), cid = (int)(blockIdx.x / C);
     const TileRef<float> tile{sp, nullptr, sE, TB};
-    for (int ii = cid; ii < count; ii += ncl) {
-        const CsInstDev I = insts[ii];
-        const int n = I.n, p = I.p;
-        for (int i = threadIdx.x; i < n * n; i += NT) sQ[i] = I.Q[i];
-        set_layer_consts<float>(lc, I.gamma, I.beta, p, n, true);   // ends with a barrier
-        double my_ex = 0.0;
-        for (int pass = 0; pass <= p; ++pass) {
+
+    // Two instance slots per cluster, run in alternating steps: step j runs one pass of slot
+    // j % 2. A step ends with its bulk stores complete, a wait for the cluster barrier phase of
+    // step j - 1 and an arrival for step j, so the data a pass reads (written by the previous
+    // pass of the same slot, two steps earlier) is released by a phase that was waited for one
+    // step ago: the cluster barrier rarely stalls. Instances come from a fixed round-robin queue.
+    int sidx[2], spass[2], sfin[2];
+    int next = cid;
+    auto refill = [&](int sl) {
+        sidx[sl] = next < count ? next : -1;
+        next += ncl;
+        spass[sl] = 0;
+        sfin[sl] = -1;
+        if (sidx[sl] >= 0) {
+            const CsInstDev& I = insts[sidx[sl]];
+            float* sQ = reinterpret_cast<float*>(sm + o.Q[sl]);
+            for (int i = threadIdx.x; i < I.n * I.n; i += NT) sQ[i] = I.Q[i];
+            set_layer_consts<float>(reinterpret_cast<LayerConst<float>*>(sm + o.lc[sl]), I.gamma, I.beta, I.p,
+                                    I.n, true);   // ends with a barrier
+        }
+    };
+    refill(0);
+    refill(1);
+    // thread 0: TMA load of tile tau of a pass of instance I into the buffers
+    const auto issue_load = [&](const CsInstDev& I, bool kindA, uint32_t tau) {
+        fence_async_global();
+        mbar_expect_tx(mbar, TD * 8 + TD * 4);
+        if (kindA) {
+            tma_load_4d(sp, &I.maps[0], 0, 0, 0, (int)tau, mbar);
+            tma_load_3d(sE, &I.maps[2], 0, 0, (int)tau, mbar);
+        } else {
+            tma_load_4d(sp, &I.maps[1], 0, 0, (int)tau, 0, mbar);
+            tma_load_4d(sE, &I.maps[3], 0, 0, (int)tau, 0, mbar);
+        }
+    };
+    bool prefetched = false;   // the first tile of this step was loaded at the end of the last one
+
+    int j = 0;
+    for (;; ++j) {
+        const int sl = j & 1;
+        if (sfin[sl] >= 0) {
+            // the instance of this slot finished two steps ago (its final pass is visible to the
+            // cluster): rank 0 merges the CTAs' <C> partials (rank order) and top-k lists
+            if (rank == 0) {
+                const CsInstDev& I = insts[sidx[sl]];
+                double* cex = reinterpret_cast<double*>(sm + o.cex[sl]);
+                TopEnt* lists = reinterpret_cast<TopEnt*>(sm + o.lists[sl]);
+                if (threadIdx.x == 0 && I.expect) {
+                    double acc = 0.0;
+                    for (int r = 0; r < C; ++r) acc += *cl.map_shared_rank(cex, r);
+                    *I.expect = acc;
+                }
+                if (I.k > 0) {
+                    const int per = TPC * I.k;
+                    for (int e = threadIdx.x; e < C * per; e += NT)
+                        ts.cand[e] = cl.map_shared_rank(lists, e / per)[e % per];
+                    __syncthreads();
+                    rank_select(ts.cand, C * per, I.k, ts.out);
+                    __syncthreads();
+                    if (threadIdx.x < (unsigned)I.k) {
+                        const TopEnt e = ts.out[threadIdx.x];
+                        if (I.topk_idx) I.topk_idx[threadIdx.x] = (uint64_t)e.z;
+                        if (I.topk_prob) I.topk_prob[threadIdx.x] = e.p;
+                    }
+                }
+            }
+            __syncthreads();
+            refill(sl);
+        }
+        if (sidx[0] < 0 && sidx[1] < 0) break;
+        if (sidx[sl] >= 0) {
+            const CsInstDev I = insts[sidx[sl]];
+            const float* sQ = reinterpret_cast<const float*>(sm + o.Q[sl]);
+            const LayerConst<float>* lc = reinterpret_cast<const LayerConst<float>*>(sm + o.lc[sl]);
+            TopEnt* lists = reinterpret_cast<TopEnt*>(sm + o.lists[sl]);
+            const int n = I.n, p = I.p, pass = spass[sl];
             const bool kindA = (pass & 1) == 0;
             const bool fin = pass == p;
-            for (int j = 0; j < TPC; ++j) {
-                const uint32_t tau = rank + (uint32_t)(j * C);
-                // the bulk stores of the previous tile must have read the buffers before they are
+            double my_ex = 0.0;
+            for (int jt = 0; jt < TPC; ++jt) {
+                const uint32_t tau = rank + (uint32_t)(jt * C);
+                float accp = 0.0f, pmax = -1.0f;   // final pass: FP32 <C> terms (32 per thread) and max |psi|^2
+                // the bulk stores of the previous tile have read the buffers before they are
                 // refilled (by TMA in passes > 0, by the threads in pass 0)
                 if (threadIdx.x == 0) bulk_wait_read();
-                if (pass == 0 && j > 0) __syncthreads();
+                if (pass == 0 && jt > 0) __syncthreads();
                 if (pass > 0) {
-                    if (threadIdx.x == 0) {
-                        if (ok) {
-                            mbar_expect_tx(mbar, TD * 8 + TD * 4);
-                            if (kindA) {
-                                tma_load_4d(sp, &I.maps[0], 0, 0, 0, (int)tau, mbar);
-                                tma_load_3d(sE, &I.maps[2], 0, 0, (int)tau, mbar);
-                            } else {
-                                tma_load_4d(sp, &I.maps[1], 0, 0, (int)tau, 0, mbar);
-                                tma_load_4d(sE, &I.maps[3], 0, 0, (int)tau, 0, mbar);
-                            }
-                        }
-                    }
+                    if (threadIdx.x == 0 && ok && !(jt == 0 && prefetched)) issue_load(I, kindA, tau);
                     if (ok) ok = mbar_wait_bounded(mbar, parity);
                     ok = __syncthreads_and(ok);
                     parity ^= 1u;
@@ -352,7 +568,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                     if (pass == 0) {
                         // energies, |+>, the first cost phase and layer 0 on window [8, 13)
                         float ev[32];
-                        w2_energies(n, tau << TB, sQ, reinterpret_cast<float*>(ts.wlists), sE, ev);
+                        w2_energies(n, tau << TB, sQ, reinterpret_cast<float*>(sm + o.escr), sE, ev);
                         const uint32_t t = threadIdx.x;
                         const int pc = __popc(tau) + __popc(t);
                         float2 v[32];
@@ -380,8 +596,14 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                         if (!fin) {
                             phase_group<5>(v, sE, threadIdx.x, 8, lc[pass]);
                             mix_layer<5>(v, 31, lc[pass]);
-                        } else if (lc[p - 1].shear) {
-                            scale_group<5>(v, lc[p - 1].post);
+                        } else {
+                            if (lc[p - 1].shear) scale_group<5>(v, lc[p - 1].post);
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                const float pr = v[i].x * v[i].x + v[i].y * v[i].y;
+                                accp = fmaf(pr, sE[threadIdx.x + (i << 8)], accp);
+                                pmax = fmaxf(pmax, pr);
+                            }
                         }
                         w2_store(sp, v);
                         if (!fin) {
@@ -403,8 +625,14 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                         if (!fin) {
                             phase_group<H>(v, sE, lo, CB, lc[pass]);
                             mix_layer<H>(v, (1 << H) - 1, lc[pass]);
-                        } else if (lc[p - 1].shear) {
-                            scale_group<H>(v, lc[p - 1].post);
+                        } else {
+                            if (lc[p - 1].shear) scale_group<H>(v, lc[p - 1].post);
+#pragma unroll
+                            for (int i = 0; i < (1 << H); ++i) {
+                                const float pr = v[i].x * v[i].x + v[i].y * v[i].y;
+                                accp = fmaf(pr, sE[lo + ((uint32_t)i << CB)], accp);
+                                pmax = fmaxf(pmax, pr);
+                            }
                         }
 #pragma unroll
                         for (int i = 0; i < (1 << H); ++i) sp[b + ((uint32_t)i << CB)] = v[i];
@@ -421,16 +649,39 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                         bulk_commit();
                     }
                 } else {
-                    // <C> partial and top-k list of the tile; the state leaves in the standard frame
+                    // <C> partial and top-k list of the tile (the top-k scratch overlays the
+                    // energies once the partial has read them); the state leaves in the
+                    // standard frame
                     const uint32_t cmask = (1u << CB) - 1u;
                     const auto zmap = [kindA, tau, cmask](uint32_t u) -> uint32_t {
                         return kindA ? (u | (tau << TB)) : ((u & cmask) | (tau << CB) | ((u >> CB) << TB));
                     };
-                    double ex = 0.0;
-                    tile_reduce<float, TmaLayout>(tile, I.k, zmap, ts, ex);
-                    const double tot = block_sum(ex, red);
+                    // this thread's 32 elements in the final sub-pass: shared index and global index
+                    const auto elem = [kindA, tau](int i, uint32_t& ix, uint32_t& z) {
+                        if (kindA) {
+                            ix = psw(threadIdx.x) + ((uint32_t)i << 8);
+                            z = threadIdx.x | ((uint32_t)i << 8) | (tau << TB);
+                        } else {
+                            const uint32_t lo = threadIdx.x + (uint32_t)((i >> H) * NT), e = (uint32_t)(i & ((1 << H) - 1));
+                            ix = psw(lo) + (e << CB);
+                            z = lo | (tau << CB) | (e << TB);
+                        }
+                    };
+                    const double tot = block_sum_df(accp, reinterpret_cast<float*>(red));   // its barriers end every energy read
                     if (threadIdx.x == 0) my_ex += tot;
-                    if (threadIdx.x < (unsigned)I.k) lists[j * I.k + threadIdx.x] = ts.out[threadIdx.x];
+                    if (I.k > 0) {
+                        if (!topk_own(sp, I.k, pmax, elem, ts, reinterpret_cast<float*>(sm + o.wbound))) {
+                            // flat distribution: the tile-wide selection, with each thread's maximum
+                            // over the elements tile_topk assigns to it
+                            float pm2 = -1.0f;
+                            for (uint32_t u = threadIdx.x; u < TD; u += NT) {
+                                const float2 v = sp[psw(u)];
+                                pm2 = fmaxf(pm2, v.x * v.x + v.y * v.y);
+                            }
+                            tile_topk<float, TmaLayout>(tile, I.k, pm2, zmap, ts);
+                        }
+                        if (threadIdx.x < (unsigned)I.k) lists[jt * I.k + threadIdx.x] = ts.out[threadIdx.x];
+                    }
                     if (I.out_psi) {
                         __syncthreads();
                         for (uint32_t u = threadIdx.x; u < TD; u += NT)
@@ -446,45 +697,48 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                     __syncthreads();
                 }
             }
-            // pass boundary: this CTA's stores are complete and visible, then the cluster barrier
-            if (threadIdx.x == 0) {
-                bulk_wait_all();
-                fence_async_global();
-            }
-            if (fin && threadIdx.x == 0) *cex = my_ex;
-            cl.sync();
-            if (threadIdx.x == 0) fence_async_global();
-        }
-        // rank 0 merges the CTAs' <C> partials (rank order) and top-k lists
-        if (rank == 0) {
-            if (threadIdx.x == 0 && I.expect) {
-                double acc = 0.0;
-                for (int r = 0; r < C; ++r) acc += *cl.map_shared_rank(cex, r);
-                *I.expect = acc;
-            }
-            if (I.k > 0) {
-                const int per = TPC * I.k;
-                for (int e = threadIdx.x; e < C * per; e += NT)
-                    ts.cand[e] = cl.map_shared_rank(lists, e / per)[e % per];
+            if (fin) {
+                if (threadIdx.x == 0) *reinterpret_cast<double*>(sm + o.cex[sl]) = my_ex;
+                sfin[sl] = j;
+            } else {
+                spass[sl] = pass + 1;
             }
         }
-        cl.sync();   // the lists of every rank have been read
-        if (rank == 0 && I.k > 0) {
-            rank_select(ts.cand, C * TPC * I.k, I.k, ts.out);
-            __syncthreads();
-            if (threadIdx.x < (unsigned)I.k) {
-                const TopEnt e = ts.out[threadIdx.x];
-                if (I.topk_idx) I.topk_idx[threadIdx.x] = (uint64_t)e.z;
-                if (I.topk_prob) I.topk_prob[threadIdx.x] = e.p;
-            }
-        }
+        // end of step j: wait for the phase of step j - 1 (the data of the other slot's next pass is
+        // then complete), start loading that pass's first tile (once this step's stores have read
+        // the buffers), then complete this step's stores and arrive for step j
         __syncthreads();
+        if (j > 0) cluster_wait();
+        {
+            const int ns = (j + 1) & 1;
+            prefetched = sidx[ns] >= 0 && sfin[ns] < 0 && spass[ns] > 0;
+            if (prefetched && threadIdx.x == 0) {
+                bulk_wait_read();
+                if (ok) issue_load(insts[sidx[ns]], (spass[ns] & 1) == 0, rank);
+            }
+        }
+        if (threadIdx.x == 0) {
+            bulk_wait_all();
+            fence_async_global();
+        }
+        // no thread starts the next step (whose merge on rank 0 writes into the energy tile) before
+        // this step's bulk stores have finished reading the buffers
+        __syncthreads();
+        if (threadIdx.x < 32) cluster_arrive_release();
+        else cluster_arrive();
     }
+    // The loop ends at the start of a step in which rank 0 may have just read every rank's
+    // shared memory (the last merge): one more arrival (after that merge) and wait, so that no CTA
+    // leaves before rank 0 is done with its shared memory.
+    if (j > 0) cluster_wait();   // steps 0..j-1 each arrived once
+    __syncthreads();
+    if (threadIdx.x < 32) cluster_arrive_release();
+    else cluster_arrive();
+    cluster_wait();
     if (threadIdx.x == 0) {
         bulk_wait_all();
         if (!ok) atomicOr(status, 1u);
     }
-    cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 template <int H>

@@ -149,3 +149,24 @@ def test_cstream_batch_invariance(q):
         if ret:
             so = full["rows"][i][6]
             np.testing.assert_array_equal(alone["psi"][:2 << n], full["psi"][2 * so:2 * so + (2 << n)])
+
+
+@pytest.mark.parametrize("n,p,ret", [(16, 3, False), (16, 3, True), (15, 2, True), (17, 1, True)])
+def test_cstream_refilled_slots_agree_with_streaming_tier(q, n, p, ret):
+    # far more instances than clusters: every cluster refills both of its instance slots several
+    # times; every instance must agree with the streaming tier (<C>, and the state and energies
+    # when returned)
+    specs = [(n, p, 8, ret)] * 330
+    a = run(q, specs, seed=3400 + n)
+    b = run(q, specs, seed=3400 + n, tier=q.QAOA_TIER_STREAM)
+    bad_ex, bad_psi, bad_e = [], [], []
+    for i, (nn, pp, k, _, qo, po, so, eo) in enumerate(a["rows"]):
+        absq = float(np.abs(a["Qs"][i]).sum())
+        if not abs(a["ex"][i] - b["ex"][i]) <= 2e-5 * absq:
+            bad_ex.append(i)
+        if so >= 0:
+            if np.abs(a["psi"][2 * so:2 * (so + (1 << nn))] - b["psi"][2 * so:2 * (so + (1 << nn))]).max() > 2e-5:
+                bad_psi.append(i)
+            if np.abs(a["E"][eo:eo + (1 << nn)] - b["E"][eo:eo + (1 << nn)]).max() > 1e-5 * absq:
+                bad_e.append(i)
+    assert not (bad_ex or bad_psi or bad_e), (bad_ex[:20], bad_psi[:20], bad_e[:20], len(bad_ex))
