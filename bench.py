@@ -703,22 +703,37 @@ def run_uneven(args):
     ps = np.array([len(x[1]) for x in inst])
     ctx = q.qaoa_create(local)
     B = QAOABatch(ctx, [x[0] for x in inst], [(x[1], x[2]) for x in inst], device=dev)
+    # a side stream: the plan is captured into a CUDA graph there (capture needs a non-legacy stream)
+    gs = torch.cuda.Stream(dev)
+    stream = gs
     for _ in range(args.warmup):
         B.run(stream)
         B.adam_step(U["lr"], stream)
     torch.cuda.synchronize()
+    # (1) per-kernel event timing of uncaptured steps: the roofline's kernel durations
     kern = {}
     q.qaoa_plan_set_timing(B.plan, True)
 
-    def body(s):
+    def body_timed(s):
         B.run(stream)
         _plan_kern_times(q, B.plan, kern)
         B.adam_step(U["lr"], stream)
+    with Clocks(local) as clk_k:
+        kstep_ms = _timed_steps(stream, args.steps, body_timed)
+    roof = plan_roofline(q, B.plan, kern, lambda: B.run(stream), clk_k, dev, workload=f"uneven_{U['count']}")
+    q.qaoa_plan_set_timing(B.plan, False)
+    # (2) the timed steps: one graph replay of the whole batch plus the Adam kernel per step
+    B.capture(stream)
+    B.run(stream)
+    B.adam_step(U["lr"], stream)
+    torch.cuda.synchronize()
+
+    def body(s):
+        B.run(stream)
+        B.adam_step(U["lr"], stream)
     with Clocks(local) as clk:
         step_ms = _timed_steps(stream, args.steps, body)
-    q.qaoa_plan_set_timing(B.plan, False)
     tot_s = max_over_ranks(sum(step_ms) / 1e3, dev)
-    roof = plan_roofline(q, B.plan, kern, lambda: B.run(stream), clk, dev, workload=f"uneven_{U['count']}")
     amps = float(np.sum((2.0 ** ns) * ps))
     # e2e: Q pool and parameters from pinned host memory, <C> of every instance back, per step
     qh = B.q.cpu().pin_memory()
@@ -727,13 +742,14 @@ def run_uneven(args):
     e2e_steps = max(2, args.steps // 4)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        B.q.copy_(qh, non_blocking=True)
-        B.params.copy_(ph, non_blocking=True)
-        B.run(stream)
-        B.adam_step(U["lr"], stream)
-        eh.copy_(B.expect, non_blocking=True)
-        torch.cuda.synchronize()
+    with torch.cuda.stream(stream):      # the copies are ordered with the graph on the same stream
+        for s in range(e2e_steps):
+            B.q.copy_(qh, non_blocking=True)
+            B.params.copy_(ph, non_blocking=True)
+            B.run(stream)
+            B.adam_step(U["lr"], stream)
+            eh.copy_(B.expect, non_blocking=True)
+            torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
     kernels = B.kernels_per_launch + 1
     B.close()
@@ -752,7 +768,9 @@ def run_uneven(args):
                  e2e={"value": B.count * e2e_steps * world / e2e_s, "unit": "instance-steps/s",
                       "h2d_bytes_per_step": int(qh.numel() * 4 + ph.numel() * 4),
                       "d2h_bytes_per_step": B.count * 8},
-                 gpu_launches=kernels * args.steps, clocks=clk.summary())
+                 gpu_launches=kernels * args.steps,
+                 launch_calls_per_step={"graph": 1, "kernel": 1, "kernels_in_graph": kernels - 1},
+                 uncaptured_ms_per_step=float(np.mean(kstep_ms)), clocks=clk.summary())
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

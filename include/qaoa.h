@@ -182,7 +182,10 @@ void qaoa_cobyla_destroy(qaoa_cobyla* s);
 qaoa_status qaoa_expect_topk_static(int n, const void* psi, const float* E, int k, double* expect,
                                     uint64_t* idx, double* prob, qaoa_stream_t stream);
 
-/* Adjoint gradient of <C> from |+> through p layers (the reverse state-vector sweep):
+/* Adjoint gradient of <C> with respect to (gamma, beta) from |+> through p layers: the reverse
+ * state-vector sweep of Jones & Gacon (2020, "Efficient calculation of gradients in classical
+ * simulations of variational quantum algorithms"), the gradient source that stands in for the
+ * paper's gradient-free COBYLA loop over the angles of Eq. 2 (Section IV).
  * expect (1 double, may be NULL), dgamma[p], dbeta[p] doubles (device). Uses workspace for the
  * forward and adjoint states when n exceeds the shared-memory tier. */
 qaoa_status qaoa_grad(qaoa_ctx* ctx, int n, int p, const float* gamma, const float* beta,
@@ -271,7 +274,11 @@ qaoa_status qaoa_plan_check(qaoa_plan* plan);
 /* Free the plan (synchronises the device first). NULL is ignored. */
 void qaoa_plan_destroy(qaoa_plan* plan);
 
-/* plan_create + plan_launch + (after a stream synchronisation) plan_destroy. Synchronous. */
+/* plan_create + plan_launch + (after a stream synchronisation) plan_destroy. Synchronous.
+ * The plan (descriptors and streaming scratch) is placed in the context workspace when that is
+ * at least as large as the plan (size it with qaoa_reserve): the call then allocates nothing.
+ * Otherwise the plan is allocated for the call, so repeated calls belong on a set-up path;
+ * the allocation-free hot path is a plan created once and launched with qaoa_plan_launch. */
 qaoa_status qaoa_batch_run(qaoa_ctx* ctx, const qaoa_inst* desc, int count,
                            const qaoa_batch_io* io, qaoa_stream_t stream);
 qaoa_status qaoa_batch_run_z(qaoa_ctx* ctx, const qaoa_inst* desc, int count,

@@ -640,7 +640,7 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     if (need) *need = bytes;
     cudaError_t e = cudaSuccess;
     if (mem) {
-        if (bytes > mem->bytes || sbase > mem->staging_bytes) {
+        if (bytes > mem->bytes || (mem->staging && sbase > mem->staging_bytes)) {
             delete P;
             return fail(QAOA_E_NOMEM, "plan needs %zu bytes (%zu of header), %zu / %zu provided", bytes, sbase,
                         mem->bytes, mem->staging_bytes);
@@ -743,7 +743,7 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
     }
     // upload the header: synchronously into the plan's own memory, else asynchronously on the
     // caller's stream from its pinned staging buffer
-    if (mem) {
+    if (mem && mem->staging) {
         std::memcpy(mem->staging, img.data(), sbase);
         e = cudaMemcpyAsync(base, mem->staging, sbase, cudaMemcpyHostToDevice, mem->st);
     } else {
@@ -1037,8 +1037,26 @@ extern "C" void qaoa_plan_destroy(qaoa_plan* P) {
 
 static qaoa_status batch_run(qaoa_ctx* c, const qaoa_inst* desc, int count, const qaoa_batch_io* io,
                              qaoa_stream_t stream, int dbl) {
+    if (!c || !desc || !io || count < 1 || !io->q || !io->params)
+        return fail(QAOA_E_INVALID, "batch_run: NULL argument or count < 1");
+    CK(cudaSetDevice(c->device));
     qaoa_plan* P = nullptr;
-    qaoa_status s = qaoa_plan_create(c, desc, count, io, dbl, &P);
+    // the plan's bytes: placed in the context workspace when it is large enough (no allocation),
+    // else allocated for this call
+    size_t need = 0;
+    const PlanMem probe{nullptr, 0, (cudaStream_t)stream, nullptr, 0};
+    qaoa_status s = dbl ? plan_create_t<double>(c, desc, count, io, &probe, &P, &need)
+                        : plan_create_t<float>(c, desc, count, io, &probe, &P, &need);
+    if (s != QAOA_OK && s != QAOA_E_NOMEM) return s;
+    P = nullptr;
+    if (need > 0 && need <= c->ws_bytes) {
+        CK(cudaStreamSynchronize((cudaStream_t)stream));   // earlier work on the stream may use the workspace
+        const PlanMem inws{c->ws, c->ws_bytes, (cudaStream_t)stream, nullptr, 0};
+        s = dbl ? plan_create_t<double>(c, desc, count, io, &inws, &P)
+                : plan_create_t<float>(c, desc, count, io, &inws, &P);
+    } else {
+        s = qaoa_plan_create(c, desc, count, io, dbl, &P);
+    }
     if (s) return s;
     s = qaoa_plan_launch(P, stream);
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

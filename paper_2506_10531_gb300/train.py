@@ -12,8 +12,8 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (QAOA_INST_GRAD, Cobyla, make_insts, make_io, qaoa_adam_step, qaoa_plan_create,
-               qaoa_plan_destroy, qaoa_plan_kernel_count, qaoa_plan_launch)
+from . import (QAOA_INST_GRAD, Cobyla, make_insts, make_io, qaoa_adam_step, qaoa_plan_capture,
+               qaoa_plan_create, qaoa_plan_destroy, qaoa_plan_kernel_count, qaoa_plan_launch)
 
 
 def footprint_bytes(n: int, grad: bool = True) -> int:
@@ -59,14 +59,24 @@ class QAOABatch:
         self.m = torch.zeros(poff, dtype=torch.float32, device=device)
         self.v = torch.zeros(poff, dtype=torch.float32, device=device)
         self.steps_done = 0
+        self.captured = False
 
     @property
     def kernels_per_launch(self) -> int:
         return qaoa_plan_kernel_count(self.plan)
 
     def run(self, stream=None):
-        """<C> (and gradients) of every instance at the current parameters (async)."""
+        """<C> (and gradients) of every instance at the current parameters (async). After
+        capture() this replays the captured graph: one launch for the whole batch."""
         qaoa_plan_launch(self.plan, stream)
+
+    def capture(self, stream):
+        """Record the plan's launch sequence into a CUDA graph on `stream` (not the legacy
+        default stream); every later run() replays it with one graph launch. The graph reads the
+        bound pools, so parameters updated in place are seen. Per-kernel timing is off for a
+        captured plan."""
+        qaoa_plan_capture(self.plan, stream)
+        self.captured = True
 
     def adam_step(self, lr: float, stream=None, beta1=0.9, beta2=0.999, eps=1e-8):
         self.steps_done += 1
@@ -111,11 +121,14 @@ class QAOAExpectation(torch.autograd.Function):
 def adam_train(batch: QAOABatch, steps: int, lr: float, stream=None):
     """`steps` Adam steps of every instance's parameters; returns <C> before each step
     (device tensor [steps, count])."""
+    import contextlib
     hist = torch.zeros(steps, batch.count, dtype=torch.float64, device=batch.params.device)
-    for s in range(steps):
-        batch.run(stream)
-        hist[s].copy_(batch.expect)
-        batch.adam_step(lr, stream)
+    on = torch.cuda.stream(stream) if isinstance(stream, torch.cuda.Stream) else contextlib.nullcontext()
+    with on:   # the history copies are ordered with the launches on the same stream
+        for s in range(steps):
+            batch.run(stream)
+            hist[s].copy_(batch.expect)
+            batch.adam_step(lr, stream)
     return hist
 
 

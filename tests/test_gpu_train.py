@@ -160,3 +160,25 @@ def test_adam_training_matches_oracle_at_final_params(q, ctx, orc):
         assert np.mean(final < h[0]) >= 0.75
     finally:
         B.close()
+
+
+def test_training_through_a_captured_graph_is_identical(q, ctx):
+    # the same Adam run with the batch plan launched kernel by kernel and replayed from one
+    # captured CUDA graph per step: identical parameters and <C> history, bit for bit
+    from paper_2506_10531_gb300.train import QAOABatch, adam_train
+    inst = sample_batch(40, seed=34, n_hi=20)
+    s = torch.cuda.Stream()
+    A = QAOABatch(ctx, [x[0] for x in inst], [(x[1], x[2]) for x in inst])
+    B = QAOABatch(ctx, [x[0] for x in inst], [(x[1], x[2]) for x in inst])
+    try:
+        ha = adam_train(A, 5, 0.05, stream=s)
+        B.capture(s)
+        hb = adam_train(B, 5, 0.05, stream=s)
+        s.synchronize()
+        assert B.captured and not A.captured
+        assert torch.equal(ha, hb)
+        assert torch.equal(A.params, B.params)
+        assert torch.equal(A.grad, B.grad)
+    finally:
+        A.close()
+        B.close()
