@@ -353,7 +353,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-HBM_FAMILIES = ("stream_pass", "stream_adjoint", "energy", "stream_finalize", "stream_grad_reduce")
+HBM_FAMILIES = ("stream_pass", "tstream_pass", "stream_adjoint", "energy", "stream_finalize", "stream_grad_reduce")
 
 
 def plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=None, steps=None, workload=None):

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libqaoa.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["qaoa_api.cu", "k_resident.cu", "k_cluster.cu", "k_stream.cu", "k_plain.cu", "k_dqaoa.cu",
-           "k_noalloc.cu", "k_cstream.cu", "qaoa_server.cu", "qaoa_tune.cu", "k_sample.cu", "dqaoa_host.cpp", "cobyla.cpp"]
+           "k_noalloc.cu", "k_cstream.cu", "k_tstream.cu", "qaoa_server.cu", "qaoa_tune.cu", "k_sample.cu", "dqaoa_host.cpp", "cobyla.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without FP contraction: the host merge rounds the same way on every architecture
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr",

@@ -1,0 +1,512 @@
+// k_tstream.cu -- TMA streaming passes of the HBM tier (complex64 states of n >= 14 qubits whose
+// passes walk the whole state in HBM; Section IV, Eq. 2: cost phase and mixer per layer, <C> and
+// the top-k bitstrings at the end).
+//
+// Each pass is one persistent launch, one CTA per SM, walking the tiles of every instance of its
+// plan group. A tile is 2^13 amplitudes, moved between HBM and shared memory by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) through a ring of three stages: while the CTA works
+// on tile k, the load of tile k + 1 is in flight and the bulk store of tile k - 1 drains, so the
+// pass keeps HBM busy in both directions. The energies are read straight from HBM inside the
+// sub-pass that needs them (the cost phase or the <C> partial): their lanes cover tile bits 0..4,
+// so every warp reads whole 128-byte lines, and the shared memory goes to the ring.
+//
+// Tiles follow the streaming tier's pass plan (stream_plan): kind A holds qubits 0..12 (2^13
+// contiguous amplitudes), kind B the 2^c contiguous amplitudes of qubits 0..c-1 times the 2^h
+// values of qubits s..s+h-1 (c = 13 - h, 1 <= h <= 9). Inside a tile the qubits are mixed in
+// register windows of at most five bits: kind A in [0,4), [4,8), [8,13) (the cost phase in the
+// last), kind B in [c, c+h) or, for h > 5, [c, c+5) and [c+5, c+h) (the phase in the last). With
+// the lanes of a warp on tile bits outside the window, the swizzle makes every shared access free
+// of bank conflicts. The final pass reduces each tile to an FP64 <C> partial and a top-k list;
+// the streaming tier's finalize kernel merges them per instance.
+#include <cuda.h>
+
+#include "qaoa_engine.cuh"
+#include "qaoa_kernels.h"
+#include "qaoa_stream.h"
+#include "qaoa_tma.cuh"
+#include "qaoa_tstream.h"
+
+namespace qaoa {
+
+namespace {
+
+using namespace tma;
+
+constexpr int TB = 13;
+constexpr uint32_t TD = 1u << TB;
+constexpr int NT = TMA_NT;
+constexpr int NSTAGE = 3;
+
+struct TsOff {
+    size_t stage[NSTAGE], lc, red, wbound, wb, cnt, cand, out, wlists, mbar, total;
+};
+__host__ __device__ inline size_t ts_al(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline TsOff ts_offsets() {
+    TsOff o{};
+    size_t x = 0;
+    for (int s = 0; s < NSTAGE; ++s) { o.stage[s] = x; x += (size_t)TD * 8; }   // 1024-aligned at run time
+    o.lc = x; x = ts_al(x + 64 * sizeof(LayerConst<float>));
+    o.red = x; x = ts_al(x + 32 * sizeof(float));
+    o.wbound = x; x = ts_al(x + sizeof(float));
+    o.wb = x; x = ts_al(x + 16 * (NT / 32) * sizeof(float));
+    o.cnt = x; x = ts_al(x + 4 * sizeof(int));
+    o.cand = x; x = ts_al(x + TOPK_CAP * sizeof(TopEnt));
+    o.out = x; x = ts_al(x + 16 * sizeof(TopEnt));
+    o.wlists = x; x = ts_al(x + (NT / 32) * 32 * sizeof(TopEnt));
+    o.mbar = x; x = ts_al(x + NSTAGE * sizeof(uint64_t));
+    o.total = x + 1024;
+    return o;
+}
+
+// Geometry of one tile of a pass: global index of tile-local index u is
+//   kind A: u | zt,  kind B: (u & lomask) | zt | ((u >> c) << s),
+// with zt the bits that the tile index fixes.
+struct Geo {
+    uint32_t lomask;
+    int c, s;
+    uint64_t zt;
+    bool kindA;
+    __device__ __forceinline__ uint64_t z(uint32_t u) const {
+        return kindA ? ((uint64_t)u | zt) : ((uint64_t)(u & lomask) | zt | ((uint64_t)(u >> c) << s));
+    }
+};
+
+// Group g of a window [A, A+R): tile index of its element 0 (the window bits clear).
+template <int A, int R>
+__device__ __forceinline__ uint32_t wbase(uint32_t g) {
+    return (g & ((1u << A) - 1u)) | ((g >> A) << (A + R));
+}
+// Shared index of element i of a group whose base has shared index pb (the swizzle is linear
+// over GF(2); for A >= 7 the window bits lie above the swizzled bits and the XOR is an add).
+template <int A>
+__device__ __forceinline__ uint32_t wix(uint32_t pb, int i) {
+    if constexpr (A >= 7) return pb + ((uint32_t)i << A);
+    else return pb ^ psw((uint32_t)i << A);
+}
+
+template <int A, int R>
+__device__ __forceinline__ void wload(const float2* sp, uint32_t pb, float2 (&v)[1 << R]) {
+    if constexpr (A == 0 && R >= 1) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2) {
+            const float4 q = *reinterpret_cast<const float4*>(sp + (pb ^ (uint32_t)j));
+            v[j] = make_float2(q.x, q.y);
+            v[j + 1] = make_float2(q.z, q.w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) v[i] = sp[wix<A>(pb, i)];
+    }
+}
+template <int A, int R>
+__device__ __forceinline__ void wstore(float2* sp, uint32_t pb, const float2 (&v)[1 << R]) {
+    if constexpr (A == 0 && R >= 1) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2)
+            *reinterpret_cast<float4*>(sp + (pb ^ (uint32_t)j)) = make_float4(v[j].x, v[j].y, v[j + 1].x, v[j + 1].y);
+    } else {
+#pragma unroll
+        for (int i = 0; i < (1 << R); ++i) sp[wix<A>(pb, i)] = v[i];
+    }
+}
+
+// What one sub-pass does to a group, in order: the mixer of layer la; then, with `phase`, the
+// cost phase of layer lb and its mixer; with `init`, the group starts as |+> (rotated frame)
+// followed by the cost phase of layer 0 and its mixer (la, phase unused); with `fin`, the
+// pending shear factor of the last layer and the thread's FP32 <C> terms and maximum |psi|^2.
+struct SubOps {
+    int la, lb;
+    bool mix_la, phase, init, fin;
+};
+
+// One sub-pass over window [A, A+R) of the tile in sp: every group of the thread (2^(13-R) /
+// 256 of them) is loaded, transformed and stored. zsh: shift of the window's bit 0 in the global
+// index (kind A: A; kind B: A - c + s).
+template <int A, int R>
+__device__ __forceinline__ void wsub(float2* sp, const Geo& geo, int zsh, const SubOps& op,
+                                     const LayerConst<float>* lc, const float* __restrict__ E, float amp0,
+                                     float& accp, float& pmax) {
+    constexpr int NGT = (1 << (TB - R)) / NT;   // groups per thread
+#pragma unroll 1
+    for (int r = 0; r < NGT; ++r) {
+        const uint32_t g = threadIdx.x + (uint32_t)(r * NT);
+        const uint32_t base = wbase<A, R>(g);
+        const uint32_t pb = psw(base);
+        const uint64_t zb = geo.z(base);
+        float2 v[1 << R];
+        if (op.init) {
+            const int pc = __popcll(zb);
+#pragma unroll
+            for (int i = 0; i < (1 << R); ++i) {
+                float s, c;
+                sincos_phase(lc[0].gpi, __ldg(E + zb + ((uint64_t)i << zsh)), s, c);
+                v[i] = times_i_pow(make_float2(amp0 * c, -amp0 * s), pc + __popc(i));
+            }
+            mix_layer<R>(v, (1 << R) - 1, lc[0]);
+        } else {
+            wload<A, R>(sp, pb, v);
+            if (op.mix_la) mix_layer<R>(v, (1 << R) - 1, lc[op.la]);
+            if (op.phase) {
+                const LayerConst<float>& k = lc[op.lb];
+#pragma unroll
+                for (int i = 0; i < (1 << R); ++i) {
+                    float s, c;
+                    sincos_phase(k.gpi, __ldg(E + zb + ((uint64_t)i << zsh)), s, c);
+                    rot_neg(v[i], s * k.pre, c * k.pre);
+                }
+                mix_layer<R>(v, (1 << R) - 1, k);
+            }
+            if (op.fin) {
+                if (lc[op.la].shear) scale_group<R>(v, lc[op.la].post);
+#pragma unroll
+                for (int i = 0; i < (1 << R); ++i) {
+                    const float pr = v[i].x * v[i].x + v[i].y * v[i].y;
+                    accp = fmaf(pr, __ldg(E + zb + ((uint64_t)i << zsh)), accp);
+                    pmax = fmaxf(pmax, pr);
+                }
+            }
+        }
+        wstore<A, R>(sp, pb, v);
+    }
+}
+
+// Element i < 32 of the thread in the last sub-pass over window [A, A+R): shared and global index.
+template <int A, int R>
+__device__ __forceinline__ void welem(const Geo& geo, int zsh, int i, uint32_t& ix, uint64_t& z) {
+    const uint32_t g = threadIdx.x + (uint32_t)((i >> R) * NT);
+    const int e = i & ((1 << R) - 1);
+    const uint32_t base = wbase<A, R>(g);
+    ix = wix<A>(psw(base), e);
+    z = geo.z(base) + ((uint64_t)e << zsh);
+}
+
+// Kind-A tile: the snake of the pass over the windows [0,4), [4,8), [8,13).
+__device__ __forceinline__ void tile_kind_a(float2* sp, const Geo& geo, const StreamPass& P,
+                                            const LayerConst<float>* lc, const float* E, float amp0,
+                                            float& accp, float& pmax) {
+    if (P.init) {
+        // |+>, the cost phase and the mixer of layer 0 (the pass opens the state), then the mixer
+        // of layer 0 on the lower windows; a pass that also closes the layer is not planned
+        wsub<8, 5>(sp, geo, 8, SubOps{0, 0, false, false, true, false}, lc, E, amp0, accp, pmax);
+        __syncthreads();
+        wsub<4, 4>(sp, geo, 4, SubOps{0, 0, true, false, false, false}, lc, E, amp0, accp, pmax);
+        __syncthreads();
+        wsub<0, 4>(sp, geo, 0, SubOps{0, 0, true, false, false, false}, lc, E, amp0, accp, pmax);
+        return;
+    }
+    const bool two = P.lb > P.la;
+    wsub<0, 4>(sp, geo, 0, SubOps{P.la, P.la, true, false, false, false}, lc, E, amp0, accp, pmax);
+    __syncthreads();
+    wsub<4, 4>(sp, geo, 4, SubOps{P.la, P.la, true, false, false, false}, lc, E, amp0, accp, pmax);
+    __syncthreads();
+    wsub<8, 5>(sp, geo, 8, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, E, amp0, accp, pmax);
+    if (two) {
+        __syncthreads();
+        wsub<4, 4>(sp, geo, 4, SubOps{P.lb, P.lb, true, false, false, false}, lc, E, amp0, accp, pmax);
+        __syncthreads();
+        wsub<0, 4>(sp, geo, 0, SubOps{P.lb, P.lb, true, false, false, false}, lc, E, amp0, accp, pmax);
+    }
+}
+
+// Kind-B tile with H high qubits: one window [c, c+H) for H <= 5, else [c, c+5) and [c+5, c+H).
+template <int H>
+__device__ __forceinline__ void tile_kind_b(float2* sp, const Geo& geo, const StreamPass& P,
+                                            const LayerConst<float>* lc, const float* E, float amp0,
+                                            float& accp, float& pmax) {
+    constexpr int C = TB - H;
+    const bool two = P.lb > P.la;
+    if constexpr (H <= 5) {
+        wsub<C, H>(sp, geo, P.s, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, E, amp0, accp, pmax);
+    } else {
+        constexpr int A2 = C + 5, R2 = H - 5;
+        wsub<C, 5>(sp, geo, P.s, SubOps{P.la, P.la, true, false, false, false}, lc, E, amp0, accp, pmax);
+        __syncthreads();
+        wsub<A2, R2>(sp, geo, P.s + 5, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, E, amp0, accp, pmax);
+        if (two) {
+            __syncthreads();
+            wsub<C, 5>(sp, geo, P.s, SubOps{P.lb, P.lb, true, false, false, false}, lc, E, amp0, accp, pmax);
+        }
+    }
+}
+
+// Element accessor of the thread's 32 elements in the pass's last sub-pass (reductions).
+template <int H>
+__device__ __forceinline__ void last_elem_b(const Geo& geo, const StreamPass& P, int i, uint32_t& ix, uint64_t& z) {
+    constexpr int C = TB - H;
+    if constexpr (H <= 5) welem<C, H>(geo, P.s, i, ix, z);
+    else welem<C + 5, H - 5>(geo, P.s + 5, i, ix, z);
+}
+
+__device__ __forceinline__ void kind_b_dispatch(int h, float2* sp, const Geo& geo, const StreamPass& P,
+                                                const LayerConst<float>* lc, const float* E, float amp0,
+                                                float& accp, float& pmax) {
+    switch (h) {
+        case 1: tile_kind_b<1>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 2: tile_kind_b<2>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 3: tile_kind_b<3>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 4: tile_kind_b<4>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 5: tile_kind_b<5>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 6: tile_kind_b<6>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 7: tile_kind_b<7>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 8: tile_kind_b<8>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        default: tile_kind_b<9>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+    }
+}
+
+__device__ __forceinline__ void last_elem(const Geo& geo, const StreamPass& P, int i, uint32_t& ix, uint64_t& z) {
+    if (P.kind == 0) {
+        welem<8, 5>(geo, 8, i, ix, z);
+        return;
+    }
+    switch (P.h) {
+        case 1: last_elem_b<1>(geo, P, i, ix, z); break;
+        case 2: last_elem_b<2>(geo, P, i, ix, z); break;
+        case 3: last_elem_b<3>(geo, P, i, ix, z); break;
+        case 4: last_elem_b<4>(geo, P, i, ix, z); break;
+        case 5: last_elem_b<5>(geo, P, i, ix, z); break;
+        case 6: last_elem_b<6>(geo, P, i, ix, z); break;
+        case 7: last_elem_b<7>(geo, P, i, ix, z); break;
+        case 8: last_elem_b<8>(geo, P, i, ix, z); break;
+        default: last_elem_b<9>(geo, P, i, ix, z); break;
+    }
+}
+
+// TMA coordinates of tile tau (TsPass::bmode, see qaoa_tstream.h).
+__device__ __forceinline__ void tile_load(const TsPass& T, const CUtensorMap* map, void* dst, uint64_t tau,
+                                          uint64_t* bar) {
+    const int mid = (int)(tau & ((1ull << T.midbits) - 1ull)), top = (int)(tau >> T.midbits);
+    switch (T.bmode) {
+        case TS_A: tma_load_4d(dst, map, 0, 0, 0, (int)tau, bar); break;
+        case TS_B5: tma_load_5d(dst, map, 0, 0, mid, 0, top, bar); break;
+        case TS_B4: tma_load_4d(dst, map, 0, 0, mid, 0, bar); break;
+        case TS_B9_5: tma_load_5d(dst, map, 0, mid, 0, 0, top, bar); break;
+        default: tma_load_4d(dst, map, 0, mid, 0, 0, bar); break;
+    }
+}
+__device__ __forceinline__ void tile_store(const TsPass& T, const CUtensorMap* map, const void* src, uint64_t tau) {
+    const int mid = (int)(tau & ((1ull << T.midbits) - 1ull)), top = (int)(tau >> T.midbits);
+    switch (T.bmode) {
+        case TS_A: tma_store_4d(map, src, 0, 0, 0, (int)tau); break;
+        case TS_B5: tma_store_5d(map, src, 0, 0, mid, 0, top); break;
+        case TS_B4: tma_store_4d(map, src, 0, 0, mid, 0); break;
+        case TS_B9_5: tma_store_5d(map, src, 0, mid, 0, 0, top); break;
+        default: tma_store_4d(map, src, 0, mid, 0, 0); break;
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_tstream_pass(const StreamPass P, const TsPass T,
+                                                       const StreamInst<float>* __restrict__ insts, int count,
+                                                       const CUtensorMap* __restrict__ maps, unsigned* status) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const uint32_t raw = saddr(sm_raw);
+    unsigned char* sm = sm_raw + (((raw + 1023u) & ~1023u) - raw);
+    const TsOff o = ts_offsets();
+    float2* stage[NSTAGE];
+    for (int s = 0; s < NSTAGE; ++s) stage[s] = reinterpret_cast<float2*>(sm + o.stage[s]);
+    LayerConst<float>* lc = reinterpret_cast<LayerConst<float>*>(sm + o.lc);
+    float* red = reinterpret_cast<float*>(sm + o.red);
+    TileTopk ts;
+    ts.wb = reinterpret_cast<float*>(sm + o.wb);
+    ts.cnt = reinterpret_cast<int*>(sm + o.cnt);
+    ts.cand = reinterpret_cast<TopEnt*>(sm + o.cand);
+    ts.out = reinterpret_cast<TopEnt*>(sm + o.out);
+    ts.wlists = reinterpret_cast<TopEnt*>(sm + o.wlists);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + o.mbar);
+    if (threadIdx.x == 0)
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&mbar[s], 1);
+    __syncthreads();
+
+    const uint64_t ntiles = 1ull << (P.n - TB);
+    const uint64_t total = ntiles * (uint64_t)count;
+    const uint64_t first = blockIdx.x, step = gridDim.x;
+    const int nmine = first < total ? (int)((total - 1 - first) / step + 1) : 0;
+    const bool loads = !P.init;
+    const bool store = !P.fin || !P.no_store;
+    uint32_t parity = 0;   // bit s: parity of the next wait on stage s
+    bool ok = true;
+    auto issue = [&](int k) {
+        const uint64_t q = first + (uint64_t)k * step;
+        const int ii = (int)(q / ntiles);
+        const uint64_t tau = q % ntiles;
+        const int s = k % NSTAGE;
+        mbar_expect_tx(&mbar[s], TD * 8);
+        tile_load(T, maps + (size_t)ii * T.maps_per_inst + T.map, stage[s], tau, &mbar[s]);
+    };
+    if (loads && nmine > 0 && threadIdx.x == 0) issue(0);
+    const float *cur_g = nullptr, *cur_b = nullptr;
+    int cur_p = 0;
+    for (int k = 0; k < nmine; ++k) {
+        const uint64_t q = first + (uint64_t)k * step;
+        const int ii = (int)(q / ntiles);
+        const uint64_t tau = q % ntiles;
+        const int s = k % NSTAGE;
+        const StreamInst<float>& I = insts[ii];
+        // the next tile's load, into the stage whose store (two tiles back) has read it
+        if (loads && k + 1 < nmine && threadIdx.x == 0 && ok) {
+            bulk_wait_read_all_but_one();
+            issue(k + 1);
+        }
+        if (I.gamma != cur_g || I.beta != cur_b || I.p != cur_p) {
+            __syncthreads();
+            set_layer_consts<float>(lc, I.gamma, I.beta, I.p, P.n, true);
+            cur_g = I.gamma;
+            cur_b = I.beta;
+            cur_p = I.p;
+        }
+        if (loads) {
+            if (ok) ok = mbar_wait_bounded(&mbar[s], (parity >> s) & 1u);
+            parity ^= 1u << s;
+        } else if (k >= NSTAGE && threadIdx.x == 0) {
+            bulk_wait_read_all_but_one();   // generated tiles: this stage's earlier store has read it
+        }
+        ok = __syncthreads_and(ok);
+        Geo geo;
+        geo.kindA = P.kind == 0;
+        geo.c = P.c;
+        geo.s = P.s;
+        geo.lomask = (1u << P.c) - 1u;
+        if (geo.kindA) {
+            geo.zt = tau << TB;
+        } else {
+            const int midbits = P.s - P.c;
+            const uint64_t mid = tau & ((1ull << midbits) - 1ull), top = tau >> midbits;
+            geo.zt = (mid << P.c) | (top << (P.s + P.h));
+        }
+        float2* sp = stage[s];
+        const float* E = reinterpret_cast<const float*>(I.E);
+        float accp = 0.0f, pmax = -1.0f;
+        if (geo.kindA) tile_kind_a(sp, geo, P, lc, E, (float)I.amp0, accp, pmax);
+        else kind_b_dispatch(P.h, sp, geo, P, lc, E, (float)I.amp0, accp, pmax);
+        __syncthreads();
+        if (P.fin) {
+            const double tot = block_sum_df(accp, red);
+            if (threadIdx.x == 0) I.part_expect[tau] = tot;
+            if (P.k > 0) {
+                const auto elem = [&geo, &P](int i, uint32_t& ix, uint32_t& z) {
+                    uint64_t zz;
+                    last_elem(geo, P, i, ix, zz);
+                    z = (uint32_t)zz;
+                };
+                if (!topk_own(sp, P.k, pmax, elem, ts, reinterpret_cast<float*>(sm + o.wbound))) {
+                    float pm2 = -1.0f;
+                    for (uint32_t u = threadIdx.x; u < TD; u += NT) {
+                        const float2 v = sp[psw(u)];
+                        pm2 = fmaxf(pm2, v.x * v.x + v.y * v.y);
+                    }
+                    const TileRef<float> tile{sp, nullptr, nullptr, TB};
+                    const auto zmap = [&geo](uint32_t u) { return (uint32_t)geo.z(u); };
+                    tile_topk<float, TmaLayout>(tile, P.k, pm2, zmap, ts);
+                }
+                if (threadIdx.x < (unsigned)P.k) {
+                    const TopEnt e = ts.out[threadIdx.x];
+                    I.part_topp[tau * P.k + threadIdx.x] = e.p;
+                    I.part_topz[tau * P.k + threadIdx.x] = e.z;
+                }
+            }
+            if (store && !P.keep_frame) {
+                // the state leaves in the standard frame: psi = (-i)^{|z|} psi~
+                __syncthreads();
+                for (uint32_t u = threadIdx.x; u < TD; u += NT)
+                    sp[psw(u)] = times_i_pow(sp[psw(u)], -__popcll(geo.z(u)));
+            }
+        }
+        if (store) {
+            fence_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tile_store(T, maps + (size_t)ii * T.maps_per_inst + T.map, sp, tau);
+                bulk_commit();
+            }
+        } else {
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        bulk_wait_all();
+        if (!ok) atomicOr(status, 1u);
+    }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encode_fn() {
+    static EncodeFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeFn) nullptr;
+        return reinterpret_cast<EncodeFn>(f);
+    }();
+    return fn;
+}
+
+bool encode(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+            const cuuint32_t* box) {
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tstream_available() { return encode_fn() != nullptr; }
+
+size_t tstream_smem_bytes() { return ts_offsets().total; }
+
+TsPass tstream_pass_geometry(const StreamPass& P, int map, int maps_per_inst) {
+    TsPass T{};
+    T.map = map;
+    T.maps_per_inst = maps_per_inst;
+    if (P.kind == 0) {
+        T.bmode = TS_A;
+        T.midbits = 0;
+        return T;
+    }
+    T.midbits = P.s - P.c;
+    const bool top = P.s + P.h < P.n;
+    if (P.h <= 8) T.bmode = top ? TS_B5 : TS_B4;
+    else T.bmode = top ? TS_B9_5 : TS_B9_4;
+    return T;
+}
+
+bool tstream_encode_map(const StreamPass& P, void* psi, void* map_out) {
+    if (!encode_fn() || P.tb != TB || P.n <= TB || P.n > 34) return false;
+    CUtensorMap* m = static_cast<CUtensorMap*>(map_out);
+    const int n = P.n;
+    if (P.kind == 0) {   // (32 floats = 16 amplitudes, 256 lines, 2 planes, tile)
+        const cuuint64_t d[4] = {32, 256, 2, 1ull << (n - TB)};
+        const cuuint64_t s[3] = {128, 32768, 65536};
+        const cuuint32_t b[4] = {32, 256, 2, 1};
+        return encode(m, psi, 4, d, s, b);
+    }
+    const int c = P.c, sh = P.s, h = P.h;
+    const bool top = sh + h < n;
+    const cuuint64_t topd = 1ull << (n - sh - h);
+    if (h <= 8) {   // (32 floats, lines of bits 4..c-1, tile bits c..s-1, hi bits s..s+h-1[, top])
+        const cuuint64_t d[5] = {32, 1ull << (c - 4), 1ull << (sh - c), 1ull << h, topd};
+        const cuuint64_t s[4] = {128, (1ull << c) * 8, (1ull << sh) * 8, (1ull << (sh + h)) * 8};
+        const cuuint32_t b[5] = {32, 1u << (c - 4), 1, 1u << h, 1};
+        return encode(m, psi, top ? 5 : 4, d, s, b);
+    }
+    // h = 9, c = 4: (32 floats, tile bits 4..s-1, hi bits s..s+7, hi bit s+8[, top])
+    const cuuint64_t d[5] = {32, 1ull << (sh - c), 256, 2, topd};
+    const cuuint64_t s[4] = {128, (1ull << sh) * 8, (1ull << (sh + 8)) * 8, (1ull << (sh + 9)) * 8};
+    const cuuint32_t b[5] = {32, 1, 256, 2, 1};
+    return encode(m, psi, top ? 5 : 4, d, s, b);
+}
+
+cudaError_t launch_tstream_pass(const StreamPass& P, const TsPass& T, const void* insts, int count,
+                                const void* maps, int grid, unsigned* status, cudaStream_t st) {
+    const size_t sm = tstream_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_tstream_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_tstream_pass<<<grid, NT, sm, st>>>(P, T, static_cast<const StreamInst<float>*>(insts), count,
+                                         static_cast<const CUtensorMap*>(maps), status);
+    return cudaGetLastError();
+}
+
+}  // namespace qaoa

@@ -18,6 +18,7 @@
 #include "qaoa_host.h"
 #include "qaoa_kernels.h"
 #include "qaoa_stream.h"
+#include "qaoa_tstream.h"
 
 using namespace qaoa;
 
@@ -408,7 +409,10 @@ struct qaoa_plan {
     struct CsGroup { int n, count; size_t desc_off; int clusters; };
     struct StrGroup { int n, p, k, count; bool grad; size_t inst_off; std::vector<StreamPass> passes;
                       std::vector<StreamPass> apasses;   // adjoint plan (adjoint tile bits)
-                      int grid, agrid; std::vector<const void*> q; std::vector<void*> e; };
+                      int grid, agrid; std::vector<const void*> q; std::vector<void*> e;
+                      // TMA streaming passes (complex64): per instance one state tensor map per
+                      // pass shape, at maps_off in the header; tsp[i] is pass i's geometry
+                      bool tma = false; size_t maps_off = 0; int maps_per_inst = 0; std::vector<TsPass> tsp; };
     std::vector<ResGroup> res;
     std::vector<CluGroup> clu;
     std::vector<CsGroup> cs;
@@ -607,6 +611,23 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         const uint64_t nta = 1ull << (g.n - tba);
         g.inst_off = hdr;
         hdr = align256(hdr + sizeof(StreamInst<T>) * g.count);
+        if (!dbl && tstream_available()) {
+            // map 0: the kind-A passes; map 1 + b: the kind-B passes of chunk b (by start qubit)
+            std::vector<int> chunk_s;
+            for (auto& ps : g.passes)
+                if (ps.kind == 1 && std::find(chunk_s.begin(), chunk_s.end(), ps.s) == chunk_s.end())
+                    chunk_s.push_back(ps.s);
+            std::sort(chunk_s.begin(), chunk_s.end());
+            g.tma = true;
+            g.maps_per_inst = 1 + (int)chunk_s.size();
+            for (auto& ps : g.passes) {
+                const int mi = ps.kind == 0 ? 0
+                                            : 1 + (int)(std::find(chunk_s.begin(), chunk_s.end(), ps.s) - chunk_s.begin());
+                g.tsp.push_back(tstream_pass_geometry(ps, mi, g.maps_per_inst));
+            }
+            g.maps_off = hdr;
+            hdr = align256(hdr + TS_MAP_BYTES * (size_t)g.maps_per_inst * g.count);
+        }
         std::vector<SI> v;
         const uint64_t D = 1ull << g.n, nt = 1ull << (g.n - tb);
         for (int i : kv.second) {
@@ -731,6 +752,17 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
                 I.part_grad = reinterpret_cast<double*>(sb + s.grad_off);
                 I.dgamma = io->grad + d.par_off;
                 I.dbeta = io->grad + d.par_off + d.p;
+            }
+            if (g.tma) {
+                // one map per pass shape, for this instance's state
+                std::vector<char> done(g.maps_per_inst, 0);
+                for (size_t pi = 0; pi < g.passes.size(); ++pi) {
+                    const int mi = g.tsp[pi].map;
+                    if (done[mi]) continue;
+                    done[mi] = 1;
+                    char* dst = img.data() + g.maps_off + TS_MAP_BYTES * ((size_t)(j - 1) * g.maps_per_inst + mi);
+                    if (!tstream_encode_map(g.passes[pi], I.psi, dst)) { g.tma = false; break; }
+                }
             }
             si.push_back(I);
             g.q.push_back(qpool + d.q_off);
@@ -960,10 +992,18 @@ qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st) {
     const int tb = stream_tile_bits(P->dbl);
     for (auto& g : P->str) {
         CK(timed("energy", [&] { return launch_energy_batch(P->dbl, g.n, base + g.inst_off, g.count, st); }));
-        for (auto& pass : g.passes)
-            CK(timed("stream_pass", [&] {
-                return launch_stream_pass(P->dbl, pass, base + g.inst_off, g.count, g.grid, st);
-            }));
+        for (size_t pi = 0; pi < g.passes.size(); ++pi) {
+            const StreamPass& pass = g.passes[pi];
+            if (g.tma)
+                CK(timed("tstream_pass", [&] {
+                    return launch_tstream_pass(pass, g.tsp[pi], base + g.inst_off, g.count, base + g.maps_off,
+                                               P->ctx->nsm, reinterpret_cast<unsigned*>(counters + PLAN_STATUS_SLOT), st);
+                }));
+            else
+                CK(timed("stream_pass", [&] {
+                    return launch_stream_pass(P->dbl, pass, base + g.inst_off, g.count, g.grid, st);
+                }));
+        }
         CK(timed("stream_finalize", [&] {
             return launch_stream_finalize(P->dbl, base + g.inst_off, g.count, 1ull << (g.n - tb), g.k, st);
         }));
