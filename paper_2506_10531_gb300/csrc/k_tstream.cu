@@ -4,11 +4,9 @@
 //
 // Each pass is one persistent launch, one CTA per SM, walking the tiles of every instance of its
 // plan group. A tile is 2^13 amplitudes, moved between HBM and shared memory by TMA
-// (cp.async.bulk.tensor, 128-byte swizzle) through a ring of three stages: while the CTA works
-// on tile k, the load of tile k + 1 is in flight and the bulk store of tile k - 1 drains, so the
-// pass keeps HBM busy in both directions. The energies are read straight from HBM inside the
-// sub-pass that needs them (the cost phase or the <C> partial): their lanes cover tile bits 0..4,
-// so every warp reads whole 128-byte lines, and the shared memory goes to the ring.
+// (cp.async.bulk.tensor; the state with the 128-byte swizzle, its energies unswizzled, the
+// energies only in passes with a cost phase or the final reductions) through a ring of two
+// stages: while the CTA works on tile k, the load of tile k + 1 is in flight.
 //
 // Tiles follow the streaming tier's pass plan (stream_plan): kind A holds qubits 0..12 (2^13
 // contiguous amplitudes), kind B the 2^c contiguous amplitudes of qubits 0..c-1 times the 2^h
@@ -35,16 +33,17 @@ using namespace tma;
 constexpr int TB = 13;
 constexpr uint32_t TD = 1u << TB;
 constexpr int NT = TMA_NT;
-constexpr int NSTAGE = 3;
+constexpr int NSTAGE = 2;
 
 struct TsOff {
-    size_t stage[NSTAGE], lc, red, wbound, wb, cnt, cand, out, wlists, mbar, total;
+    size_t stage[NSTAGE], estage[NSTAGE], lc, red, wbound, wb, cnt, cand, out, wlists, run, mbar, total;
 };
 __host__ __device__ inline size_t ts_al(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline TsOff ts_offsets() {
     TsOff o{};
     size_t x = 0;
     for (int s = 0; s < NSTAGE; ++s) { o.stage[s] = x; x += (size_t)TD * 8; }   // 1024-aligned at run time
+    for (int s = 0; s < NSTAGE; ++s) { o.estage[s] = x; x += (size_t)TD * 4; }
     o.lc = x; x = ts_al(x + 64 * sizeof(LayerConst<float>));
     o.red = x; x = ts_al(x + 32 * sizeof(float));
     o.wbound = x; x = ts_al(x + sizeof(float));
@@ -53,6 +52,7 @@ __host__ __device__ inline TsOff ts_offsets() {
     o.cand = x; x = ts_al(x + TOPK_CAP * sizeof(TopEnt));
     o.out = x; x = ts_al(x + 16 * sizeof(TopEnt));
     o.wlists = x; x = ts_al(x + (NT / 32) * 32 * sizeof(TopEnt));
+    o.run = x; x = ts_al(x + 16 * sizeof(TopEnt));
     o.mbar = x; x = ts_al(x + NSTAGE * sizeof(uint64_t));
     o.total = x + 1024;
     return o;
@@ -124,7 +124,7 @@ struct SubOps {
 // index (kind A: A; kind B: A - c + s).
 template <int A, int R>
 __device__ __forceinline__ void wsub(float2* sp, const Geo& geo, int zsh, const SubOps& op,
-                                     const LayerConst<float>* lc, const float* __restrict__ E, float amp0,
+                                     const LayerConst<float>* lc, const float* sE, float amp0,
                                      float& accp, float& pmax) {
     constexpr int NGT = (1 << (TB - R)) / NT;   // groups per thread
 #pragma unroll 1
@@ -139,7 +139,7 @@ __device__ __forceinline__ void wsub(float2* sp, const Geo& geo, int zsh, const 
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
                 float s, c;
-                sincos_phase(lc[0].gpi, __ldg(E + zb + ((uint64_t)i << zsh)), s, c);
+                sincos_phase(lc[0].gpi, sE[base + ((uint32_t)i << A)], s, c);
                 v[i] = times_i_pow(make_float2(amp0 * c, -amp0 * s), pc + __popc(i));
             }
             mix_layer<R>(v, (1 << R) - 1, lc[0]);
@@ -151,7 +151,7 @@ __device__ __forceinline__ void wsub(float2* sp, const Geo& geo, int zsh, const 
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) {
                     float s, c;
-                    sincos_phase(k.gpi, __ldg(E + zb + ((uint64_t)i << zsh)), s, c);
+                    sincos_phase(k.gpi, sE[base + ((uint32_t)i << A)], s, c);
                     rot_neg(v[i], s * k.pre, c * k.pre);
                 }
                 mix_layer<R>(v, (1 << R) - 1, k);
@@ -161,7 +161,7 @@ __device__ __forceinline__ void wsub(float2* sp, const Geo& geo, int zsh, const 
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) {
                     const float pr = v[i].x * v[i].x + v[i].y * v[i].y;
-                    accp = fmaf(pr, __ldg(E + zb + ((uint64_t)i << zsh)), accp);
+                    accp = fmaf(pr, sE[base + ((uint32_t)i << A)], accp);
                     pmax = fmaxf(pmax, pr);
                 }
             }
@@ -182,49 +182,49 @@ __device__ __forceinline__ void welem(const Geo& geo, int zsh, int i, uint32_t& 
 
 // Kind-A tile: the snake of the pass over the windows [0,4), [4,8), [8,13).
 __device__ __forceinline__ void tile_kind_a(float2* sp, const Geo& geo, const StreamPass& P,
-                                            const LayerConst<float>* lc, const float* E, float amp0,
+                                            const LayerConst<float>* lc, const float* sE, float amp0,
                                             float& accp, float& pmax) {
     if (P.init) {
         // |+>, the cost phase and the mixer of layer 0 (the pass opens the state), then the mixer
         // of layer 0 on the lower windows; a pass that also closes the layer is not planned
-        wsub<8, 5>(sp, geo, 8, SubOps{0, 0, false, false, true, false}, lc, E, amp0, accp, pmax);
+        wsub<8, 5>(sp, geo, 8, SubOps{0, 0, false, false, true, false}, lc, sE, amp0, accp, pmax);
         __syncthreads();
-        wsub<4, 4>(sp, geo, 4, SubOps{0, 0, true, false, false, false}, lc, E, amp0, accp, pmax);
+        wsub<4, 4>(sp, geo, 4, SubOps{0, 0, true, false, false, false}, lc, sE, amp0, accp, pmax);
         __syncthreads();
-        wsub<0, 4>(sp, geo, 0, SubOps{0, 0, true, false, false, false}, lc, E, amp0, accp, pmax);
+        wsub<0, 4>(sp, geo, 0, SubOps{0, 0, true, false, false, false}, lc, sE, amp0, accp, pmax);
         return;
     }
     const bool two = P.lb > P.la;
-    wsub<0, 4>(sp, geo, 0, SubOps{P.la, P.la, true, false, false, false}, lc, E, amp0, accp, pmax);
+    wsub<0, 4>(sp, geo, 0, SubOps{P.la, P.la, true, false, false, false}, lc, sE, amp0, accp, pmax);
     __syncthreads();
-    wsub<4, 4>(sp, geo, 4, SubOps{P.la, P.la, true, false, false, false}, lc, E, amp0, accp, pmax);
+    wsub<4, 4>(sp, geo, 4, SubOps{P.la, P.la, true, false, false, false}, lc, sE, amp0, accp, pmax);
     __syncthreads();
-    wsub<8, 5>(sp, geo, 8, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, E, amp0, accp, pmax);
+    wsub<8, 5>(sp, geo, 8, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, sE, amp0, accp, pmax);
     if (two) {
         __syncthreads();
-        wsub<4, 4>(sp, geo, 4, SubOps{P.lb, P.lb, true, false, false, false}, lc, E, amp0, accp, pmax);
+        wsub<4, 4>(sp, geo, 4, SubOps{P.lb, P.lb, true, false, false, false}, lc, sE, amp0, accp, pmax);
         __syncthreads();
-        wsub<0, 4>(sp, geo, 0, SubOps{P.lb, P.lb, true, false, false, false}, lc, E, amp0, accp, pmax);
+        wsub<0, 4>(sp, geo, 0, SubOps{P.lb, P.lb, true, false, false, false}, lc, sE, amp0, accp, pmax);
     }
 }
 
 // Kind-B tile with H high qubits: one window [c, c+H) for H <= 5, else [c, c+5) and [c+5, c+H).
 template <int H>
 __device__ __forceinline__ void tile_kind_b(float2* sp, const Geo& geo, const StreamPass& P,
-                                            const LayerConst<float>* lc, const float* E, float amp0,
+                                            const LayerConst<float>* lc, const float* sE, float amp0,
                                             float& accp, float& pmax) {
     constexpr int C = TB - H;
     const bool two = P.lb > P.la;
     if constexpr (H <= 5) {
-        wsub<C, H>(sp, geo, P.s, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, E, amp0, accp, pmax);
+        wsub<C, H>(sp, geo, P.s, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, sE, amp0, accp, pmax);
     } else {
         constexpr int A2 = C + 5, R2 = H - 5;
-        wsub<C, 5>(sp, geo, P.s, SubOps{P.la, P.la, true, false, false, false}, lc, E, amp0, accp, pmax);
+        wsub<C, 5>(sp, geo, P.s, SubOps{P.la, P.la, true, false, false, false}, lc, sE, amp0, accp, pmax);
         __syncthreads();
-        wsub<A2, R2>(sp, geo, P.s + 5, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, E, amp0, accp, pmax);
+        wsub<A2, R2>(sp, geo, P.s + 5, SubOps{P.la, P.lb, true, two, false, (bool)P.fin}, lc, sE, amp0, accp, pmax);
         if (two) {
             __syncthreads();
-            wsub<C, 5>(sp, geo, P.s, SubOps{P.lb, P.lb, true, false, false, false}, lc, E, amp0, accp, pmax);
+            wsub<C, 5>(sp, geo, P.s, SubOps{P.lb, P.lb, true, false, false, false}, lc, sE, amp0, accp, pmax);
         }
     }
 }
@@ -238,18 +238,18 @@ __device__ __forceinline__ void last_elem_b(const Geo& geo, const StreamPass& P,
 }
 
 __device__ __forceinline__ void kind_b_dispatch(int h, float2* sp, const Geo& geo, const StreamPass& P,
-                                                const LayerConst<float>* lc, const float* E, float amp0,
+                                                const LayerConst<float>* lc, const float* sE, float amp0,
                                                 float& accp, float& pmax) {
     switch (h) {
-        case 1: tile_kind_b<1>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        case 2: tile_kind_b<2>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        case 3: tile_kind_b<3>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        case 4: tile_kind_b<4>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        case 5: tile_kind_b<5>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        case 6: tile_kind_b<6>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        case 7: tile_kind_b<7>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        case 8: tile_kind_b<8>(sp, geo, P, lc, E, amp0, accp, pmax); break;
-        default: tile_kind_b<9>(sp, geo, P, lc, E, amp0, accp, pmax); break;
+        case 1: tile_kind_b<1>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        case 2: tile_kind_b<2>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        case 3: tile_kind_b<3>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        case 4: tile_kind_b<4>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        case 5: tile_kind_b<5>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        case 6: tile_kind_b<6>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        case 7: tile_kind_b<7>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        case 8: tile_kind_b<8>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
+        default: tile_kind_b<9>(sp, geo, P, lc, sE, amp0, accp, pmax); break;
     }
 }
 
@@ -271,7 +271,8 @@ __device__ __forceinline__ void last_elem(const Geo& geo, const StreamPass& P, i
     }
 }
 
-// TMA coordinates of tile tau (TsPass::bmode, see qaoa_tstream.h).
+// TMA coordinates of tile tau (TsPass::bmode, see qaoa_tstream.h); the energy maps have the same
+// coordinates as the state maps.
 __device__ __forceinline__ void tile_load(const TsPass& T, const CUtensorMap* map, void* dst, uint64_t tau,
                                           uint64_t* bar) {
     const int mid = (int)(tau & ((1ull << T.midbits) - 1ull)), top = (int)(tau >> T.midbits);
@@ -302,7 +303,11 @@ __global__ void __launch_bounds__(NT, 1) k_tstream_pass(const StreamPass P, cons
     unsigned char* sm = sm_raw + (((raw + 1023u) & ~1023u) - raw);
     const TsOff o = ts_offsets();
     float2* stage[NSTAGE];
-    for (int s = 0; s < NSTAGE; ++s) stage[s] = reinterpret_cast<float2*>(sm + o.stage[s]);
+    float* estage[NSTAGE];
+    for (int s = 0; s < NSTAGE; ++s) {
+        stage[s] = reinterpret_cast<float2*>(sm + o.stage[s]);
+        estage[s] = reinterpret_cast<float*>(sm + o.estage[s]);
+    }
     LayerConst<float>* lc = reinterpret_cast<LayerConst<float>*>(sm + o.lc);
     float* red = reinterpret_cast<float*>(sm + o.red);
     TileTopk ts;
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(NT, 1) k_tstream_pass(const StreamPass P, cons
     const uint64_t total = ntiles * (uint64_t)count;
     const uint64_t first = blockIdx.x, step = gridDim.x;
     const int nmine = first < total ? (int)((total - 1 - first) / step + 1) : 0;
-    const bool loads = !P.init;
+    const bool loads = !P.init || P.need_e;   // the init pass loads only the energies
     const bool store = !P.fin || !P.no_store;
     uint32_t parity = 0;   // bit s: parity of the next wait on stage s
     bool ok = true;
@@ -329,21 +334,25 @@ __global__ void __launch_bounds__(NT, 1) k_tstream_pass(const StreamPass P, cons
         const int ii = (int)(q / ntiles);
         const uint64_t tau = q % ntiles;
         const int s = k % NSTAGE;
-        mbar_expect_tx(&mbar[s], TD * 8);
-        tile_load(T, maps + (size_t)ii * T.maps_per_inst + T.map, stage[s], tau, &mbar[s]);
+        const CUtensorMap* m = maps + (size_t)ii * T.maps_per_inst;
+        mbar_expect_tx(&mbar[s], (P.init ? 0u : TD * 8) + (P.need_e ? TD * 4 : 0u));
+        if (!P.init) tile_load(T, m + T.map, stage[s], tau, &mbar[s]);
+        if (P.need_e) tile_load(T, m + T.emap, estage[s], tau, &mbar[s]);
     };
     if (loads && nmine > 0 && threadIdx.x == 0) issue(0);
     const float *cur_g = nullptr, *cur_b = nullptr;
     int cur_p = 0;
+    TopEnt* run = reinterpret_cast<TopEnt*>(sm + o.run);
+    bool run_valid = false;   // the run list holds this CTA's best k of the current instance so far
     for (int k = 0; k < nmine; ++k) {
         const uint64_t q = first + (uint64_t)k * step;
         const int ii = (int)(q / ntiles);
         const uint64_t tau = q % ntiles;
         const int s = k % NSTAGE;
         const StreamInst<float>& I = insts[ii];
-        // the next tile's load, into the stage whose store (two tiles back) has read it
+        // the next tile's load, into the other stage once the last tile's store has read it
         if (loads && k + 1 < nmine && threadIdx.x == 0 && ok) {
-            bulk_wait_read_all_but_one();
+            bulk_wait_read();
             issue(k + 1);
         }
         if (I.gamma != cur_g || I.beta != cur_b || I.p != cur_p) {
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(NT, 1) k_tstream_pass(const StreamPass P, cons
             if (ok) ok = mbar_wait_bounded(&mbar[s], (parity >> s) & 1u);
             parity ^= 1u << s;
         } else if (k >= NSTAGE && threadIdx.x == 0) {
-            bulk_wait_read_all_but_one();   // generated tiles: this stage's earlier store has read it
+            bulk_wait_read_all_but_one();   // this stage's earlier store has read it
         }
         ok = __syncthreads_and(ok);
         Geo geo;
@@ -373,35 +382,101 @@ __global__ void __launch_bounds__(NT, 1) k_tstream_pass(const StreamPass P, cons
             geo.zt = (mid << P.c) | (top << (P.s + P.h));
         }
         float2* sp = stage[s];
-        const float* E = reinterpret_cast<const float*>(I.E);
+        const float* sE = estage[s];
         float accp = 0.0f, pmax = -1.0f;
-        if (geo.kindA) tile_kind_a(sp, geo, P, lc, E, (float)I.amp0, accp, pmax);
-        else kind_b_dispatch(P.h, sp, geo, P, lc, E, (float)I.amp0, accp, pmax);
+        if (geo.kindA) tile_kind_a(sp, geo, P, lc, sE, (float)I.amp0, accp, pmax);
+        else kind_b_dispatch(P.h, sp, geo, P, lc, sE, (float)I.amp0, accp, pmax);
         __syncthreads();
         if (P.fin) {
             const double tot = block_sum_df(accp, red);
             if (threadIdx.x == 0) I.part_expect[tau] = tot;
             if (P.k > 0) {
+                // Top-k: the CTA carries one list (run) across its tiles of an instance and writes
+                // it into the slot of its last such tile (the other slots it owns stay empty); the
+                // list of an instance is unique, so this does not depend on which tiles a CTA gets.
                 const auto elem = [&geo, &P](int i, uint32_t& ix, uint32_t& z) {
                     uint64_t zz;
                     last_elem(geo, P, i, ix, zz);
                     z = (uint32_t)zz;
                 };
-                if (!topk_own(sp, P.k, pmax, elem, ts, reinterpret_cast<float*>(sm + o.wbound))) {
-                    float pm2 = -1.0f;
-                    for (uint32_t u = threadIdx.x; u < TD; u += NT) {
-                        const float2 v = sp[psw(u)];
-                        pm2 = fmaxf(pm2, v.x * v.x + v.y * v.y);
+                const int kk = P.k;
+                const auto full_tile = [&]() {   // the tile's own list into ts.out
+                    if (!topk_own(sp, kk, pmax, elem, ts, reinterpret_cast<float*>(sm + o.wbound))) {
+                        float pm2 = -1.0f;
+                        for (uint32_t u = threadIdx.x; u < TD; u += NT) {
+                            const float2 v = sp[psw(u)];
+                            pm2 = fmaxf(pm2, v.x * v.x + v.y * v.y);
+                        }
+                        const TileRef<float> tile{sp, nullptr, nullptr, TB};
+                        const auto zmap = [&geo](uint32_t u) { return (uint32_t)geo.z(u); };
+                        tile_topk<float, TmaLayout>(tile, kk, pm2, zmap, ts);
                     }
-                    const TileRef<float> tile{sp, nullptr, nullptr, TB};
-                    const auto zmap = [&geo](uint32_t u) { return (uint32_t)geo.z(u); };
-                    tile_topk<float, TmaLayout>(tile, P.k, pm2, zmap, ts);
+                };
+                // the k best of `na` entries a[] and the run list, into run (rank selection)
+                const auto merge_run = [&](const TopEnt* a, int na) {
+                    TopEnt* merged = ts.wlists;
+                    for (int c = threadIdx.x; c < na + kk; c += NT) {
+                        const TopEnt me = c < na ? a[c] : run[c - na];
+                        int rank = 0;
+                        for (int j2 = 0; j2 < na; ++j2) rank += better(a[j2].p, a[j2].z, me.p, me.z) ? 1 : 0;
+                        for (int j2 = 0; j2 < kk; ++j2) rank += better(run[j2].p, run[j2].z, me.p, me.z) ? 1 : 0;
+                        if (rank < kk) merged[rank] = me;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < (unsigned)kk) run[threadIdx.x] = merged[threadIdx.x];
+                    __syncthreads();
+                };
+                if (!run_valid) {
+                    full_tile();
+                    if (threadIdx.x < (unsigned)kk) run[threadIdx.x] = ts.out[threadIdx.x];
+                    __syncthreads();
+                    run_valid = true;
+                } else {
+                    const float lo = __double2float_rd(run[kk - 1].p) * 0.99999904632568359375f;   // (1 - 2^-20)
+                    if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
+                    if (__syncthreads_or(pmax * 1.000003814697265625f >= lo)) {
+                        if (pmax * 1.000003814697265625f >= lo) {
+                            for (int i = 0; i < 32; ++i) {
+                                uint32_t ix, z;
+                                elem(i, ix, z);
+                                const float2 v = sp[ix];
+                                if ((v.x * v.x + v.y * v.y) * 1.00000095367431640625f >= lo) {
+                                    const int pos = atomicAdd(&ts.cnt[0], 1);
+                                    if (pos < TOPK_CAP) {
+                                        ts.cand[pos].p = __hiloint2double(__float_as_int(v.y), __float_as_int(v.x));
+                                        ts.cand[pos].z = z;
+                                    } else {
+                                        ts.cnt[1] = 1;
+                                    }
+                                }
+                            }
+                        }
+                        __syncthreads();
+                        if (!ts.cnt[1]) {
+                            const int cnt = ts.cnt[0];
+                            for (int c = threadIdx.x; c < cnt; c += NT) {
+                                const double raw = ts.cand[c].p;
+                                ts.cand[c].p = exact_prob(make_float2(__int_as_float(__double2loint(raw)),
+                                                                      __int_as_float(__double2hiint(raw))));
+                            }
+                            __syncthreads();
+                            merge_run(ts.cand, cnt);
+                        } else {
+                            __syncthreads();   // every thread has read the overflow flag
+                            full_tile();
+                            merge_run(ts.out, kk);
+                        }
+                    }
                 }
-                if (threadIdx.x < (unsigned)P.k) {
-                    const TopEnt e = ts.out[threadIdx.x];
-                    I.part_topp[tau * P.k + threadIdx.x] = e.p;
-                    I.part_topz[tau * P.k + threadIdx.x] = e.z;
+                // this tile's slot: the list when it is the CTA's last tile of the instance
+                const uint64_t qn = q + step;
+                const bool last_of_inst = k + 1 >= nmine || (int)(qn / ntiles) != ii;
+                if (threadIdx.x < (unsigned)kk) {
+                    const TopEnt e = last_of_inst ? run[threadIdx.x] : TopEnt{-1.0, 0xffffffffu};
+                    I.part_topp[tau * kk + threadIdx.x] = e.p;
+                    I.part_topz[tau * kk + threadIdx.x] = e.z;
                 }
+                if (last_of_inst) run_valid = false;
             }
             if (store && !P.keep_frame) {
                 // the state leaves in the standard frame: psi = (-i)^{|z|} psi~
@@ -444,11 +519,42 @@ EncodeFn encode_fn() {
 }
 
 bool encode(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-            const cuuint32_t* box) {
+            const cuuint32_t* box, bool swz128) {
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, dims, strides, box, es,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                       CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       swz128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The map of one pass shape over an array of 2^n elements of `w` floats each (w = 2: the
+// complex64 state, swizzled; w = 1: the energies, unswizzled). The innermost dimension is the 16
+// elements of tile bits 0..3 (16 w floats); the others follow TsPass::bmode.
+bool encode_shape(const StreamPass& P, void* base, int w, CUtensorMap* m) {
+    const int n = P.n;
+    const cuuint64_t f = (cuuint64_t)w * 4;            // bytes per element
+    const cuuint32_t d0 = 16u * (cuuint32_t)w;
+    const bool swz = w == 2;
+    if (P.kind == 0) {   // (16 elements, 256 lines, 2 planes, tile)
+        const cuuint64_t d[4] = {d0, 256, 2, 1ull << (n - TB)};
+        const cuuint64_t s[3] = {16 * f, 4096 * f, 8192 * f};
+        const cuuint32_t b[4] = {d0, 256, 2, 1};
+        return encode(m, base, 4, d, s, b, swz);
+    }
+    const int c = P.c, sh = P.s, h = P.h;
+    const bool top = sh + h < n;
+    const cuuint64_t topd = 1ull << (n - sh - h);
+    if (h <= 8) {   // (16 elements, lines of bits 4..c-1, tile bits c..s-1, hi bits s..s+h-1[, top])
+        const cuuint64_t d[5] = {d0, 1ull << (c - 4), 1ull << (sh - c), 1ull << h, topd};
+        const cuuint64_t s[4] = {16 * f, (1ull << c) * f, (1ull << sh) * f, (1ull << (sh + h)) * f};
+        const cuuint32_t b[5] = {d0, 1u << (c - 4), 1, 1u << h, 1};
+        return encode(m, base, top ? 5 : 4, d, s, b, swz);
+    }
+    // h = 9, c = 4: (16 elements, tile bits 4..s-1, hi bits s..s+7, hi bit s+8[, top])
+    const cuuint64_t d[5] = {d0, 1ull << (sh - c), 256, 2, topd};
+    const cuuint64_t s[4] = {16 * f, (1ull << sh) * f, (1ull << (sh + 8)) * f, (1ull << (sh + 9)) * f};
+    const cuuint32_t b[5] = {d0, 1, 256, 2, 1};
+    return encode(m, base, top ? 5 : 4, d, s, b, swz);
 }
 
 }  // namespace
@@ -457,9 +563,10 @@ bool tstream_available() { return encode_fn() != nullptr; }
 
 size_t tstream_smem_bytes() { return ts_offsets().total; }
 
-TsPass tstream_pass_geometry(const StreamPass& P, int map, int maps_per_inst) {
+TsPass tstream_pass_geometry(const StreamPass& P, int map, int emap, int maps_per_inst) {
     TsPass T{};
     T.map = map;
+    T.emap = emap;
     T.maps_per_inst = maps_per_inst;
     if (P.kind == 0) {
         T.bmode = TS_A;
@@ -473,30 +580,10 @@ TsPass tstream_pass_geometry(const StreamPass& P, int map, int maps_per_inst) {
     return T;
 }
 
-bool tstream_encode_map(const StreamPass& P, void* psi, void* map_out) {
+bool tstream_encode_maps(const StreamPass& P, void* psi, void* E, void* psi_map, void* e_map) {
     if (!encode_fn() || P.tb != TB || P.n <= TB || P.n > 34) return false;
-    CUtensorMap* m = static_cast<CUtensorMap*>(map_out);
-    const int n = P.n;
-    if (P.kind == 0) {   // (32 floats = 16 amplitudes, 256 lines, 2 planes, tile)
-        const cuuint64_t d[4] = {32, 256, 2, 1ull << (n - TB)};
-        const cuuint64_t s[3] = {128, 32768, 65536};
-        const cuuint32_t b[4] = {32, 256, 2, 1};
-        return encode(m, psi, 4, d, s, b);
-    }
-    const int c = P.c, sh = P.s, h = P.h;
-    const bool top = sh + h < n;
-    const cuuint64_t topd = 1ull << (n - sh - h);
-    if (h <= 8) {   // (32 floats, lines of bits 4..c-1, tile bits c..s-1, hi bits s..s+h-1[, top])
-        const cuuint64_t d[5] = {32, 1ull << (c - 4), 1ull << (sh - c), 1ull << h, topd};
-        const cuuint64_t s[4] = {128, (1ull << c) * 8, (1ull << sh) * 8, (1ull << (sh + h)) * 8};
-        const cuuint32_t b[5] = {32, 1u << (c - 4), 1, 1u << h, 1};
-        return encode(m, psi, top ? 5 : 4, d, s, b);
-    }
-    // h = 9, c = 4: (32 floats, tile bits 4..s-1, hi bits s..s+7, hi bit s+8[, top])
-    const cuuint64_t d[5] = {32, 1ull << (sh - c), 256, 2, topd};
-    const cuuint64_t s[4] = {128, (1ull << sh) * 8, (1ull << (sh + 8)) * 8, (1ull << (sh + 9)) * 8};
-    const cuuint32_t b[5] = {32, 1, 256, 2, 1};
-    return encode(m, psi, top ? 5 : 4, d, s, b);
+    return encode_shape(P, psi, 2, static_cast<CUtensorMap*>(psi_map)) &&
+           encode_shape(P, E, 1, static_cast<CUtensorMap*>(e_map));
 }
 
 cudaError_t launch_tstream_pass(const StreamPass& P, const TsPass& T, const void* insts, int count,

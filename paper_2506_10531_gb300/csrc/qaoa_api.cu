@@ -619,11 +619,12 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
                     chunk_s.push_back(ps.s);
             std::sort(chunk_s.begin(), chunk_s.end());
             g.tma = true;
-            g.maps_per_inst = 1 + (int)chunk_s.size();
+            const int nshape = 1 + (int)chunk_s.size();   // state maps, then the energy maps
+            g.maps_per_inst = 2 * nshape;
             for (auto& ps : g.passes) {
                 const int mi = ps.kind == 0 ? 0
                                             : 1 + (int)(std::find(chunk_s.begin(), chunk_s.end(), ps.s) - chunk_s.begin());
-                g.tsp.push_back(tstream_pass_geometry(ps, mi, g.maps_per_inst));
+                g.tsp.push_back(tstream_pass_geometry(ps, mi, nshape + mi, g.maps_per_inst));
             }
             g.maps_off = hdr;
             hdr = align256(hdr + TS_MAP_BYTES * (size_t)g.maps_per_inst * g.count);
@@ -757,11 +758,15 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
                 // one map per pass shape, for this instance's state
                 std::vector<char> done(g.maps_per_inst, 0);
                 for (size_t pi = 0; pi < g.passes.size(); ++pi) {
-                    const int mi = g.tsp[pi].map;
+                    const int mi = g.tsp[pi].map, ei = g.tsp[pi].emap;
                     if (done[mi]) continue;
                     done[mi] = 1;
-                    char* dst = img.data() + g.maps_off + TS_MAP_BYTES * ((size_t)(j - 1) * g.maps_per_inst + mi);
-                    if (!tstream_encode_map(g.passes[pi], I.psi, dst)) { g.tma = false; break; }
+                    char* row = img.data() + g.maps_off + TS_MAP_BYTES * (size_t)(j - 1) * g.maps_per_inst;
+                    if (!tstream_encode_maps(g.passes[pi], I.psi, const_cast<T*>(I.E), row + TS_MAP_BYTES * mi,
+                                             row + TS_MAP_BYTES * ei)) {
+                        g.tma = false;
+                        break;
+                    }
                 }
             }
             si.push_back(I);

@@ -16,7 +16,8 @@ enum : int { TS_A = 0, TS_B5 = 1, TS_B4 = 2, TS_B9_5 = 3, TS_B9_4 = 4 };
 struct TsPass {
     int bmode;          // TS_*
     int midbits;        // kind B: tile-index bits below the chunk (s - c)
-    int map;            // index of this pass's map among an instance's maps
+    int map;            // index of this pass's state map among an instance's maps
+    int emap;           // index of its energy map
     int maps_per_inst;  // maps per instance in the plan's map array
 };
 
@@ -25,10 +26,11 @@ constexpr size_t TS_MAP_BYTES = 128;   // one CUtensorMap, 64-byte aligned
 // The driver's tensor-map encoder could be found.
 bool tstream_available();
 size_t tstream_smem_bytes();
-TsPass tstream_pass_geometry(const StreamPass& P, int map, int maps_per_inst);
-// Encode the state tensor map of pass P (any pass of the same kind and chunk gives the same
-// map) for a state at psi (16-byte aligned) into map_out (host, 64-byte aligned).
-bool tstream_encode_map(const StreamPass& P, void* psi, void* map_out);
+TsPass tstream_pass_geometry(const StreamPass& P, int map, int emap, int maps_per_inst);
+// Encode the tensor maps of pass P (any pass of the same kind and chunk gives the same maps) for
+// a state at psi and its energies at E (both 16-byte aligned) into psi_map / e_map (host,
+// 64-byte aligned).
+bool tstream_encode_maps(const StreamPass& P, void* psi, void* E, void* psi_map, void* e_map);
 // One pass over `count` instances (device array of StreamInst<float>) whose maps start at `maps`
 // (device); a bounded wait that ran out sets bit 0 of *status.
 cudaError_t launch_tstream_pass(const StreamPass& P, const TsPass& T, const void* insts, int count,
