@@ -1002,7 +1002,7 @@ qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st) {
             if (g.tma)
                 CK(timed("tstream_pass", [&] {
                     return launch_tstream_pass(pass, g.tsp[pi], base + g.inst_off, g.count, base + g.maps_off,
-                                               P->ctx->nsm, reinterpret_cast<unsigned*>(counters + PLAN_STATUS_SLOT), st);
+                                               2 * P->ctx->nsm, reinterpret_cast<unsigned*>(counters + PLAN_STATUS_SLOT), st);
                 }));
             else
                 CK(timed("stream_pass", [&] {
