@@ -39,6 +39,10 @@ WORKLOAD = ("DQAOA batch cycle: dense N=1000 QUBO U[-1,1], 256 random conditione
             "of n=16, p=3 fixed parameters, complex64, top-8 merged")
 METRIC = "sub-QUBO solves/s (DQAOA cycle: decompose + energies + p layers + <C> + top-k + merge)"
 UNIT = "solves/s"
+# the same cycle at N = 10^4 (ten times the sub-QUBOs): where the aggregation grows with N
+CFG_10K = dict(synth.DQAOA_BATCH, N=10000, m=2560)
+WORKLOAD_10K = ("DQAOA batch cycle at large N: dense N=10000 QUBO U[-1,1], 2560 random conditioned "
+                "sub-QUBOs of n=16, p=3 fixed parameters, complex64, top-8 merged")
 
 
 def dist_env():
@@ -125,6 +129,10 @@ def measured_peaks():
 # Source files that define each kernel family (the kernel itself and the headers it includes).
 KERNEL_SOURCES = {
     "stream": ["k_stream.cu", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_stream.h", "qaoa_kernels.h"],
+    "tstream_pass": ["k_tstream.cu", "qaoa_tma.cuh", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_tstream.h",
+                     "qaoa_stream.h", "qaoa_kernels.h"],
+    "cstream": ["k_cstream.cu", "qaoa_tma.cuh", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_cstream.h",
+                "qaoa_kernels.h"],
     "resident": ["k_resident.cu", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_kernels.h"],
     "cluster": ["k_cluster.cu", "qaoa_engine.cuh", "qaoa_common.cuh", "qaoa_kernels.h"],
 }
@@ -270,6 +278,7 @@ def run_ours(args):
     kern = {}
     energies = []
     phases = []
+    spans = []
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -281,6 +290,7 @@ def run_ours(args):
             ev[s][1].record(stream)
             energies.append(e)
             phases.append(q.dqaoa_session_timing(sess))
+            spans.append(q.dqaoa_session_solve_ms(sess))
             for pl in plans:
                 for name, ms in q.qaoa_plan_kernel_times(pl):
                     kern.setdefault(name, []).append(ms)
@@ -297,7 +307,7 @@ def run_ours(args):
     def relaunch():
         q.dqaoa_session_cycle(sess, Qh, 0, x, seed, 999, stream)
     roof = plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=method_flops_per_step(m, k, p),
-                         steps=args.steps, workload="dqaoa")
+                         steps=args.steps, workload="dqaoa", span_ms=spans if len(plans) > 1 else None)
 
     # ---- kernel-only batch throughput and the plain one-instance-per-launch path ----
     kb = time_plan_only(q, plans, stream, args.steps, l2_flush)
@@ -338,6 +348,7 @@ def run_ours(args):
         "kernel_only": kb, "plain_gpu_path": plain,
         "batched_over_plain": kb["solves_per_s"] / plain["solves_per_s"],
         "kernel_ms_per_step": {nm: sum(v) / args.steps for nm, v in kern.items()},
+        "solve_span_ms_per_step": statistics.mean(spans),
         # host clock: index draw + uploads + launches, device span, merge, whole call
         "cycle_phases_ms": {key: float(np.mean([ph[key] for ph in phases])) for key in phases[0]},
         "roofline": roof,
@@ -356,7 +367,8 @@ def run_ours(args):
 HBM_FAMILIES = ("stream_pass", "tstream_pass", "stream_adjoint", "energy", "stream_finalize", "stream_grad_reduce")
 
 
-def plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=None, steps=None, workload=None):
+def plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=None, steps=None, workload=None,
+                  span_ms=None):
     """Roofline entry of the kernel family with the largest time in `kern` ({family: [ms per
     launch]}, measured with CUDA events on the launch stream inside the timed region).
 
@@ -367,7 +379,9 @@ def plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=None
     chip, SMEM / FP32 bound): achieved = the method's FP32 operations per step / the dominant
     family's event time per step, against SMs x 128 FP32 lanes x 2 x median SM clock. The same
     family's HBM view (the bytes the implementation chose to move) is reported beside it as
-    `implementation_traffic`, not as the bound."""
+    `implementation_traffic`, not as the bound. span_ms (per step): the dominant family's device
+    span when its launches overlap (two chunk solves on two streams); it replaces the sum of its
+    launch times."""
     import torch
     if not isinstance(plans, (list, tuple)):
         plans = [plans]
@@ -385,13 +399,18 @@ def plan_roofline(q, plans, kern, relaunch, clk, dev, method_flops_per_step=None
     fam_bytes = [b for nm, b in zip(order, kbytes) if nm == dom]
     per_launch_ms = statistics.mean(kern[dom])
     per_launch_bytes = statistics.mean(fam_bytes) if fam_bytes else 0.0
+    if span_ms:
+        # one "launch" = the overlapped launches of one step
+        per_launch_ms = statistics.mean(span_ms)
+        per_launch_bytes = float(sum(fam_bytes))
+        fam_ms[dom] = sum(span_ms) * steps / len(span_ms)
     peaks, peak_kind = measured_peaks()
     hbm_achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
     hbm = {"bound": "hbm", "kernel": dom, "achieved": hbm_achieved, "peak": peaks["hbm_gbs"],
            "unit": "GB/s", "frac": hbm_achieved / peaks["hbm_gbs"],
            "traffic": ncu_traffic(workload, dom), "peak_source": peak_kind + " (hbm_gbs, copy burst)",
            "algorithmic_bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-           "launches_per_step": len(fam_bytes)}
+           "launches_per_step": 1 if span_ms else len(fam_bytes)}
     if method_flops_per_step is None:
         return hbm
     props = torch.cuda.get_device_properties(dev)
@@ -418,17 +437,29 @@ def method_flops_per_step(m, k, p):
 
 
 def time_plan_only(q, plans, stream, steps, l2_flush):
+    """The chunk plans alone, launched as the session launches them: the first on `stream`, the
+    others on a second stream that starts with it (their solves overlap on the device)."""
     import torch
+    side = torch.cuda.Stream()
+
+    def launch_all():
+        start = torch.cuda.Event()
+        start.record(stream)
+        side.wait_event(start)
+        for i, pl in enumerate(plans):
+            q.qaoa_plan_launch(pl, stream if i == 0 else side)
+        done = torch.cuda.Event()
+        done.record(side)
+        stream.wait_event(done)
+
     for _ in range(3):
-        for pl in plans:
-            q.qaoa_plan_launch(pl, stream)
+        launch_all()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     for s in range(steps):
         l2_flush()
         ev[s][0].record(stream)
-        for pl in plans:
-            q.qaoa_plan_launch(pl, stream)
+        launch_all()
         ev[s][1].record(stream)
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
@@ -1010,7 +1041,9 @@ CONFIGS = {"large": run_large, "maxcut": run_maxcut, "plain10": run_plain10, "un
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 500 DQAOA cycles, about 0.25 s, for the dqaoa "
+                         "configuration; 20 for the others)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1019,15 +1052,22 @@ def main():
                     help="qubits of the large configuration (smaller values: profiling cases)")
     ap.add_argument("--uneven-count", type=int, default=0,
                     help="instances of the uneven batch (0: the full 4096; smaller: profiling cases)")
-    ap.add_argument("--config", default="dqaoa", choices=["dqaoa"] + sorted(CONFIGS),
+    ap.add_argument("--config", default="dqaoa", choices=["dqaoa", "dqaoa10k"] + sorted(CONFIGS),
                     help="dqaoa: the DQAOA batch cycle (headline); the others are the further "
                          "measured configurations")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 500 if args.config == "dqaoa" and args.impl == "ours" else 20
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "dqaoa":
+        run_ours(args)
+    elif args.config == "dqaoa10k":
+        global CFG, WORKLOAD
+        CFG, WORKLOAD = dict(CFG_10K), WORKLOAD_10K
+        args.no_cpu_baseline = True   # the oracle baseline is quoted on the N = 1000 cycle
         run_ours(args)
     else:
         import torch

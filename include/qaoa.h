@@ -306,7 +306,8 @@ qaoa_status qaoa_plain_solve(qaoa_ctx* ctx, int n, int p, const float* Q, const 
 /* DQAOA decomposition and aggregation (host, FP64)                                          */
 /* ---------------------------------------------------------------------------------------- */
 
-enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1, DQAOA_BFS = 2, DQAOA_PFS = 3, DQAOA_SIGNED_IMPACT = 16 };
+enum { DQAOA_RANDOM = 0, DQAOA_IFD = 1, DQAOA_BFS = 2, DQAOA_PFS = 3, DQAOA_SIGNED_IMPACT = 16,
+       DQAOA_PAPER_MIXER = 32 };
 
 /* Section V-A. Sub-QUBO index sets: idx[m*k] (host int32), each row sorted ascending.
  *   DQAOA_RANDOM: row j draws k distinct variables of 0..N-1 uniformly without replacement,
@@ -334,18 +335,19 @@ qaoa_status dqaoa_draw_indices(const double* Q, int N, const uint8_t* x, int met
  * symmetric, host doubles). With conditioned != 0 the couplings to the fixed variables
  * outside S_j are folded into the diagonal, Qsub[a][a] += 2 sum_{l not in S_j} Q[S_a][l] x_l,
  * so the sub-QUBO energy of y is E(x with x_S = y) minus a constant. The paper fixes the value
- * of that sum, not the order of its FP64 additions: here it is eight interleaved partial sums
- * (l = r mod 8, each ascending) combined pairwise, the order dqaoa_subqubo_build uses on the
- * device, so host and device matrices agree bit for bit; against any other order (a plain
- * ascending sum) an entry differs by FP64 rounding only. */
+ * of that sum, not the order of its FP64 additions: here it is 32 interleaved partial sums
+ * (l = r mod 32, each ascending) combined by the tree v_r <- v_r + v_{r xor d}, d = 16, 8, 4, 2,
+ * 1 (result v_0), the order dqaoa_subqubo_build uses on the device (one warp per row), so host
+ * and device matrices agree bit for bit; against any other order (a plain ascending sum) an
+ * entry differs by FP64 rounding only. */
 qaoa_status dqaoa_decompose(const double* Q, int N, const uint8_t* x, int method, int conditioned,
                             int m, int k, uint64_t seed, uint64_t cycle, int32_t* idx,
                             double* Qsub);
 
 /* The same sub-QUBO matrices built on the device, as FP32 for the complex64 solver:
  * Q_dev N*N doubles, x_dev N bytes, idx_dev m*k int32, qsub_dev m*k*k floats (all device).
- * The conditioning sum is accumulated in FP64 in the order dqaoa_decompose states (eight
- * interleaved partial sums combined pairwise) and rounded once to FP32. Async. */
+ * The conditioning sum is accumulated in FP64 in the order dqaoa_decompose states (32
+ * interleaved partial sums combined by an xor tree) and rounded once to FP32. Async. */
 qaoa_status dqaoa_subqubo_build(qaoa_ctx* ctx, const double* Q_dev, int N, const uint8_t* x_dev,
                                 int m, int k, const int32_t* idx_dev, int conditioned,
                                 float* qsub_dev, qaoa_stream_t stream);
@@ -371,7 +373,11 @@ typedef struct dqaoa_session dqaoa_session;
 
 /* gamma, beta: p host doubles (the fixed parameters every sub-QUBO uses); K: top-k candidates
  * per sub-QUBO fed to the merge (1..16); method: one of DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS,
- * DQAOA_PFS, the last three optionally | DQAOA_SIGNED_IMPACT. Allocates. */
+ * DQAOA_PFS, the last three optionally | DQAOA_SIGNED_IMPACT, and any of them optionally
+ * | DQAOA_PAPER_MIXER: the mixer of Section IV's ansatz as printed, H_X = -sum_i X_i, i.e.
+ * e^{+i beta_l sum X} per layer; without it the session applies e^{-i beta_l sum X} (the two are
+ * the same circuit at beta -> -beta, which is how the flag is applied: the session stores -beta).
+ * Allocates. */
 qaoa_status dqaoa_session_create(qaoa_ctx* ctx, int N, int m, int k, int p, int K, int method,
                                  int conditioned, const double* gamma, const double* beta,
                                  dqaoa_session** out);
@@ -386,10 +392,33 @@ qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed
 /* Device work of the last cycle: per-sub-QUBO <C> (m doubles) and top-K indices (m*K uint64),
  * copied to host arrays (either may be NULL). */
 qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk);
+/* A cycle whose sub-solutions are read from measured shots, as Section IV reads the candidate
+ * bitstring from a measurement of the optimised state (dqaoa_session_cycle takes the top-K
+ * bitstrings instead). Decomposition and solve as in dqaoa_session_cycle; then each sub-QUBO's
+ * final state is sampled `shots` times by inverse CDF over |psi|^2 (qaoa_sample) with the
+ * caller's uniforms u[j*shots + s] in [0, 1) (host doubles, m*shots), and the merge receives one
+ * candidate per sub-QUBO: the shot of lowest sub-QUBO energy y^T Qsub_j y, evaluated in FP64 on
+ * the sub-QUBO matrix of dqaoa_subqubo_build before its FP32 rounding (ties: the smaller
+ * bitstring). This is the best measurement of the shots, the sub-solution the paper's QAOA
+ * solver returns. shots: 1..2^20. The first call allocates the session's state pool
+ * (m * 2^k complex64), its sampler scratch and a plan over all m sub-QUBOs; a call with more
+ * shots than any before reallocates the shot buffers. Synchronous on `stream`; QAOA_E_TIMEOUT
+ * when a device-side wait of the solve ran out (x is then left unchanged). */
+qaoa_status dqaoa_session_cycle_sampled(dqaoa_session* s, const double* Q, int q_changed, uint8_t* x,
+                                        uint64_t seed, uint64_t cycle, int shots, const double* u,
+                                        double* energy_out, int* accepted_out, qaoa_stream_t stream);
+/* Of the last sampled cycle, copied to host arrays (any may be NULL): the shots (m*shots
+ * uint64, sub-QUBO j at j*shots), the candidate chosen per sub-QUBO (m uint64), and the final
+ * states (m * 2^k complex64, standard frame, sub-QUBO j at j * 2^k). QAOA_E_INVALID before the
+ * first sampled cycle. Synchronous. */
+qaoa_status dqaoa_session_shots(dqaoa_session* s, uint64_t* shots_out, uint64_t* best_out, void* psi_out);
 /* Times of the last cycle in ms, out[4]: the host's decompose-and-enqueue time (index draw,
  * copies and launches), the device time from the first copy to the last chunk's results, the
  * host merge time (the first chunk's merge overlaps the device), and the whole call. */
 qaoa_status dqaoa_session_timing(dqaoa_session* s, double* out);
+/* Device time of the last dqaoa_session_cycle's solve in ms: from the first chunk's launch to
+ * the end of the last chunk's kernels (the chunks may overlap on the device). */
+qaoa_status dqaoa_session_solve_ms(dqaoa_session* s, double* ms);
 /* The batched plans the session launches, in order (for timing and kernel counts): the m
  * sub-QUBOs are solved in two chunks when m >= 128, else in one. The host merges the first chunk
  * while the device solves the second; the first holds ceil(0.65 m) sub-QUBOs rounded up to a
@@ -445,6 +474,16 @@ qaoa_status qaoa_server_tick(qaoa_server* s, qaoa_stream_t stream, int* active, 
 /* Copy up to max finished jobs into out (in completion order) and return how many; with
  * wait != 0 first waits for every tick in flight. */
 int qaoa_server_poll(qaoa_server* s, int wait, qaoa_job_result* out, int max);
+/* Withdraw a job. A queued job leaves the queue; an admitted job leaves between ticks (its slot
+ * and scratch are free for the next admission; the ticks already enqueued still run its step,
+ * and no result of it is ever returned). QAOA_E_INVALID when the id is unknown, already
+ * returned, or the job's final pass is already enqueued. */
+qaoa_status qaoa_server_cancel(qaoa_server* s, int64_t job_id);
+/* Fault injection on the host: the next `count` admission attempts fail as if the job's scratch
+ * could not be allocated (the job keeps its place at the head of the queue, admission stops for
+ * that tick and resumes at the next; the jobs already admitted run on). failures (may be NULL):
+ * admission failures so far. count 0 clears a pending injection. */
+qaoa_status qaoa_server_fail_admissions(qaoa_server* s, int count, long long* failures);
 /* Queue and admission state, plus totals over the ticks so far: the algorithmic DRAM bytes of
  * every launched tick, the device time of the ticks already harvested and the kernel launches
  * enqueued (any may be NULL). */

@@ -21,6 +21,7 @@ QAOA_INST_GRAD = 1
 QAOA_TIER_AUTO, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM, QAOA_TIER_CSTREAM = 0, 2, 3, 4
 DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS, DQAOA_PFS = 0, 1, 2, 3
 DQAOA_SIGNED_IMPACT = 16   # or-ed with IFD / BFS / PFS: rank by impact ascending
+DQAOA_PAPER_MIXER = 32     # session: the printed mixer H_X = -sum X (beta -> -beta)
 
 # Every symbol include/qaoa.h declares.
 EXPORTS = [
@@ -34,9 +35,10 @@ EXPORTS = [
     "qaoa_plan_set_timing", "qaoa_plan_kernel_times", "qaoa_plan_kernel_bytes",
     "qaoa_expect_topk_static", "qaoa_adam_step",
     "dqaoa_session_create", "dqaoa_session_cycle", "dqaoa_session_results", "dqaoa_session_plan",
-    "dqaoa_session_destroy",
+    "dqaoa_session_destroy", "dqaoa_session_cycle_sampled", "dqaoa_session_shots", "dqaoa_session_solve_ms",
     "qaoa_server_create", "qaoa_server_destroy", "qaoa_server_job_bytes", "qaoa_server_submit",
     "qaoa_server_tick", "qaoa_server_poll", "qaoa_server_stats", "qaoa_server_clock",
+    "qaoa_server_cancel", "qaoa_server_fail_admissions",
     "qaoa_autotune", "qaoa_tuning_get", "qaoa_tuning_save", "qaoa_tuning_load", "qaoa_plan_capture",
     "dqaoa_session_timing", "qaoa_sample",
     "qaoa_cobyla_create", "qaoa_cobyla_ask", "qaoa_cobyla_tell", "qaoa_cobyla_result", "qaoa_cobyla_destroy",
@@ -129,7 +131,10 @@ def _declare(L):
     L.dqaoa_session_create.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, C.POINTER(vp)]
     L.dqaoa_session_cycle.argtypes = [vp, vp, i32, vp, u64, u64, vp, vp, vp]
     L.dqaoa_session_results.argtypes = [vp, vp, vp]
+    L.dqaoa_session_cycle_sampled.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
+    L.dqaoa_session_shots.argtypes = [vp, vp, vp, vp]
     L.dqaoa_session_timing.argtypes = [vp, vp]
+    L.dqaoa_session_solve_ms.argtypes = [vp, vp]
     L.dqaoa_session_plan.argtypes = [vp, i32]
     L.dqaoa_session_plan.restype = vp
     L.dqaoa_session_destroy.argtypes = [vp]
@@ -145,6 +150,8 @@ def _declare(L):
     L.qaoa_server_poll.restype = i32
     L.qaoa_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(sz), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.qaoa_server_cancel.argtypes = [vp, i64]
+    L.qaoa_server_fail_admissions.argtypes = [vp, i32, C.POINTER(C.c_longlong)]
     L.qaoa_autotune.argtypes = [vp, i32, i32, i32, i32, vp, C.POINTER(C.c_double)]
     L.qaoa_tuning_get.argtypes = [vp, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_double)]
     L.qaoa_tuning_save.argtypes = [vp, C.c_char_p]
@@ -449,6 +456,36 @@ def dqaoa_session_results(sess, m, K):
     return ex, tk
 
 
+def dqaoa_session_solve_ms(sess) -> float:
+    """Device ms of the last cycle's chunk solves (first launch to last kernel end)."""
+    v = C.c_double()
+    _check(lib().dqaoa_session_solve_ms(sess, C.byref(v)))
+    return v.value
+
+
+def dqaoa_session_cycle_sampled(sess, Q, q_changed, x, seed, cycle, u, stream=None):
+    """One DQAOA cycle with shot-based sub-solutions; u: (m, shots) host float64 uniforms in
+    [0, 1). x (host uint8) is updated in place. Returns (energy, accepted)."""
+    import numpy as np
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    e = C.c_double()
+    a = C.c_int()
+    _check(lib().dqaoa_session_cycle_sampled(sess, ptr(Q), int(q_changed), ptr(x), seed, cycle, int(u.shape[-1]),
+                                             ptr(u), C.byref(e), C.byref(a), stream_ptr(stream)))
+    return e.value, a.value
+
+
+def dqaoa_session_shots(sess, m, k, shots, states=False):
+    """(shots (m, shots) uint64, chosen candidate (m,) uint64, states (m, 2^k) complex64 or None)
+    of the last sampled cycle."""
+    import numpy as np
+    z = np.zeros((m, shots), dtype=np.uint64)
+    best = np.zeros(m, dtype=np.uint64)
+    psi = np.zeros((m, 1 << k), dtype=np.complex64) if states else None
+    _check(lib().dqaoa_session_shots(sess, ptr(z), ptr(best), ptr(psi) if states else None))
+    return z, best, psi
+
+
 def dqaoa_session_plan(sess, i=0):
     """Plan i of the session (None past the last one)."""
     h = lib().dqaoa_session_plan(sess, i)
@@ -541,6 +578,18 @@ def qaoa_server_stats(srv):
     _check(lib().qaoa_server_stats(srv, C.byref(q), C.byref(a), C.byref(u), C.byref(b), C.byref(t),
                                    C.byref(n)))
     return q.value, a.value, u.value, b.value, t.value, n.value
+
+
+def qaoa_server_cancel(srv, job_id):
+    _check(lib().qaoa_server_cancel(srv, job_id))
+
+
+def qaoa_server_fail_admissions(srv, count) -> int:
+    """Make the next `count` admission attempts fail (host-side fault injection); returns the
+    admission failures so far."""
+    f = C.c_longlong()
+    _check(lib().qaoa_server_fail_admissions(srv, count, C.byref(f)))
+    return f.value
 
 
 def qaoa_server_clock() -> float:

@@ -238,18 +238,21 @@ void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, cons
             for (int b = 0; b < k; ++b) Qs[a * k + b] = Q[(int64_t)S[a] * N + S[b]];
         if (!conditioned) continue;
         for (int a = 0; a < k; ++a) inS[S[a]] = 1;
-        // conditioning sum in eight interleaved partial sums (l = r mod 8, ascending), combined
-        // pairwise: the summation order the device kernel uses
+        // conditioning sum in 32 interleaved partial sums (l = r mod 32, ascending), combined by
+        // the xor tree v_r <- v_r + v_{r^d}, d = 16, 8, 4, 2, 1: the device kernel's order
         for (int a = 0; a < k; ++a) {
             const double* row = Q + (int64_t)S[a] * N;
-            double sr[8];
-            for (int r = 0; r < 8; ++r) {
+            double sr[32], nv[32];
+            for (int r = 0; r < 32; ++r) {
                 sr[r] = 0.0;
-                for (int l = r; l < N; l += 8)
+                for (int l = r; l < N; l += 32)
                     if (!inS[l] && x[l]) sr[r] += row[l];
             }
-            const double h = ((sr[0] + sr[1]) + (sr[2] + sr[3])) + ((sr[4] + sr[5]) + (sr[6] + sr[7]));
-            Qs[a * k + a] += 2.0 * h;
+            for (int d = 16; d >= 1; d >>= 1) {
+                for (int r = 0; r < 32; ++r) nv[r] = sr[r] + sr[r ^ d];
+                for (int r = 0; r < 32; ++r) sr[r] = nv[r];
+            }
+            Qs[a * k + a] = Q[(int64_t)S[a] * N + S[a]] + 2.0 * sr[0];
         }
         for (int a = 0; a < k; ++a) inS[S[a]] = 0;
     }
@@ -265,7 +268,7 @@ void build_subqubos(const double* Q, int N, const uint8_t* x, int m, int k, cons
 template <bool BLK, int KC>
 static int merge_loop(const double* Q, int N, uint8_t* x, int m, int k_rt, const int32_t* idx, int K,
                       const uint64_t* cand, const double* qblk, double tau, double* hq_in,
-                      double& energy) {
+                      double& energy, const double* pair, uint8_t* chg) {
     const int k = KC > 0 ? KC : k_rt;
     int accepted = 0;
     int nz[64];
@@ -279,9 +282,11 @@ static int merge_loop(const double* Q, int N, uint8_t* x, int m, int k_rt, const
         // bits of y ^ xs, visited in ascending order without a data-dependent branch per position;
         // h2 = 2 h on S_j (exact doubling), refreshed whenever a candidate is accepted
         uint64_t xs = 0;
+        bool fresh = pair != nullptr;   // no variable of S_j has flipped this cycle
         for (int a = 0; a < k; ++a) {
             xs |= (uint64_t)(x[S[a]] != 0) << a;
             h2[a] = 2.0 * hq[S[a]];
+            if (pair && chg[S[a]]) fresh = false;
         }
         for (int c = 0; c < K; ++c) {
             const uint64_t y = cand[(int64_t)j * K + c];
@@ -297,7 +302,12 @@ static int merge_loop(const double* Q, int N, uint8_t* x, int m, int k_rt, const
             // so they advance together (each keeps its own order)
             double inner[64];
             double dE = 0.0;
-            if constexpr (BLK) {
+            if (fresh) {
+                // the device's pair term for this d, plus the linear term for the current h
+                double lin = 0.0;
+                for (int u = 0; u < cnt; ++u) lin += d[u] * h2[nz[u]];
+                dE = lin + pair[(int64_t)j * K + c];
+            } else if constexpr (BLK) {
                 // with the block at hand, every row a of it advances (contiguous, vectorisable:
                 // Q[S_a][S_v] = Q[S_v][S_a] is row v of the symmetric block) and the changed
                 // rows are read at the end; the sums of the changed rows are the same sums
@@ -318,9 +328,11 @@ static int merge_loop(const double* Q, int N, uint8_t* x, int m, int k_rt, const
                 for (int u = 0; u < cnt; ++u) dE += d[u] * (h2[nz[u]] + inner[u]);
             }
             if (dE < -tau) {
+                fresh = false;
                 for (int u = 0; u < cnt; ++u) {
                     const int var = S[nz[u]];
                     x[var] = (uint8_t)(d[u] > 0.0);
+                    if (chg) chg[var] = 1;
                     // column var of the symmetric Q == row var
                     const double* __restrict__ row = Q + (int64_t)var * N;
                     const double du = d[u];
@@ -339,51 +351,66 @@ static int merge_loop(const double* Q, int N, uint8_t* x, int m, int k_rt, const
     return accepted;
 }
 
+void merge_setup_from(int N, const uint8_t* x, const double* h, const double* colabs, MergeCache* cache) {
+    double absq = 0.0;
+    for (int l = 0; l < N; ++l) absq += colabs[l];
+    cache->tau = 1e-12 * absq;
+    cache->h.assign(h, h + N);
+    double energy = 0.0;
+    for (int i = 0; i < N; ++i)
+        if (x[i]) energy += h[i];
+    cache->energy = energy;
+    cache->valid = true;
+}
+
+void merge_setup_host(const double* Q, int N, const uint8_t* x, MergeCache* cache) {
+    constexpr int RB = MERGE_RB;   // rows per block, as in the device set-up
+    std::vector<double> h(N, 0.0), a(N, 0.0), hb(N), ab(N);
+    for (int i0 = 0; i0 < N; i0 += RB) {
+        std::fill(hb.begin(), hb.end(), 0.0);
+        std::fill(ab.begin(), ab.end(), 0.0);
+        const int i1 = std::min(N, i0 + RB);
+        double* __restrict__ hp = hb.data();
+        double* __restrict__ ap = ab.data();
+        for (int i = i0; i < i1; ++i) {
+            const double* __restrict__ row = Q + (int64_t)i * N;
+            for (int l = 0; l < N; ++l) ap[l] += std::fabs(row[l]);
+            if (x[i])
+                for (int l = 0; l < N; ++l) hp[l] += row[l];
+        }
+        for (int l = 0; l < N; ++l) {
+            h[l] += hb[l];
+            a[l] += ab[l];
+        }
+    }
+    merge_setup_from(N, x, h.data(), a.data(), cache);
+}
+
 int merge(const double* Q, int N, uint8_t* x, int m, int k, const int32_t* idx, int K,
           const uint64_t* cand, double* energy_out, int* accepted_out, MergeCache* cache,
-          const double* qblk) {
-    std::vector<double> h_local;
-    std::vector<double>& h = cache ? cache->h : h_local;
-    double energy = 0.0, tau = 0.0;
-    if (cache && cache->valid) {
-        energy = cache->energy;
-        tau = cache->tau;
+          const double* qblk, const double* pair) {
+    MergeCache local;
+    MergeCache* mc = cache ? cache : &local;
+    if (!mc->valid) merge_setup_host(Q, N, x, mc);
+    double energy = mc->energy;
+    const double tau = mc->tau;
+    uint8_t* chg = nullptr;
+    if (pair) {
+        if (mc->chg.size() != (size_t)N) mc->chg.assign(N, 0);
+        chg = mc->chg.data();
     } else {
-        // tau only scales the acceptance threshold: eight partial sums (vectorisable)
-        const int64_t NN = (int64_t)N * N;
-        double part[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        int64_t t = 0;
-        for (; t + 8 <= NN; t += 8)
-            for (int u = 0; u < 8; ++u) part[u] += std::fabs(Q[t + u]);
-        double absq = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
-        for (; t < NN; ++t) absq += std::fabs(Q[t]);
-        tau = 1e-12 * absq;
-        // h = Qx: the rows of the set variables added in ascending order (symmetric Q: column l
-        // = row l), whole rows at a time; then E(x) = sum_i x_i h_i
-        h.assign(N, 0.0);
-        double* hp = h.data();
-        for (int i = 0; i < N; ++i) {
-            if (!x[i]) continue;
-            const double* row = Q + (int64_t)i * N;
-            for (int l = 0; l < N; ++l) hp[l] += row[l];
-        }
-        for (int i = 0; i < N; ++i)
-            if (x[i]) energy += hp[i];
+        pair = nullptr;
     }
     int accepted;
-    double* hp0 = h.data();
-    if (!qblk) accepted = merge_loop<false, 0>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
-    else if (k == 16) accepted = merge_loop<true, 16>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
-    else if (k == 12) accepted = merge_loop<true, 12>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
-    else if (k == 20) accepted = merge_loop<true, 20>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
-    else accepted = merge_loop<true, 0>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy);
+    double* hp0 = mc->h.data();
+    if (!qblk) accepted = merge_loop<false, 0>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy, pair, chg);
+    else if (k == 16) accepted = merge_loop<true, 16>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy, pair, chg);
+    else if (k == 12) accepted = merge_loop<true, 12>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy, pair, chg);
+    else if (k == 20) accepted = merge_loop<true, 20>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy, pair, chg);
+    else accepted = merge_loop<true, 0>(Q, N, x, m, k, idx, K, cand, qblk, tau, hp0, energy, pair, chg);
     if (energy_out) *energy_out = energy;
     if (accepted_out) *accepted_out = accepted;
-    if (cache) {
-        cache->energy = energy;
-        cache->tau = tau;
-        cache->valid = true;
-    }
+    mc->energy = energy;
     return 0;
 }
 

@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
     int j = 0;
     for (;; ++j) {
         const int sl = j & 1;
+        bool stored = false;   // thread 0: this step committed a bulk store group
         if (sfin[sl] >= 0) {
             // the instance of this slot finished two steps ago (its final pass is visible to the
             // cluster): rank 0 merges the CTAs' <C> partials (rank order) and top-k lists
@@ -454,6 +455,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                         else tma_store_4d(&I.maps[1], sp, 0, 0, (int)tau, 0);
                         if (pass == 0) tma_store_3d(&I.maps[2], sE, 0, 0, (int)tau);
                         bulk_commit();
+                        stored = true;
                     }
                 } else {
                     // <C> partial and top-k list of the tile (the top-k scratch overlays the
@@ -499,6 +501,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                             if (kindA) tma_store_4d(&I.maps[0], sp, 0, 0, 0, (int)tau);
                             else tma_store_4d(&I.maps[1], sp, 0, 0, (int)tau, 0);
                             bulk_commit();
+                            stored = true;
                         }
                     }
                     __syncthreads();
@@ -511,41 +514,49 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                 spass[sl] = pass + 1;
             }
         }
-        // end of step j: wait for the phase of step j - 1 (the data of the other slot's next pass is
-        // then complete), start loading that pass's first tile (once this step's stores have read
-        // the buffers), then complete this step's stores and arrive for step j
+        // end of step j. Step j's bulk stores drain while step j + 1 computes: here only step
+        // j - 1's stores must be complete (every group but the newest when step j committed one,
+        // a group per stored tile, so step j - 1's are older; else all), and every store must have read
+        // the buffers (the next step's prefetch, or rank 0's merge in the energy tile, reuses
+        // them). Then the cluster phase of step j - 1 (arrive after those stores; wait: every
+        // CTA's step j - 1 data is complete) and the prefetch of the next step's first tile,
+        // which belongs to the slot step j - 1 advanced.
         __syncthreads();
-        if (j > 0) cluster_wait();
+        if (threadIdx.x == 0) {
+            bulk_wait_read();
+            if (j > 0) {
+                if (stored) bulk_wait_all_but_one();
+                else bulk_wait_all();   // step j stored nothing: the newest group may be step j - 1's
+                fence_async_global();
+            }
+        }
+        __syncthreads();
+        if (j > 0) {
+            if (threadIdx.x < 32) cluster_arrive_release();
+            else cluster_arrive();
+            cluster_wait();
+        }
         {
             const int ns = (j + 1) & 1;
             prefetched = sidx[ns] >= 0 && sfin[ns] < 0 && spass[ns] > 0;
-            if (prefetched && threadIdx.x == 0) {
-                bulk_wait_read();
-                if (ok) issue_load(insts[sidx[ns]], (spass[ns] & 1) == 0, rank);
-            }
+            if (prefetched && threadIdx.x == 0 && ok) issue_load(insts[sidx[ns]], (spass[ns] & 1) == 0, rank);
         }
-        if (threadIdx.x == 0) {
-            bulk_wait_all();
-            fence_async_global();
-        }
-        // no thread starts the next step (whose merge on rank 0 writes into the energy tile) before
-        // this step's bulk stores have finished reading the buffers
-        __syncthreads();
-        if (threadIdx.x < 32) cluster_arrive_release();
-        else cluster_arrive();
     }
-    // The loop ends at the start of a step in which rank 0 may have just read every rank's
-    // shared memory (the last merge): one more arrival (after that merge) and wait, so that no CTA
-    // leaves before rank 0 is done with its shared memory.
-    if (j > 0) cluster_wait();   // steps 0..j-1 each arrived once
-    __syncthreads();
-    if (threadIdx.x < 32) cluster_arrive_release();
-    else cluster_arrive();
-    cluster_wait();
+    // The loop ends at the start of a step j in which rank 0 may have just read every rank's
+    // shared memory (the last merge). Every store completes, then the phase of step j - 1, which
+    // each CTA arrives at after that merge in its program order: no CTA leaves before rank 0 is
+    // done with its shared memory.
     if (threadIdx.x == 0) {
         bulk_wait_all();
-        if (!ok) atomicOr(status, 1u);
+        fence_async_global();
     }
+    __syncthreads();
+    if (j > 0) {
+        if (threadIdx.x < 32) cluster_arrive_release();
+        else cluster_arrive();
+        cluster_wait();
+    }
+    if (threadIdx.x == 0 && !ok) atomicOr(status, 1u);
 }
 
 template <int H>

@@ -4,29 +4,30 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "qaoa_host.h"
+
 namespace qaoa {
 
 namespace {
 
-// One CTA per sub-QUBO. The conditioning term of row a is the FP64 sum over l not in S with
-// x_l = 1 of Q[S_a][l], taken as eight partial sums over l = r (mod 8) (thread 8a + r, ascending
-// l) combined pairwise ((s0+s1)+(s2+s3))+((s4+s5)+(s6+s7)) by xor-shuffles within the row's eight
-// lanes (addition is commutative, so every lane ends with the same bits). The rows are staged
-// through shared memory in chunks of SQ_CHUNK columns, loaded by all warps with coalesced reads.
-// All threads then write the k*k FP32 entries and, when qblk is given, the raw FP64 block
-// Q[S, S] (the merge evaluates its candidates on it).
-constexpr int SQ_CHUNK = 128;
-
-__global__ void __launch_bounds__(256) k_subqubo(const double* __restrict__ Q, int N,
-                                                 const uint8_t* __restrict__ x, int k,
-                                                 const int32_t* __restrict__ idx, int conditioned,
-                                                 float* __restrict__ qsub, double* __restrict__ qblk) {
+// One CTA per sub-QUBO, one warp per row. The conditioning term of row a is the FP64 sum over
+// l not in S with x_l = 1 of Q[S_a][l], taken as 32 partial sums over l = r (mod 32) (lane r,
+// ascending l; a warp's loads cover 256 contiguous bytes) combined by the xor tree
+// v_r <- v_r + v_{r^d} for d = 16, 8, 4, 2, 1 (addition is commutative, so every lane ends with
+// the same bits; build_subqubos adds in the same order). The partial sums are short (N / 32
+// terms): a long dependent chain of FP64 adds is slow on this GPU. All threads first write the
+// k*k FP32 entries and, when qblk is given, the raw FP64 block Q[S, S] (the merge evaluates its
+// candidates on it); when qdiag is given, the FP64 diagonal of the sub-QUBO before its rounding
+// to FP32 (Q[S_a][S_a], plus the conditioning term).
+__global__ void __launch_bounds__(1024) k_subqubo(const double* __restrict__ Q, int N,
+                                                  const uint8_t* __restrict__ x, int k,
+                                                  const int32_t* __restrict__ idx, int conditioned,
+                                                  float* __restrict__ qsub, double* __restrict__ qblk,
+                                                  double* __restrict__ qdiag) {
     extern __shared__ __align__(8) unsigned char sq_smem[];
-    double* rows = reinterpret_cast<double*>(sq_smem);                    // k x (SQ_CHUNK + 1)
-    int32_t* S = reinterpret_cast<int32_t*>(rows + (size_t)k * (SQ_CHUNK + 1));
-    uint8_t* xm = reinterpret_cast<uint8_t*>(S + k);
+    int32_t* S = reinterpret_cast<int32_t*>(sq_smem);
+    uint8_t* xm = reinterpret_cast<uint8_t*>(S + 32);
     const int j = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = threadIdx.x; a < k; a += blockDim.x) S[a] = idx[(int64_t)j * k + a];
     if (conditioned)
         for (int l = threadIdx.x; l < N; l += blockDim.x) xm[l] = x[l];
@@ -41,43 +42,198 @@ __global__ void __launch_bounds__(256) k_subqubo(const double* __restrict__ Q, i
         const double q = Q[(int64_t)S[a] * N + S[b]];
         if (a != b || !conditioned) out[e] = (float)q;
         if (qblk) qblk[(int64_t)j * k * k + e] = q;
+        if (qdiag && a == b && !conditioned) qdiag[(int64_t)j * k + a] = q;
     }
     if (!conditioned) return;
-    const int ra = threadIdx.x >> 3, rr = threadIdx.x & 7;   // row and residue of this thread
+    const int ra = threadIdx.x >> 5, rr = threadIdx.x & 31;   // row and residue of this lane
+    if (ra >= k) return;                                      // whole warps
+    const double* row = Q + (int64_t)S[ra] * N;
     double h = 0.0;
-    for (int c0 = 0; c0 < N; c0 += SQ_CHUNK) {
-        const int len = min(SQ_CHUNK, N - c0);
-        for (int a = warp; a < k; a += nw) {
-            const double* row = Q + (int64_t)S[a] * N + c0;
-            for (int l = lane; l < len; l += 32) rows[a * (SQ_CHUNK + 1) + l] = row[l];
+    for (int l0 = rr; l0 < N; l0 += 128) {
+        double v[4];
+        bool on[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int l = l0 + 32 * u;
+            on[u] = l < N && xm[l];
+            v[u] = on[u] ? __ldg(row + l) : 0.0;
         }
-        __syncthreads();
-        if (ra < k) {
-            const double* r = rows + ra * (SQ_CHUNK + 1);
-            // c0 is a multiple of 8, so column c0 + l has residue l mod 8
-            for (int l = rr; l < len; l += 8)
-                if (xm[c0 + l]) h += r[l];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (on[u]) h += v[u];
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) h = h + __shfl_xor_sync(0xffffffffu, h, d);
+    if (rr == 0) {
+        const double d = Q[(int64_t)S[ra] * N + S[ra]] + 2.0 * h;
+        out[ra * k + ra] = (float)d;
+        if (qdiag) qdiag[(int64_t)j * k + ra] = d;
+    }
+}
+
+// One CTA per sub-QUBO: E(y) = sum_a y_a (D_a + sum_{b != a} y_b Q_ab), a and b ascending, in
+// FP64, for each of its shots; the block keeps the lowest (E, y) pair (ties: smaller y).
+__global__ void __launch_bounds__(256) k_best_shot(int k, int shots, const double* __restrict__ qblk,
+                                                   const double* __restrict__ qdiag,
+                                                   const uint64_t* __restrict__ z, uint64_t* __restrict__ best) {
+    __shared__ double sq[32 * 32];
+    __shared__ double be[256];
+    __shared__ uint64_t bz[256];
+    const int j = blockIdx.x;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x)
+        sq[e] = (e / k == e % k) ? qdiag[(int64_t)j * k + e / k] : qblk[(int64_t)j * k * k + e];
+    __syncthreads();
+    double myE = 0.0;
+    uint64_t myz = ~0ull;
+    bool have = false;
+    for (int s = threadIdx.x; s < shots; s += blockDim.x) {
+        const uint64_t y = z[(int64_t)j * shots + s];
+        double E = 0.0;
+        for (int a = 0; a < k; ++a) {
+            if (!((y >> a) & 1u)) continue;
+            double r = sq[a * k + a];
+            for (int b = 0; b < k; ++b)
+                if (b != a && ((y >> b) & 1u)) r += sq[a * k + b];
+            E += r;
+        }
+        if (!have || E < myE || (E == myE && y < myz)) { myE = E; myz = y; have = true; }
+    }
+    be[threadIdx.x] = have ? myE : 0.0;
+    bz[threadIdx.x] = have ? myz : ~0ull;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            const int o = threadIdx.x + w;
+            // an empty slot (no shot) has y = ~0 and loses to every real shot
+            const bool take = bz[o] != ~0ull &&
+                              (bz[threadIdx.x] == ~0ull || be[o] < be[threadIdx.x] ||
+                               (be[o] == be[threadIdx.x] && bz[o] < bz[threadIdx.x]));
+            if (take) { be[threadIdx.x] = be[o]; bz[threadIdx.x] = bz[o]; }
         }
         __syncthreads();
     }
-    h = h + __shfl_xor_sync(0xffffffffu, h, 1);
-    h = h + __shfl_xor_sync(0xffffffffu, h, 2);
-    h = h + __shfl_xor_sync(0xffffffffu, h, 4);
-    if (ra < k && rr == 0) out[ra * k + ra] = (float)(Q[(int64_t)S[ra] * N + S[ra]] + 2.0 * h);
+    if (threadIdx.x == 0) best[j] = bz[0];
+}
+
+// Aggregation set-up on the device (Section V step 3), for a merge that starts without a cached
+// h = Qx: with rows taken in blocks of MS_RB (short FP64 chains), block b of the grid's y dimension adds, for each
+// column l of its x dimension, the rows i of row block b in ascending order, h_b[l] over the
+// rows with x_i = 1 and a_b[l] = sum |Q[i][l]| over all of them; k_merge_setup_sum then adds the
+// row blocks in ascending order: h[l] = (Q x)_l (Q symmetric: column l = row l) and the column
+// sums of |Q| whose total scales the acceptance threshold. merge_setup_host adds in the same
+// order, so both give the same bits.
+constexpr int MS_RB = MERGE_RB;
+
+__global__ void __launch_bounds__(256) k_merge_setup(const double* __restrict__ Q, int N,
+                                                     const uint8_t* __restrict__ x, double* __restrict__ hp,
+                                                     double* __restrict__ ap) {
+    __shared__ uint8_t xs[MS_RB];
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = blockIdx.y * MS_RB;
+    const int rows = min(MS_RB, N - i0);
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) xs[r] = x[i0 + r];
+    __syncthreads();
+    if (l >= N) return;
+    double h = 0.0, a = 0.0;
+    const double* q = Q + (int64_t)i0 * N + l;
+#pragma unroll 8
+    for (int r = 0; r < rows; ++r) {
+        const double v = __ldg(q + (int64_t)r * N);
+        a += fabs(v);
+        if (xs[r]) h += v;
+    }
+    hp[(int64_t)blockIdx.y * N + l] = h;
+    ap[(int64_t)blockIdx.y * N + l] = a;
+}
+
+__global__ void __launch_bounds__(256) k_merge_setup_sum(int N, int blocks, const double* __restrict__ hp,
+                                                         const double* __restrict__ ap, double* __restrict__ h,
+                                                         double* __restrict__ colabs) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= N) return;
+    double hs = 0.0, as = 0.0;
+    for (int b = 0; b < blocks; ++b) {
+        hs += hp[(int64_t)b * N + l];
+        as += ap[(int64_t)b * N + l];
+    }
+    h[l] = hs;
+    colabs[l] = as;
+}
+
+// The pair term of each candidate's energy change against the solution x the cycle started
+// with: d = y - x_S, P = sum_u d_u sum_v Q_{S_u S_v} d_v over the changed positions, FP64, from
+// the raw block Q[S, S]. One warp per candidate: lane u sums its row over v ascending, and the
+// lanes' terms d_u * inner_u (zero for unchanged u) are added by the xor tree (d = 16 .. 1).
+// The merge adds the linear term 2 sum_u d_u (Qx)_{S_u} for the x it has reached.
+__global__ void __launch_bounds__(256) k_cand_pair(int m, int k, int K, const int32_t* __restrict__ idx,
+                                                   const uint8_t* __restrict__ x, const double* __restrict__ qblk,
+                                                   const uint64_t* __restrict__ cand, double* __restrict__ pair) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= (int64_t)m * K) return;   // warp-uniform
+    const int64_t j = t / K;
+    const int32_t* S = idx + j * k;
+    const bool xa = lane < k && x[S[lane]] != 0;
+    const uint64_t xs = (uint64_t)__ballot_sync(0xffffffffu, xa);   // k <= 30: one ballot holds x_S
+    const uint64_t kmask = (1ull << k) - 1ull;
+    const uint64_t y = cand[t], diff = (y ^ xs) & kmask;
+    double term = 0.0;
+    if (lane < k && ((diff >> lane) & 1u)) {
+        const double* row = qblk + j * k * k + (int64_t)lane * k;
+        double inner = 0.0;
+        for (uint64_t dv = diff; dv; dv &= dv - 1) {
+            const int v = __ffsll((long long)dv) - 1;
+            const double q = row[v];
+            inner = inner + (((y >> v) & 1u) ? q : -q);
+        }
+        term = ((y >> lane) & 1u) ? inner : -inner;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) term = term + __shfl_xor_sync(0xffffffffu, term, d);
+    if (lane == 0) pair[t] = term;
 }
 
 }  // namespace
 
 cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int k,
                            const int32_t* idx, int conditioned, float* qsub, cudaStream_t st,
-                           double* qblk) {
-    const size_t sm = (size_t)k * (SQ_CHUNK + 1) * sizeof(double) + k * sizeof(int32_t) + (size_t)N;
+                           double* qblk, double* qdiag) {
+    const size_t sm = 32 * sizeof(int32_t) + (size_t)N;
     if (sm > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(k_subqubo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    // eight threads per row (k <= 30): 256 threads cover every row
-    k_subqubo<<<m, 256, sm, st>>>(Q, N, x, k, idx, conditioned, qsub, qblk);
+    // a warp per row (k <= 30)
+    k_subqubo<<<m, 32 * k, sm, st>>>(Q, N, x, k, idx, conditioned, qsub, qblk, qdiag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_best_shot(int m, int k, int shots, const double* qblk, const double* qdiag,
+                             const uint64_t* z, uint64_t* best, cudaStream_t st) {
+    if (k < 1 || k > 32 || shots < 1) return cudaErrorInvalidValue;
+    k_best_shot<<<m, 256, 0, st>>>(k, shots, qblk, qdiag, z, best);
+    return cudaGetLastError();
+}
+
+int merge_setup_blocks(int N) { return (N + MS_RB - 1) / MS_RB; }
+
+cudaError_t launch_merge_setup(const double* Q, int N, const uint8_t* x, double* scratch, double* h,
+                               double* colabs, cudaStream_t st) {
+    const int rb = merge_setup_blocks(N);
+    if (rb > 65535) return cudaErrorInvalidValue;
+    double* hp = scratch;
+    double* ap = scratch + (size_t)rb * N;
+    const unsigned cols = (unsigned)((N + 255) / 256);
+    k_merge_setup<<<dim3(cols, (unsigned)rb), 256, 0, st>>>(Q, N, x, hp, ap);
+    k_merge_setup_sum<<<cols, 256, 0, st>>>(N, rb, hp, ap, h, colabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cand_pair(int m, int k, int K, const int32_t* idx, const uint8_t* x, const double* qblk,
+                             const uint64_t* cand, double* pair, cudaStream_t st) {
+    if (m < 1 || k < 1 || k > 30 || K < 1) return cudaErrorInvalidValue;
+    const int64_t n = (int64_t)m * K;   // candidates, one warp each
+    k_cand_pair<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(m, k, K, idx, x, qblk, cand, pair);
     return cudaGetLastError();
 }
 

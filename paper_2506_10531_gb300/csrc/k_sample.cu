@@ -10,6 +10,9 @@
 //   3. k_sample_draw:  one warp per shot: t = u * total, the last part whose offset is <= t, then
 //      a walk through that part 32 amplitudes at a time with a warp prefix scan until the running
 //      sum exceeds t. Every loop is bounded by the part length; nothing waits on another block.
+// A batch of states of equal n (a DQAOA cycle's sub-QUBO states, 2^n amplitudes apart) runs as
+// one launch of each kernel, the state index in blockIdx.y; each state has its own scratch
+// (2P + 1 doubles), uniforms and shots.
 #include <cuda_runtime.h>
 
 #include "qaoa_common.cuh"
@@ -21,10 +24,12 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__global__ void __launch_bounds__(256) k_sample_parts(const float2* __restrict__ psi, int pb,
-                                                      double* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_sample_parts(const float2* __restrict__ psi, int n, int pb,
+                                                      double* __restrict__ scratch) {
     __shared__ double red[8];
     const uint64_t L = 1ull << pb, base = (uint64_t)blockIdx.x << pb;
+    psi += (uint64_t)blockIdx.y << n;
+    double* part = scratch + (size_t)blockIdx.y * (2 * ((size_t)1 << (n - pb)) + 1);
     double acc = 0.0;
     for (uint64_t u = threadIdx.x; u < L; u += blockDim.x) acc += exact_prob(psi[base + u]);
     acc = warp_sum(acc);
@@ -37,9 +42,11 @@ __global__ void __launch_bounds__(256) k_sample_parts(const float2* __restrict__
     }
 }
 
-__global__ void k_sample_scan(const double* __restrict__ part, int parts, double* __restrict__ off,
-                              double* __restrict__ total) {
+__global__ void k_sample_scan(double* __restrict__ scratch, int parts) {
     if (threadIdx.x != 0) return;
+    const double* part = scratch + (size_t)blockIdx.x * (2 * (size_t)parts + 1);
+    double* off = const_cast<double*>(part) + parts;
+    double* total = off + parts;
     double acc = 0.0;
     for (int b = 0; b < parts; ++b) {
         off[b] = acc;
@@ -48,14 +55,18 @@ __global__ void k_sample_scan(const double* __restrict__ part, int parts, double
     *total = acc;
 }
 
-__global__ void __launch_bounds__(256) k_sample_draw(const float2* __restrict__ psi, int pb, int parts,
-                                                     const double* __restrict__ off,
-                                                     const double* __restrict__ total, int64_t shots,
+__global__ void __launch_bounds__(256) k_sample_draw(const float2* __restrict__ psi, int n, int pb, int parts,
+                                                     const double* __restrict__ scratch, int64_t shots,
                                                      const double* __restrict__ u,
                                                      uint64_t* __restrict__ out) {
     const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // one warp per shot
     const int lane = threadIdx.x & 31;
     if (s >= shots) return;                                                    // warp-uniform
+    psi += (uint64_t)blockIdx.y << n;
+    const double* off = scratch + (size_t)blockIdx.y * (2 * (size_t)parts + 1) + parts;
+    const double* total = off + parts;
+    u += (size_t)blockIdx.y * shots;
+    out += (size_t)blockIdx.y * shots;
     const double t = u[s] * *total;
     // the last part whose offset is <= t (offsets are non-decreasing; parts before a run of
     // empty parts are skipped that way)
@@ -99,19 +110,18 @@ size_t sample_scratch_bytes(int n) {
     return (2 * parts + 1) * sizeof(double);
 }
 
-cudaError_t launch_sample(int n, const void* psi, int64_t shots, const double* u, uint64_t* out,
+cudaError_t launch_sample(int n, const void* psi, int count, int64_t shots, const double* u, uint64_t* out,
                           double* scratch, cudaStream_t st) {
+    if (count < 1 || count > 65535) return cudaErrorInvalidValue;
     const int pb = sample_part_bits(n);
     const int parts = 1 << (n - pb);
-    double* part = scratch;
-    double* off = scratch + parts;
-    double* total = off + parts;
     const float2* ps = static_cast<const float2*>(psi);
-    k_sample_parts<<<parts, 256, 0, st>>>(ps, pb, part);
-    k_sample_scan<<<1, 32, 0, st>>>(part, parts, off, total);
+    k_sample_parts<<<dim3((unsigned)parts, (unsigned)count), 256, 0, st>>>(ps, n, pb, scratch);
+    k_sample_scan<<<(unsigned)count, 32, 0, st>>>(scratch, parts);
     if (shots > 0) {
         const int64_t blocks = (shots * 32 + 255) / 256;
-        k_sample_draw<<<(unsigned)blocks, 256, 0, st>>>(ps, pb, parts, off, total, shots, u, out);
+        k_sample_draw<<<dim3((unsigned)blocks, (unsigned)count), 256, 0, st>>>(ps, n, pb, parts, scratch, shots, u,
+                                                                              out);
     }
     return cudaGetLastError();
 }

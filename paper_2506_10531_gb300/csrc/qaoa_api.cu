@@ -381,7 +381,7 @@ extern "C" qaoa_status qaoa_sample(qaoa_ctx* c, int n, const void* psi, int64_t 
         return fail(QAOA_E_INVALID, "sample: n=%d shots=%lld or NULL pointer", n, (long long)shots);
     qaoa_status st = ensure_ws(c, sample_scratch_bytes(n));
     if (st) return st;
-    CK(launch_sample(n, psi, shots, u, out, static_cast<double*>(c->ws), (cudaStream_t)s));
+    CK(launch_sample(n, psi, 1, shots, u, out, static_cast<double*>(c->ws), (cudaStream_t)s));
     return QAOA_OK;
 }
 extern "C" qaoa_status qaoa_grad(qaoa_ctx* c, int n, int p, const float* g, const float* b, const float* E,
@@ -1222,6 +1222,10 @@ struct dqaoa_session {
     int32_t* idx_dev = nullptr;
     float* qsub = nullptr;
     double* qblk = nullptr;       // raw FP64 blocks Q[S_j, S_j] for the merge
+    double* pair = nullptr;       // pair term of each candidate's energy change (m*K)
+    double* mh = nullptr;         // merge set-up on the device: h = Qx, column sums of |Q|, scratch
+    double* mca = nullptr;
+    double* mscr = nullptr;
     float* params = nullptr;
     double* expect = nullptr;
     uint64_t* topk = nullptr;
@@ -1231,6 +1235,9 @@ struct dqaoa_session {
     uint64_t* topk_h = nullptr;
     double* expect_h = nullptr;
     double* qblk_h = nullptr;
+    double* pair_h = nullptr;
+    double* mh_h = nullptr;       // h and the column sums from the device set-up
+    double* mca_h = nullptr;
     unsigned* status_h = nullptr; // device status word of each chunk plan after its launch
     // the sub-QUBOs are solved in chunks, one plan each, so that the host merges chunk c while
     // the device solves chunk c + 1 (the merge is sequential over sub-QUBOs in index order)
@@ -1242,7 +1249,9 @@ struct dqaoa_session {
     cudaEvent_t dev_begin = nullptr, dev_end = nullptr;   // device part of the last cycle
     // the FP64 blocks go to the host on a side stream, beside the first chunk's kernels
     cudaStream_t side = nullptr;
-    cudaEvent_t sub_done = nullptr, qblk_done = nullptr;
+    cudaEvent_t sub_done = nullptr, qblk_done = nullptr, setup_done = nullptr;
+    cudaStream_t solve2 = nullptr;  // the second chunk's solve
+    cudaEvent_t solve_begin = nullptr, solve_end = nullptr;   // span of the chunk solves
     double t_decompose = 0.0, t_merge = 0.0, t_cycle = 0.0; // host ms of the last cycle
     MergeCache cache;             // h = Qx and E(x) after the last merge
     StrongGraph graph;            // BFS / PFS strong-interaction graph of the current Q
@@ -1252,15 +1261,32 @@ struct dqaoa_session {
     std::vector<int32_t> next_idx;
     bool next_valid = false;
     uint64_t next_seed = 0, next_cycle = 0;
+    // sampled cycles (dqaoa_session_cycle_sampled), set up on first use: one plan over all m
+    // sub-QUBOs that returns their states, then shots and the best shot of each on the device
+    qaoa_plan* s_plan = nullptr;
+    void* s_dev = nullptr;        // states (m * 2^k complex64), FP64 diagonals, sampler scratch
+    void* s_shot_dev = nullptr;   // uniforms, shots (m * s_shots each), best shots (m)
+    int s_shots = 0;              // shots per sub-QUBO the buffers hold
+    int s_last_shots = 0;         // shots per sub-QUBO of the last sampled cycle (0: none yet)
+    void* s_psi = nullptr;
+    double* s_qdiag = nullptr;
+    double* s_scratch = nullptr;
+    double* s_u = nullptr;
+    uint64_t* s_z = nullptr;
+    uint64_t* s_best = nullptr;
+    uint64_t* s_best_h = nullptr; // pinned, with the plan's status word after it
+    unsigned* s_status_h = nullptr;
 };
 
 extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, int p, int K, int method,
                                             int conditioned, const double* gamma, const double* beta,
                                             dqaoa_session** out) {
     if (!c || !out || N < 1 || m < 1 || k < 1 || k > N || k > NMAX || p < 1 || p > PMAX || K < 1 ||
-        K > KMAX || (uint64_t)K > (1ull << k) || !gamma || !beta || (method & ~31) || (method & 15) > DQAOA_PFS ||
-        method == (DQAOA_RANDOM | DQAOA_SIGNED_IMPACT))
+        K > KMAX || (uint64_t)K > (1ull << k) || !gamma || !beta || (method & ~63) || (method & 15) > DQAOA_PFS ||
+        (method & 31) == (DQAOA_RANDOM | DQAOA_SIGNED_IMPACT))
         return fail(QAOA_E_INVALID, "session_create: bad arguments");
+    const bool paper_mixer = (method & DQAOA_PAPER_MIXER) != 0;
+    method &= 31;
     if ((method & 15) == DQAOA_IFD && m + k - 1 > N) return fail(QAOA_E_INVALID, "IFD needs m + k - 1 <= N");
     if (((method & 15) == DQAOA_BFS || (method & 15) == DQAOA_PFS) && m > N)
         return fail(QAOA_E_INVALID, "BFS / PFS need m <= N");
@@ -1278,6 +1304,10 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     const size_t op = o; o = align256(o + (size_t)2 * p * sizeof(float));
     const size_t oe = o; o = align256(o + (size_t)m * sizeof(double));
     const size_t ot = o; o = align256(o + (size_t)m * K * sizeof(uint64_t));
+    const size_t opr = o; o = align256(o + (size_t)m * K * sizeof(double));
+    const size_t omh = o; o = align256(o + (size_t)N * sizeof(double));
+    const size_t omc = o; o = align256(o + (size_t)N * sizeof(double));
+    const size_t oms = o; o = align256(o + (size_t)2 * merge_setup_blocks(N) * N * sizeof(double));
     cudaError_t e = cudaMalloc(&s->dev, o);
     if (e != cudaSuccess) { delete s; return fail(QAOA_E_NOMEM, "session cudaMalloc: %s", cudaGetErrorString(e)); }
     char* b = static_cast<char*>(s->dev);
@@ -1289,6 +1319,10 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     s->params = reinterpret_cast<float*>(b + op);
     s->expect = reinterpret_cast<double*>(b + oe);
     s->topk = reinterpret_cast<uint64_t*>(b + ot);
+    s->pair = reinterpret_cast<double*>(b + opr);
+    s->mh = reinterpret_cast<double*>(b + omh);
+    s->mca = reinterpret_cast<double*>(b + omc);
+    s->mscr = reinterpret_cast<double*>(b + oms);
     size_t h = 0;
     const size_t hi = h; h = align256(h + (size_t)m * k * sizeof(int32_t));
     const size_t hx = h; h = align256(h + (size_t)N);
@@ -1296,6 +1330,9 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     const size_t he = h; h = align256(h + (size_t)m * sizeof(double));
     const size_t hb2 = h; h = align256(h + (size_t)m * k * k * sizeof(double));
     const size_t hst = h; h = align256(h + 2 * sizeof(unsigned));
+    const size_t hpr = h; h = align256(h + (size_t)m * K * sizeof(double));
+    const size_t hmh = h; h = align256(h + (size_t)N * sizeof(double));
+    const size_t hmc = h; h = align256(h + (size_t)N * sizeof(double));
     e = cudaMallocHost(&s->host, h);
     if (e != cudaSuccess) { cudaFree(s->dev); delete s; return fail(QAOA_E_NOMEM, "session cudaMallocHost"); }
     char* hb = static_cast<char*>(s->host);
@@ -1305,8 +1342,12 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     s->expect_h = reinterpret_cast<double*>(hb + he);
     s->qblk_h = reinterpret_cast<double*>(hb + hb2);
     s->status_h = reinterpret_cast<unsigned*>(hb + hst);
+    s->pair_h = reinterpret_cast<double*>(hb + hpr);
+    s->mh_h = reinterpret_cast<double*>(hb + hmh);
+    s->mca_h = reinterpret_cast<double*>(hb + hmc);
     std::vector<float> par(2 * p);
-    for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)beta[l]; }
+    // the paper's mixer H_X = -sum X is this library's mixer at -beta
+    for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)(paper_mixer ? -beta[l] : beta[l]); }
     e = cudaMemcpy(s->params, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { dqaoa_session_destroy(s); return cuda_fail(e, "session params upload"); }
     // Two chunks from m = 128 on. The first takes about two thirds, rounded up to whole waves
@@ -1352,7 +1393,10 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     if (cudaEventCreate(&s->dev_begin) != cudaSuccess || cudaEventCreate(&s->dev_end) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->sub_done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->qblk_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&s->qblk_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->setup_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&s->solve_begin) != cudaSuccess || cudaEventCreate(&s->solve_end) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->solve2, cudaStreamNonBlocking) != cudaSuccess) {
         dqaoa_session_destroy(s);
         return fail(QAOA_E_CUDA, "session events");
     }
@@ -1360,19 +1404,21 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     return QAOA_OK;
 }
 
-extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed, uint8_t* x,
-                                           uint64_t seed, uint64_t cycle, double* energy_out,
-                                           int* accepted_out, qaoa_stream_t stream) {
-    if (!s || !Q || !x) return fail(QAOA_E_INVALID, "session_cycle: NULL argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    const int N = s->N, m = s->m, k = s->k, K = s->K;
-    auto now_ms = []() {
-        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
-    };
-    const double t0 = now_ms();
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Decomposition step of a cycle (Section V-A): the index sets on the host (random sets drawn
+// ahead during the previous cycle when seed and cycle match), Q (when changed), x and the index
+// sets to the device, then the matrices of the first `rows` sub-QUBOs on the device (with their
+// FP64 diagonals when qdiag is given); the caller builds the others. dev_begin is recorded
+// before the first per-cycle copy.
+qaoa_status session_decompose(dqaoa_session* s, const double* Q, int q_changed, const uint8_t* x, uint64_t seed,
+                              uint64_t cycle, cudaStream_t st, double* qdiag, int rows) {
+    const int N = s->N, m = s->m, k = s->k;
     if (q_changed) CK(cudaMemcpyAsync(s->Q_dev, Q, (size_t)N * N * sizeof(double), cudaMemcpyHostToDevice, st));
-    // decompose: index sets on the host (random sets drawn ahead during the previous cycle
-    // when seed and cycle match), matrices on the device
     qaoa_status r = QAOA_OK;
     if (s->method == DQAOA_RANDOM && s->next_valid && s->next_seed == seed && s->next_cycle == cycle)
         std::memcpy(s->idx_h, s->next_idx.data(), (size_t)m * k * sizeof(int32_t));
@@ -1390,20 +1436,54 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     CK(cudaEventRecord(s->dev_begin, st));
     CK(cudaMemcpyAsync(s->x_dev, s->x_h, (size_t)N, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->idx_dev, s->idx_h, (size_t)m * k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CK(launch_subqubo(s->Q_dev, N, s->x_dev, m, k, s->idx_dev, s->conditioned, s->qsub, st, s->qblk));
+    CK(launch_subqubo(s->Q_dev, N, s->x_dev, rows, k, s->idx_dev, s->conditioned, s->qsub, st, s->qblk, qdiag));
+    return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed, uint8_t* x,
+                                           uint64_t seed, uint64_t cycle, double* energy_out,
+                                           int* accepted_out, qaoa_stream_t stream) {
+    if (!s || !Q || !x) return fail(QAOA_E_INVALID, "session_cycle: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = s->N, m = s->m, k = s->k, K = s->K;
+    const double t0 = now_ms();
+    // h = Qx from the last merge stays valid while Q is unchanged and x is the solution that
+    // merge left; else the device sets it up (beside the solve, on the side stream)
+    const bool need_setup = !(s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
+                              std::memcmp(s->x_last.data(), x, (size_t)N) == 0);
+    qaoa_status r = session_decompose(s, Q, q_changed, x, seed, cycle, st, nullptr, m);
+    if (r) return r;
     CK(cudaEventRecord(s->sub_done, st));
+    // the second chunk's solve runs on its own stream: its clusters take the SMs the first
+    // chunk's clusters leave while that chunk's last instances finish
+    if (s->chunks == 2) CK(cudaStreamWaitEvent(s->solve2, s->sub_done, 0));
     CK(cudaStreamWaitEvent(s->side, s->sub_done, 0));
     CK(cudaMemcpyAsync(s->qblk_h, s->qblk, (size_t)m * k * k * sizeof(double), cudaMemcpyDeviceToHost, s->side));
     CK(cudaEventRecord(s->qblk_done, s->side));
+    if (need_setup) {
+        CK(launch_merge_setup(s->Q_dev, N, s->x_dev, s->mscr, s->mh, s->mca, s->side));
+        CK(cudaMemcpyAsync(s->mh_h, s->mh, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s->side));
+        CK(cudaMemcpyAsync(s->mca_h, s->mca, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, s->side));
+        CK(cudaEventRecord(s->setup_done, s->side));
+    }
     // solve the sub-QUBOs chunk by chunk; each chunk's results come back behind its own event
+    CK(cudaEventRecord(s->solve_begin, st));
     for (int ch = 0; ch < s->chunks; ++ch) {
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
-        r = qaoa_plan_launch(s->plans[ch], stream);
+        cudaStream_t cs = ch == 0 ? st : s->solve2;
+        r = qaoa_plan_launch(s->plans[ch], (qaoa_stream_t)cs);
         if (r) return r;
-        // results to the host on the side stream: the next chunk's kernels do not wait for them
-        CK(cudaEventRecord(s->chunk_solved[ch], st));
+        // results to the host on the side stream, after the pair terms of the chunk's candidates
+        // against the cycle's starting x: the solves do not wait for either
+        CK(cudaEventRecord(s->chunk_solved[ch], cs));
         CK(cudaStreamWaitEvent(s->side, s->chunk_solved[ch], 0));
+        CK(launch_cand_pair(mc, k, K, s->idx_dev + (size_t)j0 * k, s->x_dev, s->qblk + (size_t)j0 * k * k,
+                            s->topk + (size_t)j0 * K, s->pair + (size_t)j0 * K, s->side));
         CK(cudaMemcpyAsync(s->topk_h + (size_t)j0 * K, s->topk + (size_t)j0 * K, (size_t)mc * K * sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, s->side));
+        CK(cudaMemcpyAsync(s->pair_h + (size_t)j0 * K, s->pair + (size_t)j0 * K, (size_t)mc * K * sizeof(double),
                            cudaMemcpyDeviceToHost, s->side));
         CK(cudaMemcpyAsync(s->expect_h + j0, s->expect + j0, (size_t)mc * sizeof(double), cudaMemcpyDeviceToHost, s->side));
         CK(cudaMemcpyAsync(s->status_h + ch, static_cast<char*>(s->plans[ch]->dev) + PLAN_STATUS_SLOT * sizeof(int),
@@ -1411,6 +1491,8 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         CK(cudaEventRecord(s->chunk_done[ch], s->side));
     }
     CK(cudaEventRecord(s->dev_end, s->side));
+    if (s->chunks == 2) CK(cudaStreamWaitEvent(st, s->chunk_solved[1], 0));   // the caller's stream covers the cycle
+    CK(cudaEventRecord(s->solve_end, st));
     const double t1 = now_ms();
     if (s->method == DQAOA_RANDOM) {   // overlaps the device work of this cycle
         s->next_idx.resize((size_t)m * k);
@@ -1419,13 +1501,18 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         s->next_seed = seed;
         s->next_cycle = cycle + 1;
     }
-    // aggregate chunk by chunk in sub-QUBO order (reusing h = Qx when Q is unchanged and x is the
-    // solution the last merge left); merging chunk c overlaps the device work of chunk c + 1
-    s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
-                     std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
+    // aggregate chunk by chunk in sub-QUBO order; merging chunk c overlaps the device work of
+    // chunk c + 1
     int accepted = 0;
     double t_merge = 0.0;
     CK(cudaEventSynchronize(s->qblk_done));
+    if (need_setup) {
+        CK(cudaEventSynchronize(s->setup_done));
+        const double ts = now_ms();
+        merge_setup_from(N, x, s->mh_h, s->mca_h, &s->cache);
+        t_merge += now_ms() - ts;
+    }
+    s->cache.chg.assign((size_t)N, 0);
     for (int ch = 0; ch < s->chunks; ++ch) {
         CK(cudaEventSynchronize(s->chunk_done[ch]));
         if (s->status_h[ch]) {
@@ -1437,7 +1524,7 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
         int acc = 0;
         merge(Q, N, x, mc, k, s->idx_h + (size_t)j0 * k, K, s->topk_h + (size_t)j0 * K, energy_out, &acc,
-              &s->cache, s->qblk_h + (size_t)j0 * k * k);
+              &s->cache, s->qblk_h + (size_t)j0 * k * k, s->pair_h + (size_t)j0 * K);
         accepted += acc;
         t_merge += now_ms() - tm;
     }
@@ -1461,10 +1548,123 @@ extern "C" qaoa_status dqaoa_session_timing(dqaoa_session* s, double* out) {
     return QAOA_OK;
 }
 
+extern "C" qaoa_status dqaoa_session_solve_ms(dqaoa_session* s, double* ms) {
+    if (!s || !ms) return fail(QAOA_E_INVALID, "session_solve_ms: NULL argument");
+    float v = 0.0f;
+    CK(cudaEventElapsedTime(&v, s->solve_begin, s->solve_end));
+    *ms = v;
+    return QAOA_OK;
+}
+
 extern "C" qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk) {
     if (!s) return fail(QAOA_E_INVALID, "session is NULL");
     if (expect) std::memcpy(expect, s->expect_h, (size_t)s->m * sizeof(double));
     if (topk) std::memcpy(topk, s->topk_h, (size_t)s->m * s->K * sizeof(uint64_t));
+    return QAOA_OK;
+}
+
+namespace {
+
+// Buffers of the sampled cycles: the plan and the state pool once, the shot buffers again when a
+// call asks for more shots than they hold.
+qaoa_status session_sampling_setup(dqaoa_session* s, int shots) {
+    const int m = s->m, k = s->k, p = s->p;
+    if (!s->s_plan) {
+        size_t o = 0;
+        const size_t ops = o; o = align256(o + ((size_t)m << k) * 8);
+        const size_t odg = o; o = align256(o + (size_t)m * k * sizeof(double));
+        const size_t osc = o; o = align256(o + (size_t)m * sample_scratch_bytes(k));
+        cudaError_t e = cudaMalloc(&s->s_dev, o);
+        if (e != cudaSuccess) { s->s_dev = nullptr; return fail(QAOA_E_NOMEM, "sampled cycle: cudaMalloc: %s", cudaGetErrorString(e)); }
+        char* b = static_cast<char*>(s->s_dev);
+        s->s_psi = b + ops;
+        s->s_qdiag = reinterpret_cast<double*>(b + odg);
+        s->s_scratch = reinterpret_cast<double*>(b + osc);
+        e = cudaMallocHost(&s->s_best_h, (size_t)m * sizeof(uint64_t) + 16);
+        if (e != cudaSuccess) { s->s_best_h = nullptr; return fail(QAOA_E_NOMEM, "sampled cycle: cudaMallocHost"); }
+        s->s_status_h = reinterpret_cast<unsigned*>(s->s_best_h + m);
+        std::vector<qaoa_inst> d(m);
+        for (int j = 0; j < m; ++j) d[j] = qaoa_inst{k, p, 0, 0, (int64_t)j * k * k, 0, (int64_t)j << k, -1};
+        qaoa_batch_io io{};
+        io.q = s->qsub;
+        io.params = s->params;
+        io.psi = s->s_psi;
+        io.expect = s->expect;
+        qaoa_status st = qaoa_plan_create(s->ctx, d.data(), m, &io, 0, &s->s_plan);
+        if (st) { s->s_plan = nullptr; return st; }
+    }
+    if (shots > s->s_shots) {
+        cudaFree(s->s_shot_dev);
+        s->s_shot_dev = nullptr;
+        s->s_shots = 0;
+        size_t o = 0;
+        const size_t ou = o; o = align256(o + (size_t)m * shots * sizeof(double));
+        const size_t oz = o; o = align256(o + (size_t)m * shots * sizeof(uint64_t));
+        const size_t ob = o; o = align256(o + (size_t)m * sizeof(uint64_t));
+        cudaError_t e = cudaMalloc(&s->s_shot_dev, o);
+        if (e != cudaSuccess) { s->s_shot_dev = nullptr; return fail(QAOA_E_NOMEM, "sampled cycle: cudaMalloc: %s", cudaGetErrorString(e)); }
+        char* b = static_cast<char*>(s->s_shot_dev);
+        s->s_u = reinterpret_cast<double*>(b + ou);
+        s->s_z = reinterpret_cast<uint64_t*>(b + oz);
+        s->s_best = reinterpret_cast<uint64_t*>(b + ob);
+        s->s_shots = shots;
+    }
+    return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" qaoa_status dqaoa_session_cycle_sampled(dqaoa_session* s, const double* Q, int q_changed, uint8_t* x,
+                                                   uint64_t seed, uint64_t cycle, int shots, const double* u,
+                                                   double* energy_out, int* accepted_out, qaoa_stream_t stream) {
+    if (!s || !Q || !x || !u || shots < 1 || shots > (1 << 20))
+        return fail(QAOA_E_INVALID, "session_cycle_sampled: bad arguments");
+    if (s->m > 65535) return fail(QAOA_E_INVALID, "session_cycle_sampled: m > 65535");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = s->N, m = s->m, k = s->k;
+    CK(cudaSetDevice(s->ctx->device));
+    qaoa_status r = session_sampling_setup(s, shots);
+    if (r) return r;
+    const double t0 = now_ms();
+    r = session_decompose(s, Q, q_changed, x, seed, cycle, st, s->s_qdiag, m);
+    if (r) return r;
+    CK(cudaMemcpyAsync(s->s_u, u, (size_t)m * shots * sizeof(double), cudaMemcpyHostToDevice, st));
+    r = qaoa_plan_launch(s->s_plan, stream);
+    if (r) return r;
+    CK(launch_sample(k, s->s_psi, m, shots, s->s_u, s->s_z, s->s_scratch, st));
+    CK(launch_best_shot(m, k, shots, s->qblk, s->s_qdiag, s->s_z, s->s_best, st));
+    CK(cudaMemcpyAsync(s->s_best_h, s->s_best, (size_t)m * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->qblk_h, s->qblk, (size_t)m * k * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->expect_h, s->expect, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->s_status_h, static_cast<char*>(s->s_plan->dev) + PLAN_STATUS_SLOT * sizeof(int),
+                       sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(s->dev_end, st));
+    const double t1 = now_ms();
+    CK(cudaStreamSynchronize(st));
+    s->s_last_shots = shots;
+    if (*s->s_status_h) return fail(QAOA_E_TIMEOUT, "session_cycle_sampled: a device-side wait ran out of time");
+    s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
+                     std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
+    const double tm = now_ms();
+    int acc = 0;
+    merge(Q, N, x, m, k, s->idx_h, 1, s->s_best_h, energy_out, &acc, &s->cache, s->qblk_h);
+    if (accepted_out) *accepted_out = acc;
+    s->x_last.assign(x, x + N);
+    s->t_decompose = t1 - t0;
+    s->t_merge = now_ms() - tm;
+    s->t_cycle = now_ms() - t0;
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status dqaoa_session_shots(dqaoa_session* s, uint64_t* shots_out, uint64_t* best_out,
+                                           void* psi_out) {
+    if (!s) return fail(QAOA_E_INVALID, "session is NULL");
+    if (!s->s_plan || !s->s_last_shots) return fail(QAOA_E_INVALID, "session_shots: no sampled cycle has run");
+    CK(cudaSetDevice(s->ctx->device));
+    const size_t m = (size_t)s->m;
+    if (shots_out) CK(cudaMemcpy(shots_out, s->s_z, m * s->s_last_shots * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (best_out) std::memcpy(best_out, s->s_best_h, m * sizeof(uint64_t));
+    if (psi_out) CK(cudaMemcpy(psi_out, s->s_psi, (m << s->k) * 8, cudaMemcpyDeviceToHost));
     return QAOA_OK;
 }
 
@@ -1484,7 +1684,15 @@ extern "C" void dqaoa_session_destroy(dqaoa_session* s) {
     if (s->dev_end) cudaEventDestroy(s->dev_end);
     if (s->sub_done) cudaEventDestroy(s->sub_done);
     if (s->qblk_done) cudaEventDestroy(s->qblk_done);
+    if (s->setup_done) cudaEventDestroy(s->setup_done);
+    if (s->solve_begin) cudaEventDestroy(s->solve_begin);
+    if (s->solve_end) cudaEventDestroy(s->solve_end);
+    if (s->solve2) cudaStreamDestroy(s->solve2);
     if (s->side) cudaStreamDestroy(s->side);
+    qaoa_plan_destroy(s->s_plan);
+    cudaFree(s->s_dev);
+    cudaFree(s->s_shot_dev);
+    if (s->s_best_h) cudaFreeHost(s->s_best_h);
     cudaFreeHost(s->host);
     cudaFree(s->dev);
     delete s;

@@ -125,6 +125,8 @@ struct qaoa_server {
     double bytes_total = 0.0;   // algorithmic DRAM bytes of every launched tick
     double gpu_ms_total = 0.0;  // device time of the harvested ticks
     long long launches = 0;     // kernel launches enqueued
+    int fail_next = 0;          // admissions still to fail (qaoa_server_fail_admissions)
+    long long admit_failures = 0;
 };
 
 namespace {
@@ -300,6 +302,13 @@ extern "C" qaoa_status qaoa_server_tick(qaoa_server* s, qaoa_stream_t stream, in
     float* up = reinterpret_cast<float*>(R.host + s->off_up);
     size_t upn = 0;
     while (!s->queue.empty() && !s->free_slots.empty() && s->used + s->queue.front()->foot <= s->scratch_cap) {
+        if (s->fail_next > 0) {
+            // the job's scratch could not be had: it keeps its place at the head of the queue
+            // (FIFO, nobody overtakes it) and admission resumes at the next tick
+            --s->fail_next;
+            ++s->admit_failures;
+            break;
+        }
         Job* j = s->queue.front();
         s->queue.pop_front();
         j->slot = s->free_slots.back();
@@ -402,6 +411,36 @@ extern "C" qaoa_status qaoa_server_tick(qaoa_server* s, qaoa_stream_t stream, in
     SCK(cudaEventRecord(R.ev, st), "cudaEventRecord");
     R.busy = true;
     ++s->tick_no;
+    return QAOA_OK;
+}
+
+extern "C" qaoa_status qaoa_server_cancel(qaoa_server* s, int64_t job_id) {
+    if (!s) return qaoa::set_error(QAOA_E_INVALID, "server_cancel: NULL server");
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if ((*it)->id != job_id) continue;
+        delete *it;
+        s->queue.erase(it);
+        return QAOA_OK;
+    }
+    for (auto it = s->active.begin(); it != s->active.end(); ++it) {
+        Job* j = *it;
+        if (j->id != job_id) continue;
+        // an admitted job leaves between ticks: the ticks already enqueued still read its slot,
+        // and a job admitted into the slot later uploads its inputs behind them on the stream
+        s->free_slots.push_back(j->slot);
+        s->used -= j->foot;
+        delete j;
+        s->active.erase(it);
+        return QAOA_OK;
+    }
+    return qaoa::set_error(QAOA_E_INVALID, "server_cancel: the job is not queued or running (unknown, or its "
+                           "final pass is already enqueued)");
+}
+
+extern "C" qaoa_status qaoa_server_fail_admissions(qaoa_server* s, int count, long long* failures) {
+    if (!s || count < 0) return qaoa::set_error(QAOA_E_INVALID, "server_fail_admissions: bad arguments");
+    s->fail_next = count;
+    if (failures) *failures = s->admit_failures;
     return QAOA_OK;
 }
 

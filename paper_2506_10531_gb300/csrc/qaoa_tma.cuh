@@ -99,6 +99,8 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 // every committed bulk store has completed (its writes are visible to this thread)
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// every committed bulk store but the most recent group has completed
+__device__ __forceinline__ void bulk_wait_all_but_one() { asm volatile("cp.async.bulk.wait_group 1;\n" ::: "memory"); }
 // generic-proxy shared-memory writes become visible to the async proxy (before a TMA store)
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 // order global accesses of the generic and the async proxy (around the cluster hand-off)
@@ -170,38 +172,53 @@ __device__ __forceinline__ bool topk_own(const float2* sp, int k, float pmax, El
     if (lane < k) ts.wb[warp * k + lane] = srt;
     if (threadIdx.x == 0) { ts.cnt[0] = 0; ts.cnt[1] = 0; }
     __syncthreads();
-    const int nl = (TMA_NT / 32) * k;
+    const int nl = (TMA_NT / 32) * k;   // a multiple of 8; ts.wb is 16-byte aligned
     if (threadIdx.x < (unsigned)nl) {
         const float me = ts.wb[threadIdx.x];
+        const int t = (int)threadIdx.x;
+        const float4* w4 = reinterpret_cast<const float4*>(ts.wb);
         int rank = 0;
-        for (int q = 0; q < nl; ++q) {
-            const float o = ts.wb[q];
-            rank += (o > me || (o == me && q < (int)threadIdx.x)) ? 1 : 0;
+#pragma unroll 4
+        for (int q4 = 0; q4 < nl / 4; ++q4) {
+            const float4 o = w4[q4];
+            const int q = 4 * q4;
+            rank += (o.x > me || (o.x == me && q < t)) ? 1 : 0;
+            rank += (o.y > me || (o.y == me && q + 1 < t)) ? 1 : 0;
+            rank += (o.z > me || (o.z == me && q + 2 < t)) ? 1 : 0;
+            rank += (o.w > me || (o.w == me && q + 3 < t)) ? 1 : 0;
         }
         if (rank == k - 1) *wbound = me;
     }
     __syncthreads();
     const float bnd = *wbound;
     const float lo = bnd > 0.0f ? bnd * 0.99999904632568359375f : -1.0f;   // (1 - 2^-20)
-    // (2) candidates: only threads whose maximum can reach the bound scan their elements; a
-    //     candidate is buffered with its amplitude (the slot's probability field holds the two
-    //     floats) and its exact FP64 probability is formed afterwards, one thread per candidate,
-    //     so that the slow FP64 pipe never runs in a serial per-thread chain
+    // (2) candidates: only threads whose maximum can reach the bound test their elements (all
+    //     32 loads first, independent of one another, then the appends); a candidate is
+    //     buffered with its amplitude (the slot's probability field holds the two floats) and
+    //     its exact FP64 probability is formed afterwards, one thread per candidate, so that the
+    //     slow FP64 pipe never runs in a serial per-thread chain
     if (pmax * 1.000003814697265625f >= lo) {
-#pragma unroll 4
+        uint32_t cm = 0;
+#pragma unroll
         for (int i = 0; i < 32; ++i) {
             uint32_t ix, z;
             elem(i, ix, z);
             const float2 v = sp[ix];
             const float pf = v.x * v.x + v.y * v.y;
-            if (pf * 1.00000095367431640625f >= lo) {
-                const int pos = atomicAdd(&ts.cnt[0], 1);
-                if (pos < TOPK_CAP) {
-                    ts.cand[pos].p = __hiloint2double(__float_as_int(v.y), __float_as_int(v.x));
-                    ts.cand[pos].z = z;
-                } else {
-                    ts.cnt[1] = 1;
-                }
+            cm |= (pf * 1.00000095367431640625f >= lo) ? (1u << i) : 0u;
+        }
+        while (cm) {
+            const int i = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            uint32_t ix, z;
+            elem(i, ix, z);
+            const float2 v = sp[ix];
+            const int pos = atomicAdd(&ts.cnt[0], 1);
+            if (pos < TOPK_CAP) {
+                ts.cand[pos].p = __hiloint2double(__float_as_int(v.y), __float_as_int(v.x));
+                ts.cand[pos].z = z;
+            } else {
+                ts.cnt[1] = 1;
             }
         }
     }

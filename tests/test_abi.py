@@ -52,6 +52,10 @@ def test_invalid_arguments_rejected_before_any_launch(libpath):
     L = q.lib()
     assert L.qaoa_run_layers(None, 10, 1, None, None, None, None, 1, None) == q.QAOA_E_INVALID
     assert L.dqaoa_merge(None, 0, None, 0, 0, None, 0, None, None, None) == q.QAOA_E_INVALID
+    assert L.dqaoa_session_cycle_sampled(None, None, 0, None, 0, 0, 16, None, None, None, None) == q.QAOA_E_INVALID
+    assert L.dqaoa_session_shots(None, None, None, None) == q.QAOA_E_INVALID
+    assert L.qaoa_server_cancel(None, 1) == q.QAOA_E_INVALID
+    assert L.qaoa_server_fail_admissions(None, 1, None) == q.QAOA_E_INVALID
     assert b"bad" in L.qaoa_last_error() or len(L.qaoa_last_error()) > 0
     assert q.qaoa_workspace_bytes(0) == 0 and q.qaoa_workspace_bytes(31) == 0
     assert q.qaoa_workspace_bytes(30) > q.qaoa_workspace_bytes(20) > 0

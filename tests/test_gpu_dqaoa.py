@@ -159,3 +159,37 @@ def test_session_graph_decompositions_on_maxcut(q, orc, method):
     finally:
         q.qaoa_destroy(ctx)
     assert synth.cut_value(Q, xs[-1]) >= synth.cut_value(Q, x0)
+
+
+@pytest.mark.parametrize("N,m", [(1000, 256), (10000, 512)])
+def test_session_merge_large_n(q, orc, N, m):
+    # the aggregation at N = 1000 and N = 10^4: h = Qx set up on the device (first cycle, and again
+    # when Q is re-sent), the candidates' pair terms on the device, the sequential accept rule on
+    # the host; accept decisions and x bit-exact against the oracle's merge of the same candidates,
+    # over three cycles (fresh set-up, cached h, Q re-sent)
+    k, p, K = 16, 2, 4
+    Q = synth.symmetric_q(N, seed=61)
+    x0 = synth.bits(62, N)
+    ctx = q.qaoa_create(0)
+    xs, cands, stats = [], [], []
+    try:
+        s = q.dqaoa_session_create(ctx, N, m, k, p, K, q.DQAOA_RANDOM, True, [0.3, 0.6], [0.5, 0.25])
+        x = x0.copy()
+        for c, qc in enumerate((1, 0, 1)):
+            e, acc = q.dqaoa_session_cycle(s, Q, qc, x, 61, c)
+            _, cand = q.dqaoa_session_results(s, m, K)
+            xs.append(x.copy())
+            cands.append(cand)
+            stats.append((e, acc))
+        q.dqaoa_session_destroy(s)
+    finally:
+        q.qaoa_destroy(ctx)
+    absq = np.abs(Q).sum()
+    xo = x0
+    for c in range(3):
+        idx, _ = orc.decompose(Q, xo, m, k, 61, c, conditioned=True)
+        xo, eo, ao = orc.merge(Q, xo, idx, cands[c])
+        np.testing.assert_array_equal(xs[c], xo)
+        assert stats[c][1] == ao, c
+        assert stats[c][0] == pytest.approx(eo, abs=1e-9 * absq), c
+    assert stats[-1][0] < orc.qubo_energy(Q, x0)

@@ -152,3 +152,69 @@ def test_admission_budget_and_oracle(q, ctx, orc):
         assert np.all(np.abs(got - rp) <= 4e-5 * np.sqrt(rp[0]))
         for z, pz in zip(r.topk_idx[:K], got):
             assert abs(pr[int(z)] - pz) <= 4e-5 * np.sqrt(rp[0])
+
+
+def same_result(a, b):
+    assert a.expect == b.expect
+    np.testing.assert_array_equal(np.array(a.topk_idx[:K]), np.array(b.topk_idx[:K]))
+    np.testing.assert_array_equal(np.array(a.params[:2 * a.p]), np.array(b.params[:2 * b.p]))
+
+
+def test_cancel_queued_and_running_jobs(q, ctx):
+    # host-side failure handling: a queued job and a running job are withdrawn; the others
+    # finish with the results they have alone, and the withdrawn ones never report
+    jobs = [job(10, 2, 501, steps=5), job(14, 3, 502, steps=8), job(12, 2, 503, steps=8), job(16, 1, 504, steps=4)]
+    srv = q.qaoa_server_create(ctx, 8 << 30, 2, K)   # two slots: jobs 2 and 3 wait in the queue
+    try:
+        ids = [q.qaoa_server_submit(srv, jb["n"], jb["p"], jb["Q"], jb["params"], jb["steps"], jb["lr"]) for jb in jobs]
+        q.qaoa_server_tick(srv)                       # admits jobs 0 and 1
+        q.qaoa_server_cancel(srv, ids[2])             # queued
+        q.qaoa_server_cancel(srv, ids[1])             # running: its slot goes to job 3
+        with pytest.raises(q.QaoaError):
+            q.qaoa_server_cancel(srv, ids[2])         # already gone
+        with pytest.raises(q.QaoaError):
+            q.qaoa_server_cancel(srv, 10 ** 9)        # unknown
+        out = {}
+        for _ in range(60):
+            a, qd = q.qaoa_server_tick(srv)
+            for r in q.qaoa_server_poll(srv, wait=True):
+                out[r.job_id] = r
+            if len(out) == 2 and a == 0 and qd == 0:
+                break
+        queued, active, used, _, _, _ = q.qaoa_server_stats(srv)
+        assert queued == 0 and active == 0 and used == 0
+        for r in q.qaoa_server_poll(srv, wait=True):
+            out[r.job_id] = r
+    finally:
+        q.qaoa_server_destroy(srv)
+    assert sorted(out) == sorted([ids[0], ids[3]])
+    alone0 = run_server(q, ctx, [(0, jobs[0])])[0]
+    alone3 = run_server(q, ctx, [(0, jobs[3])])[0]
+    same_result(out[ids[0]], alone0)
+    same_result(out[ids[3]], alone3)
+
+
+def test_admission_failure_injected(q, ctx):
+    # the next two admission attempts fail as if the job's scratch could not be allocated: the
+    # job keeps its place, admission resumes after two ticks, and every result is unchanged
+    jobs = [job(11, 2, 511, steps=3), job(13, 2, 512, steps=3), job(15, 1, 513, steps=2)]
+    srv = q.qaoa_server_create(ctx, 8 << 30, 8, K)
+    try:
+        ids = [q.qaoa_server_submit(srv, jb["n"], jb["p"], jb["Q"], jb["params"], jb["steps"], jb["lr"]) for jb in jobs]
+        assert q.qaoa_server_fail_admissions(srv, 2) == 0
+        assert q.qaoa_server_tick(srv) == (0, 3)
+        assert q.qaoa_server_tick(srv) == (0, 3)
+        assert q.qaoa_server_fail_admissions(srv, 0) == 2
+        assert q.qaoa_server_tick(srv) == (3, 0)
+        out = {}
+        for _ in range(40):
+            q.qaoa_server_tick(srv)
+            for r in q.qaoa_server_poll(srv, wait=True):
+                out[r.job_id] = r
+            if len(out) == 3:
+                break
+    finally:
+        q.qaoa_server_destroy(srv)
+    ref = run_server(q, ctx, [(0, jb) for jb in jobs])
+    for i in range(3):
+        same_result(out[ids[i]], ref[i])
