@@ -71,7 +71,8 @@ size_t qaoa_workspace_bytes(int n, int dbl);
  *     (resident for n <= 14, cluster streaming for n = 15..17, streaming above);
  *   QAOA_TIER_CLUSTER: cluster tier with `param` local qubits per CTA (13 or 14; the cluster
  *     then has 2^(n - param) CTAs, at most 16); only 15 <= n <= 18;
- *   QAOA_TIER_STREAM: HBM streaming; n >= 15;
+ *   QAOA_TIER_STREAM: HBM streaming; n >= 15; `param` picks the forward passes: 0 TMA passes with
+ *     two CTAs per SM (default), 1 TMA passes with one CTA per SM, 2 per-thread cp.async passes;
  *   QAOA_TIER_CSTREAM: cluster streaming (one thread-block cluster per instance runs all its
  *     passes through L2, tiles moved by TMA); 15 <= n <= 17, forward runs only (gradient
  *     instances use the streaming tier). QAOA_E_UNSUPPORTED if the device cannot run it.
@@ -80,15 +81,16 @@ enum { QAOA_TIER_AUTO = 0, QAOA_TIER_CLUSTER = 2, QAOA_TIER_STREAM = 3, QAOA_TIE
 qaoa_status qaoa_set_tier(qaoa_ctx* ctx, int n, int tier, int param);
 
 /* Autotuner (no counterpart in the paper). Times every kernel configuration that can run a
- * complex64 batch of `count` instances of (n, p) with top-k length k -- for 15 <= n <= 18 the
- * cluster tier with 13 or 14 local qubits per CTA and the streaming tier; elsewhere the single
- * configuration -- on synthetic inputs (best of 5 timed plan launches on `stream`, CUDA events)
- * and stores the fastest for (n, p) in the context; plans created later use it unless
- * qaoa_set_tier overrides n. best_ms (may be NULL): the winning batch time. Synchronous;
- * allocates temporary buffers. */
+ * complex64 batch of `count` instances of (n, p) with top-k length k -- for 15 <= n <= 30 the
+ * three variants of the streaming tier (param 0, 1, 2 above), for 15 <= n <= 18 also the cluster
+ * tier with 13 or 14 local qubits per CTA, for 15 <= n <= 17 the cluster-streaming tier; for
+ * n <= 14 the single (resident) configuration -- on synthetic inputs (best of 5 timed plan
+ * launches on `stream`, CUDA events) and stores the fastest (tier, param) for (n, p) in the
+ * context; plans created later use it unless qaoa_set_tier overrides n. best_ms (may be NULL):
+ * the winning batch time. Synchronous; allocates temporary buffers. */
 qaoa_status qaoa_autotune(qaoa_ctx* ctx, int n, int p, int k, int count, qaoa_stream_t stream,
                           double* best_ms);
-/* The stored choice for (n, p): tier 0 when none. */
+/* The stored choice for (n, p): tier 0 when none; param as in qaoa_set_tier. */
 qaoa_status qaoa_tuning_get(qaoa_ctx* ctx, int n, int p, int* tier, int* param, double* ms);
 /* Save / load the stored choices as JSON ({"format": "libqaoa-tuning-1", "entries": [...]}).
  * Loading adds the file's valid entries to the context. */

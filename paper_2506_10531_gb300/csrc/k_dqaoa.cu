@@ -49,17 +49,17 @@ __global__ void __launch_bounds__(1024) k_subqubo(const double* __restrict__ Q, 
     if (ra >= k) return;                                      // whole warps
     const double* row = Q + (int64_t)S[ra] * N;
     double h = 0.0;
-    for (int l0 = rr; l0 < N; l0 += 128) {
-        double v[4];
-        bool on[4];
+    for (int l0 = rr; l0 < N; l0 += 256) {
+        double v[8];
+        bool on[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
             const int l = l0 + 32 * u;
             on[u] = l < N && xm[l];
             v[u] = on[u] ? __ldg(row + l) : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
             if (on[u]) h += v[u];
     }
 #pragma unroll

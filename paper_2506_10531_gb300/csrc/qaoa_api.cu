@@ -310,7 +310,9 @@ extern "C" qaoa_status qaoa_set_tier(qaoa_ctx* c, int n, int tier, int param) {
     if (tier == QAOA_TIER_AUTO) { c->tier[n] = 0; c->cluster_L[n] = 0; return QAOA_OK; }
     if (tier == QAOA_TIER_STREAM) {
         if (n <= RES_NMAX_F) return fail(QAOA_E_INVALID, "set_tier: n=%d is always resident", n);
+        if (param < 0 || param > 2) return fail(QAOA_E_INVALID, "set_tier: streaming variant %d (0..2)", param);
         c->tier[n] = tier;
+        c->cluster_L[n] = param;
         return QAOA_OK;
     }
     if (tier == QAOA_TIER_CSTREAM) {
@@ -412,7 +414,8 @@ struct qaoa_plan {
                       int grid, agrid; std::vector<const void*> q; std::vector<void*> e;
                       // TMA streaming passes (complex64): per instance one state tensor map per
                       // pass shape, at maps_off in the header; tsp[i] is pass i's geometry
-                      bool tma = false; size_t maps_off = 0; int maps_per_inst = 0; std::vector<TsPass> tsp; };
+                      bool tma = false; size_t maps_off = 0; int maps_per_inst = 0; std::vector<TsPass> tsp;
+                      int tgrid = 0; };   // TMA passes' persistent grid
     std::vector<ResGroup> res;
     std::vector<CluGroup> clu;
     std::vector<CsGroup> cs;
@@ -611,7 +614,9 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
         const uint64_t nta = 1ull << (g.n - tba);
         g.inst_off = hdr;
         hdr = align256(hdr + sizeof(StreamInst<T>) * g.count);
-        if (!dbl && tstream_available()) {
+        const int variant = dbl ? 2 : eff_stream_variant(c, g.n, g.p);
+        g.tgrid = (variant == 1 ? 1 : 2) * c->nsm;
+        if (!dbl && variant != 2 && tstream_available()) {
             // map 0: the kind-A passes; map 1 + b: the kind-B passes of chunk b (by start qubit)
             std::vector<int> chunk_s;
             for (auto& ps : g.passes)
@@ -1002,7 +1007,7 @@ qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st) {
             if (g.tma)
                 CK(timed("tstream_pass", [&] {
                     return launch_tstream_pass(pass, g.tsp[pi], base + g.inst_off, g.count, base + g.maps_off,
-                                               2 * P->ctx->nsm, reinterpret_cast<unsigned*>(counters + PLAN_STATUS_SLOT), st);
+                                               g.tgrid, reinterpret_cast<unsigned*>(counters + PLAN_STATUS_SLOT), st);
                 }));
             else
                 CK(timed("stream_pass", [&] {
@@ -1324,8 +1329,9 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     s->mca = reinterpret_cast<double*>(b + omc);
     s->mscr = reinterpret_cast<double*>(b + oms);
     size_t h = 0;
-    const size_t hi = h; h = align256(h + (size_t)m * k * sizeof(int32_t));
+    // x then the index sets, spaced as on the device (ox, oi): one copy moves both
     const size_t hx = h; h = align256(h + (size_t)N);
+    const size_t hi = h; h = align256(h + (size_t)m * k * sizeof(int32_t));
     const size_t ht = h; h = align256(h + (size_t)m * K * sizeof(uint64_t));
     const size_t he = h; h = align256(h + (size_t)m * sizeof(double));
     const size_t hb2 = h; h = align256(h + (size_t)m * k * k * sizeof(double));
@@ -1338,6 +1344,11 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     char* hb = static_cast<char*>(s->host);
     s->idx_h = reinterpret_cast<int32_t*>(hb + hi);
     s->x_h = reinterpret_cast<uint8_t*>(hb + hx);
+    if (reinterpret_cast<char*>(s->idx_h) - reinterpret_cast<char*>(s->x_h) !=
+        reinterpret_cast<char*>(s->idx_dev) - reinterpret_cast<char*>(s->x_dev)) {
+        dqaoa_session_destroy(s);
+        return fail(QAOA_E_INVALID, "session_create: staging layout mismatch");
+    }
     s->topk_h = reinterpret_cast<uint64_t*>(hb + ht);
     s->expect_h = reinterpret_cast<double*>(hb + he);
     s->qblk_h = reinterpret_cast<double*>(hb + hb2);
@@ -1434,8 +1445,10 @@ qaoa_status session_decompose(dqaoa_session* s, const double* Q, int q_changed, 
     if (r) return r;
     std::memcpy(s->x_h, x, (size_t)N);
     CK(cudaEventRecord(s->dev_begin, st));
-    CK(cudaMemcpyAsync(s->x_dev, s->x_h, (size_t)N, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(s->idx_dev, s->idx_h, (size_t)m * k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->x_dev, s->x_h,
+                       (size_t)(reinterpret_cast<char*>(s->idx_h) - reinterpret_cast<char*>(s->x_h)) +
+                           (size_t)m * k * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, st));
     CK(launch_subqubo(s->Q_dev, N, s->x_dev, rows, k, s->idx_dev, s->conditioned, s->qsub, st, s->qblk, qdiag));
     return QAOA_OK;
 }

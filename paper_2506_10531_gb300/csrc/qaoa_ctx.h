@@ -38,6 +38,14 @@ inline int eff_tier(const qaoa_ctx* c, int n, int p) {
 // The cluster-streaming tier can run n-qubit instances on the context's device (tensor-map
 // encoder found, a cluster of its shape fits); cached per n.
 bool cstream_usable(qaoa_ctx* c, int n);
+// Variant of the HBM-streaming tier's forward passes: 0 TMA passes with two CTAs per SM, 1 TMA
+// passes with one CTA per SM, 2 the per-thread cp.async passes (qaoa_set_tier's param, else the
+// autotuner's, else 0).
+inline int eff_stream_variant(const qaoa_ctx* c, int n, int p) {
+    if (c->tier[n] == QAOA_TIER_STREAM) return c->cluster_L[n];
+    if (p >= 1 && p <= 64 && c->tuned[n][p].tier == QAOA_TIER_STREAM) return c->tuned[n][p].L;
+    return 0;
+}
 inline int eff_cluster_L(const qaoa_ctx* c, int n, int p) {
     if (c->tier[n] == QAOA_TIER_CLUSTER && c->cluster_L[n]) return c->cluster_L[n];
     if (p >= 1 && p <= 64 && c->tuned[n][p].tier == QAOA_TIER_CLUSTER && c->tuned[n][p].L) return c->tuned[n][p].L;

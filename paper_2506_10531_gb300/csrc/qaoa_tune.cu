@@ -1,10 +1,12 @@
 // qaoa_tune.cu -- autotuner and tuning table of libqaoa.
 //
 // For complex64 batches of `count` instances of (n, p) with top-k length k the tuner times every
-// kernel configuration that can run them -- the cluster tier with 13 or 14 local qubits per CTA
-// (2^(n-L) CTAs per cluster, at most 16) and the HBM-streaming tier, for 15 <= n <= 18 -- on
-// synthetic inputs, with CUDA events around whole plan launches (best of several), and stores the
-// fastest in the context. Plans created afterwards use the stored choice unless qaoa_set_tier
+// kernel configuration that can run them on synthetic inputs, with CUDA events around whole plan
+// launches (best of several), and stores the fastest in the context. For 15 <= n <= 30: the
+// HBM-streaming tier's three forward-pass variants (TMA passes with two CTAs per SM or one, the
+// per-thread cp.async passes); for 15 <= n <= 18 also the DSMEM cluster tier with 13 or 14 local
+// qubits per CTA (2^(n-L) CTAs per cluster, at most 16); for 15 <= n <= 17 the cluster-streaming
+// tier. Plans created afterwards use the stored choice unless qaoa_set_tier
 // overrides it. The table is saved and loaded as a small JSON document, so a sweep done once
 // per machine can be reused (the offline sweep / online cache split).
 #include <cuda_runtime.h>
@@ -61,11 +63,12 @@ extern "C" qaoa_status qaoa_autotune(qaoa_ctx* c, int n, int p, int k, int count
     cudaStream_t st = (cudaStream_t)stream;
     TCK(cudaSetDevice(c->device), "cudaSetDevice");
     std::vector<Candidate> cand;
-    if (n >= 15 && n <= 18) {
+    if (n >= 15) {
         if (n <= qaoa::CS_NMAX && qaoa::cstream_usable(c, n)) cand.push_back({QAOA_TIER_CSTREAM, 0});
-        for (int L = 14; L >= 13; --L)
-            if (n - L >= 1 && n - L <= 4) cand.push_back({QAOA_TIER_CLUSTER, L});
-        cand.push_back({QAOA_TIER_STREAM, 0});
+        if (n <= 18)
+            for (int L = 14; L >= 13; --L)
+                if (n - L >= 1 && n - L <= 4) cand.push_back({QAOA_TIER_CLUSTER, L});
+        for (int v = 0; v <= 2; ++v) cand.push_back({QAOA_TIER_STREAM, v});
     } else {
         cand.push_back({0, 0});   // one configuration: time it, store nothing
     }
@@ -207,9 +210,9 @@ extern "C" qaoa_status qaoa_tuning_load(qaoa_ctx* c, const char* path) {
         double ms = 0.0;
         if (sscanf(text.c_str() + pos, "{\"n\": %d, \"p\": %d, \"tier\": %d, \"L\": %d, \"ms\": %lf, \"count\": %d, \"k\": %d}",
                    &n, &p, &tier, &L, &ms, &cnt, &k) == 7 &&
-            n >= 15 && n <= 18 && p >= 1 && p <= 64 &&
-            (tier == QAOA_TIER_STREAM || (tier == QAOA_TIER_CSTREAM && n <= qaoa::CS_NMAX) ||
-             (tier == QAOA_TIER_CLUSTER && n - L >= 1 && n - L <= 4 && L >= 10))) {
+            n >= 15 && n <= 30 && p >= 1 && p <= 64 &&
+            ((tier == QAOA_TIER_STREAM && L >= 0 && L <= 2) || (tier == QAOA_TIER_CSTREAM && n <= qaoa::CS_NMAX) ||
+             (tier == QAOA_TIER_CLUSTER && n <= 18 && n - L >= 1 && n - L <= 4 && L >= 10))) {
             qaoa_tuned& t = c->tuned[n][p];
             t.tier = tier;
             t.L = L;

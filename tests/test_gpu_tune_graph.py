@@ -126,3 +126,51 @@ def test_plan_graph_capture_replays(q):
         q.qaoa_plan_destroy(direct)
     finally:
         q.qaoa_destroy(ctx)
+
+
+def test_streaming_variants_agree_and_tune(q, tmp_path):
+    # the streaming tier's forward-pass variants (TMA passes with two or one CTA per SM, the
+    # cp.async passes) give the same results (the two TMA grids bit for bit: same arithmetic per
+    # tile, fixed reduction order), and the tuner stores a variant for n = 20 that plans follow
+    specs = [(20, 2, 8)] * 3
+    out = {}
+    for v in (0, 1, 2):
+        ctx = q.qaoa_create(0)
+        try:
+            q.qaoa_set_tier(ctx, 20, q.QAOA_TIER_STREAM, v)
+            insts, io, _, (ex, ti, tp) = batch(q, specs, 41)
+            plan = q.qaoa_plan_create(ctx, insts, io)
+            try:
+                q.qaoa_plan_set_timing(plan, True)
+                q.qaoa_plan_launch(plan)
+                torch.cuda.synchronize()
+                names = {nm for nm, _ in q.qaoa_plan_kernel_times(plan)}
+                q.qaoa_plan_check(plan)
+            finally:
+                q.qaoa_plan_destroy(plan)
+            out[v] = (ex.cpu().numpy(), ti.cpu().numpy(), tp.cpu().numpy(), names)
+        finally:
+            q.qaoa_destroy(ctx)
+    assert "tstream_pass" in out[0][3] and "tstream_pass" in out[1][3] and "stream_pass" in out[2][3]
+    for a, b in zip(out[0][:3], out[1][:3]):
+        np.testing.assert_array_equal(a, b)
+    absq = max(float(np.abs(synth.symmetric_q(20, seed=41 + i)).sum()) for i in range(3))
+    assert np.max(np.abs(out[2][0] - out[0][0])) <= 2e-5 * absq
+    assert np.max(np.abs(out[2][2] - out[0][2])) <= 1e-6 * max(out[0][2].max(), 1e-30) + 1e-12
+    ctx = q.qaoa_create(0)
+    try:
+        with pytest.raises(q.QaoaError):
+            q.qaoa_set_tier(ctx, 20, q.QAOA_TIER_STREAM, 3)
+        ms = q.qaoa_autotune(ctx, 20, 2, 8, 4)
+        tier, prm, _ = q.qaoa_tuning_get(ctx, 20, 2)
+        assert ms > 0 and tier == q.QAOA_TIER_STREAM and prm in (0, 1, 2)
+        path = tmp_path / "tuning20.json"
+        q.qaoa_tuning_save(ctx, str(path))
+    finally:
+        q.qaoa_destroy(ctx)
+    ctx = q.qaoa_create(0)
+    try:
+        q.qaoa_tuning_load(ctx, str(path))
+        assert q.qaoa_tuning_get(ctx, 20, 2)[:2] == (tier, prm)
+    finally:
+        q.qaoa_destroy(ctx)
