@@ -286,6 +286,7 @@ __device__ __forceinline__ void tile_load(const TsPass& T, const CUtensorMap* ma
     const int mid = (int)(tau & ((1ull << T.midbits) - 1ull)), top = (int)(tau >> T.midbits);
     switch (T.bmode) {
         case TS_A: tma_load_4d(dst, map, 0, 0, 0, (int)tau, bar); break;
+        case TS_A3: tma_load_3d(dst, map, 0, 0, (int)tau, bar); break;
         case TS_B5: tma_load_5d(dst, map, 0, 0, mid, 0, top, bar); break;
         case TS_B4: tma_load_4d(dst, map, 0, 0, mid, 0, bar); break;
         case TS_B9_5: tma_load_5d(dst, map, 0, mid, 0, 0, top, bar); break;
@@ -296,6 +297,7 @@ __device__ __forceinline__ void tile_store(const TsPass& T, const CUtensorMap* m
     const int mid = (int)(tau & ((1ull << T.midbits) - 1ull)), top = (int)(tau >> T.midbits);
     switch (T.bmode) {
         case TS_A: tma_store_4d(map, src, 0, 0, 0, (int)tau); break;
+        case TS_A3: tma_store_3d(map, src, 0, 0, (int)tau); break;
         case TS_B5: tma_store_5d(map, src, 0, 0, mid, 0, top); break;
         case TS_B4: tma_store_4d(map, src, 0, 0, mid, 0); break;
         case TS_B9_5: tma_store_5d(map, src, 0, mid, 0, 0, top); break;
@@ -494,10 +496,143 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_pass(const StreamPass P, cons
                 bulk_commit();
             }
         } else {
+            fence_async_smem();   // the sub-passes' shared writes before the next tile's TMA writes
             __syncthreads();
         }
         // the next tile's load, once this tile's store has read the buffer
         if (loads && k + 1 < nmine && threadIdx.x == 0 && ok) {
+            bulk_wait_read();
+            issue(k + 1);
+        }
+    }
+    if (threadIdx.x == 0) {
+        bulk_wait_all();
+        if (!ok) atomicOr(status, 1u);
+    }
+}
+
+// ---- adjoint passes ---------------------------------------------------------------------------
+// The forward pass P undone on 2^12-amplitude tiles of psi and lam (both in the rotated frame),
+// with the adjoint sub-passes of the tile engine on the TMA layout (amplitudes in the 128-byte
+// swizzle, energies unswizzled): the local snake of P run in reverse, a single layer that opens
+// with its cost phase ordered so that the phase (an energy read) shares the top window, where
+// the lanes of a warp cover the low tile bits. Per tile the four FP64 gradient partials of the
+// cp.async adjoint ([0] Im <lam|B|psi> of layer lb, [1] of la, [2] Im <lam|E|psi> of lb, [3] of
+// la) are written; psi and lam go back by TMA unless this is the last adjoint pass. Persistent,
+// two CTAs per SM (psi, lam and energies of a tile: 80 KiB), a CTA's next tile loaded once the
+// bulk stores of the current one have read the buffers.
+constexpr uint32_t TDA = 1u << TSA_TB;
+
+struct TaOff {
+    size_t psi, lam, E, lc, red, mbar, total;
+};
+__host__ __device__ inline TaOff ta_offsets() {
+    TaOff o{};
+    size_t x = 0;
+    o.psi = x; x += (size_t)TDA * 8;   // 1024-aligned at run time (swizzled)
+    o.lam = x; x += (size_t)TDA * 8;   // 32 KiB further: still 1024-aligned
+    o.E = x; x += (size_t)TDA * 4;
+    o.lc = x; x = ts_al(x + 64 * sizeof(LayerConst<float>));
+    o.red = x; x = ts_al(x + 32 * sizeof(double));
+    o.mbar = x; x = ts_al(x + sizeof(uint64_t));
+    o.total = x + 1024;
+    return o;
+}
+
+__global__ void __launch_bounds__(NT, 2) k_tstream_adj_pass(const StreamPass P, const TsPass T, int si,
+                                                           int lam_first, int store,
+                                                           const StreamInst<float>* __restrict__ insts, int count,
+                                                           const CUtensorMap* __restrict__ maps, unsigned* status) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const uint32_t raw = saddr(sm_raw);
+    unsigned char* sm = sm_raw + (((raw + 1023u) & ~1023u) - raw);
+    const TaOff o = ta_offsets();
+    float2* spsi = reinterpret_cast<float2*>(sm + o.psi);
+    float2* slam = reinterpret_cast<float2*>(sm + o.lam);
+    float* sE = reinterpret_cast<float*>(sm + o.E);
+    LayerConst<float>* lc = reinterpret_cast<LayerConst<float>*>(sm + o.lc);
+    double* red = reinterpret_cast<double*>(sm + o.red);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + o.mbar);
+    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    __syncthreads();
+
+    constexpr int RA = Num<float>::RB_ADJ;
+    const uint64_t ntiles = 1ull << (P.n - TSA_TB);
+    const uint64_t total = ntiles * (uint64_t)count;
+    const uint64_t first = blockIdx.x, step = gridDim.x;
+    const int nmine = first < total ? (int)((total - 1 - first) / step + 1) : 0;
+    const bool need_e = lam_first || P.ph_first || P.lb > P.la;
+    uint32_t parity = 0;
+    bool ok = true;
+    auto issue = [&](int k) {
+        const uint64_t q = first + (uint64_t)k * step;
+        const int ii = (int)(q / ntiles);
+        const uint64_t tau = q % ntiles;
+        const CUtensorMap* m = maps + (size_t)ii * T.maps_per_inst;
+        mbar_expect_tx(mbar, TDA * 8 + (lam_first ? 0u : TDA * 8) + (need_e ? TDA * 4 : 0u));
+        tile_load(T, m + T.map, spsi, tau, mbar);
+        if (!lam_first) tile_load(T, m + T.map + 1, slam, tau, mbar);
+        if (need_e) tile_load(T, m + T.emap, sE, tau, mbar);
+    };
+    if (nmine > 0 && threadIdx.x == 0) issue(0);
+    const float *cur_g = nullptr, *cur_b = nullptr;
+    int cur_p = 0;
+    const TileRef<float> tile{spsi, slam, sE, TSA_TB};
+    const int m0 = (P.kind == 0) ? 0 : P.c;
+    const int G = num_windows(m0, TSA_TB, RA);
+    const int nl = P.lb - P.la + 1;
+    const int S = snake_len(G, nl);
+    for (int k = 0; k < nmine; ++k) {
+        const uint64_t q = first + (uint64_t)k * step;
+        const int ii = (int)(q / ntiles);
+        const uint64_t tau = q % ntiles;
+        const StreamInst<float>& I = insts[ii];
+        if (I.gamma != cur_g || I.beta != cur_b || I.p != cur_p) {
+            __syncthreads();
+            set_layer_consts<float>(lc, I.gamma, I.beta, I.p, P.n, false);
+            cur_g = I.gamma;
+            cur_b = I.beta;
+            cur_p = I.p;
+        }
+        if (ok) ok = mbar_wait_bounded(mbar, parity);
+        parity ^= 1u;
+        float ab[2] = {0.0f, 0.0f}, ag[2] = {0.0f, 0.0f};
+        for (int kk = S - 1; kk >= 0; --kk) {
+            SubPass sp;
+            snake_step(kk, G, nl, P.la, P.ph_first, m0, TSA_TB, TSA_TB, RA, sp, true);
+            float lb_[2] = {0.0f, 0.0f}, lg_[2] = {0.0f, 0.0f};
+            subpass_adj<float, RA, TmaLayout>(tile, sp, lc, lam_first && kk == S - 1, lb_, lg_);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int slot = P.lb - (sp.lb - j);
+                if (j <= sp.lb - sp.la) {
+                    if (slot == 0) { ab[0] += lb_[j]; ag[0] += lg_[j]; }
+                    else { ab[1] += lb_[j]; ag[1] += lg_[j]; }
+                }
+            }
+            __syncthreads();
+        }
+        double* out = I.part_grad + ((uint64_t)si << (P.n - TSA_TB)) * 4 + tau * 4;
+        const double v0 = block_sum((double)ab[0], red);
+        const double v1 = block_sum((double)ab[1], red);
+        const double v2 = block_sum((double)ag[0], red);
+        const double v3 = block_sum((double)ag[1], red);
+        if (threadIdx.x == 0) { out[0] = v0; out[1] = v1; out[2] = v2; out[3] = v3; }
+        if (store) {
+            fence_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const CUtensorMap* m = maps + (size_t)ii * T.maps_per_inst;
+                tile_store(T, m + T.map, spsi, tau);
+                tile_store(T, m + T.map + 1, slam, tau);
+                bulk_commit();
+            }
+        } else {
+            fence_async_smem();   // the sub-passes' shared writes before the next tile's TMA writes
+            __syncthreads();
+        }
+        // the next tile's loads, once this tile's stores have read the buffers
+        if (k + 1 < nmine && threadIdx.x == 0 && ok) {
             bulk_wait_read();
             issue(k + 1);
         }
@@ -541,6 +676,12 @@ bool encode_shape(const StreamPass& P, void* base, int w, CUtensorMap* m) {
     const cuuint64_t f = (cuuint64_t)w * 4;            // bytes per element
     const cuuint32_t d0 = 16u * (cuuint32_t)w;
     const bool swz = w == 2;
+    if (P.kind == 0 && P.tb == TSA_TB) {   // (16 elements, 256 lines, tile): the adjoint's tiles
+        const cuuint64_t d[3] = {d0, 256, 1ull << (n - TSA_TB)};
+        const cuuint64_t s[2] = {16 * f, 4096 * f};
+        const cuuint32_t b[3] = {d0, 256, 1};
+        return encode(m, base, 3, d, s, b, swz);
+    }
     if (P.kind == 0) {   // (16 elements, 256 lines, 2 planes, tile)
         const cuuint64_t d[4] = {d0, 256, 2, 1ull << (n - TB)};
         const cuuint64_t s[3] = {16 * f, 4096 * f, 8192 * f};
@@ -599,6 +740,44 @@ cudaError_t launch_tstream_pass(const StreamPass& P, const TsPass& T, const void
     if (e != cudaSuccess) return e;
     k_tstream_pass<<<grid, NT, sm, st>>>(P, T, static_cast<const StreamInst<float>*>(insts), count,
                                          static_cast<const CUtensorMap*>(maps), status);
+    return cudaGetLastError();
+}
+
+size_t tstream_adj_smem_bytes() { return ta_offsets().total; }
+
+TsPass tstream_adj_geometry(const StreamPass& P, int map, int maps_per_inst) {
+    TsPass T{};
+    T.map = map;
+    T.emap = map + 2;
+    T.maps_per_inst = maps_per_inst;
+    if (P.kind == 0) {
+        T.bmode = TS_A3;
+        T.midbits = 0;
+        return T;
+    }
+    T.midbits = P.s - P.c;
+    T.bmode = (P.s + P.h < P.n) ? TS_B5 : TS_B4;
+    return T;
+}
+
+bool tstream_encode_adj_maps(const StreamPass& P, void* psi, void* lam, void* E, void* maps3) {
+    if (!encode_fn() || P.tb != TSA_TB || P.n <= TSA_TB || P.n > 34 || (P.kind == 1 && (P.h > 8 || P.c < 4)))
+        return false;
+    char* b = static_cast<char*>(maps3);
+    return encode_shape(P, psi, 2, reinterpret_cast<CUtensorMap*>(b)) &&
+           encode_shape(P, lam, 2, reinterpret_cast<CUtensorMap*>(b + TS_MAP_BYTES)) &&
+           encode_shape(P, E, 1, reinterpret_cast<CUtensorMap*>(b + 2 * TS_MAP_BYTES));
+}
+
+cudaError_t launch_tstream_adj_pass(const StreamPass& P, const TsPass& T, int si, bool lam_first, bool store,
+                                    const void* insts, int count, const void* maps, int grid, unsigned* status,
+                                    cudaStream_t st) {
+    const size_t sm = tstream_adj_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_tstream_adj_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_tstream_adj_pass<<<grid, NT, sm, st>>>(P, T, si, lam_first ? 1 : 0, store ? 1 : 0,
+                                             static_cast<const StreamInst<float>*>(insts), count,
+                                             static_cast<const CUtensorMap*>(maps), status);
     return cudaGetLastError();
 }
 

@@ -415,7 +415,10 @@ struct qaoa_plan {
                       // TMA streaming passes (complex64): per instance one state tensor map per
                       // pass shape, at maps_off in the header; tsp[i] is pass i's geometry
                       bool tma = false; size_t maps_off = 0; int maps_per_inst = 0; std::vector<TsPass> tsp;
-                      int tgrid = 0; };   // TMA passes' persistent grid
+                      int tgrid = 0;   // TMA passes' persistent grid
+                      // TMA adjoint passes: per instance three maps (psi, lam, E) per adjoint pass
+                      // shape at amaps_off; atsp[i] is adjoint pass i's geometry
+                      bool tadj = false; size_t amaps_off = 0; int amaps_per_inst = 0; std::vector<TsPass> atsp; };
     std::vector<ResGroup> res;
     std::vector<CluGroup> clu;
     std::vector<CsGroup> cs;
@@ -633,6 +636,23 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             }
             g.maps_off = hdr;
             hdr = align256(hdr + TS_MAP_BYTES * (size_t)g.maps_per_inst * g.count);
+            if (g.grad && tba == TSA_TB) {
+                // adjoint shapes: kind A, then the kind-B chunks of the adjoint plan by start qubit
+                std::vector<int> achunk;
+                for (auto& ps : g.apasses)
+                    if (ps.kind == 1 && std::find(achunk.begin(), achunk.end(), ps.s) == achunk.end())
+                        achunk.push_back(ps.s);
+                std::sort(achunk.begin(), achunk.end());
+                g.amaps_per_inst = 3 * (1 + (int)achunk.size());
+                for (auto& ps : g.apasses) {
+                    const int ai = ps.kind == 0 ? 0
+                                                : 1 + (int)(std::find(achunk.begin(), achunk.end(), ps.s) - achunk.begin());
+                    g.atsp.push_back(tstream_adj_geometry(ps, 3 * ai, g.amaps_per_inst));
+                }
+                g.amaps_off = hdr;
+                hdr = align256(hdr + TS_MAP_BYTES * (size_t)g.amaps_per_inst * g.count);
+                g.tadj = true;
+            }
         }
         std::vector<SI> v;
         const uint64_t D = 1ull << g.n, nt = 1ull << (g.n - tb);
@@ -774,6 +794,20 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
                     }
                 }
             }
+            if (g.tadj) {
+                std::vector<char> done(g.amaps_per_inst, 0);
+                for (size_t pi = 0; pi < g.apasses.size(); ++pi) {
+                    const int mi = g.atsp[pi].map;
+                    if (done[mi]) continue;
+                    done[mi] = 1;
+                    char* row = img.data() + g.amaps_off + TS_MAP_BYTES * (size_t)(j - 1) * g.amaps_per_inst;
+                    if (!tstream_encode_adj_maps(g.apasses[pi], I.psi, I.lam, const_cast<T*>(I.E),
+                                                 row + TS_MAP_BYTES * mi)) {
+                        g.tadj = false;
+                        break;
+                    }
+                }
+            }
             si.push_back(I);
             g.q.push_back(qpool + d.q_off);
             g.e.push_back(Ebuf);
@@ -897,7 +931,10 @@ size_t plan_inst_scratch_bytes(qaoa_ctx* c, int n, int p, int k, bool grad) {
 // Upper bound of a complex64 plan's header (counters and descriptor arrays) for `count` instances.
 size_t plan_header_bound(int count) {
     const size_t d = std::max(std::max(sizeof(InstDesc<float>), sizeof(StreamInst<float>)), cstream_inst_bytes());
-    return align256(256 + (size_t)count * (align256(d) + CS_MAPS_BYTES + 512));
+    // tensor maps per instance: the cluster-streaming tier's, or at n <= 30 the TMA streaming
+    // tier's forward maps (at most 3 shapes x 2) and adjoint maps (at most 4 shapes x 3)
+    const size_t maps = std::max<size_t>(CS_MAPS_BYTES, 18 * TS_MAP_BYTES);
+    return align256(256 + (size_t)count * (align256(d) + maps + 512));
 }
 
 // A complex64 plan placed in caller memory, its header uploaded on `st` from pinned `staging`.
@@ -1021,6 +1058,10 @@ qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st) {
             const int SA = (int)g.apasses.size();
             for (int s = SA - 1; s >= 0; --s)
                 CK(timed("stream_adjoint", [&] {
+                    if (g.tadj)
+                        return launch_tstream_adj_pass(g.apasses[s], g.atsp[s], s, s == SA - 1, s > 0, base + g.inst_off,
+                                                       g.count, base + g.amaps_off, 2 * P->ctx->nsm,
+                                                       reinterpret_cast<unsigned*>(counters + PLAN_STATUS_SLOT), st);
                     return launch_stream_adj_pass(P->dbl, g.apasses[s], s, s == SA - 1, s > 0, base + g.inst_off,
                                                   g.count, g.agrid, st);
                 }));

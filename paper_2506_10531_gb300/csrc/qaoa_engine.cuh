@@ -95,9 +95,12 @@ __device__ __forceinline__ int snake_len(int G, int nl) {
 }
 
 // The s-th sub-pass of the snake over layers L0..L0+nl-1 (ph_first of the very first one is
-// given by `first_ph`). Returns window index w plus the SubPass fields.
+// given by `first_ph`). Returns window index w plus the SubPass fields. top_phase: a single
+// layer that opens with its cost phase runs its windows top down, so the phase shares the top
+// window (the mixer windows of one layer commute); the TMA adjoint keeps every energy read in a
+// window whose lanes cover the low tile bits that way.
 __device__ __forceinline__ void snake_step(int s, int G, int nl, int L0, int first_ph, int m0,
-                                           int m1, int tb, int R, SubPass& sp) {
+                                           int m1, int tb, int R, SubPass& sp, bool top_phase = false) {
     int w, la, lb, phf;
     if (G <= 1) {
         w = 0;
@@ -108,7 +111,7 @@ __device__ __forceinline__ void snake_step(int s, int G, int nl, int L0, int fir
         int l, pos;
         if (s < G) { l = 0; pos = s; }
         else { l = 1 + (s - G) / (G - 1); pos = 1 + (s - G) % (G - 1); }
-        const bool fwd = (l % 2) == 0;
+        const bool fwd = (l % 2) == 0 && !(top_phase && nl == 1 && first_ph);
         w = fwd ? pos : (G - 1 - pos);
         la = L0 + l;
         lb = (pos == G - 1 && l + 1 < nl) ? la + 1 : la;
@@ -206,6 +209,15 @@ __device__ __forceinline__ T mix_group_adj(C (&v)[1 << R], C (&u)[1 << R], int m
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
+// Shared-memory layout of a tile: position of amplitude u (p) and of energy u (e). The engine's
+// own swizzle for both; the TMA tiers use the hardware's 128-byte swizzle for amplitudes and
+// unswizzled energies. Both maps are linear over GF(2).
+template <typename T>
+struct SwzLayout {
+    __device__ __forceinline__ static uint32_t p(uint32_t u) { return swz<T>(u); }
+    __device__ __forceinline__ static uint32_t e(uint32_t u) { return swz<T>(u); }
+};
+
 // Element addresses of a group. The swizzle is linear over GF(2) and a group's base index and
 // its window offsets (i << A) have disjoint bits, so
 //   swz(base | (i << A)) = swz(base) ^ swz(i << A),
@@ -215,41 +227,41 @@ __device__ __forceinline__ uint32_t woff(int i) { return swz<T>((uint32_t)i << A
 
 // Load / store the 2^R amplitudes of a group (window start A). complex64 windows starting at
 // bit 0 move aligned pairs with one 16-byte shared access (the swizzle keeps pairs adjacent).
-template <int R, int A>
+template <int R, int A, typename Lay = SwzLayout<float>>
 __device__ __forceinline__ void load_group(const float2* psi, uint32_t sb, float2 (&v)[1 << R]) {
     if (A == 0 && R >= 1) {
 #pragma unroll
         for (int i = 0; i < (1 << R); i += 2) {
-            const float4 t = *reinterpret_cast<const float4*>(psi + (sb ^ woff<float, A>(i)));
+            const float4 t = *reinterpret_cast<const float4*>(psi + (sb ^ Lay::p((uint32_t)i << A)));
             v[i] = make_float2(t.x, t.y);
             v[i + 1] = make_float2(t.z, t.w);
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < (1 << R); ++i) v[i] = psi[sb ^ woff<float, A>(i)];
+        for (int i = 0; i < (1 << R); ++i) v[i] = psi[sb ^ Lay::p((uint32_t)i << A)];
     }
 }
-template <int R, int A>
+template <int R, int A, typename Lay = SwzLayout<float>>
 __device__ __forceinline__ void store_group(float2* psi, uint32_t sb, const float2 (&v)[1 << R]) {
     if (A == 0 && R >= 1) {
 #pragma unroll
         for (int i = 0; i < (1 << R); i += 2)
-            *reinterpret_cast<float4*>(psi + (sb ^ woff<float, A>(i))) =
+            *reinterpret_cast<float4*>(psi + (sb ^ Lay::p((uint32_t)i << A))) =
                 make_float4(v[i].x, v[i].y, v[i + 1].x, v[i + 1].y);
     } else {
 #pragma unroll
-        for (int i = 0; i < (1 << R); ++i) psi[sb ^ woff<float, A>(i)] = v[i];
+        for (int i = 0; i < (1 << R); ++i) psi[sb ^ Lay::p((uint32_t)i << A)] = v[i];
     }
 }
-template <int R, int A>
+template <int R, int A, typename Lay = SwzLayout<double>>
 __device__ __forceinline__ void load_group(const double2* psi, uint32_t sb, double2 (&v)[1 << R]) {
 #pragma unroll
-    for (int i = 0; i < (1 << R); ++i) v[i] = psi[sb ^ woff<double, A>(i)];
+    for (int i = 0; i < (1 << R); ++i) v[i] = psi[sb ^ Lay::p((uint32_t)i << A)];
 }
-template <int R, int A>
+template <int R, int A, typename Lay = SwzLayout<double>>
 __device__ __forceinline__ void store_group(double2* psi, uint32_t sb, const double2 (&v)[1 << R]) {
 #pragma unroll
-    for (int i = 0; i < (1 << R); ++i) psi[sb ^ woff<double, A>(i)] = v[i];
+    for (int i = 0; i < (1 << R); ++i) psi[sb ^ Lay::p((uint32_t)i << A)] = v[i];
 }
 
 // Shared state of one tile.
@@ -338,25 +350,26 @@ __device__ __forceinline__ void subpass_fwd(const TileRef<T>& t, const SubPass& 
 }
 
 // Adjoint sub-pass with a compile-time window start A (see subpass_adj).
-template <typename T, int R, int A>
+template <typename T, int R, int A, typename Lay = SwzLayout<T>>
 __device__ __forceinline__ void subpass_adj_a(const TileRef<T>& t, const SubPass& sp,
                                               const LayerConst<T>* lc, bool lam_from_E,
                                               T (&acc_b)[2], T (&acc_g)[2]) {
     using C = typename Num<T>::C;
     const uint32_t ngroups = 1u << (t.tb - R);
     for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-        const uint32_t sb = swz<T>(group_base<R>(g, A));
+        const uint32_t base = group_base<R>(g, A);
+        const uint32_t sb = Lay::p(base), eb = Lay::e(base);
         C v[1 << R], u[1 << R];
-        load_group<R, A>(t.psi, sb, v);
+        load_group<R, A, Lay>(t.psi, sb, v);
         if (lam_from_E) {
 #pragma unroll
             for (int i = 0; i < (1 << R); ++i) {
-                const T e = t.E[sb ^ woff<T, A>(i)];
+                const T e = t.E[eb ^ Lay::e((uint32_t)i << A)];
                 u[i].x = e * v[i].x;
                 u[i].y = e * v[i].y;
             }
         } else {
-            load_group<R, A>(t.lam, sb, u);
+            load_group<R, A, Lay>(t.lam, sb, u);
         }
         for (int l = sp.lb; l >= sp.la; --l) {
             const int j = sp.lb - l;
@@ -367,7 +380,7 @@ __device__ __forceinline__ void subpass_adj_a(const TileRef<T>& t, const SubPass
                 T ag[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
                 for (int i = 0; i < (1 << R); ++i) {
-                    const T e = t.E[sb ^ woff<T, A>(i)];
+                    const T e = t.E[eb ^ Lay::e((uint32_t)i << A)];
                     ag[i & 3] = fma(e, im_conj_mul(u[i], v[i]), ag[i & 3]);
                     T s, c;
                     sincos_phase(gp, e, s, c);
@@ -378,8 +391,8 @@ __device__ __forceinline__ void subpass_adj_a(const TileRef<T>& t, const SubPass
                 if (j == 0) acc_g[0] += agt; else acc_g[1] += agt;
             }
         }
-        store_group<R, A>(t.psi, sb, v);
-        store_group<R, A>(t.lam, sb, u);
+        store_group<R, A, Lay>(t.psi, sb, v);
+        store_group<R, A, Lay>(t.lam, sb, u);
     }
 }
 
@@ -387,21 +400,21 @@ __device__ __forceinline__ void subpass_adj_a(const TileRef<T>& t, const SubPass
 //   acc_b[j] += Im <lam| sum_q X_q |psi> (window qubits) for layer lb - j,
 //   acc_g[j] += Im <lam| E |psi>                          for layer lb - j (its cost op).
 // lam_from_E: lam = E psi is formed on load (first adjoint sub-pass).
-template <typename T, int R>
+template <typename T, int R, typename Lay = SwzLayout<T>>
 __device__ __forceinline__ void subpass_adj(const TileRef<T>& t, const SubPass& sp,
                                             const LayerConst<T>* lc, bool lam_from_E,
                                             T (&acc_b)[2], T (&acc_g)[2]) {
     switch (sp.a) {
-        case 0: subpass_adj_a<T, R, 0>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 1: subpass_adj_a<T, R, 1>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 2: subpass_adj_a<T, R, 2>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 3: subpass_adj_a<T, R, 3>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 4: subpass_adj_a<T, R, 4>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 5: subpass_adj_a<T, R, 5>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 6: subpass_adj_a<T, R, 6>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 7: subpass_adj_a<T, R, 7>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        case 8: subpass_adj_a<T, R, 8>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
-        default: subpass_adj_a<T, R, 9>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 0: subpass_adj_a<T, R, 0, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 1: subpass_adj_a<T, R, 1, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 2: subpass_adj_a<T, R, 2, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 3: subpass_adj_a<T, R, 3, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 4: subpass_adj_a<T, R, 4, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 5: subpass_adj_a<T, R, 5, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 6: subpass_adj_a<T, R, 6, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 7: subpass_adj_a<T, R, 7, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        case 8: subpass_adj_a<T, R, 8, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
+        default: subpass_adj_a<T, R, 9, Lay>(t, sp, lc, lam_from_E, acc_b, acc_g); break;
     }
 }
 
@@ -651,11 +664,6 @@ __device__ __noinline__ bool build_tile_energy_any(int n, int L, uint32_t zfix, 
 // ---- final reductions of a tile -----------------------------------------------------------
 // Shared-memory placement of tile index u for the state (p) and the energies (e): the engine's
 // swizzle for both (default), or another layout supplied by a tier (a TMA-staged tile).
-template <typename T>
-struct SwzLayout {
-    __device__ __forceinline__ static uint32_t p(uint32_t u) { return swz<T>(u); }
-    __device__ __forceinline__ static uint32_t e(uint32_t u) { return swz<T>(u); }
-};
 
 // Shared scratch of tile_reduce (sizes: wb 16 * nwarps floats, cand TOPK_CAP entries, out 16,
 // wlists 32 * nwarps entries, cnt 4 ints).

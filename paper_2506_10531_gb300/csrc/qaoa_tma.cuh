@@ -20,7 +20,8 @@ constexpr int TMA_NT = 256;
 __device__ __forceinline__ uint32_t psw(uint32_t u) { return u ^ ((u >> 3) & 14u); }
 
 struct TmaLayout {
-    __device__ __forceinline__ static uint32_t p(uint32_t u) { return psw(u); }
+    __device__ __forceinline__ static uint32_t p(uint32_t u) { return psw(u); }   // amplitudes
+    __device__ __forceinline__ static uint32_t e(uint32_t u) { return u; }        // energies
 };
 
 // ---- TMA, mbarrier and proxy-fence primitives ------------------------------------------------

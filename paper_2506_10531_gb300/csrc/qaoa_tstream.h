@@ -1,5 +1,5 @@
 // qaoa_tstream.h -- internal interface of the TMA streaming passes (k_tstream.cu): the forward
-// passes of the HBM tier for complex64, with tiles moved by TMA through a three-stage ring.
+// and adjoint passes of the HBM tier for complex64, with tiles moved by TMA.
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -11,7 +11,10 @@ namespace qaoa {
 // Shape of the tensor map of a pass (TMA coordinates of a tile): kind A; kind B with h <= 8 and
 // qubits above the chunk (5-D) or without (4-D); kind B with h = 9, whose 512 high values are
 // split over two box dimensions (at most 256 each), 5-D or 4-D.
-enum : int { TS_A = 0, TS_B5 = 1, TS_B4 = 2, TS_B9_5 = 3, TS_B9_4 = 4 };
+enum : int { TS_A = 0, TS_B5 = 1, TS_B4 = 2, TS_B9_5 = 3, TS_B9_4 = 4, TS_A3 = 5 };   // TS_A3: kind A of
+// the adjoint's 12-bit tiles, 3-D
+// Tile bits of the adjoint passes (the adjoint plan of stream_plan with stream_adj_tile_bits).
+constexpr int TSA_TB = 12;
 
 struct TsPass {
     int bmode;          // TS_*
@@ -35,5 +38,15 @@ bool tstream_encode_maps(const StreamPass& P, void* psi, void* E, void* psi_map,
 // (device); a bounded wait that ran out sets bit 0 of *status.
 cudaError_t launch_tstream_pass(const StreamPass& P, const TsPass& T, const void* insts, int count,
                                 const void* maps, int grid, unsigned* status, cudaStream_t st);
+
+// Adjoint passes (tiles of TSA_TB bits, kind-B chunks of h <= 8 high qubits): per pass shape
+// three maps (state psi, adjoint state lam, energies) at indices T.map, T.map + 1, T.map + 2.
+size_t tstream_adj_smem_bytes();
+TsPass tstream_adj_geometry(const StreamPass& P, int map, int maps_per_inst);
+bool tstream_encode_adj_maps(const StreamPass& P, void* psi, void* lam, void* E, void* maps3);
+// Adjoint pass `si` of the adjoint plan over `count` instances (see launch_stream_adj_pass).
+cudaError_t launch_tstream_adj_pass(const StreamPass& P, const TsPass& T, int si, bool lam_first, bool store,
+                                    const void* insts, int count, const void* maps, int grid, unsigned* status,
+                                    cudaStream_t st);
 
 }  // namespace qaoa

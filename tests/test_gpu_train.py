@@ -182,3 +182,49 @@ def test_training_through_a_captured_graph_is_identical(q, ctx):
     finally:
         A.close()
         B.close()
+
+
+def test_tma_adjoint_matches_cp_async_adjoint(q, orc):
+    # the TMA adjoint passes (default) and the per-thread cp.async adjoint (streaming variant 2)
+    # on the same gradient batch (n 14..24, every adjoint pass shape: kind A, kind-B chunks of
+    # 1..8 high qubits): gradients and <C> agree within the parity tolerance, and both match the
+    # FP64 oracle on a sample
+    from paper_2506_10531_gb300.train import QAOABatch
+    inst = []
+    for i, (n, p) in enumerate([(14, 3), (15, 2), (16, 4), (17, 1), (19, 2), (20, 3), (21, 2), (22, 1), (24, 2)]):
+        Q = synth.symmetric_q(n, seed=700 + i, dist="normal")
+        g, b = synth.random_params(p, seed=800 + i)
+        inst.append((Q, g, b))
+    out = {}
+    for variant in (0, 2):
+        ctx = q.qaoa_create(0)
+        try:
+            for n in range(15, 25):
+                q.qaoa_set_tier(ctx, n, q.QAOA_TIER_STREAM, variant)
+            B = QAOABatch(ctx, [x[0] for x in inst], [(x[1], x[2]) for x in inst])
+            try:
+                B.run()
+                torch.cuda.synchronize()
+                q.qaoa_plan_check(B.plan)
+                out[variant] = (B.grad.cpu().numpy(), B.expect.cpu().numpy(), B.params.cpu().numpy().astype(np.float64))
+            finally:
+                B.close()
+        finally:
+            q.qaoa_destroy(ctx)
+    g0, e0, params = out[0]
+    g2, e2, _ = out[2]
+    off = 0
+    for i, (Q, gg, _) in enumerate(inst):
+        n, p = Q.shape[0], len(gg)
+        Qd = Q.astype(np.float32).astype(np.float64)
+        absq = np.abs(Qd).sum()
+        a, b = g0[off:off + 2 * p], g2[off:off + 2 * p]
+        scale = max(np.max(np.abs(b)), 1.0)
+        assert np.max(np.abs(a - b)) <= 1e-5 * scale * max(1.0, n / 4), (i, n, p)
+        assert abs(e0[i] - e2[i]) <= 1e-5 * absq, (i, n, p)
+        if n <= 20:
+            E = orc.energies(Qd)
+            e_o, dg_o, db_o = orc.grad(n, params[off:off + p], params[off + p:off + 2 * p], E)
+            ref = np.concatenate([dg_o, db_o])
+            assert np.max(np.abs(a - ref)) <= 1e-5 * max(np.max(np.abs(ref)), 1.0) * max(1.0, n / 4), (i, n, p)
+        off += 2 * p
