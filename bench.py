@@ -548,8 +548,9 @@ def run_large(args):
     ex = torch.zeros(1, dtype=torch.float64, device=dev)
     ti = torch.zeros(k, dtype=torch.int64, device=dev)
     tp = torch.zeros(k, dtype=torch.float64, device=dev)
-    io = q.make_io(qd, pd, expect=ex, topk_idx=ti, topk_prob=tp, k_stride=k)
-    insts = q.make_insts([(n, p, k, 0, 0, 0, -1, -1)])
+    grad = torch.zeros(2 * p, dtype=torch.float64, device=dev) if args.large_grad else None
+    io = q.make_io(qd, pd, expect=ex, topk_idx=ti, topk_prob=tp, k_stride=k, grad=grad)
+    insts = q.make_insts([(n, p, k, q.QAOA_INST_GRAD if args.large_grad else 0, 0, 0, -1, -1)])
     plan = q.qaoa_plan_create(ctx, insts, io)
     for _ in range(args.warmup):
         q.qaoa_plan_launch(plan, stream)
@@ -567,7 +568,7 @@ def run_large(args):
     amps = (1 << n) * p * world
     roof = plan_roofline(q, plan, kern, lambda: q.qaoa_plan_launch(plan, stream), clk, dev,
                          workload=f"large_n{n}")
-    per_pass = {"ms": [round(v, 3) for v in kern.get("stream_pass", [])[:8]]}
+    per_pass = {"ms": [round(v, 3) for v in (kern.get("tstream_pass") or kern.get("stream_pass") or [])[:8]]}
     # e2e: Q and parameters from pinned host memory, <C> and top-k back, every step
     Qp = torch.from_numpy(Q.reshape(-1)).pin_memory()
     Pp = torch.from_numpy(par).pin_memory()
@@ -590,13 +591,14 @@ def run_large(args):
                  amps * args.steps / tot_s, "amp-layer-updates/s", args, world, 1e3 * tot_s / args.steps,
                  "c64 state, f32 energies, f64 reductions",
                  {"workload": f"large instance: dense n={n} QUBO U[-1,1] (seed 5), p=2, gamma=(0.4,0.7), "
-                              f"beta=(0.6,0.3), complex64 ({(8 << n) / 2**30:g} GiB) + FP32 energies, top-8",
+                              f"beta=(0.6,0.3), complex64 ({(8 << n) / 2**30:g} GiB) + FP32 energies, top-8"
+                              + (", with adjoint gradients (profiling case)" if args.large_grad else ""),
                   "l2": "inputs larger than L2 (state + energies)", "parallelism": f"replicas x{world}"},
                  solves_per_s=args.steps * world / tot_s,
                  amp_gate_updates_per_s=amps * (n + 1) * args.steps / tot_s,
                  latency_ms={"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
                  kernel_ms_per_step={nm: sum(v) / args.steps for nm, v in kern.items()},
-                 stream_pass_ms_first_step=per_pass, roofline=roof,
+                 pass_ms_first_step=per_pass, roofline=roof,
                  e2e={"value": amps * args.steps / e2e_s, "unit": "amp-layer-updates/s",
                       "h2d_bytes_per_step": Q.nbytes + par.nbytes, "d2h_bytes_per_step": 8 * (1 + 2 * k)},
                  gpu_launches=kernels * args.steps, clocks=clk.summary())
@@ -1050,6 +1052,8 @@ def main():
     ap.add_argument("--requests", type=int, default=100, help="requests per rate (serving config)")
     ap.add_argument("--large-n", type=int, default=LARGE["n"],
                     help="qubits of the large configuration (smaller values: profiling cases)")
+    ap.add_argument("--large-grad", action="store_true",
+                    help="large configuration with adjoint gradients (a profiling case of the adjoint passes)")
     ap.add_argument("--uneven-count", type=int, default=0,
                     help="instances of the uneven batch (0: the full 4096; smaller: profiling cases)")
     ap.add_argument("--config", default="dqaoa", choices=["dqaoa", "dqaoa10k"] + sorted(CONFIGS),
