@@ -37,6 +37,18 @@ __global__ void __launch_bounds__(1024) k_subqubo(const double* __restrict__ Q, 
     }
     __syncthreads();
     float* out = qsub + (int64_t)j * k * k;
+    const int ra = threadIdx.x >> 5, rr = threadIdx.x & 31;   // row and residue of this lane
+    const bool rowlane = conditioned && ra < k;               // whole warps
+    const double* row = rowlane ? Q + (int64_t)S[ra] * N : nullptr;
+    // the first 16 terms of this lane's partial sum are loaded before the element copies, so
+    // that both sets of global reads are in flight together
+    constexpr int NB = 16;
+    double v[NB];
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int l = rr + 32 * u;
+        v[u] = (rowlane && l < N && xm[l]) ? __ldg(row + l) : 0.0;
+    }
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         const int a = e / k, b = e % k;
         const double q = Q[(int64_t)S[a] * N + S[b]];
@@ -44,23 +56,23 @@ __global__ void __launch_bounds__(1024) k_subqubo(const double* __restrict__ Q, 
         if (qblk) qblk[(int64_t)j * k * k + e] = q;
         if (qdiag && a == b && !conditioned) qdiag[(int64_t)j * k + a] = q;
     }
-    if (!conditioned) return;
-    const int ra = threadIdx.x >> 5, rr = threadIdx.x & 31;   // row and residue of this lane
-    if (ra >= k) return;                                      // whole warps
-    const double* row = Q + (int64_t)S[ra] * N;
+    if (!rowlane) return;
     double h = 0.0;
-    for (int l0 = rr; l0 < N; l0 += 256) {
-        double v[8];
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+        if (rr + 32 * u < N && xm[rr + 32 * u]) h += v[u];
+    for (int l0 = rr + 32 * NB; l0 < N; l0 += 256) {
+        double w[8];
         bool on[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int l = l0 + 32 * u;
             on[u] = l < N && xm[l];
-            v[u] = on[u] ? __ldg(row + l) : 0.0;
+            w[u] = on[u] ? __ldg(row + l) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            if (on[u]) h += v[u];
+            if (on[u]) h += w[u];
     }
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) h = h + __shfl_xor_sync(0xffffffffu, h, d);
@@ -165,12 +177,24 @@ __global__ void __launch_bounds__(256) k_merge_setup_sum(int N, int blocks, cons
 // the raw block Q[S, S]. One warp per candidate: lane u sums its row over v ascending, and the
 // lanes' terms d_u * inner_u (zero for unchanged u) are added by the xor tree (d = 16 .. 1).
 // The merge adds the linear term 2 sum_u d_u (Qx)_{S_u} for the x it has reached.
+// With `packed`, the kernel also gathers what the host reads of the chunk into one block (the
+// pair terms at `pair`, then the candidates, the <C> values and the plan's status word), so
+// that one copy brings them back.
 __global__ void __launch_bounds__(256) k_cand_pair(int m, int k, int K, const int32_t* __restrict__ idx,
                                                    const uint8_t* __restrict__ x, const double* __restrict__ qblk,
-                                                   const uint64_t* __restrict__ cand, double* __restrict__ pair) {
+                                                   const uint64_t* __restrict__ cand, double* __restrict__ pair,
+                                                   const double* __restrict__ expect, const unsigned* __restrict__ status,
+                                                   int packed) {
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= (int64_t)m * K) return;   // warp-uniform
+    if (packed && lane == 0) {
+        uint64_t* cand_out = reinterpret_cast<uint64_t*>(pair + (int64_t)m * K);
+        double* expect_out = reinterpret_cast<double*>(cand_out + (int64_t)m * K);
+        cand_out[t] = cand[t];
+        if (t % K == 0) expect_out[t / K] = expect[t / K];
+        if (t == 0) *reinterpret_cast<unsigned*>(expect_out + m) = *status;
+    }
     const int64_t j = t / K;
     const int32_t* S = idx + j * k;
     const bool xa = lane < k && x[S[lane]] != 0;
@@ -230,10 +254,12 @@ cudaError_t launch_merge_setup(const double* Q, int N, const uint8_t* x, double*
 }
 
 cudaError_t launch_cand_pair(int m, int k, int K, const int32_t* idx, const uint8_t* x, const double* qblk,
-                             const uint64_t* cand, double* pair, cudaStream_t st) {
+                             const uint64_t* cand, double* pair, cudaStream_t st, const double* expect,
+                             const unsigned* status) {
     if (m < 1 || k < 1 || k > 30 || K < 1) return cudaErrorInvalidValue;
     const int64_t n = (int64_t)m * K;   // candidates, one warp each
-    k_cand_pair<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(m, k, K, idx, x, qblk, cand, pair);
+    k_cand_pair<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(m, k, K, idx, x, qblk, cand, pair, expect, status,
+                                                          expect && status ? 1 : 0);
     return cudaGetLastError();
 }
 

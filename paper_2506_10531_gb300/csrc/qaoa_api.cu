@@ -1268,7 +1268,6 @@ struct dqaoa_session {
     int32_t* idx_dev = nullptr;
     float* qsub = nullptr;
     double* qblk = nullptr;       // raw FP64 blocks Q[S_j, S_j] for the merge
-    double* pair = nullptr;       // pair term of each candidate's energy change (m*K)
     double* mh = nullptr;         // merge set-up on the device: h = Qx, column sums of |Q|, scratch
     double* mca = nullptr;
     double* mscr = nullptr;
@@ -1278,13 +1277,10 @@ struct dqaoa_session {
     void* host = nullptr;         // pinned staging
     int32_t* idx_h = nullptr;
     uint8_t* x_h = nullptr;
-    uint64_t* topk_h = nullptr;
     double* expect_h = nullptr;
     double* qblk_h = nullptr;
-    double* pair_h = nullptr;
     double* mh_h = nullptr;       // h and the column sums from the device set-up
     double* mca_h = nullptr;
-    unsigned* status_h = nullptr; // device status word of each chunk plan after its launch
     // the sub-QUBOs are solved in chunks, one plan each, so that the host merges chunk c while
     // the device solves chunk c + 1 (the merge is sequential over sub-QUBOs in index order)
     int chunks = 1;
@@ -1297,6 +1293,12 @@ struct dqaoa_session {
     cudaStream_t side = nullptr;
     cudaEvent_t sub_done = nullptr, qblk_done = nullptr, setup_done = nullptr;
     cudaStream_t solve2 = nullptr;  // the second chunk's solve
+    // per chunk one packed block (pair terms, candidates, <C>, status word) on the device and its
+    // pinned copy: one copy per chunk brings back everything the merge reads
+    char* pk_dev = nullptr;
+    char* pk_h = nullptr;
+    size_t pk_off[2] = {0, 0};
+    bool last_sampled = false;      // the last cycle was dqaoa_session_cycle_sampled
     cudaEvent_t solve_begin = nullptr, solve_end = nullptr;   // span of the chunk solves
     double t_decompose = 0.0, t_merge = 0.0, t_cycle = 0.0; // host ms of the last cycle
     MergeCache cache;             // h = Qx and E(x) after the last merge
@@ -1350,7 +1352,6 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     const size_t op = o; o = align256(o + (size_t)2 * p * sizeof(float));
     const size_t oe = o; o = align256(o + (size_t)m * sizeof(double));
     const size_t ot = o; o = align256(o + (size_t)m * K * sizeof(uint64_t));
-    const size_t opr = o; o = align256(o + (size_t)m * K * sizeof(double));
     const size_t omh = o; o = align256(o + (size_t)N * sizeof(double));
     const size_t omc = o; o = align256(o + (size_t)N * sizeof(double));
     const size_t oms = o; o = align256(o + (size_t)2 * merge_setup_blocks(N) * N * sizeof(double));
@@ -1365,7 +1366,6 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     s->params = reinterpret_cast<float*>(b + op);
     s->expect = reinterpret_cast<double*>(b + oe);
     s->topk = reinterpret_cast<uint64_t*>(b + ot);
-    s->pair = reinterpret_cast<double*>(b + opr);
     s->mh = reinterpret_cast<double*>(b + omh);
     s->mca = reinterpret_cast<double*>(b + omc);
     s->mscr = reinterpret_cast<double*>(b + oms);
@@ -1373,11 +1373,8 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     // x then the index sets, spaced as on the device (ox, oi): one copy moves both
     const size_t hx = h; h = align256(h + (size_t)N);
     const size_t hi = h; h = align256(h + (size_t)m * k * sizeof(int32_t));
-    const size_t ht = h; h = align256(h + (size_t)m * K * sizeof(uint64_t));
     const size_t he = h; h = align256(h + (size_t)m * sizeof(double));
     const size_t hb2 = h; h = align256(h + (size_t)m * k * k * sizeof(double));
-    const size_t hst = h; h = align256(h + 2 * sizeof(unsigned));
-    const size_t hpr = h; h = align256(h + (size_t)m * K * sizeof(double));
     const size_t hmh = h; h = align256(h + (size_t)N * sizeof(double));
     const size_t hmc = h; h = align256(h + (size_t)N * sizeof(double));
     e = cudaMallocHost(&s->host, h);
@@ -1390,11 +1387,8 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
         dqaoa_session_destroy(s);
         return fail(QAOA_E_INVALID, "session_create: staging layout mismatch");
     }
-    s->topk_h = reinterpret_cast<uint64_t*>(hb + ht);
     s->expect_h = reinterpret_cast<double*>(hb + he);
     s->qblk_h = reinterpret_cast<double*>(hb + hb2);
-    s->status_h = reinterpret_cast<unsigned*>(hb + hst);
-    s->pair_h = reinterpret_cast<double*>(hb + hpr);
     s->mh_h = reinterpret_cast<double*>(hb + hmh);
     s->mca_h = reinterpret_cast<double*>(hb + hmc);
     std::vector<float> par(2 * p);
@@ -1441,6 +1435,23 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
                               cudaEventCreateWithFlags(&s->chunk_solved[ch], cudaEventDisableTiming) != cudaSuccess))
             st = fail(QAOA_E_CUDA, "session event");
         if (st) { dqaoa_session_destroy(s); return st; }
+    }
+    {
+        size_t pk = 0;
+        for (int ch = 0; ch < s->chunks; ++ch) {
+            s->pk_off[ch] = pk;
+            pk += cand_pack_bytes(s->chunk_start[ch + 1] - s->chunk_start[ch], K);
+        }
+        if (cudaMalloc(&s->pk_dev, pk) != cudaSuccess) {
+            s->pk_dev = nullptr;
+            dqaoa_session_destroy(s);
+            return fail(QAOA_E_NOMEM, "session cudaMalloc (result blocks)");
+        }
+        if (cudaMallocHost(&s->pk_h, pk) != cudaSuccess) {
+            s->pk_h = nullptr;
+            dqaoa_session_destroy(s);
+            return fail(QAOA_E_NOMEM, "session cudaMallocHost (result blocks)");
+        }
     }
     if (cudaEventCreate(&s->dev_begin) != cudaSuccess || cudaEventCreate(&s->dev_end) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1529,24 +1540,24 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         cudaStream_t cs = ch == 0 ? st : s->solve2;
         r = qaoa_plan_launch(s->plans[ch], (qaoa_stream_t)cs);
         if (r) return r;
-        // results to the host on the side stream, after the pair terms of the chunk's candidates
-        // against the cycle's starting x: the solves do not wait for either
         CK(cudaEventRecord(s->chunk_solved[ch], cs));
-        CK(cudaStreamWaitEvent(s->side, s->chunk_solved[ch], 0));
+        // the pair terms of the chunk's candidates against the cycle's starting x, packed with
+        // the chunk's results into one block that one copy brings back (on the chunk's stream:
+        // the next chunk's solve runs on the other one)
         CK(launch_cand_pair(mc, k, K, s->idx_dev + (size_t)j0 * k, s->x_dev, s->qblk + (size_t)j0 * k * k,
-                            s->topk + (size_t)j0 * K, s->pair + (size_t)j0 * K, s->side));
-        CK(cudaMemcpyAsync(s->topk_h + (size_t)j0 * K, s->topk + (size_t)j0 * K, (size_t)mc * K * sizeof(uint64_t),
-                           cudaMemcpyDeviceToHost, s->side));
-        CK(cudaMemcpyAsync(s->pair_h + (size_t)j0 * K, s->pair + (size_t)j0 * K, (size_t)mc * K * sizeof(double),
-                           cudaMemcpyDeviceToHost, s->side));
-        CK(cudaMemcpyAsync(s->expect_h + j0, s->expect + j0, (size_t)mc * sizeof(double), cudaMemcpyDeviceToHost, s->side));
-        CK(cudaMemcpyAsync(s->status_h + ch, static_cast<char*>(s->plans[ch]->dev) + PLAN_STATUS_SLOT * sizeof(int),
-                           sizeof(unsigned), cudaMemcpyDeviceToHost, s->side));
-        CK(cudaEventRecord(s->chunk_done[ch], s->side));
+                            s->topk + (size_t)j0 * K, reinterpret_cast<double*>(s->pk_dev + s->pk_off[ch]), cs,
+                            s->expect + j0,
+                            reinterpret_cast<const unsigned*>(static_cast<char*>(s->plans[ch]->dev) +
+                                                              PLAN_STATUS_SLOT * sizeof(int))));
+        CK(cudaMemcpyAsync(s->pk_h + s->pk_off[ch], s->pk_dev + s->pk_off[ch], cand_pack_bytes(mc, K),
+                           cudaMemcpyDeviceToHost, cs));
+        CK(cudaEventRecord(s->chunk_done[ch], cs));
     }
+    for (int ch = 0; ch < s->chunks; ++ch) CK(cudaStreamWaitEvent(s->side, s->chunk_done[ch], 0));
     CK(cudaEventRecord(s->dev_end, s->side));
     if (s->chunks == 2) CK(cudaStreamWaitEvent(st, s->chunk_solved[1], 0));   // the caller's stream covers the cycle
     CK(cudaEventRecord(s->solve_end, st));
+    CK(cudaStreamWaitEvent(st, s->dev_end, 0));
     const double t1 = now_ms();
     if (s->method == DQAOA_RANDOM) {   // overlaps the device work of this cycle
         s->next_idx.resize((size_t)m * k);
@@ -1569,7 +1580,11 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
     s->cache.chg.assign((size_t)N, 0);
     for (int ch = 0; ch < s->chunks; ++ch) {
         CK(cudaEventSynchronize(s->chunk_done[ch]));
-        if (s->status_h[ch]) {
+        const int mcc = s->chunk_start[ch + 1] - s->chunk_start[ch];
+        const double* pair_c = reinterpret_cast<const double*>(s->pk_h + s->pk_off[ch]);
+        const uint64_t* cand_c = reinterpret_cast<const uint64_t*>(pair_c + (size_t)mcc * K);
+        const unsigned status_c = *reinterpret_cast<const unsigned*>(reinterpret_cast<const double*>(cand_c + (size_t)mcc * K) + mcc);
+        if (status_c) {
             // a device-side wait of this chunk ran out: its results are not valid, x is left as is
             cudaStreamSynchronize(st);
             return fail(QAOA_E_TIMEOUT, "session_cycle: a device-side wait of chunk %d ran out of time", ch);
@@ -1577,13 +1592,14 @@ extern "C" qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, in
         const double tm = now_ms();
         const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
         int acc = 0;
-        merge(Q, N, x, mc, k, s->idx_h + (size_t)j0 * k, K, s->topk_h + (size_t)j0 * K, energy_out, &acc,
-              &s->cache, s->qblk_h + (size_t)j0 * k * k, s->pair_h + (size_t)j0 * K);
+        merge(Q, N, x, mc, k, s->idx_h + (size_t)j0 * k, K, cand_c, energy_out, &acc, &s->cache,
+              s->qblk_h + (size_t)j0 * k * k, pair_c);
         accepted += acc;
         t_merge += now_ms() - tm;
     }
     CK(cudaStreamSynchronize(st));
     if (accepted_out) *accepted_out = accepted;
+    s->last_sampled = false;
     s->x_last.assign(x, x + N);
     s->t_decompose = t1 - t0;
     s->t_merge = t_merge;
@@ -1612,8 +1628,16 @@ extern "C" qaoa_status dqaoa_session_solve_ms(dqaoa_session* s, double* ms) {
 
 extern "C" qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk) {
     if (!s) return fail(QAOA_E_INVALID, "session is NULL");
-    if (expect) std::memcpy(expect, s->expect_h, (size_t)s->m * sizeof(double));
-    if (topk) std::memcpy(topk, s->topk_h, (size_t)s->m * s->K * sizeof(uint64_t));
+    if (expect && s->last_sampled) std::memcpy(expect, s->expect_h, (size_t)s->m * sizeof(double));
+    for (int ch = 0; ch < s->chunks; ++ch) {
+        // the packed block of each chunk: pair terms, candidates, <C>
+        const int j0 = s->chunk_start[ch], mc = s->chunk_start[ch + 1] - j0;
+        const double* pair_c = reinterpret_cast<const double*>(s->pk_h + s->pk_off[ch]);
+        const uint64_t* cand_c = reinterpret_cast<const uint64_t*>(pair_c + (size_t)mc * s->K);
+        const double* ex_c = reinterpret_cast<const double*>(cand_c + (size_t)mc * s->K);
+        if (expect && !s->last_sampled) std::memcpy(expect + j0, ex_c, (size_t)mc * sizeof(double));
+        if (topk) std::memcpy(topk + (size_t)j0 * s->K, cand_c, (size_t)mc * s->K * sizeof(uint64_t));
+    }
     return QAOA_OK;
 }
 
@@ -1696,6 +1720,7 @@ extern "C" qaoa_status dqaoa_session_cycle_sampled(dqaoa_session* s, const doubl
     const double t1 = now_ms();
     CK(cudaStreamSynchronize(st));
     s->s_last_shots = shots;
+    s->last_sampled = true;
     if (*s->s_status_h) return fail(QAOA_E_TIMEOUT, "session_cycle_sampled: a device-side wait ran out of time");
     s->cache.valid = s->cache.valid && !q_changed && s->x_last.size() == (size_t)N &&
                      std::memcmp(s->x_last.data(), x, (size_t)N) == 0;
@@ -1744,6 +1769,8 @@ extern "C" void dqaoa_session_destroy(dqaoa_session* s) {
     if (s->solve2) cudaStreamDestroy(s->solve2);
     if (s->side) cudaStreamDestroy(s->side);
     qaoa_plan_destroy(s->s_plan);
+    cudaFree(s->pk_dev);
+    if (s->pk_h) cudaFreeHost(s->pk_h);
     cudaFree(s->s_dev);
     cudaFree(s->s_shot_dev);
     if (s->s_best_h) cudaFreeHost(s->s_best_h);

@@ -49,9 +49,14 @@ int merge_setup_blocks(int N);
 // device set-up: scratch holds 2 * merge_setup_blocks(N) * N doubles; h, colabs: N doubles each
 cudaError_t launch_merge_setup(const double* Q, int N, const uint8_t* x, double* scratch, double* h,
                                double* colabs, cudaStream_t st);
-// pair terms of m*K candidates against x (device): idx m*k, qblk m*k*k, cand m*K, pair m*K
+// pair terms of m*K candidates against x (device): idx m*k, qblk m*k*k, cand m*K, pair m*K.
+// With expect and status given, pair is the start of a packed block: m*K pair terms, then the
+// m*K candidates, the m <C> values (copied from expect) and the status word (from *status).
 cudaError_t launch_cand_pair(int m, int k, int K, const int32_t* idx, const uint8_t* x, const double* qblk,
-                             const uint64_t* cand, double* pair, cudaStream_t st);
+                             const uint64_t* cand, double* pair, cudaStream_t st, const double* expect = nullptr,
+                             const unsigned* status = nullptr);
+// bytes of the packed block of m sub-QUBOs with K candidates each
+inline size_t cand_pack_bytes(int m, int K) { return ((size_t)m * K * 16 + (size_t)m * 8 + 16 + 255) & ~(size_t)255; }
 cudaError_t launch_subqubo(const double* Q, int N, const uint8_t* x, int m, int k,
                            const int32_t* idx, int conditioned, float* qsub, cudaStream_t st,
                            double* qblk = nullptr, double* qdiag = nullptr);
