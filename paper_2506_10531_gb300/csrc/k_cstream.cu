@@ -84,6 +84,23 @@ __host__ __device__ inline CsOff cs_offsets(int tpc) {
     return o;
 }
 
+// Rank selection of the CTAs' merged lists (probability descending, index ascending; empty
+// entries rank last): like rank_select, with the comparison loop unrolled so that its shared
+// loads are in flight together.
+__device__ __forceinline__ void cs_rank_select(const TopEnt* cand, int count, int k, TopEnt* out) {
+    for (int c = threadIdx.x; c < count; c += blockDim.x) {
+        const TopEnt me = cand[c];
+        if (!is_entry(me.p)) continue;
+        int rank = 0;
+#pragma unroll 8
+        for (int j = 0; j < count; ++j) {
+            const TopEnt o = cand[j];
+            rank += (is_entry(o.p) && better(o.p, o.z, me.p, me.z)) ? 1 : 0;
+        }
+        if (rank < k) out[rank] = me;
+    }
+}
+
 // ---- register windows of a kind-A tile -------------------------------------------------------
 // W2: bits [8, 13). Thread t owns u = t | (i << 8), i < 32: psw(u) = psw(t) + (i << 8) and the
 // energy of u is at t + (i << 8).
@@ -281,10 +298,11 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
     const TileRef<float> tile{sp, nullptr, sE, TB};
 
     // Two instance slots per cluster, run in alternating steps: step j runs one pass of slot
-    // j % 2. A step ends with its bulk stores complete, a wait for the cluster barrier phase of
-    // step j - 1 and an arrival for step j, so the data a pass reads (written by the previous
-    // pass of the same slot, two steps earlier) is released by a phase that was waited for one
-    // step ago: the cluster barrier rarely stalls. Instances come from a fixed round-robin queue.
+    // j % 2. At the end of step j the stores of step j - 1 are complete and every CTA arrives at
+    // and waits for the cluster barrier phase of step j - 1, so the data a pass reads (written by
+    // the previous pass of the same slot, two steps earlier) is visible before its first tile is
+    // loaded, while step j's stores drain during step j + 1. Instances come from a fixed
+    // round-robin queue.
     int sidx[2], spass[2], sfin[2];
     int next = cid;
     auto refill = [&](int sl) {
@@ -293,11 +311,29 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
         spass[sl] = 0;
         sfin[sl] = -1;
         if (sidx[sl] >= 0) {
-            const CsInstDev& I = insts[sidx[sl]];
+            // the descriptor's fields in one round trip, then Q and the parameters in flight
+            // together (staged in the pass-0 scratch, which is free here)
+            const CsInstDev* Ip = insts + sidx[sl];
+            const int n = Ip->n, p = Ip->p;
+            const float* Qg = Ip->Q;
+            const float* gg = Ip->gamma;
+            const float* bg = Ip->beta;
             float* sQ = reinterpret_cast<float*>(sm + o.Q[sl]);
-            for (int i = threadIdx.x; i < I.n * I.n; i += NT) sQ[i] = I.Q[i];
-            set_layer_consts<float>(reinterpret_cast<LayerConst<float>*>(sm + o.lc[sl]), I.gamma, I.beta, I.p,
-                                    I.n, true);   // ends with a barrier
+            float* gst = reinterpret_cast<float*>(sm + o.escr);
+            float* bst = gst + 64;
+            const int nn = n * n;
+            const float q0 = (int)threadIdx.x < nn ? Qg[threadIdx.x] : 0.0f;
+            const float q1 = (int)threadIdx.x + NT < nn ? Qg[threadIdx.x + NT] : 0.0f;
+            if ((int)threadIdx.x < p) {
+                gst[threadIdx.x] = gg[threadIdx.x];
+                bst[threadIdx.x] = bg[threadIdx.x];
+            }
+            if ((int)threadIdx.x < nn) sQ[threadIdx.x] = q0;
+            if ((int)threadIdx.x + NT < nn) sQ[threadIdx.x + NT] = q1;
+            // thread l reads back only its own staged gamma_l, beta_l; the Q stores are ordered
+            // before their readers by the barriers that end set_layer_consts
+            set_layer_consts<float>(reinterpret_cast<LayerConst<float>*>(sm + o.lc[sl]), gst, bst, p, n,
+                                    true);
         }
     };
     refill(0);
@@ -328,8 +364,13 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                 double* cex = reinterpret_cast<double*>(sm + o.cex[sl]);
                 TopEnt* lists = reinterpret_cast<TopEnt*>(sm + o.lists[sl]);
                 if (threadIdx.x == 0 && I.expect) {
+                    // the C remote loads in flight together, then the sum in rank order
+                    double part[C];
+#pragma unroll
+                    for (int r = 0; r < C; ++r) part[r] = *cl.map_shared_rank(cex, r);
                     double acc = 0.0;
-                    for (int r = 0; r < C; ++r) acc += *cl.map_shared_rank(cex, r);
+#pragma unroll
+                    for (int r = 0; r < C; ++r) acc += part[r];
                     *I.expect = acc;
                 }
                 if (I.k > 0) {
@@ -337,7 +378,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                     for (int e = threadIdx.x; e < C * per; e += NT)
                         ts.cand[e] = cl.map_shared_rank(lists, e / per)[e % per];
                     __syncthreads();
-                    rank_select(ts.cand, C * per, I.k, ts.out);
+                    cs_rank_select(ts.cand, C * per, I.k, ts.out);
                     __syncthreads();
                     if (threadIdx.x < (unsigned)I.k) {
                         const TopEnt e = ts.out[threadIdx.x];
