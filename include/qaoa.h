@@ -76,15 +76,20 @@ size_t qaoa_workspace_bytes(int n, int dbl);
  *   QAOA_TIER_CSTREAM: cluster streaming (one thread-block cluster per instance runs all its
  *     passes through L2, tiles moved by TMA); 15 <= n <= 17, forward runs only (gradient
  *     instances use the streaming tier). QAOA_E_UNSUPPORTED if the device cannot run it.
+ *   QAOA_TIER_RESIDENT: only n <= 14 (always resident); `param` is the widest register window of
+ *     the forward sub-passes (5 qubits, or 4 for n <= 13; 0: the default, 4 for n <= 12 and 5
+ *     above): a block has 2^(n - window) threads, so 4 doubles the threads per instance.
  * The resident tier is always used for n <= 14. */
-enum { QAOA_TIER_AUTO = 0, QAOA_TIER_CLUSTER = 2, QAOA_TIER_STREAM = 3, QAOA_TIER_CSTREAM = 4 };
+enum { QAOA_TIER_AUTO = 0, QAOA_TIER_RESIDENT = 1, QAOA_TIER_CLUSTER = 2, QAOA_TIER_STREAM = 3,
+       QAOA_TIER_CSTREAM = 4 };
 qaoa_status qaoa_set_tier(qaoa_ctx* ctx, int n, int tier, int param);
 
 /* Autotuner (no counterpart in the paper). Times every kernel configuration that can run a
  * complex64 batch of `count` instances of (n, p) with top-k length k -- for 15 <= n <= 30 the
  * three variants of the streaming tier (param 0, 1, 2 above), for 15 <= n <= 18 also the cluster
  * tier with 13 or 14 local qubits per CTA, for 15 <= n <= 17 the cluster-streaming tier; for
- * n <= 14 the single (resident) configuration -- on synthetic inputs (best of 5 timed plan
+ * 6 <= n <= 14 the resident tier's register windows of 5 and (n <= 13) 4 qubits (the block sizes
+ * they imply); for n <= 5 the single configuration -- on synthetic inputs (best of 5 timed plan
  * launches on `stream`, CUDA events) and stores the fastest (tier, param) for (n, p) in the
  * context; plans created later use it unless qaoa_set_tier overrides n. best_ms (may be NULL):
  * the winning batch time. Synchronous; allocates temporary buffers. */

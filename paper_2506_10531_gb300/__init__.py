@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libqaoa.so")
 
 QAOA_OK, QAOA_E_INVALID, QAOA_E_NOMEM, QAOA_E_CUDA, QAOA_E_TIMEOUT, QAOA_E_UNSUPPORTED = range(6)
 QAOA_INST_GRAD = 1
-QAOA_TIER_AUTO, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM, QAOA_TIER_CSTREAM = 0, 2, 3, 4
+QAOA_TIER_AUTO, QAOA_TIER_RESIDENT, QAOA_TIER_CLUSTER, QAOA_TIER_STREAM, QAOA_TIER_CSTREAM = 0, 1, 2, 3, 4
 DQAOA_RANDOM, DQAOA_IFD, DQAOA_BFS, DQAOA_PFS = 0, 1, 2, 3
 DQAOA_SIGNED_IMPACT = 16   # or-ed with IFD / BFS / PFS: rank by impact ascending
 DQAOA_PAPER_MIXER = 32     # session: the printed mixer H_X = -sum X (beta -> -beta)

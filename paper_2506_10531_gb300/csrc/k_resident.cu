@@ -9,6 +9,8 @@
 //      above) and the k most probable bitstrings (the sub-solution of Section IV), fused into
 //      the last sub-pass,
 //   4. optionally runs the adjoint sweep for d<C>/d(gamma, beta) on the same shared tile.
+#include <algorithm>
+
 #include "qaoa_engine.cuh"
 #include "qaoa_kernels.h"
 
@@ -120,6 +122,13 @@ __device__ void adjoint_run(const InstDesc<T>& d, const Smem<T>& s) {
     __syncthreads();
 }
 
+// Forward register window of an n-qubit instance: rb, narrowed to rmax when asked unless a
+// window would then start above bit 9 (the engine's window starts are 0..9), at most n.
+__host__ __device__ inline int resident_window(int n, int rb, int rmax) {
+    const int r = (rmax < rb && n - rmax <= 9) ? rmax : rb;
+    return n < r ? n : r;
+}
+
 template <typename T, int R, int RA>
 __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
     using C = typename Num<T>::C;
@@ -178,10 +187,12 @@ __device__ void run_instance(const InstDesc<T>& d, unsigned char* sm) {
 }
 
 template <typename T>
-__device__ void dispatch_instance(const InstDesc<T>& d, unsigned char* sm) {
+__device__ void dispatch_instance(const InstDesc<T>& d, unsigned char* sm, int rmax) {
     constexpr int RBF = Num<T>::RB, RBA = Num<T>::RB_ADJ;
-    // register windows: RB (forward) and RB_ADJ (adjoint) qubits, fewer when n is smaller
-    const int rf = min(d.n, RBF), ra = min(d.n, RBA);
+    // register windows: RB (forward, or rmax when the launch asks for narrower windows that keep
+    // every window start within the engine's 0..9) and RB_ADJ (adjoint) qubits, fewer when n is
+    // smaller
+    const int rf = resident_window(d.n, RBF, rmax), ra = min(d.n, RBA);
     if (rf == RBF && ra == RBA) run_instance<T, RBF, RBA>(d, sm);
     else if (rf == 4 && ra == 4) run_instance<T, 4, 4>(d, sm);
     else if (rf == 3) run_instance<T, 3, 3>(d, sm);
@@ -193,11 +204,11 @@ __device__ void dispatch_instance(const InstDesc<T>& d, unsigned char* sm) {
 // with desc == nullptr the single instance `one` (passed by value) is run by block 0.
 template <typename T>
 __global__ void __launch_bounds__(512) k_resident(const InstDesc<T>* __restrict__ desc, int count,
-                                                  int* queue, const InstDesc<T> one) {
+                                                  int* queue, const InstDesc<T> one, int rmax) {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_next;
     if (desc == nullptr) {
-        if (blockIdx.x == 0) dispatch_instance<T>(one, sm);
+        if (blockIdx.x == 0) dispatch_instance<T>(one, sm, rmax);
         return;
     }
     for (;;) {
@@ -207,29 +218,29 @@ __global__ void __launch_bounds__(512) k_resident(const InstDesc<T>* __restrict_
         __syncthreads();
         if (ii >= count) break;
         const InstDesc<T> d = desc[ii];
-        dispatch_instance<T>(d, sm);
+        dispatch_instance<T>(d, sm, rmax);
         __syncthreads();
     }
 }
 
 }  // namespace
 
-int resident_threads(bool dbl, int n) {
-    const int R = dbl ? Num<double>::RB : Num<float>::RB;
+int resident_threads(bool dbl, int n, int rmax) {
+    const int R = resident_window(n, dbl ? Num<double>::RB : Num<float>::RB, rmax);
     const int g = (n > R) ? (1 << (n - R)) : 1;
     return g < 32 ? 32 : (g > 512 ? 512 : g);
 }
 
-size_t resident_smem_bytes(bool dbl, int n, int p, bool grad) {
+size_t resident_smem_bytes(bool dbl, int n, int p, bool grad, int rmax) {
     size_t off[12];
-    const int th = resident_threads(dbl, n);
+    const int th = resident_threads(dbl, n, rmax);
     return dbl ? smem_layout<double>(n, p, grad, th, off) : smem_layout<float>(n, p, grad, th, off);
 }
 
-int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad) {
+int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad, int rmax) {
     int nb = 0;
-    const int th = resident_threads(dbl, n);
-    const size_t sm = resident_smem_bytes(dbl, n, pmax, grad);
+    const int th = resident_threads(dbl, n, rmax);
+    const size_t sm = resident_smem_bytes(dbl, n, pmax, grad, rmax);
     // the occupancy query counts a block that needs more than 48 KB of dynamic shared memory only
     // once the kernel may use that much, so the limit is raised first (the launch sets it again)
     if (dbl) {
@@ -245,22 +256,22 @@ int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad) {
 }
 
 cudaError_t launch_resident(bool dbl, const void* desc, int count, int n, int pmax, bool grad,
-                            int* queue, int grid, cudaStream_t st, const void* one) {
-    const int th = resident_threads(dbl, n);
-    const size_t sm = resident_smem_bytes(dbl, n, pmax, grad);
+                            int* queue, int grid, cudaStream_t st, const void* one, int rmax) {
+    const int th = resident_threads(dbl, n, rmax);
+    const size_t sm = resident_smem_bytes(dbl, n, pmax, grad, rmax);
     cudaError_t e;
     if (dbl) {
         e = cudaFuncSetAttribute(k_resident<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         InstDesc<double> o{};
         if (one) o = *static_cast<const InstDesc<double>*>(one);
-        k_resident<double><<<grid, th, sm, st>>>(static_cast<const InstDesc<double>*>(desc), count, queue, o);
+        k_resident<double><<<grid, th, sm, st>>>(static_cast<const InstDesc<double>*>(desc), count, queue, o, rmax);
     } else {
         e = cudaFuncSetAttribute(k_resident<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         InstDesc<float> o{};
         if (one) o = *static_cast<const InstDesc<float>*>(one);
-        k_resident<float><<<grid, th, sm, st>>>(static_cast<const InstDesc<float>*>(desc), count, queue, o);
+        k_resident<float><<<grid, th, sm, st>>>(static_cast<const InstDesc<float>*>(desc), count, queue, o, rmax);
     }
     return cudaGetLastError();
 }

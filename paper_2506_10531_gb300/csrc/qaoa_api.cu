@@ -308,6 +308,14 @@ extern "C" qaoa_status qaoa_reserve(qaoa_ctx* c, size_t bytes) {
 extern "C" qaoa_status qaoa_set_tier(qaoa_ctx* c, int n, int tier, int param) {
     if (!c || n < 1 || n > NMAX) return fail(QAOA_E_INVALID, "set_tier: bad ctx or n");
     if (tier == QAOA_TIER_AUTO) { c->tier[n] = 0; c->cluster_L[n] = 0; return QAOA_OK; }
+    if (tier == QAOA_TIER_RESIDENT) {
+        if (n > RES_NMAX_F || !(param == 0 || (param == 4 && n <= 13) || param == 5))
+            return fail(QAOA_E_INVALID, "set_tier: resident needs n <= %d and a window of 5 qubits, or 4 for n <= 13 "
+                        "(0: default)", RES_NMAX_F);
+        c->tier[n] = tier;
+        c->cluster_L[n] = param;
+        return QAOA_OK;
+    }
     if (tier == QAOA_TIER_STREAM) {
         if (n <= RES_NMAX_F) return fail(QAOA_E_INVALID, "set_tier: n=%d is always resident", n);
         if (param < 0 || param > 2) return fail(QAOA_E_INVALID, "set_tier: streaming variant %d (0..2)", param);
@@ -406,7 +414,7 @@ struct qaoa_plan {
     size_t dev_bytes = 0;
     bool owns = true;             // dev was allocated by the plan (else caller memory)
     cudaGraphExec_t graph = nullptr;  // captured launch sequence (qaoa_plan_capture)
-    struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; };
+    struct ResGroup { int n, pmax, count; bool grad; size_t desc_off; int grid; int q_slot; int rmax; };
     struct CluGroup { int n, L, pmax, count; size_t desc_off; int clusters; };
     struct CsGroup { int n, count; size_t desc_off; int clusters; };
     struct StrGroup { int n, p, k, count; bool grad; size_t inst_off; std::vector<StreamPass> passes;
@@ -530,7 +538,8 @@ qaoa_status plan_create_t(qaoa_ctx* c, const qaoa_inst* desc, int count, const q
             rdesc.push_back(make_desc(i));
         }
         hdr = align256(hdr + sizeof(InstDesc<T>) * g.count);
-        const int occ = std::max(1, resident_max_blocks_per_sm(dbl, g.n, g.pmax, g.grad));
+        g.rmax = dbl ? RES_RMAX : eff_resident_rmax(c, g.n, g.pmax);
+        const int occ = std::max(1, resident_max_blocks_per_sm(dbl, g.n, g.pmax, g.grad, g.rmax));
         g.grid = std::min(g.count, occ * c->nsm);
         P->res.push_back(g);
     }
@@ -1024,7 +1033,7 @@ qaoa_status plan_enqueue(qaoa_plan* P, cudaStream_t st) {
         CK(cudaMemsetAsync(counters + g.q_slot, 0, sizeof(int), st));
         CK(timed("resident", [&] {
             return launch_resident(P->dbl, base + g.desc_off, g.count, g.n, g.pmax, g.grad,
-                                   counters + g.q_slot, g.grid, st);
+                                   counters + g.q_slot, g.grid, st, nullptr, g.rmax);
         }));
     }
     for (auto& g : P->clu)

@@ -4,6 +4,7 @@
 #include <stddef.h>
 
 #include "../../include/qaoa.h"
+#include "qaoa_kernels.h"
 
 // One autotuned choice for complex64 batches of (n, p): the kernel tier and, for the cluster
 // tier, the local qubits per CTA; ms is the measured batch time it won with.
@@ -38,6 +39,15 @@ inline int eff_tier(const qaoa_ctx* c, int n, int p) {
 // The cluster-streaming tier can run n-qubit instances on the context's device (tensor-map
 // encoder found, a cluster of its shape fits); cached per n.
 bool cstream_usable(qaoa_ctx* c, int n);
+// Widest forward register window of the resident tier (complex64) for (n, p): qaoa_set_tier's
+// param with QAOA_TIER_RESIDENT, else the autotuner's choice, else 4 qubits for n <= 12 (twice
+// the threads per instance: measured on GB300 6-17% faster for batches of n = 8..12) and 5 above
+// (n = 14: 12% slower with 4).
+inline int eff_resident_rmax(const qaoa_ctx* c, int n, int p) {
+    if (c->tier[n] == QAOA_TIER_RESIDENT && c->cluster_L[n]) return c->cluster_L[n];
+    if (p >= 1 && p <= 64 && c->tuned[n][p].tier == QAOA_TIER_RESIDENT && c->tuned[n][p].L) return c->tuned[n][p].L;
+    return n <= 12 ? 4 : RES_RMAX;
+}
 // Variant of the HBM-streaming tier's forward passes: 0 TMA passes with two CTAs per SM, 1 TMA
 // passes with one CTA per SM, 2 the per-thread cp.async passes (qaoa_set_tier's param, else the
 // autotuner's, else 0).

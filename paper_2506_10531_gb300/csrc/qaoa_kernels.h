@@ -40,14 +40,18 @@ struct InstDesc {
 constexpr int RES_NMAX_F = 14, RES_NMAX_F_ADJ = 13;
 constexpr int RES_NMAX_D = 13, RES_NMAX_D_ADJ = 12;
 
-size_t resident_smem_bytes(bool dbl, int n, int p, bool grad);
-int resident_threads(bool dbl, int n);
+// rmax: widest forward register window (qubits) a launch uses; the block has 2^(n - window)
+// threads (32..512), so a narrower window means more threads per instance.
+constexpr int RES_RMAX = 8;   // no narrowing
+size_t resident_smem_bytes(bool dbl, int n, int p, bool grad, int rmax = RES_RMAX);
+int resident_threads(bool dbl, int n, int rmax = RES_RMAX);
 // Launch a resident-tier kernel over `count` device descriptors (all with the same n).
 // queue: device int zeroed by the caller before the launch (work counter). With desc ==
 // nullptr the host descriptor `one` is passed by value and run by one block.
 cudaError_t launch_resident(bool dbl, const void* desc, int count, int n, int pmax, bool grad,
-                            int* queue, int grid, cudaStream_t st, const void* one = nullptr);
-int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad);
+                            int* queue, int grid, cudaStream_t st, const void* one = nullptr,
+                            int rmax = RES_RMAX);
+int resident_max_blocks_per_sm(bool dbl, int n, int pmax, bool grad, int rmax = RES_RMAX);
 
 // ---- cluster tier: one cluster of 2^(n-L) CTAs per complex64 instance (15 <= n <= 18) ----
 constexpr int CL_NMIN = 15, CL_NMAX = 18;

@@ -6,7 +6,8 @@
 // HBM-streaming tier's three forward-pass variants (TMA passes with two CTAs per SM or one, the
 // per-thread cp.async passes); for 15 <= n <= 18 also the DSMEM cluster tier with 13 or 14 local
 // qubits per CTA (2^(n-L) CTAs per cluster, at most 16); for 15 <= n <= 17 the cluster-streaming
-// tier. Plans created afterwards use the stored choice unless qaoa_set_tier
+// tier; for 6 <= n <= 14 the resident tier with forward register windows of 5 qubits or (n <= 13)
+// 4 qubits (blocks of 2^(n-5) or 2^(n-4) threads). Plans created afterwards use the stored choice unless qaoa_set_tier
 // overrides it. The table is saved and loaded as a small JSON document, so a sweep done once
 // per machine can be reused (the offline sweep / online cache split).
 #include <cuda_runtime.h>
@@ -69,6 +70,9 @@ extern "C" qaoa_status qaoa_autotune(qaoa_ctx* c, int n, int p, int k, int count
             for (int L = 14; L >= 13; --L)
                 if (n - L >= 1 && n - L <= 4) cand.push_back({QAOA_TIER_CLUSTER, L});
         for (int v = 0; v <= 2; ++v) cand.push_back({QAOA_TIER_STREAM, v});
+    } else if (n >= 6) {
+        cand.push_back({QAOA_TIER_RESIDENT, 5});
+        if (n <= 13) cand.push_back({QAOA_TIER_RESIDENT, 4});
     } else {
         cand.push_back({0, 0});   // one configuration: time it, store nothing
     }
@@ -210,8 +214,9 @@ extern "C" qaoa_status qaoa_tuning_load(qaoa_ctx* c, const char* path) {
         double ms = 0.0;
         if (sscanf(text.c_str() + pos, "{\"n\": %d, \"p\": %d, \"tier\": %d, \"L\": %d, \"ms\": %lf, \"count\": %d, \"k\": %d}",
                    &n, &p, &tier, &L, &ms, &cnt, &k) == 7 &&
-            n >= 15 && n <= 30 && p >= 1 && p <= 64 &&
+            n >= 1 && n <= 30 && p >= 1 && p <= 64 && (tier == QAOA_TIER_RESIDENT || n >= 15) &&
             ((tier == QAOA_TIER_STREAM && L >= 0 && L <= 2) || (tier == QAOA_TIER_CSTREAM && n <= qaoa::CS_NMAX) ||
+             (tier == QAOA_TIER_RESIDENT && n <= 14 && ((L == 4 && n <= 13) || L == 5)) ||
              (tier == QAOA_TIER_CLUSTER && n <= 18 && n - L >= 1 && n - L <= 4 && L >= 10))) {
             qaoa_tuned& t = c->tuned[n][p];
             t.tier = tier;

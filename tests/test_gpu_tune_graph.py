@@ -52,8 +52,8 @@ def test_autotune_table_roundtrip(q, tmp_path):
         if tier == q.QAOA_TIER_CLUSTER:
             assert prm in (13, 14)
         assert q.qaoa_tuning_get(ctx, 16, 4)[0] == 0       # only the tuned shape is stored
-        ms_small = q.qaoa_autotune(ctx, 12, 2, 8, 64)       # one configuration: timed, not stored
-        assert ms_small > 0 and q.qaoa_tuning_get(ctx, 12, 2)[0] == 0
+        ms_small = q.qaoa_autotune(ctx, 5, 2, 8, 64)        # one configuration: timed, not stored
+        assert ms_small > 0 and q.qaoa_tuning_get(ctx, 5, 2)[0] == 0
         path = tmp_path / "tuning.json"
         q.qaoa_tuning_save(ctx, str(path))
         doc = json.loads(path.read_text())
@@ -172,5 +172,44 @@ def test_streaming_variants_agree_and_tune(q, tmp_path):
     try:
         q.qaoa_tuning_load(ctx, str(path))
         assert q.qaoa_tuning_get(ctx, 20, 2)[:2] == (tier, prm)
+    finally:
+        q.qaoa_destroy(ctx)
+
+
+def test_resident_window_variants_agree_and_tune(q):
+    # the resident tier with forward register windows of 5 and 4 qubits (blocks of 2^(n-5) and
+    # 2^(n-4) threads) gives the same results within rounding; the tuner stores one for n = 12
+    specs = [(12, 3, 8)] * 6 + [(9, 2, 8)] * 3 + [(13, 1, 8)] * 2
+    out = {}
+    for r in (5, 4):
+        ctx = q.qaoa_create(0)
+        try:
+            for n in (9, 12, 13):
+                q.qaoa_set_tier(ctx, n, q.QAOA_TIER_RESIDENT, r)
+            insts, io, _, (ex, ti, tp) = batch(q, specs, 61)
+            plan = q.qaoa_plan_create(ctx, insts, io)
+            try:
+                q.qaoa_plan_launch(plan)
+                torch.cuda.synchronize()
+            finally:
+                q.qaoa_plan_destroy(plan)
+            out[r] = (ex.cpu().numpy(), ti.cpu().numpy(), tp.cpu().numpy())
+        finally:
+            q.qaoa_destroy(ctx)
+    for i, (n, p, k) in enumerate(specs):
+        absq = float(np.abs(synth.symmetric_q(n, seed=61 + i)).sum())
+        assert abs(out[5][0][i] - out[4][0][i]) <= 2e-5 * absq, i
+        a, b = out[5][2][i * 8:(i + 1) * 8], out[4][2][i * 8:(i + 1) * 8]
+        # probabilities of amplitudes within 1e-5 of each other: |dp| <= 2e-5 sqrt(p) + 1e-10
+        assert np.max(np.abs(a - b)) <= 2e-5 * np.sqrt(a.max()) + 1e-10, i
+    ctx = q.qaoa_create(0)
+    try:
+        with pytest.raises(q.QaoaError):
+            q.qaoa_set_tier(ctx, 12, q.QAOA_TIER_RESIDENT, 3)
+        with pytest.raises(q.QaoaError):
+            q.qaoa_set_tier(ctx, 14, q.QAOA_TIER_RESIDENT, 4)   # a window would start at bit 10
+        ms = q.qaoa_autotune(ctx, 12, 3, 8, 256)
+        tier, prm, _ = q.qaoa_tuning_get(ctx, 12, 3)
+        assert ms > 0 and tier == q.QAOA_TIER_RESIDENT and prm in (4, 5)
     finally:
         q.qaoa_destroy(ctx)
