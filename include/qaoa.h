@@ -397,7 +397,8 @@ qaoa_status dqaoa_session_cycle(dqaoa_session* s, const double* Q, int q_changed
                                 uint64_t seed, uint64_t cycle, double* energy_out,
                                 int* accepted_out, qaoa_stream_t stream);
 /* Device work of the last cycle: per-sub-QUBO <C> (m doubles) and top-K indices (m*K uint64),
- * copied to host arrays (either may be NULL). */
+ * copied to host arrays (either may be NULL). A sampled cycle computes no top-K: after one,
+ * expect is its <C> and topk is still the last dqaoa_session_cycle's. */
 qaoa_status dqaoa_session_results(dqaoa_session* s, double* expect, uint64_t* topk);
 /* A cycle whose sub-solutions are read from measured shots, as Section IV reads the candidate
  * bitstring from a measurement of the optimised state (dqaoa_session_cycle takes the top-K

@@ -142,3 +142,46 @@ def test_session_sampled_cycle(q, orc, N, m, k, p, shots):
     np.testing.assert_array_equal(x2, xo2)
     assert acc2 == ao2
     assert e2 == pytest.approx(eo2, abs=1e-9 * np.abs(Q).sum())
+
+
+def test_sampled_cycle_edges(q, orc):
+    # one shot per sub-QUBO (the shot is the candidate), a single-chunk session (m < 128) with
+    # the IFD decomposition and the paper's mixer sign, and a call with more shots than before
+    # (the shot buffers grow): merged x bit-exact with the oracle's merge of the chosen shots
+    N, m, k, p = 200, 20, 10, 2
+    Q = synth.symmetric_q(N, seed=91)
+    x0 = synth.bits(92, N)
+    g, b = [0.35, 0.6], [0.45, 0.3]
+    ctx = q.qaoa_create(0)
+    try:
+        s = q.dqaoa_session_create(ctx, N, m, k, p, 4, q.DQAOA_IFD | q.DQAOA_PAPER_MIXER, True, g, b)
+        x = x0.copy()
+        u1 = synth.uniform01(93, m).reshape(m, 1)
+        e1, a1 = q.dqaoa_session_cycle_sampled(s, Q, 1, x, 0, 0, u1)
+        z1, best1, psi1 = q.dqaoa_session_shots(s, m, k, 1, states=True)
+        x_after1 = x.copy()
+        u2 = synth.uniform01(94, m * 300).reshape(m, 300)
+        e2, a2 = q.dqaoa_session_cycle_sampled(s, Q, 0, x, 0, 1, u2)
+        z2, best2, _ = q.dqaoa_session_shots(s, m, k, 300)
+        q.dqaoa_session_destroy(s)
+    finally:
+        q.qaoa_destroy(ctx)
+    np.testing.assert_array_equal(best1, z1[:, 0])          # one shot: it is the candidate
+    idx1, qs1 = orc.decompose(Q, x0, m, k, 0, 0, method=orc.IFD, conditioned=True)
+    for j in range(m):                                      # the paper's mixer: mixer_sign = -1
+        E = orc.energies(qs1[j])
+        psi_o = orc.state(k, f32(g), f32(b), E, mixer_sign=-1)
+        assert np.max(np.abs(psi1[j].astype(np.complex128) - psi_o)) <= 1e-5, j
+    xo1, eo1, ao1 = orc.merge(Q, x0, idx1, best1.reshape(m, 1))
+    np.testing.assert_array_equal(x_after1, xo1)
+    assert a1 == ao1 and e1 == pytest.approx(eo1, abs=1e-9 * np.abs(Q).sum())
+    idx2, qs2 = orc.decompose(Q, xo1, m, k, 0, 1, method=orc.IFD, conditioned=True)
+    for j in range(m):
+        ys = np.unique(z2[j])
+        es = np.array([sub_energy(qs2[j], y, k) for y in ys])
+        order = np.lexsort((ys, es))
+        if len(ys) == 1 or es[order[1]] - es[order[0]] > 1e-9 * np.abs(qs2[j]).sum():
+            assert int(best2[j]) == int(ys[order[0]]), j
+    xo2, eo2, ao2 = orc.merge(Q, xo1, idx2, best2.reshape(m, 1))
+    np.testing.assert_array_equal(x, xo2)
+    assert a2 == ao2 and e2 == pytest.approx(eo2, abs=1e-9 * np.abs(Q).sum())
