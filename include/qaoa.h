@@ -428,10 +428,12 @@ qaoa_status dqaoa_session_timing(dqaoa_session* s, double* out);
  * the end of the last chunk's kernels (the chunks may overlap on the device). */
 qaoa_status dqaoa_session_solve_ms(dqaoa_session* s, double* ms);
 /* The batched plans the session launches, in order (for timing and kernel counts): the m
- * sub-QUBOs are solved in two chunks when m >= 128, else in one. The host merges the first chunk
- * while the device solves the second; the first holds ceil(0.65 m) sub-QUBOs rounded up to a
- * multiple of the instances whose tiles give each block of a streaming launch one tile (at most
- * m - 1). Returns NULL for i past the last plan. */
+ * sub-QUBOs are solved in two chunks when m >= 128, else in one, the second on its own stream
+ * (the two solves overlap on the device). The host merges the first chunk while the device
+ * solves the second; the first holds floor(11 m / 16) sub-QUBOs (floor(9 m / 16) for N > 4096)
+ * for the cluster-streaming tier,
+ * else ceil(0.65 m) rounded up to a multiple of the instances whose tiles give each block of a
+ * streaming launch one tile (at most m - 1). Returns NULL for i past the last plan. */
 qaoa_plan* dqaoa_session_plan(dqaoa_session* s, int i);
 void dqaoa_session_destroy(dqaoa_session* s);
 

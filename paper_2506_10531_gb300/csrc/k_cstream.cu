@@ -8,9 +8,9 @@
 // 120 GB/s per SM from L2), so the tier keeps the state in global memory and moves tiles
 // between L2 and shared memory, like the streaming tier. What differs is the order: the C CTAs
 // of one cluster run every pass of ONE instance, separated by cluster barriers, before taking
-// the next instance. With about 40 clusters in flight the working set (state and energies of
-// the instances in flight, 0.75-1.5 MiB each) stays far below the 126 MB L2, so the passes
-// read and write L2, not HBM, and the whole batch is one launch.
+// the next instance. With about 70 clusters of 4 CTAs in flight, two instances each, the working
+// set (state and energies of the instances in flight, 0.75-1.5 MiB each) stays below the 126 MB
+// L2, so the passes read and write L2, not HBM, and the whole batch is one launch.
 //
 // Passes (2^H tiles each, H = n - 13; CTA rank r takes tiles r, r + C, ...):
 //   kind A: tile bits 0..12 are qubits 0..12 (2^13 contiguous amplitudes);
@@ -47,6 +47,12 @@ namespace {
 using namespace tma;
 
 constexpr int TB = CS_TILE_BITS;
+// CTAs per cluster for a pass of `ntile` tiles (each CTA then takes ntile / C tiles per pass).
+// Measured on GB300 (batches of 128-256 instances): 4 CTAs beat 8 by 4-7% at n = 16 and 17 (twice
+// the clusters in flight, half the cluster barriers per tile), except where the instance count
+// falls just past a multiple of the slots in flight.
+constexpr int CS_CMAX = 4;
+__host__ __device__ constexpr int cs_cluster(int ntile) { return ntile < CS_CMAX ? ntile : CS_CMAX; }
 constexpr uint32_t TD = 1u << TB;
 constexpr int NT = 256;
 
@@ -270,7 +276,7 @@ template <int H>
 __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__ insts, int count,
                                                   unsigned* status) {
     constexpr int NTILE = 1 << H;                 // tiles per pass
-    constexpr int C = NTILE < 8 ? NTILE : 8;      // CTAs per cluster
+    constexpr int C = cs_cluster(NTILE);          // CTAs per cluster
     constexpr int TPC = NTILE / C;                // tiles per CTA per pass
     constexpr int CB = TB - H;                    // contiguous bits of a kind-B tile
     constexpr int NB = 1 << (CB - 8);             // kind-B groups per thread
@@ -604,7 +610,7 @@ template <int H>
 cudaError_t cs_launch_h(const void* insts, int count, int clusters, cudaStream_t st, int* max_clusters,
                         unsigned* status) {
     constexpr int NTILE = 1 << H;
-    constexpr int C = NTILE < 8 ? NTILE : 8;
+    constexpr int C = cs_cluster(NTILE);
     const size_t smem = cs_offsets(NTILE / C).total;
     cudaError_t e = cudaFuncSetAttribute(k_cstream<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -674,7 +680,7 @@ cudaError_t cstream_max_clusters(int n, int* out) {
     }
 }
 
-int cstream_cluster_size(int n) { return (1 << (n - TB)) < 8 ? (1 << (n - TB)) : 8; }
+int cstream_cluster_size(int n) { return cs_cluster(1 << (n - TB)); }
 
 // The four tensor maps of one instance: state and energies (2^n values each, 16-byte aligned)
 // as kind-A and kind-B tiles. Returns false if the driver refuses one of them.

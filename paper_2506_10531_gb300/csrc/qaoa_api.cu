@@ -1405,27 +1405,32 @@ extern "C" qaoa_status dqaoa_session_create(qaoa_ctx* c, int N, int m, int k, in
     for (int l = 0; l < p; ++l) { par[l] = (float)gamma[l]; par[p + l] = (float)(paper_mixer ? -beta[l] : beta[l]); }
     e = cudaMemcpy(s->params, par.data(), par.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { dqaoa_session_destroy(s); return cuda_fail(e, "session params upload"); }
-    // Two chunks from m = 128 on. The first takes about two thirds, rounded up to whole waves
-    // (instances whose tiles give every block of a streaming launch one tile), so that the merge
-    // left after the device finishes is short while the second chunk's device time still covers
-    // most of the first chunk's merge (measured on GB300 for 256 sub-QUBOs of n = 16: 190 / 66
-    // beats 152 / 104, 128 / 128 and 114 / 142 by 4-8%).
+    // Two chunks from m = 128 on, so that the host merges the first while the device solves the
+    // second. Streaming tier: about two thirds, rounded up to whole waves (instances whose tiles
+    // give every block of a launch one tile; measured on GB300 for 256 sub-QUBOs of n = 16: 190 /
+    // 66 beat 152 / 104, 128 / 128 and 114 / 142 by 4-8%). Cluster-streaming tier, whose two
+    // chunk launches overlap on the device: 11/16 of m for N <= 4096 (measured for 256
+    // sub-QUBOs at N = 1000: splits from 128 to 216 within 4%, 176 best, 232 8% slower), 9/16
+    // above (at N = 10^4 the merge costs about 0.8 of the solve).
     s->chunks = m >= 128 ? 2 : 1;
     int m0 = m;
     if (s->chunks == 2) {
-        int w = 1;
         const int tier = eff_tier(c, k, p);
         if (k >= CS_NMIN && k <= CS_NMAX && tier == QAOA_TIER_CSTREAM && cstream_usable(c, k)) {
-            // whole waves of clusters (one instance per cluster at a time)
-            int mc = 0;
-            cstream_max_clusters(k, &mc);
-            w = std::max(1, mc);
-        } else if (k >= 16 && (k > 18 || tier == QAOA_TIER_STREAM)) {
-            const int tiles = 1 << (k - stream_tile_bits(false));
-            w = std::max(1, 2 * c->nsm / tiles);
+            // the first chunk's merge should end before the second chunk's solve does: with the
+            // merge's cost growing with N (the update of h per flipped variable), a larger N
+            // takes a smaller first chunk
+            m0 = N <= 4096 ? (m * 11) / 16 : (m * 9) / 16;
+        } else {
+            int w = 1;
+            if (k >= 16 && (k > 18 || tier == QAOA_TIER_STREAM)) {
+                const int tiles = 1 << (k - stream_tile_bits(false));
+                w = std::max(1, 2 * c->nsm / tiles);
+            }
+            m0 = (m * 13 + 19) / 20;
+            m0 = (m0 + w - 1) / w * w;
         }
-        m0 = (m * 13 + 19) / 20;
-        m0 = std::min(m - 1, (m0 + w - 1) / w * w);
+        m0 = std::max(1, std::min(m - 1, m0));
     }
     s->chunk_start[1] = m0;
     s->chunk_start[2] = m;
