@@ -368,6 +368,9 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_pass(const StreamPass P, cons
         if (loads) {
             if (ok) ok = mbar_wait_bounded(&mbar[s], (parity >> s) & 1u);
             parity ^= 1u << s;
+            // the init pass loads only the energies, issued before the last tile's store had read
+            // the state buffer: that read must be over before this tile writes the buffer
+            if (P.init && k >= 1 && threadIdx.x == 0) bulk_wait_read();
         } else if (k >= 1 && threadIdx.x == 0) {
             bulk_wait_read();   // the buffer's earlier store has read it
         }
@@ -499,9 +502,10 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_pass(const StreamPass P, cons
             fence_async_smem();   // the sub-passes' shared writes before the next tile's TMA writes
             __syncthreads();
         }
-        // the next tile's load, once this tile's store has read the buffer
+        // the next tile's load, once this tile's store has read the buffer (the init pass loads
+        // only the energies, whose buffer the store does not read: at once)
         if (loads && k + 1 < nmine && threadIdx.x == 0 && ok) {
-            bulk_wait_read();
+            if (!P.init) bulk_wait_read();
             issue(k + 1);
         }
     }
