@@ -337,17 +337,22 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_pass(const StreamPass P, cons
     const bool store = !P.fin || !P.no_store;
     uint32_t parity = 0;   // bit s: parity of the next wait on stage s
     bool ok = true;
-    auto issue = [&](int k) {
+    // the energies first (their buffer is never stored from), then, once the last tile's store
+    // has read the state buffer (wait_store), the state
+    auto issue = [&](int k, bool wait_store) {
         const uint64_t q = first + (uint64_t)k * step;
         const int ii = (int)(q / ntiles);
         const uint64_t tau = q % ntiles;
         const int s = k % NSTAGE;
         const CUtensorMap* m = maps + (size_t)ii * T.maps_per_inst;
         mbar_expect_tx(&mbar[s], (P.init ? 0u : TD * 8) + (P.need_e ? TD * 4 : 0u));
-        if (!P.init) tile_load(T, m + T.map, stage0 + (size_t)s * TD, tau, &mbar[s]);
         if (P.need_e) tile_load(T, m + T.emap, estage0 + (size_t)s * TD, tau, &mbar[s]);
+        if (!P.init) {
+            if (wait_store) bulk_wait_read();
+            tile_load(T, m + T.map, stage0 + (size_t)s * TD, tau, &mbar[s]);
+        }
     };
-    if (loads && nmine > 0 && threadIdx.x == 0) issue(0);
+    if (loads && nmine > 0 && threadIdx.x == 0) issue(0, false);
     const float *cur_g = nullptr, *cur_b = nullptr;
     int cur_p = 0;
     TopEnt* run = reinterpret_cast<TopEnt*>(sm + o.run);
@@ -502,12 +507,9 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_pass(const StreamPass P, cons
             fence_async_smem();   // the sub-passes' shared writes before the next tile's TMA writes
             __syncthreads();
         }
-        // the next tile's load, once this tile's store has read the buffer (the init pass loads
-        // only the energies, whose buffer the store does not read: at once)
-        if (loads && k + 1 < nmine && threadIdx.x == 0 && ok) {
-            if (!P.init) bulk_wait_read();
-            issue(k + 1);
-        }
+        // the next tile's loads: the energies at once, the state once this tile's store has read
+        // the buffer (the init pass loads only the energies)
+        if (loads && k + 1 < nmine && threadIdx.x == 0 && ok) issue(k + 1, true);
     }
     if (threadIdx.x == 0) {
         bulk_wait_all();
@@ -568,17 +570,20 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_adj_pass(const StreamPass P, 
     const bool need_e = lam_first || P.ph_first || P.lb > P.la;
     uint32_t parity = 0;
     bool ok = true;
-    auto issue = [&](int k) {
+    // the energies first (never stored from), then, once the last tile's stores have read the
+    // state buffers (wait_store), psi and lam
+    auto issue = [&](int k, bool wait_store) {
         const uint64_t q = first + (uint64_t)k * step;
         const int ii = (int)(q / ntiles);
         const uint64_t tau = q % ntiles;
         const CUtensorMap* m = maps + (size_t)ii * T.maps_per_inst;
         mbar_expect_tx(mbar, TDA * 8 + (lam_first ? 0u : TDA * 8) + (need_e ? TDA * 4 : 0u));
+        if (need_e) tile_load(T, m + T.emap, sE, tau, mbar);
+        if (wait_store) bulk_wait_read();
         tile_load(T, m + T.map, spsi, tau, mbar);
         if (!lam_first) tile_load(T, m + T.map + 1, slam, tau, mbar);
-        if (need_e) tile_load(T, m + T.emap, sE, tau, mbar);
     };
-    if (nmine > 0 && threadIdx.x == 0) issue(0);
+    if (nmine > 0 && threadIdx.x == 0) issue(0, false);
     const float *cur_g = nullptr, *cur_b = nullptr;
     int cur_p = 0;
     const TileRef<float> tile{spsi, slam, sE, TSA_TB};
@@ -635,11 +640,9 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_adj_pass(const StreamPass P, 
             fence_async_smem();   // the sub-passes' shared writes before the next tile's TMA writes
             __syncthreads();
         }
-        // the next tile's loads, once this tile's stores have read the buffers
-        if (k + 1 < nmine && threadIdx.x == 0 && ok) {
-            bulk_wait_read();
-            issue(k + 1);
-        }
+        // the next tile's loads: the energies at once, psi and lam once this tile's stores have
+        // read the buffers
+        if (k + 1 < nmine && threadIdx.x == 0 && ok) issue(k + 1, true);
     }
     if (threadIdx.x == 0) {
         bulk_wait_all();
