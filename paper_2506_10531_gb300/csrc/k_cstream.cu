@@ -344,17 +344,17 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
     };
     refill(0);
     refill(1);
-    // thread 0: TMA load of tile tau of a pass of instance I into the buffers
-    const auto issue_load = [&](const CsInstDev& I, bool kindA, uint32_t tau) {
+    // thread 0: TMA load of tile tau of a pass of instance I into the buffers: the energies at
+    // once (no store of a pass > 0 reads their buffer), the state once the last tile's store has
+    // read the state buffer (wait_store)
+    const auto issue_load = [&](const CsInstDev& I, bool kindA, uint32_t tau, bool wait_store) {
         fence_async_global();
         mbar_expect_tx(mbar, TD * 8 + TD * 4);
-        if (kindA) {
-            tma_load_4d(sp, &I.maps[0], 0, 0, 0, (int)tau, mbar);
-            tma_load_3d(sE, &I.maps[2], 0, 0, (int)tau, mbar);
-        } else {
-            tma_load_4d(sp, &I.maps[1], 0, 0, (int)tau, 0, mbar);
-            tma_load_4d(sE, &I.maps[3], 0, 0, (int)tau, 0, mbar);
-        }
+        if (kindA) tma_load_3d(sE, &I.maps[2], 0, 0, (int)tau, mbar);
+        else tma_load_4d(sE, &I.maps[3], 0, 0, (int)tau, 0, mbar);
+        if (wait_store) bulk_wait_read();
+        if (kindA) tma_load_4d(sp, &I.maps[0], 0, 0, 0, (int)tau, mbar);
+        else tma_load_4d(sp, &I.maps[1], 0, 0, (int)tau, 0, mbar);
     };
     bool prefetched = false;   // the first tile of this step was loaded at the end of the last one
 
@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                     }
                 }
             }
+            fence_async_smem();   // the merge's writes to the energy tile before a TMA load refills it
             __syncthreads();
             refill(sl);
         }
@@ -410,11 +411,14 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                 const uint32_t tau = rank + (uint32_t)(jt * C);
                 float accp = 0.0f, pmax = -1.0f;   // final pass: FP32 <C> terms (32 per thread) and max |psi|^2
                 // the bulk stores of the previous tile have read the buffers before they are
-                // refilled (by TMA in passes > 0, by the threads in pass 0)
-                if (threadIdx.x == 0) bulk_wait_read();
-                if (pass == 0 && jt > 0) __syncthreads();
+                // refilled (by the threads in pass 0, by TMA in passes > 0, whose load waits for
+                // them itself; the first tile of a step follows the end-of-step wait)
+                if (pass == 0 && jt > 0) {
+                    if (threadIdx.x == 0) bulk_wait_read();
+                    __syncthreads();
+                }
                 if (pass > 0) {
-                    if (threadIdx.x == 0 && ok && !(jt == 0 && prefetched)) issue_load(I, kindA, tau);
+                    if (threadIdx.x == 0 && ok && !(jt == 0 && prefetched)) issue_load(I, kindA, tau, jt > 0);
                     if (ok) ok = mbar_wait_bounded(mbar, parity);
                     ok = __syncthreads_and(ok);
                     parity ^= 1u;
@@ -551,6 +555,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                             stored = true;
                         }
                     }
+                    fence_async_smem();   // the top-k scratch writes before the next tile's TMA writes
                     __syncthreads();
                 }
             }
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
         {
             const int ns = (j + 1) & 1;
             prefetched = sidx[ns] >= 0 && sfin[ns] < 0 && spass[ns] > 0;
-            if (prefetched && threadIdx.x == 0 && ok) issue_load(insts[sidx[ns]], (spass[ns] & 1) == 0, rank);
+            if (prefetched && threadIdx.x == 0 && ok) issue_load(insts[sidx[ns]], (spass[ns] & 1) == 0, rank, false);
         }
     }
     // The loop ends at the start of a step j in which rank 0 may have just read every rank's
