@@ -61,10 +61,11 @@ constexpr int NT = 256;
 // doubles as the top-k scratch of the final pass (after the <C> partial has read it) and of the
 // merge on rank 0. Per slot: Q, layer constants, the CTA's top-k lists and <C> partial.
 struct CsOff {
-    size_t psi, E, red, escr, wbound, Q[2], lc[2], lists[2], cex[2], mbar, total;
+    size_t psi, E, red, escr, wbound, Q[2], lc[2], lists[2], cex[2], desc[2], mbar, total;
     size_t wb, cnt, cand, out, wlists;   // inside the energy tile
 };
 __host__ __device__ inline size_t cs_al(size_t x) { return (x + 15) & ~(size_t)15; }
+constexpr size_t CS_DESC_BYTES = 128;   // a slot's copy of its instance descriptor
 __host__ __device__ inline CsOff cs_offsets(int tpc) {
     CsOff o{};
     size_t x = 0;
@@ -78,6 +79,7 @@ __host__ __device__ inline CsOff cs_offsets(int tpc) {
         o.lc[s] = x; x = cs_al(x + 64 * sizeof(LayerConst<float>));
         o.lists[s] = x; x = cs_al(x + (size_t)tpc * 16 * sizeof(TopEnt));
         o.cex[s] = x; x = cs_al(x + sizeof(double));
+        o.desc[s] = x; x = cs_al(x + CS_DESC_BYTES);
     }
     o.mbar = x; x = cs_al(x + sizeof(uint64_t));
     o.total = x + 1024;                                    // room to align psi to 1024 bytes
@@ -186,6 +188,7 @@ struct CsInstDev {
     double* topk_prob;
     const CUtensorMap* maps;   // psi kind A, psi kind B, E kind A, E kind B
 };
+static_assert(sizeof(CsInstDev) <= CS_DESC_BYTES && sizeof(CsInstDev) % 8 == 0, "descriptor copy");
 
 // Energies of kind-A tile tau of pass 0 in the W2 layout (thread t owns u = t | j << 8), with
 // the tile's fixed global bits S = tau << 13. With P_ik = Q_ik + Q_ki (i < k, tile qubits),
@@ -194,9 +197,8 @@ struct CsInstDev {
 //   W_b(t) = sum_{i<8} t_i P_{i,8+b},   Eh[j] = sum_{b in j} d_{8+b} + sum_{b<c in j} P_{8+b,8+c},
 // every pair of set bits of z counted once with both Q_ik and Q_ki. The tables (scr: 256 floats)
 // are built once per tile; each thread's sums are unrolled with 0/1 weights (independent loads,
-// no serial chains). ev[j] receives the energies, also written to sE (unswizzled).
-__device__ __forceinline__ void w2_energies(int n, uint32_t zfix, const float* Qs, float* scr, float* sE,
-                                            float (&ev)[32]) {
+// no serial chains). ev[j] receives the energies (the caller writes them to the energy tile).
+__device__ __forceinline__ void w2_energies(int n, uint32_t zfix, const float* Qs, float* scr, float (&ev)[32]) {
     float* P = scr;           // 13 x 13, upper triangle
     float* d = scr + 169;     // 13
     float* Eh = scr + 184;    // 32
@@ -266,10 +268,7 @@ __device__ __forceinline__ void w2_energies(int n, uint32_t zfix, const float* Q
 #pragma unroll
         for (int m = 0; m < (1 << bb); ++m) X[m | (1 << bb)] = X[m] + W[bb];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        ev[j] = base + (Eh[j] + X[j]);
-        sE[t + ((uint32_t)j << 8)] = ev[j];
-    }
+    for (int j = 0; j < 32; ++j) ev[j] = base + (Eh[j] + X[j]);
 }
 
 template <int H>
@@ -320,6 +319,11 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
             // the descriptor's fields in one round trip, then Q and the parameters in flight
             // together (staged in the pass-0 scratch, which is free here)
             const CsInstDev* Ip = insts + sidx[sl];
+            // the slot's shared copy of the descriptor, read by every step and prefetch of the
+            // instance (ordered before them by the barriers that end set_layer_consts)
+            if (threadIdx.x < sizeof(CsInstDev) / 8)
+                reinterpret_cast<unsigned long long*>(sm + o.desc[sl])[threadIdx.x] =
+                    reinterpret_cast<const unsigned long long*>(Ip)[threadIdx.x];
             const int n = Ip->n, p = Ip->p;
             const float* Qg = Ip->Q;
             const float* gg = Ip->gamma;
@@ -366,7 +370,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
             // the instance of this slot finished two steps ago (its final pass is visible to the
             // cluster): rank 0 merges the CTAs' <C> partials (rank order) and top-k lists
             if (rank == 0) {
-                const CsInstDev& I = insts[sidx[sl]];
+                const CsInstDev& I = *reinterpret_cast<const CsInstDev*>(sm + o.desc[sl]);
                 double* cex = reinterpret_cast<double*>(sm + o.cex[sl]);
                 TopEnt* lists = reinterpret_cast<TopEnt*>(sm + o.lists[sl]);
                 if (threadIdx.x == 0 && I.expect) {
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
         }
         if (sidx[0] < 0 && sidx[1] < 0) break;
         if (sidx[sl] >= 0) {
-            const CsInstDev I = insts[sidx[sl]];
+            const CsInstDev& I = *reinterpret_cast<const CsInstDev*>(sm + o.desc[sl]);
             const float* sQ = reinterpret_cast<const float*>(sm + o.Q[sl]);
             const LayerConst<float>* lc = reinterpret_cast<const LayerConst<float>*>(sm + o.lc[sl]);
             TopEnt* lists = reinterpret_cast<TopEnt*>(sm + o.lists[sl]);
@@ -411,12 +415,9 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                 const uint32_t tau = rank + (uint32_t)(jt * C);
                 float accp = 0.0f, pmax = -1.0f;   // final pass: FP32 <C> terms (32 per thread) and max |psi|^2
                 // the bulk stores of the previous tile have read the buffers before they are
-                // refilled (by the threads in pass 0, by TMA in passes > 0, whose load waits for
-                // them itself; the first tile of a step follows the end-of-step wait)
-                if (pass == 0 && jt > 0) {
-                    if (threadIdx.x == 0) bulk_wait_read();
-                    __syncthreads();
-                }
+                // refilled (by TMA in passes > 0, whose load waits for them itself; by the threads
+                // in pass 0, once the tile's energies are in registers; the first tile of a step
+                // follows the end-of-step wait)
                 if (pass > 0) {
                     if (threadIdx.x == 0 && ok && !(jt == 0 && prefetched)) issue_load(I, kindA, tau, jt > 0);
                     if (ok) ok = mbar_wait_bounded(mbar, parity);
@@ -427,8 +428,14 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
                     if (pass == 0) {
                         // energies, |+>, the first cost phase and layer 0 on window [8, 13)
                         float ev[32];
-                        w2_energies(n, tau << TB, sQ, reinterpret_cast<float*>(sm + o.escr), sE, ev);
+                        w2_energies(n, tau << TB, sQ, reinterpret_cast<float*>(sm + o.escr), ev);
+                        if (jt > 0) {
+                            if (threadIdx.x == 0) bulk_wait_read();
+                            __syncthreads();
+                        }
                         const uint32_t t = threadIdx.x;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sE[t + ((uint32_t)i << 8)] = ev[i];
                         const int pc = __popc(tau) + __popc(t);
                         float2 v[32];
 #pragma unroll
@@ -591,7 +598,7 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
         {
             const int ns = (j + 1) & 1;
             prefetched = sidx[ns] >= 0 && sfin[ns] < 0 && spass[ns] > 0;
-            if (prefetched && threadIdx.x == 0 && ok) issue_load(insts[sidx[ns]], (spass[ns] & 1) == 0, rank, false);
+            if (prefetched && threadIdx.x == 0 && ok) issue_load(*reinterpret_cast<const CsInstDev*>(sm + o.desc[ns]), (spass[ns] & 1) == 0, rank, false);
         }
     }
     // The loop ends at the start of a step j in which rank 0 may have just read every rank's
