@@ -575,26 +575,25 @@ __global__ void __launch_bounds__(NT, 2) k_cstream(const CsInstDev* __restrict__
         }
         // end of step j. Step j's bulk stores drain while step j + 1 computes: here only step
         // j - 1's stores must be complete (every group but the newest when step j committed one,
-        // a group per stored tile, so step j - 1's are older; else all), and every store must have read
-        // the buffers (the next step's prefetch, or rank 0's merge in the energy tile, reuses
-        // them). Then the cluster phase of step j - 1 (arrive after those stores; wait: every
-        // CTA's step j - 1 data is complete) and the prefetch of the next step's first tile,
-        // which belongs to the slot step j - 1 advanced.
+        // a group per stored tile, so step j - 1's are older; else all) before the CTA arrives at
+        // the cluster phase of step j - 1. While that phase completes (wait: every CTA's step
+        // j - 1 data is complete), every store finishes reading the buffers, which the next
+        // step's prefetch of its first tile (the slot step j - 1 advanced), the pass-0 threads
+        // or rank 0's merge in the energy tile reuse once the barrier after the wait is passed.
         __syncthreads();
-        if (threadIdx.x == 0) {
-            bulk_wait_read();
-            if (j > 0) {
-                if (stored) bulk_wait_all_but_one();
-                else bulk_wait_all();   // step j stored nothing: the newest group may be step j - 1's
-                fence_async_global();
-            }
+        if (threadIdx.x == 0 && j > 0) {
+            if (stored) bulk_wait_all_but_one();
+            else bulk_wait_all();   // step j stored nothing: the newest group may be step j - 1's
+            fence_async_global();
         }
-        __syncthreads();
         if (j > 0) {
+            __syncthreads();
             if (threadIdx.x < 32) cluster_arrive_release();
             else cluster_arrive();
-            cluster_wait();
         }
+        if (threadIdx.x == 0) bulk_wait_read();
+        if (j > 0) cluster_wait();
+        __syncthreads();
         {
             const int ns = (j + 1) & 1;
             prefetched = sidx[ns] >= 0 && sfin[ns] < 0 && spass[ns] > 0;
