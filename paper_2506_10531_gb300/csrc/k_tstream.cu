@@ -293,6 +293,18 @@ __device__ __forceinline__ void tile_load(const TsPass& T, const CUtensorMap* ma
         default: tma_load_4d(dst, map, 0, mid, 0, 0, bar); break;
     }
 }
+// L2 prefetch of the tile tile_load would copy (a cache hint only)
+__device__ __forceinline__ void tile_prefetch(const TsPass& T, const CUtensorMap* map, uint64_t tau) {
+    const int mid = (int)(tau & ((1ull << T.midbits) - 1ull)), top = (int)(tau >> T.midbits);
+    switch (T.bmode) {
+        case TS_A: tma_prefetch_4d(map, 0, 0, 0, (int)tau); break;
+        case TS_A3: tma_prefetch_3d(map, 0, 0, (int)tau); break;
+        case TS_B5: tma_prefetch_5d(map, 0, 0, mid, 0, top); break;
+        case TS_B4: tma_prefetch_4d(map, 0, 0, mid, 0); break;
+        case TS_B9_5: tma_prefetch_5d(map, 0, mid, 0, 0, top); break;
+        default: tma_prefetch_4d(map, 0, mid, 0, 0); break;
+    }
+}
 __device__ __forceinline__ void tile_store(const TsPass& T, const CUtensorMap* map, const void* src, uint64_t tau) {
     const int mid = (int)(tau & ((1ull << T.midbits) - 1ull)), top = (int)(tau >> T.midbits);
     switch (T.bmode) {
@@ -335,6 +347,7 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_pass(const StreamPass P, cons
     const int nmine = first < total ? (int)((total - 1 - first) / step + 1) : 0;
     const bool loads = !P.init || P.need_e;   // the init pass loads only the energies
     const bool store = !P.fin || !P.no_store;
+    const bool pf = P.init || !store;
     uint32_t parity = 0;   // bit s: parity of the next wait on stage s
     bool ok = true;
     // the energies first (their buffer is never stored from), then, once the last tile's store
@@ -350,6 +363,14 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_pass(const StreamPass P, cons
         if (!P.init) {
             if (wait_store) bulk_wait_read();
             tile_load(T, m + T.map, stage0 + (size_t)s * TD, tau, &mbar[s]);
+        }
+        // the tile after it towards L2, a tile's compute ahead of its own load (in the passes
+        // that store no state: with the state stores in flight it slowed the others down)
+        if (pf && k + 1 < nmine) {
+            const uint64_t q1 = q + step;
+            const CUtensorMap* m1 = maps + (size_t)(q1 / ntiles) * T.maps_per_inst;
+            if (P.need_e) tile_prefetch(T, m1 + T.emap, q1 % ntiles);
+            if (!P.init) tile_prefetch(T, m1 + T.map, q1 % ntiles);
         }
     };
     if (loads && nmine > 0 && threadIdx.x == 0) issue(0, false);
@@ -582,6 +603,14 @@ __global__ void __launch_bounds__(NT, 2) k_tstream_adj_pass(const StreamPass P, 
         if (wait_store) bulk_wait_read();
         tile_load(T, m + T.map, spsi, tau, mbar);
         if (!lam_first) tile_load(T, m + T.map + 1, slam, tau, mbar);
+        // the tile after it towards L2, a tile's compute ahead of its own loads
+        if (k + 1 < nmine) {
+            const uint64_t q1 = q + step;
+            const CUtensorMap* m1 = maps + (size_t)(q1 / ntiles) * T.maps_per_inst;
+            if (need_e) tile_prefetch(T, m1 + T.emap, q1 % ntiles);
+            tile_prefetch(T, m1 + T.map, q1 % ntiles);
+            if (!lam_first) tile_prefetch(T, m1 + T.map + 1, q1 % ntiles);
+        }
     };
     if (nmine > 0 && threadIdx.x == 0) issue(0, false);
     const float *cur_g = nullptr, *cur_b = nullptr;
