@@ -333,8 +333,36 @@ static int merge_loop(const double* Q, int N, uint8_t* x, int m, int k_rt, const
                     const int var = S[nz[u]];
                     x[var] = (uint8_t)(d[u] > 0.0);
                     if (chg) chg[var] = 1;
-                    // column var of the symmetric Q == row var
-                    const double* __restrict__ row = Q + (int64_t)var * N;
+                }
+                // h += d_u * (column S[nz[u]] of the symmetric Q == its row) for u ascending:
+                // every h[l] takes the same adds in the same order as one row at a time, with
+                // eight, then four rows per sweep over h
+                int u = 0;
+                for (; u + 8 <= cnt; u += 8) {
+                    const double* __restrict__ r0 = Q + (int64_t)S[nz[u]] * N;
+                    const double* __restrict__ r1 = Q + (int64_t)S[nz[u + 1]] * N;
+                    const double* __restrict__ r2 = Q + (int64_t)S[nz[u + 2]] * N;
+                    const double* __restrict__ r3 = Q + (int64_t)S[nz[u + 3]] * N;
+                    const double* __restrict__ r4 = Q + (int64_t)S[nz[u + 4]] * N;
+                    const double* __restrict__ r5 = Q + (int64_t)S[nz[u + 5]] * N;
+                    const double* __restrict__ r6 = Q + (int64_t)S[nz[u + 6]] * N;
+                    const double* __restrict__ r7 = Q + (int64_t)S[nz[u + 7]] * N;
+                    const double d0 = d[u], d1 = d[u + 1], d2 = d[u + 2], d3 = d[u + 3];
+                    const double d4 = d[u + 4], d5 = d[u + 5], d6 = d[u + 6], d7 = d[u + 7];
+                    for (int l = 0; l < N; ++l)
+                        hq[l] = (((((((hq[l] + d0 * r0[l]) + d1 * r1[l]) + d2 * r2[l]) + d3 * r3[l]) + d4 * r4[l]) +
+                                  d5 * r5[l]) + d6 * r6[l]) + d7 * r7[l];
+                }
+                for (; u + 4 <= cnt; u += 4) {
+                    const double* __restrict__ r0 = Q + (int64_t)S[nz[u]] * N;
+                    const double* __restrict__ r1 = Q + (int64_t)S[nz[u + 1]] * N;
+                    const double* __restrict__ r2 = Q + (int64_t)S[nz[u + 2]] * N;
+                    const double* __restrict__ r3 = Q + (int64_t)S[nz[u + 3]] * N;
+                    const double d0 = d[u], d1 = d[u + 1], d2 = d[u + 2], d3 = d[u + 3];
+                    for (int l = 0; l < N; ++l) hq[l] = (((hq[l] + d0 * r0[l]) + d1 * r1[l]) + d2 * r2[l]) + d3 * r3[l];
+                }
+                for (; u < cnt; ++u) {
+                    const double* __restrict__ row = Q + (int64_t)S[nz[u]] * N;
                     const double du = d[u];
                     for (int l = 0; l < N; ++l) hq[l] += du * row[l];
                 }
